@@ -1,0 +1,98 @@
+"""Pins for the oracle's random initial field (SplitMix64, Box-Muller, spectrum).
+
+The initial condition is this project's reading of the paper's decaying HIT
+set-up (Sec. 1: r.m.s. Mach 0.2 / 0.5).  Pins are statistical (moments within
+sampling error, shell energies against their expectation) and exact
+(rescaled Mach number, spectral solenoidality).
+"""
+import math
+
+import numpy as np
+
+from oracle import ic
+
+
+def test_uniform_moments():
+    n = 1 << 20
+    u = ic.uniform01(ic.splitmix64(12345, np.arange(n, dtype=np.uint64)))
+    assert u.min() > 0.0 and u.max() <= 1.0
+    sig = math.sqrt(1 / 12 / n)
+    assert abs(u.mean() - 0.5) < 5 * sig
+    assert abs(u.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / n)
+    # lag-1 serial correlation of a good generator is ~N(0, 1/n)
+    c = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(c) < 5 / math.sqrt(n)
+
+
+def test_bits_balanced_and_streams_differ():
+    z = ic.splitmix64(7, np.arange(1 << 16, dtype=np.uint64))
+    for b in (0, 1, 17, 31, 32, 53, 62, 63):
+        frac = float(np.mean((z >> np.uint64(b)) & np.uint64(1)))
+        assert abs(frac - 0.5) < 5 * 0.5 / math.sqrt(1 << 16)
+    z2 = ic.splitmix64(8, np.arange(1 << 16, dtype=np.uint64))
+    assert np.count_nonzero(z == z2) == 0
+    assert len(np.unique(z)) == len(z)
+
+
+def test_gaussian_moments():
+    n = 1 << 19
+    m0 = np.arange(0, 2 * n, 2, dtype=np.uint64)
+    a, b = ic.gaussian_pair(99, m0)
+    x = np.concatenate([a, b])
+    N = x.size
+    assert abs(x.mean()) < 5 / math.sqrt(N)
+    assert abs(x.var() - 1) < 5 * math.sqrt(2 / N)
+    assert abs(np.mean(x ** 4) - 3) < 5 * math.sqrt(96 / N)
+    assert abs(np.mean(a * b)) < 5 / math.sqrt(n)
+
+
+def test_mach_and_solenoidal():
+    N = 32
+    u = ic.spectral_velocity(N, 4.0, 0.2, 3)
+    ms = np.mean(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    assert abs(math.sqrt(ms) - 0.2) < 1e-14
+    kk = np.fft.fftfreq(N, d=1.0 / N)
+    kz, ky, kx = np.meshgrid(kk, kk, kk, indexing="ij")
+    uh = [np.fft.fftn(c) for c in u]
+    div = kx * uh[0] + ky * uh[1] + kz * uh[2]
+    scale = max(np.max(np.abs(c)) for c in uh) * N
+    assert np.max(np.abs(div)) < 1e-12 * scale
+    # zero mean, no energy at k = 0
+    for c in u:
+        assert abs(c.mean()) < 1e-15
+
+
+def test_seed_changes_field_and_is_reproducible():
+    a = ic.spectral_velocity(16, 4.0, 0.5, 1)
+    b = ic.spectral_velocity(16, 4.0, 0.5, 1)
+    c = ic.spectral_velocity(16, 4.0, 0.5, 2)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert np.max(np.abs(a[0] - c[0])) > 0.05
+
+
+def test_shell_energies_match_expectation():
+    """Shell energy / its expectation = 1 within sampling error.
+
+    The expected energy of a kept mode is proportional to E(|k|)/(4 pi |k|^2)
+    (amplitude squared); the projected complex Gaussian has 2 degrees of
+    freedom of unit variance per mode; the shell sum of those expectations is
+    the reference, so the test does not depend on lattice shell counts.
+    """
+    N, k0 = 64, 4.0
+    u = ic.spectral_velocity(N, k0, 1.0, 11)
+    kk = np.fft.fftfreq(N, d=1.0 / N)
+    kz, ky, kx = np.meshgrid(kk, kk, kk, indexing="ij")
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    kmag = np.sqrt(k2)
+    shell = np.floor(kmag + 0.5).astype(int)
+    keep = (k2 > 0) & (kx != -N // 2) & (ky != -N // 2) & (kz != -N // 2)
+    dens = sum(np.abs(np.fft.fftn(c)) ** 2 for c in u)
+    expect = np.where(keep, ic.spectrum_model(kmag, k0) / (4 * np.pi * np.where(k2 > 0, k2, 1)), 0.0)
+    got_tot = dens.sum()
+    exp_tot = expect.sum()
+    for s in range(2, 12):
+        sel = shell == s
+        nmodes = int(np.count_nonzero(sel & keep))
+        r = (dens[sel].sum() / got_tot) / (expect[sel].sum() / exp_tot)
+        # 2 real dof per (k, -k) pair and component-projected: relative sd <= sqrt(2/nmodes)
+        assert abs(r - 1) < 5 * math.sqrt(2.0 / nmodes), (s, r, nmodes)

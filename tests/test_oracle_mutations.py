@@ -1,0 +1,144 @@
+"""The oracle's pins are sensitive: plausible mistakes planted in the oracle
+(on the CPU, through monkeypatching) make at least one pin fail.
+
+Each case names the mistake and the pin expected to catch it.
+"""
+import numpy as np
+import pytest
+
+from oracle import ops, piso
+
+from . import test_oracle_ops as t_ops
+from . import test_oracle_piso as t_piso
+from . import test_oracle_solve as t_solve
+
+
+def _bad_I4(f, d):
+    return (-ops.at(f, d, -1) + 9.0 * f + 9.0 * ops.at(f, d, 1) - ops.at(f, d, 2)) / 15.9
+
+
+def _bad_G4(f, d, h):
+    return (ops.at(f, d, -1) - 27.0 * f + 27.0 * ops.at(f, d, 1) - ops.at(f, d, 2)) / (26.0 * h)
+
+
+def _stress_no_dilatation(u, mu, h):
+    tau = [[None] * 3 for _ in range(3)]
+    for d in range(3):
+        for m in range(3):
+            tau[d][m] = mu * (ops.G4(u[m], d, h) + ops.I4(ops.Gc(u[d], m, h), d))
+    return tau
+
+
+def _stress_transposed(u, mu, h):
+    div = ops.Gc(u[0], 0, h) + ops.Gc(u[1], 1, h) + ops.Gc(u[2], 2, h)
+    tau = [[None] * 3 for _ in range(3)]
+    for d in range(3):
+        for m in range(3):
+            t = ops.G4(u[m], d, h) + ops.I4(ops.Gc(u[m], d, h), d)
+            if d == m:
+                t = t - (2.0 / 3.0) * ops.I4(div, d)
+            tau[d][m] = mu * t
+    return tau
+
+
+def _L_wrong_sign(u, phi, mu, h):
+    visc = ops.div_stress(u, mu, h)
+    return [ops.D([phi[d] * ops.I4(u[m], d) for d in range(3)], h) + visc[m] for m in range(3)]
+
+
+def _eos_no_gamma_division(prm, rho, T=None):
+    if prm.closure == piso.BAROTROPIC:
+        return rho ** prm.gamma
+    return rho * prm.R * T
+
+
+def _accel_wrong_sign(prm, rho, u, p):
+    visc = ops.div_stress(u, prm.mu, prm.h)
+    return [(ops.Gc(p, m, prm.h) + visc[m]) / rho for m in range(3)]
+
+
+def _energy_no_pressure_work(prm, phi, u, rho, p, E, T):
+    tau = ops.stress(u, prm.mu, prm.h)
+    F = []
+    for d in range(3):
+        work = sum(tau[d][m] * ops.I4(u[m], d) for m in range(3))
+        F.append(phi[d] * ops.I4(E, d) - work - prm.kappa * ops.G4(T, d, prm.h))
+    return F
+
+
+CASES = [
+    ("I4 normalisation", ops, "I4", _bad_I4, lambda: t_ops.test_symbols(16, 1, 0)),
+    ("G4 normalisation", ops, "G4", _bad_G4, lambda: t_ops.test_order_G4()),
+    ("stress without 2/3 div", ops, "stress", _stress_no_dilatation,
+     lambda: t_ops.test_viscous_stress_closed_form()),
+    ("stress transposed gradient", ops, "stress", _stress_transposed,
+     lambda: t_ops.test_viscous_stress_closed_form()),
+    ("convection sign", ops, "L", _L_wrong_sign, lambda: t_ops.test_convection_closed_form()),
+    ("barotropic EOS without 1/gamma", piso, "eos_pressure", _eos_no_gamma_division,
+     lambda: t_piso.test_acoustic_wave_speed()),
+    ("Du/Dt pressure sign", piso, "accel", _accel_wrong_sign,
+     lambda: t_piso.test_dust_drift_pressure_closed_form()),
+    ("enthalpy flux without p/rho", piso, "energy_flux", _energy_no_pressure_work,
+     lambda: t_piso.test_isobaric_heat_conduction_rate()),
+]
+
+
+@pytest.mark.parametrize("name,mod,attr,bad,pin", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(monkeypatch, name, mod, attr, bad, pin):
+    monkeypatch.setattr(mod, attr, bad)
+    with pytest.raises(AssertionError):
+        pin()
+
+
+def test_dropped_trapezoid_average_is_caught(monkeypatch):
+    """R^k = L(u^{k-1}) instead of (R^n + L)/2: first order in time, TG rate moves."""
+    orig_L = ops.L
+    calls = {"n": 0}
+
+    def L_counting(u, phi, mu, h):
+        calls["n"] += 1
+        out = orig_L(u, phi, mu, h)
+        # the predictor call (first of each step) is kept; corrector calls return 2L - R^n
+        # which turns (R^n + L)/2 into L
+        return out
+
+    monkeypatch.setattr(ops, "L", L_counting)
+    r, nu, h = t_piso._tg_rate(16, nsteps=4)
+    assert abs(r / (6 * nu * t_piso.s1(h)) - 1) < 2e-5  # unmodified: passes
+
+    state = {}
+
+    def L_biased(u, phi, mu, h):
+        out = orig_L(u, phi, mu, h)
+        if "Rn" not in state or state.get("fresh", False):
+            state["Rn"] = out
+            state["fresh"] = False
+            return out
+        return [2 * out[m] - state["Rn"][m] for m in range(3)]
+
+    orig_step = piso.step
+
+    def step_wrapped(prm, st, precond=None, dt=None):
+        state["fresh"] = True
+        state.pop("Rn", None)
+        return orig_step(prm, st, precond, dt)
+
+    monkeypatch.setattr(ops, "L", L_biased)
+    monkeypatch.setattr(piso, "step", step_wrapped)
+    r, nu, h = t_piso._tg_rate(16, nsteps=4)
+    assert abs(r / (6 * nu * t_piso.s1(h)) - 1) > 2e-5
+
+
+def test_solver_pin_catches_wrong_laplacian(monkeypatch):
+    def helm_bad(prm, psi, dt, HbyA=None):
+        h = prm.h
+
+        def matvec(x):
+            lap = ops.D([ops.G2(x, d, h) for d in range(3)], h)
+            return psi * x / dt - dt * lap
+
+        return matvec, psi / dt + 6.0 * dt / (h * h)
+
+    monkeypatch.setattr(piso, "helmholtz", helm_bad)
+    with pytest.raises(AssertionError):
+        t_solve.test_pcg_uniform_psi_matches_fourier()

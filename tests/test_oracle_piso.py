@@ -1,0 +1,229 @@
+"""Pins for the oracle's PISO step (Algorithm O).
+
+Each test fixes part of the step against something other than the oracle:
+an analytic rate, an exact conservation law, an invariant, or a closed-form
+leading-order response derived from the paper's physics (Sec. 2: PISO with
+fourth-order interpolation; Fourier and barotropic closures; first-order
+Stokes expansion u_p = u - tau_p Du/Dt; Marble's limit tau_p = 0).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import diag, piso
+
+
+def grid(N):
+    h = 2 * math.pi / N
+    c = (np.arange(N) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    return x, y, z, h
+
+
+def s1(h):
+    """Symbol magnitude of D o G4 at k = 1 (from the stencil coefficients)."""
+    th = h / 2
+    return (2 * np.sin(th) / h) * (27 * np.sin(th) - np.sin(3 * th)) / (12 * h)
+
+
+def g1(h):
+    """Symbol magnitude of the Gauss gradient at k = 1."""
+    return (10 * np.sin(h) - np.sin(2 * h)) / (8 * h)
+
+
+def random_state(prm, seed, amp=0.05):
+    rng = np.random.default_rng(seed)
+    N = prm.N
+    sh = (N, N, N)
+    rho = 1.0 + amp * rng.standard_normal(sh)
+    u = [0.2 * rng.standard_normal(sh) for _ in range(3)]
+    Y = [0.01 + 0.002 * rng.random(sh) for _ in range(prm.n_dust)]
+    T = 1.0 + amp * rng.standard_normal(sh) if prm.closure == piso.FOURIER else None
+    return piso.make_state(prm, rho, u, Y, T)
+
+
+@pytest.mark.parametrize("closure", [piso.BAROTROPIC, piso.FOURIER])
+def test_uniform_state_stays_uniform(closure):
+    N = 8
+    prm = piso.Params(N=N, closure=closure, tau_p=[0.05, 0.2], Y0=[0.01, 0.03], dt_max=0.1)
+    ones = np.ones((N, N, N))
+    st = piso.make_state(prm, 1.3 * ones, [0.1 * ones, 0.05 * ones, 0 * ones],
+                         [0.01 * ones, 0.03 * ones], 1.1 * ones if closure else None)
+    new, info = piso.step(prm, st)
+    assert info["iters"] == [0, 0]
+    for a, b in [(new["rho"], st["rho"]), (new["p"], st["p"])] + list(zip(new["u"][:2], st["u"][:2])) \
+            + list(zip(new["Y"], st["Y"])):
+        assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+    assert np.max(np.abs(new["u"][2])) == 0.0
+
+
+@pytest.mark.parametrize("closure,transonic", [(piso.BAROTROPIC, False), (piso.FOURIER, False),
+                                               (piso.BAROTROPIC, True)])
+def test_exact_conservation(closure, transonic):
+    prm = piso.Params(N=12, closure=closure, tau_p=[0.02, 0.1, 0.3], Y0=[0.02] * 3,
+                      transonic=transonic, p_tol=1e-12)
+    st = random_state(prm, 3)
+    t0 = piso.totals(prm, st)
+    for _ in range(2):
+        st, info = piso.step(prm, st)
+        assert max(info["rel_res"]) < 1e-11
+    t1 = piso.totals(prm, st)
+    assert abs(t1["mass"] - t0["mass"]) <= 1e-14 * t0["mass"]
+    for a, b in zip(t1["dust"], t0["dust"]):
+        assert abs(a - b) <= 1e-14 * b
+    if closure == piso.FOURIER:
+        assert abs(t1["energy"] - t0["energy"]) <= 1e-14 * t0["energy"]
+
+
+def _tg_rate(N, nsteps=20):
+    A, nu = 1e-3, 0.005
+    x, y, z, h = grid(N)
+    prm = piso.Params(N=N, nu=nu, tau_p=[0.0], Y0=[0.01], dt_max=0.05)
+    u = [A * np.sin(x) * np.cos(y) * np.cos(z), -A * np.cos(x) * np.sin(y) * np.cos(z), 0 * x]
+    st = piso.make_state(prm, np.ones_like(x), u, [np.full_like(x, 0.01)])
+    ke0 = diag.diagnostics(st["rho"], st["u"], h)["ke_u"]
+    for _ in range(nsteps):
+        st, _info = piso.step(prm, st)
+    ke = diag.diagnostics(st["rho"], st["u"], h)["ke_u"]
+    return -math.log(ke / ke0) / st["t"], nu, h
+
+
+def test_taylor_green_viscous_decay():
+    """KE of a small-amplitude TG vortex decays at 2 nu |k|^2 = 6 nu.
+
+    Discretely the rate is 6 nu s(h) with s the D o G4 symbol (the field is
+    exactly solenoidal for the Gauss divergence); it tends to 6 nu at order 2.
+    Nonlinear and time-stepping effects at A = 1e-3, dt = 0.05 are < 1e-5.
+    """
+    r16, nu, h16 = _tg_rate(16)
+    r32, _, h32 = _tg_rate(32)
+    assert abs(r32 / (6 * nu * s1(h32)) - 1) < 2e-5
+    assert abs(r16 / (6 * nu * s1(h16)) - 1) < 2e-5
+    dev16 = abs(r16 / (6 * nu) - 1)
+    dev32 = abs(r32 / (6 * nu) - 1)
+    assert dev32 < 2.5e-3
+    assert 3.6 < dev16 / dev32 < 4.4  # second order
+
+
+def test_passive_tracer_marble_limit():
+    """tau_p = 0: dust is a passive scalar; the scheme is affine in Y."""
+    prm = piso.Params(N=10, tau_p=[0.0, 0.0], Y0=[0.0, 0.0], p_tol=1e-12)
+    st = random_state(prm, 7)
+    st["Y"][1] = 2.0 * st["Y"][0] + 3.0
+    new, _ = piso.step(prm, st)
+    np.testing.assert_allclose(new["Y"][1], 2.0 * new["Y"][0] + 3.0, rtol=0, atol=1e-13)
+    # uniform dust stays uniform when it moves with the gas
+    prm1 = piso.Params(N=10, tau_p=[0.0], Y0=[0.0])
+    st1 = random_state(prm1, 8)
+    st1["Y"][0] = np.full_like(st1["rho"], 0.02)
+    new1, _ = piso.step(prm1, st1)
+    assert np.max(np.abs(new1["Y"][0] - 0.02)) < 1e-15
+
+
+def test_first_order_in_tau_p():
+    """u_p = u - tau_p Du/Dt is a first-order expansion: response linear in tau_p."""
+    eps = 1e-4
+    outs = []
+    for tp in (0.0, eps, 2 * eps):
+        prm = piso.Params(N=10, tau_p=[tp], Y0=[0.0], p_tol=1e-13)
+        st = random_state(prm, 11)
+        new, _ = piso.step(prm, st, dt=0.02)
+        outs.append(new["Y"][0])
+    d1 = outs[1] - outs[0]
+    d2 = outs[2] - outs[0]
+    assert np.max(np.abs(d1)) > 1e-9
+    ratio = np.sum(d2 * d1) / np.sum(d1 * d1)
+    assert abs(ratio - 2.0) < 1e-2
+
+
+def test_dust_drift_pressure_closed_form():
+    """u = 0, T = 1 + eps cos x (Fourier, rho = 1): dust gathers at high pressure.
+
+    Leading order: (rho Y)^{n+1} - Y0 rho^{n+1} = dt Y0 tau_p D(I4(-Gc p))
+    = dt Y0 tau_p g^2 R eps cos x, g the Gauss-gradient symbol; error O(dt).
+    """
+    N, eps, Y0, tp = 16, 1e-3, 0.01, 0.1
+    x, y, z, h = grid(N)
+    errs = []
+    for dt in (1e-3, 1e-4):
+        prm = piso.Params(N=N, closure=piso.FOURIER, nu=0.005, tau_p=[tp], Y0=[Y0])
+        st = piso.make_state(prm, np.ones_like(x), [0 * x] * 3, [np.full_like(x, Y0)], 1 + eps * np.cos(x))
+        new, _ = piso.step(prm, st, dt=dt)
+        delta = new["rho"] * new["Y"][0] - Y0 * new["rho"]
+        ref = dt * Y0 * tp * g1(h) ** 2 * prm.R * eps * np.cos(x)
+        errs.append(np.max(np.abs(delta - ref)) / np.max(np.abs(ref)))
+    assert errs[0] < 1e-5 and errs[1] < 1e-6
+    assert 8 < errs[0] / errs[1] < 12  # first order in dt
+
+
+def test_dust_drift_dilatation_closed_form():
+    """u = (eps sin x, 0, 0), uniform p: Du/Dt = mu (D G4 u + Gc(div u)/3) / rho.
+
+    Leading order dust excess: dt Y0 tau_p mu eps (-s - g^2/3) g cos x, i.e.
+    -(4/3) mu in the continuum (pins the 1/3 from the 2/3 of the stress).
+    """
+    N, eps, Y0, tp, mu = 16, 1e-3, 0.01, 0.1, 0.05
+    x, y, z, h = grid(N)
+    errs = []
+    for dt in (1e-3, 1e-4):
+        prm = piso.Params(N=N, nu=mu, tau_p=[tp], Y0=[Y0])
+        st = piso.make_state(prm, np.ones_like(x), [eps * np.sin(x), 0 * x, 0 * x], [np.full_like(x, Y0)])
+        new, _ = piso.step(prm, st, dt=dt)
+        delta = new["rho"] * new["Y"][0] - Y0 * new["rho"]
+        ref = dt * Y0 * tp * mu * eps * (-s1(h) - g1(h) ** 2 / 3) * g1(h) * np.cos(x)
+        errs.append(np.max(np.abs(delta - ref)) / np.max(np.abs(ref)))
+    assert errs[0] < 1e-4 and errs[1] < 1e-5
+    assert 8 < errs[0] / errs[1] < 12
+
+
+def _heat_rate(N):
+    eps, nu, Pr, dt = 1e-3, 0.02, 0.7, 0.05
+    x, y, z, h = grid(N)
+    prm = piso.Params(N=N, closure=piso.FOURIER, nu=nu, Pr=Pr, tau_p=[0.0], Y0=[0.0], dt_max=dt)
+    lam = nu / Pr * s1(h)
+    T = 1 + eps * np.sin(x)
+    # start on the isobaric thermal mode: div u = dT/dt / T
+    st = piso.make_state(prm, 1 / T, [lam * eps * np.cos(x), 0 * x, 0 * x], [0 * x], T)
+    a0 = np.sum(st["T"] * np.sin(x)) / np.sum(np.sin(x) ** 2)
+    for _ in range(80):
+        st, _info = piso.step(prm, st)
+    a1 = np.sum(st["T"] * np.sin(x)) / np.sum(np.sin(x) ** 2)
+    return -math.log(a1 / a0) / st["t"], lam, nu / Pr
+
+
+def test_isobaric_heat_conduction_rate():
+    """Fourier closure: a temperature wave at uniform p decays at kappa k^2/(rho c_p).
+
+    kappa/c_p = mu/Pr; with c_v instead of c_p the rate would be gamma times
+    larger, so the pressure-work / enthalpy flux terms are pinned too.
+    """
+    r16, lam16, a = _heat_rate(16)
+    r8, lam8, _ = _heat_rate(8)
+    assert abs(r16 / lam16 - 1) < 2e-3
+    assert abs(r8 / lam8 - 1) < 5e-3
+    d8, d16 = abs(r8 / a - 1), abs(r16 / a - 1)
+    assert 3.0 < d8 / d16 < 5.0
+
+
+def _acoustic_omega(N, dt=0.01):
+    eps = 1e-4
+    x, y, z, h = grid(N)
+    prm = piso.Params(N=N, nu=0.0, tau_p=[0.0], Y0=[0.0], dt_max=dt, p_tol=1e-13)
+    st = piso.make_state(prm, 1 + eps * np.cos(x), [0 * x] * 3, [0 * x])
+    for _ in range(int(round(1.0 / dt))):
+        st, _info = piso.step(prm, st)
+    a = np.sum((st["rho"] - 1) * np.cos(x)) / np.sum(np.cos(x) ** 2)
+    return math.acos(a / eps) / st["t"]
+
+
+def test_acoustic_wave_speed():
+    """A k = 1 density wave oscillates at omega = c k with c^2 = gamma p / rho = 1.
+
+    Pins psi = rho/(gamma p) and the EOS: a missing gamma moves c by
+    sqrt(1.4).  Discretisation error converges at second order or better.
+    """
+    w8 = _acoustic_omega(8)
+    w16 = _acoustic_omega(16)
+    assert abs(w16 - 1) < 1e-2
+    assert abs(w16 - 1) < abs(w8 - 1) / 3

@@ -1,0 +1,126 @@
+"""Pins for the oracle's pressure-correction operator and Krylov solvers.
+
+M p = psi p / dt - (dt/2) D(G2 p) (+ (1/2) D(I4(psi p) I4(HbyA)) transonic).
+With uniform psi and HbyA the operator is diagonal in Fourier space; its
+eigenvalues follow from the stencil symbols (2 sin(kh/2)/h for the compact
+difference; Gc's symbol for D o I4).  For variable psi the matrix is
+assembled here entry by entry from the 7-point stencil coefficients and
+solved by dense LU.
+"""
+import math
+
+import numpy as np
+import scipy.linalg
+
+from oracle import krylov, piso
+
+
+def _rand(N, seed):
+    return np.random.default_rng(seed).standard_normal((N, N, N))
+
+
+def _fourier_solve(b, lam):
+    return np.real(np.fft.ifftn(np.fft.fftn(b) / lam))
+
+
+def _kgrid(N):
+    kk = np.fft.fftfreq(N, d=1.0 / N)
+    kz, ky, kx = np.meshgrid(kk, kk, kk, indexing="ij")
+    return kx, ky, kz
+
+
+def test_pcg_uniform_psi_matches_fourier():
+    N, dt, psi0 = 16, 0.13, 0.83
+    prm = piso.Params(N=N, p_tol=1e-14, p_maxit=400)
+    h = prm.h
+    psi = np.full((N, N, N), psi0)
+    matvec, diag = piso.helmholtz(prm, psi, dt)
+    b = _rand(N, 1)
+    x, it, rec, true = krylov.pcg(matvec, b, diag, prm.p_tol, prm.p_maxit)
+    K = _kgrid(N)
+    lam = psi0 / dt + 0.5 * dt * sum(4 * np.sin(k * h / 2) ** 2 / h ** 2 for k in K)
+    xe = _fourier_solve(b, lam)
+    assert true < 1e-13
+    assert np.max(np.abs(x - xe)) < 1e-12 * np.max(np.abs(xe))
+
+
+def test_pcg_variable_psi_matches_dense_lu():
+    N, dt = 8, 0.2
+    prm = piso.Params(N=N, p_tol=1e-15, p_maxit=600)
+    h = prm.h
+    rng = np.random.default_rng(5)
+    psi = 0.7 + 0.5 * rng.random((N, N, N))
+    matvec, diag = piso.helmholtz(prm, psi, dt)
+    b = rng.standard_normal((N, N, N))
+    n = N ** 3
+    A = np.zeros((n, n))
+    off = -0.5 * dt / h ** 2
+
+    def idx(i, j, k):
+        return (i % N) + N * ((j % N) + N * (k % N))
+
+    for k in range(N):
+        for j in range(N):
+            for i in range(N):
+                r = idx(i, j, k)
+                A[r, r] += psi[k, j, i] / dt + 3 * dt / h ** 2
+                for (di, dj, dk) in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    A[r, idx(i + di, j + dj, k + dk)] += off
+    xe = scipy.linalg.solve(A, b.reshape(-1)).reshape(N, N, N)
+    x, it, rec, true = krylov.pcg(matvec, b, diag, 1e-14, 600)
+    assert np.max(np.abs(x - xe)) < 1e-12 * np.max(np.abs(xe))
+    # Jacobi diagonal equals the assembled diagonal
+    np.testing.assert_allclose(diag.reshape(-1), np.diag(A), rtol=1e-15)
+
+
+def test_bicgstab_transonic_matches_fourier():
+    N, dt, psi0 = 16, 0.1, 0.9
+    U = (0.3, -0.2, 0.15)
+    prm = piso.Params(N=N, transonic=True)
+    h = prm.h
+    psi = np.full((N, N, N), psi0)
+    HbyA = [np.full((N, N, N), U[d]) for d in range(3)]
+    matvec, diag = piso.helmholtz(prm, psi, dt, HbyA)
+    b = _rand(N, 2)
+    x, it, rec, true = krylov.bicgstab(matvec, b, diag, 1e-14, 400)
+    K = _kgrid(N)
+    g = [(10 * np.sin(k * h) - np.sin(2 * k * h)) / (8 * h) for k in K]
+    lam = psi0 / dt + 0.5 * dt * sum(4 * np.sin(k * h / 2) ** 2 / h ** 2 for k in K) \
+        + 0.5 * psi0 * 1j * sum(U[d] * g[d] for d in range(3))
+    xe = _fourier_solve(b, lam)
+    assert true < 1e-13
+    assert np.max(np.abs(x - xe)) < 1e-11 * np.max(np.abs(xe))
+
+
+def test_fcg_with_jacobi_equals_pcg_solution():
+    N, dt = 12, 0.17
+    prm = piso.Params(N=N)
+    rng = np.random.default_rng(9)
+    psi = 0.8 + 0.3 * rng.random((N, N, N))
+    matvec, diag = piso.helmholtz(prm, psi, dt)
+    b = rng.standard_normal((N, N, N))
+    x1, it1, _, t1 = krylov.pcg(matvec, b, diag, 1e-12, 500)
+    x2, it2, _, t2 = krylov.fcg(matvec, b, lambda r: r / diag, diag, 1e-12, 500)
+    assert t1 < 1e-12 and t2 < 1e-12
+    # with a fixed SPD preconditioner FCG(1) is PCG in exact arithmetic
+    assert abs(it1 - it2) <= 1
+    assert np.max(np.abs(x1 - x2)) < 1e-10 * np.max(np.abs(x1))
+
+
+def test_fcg_rejects_bad_direction():
+    N, dt = 8, 0.2
+    prm = piso.Params(N=N)
+    psi = np.full((N, N, N), 1.0)
+    matvec, diag = piso.helmholtz(prm, psi, dt)
+    b = _rand(N, 4)
+    # an adversarial "preconditioner" returning -r is replaced by Jacobi
+    x, it, _, true = krylov.fcg(matvec, b, lambda r: -r, diag, 1e-12, 500)
+    assert true < 1e-12
+
+
+def test_zero_rhs():
+    N = 8
+    prm = piso.Params(N=N)
+    matvec, diag = piso.helmholtz(prm, np.ones((N, N, N)), 0.1)
+    x, it, rec, true = krylov.pcg(matvec, np.zeros((N, N, N)), diag, 1e-10, 10)
+    assert it == 0 and not np.any(x)
