@@ -1,0 +1,295 @@
+"""Benchmark: cell-steps/s of the compressible fast-Eulerian PISO step at 256^3.
+
+Default workload ``hit256``: 256^3 periodic box, barotropic (gamma 1.4),
+r.m.s. Mach 0.2, spectrum peak k0 = 8, nu = 0.001, one dust class (tau_p 0.05,
+Y 0.01), CFL 0.5 adaptive step, 2 PISO correctors, pressure residual 1e-8;
+synthetic spectral initial field (seed 0, one per rank).  One bench "step" is
+one PISO time step of the whole box.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is device-timed throughput with the
+state resident in HBM; ``e2e`` repeats the measurement through the public API
+with the state copied from and back to pinned host buffers every step.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "hit256"
+METRIC = "cell-steps/s at 256^3 (learned vs plain solve, same residual); % of HBM peak"
+UNIT = "cell-steps/s"
+
+# Algorithmic words per cell (one N^3 array element read or written once) per
+# launch of each kernel, barotropic closure, nd dust classes.
+def alg_words(kernel, nd):
+    table = {
+        "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 11,
+        "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4, "corr": 21, "accel": 9,
+        "dust": 8 + 4 * nd + 2,  # last corrector adds u reads and p write; averaged over 2 correctors
+        "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
+    }
+    return table[kernel]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(N, steps, cfg):
+    """Time `steps` oracle steps of the workload physics on an N^3 box (spectral IC)."""
+    from oracle import piso
+    prm = piso.Params(N=N, closure=cfg["closure"], nu=cfg["nu"], tau_p=list(cfg["tau_p"]), Y0=list(cfg["Y0"]),
+                      mach_rms=cfg["mach_rms"], k0=cfg["k0"], seed=cfg["seed"], cfl=cfg["cfl"],
+                      p_tol=cfg["p_tol"])
+    st = piso.initial_state(prm)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st, _info = piso.step(prm, st)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, cfg, rank):
+    if rank != 0:
+        return
+    N = args.ref_n
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_sample(N, 1, cfg)
+        if i >= args.warmup:
+            times.append(t)
+    total = sum(times)
+    value = N ** 3 * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_N": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: one oracle PISO step of the %s physics on a %d^3 box" % (WORKLOAD, N)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--ref-n", type=int, default=64)
+    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", default=None, help="kernel timed live for the roofline (default: largest share)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_1404_0959_gb300.inputs import WORKLOADS
+    cfg = dict(WORKLOADS[WORKLOAD])
+    cfg["N"] = args.N
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, cfg, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1404_0959_gb300 import build, fe
+    if rank == 0:
+        build.build()
+    barrier()
+
+    precision = fe.FE_FP64 if args.precision == "fp64" else fe.FE_FP32_MIXED
+    N = cfg["N"]
+    nd = len(cfg["tau_p"])
+    box = dict(N=N, nu=cfg["nu"], tau_p=list(cfg["tau_p"]), Y0=list(cfg["Y0"]), mach_rms=cfg["mach_rms"],
+               k0=cfg["k0"], seed=cfg["seed"] + rank)
+    stream = torch.cuda.current_stream()
+    s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
+                  p_maxit=1000, stream=stream.cuda_stream)
+    s.init_state(0, fe.FE_INIT_SPECTRAL)
+    code, _ = s.step(args.warmup)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+
+    # untimed pass: per-kernel device time over one step, one kernel id at a time
+    names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir", "corr",
+             "accel", "dust"]
+    share = {}
+    for k in names:
+        s.profile_start(k)
+        s.step(1)
+        p = s.profile_stop()
+        share[k] = (p["target_ms"], p["target_launches"])
+    kernel = args.kernel or max(share, key=lambda k: share[k][0])
+
+    # timed region
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    s.profile_start(kernel)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    code, info = s.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = s.profile_stop()
+    ck = clocks.stop()
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    t = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    cells = float(N) ** 3
+    value = cells * args.steps * world / t
+    w = 8 if precision == fe.FE_FP64 else 4
+    hbm, peak_kind = peaks()
+    per_launch_ms = prof["target_ms"] / max(prof["target_launches"], 1)
+    alg_bytes = alg_words(kernel, nd) * w * cells
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    iters = info[0]["iters"]
+
+    # end to end through the public API: state from pinned host, step, state back
+    e2e = None
+    if not args.no_e2e:
+        fields = [fe.FE_RHO, fe.FE_UX, fe.FE_UY, fe.FE_UZ, fe.FE_P, fe.FE_PHIX, fe.FE_PHIY, fe.FE_PHIZ] + \
+                 [fe.FE_Y0 + j for j in range(nd)]
+        dt_ = torch.float64 if w == 8 else torch.float32
+        host = {f: torch.empty((N, N, N), dtype=dt_, pin_memory=True) for f in fields}
+        for f in fields:
+            fe.fe_get_field(s.ctx, 0, f, host[f].data_ptr(), 0)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for f in fields:
+                fe.fe_set_field(s.ctx, 0, f, host[f].data_ptr(), 0)
+            code, _ = s.step(1)
+            for f in fields:
+                fe.fe_get_field(s.ctx, 0, f, host[f].data_ptr(), 0)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        nbytes = len(fields) * cells * w
+        e2e = {"value": cells * args.steps * world / te, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
+               "d2h_bytes_per_step": int(nbytes)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        tc = oracle_sample(args.cpu_n, 1, cfg)
+        cpu = {"value": args.cpu_n ** 3 / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one FP64 oracle PISO step of the %s physics on a %d^3 box (spectral IC, same seed)"
+                         % (WORKLOAD, args.cpu_n)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if w == 8 else "f32 fields, f64 reductions",
+                "data": "synthetic spectral HIT field (seed per rank), no dataset",
+                "config": {"workload": WORKLOAD, "N": N, "closure": "barotropic", "mach_rms": cfg["mach_rms"],
+                           "k0": cfg["k0"], "nu": cfg["nu"], "tau_p": cfg["tau_p"], "Y0": cfg["Y0"],
+                           "p_tol": cfg["p_tol"], "solver": "jacobi-pcg", "precision": args.precision,
+                           "n_corr": 2, "krylov_iters_last_step": iters,
+                           "l2": "state of %.1f GB >> 126 MB L2, no flush needed" % (
+                               (40 + 4 * nd) * cells * w / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single box"},
+                "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                             "alg_bytes_per_launch": alg_bytes, "launches": prof["target_launches"],
+                             "ms_per_launch": per_launch_ms},
+                "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items()},
+                "gpu_launches": prof["launches"],
+                "clocks": ck, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

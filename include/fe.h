@@ -1,0 +1,232 @@
+/*
+ * fe.h -- C ABI of libfe.so: compressible fast-Eulerian PISO step on GB300.
+ *
+ * Method: Cerminara, Berselli, Esposti Ongaro, Salvetti, "Direct numerical
+ * simulation of a compressible multiphase flow through the fast Eulerian
+ * approach" (arXiv:1404.0959).  Sec. 2 par. 1: PISO pressure-velocity
+ * coupling with fourth-order central interpolation and an adaptive time step;
+ * Sec. 2 par. 2 and footnotes: Equilibrium-Eulerian dust (first-order Stokes
+ * expansion u_p = u - tau_p Du/Dt), Fourier (q = -k grad T) or barotropic
+ * (p ~ rho^gamma) closure; Sec. 1: decaying homogeneous isotropic turbulence
+ * at r.m.s. Mach 0.2 / 0.5 on a periodic box.  The paper prints no
+ * equations; the discrete step implemented here is stated in full in the
+ * documentation of fe_step below.
+ *
+ * Conventions (every entry point):
+ *  - Return 0 (FE_OK) on success, a negative FE_ERR_* code on failure;
+ *    fe_strerror() gives a message.  FE_ERR_INVALID_ARG leaves the context
+ *    unchanged.
+ *  - One context = one or more independent periodic boxes ("ensemble"),
+ *    all advanced together; every kernel launch covers all boxes.
+ *  - Grid: box [0, 2 pi)^3, N^3 cells, h = 2 pi / N; a cell field is N^3
+ *    contiguous values, flat index i + N*(j + N*k), x fastest (SoA).  A face
+ *    field of direction d holds at cell index c the value on the face
+ *    between cell c and its +d neighbour.
+ *  - Field precision: FE_FP64 -> double; FE_FP32_MIXED -> float (Krylov dot
+ *    products, refinement residuals and conserved totals still in double).
+ *  - Device pointers are borrowed: the caller keeps them alive and issues
+ *    its own work on the stream given to fe_create (work is ordered on that
+ *    stream).  Host pointers are read/written synchronously before return.
+ *  - The context owns all of its device memory (allocated in fe_create,
+ *    freed in fe_destroy).  Calls on one context must not run concurrently.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FE_OK                  0
+#define FE_ERR_INVALID_ARG    -1
+#define FE_ERR_CUDA           -2
+#define FE_ERR_NOT_CONVERGED  -3
+#define FE_ERR_NONFINITE      -4
+#define FE_ERR_OOM            -5
+#define FE_ERR_UNSUPPORTED    -6
+
+/* precision */
+#define FE_FP64        0
+#define FE_FP32_MIXED  1
+
+/* closure (Sec. 2 footnotes) */
+#define FE_BAROTROPIC  0   /* p = rho^gamma / gamma, no energy equation     */
+#define FE_FOURIER     1   /* total-energy equation, q = -kappa grad T      */
+
+/* pressure-correction solver */
+#define FE_PCG_JACOBI       0   /* SPD operator (transonic = 0)              */
+#define FE_BICGSTAB_JACOBI  1   /* any operator (required for transonic = 1) */
+#define FE_FCG_LEARNED      2   /* flexible CG, learned preconditioner with  *
+                                 * Jacobi fallback (needs fe_load_preconditioner) */
+
+/* field ids for fe_set_field / fe_get_field */
+#define FE_RHO   0
+#define FE_UX    1
+#define FE_UY    2
+#define FE_UZ    3
+#define FE_P     4
+#define FE_T     5   /* temperature, Fourier closure only */
+#define FE_PHIX  6   /* face mass flux per unit area, x faces */
+#define FE_PHIY  7
+#define FE_PHIZ  8
+#define FE_Y0    9   /* dust mass fraction of class j is FE_Y0 + j */
+
+/* fe_init_state modes */
+#define FE_INIT_SPECTRAL 0  /* random solenoidal u from (seed, k0, mach_rms); rho = T = 1, Y = Y0 */
+#define FE_INIT_DERIVE   1  /* keep rho, u, Y (and T) already set; derive p (EOS) and phi = I4(rho) I4(u) */
+
+#define FE_MAX_DUST 8
+
+typedef struct fe_ctx fe_ctx;   /* opaque */
+
+typedef struct {
+    int32_t n_boxes;            /* >= 1                                          */
+    const int32_t* N;           /* [n_boxes] cells per side, 8 <= N <= 512       */
+    int32_t precision;          /* FE_FP64 | FE_FP32_MIXED                       */
+    int32_t closure;            /* FE_BAROTROPIC | FE_FOURIER                    */
+    double gamma;               /* ratio of specific heats (1.4)                 */
+    double Pr;                  /* Prandtl number (Fourier)                      */
+    const double* nu;           /* [n_boxes] kinematic viscosity; mu = nu        */
+    int32_t n_dust;             /* dust classes, 0..FE_MAX_DUST                  */
+    const double* tau_p;        /* [n_boxes * n_dust] particle relaxation times  */
+    const double* Y0;           /* [n_boxes * n_dust] initial mass fractions     */
+    const double* mach_rms;     /* [n_boxes] initial r.m.s. Mach number          */
+    const double* k0;           /* [n_boxes] spectrum peak wavenumber            */
+    const uint64_t* seed;       /* [n_boxes] RNG seeds                           */
+    double cfl;                 /* Courant number of the adaptive step (0.5)     */
+    double dt_growth_max;       /* max dt ratio between steps (1.2)              */
+    double dt_max;              /* upper bound on dt (use HUGE_VAL for none)     */
+    int32_t n_corr;             /* PISO correctors, >= 1 (2 recommended)         */
+    int32_t solver;             /* FE_PCG_JACOBI | FE_BICGSTAB_JACOBI | FE_FCG_LEARNED */
+    double p_tol;               /* ||b - M x||_2 <= p_tol ||b||_2                */
+    int32_t p_maxit;            /* Krylov iteration cap per solve                */
+    int32_t transonic;          /* 1: add the psi-convection term (non-symmetric) */
+} fe_params;
+
+typedef struct {
+    double t;                   /* time after the step                           */
+    double dt;                  /* step just taken                               */
+    int32_t iters[4];           /* Krylov iterations of correctors 1..4          */
+    double rel_res[4];          /* true relative residual of correctors 1..4     */
+} fe_step_info;
+
+typedef struct {
+    int32_t iters;              /* Krylov iterations                             */
+    double rel_res_true;        /* ||b - M x|| / ||b|| recomputed from x         */
+} fe_solve_info;
+
+typedef struct {
+    double ke;                  /* <rho |u|^2> / 2                               */
+    double ke_u;                /* <|u|^2> / 2                                   */
+    double enstrophy;           /* <|curl u|^2> / 2 (Gauss-gradient curl)        */
+    double taylor;              /* sqrt(sum_d <u_d^2> / sum_d <(d u_d/d x_d)^2>) */
+    double rho_rms;             /* sqrt(<(rho - <rho>)^2>)                       */
+    double mass;                /* h^3 sum rho                                   */
+    double dust_mass[FE_MAX_DUST]; /* h^3 sum rho Y_j                            */
+    double energy;              /* h^3 sum rho E (Fourier) or h^3 sum rho|u|^2/2 */
+    double t;                   /* current time                                  */
+    double dt_prev;             /* last step                                     */
+} fe_diag;
+
+/* Allocate a context for prm (arrays are copied).  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  Uses the current device. */
+int fe_create(const fe_params* prm, void* cuda_stream, fe_ctx** out);
+
+/* Initial state of one box (box >= 0) or of all boxes (box = -1).
+ * FE_INIT_SPECTRAL: decaying-HIT start (Sec. 1): u random solenoidal with
+ * E(k) ~ k^4 exp(-2 (k/k0)^2), r.m.s. |u| = mach_rms (sound speed 1);
+ * rho = 1, T = 1, Y_j = Y0_j, then as FE_INIT_DERIVE.  The random numbers
+ * are SplitMix64 draws 2(3f+c), 2(3f+c)+1 for FFT mode f, component c,
+ * through Box-Muller.  FE_INIT_DERIVE: p from the closure, phi = I4(rho)
+ * I4(u_d), t = 0, no previous step (growth limit inactive). */
+int fe_init_state(fe_ctx* ctx, int box, int mode);
+
+/* Copy one field of the current state in (set) or out (get).  src/dst hold
+ * N^3 values of the context precision; *_is_device selects device or host
+ * memory.  Setting FE_RHO, FE_UX..FE_UZ, FE_T or FE_Y0+j does not update p or phi: call
+ * fe_init_state(FE_INIT_DERIVE) or set FE_P and FE_PHI* explicitly
+ * (checkpoint restore). */
+int fe_set_field(fe_ctx* ctx, int box, int field, const void* src, int src_is_device);
+int fe_get_field(fe_ctx* ctx, int box, int field, void* dst, int dst_is_device);
+
+/* Time and previous step of a box (checkpoint restore; dt_prev <= 0 means none). */
+int fe_set_clock(fe_ctx* ctx, int box, double t, double dt_prev);
+
+/* Advance every box by nsteps PISO steps (Sec. 2 par. 1).  For each box,
+ * with operators I4 (4-point 4th-order face interpolation), G4 (4-point
+ * face gradient), G2 (compact face gradient), D (face-to-cell divergence),
+ * Gc (Gauss cell gradient from I4 faces), psi = rho^n/(gamma p^n), mu = nu:
+ *   dt = min(cfl h / max sum_d|u_d|, dt_growth_max dt_prev, dt_max)
+ *   rho0 = rho^n - dt D(phi^n); R^n = L(u^n, phi^n) with
+ *   L_m(u, phi) = -D(phi I4(u_m)) + D(tau_.m),
+ *   tau_dm = mu (G4_d u_m + I4_d Gc_m u_d - 2/3 delta_dm I4_d div u);
+ *   u* = (rho^n u^n + dt (R^n - Gc p^n)) / rho0;
+ *   corrector k = 1..n_corr (iterate 0 = (u*, phi^n, p^n, rho0)):
+ *     HbyA = (rho^n u^n + dt (R^n + L(u^{k-1}, phi^{k-1}))/2) / rho^{k-1}
+ *     phi* = I4(rho^{k-1}) I4(HbyA) - dt G2(p^{k-1})
+ *     solve psi p'/dt - dt/2 D(G2 p') [+ D(I4(psi p') I4(HbyA))/2] =
+ *           -[(rho^{k-1} - rho^n)/dt + D(phi^n)/2 + D(phi*)/2]
+ *     p^k = p^{k-1} + p'; phi^k = phi* - dt G2 p' [+ I4(psi p') I4(HbyA)]
+ *     u^k = HbyA - dt Gc(p^k) / rho^{k-1}; rho^k = rho^n - dt/2 D(phi^n + phi^k)
+ *     Du/Dt = (-Gc p^k + D tau(u^k)) / rho^k; per dust class
+ *     phi_p = phi^k - tau_p I4(rho^k) I4(Du/Dt);
+ *     (rho Y)^k = rho^n Y^n - dt/2 [D(phi_p^n I4 Y^n) + D(phi_p^k I4 Y^{k-1})]
+ *     Fourier: (rho E)^k likewise with flux phi I4(E + p/rho)
+ *              - sum_m tau_dm I4(u_m) - kappa G4(T), kappa = mu c_p / Pr
+ *   closure: barotropic p = rho^gamma/gamma; Fourier T = (E - |u|^2/2)/c_v,
+ *   p = rho R T with R = 1/gamma, c_v = R/(gamma-1).
+ * info: NULL or [n_boxes] records of the last step.  On
+ * FE_ERR_NOT_CONVERGED / FE_ERR_NONFINITE the failing step is not
+ * committed (state stays at the previous step). */
+int fe_step(fe_ctx* ctx, int nsteps, fe_step_info* info);
+
+/* Solve the pressure-correction equation M x = b of one box with the psi
+ * of its current state and the given dt, the operator, solver and
+ * preconditioner of the context (transonic term uses HbyA = u of the current
+ * state).  b, x: device arrays (N^3, context precision).  x starts at 0.
+ * Stops at ||r|| <= tol ||b|| or maxit; info->rel_res_true is recomputed
+ * from x.  Returns FE_ERR_NOT_CONVERGED if maxit was reached. */
+int fe_solve_pressure(fe_ctx* ctx, int box, const void* b, void* x, double dt,
+                      double tol, int maxit, fe_solve_info* info);
+
+/* Turbulence diagnostics of one box (Sec. 2 par. 1: spectrum, enstrophy,
+ * kinetic energy, Taylor microscale; Fig. 1: density r.m.s.).  spectrum:
+ * NULL or a host array of nbins doubles, E(k) = sum over modes with
+ * round(|k|) = k of |u_hat|^2 / (2 N^6). */
+int fe_diagnostics(fe_ctx* ctx, int box, fe_diag* out, double* spectrum, int nbins);
+
+/* Q criterion (|Omega|^2 - |S|^2)/2 of the current velocity of a box into a
+ * device array of N^3 context-precision values (Fig. 3 of the paper shows
+ * Q iso-surfaces). */
+int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
+
+/* Instrumentation (not part of the method).  fe_profile_start resets the
+ * counters of the context and, when kernel_id >= 0, brackets every later
+ * launch of that kernel with CUDA events on the context's stream;
+ * fe_profile_stop synchronises the stream and reports the number of kernel
+ * launches since the start (total and per kernel id) and the summed device
+ * time of the bracketed launches.  Kernel ids run 0 .. fe_kernel_count()-1,
+ * fe_kernel_name() gives their names. */
+#define FE_PROFILE_MAX_KERNELS 32
+typedef struct {
+    int64_t launches;                          /* all kernels of this context */
+    int64_t target_launches;                   /* launches of kernel_id       */
+    double target_ms;                          /* their summed event time     */
+    int64_t counts[FE_PROFILE_MAX_KERNELS];    /* launches per kernel id      */
+} fe_profile_info;
+int fe_profile_start(fe_ctx* ctx, int kernel_id);
+int fe_profile_stop(fe_ctx* ctx, fe_profile_info* out);
+int fe_kernel_count(void);
+const char* fe_kernel_name(int kernel_id);
+
+void fe_destroy(fe_ctx* ctx);
+const char* fe_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

@@ -1,0 +1,628 @@
+// fe_api.cu -- the C ABI of libfe (include/fe.h): context, memory plan, the
+// PISO step driver (Sec. 2 par. 1 of arXiv:1404.0959) and the solve /
+// diagnostics entry points.  All device memory of a context is allocated in
+// fe_create (one slab per box) and freed in fe_destroy; the step itself
+// allocates nothing.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fe_internal.cuh"
+
+using namespace fe;
+
+namespace fe {
+bool fft_supported(int N);
+template <typename T> int ic_spectral(T*, T*, T*, int, uint64_t, double, double, cudaStream_t);
+template <typename T> void fill(T*, long, double, cudaStream_t);
+template <typename T> int spectrum(const T*, const T*, const T*, int, double*, int, cudaStream_t);
+template <typename T> int diag_sums(const Launch&, const BoxDev&, int, int, double*);
+template <typename T> void qcrit(const Launch&, int, int, T*);
+}  // namespace fe
+
+namespace fe {
+struct Prof {
+  bool on = false;
+  int target = -1;
+  long long count[KID_COUNT] = {};
+  std::vector<cudaEvent_t> ev;  // start/stop pairs of the target kernel
+  size_t used = 0;
+  bool failed = false;
+};
+void prof_begin(Prof* p, int kid, cudaStream_t st) {
+  if (!p || !p->on) return;
+  p->count[kid]++;
+  if (kid != p->target) return;
+  while (p->ev.size() < 2 * (p->used + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      p->failed = true;
+      return;
+    }
+    p->ev.push_back(e);
+  }
+  cudaEventRecord(p->ev[2 * p->used], st);
+}
+void prof_end(Prof* p, int kid, cudaStream_t st) {
+  if (!p || !p->on || kid != p->target || p->failed) return;
+  cudaEventRecord(p->ev[2 * p->used + 1], st);
+  p->used++;
+}
+}  // namespace fe
+
+static const char* kKernelNames[KID_COUNT] = {
+    "dt",      "div",       "pred",      "fluxn",  "asm",      "rhs",       "corr",    "accel",
+    "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
+    "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "other"};
+
+struct fe_ctx {
+  fe_params prm;
+  std::vector<int32_t> N;
+  std::vector<double> nu, tau_p, Y0, mach, k0;
+  std::vector<uint64_t> seed;
+  cudaStream_t st = nullptr;
+  int nb = 0;
+  bool fp64 = true;
+  std::vector<BoxDev> hbox;
+  std::vector<void*> slabs;
+  BoxDev* dbox = nullptr;
+  int2* dwork = nullptr;
+  int nblocks = 0;
+  double* dpart = nullptr;
+  double* dsc = nullptr;
+  int* dcnt = nullptr;
+  int* dactive = nullptr;
+  int* hactive = nullptr;  // pinned
+  double* hsc = nullptr;   // pinned copy of all box scalars
+  int cur = 0;             // state set holding the current state
+  int poll = 1;            // Krylov iterations between convergence polls
+  Prof prof;
+  Launch L() { return Launch{dbox, dwork, nblocks, dpart, dactive, st, &prof}; }
+};
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return FE_ERR_CUDA;    \
+  } while (0)
+
+static size_t slot_bytes(int N, size_t esz) {
+  size_t b = (size_t)N * N * N * esz;
+  return (b + 255) & ~(size_t)255;
+}
+
+// Which slots a box needs and their element sizes.
+static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan) {
+  const size_t e = c->fp64 ? 8 : 4;
+  const int nd = c->prm.n_dust;
+  const bool fourier = c->prm.closure == FE_FOURIER;
+  for (int set = 0; set < 2; ++set) {
+    for (int f = F_RHO; f <= F_P; ++f) plan.push_back({S(set, f), e});
+    if (fourier) plan.push_back({S(set, F_T), e});
+    for (int j = 0; j < nd; ++j) plan.push_back({S(set, F_Y0 + j), e});
+  }
+  int w[] = {W_DIV, W_DIVPHI, W_RN0, W_RN1, W_RN2, W_AN0, W_AN1, W_AN2, W_PSI, W_HB0, W_HB1, W_HB2,
+             W_PS0, W_PS1, W_PS2, W_PW0, W_PW1, K_B, K_X, K_R, K_PD, K_Q, K_AUX};
+  for (int s : w) plan.push_back({s, e});
+  if (fourier)
+    for (int s : {W_EW0, W_EW1, W_FEN}) plan.push_back({s, e});
+  for (int j = 0; j < nd; ++j) {
+    plan.push_back({W_FYN0 + j, e});
+    plan.push_back({W_YW0 + j, e});
+    plan.push_back({W_YW1 + j, e});
+  }
+  if (c->prm.solver == FE_BICGSTAB_JACOBI)
+    for (int s : {K_RHAT, K_V, K_S, K_T}) plan.push_back({s, e});
+  if (!c->fp64) {
+    plan.push_back({K_X64, 8});
+    plan.push_back({K_B64, 8});
+  }
+}
+
+static int validate(const fe_params* p) {
+  if (!p || p->n_boxes < 1 || !p->N || !p->nu || !p->mach_rms || !p->k0 || !p->seed) return FE_ERR_INVALID_ARG;
+  if (p->precision != FE_FP64 && p->precision != FE_FP32_MIXED) return FE_ERR_INVALID_ARG;
+  if (p->closure != FE_BAROTROPIC && p->closure != FE_FOURIER) return FE_ERR_INVALID_ARG;
+  if (p->n_dust < 0 || p->n_dust > FE_MAX_DUST) return FE_ERR_INVALID_ARG;
+  if (p->n_dust > 0 && (!p->tau_p || !p->Y0)) return FE_ERR_INVALID_ARG;
+  if (p->n_corr < 1 || p->n_corr > 4) return FE_ERR_INVALID_ARG;
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->p_tol > 0.0) || p->p_maxit < 1) return FE_ERR_INVALID_ARG;
+  if (p->closure == FE_FOURIER && !(p->Pr > 0.0)) return FE_ERR_INVALID_ARG;
+  if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED)
+    return FE_ERR_INVALID_ARG;
+  if (p->transonic && p->solver == FE_PCG_JACOBI) return FE_ERR_INVALID_ARG;
+  if (p->solver == FE_FCG_LEARNED) return FE_ERR_UNSUPPORTED;
+  for (int b = 0; b < p->n_boxes; ++b)
+    if (p->N[b] < 8 || p->N[b] > 512 || !(p->nu[b] >= 0.0)) return FE_ERR_INVALID_ARG;
+  return FE_OK;
+}
+
+static int tz_for(int N) { return N >= 128 ? 8 : 4; }
+
+extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
+  if (!out) return FE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int v = validate(prm);
+  if (v != FE_OK) return v;
+  fe_ctx* c = new (std::nothrow) fe_ctx();
+  if (!c) return FE_ERR_OOM;
+  c->prm = *prm;
+  c->nb = prm->n_boxes;
+  c->fp64 = prm->precision == FE_FP64;
+  c->st = (cudaStream_t)stream;
+  const int nb = c->nb, nd = prm->n_dust;
+  c->N.assign(prm->N, prm->N + nb);
+  c->nu.assign(prm->nu, prm->nu + nb);
+  c->mach.assign(prm->mach_rms, prm->mach_rms + nb);
+  c->k0.assign(prm->k0, prm->k0 + nb);
+  c->seed.assign(prm->seed, prm->seed + nb);
+  if (nd > 0) {
+    c->tau_p.assign(prm->tau_p, prm->tau_p + (size_t)nb * nd);
+    c->Y0.assign(prm->Y0, prm->Y0 + (size_t)nb * nd);
+  }
+  c->prm.N = c->N.data();
+  c->prm.nu = c->nu.data();
+  c->prm.mach_rms = c->mach.data();
+  c->prm.k0 = c->k0.data();
+  c->prm.seed = c->seed.data();
+  c->prm.tau_p = nd ? c->tau_p.data() : nullptr;
+  c->prm.Y0 = nd ? c->Y0.data() : nullptr;
+
+  // work list and descriptors
+  std::vector<int2> work;
+  c->hbox.resize(nb);
+  std::vector<std::pair<int, size_t>> plan;
+  slot_plan(c, plan);
+  int rc = FE_OK;
+  for (int b = 0; b < nb && rc == FE_OK; ++b) {
+    BoxDev& B = c->hbox[b];
+    memset(&B, 0, sizeof(B));
+    const int N = c->N[b];
+    B.N = N;
+    B.nd = nd;
+    B.closure = prm->closure;
+    B.transonic = prm->transonic;
+    B.tz = tz_for(N);
+    B.tnx = (N + TX - 1) / TX;
+    B.tny = (N + TY - 1) / TY;
+    B.tnz = (N + B.tz - 1) / B.tz;
+    B.ntiles = B.tnx * B.tny * B.tnz;
+    B.tile0 = (int)work.size();
+    for (int q = 0; q < B.ntiles; ++q) work.push_back(make_int2(b, q));
+    B.h = 2.0 * M_PI / N;
+    B.ih = 1.0 / B.h;
+    B.mu = c->nu[b];
+    B.gamma = prm->gamma;
+    B.R = 1.0 / prm->gamma;
+    B.cv = B.R / (prm->gamma - 1.0);
+    B.kappa = prm->closure == FE_FOURIER ? B.mu * prm->gamma * B.cv / prm->Pr : 0.0;
+    B.cfl = prm->cfl;
+    B.growth = prm->dt_growth_max > 0 ? prm->dt_growth_max : HUGE_VAL;
+    B.dtmax = prm->dt_max > 0 ? prm->dt_max : HUGE_VAL;
+    for (int j = 0; j < nd; ++j) B.tau_p[j] = c->tau_p[(size_t)b * nd + j];
+    size_t total = 0;
+    for (auto& s : plan) total += slot_bytes(N, s.second);
+    void* slab = nullptr;
+    if (cudaMalloc(&slab, total) != cudaSuccess) {
+      rc = FE_ERR_OOM;
+      break;
+    }
+    c->slabs.push_back(slab);
+    cudaMemsetAsync(slab, 0, total, c->st);
+    size_t off = 0;
+    for (auto& s : plan) {
+      B.f[s.first] = (char*)slab + off;
+      off += slot_bytes(N, s.second);
+    }
+  }
+  if (rc == FE_OK) {
+    c->nblocks = (int)work.size();
+    if (cudaMalloc(&c->dbox, nb * sizeof(BoxDev)) != cudaSuccess ||
+        cudaMalloc(&c->dwork, work.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&c->dpart, (size_t)c->nblocks * MAXP * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->dsc, (size_t)nb * NSC * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->dcnt, nb * sizeof(int)) != cudaSuccess || cudaMalloc(&c->dactive, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->hactive, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->hsc, (size_t)nb * NSC * sizeof(double)) != cudaSuccess)
+      rc = FE_ERR_OOM;
+  }
+  if (rc == FE_OK) {
+    memset(c->hsc, 0, (size_t)nb * NSC * sizeof(double));
+    for (int b = 0; b < nb; ++b) {
+      c->hbox[b].sc = c->dsc + (size_t)b * NSC;
+      c->hbox[b].cnt = c->dcnt + b;
+      double* s = c->hsc + (size_t)b * NSC;
+      s[SC_TOL] = prm->p_tol;
+      s[SC_MAXIT] = prm->p_maxit;
+      s[SC_DONE] = 1.0;
+    }
+    cudaMemcpyAsync(c->dbox, c->hbox.data(), nb * sizeof(BoxDev), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->dwork, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->dsc, c->hsc, (size_t)nb * NSC * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(c->dcnt, 0, nb * sizeof(int), c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = FE_ERR_CUDA;
+  }
+  if (rc != FE_OK) {
+    fe_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return FE_OK;
+}
+
+extern "C" void fe_destroy(fe_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (void* s : c->slabs) cudaFree(s);
+  for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  cudaFree(c->dbox);
+  cudaFree(c->dwork);
+  cudaFree(c->dpart);
+  cudaFree(c->dsc);
+  cudaFree(c->dcnt);
+  cudaFree(c->dactive);
+  if (c->hactive) cudaFreeHost(c->hactive);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  delete c;
+}
+
+extern "C" const char* fe_strerror(int code) {
+  switch (code) {
+    case FE_OK: return "ok";
+    case FE_ERR_INVALID_ARG: return "invalid argument";
+    case FE_ERR_CUDA: return "CUDA error";
+    case FE_ERR_NOT_CONVERGED: return "pressure solve did not converge";
+    case FE_ERR_NONFINITE: return "non-finite value in the new state";
+    case FE_ERR_OOM: return "out of device memory";
+    case FE_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+// ---- helpers ---------------------------------------------------------------------------------
+static int field_slot(const fe_ctx* c, int field, int set) {
+  if (field >= FE_RHO && field <= FE_UZ) return S(set, F_RHO + field);  // RHO, U0..2 line up
+  if (field == FE_P) return S(set, F_P);
+  if (field == FE_T) return c->prm.closure == FE_FOURIER ? S(set, F_T) : -1;
+  if (field >= FE_PHIX && field <= FE_PHIZ) return S(set, F_PHI0 + (field - FE_PHIX));
+  if (field >= FE_Y0 && field < FE_Y0 + c->prm.n_dust) return S(set, F_Y0 + (field - FE_Y0));
+  return -1;
+}
+
+static int pull_scalars(fe_ctx* c) {
+  CK(cudaMemcpyAsync(c->hsc, c->dsc, (size_t)c->nb * NSC * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+static int push_scalar(fe_ctx* c, int box, int idx, double v) {
+  c->hsc[(size_t)box * NSC + idx] = v;
+  CK(cudaMemcpyAsync(c->dsc + (size_t)box * NSC + idx, c->hsc + (size_t)box * NSC + idx, sizeof(double),
+                     cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+// Krylov driver for all boxes: operator/psi/dt already in place, rhs in K_B.
+template <typename T>
+static int krylov(fe_ctx* c, int maxit) {
+  Launch L = c->L();
+  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
+  const bool bicg = c->prm.solver == FE_BICGSTAB_JACOBI;
+  if (bicg) launch_bicg_init<T>(L);
+  else launch_cg_init<T>(L, 0.0);
+  int it = 0;
+  while (true) {
+    CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (*c->hactive == 0 || it >= maxit) break;
+    for (int q = 0; q < c->poll && it < maxit; ++q, ++it) {
+      if (bicg) {
+        launch_bicg_p<T>(L);
+        launch_bicg_v<T>(L);
+        launch_bicg_s<T>(L);
+        launch_bicg_x<T>(L);
+      } else {
+        launch_cg_matvec<T>(L);
+        launch_cg_update<T>(L);
+        launch_cg_dir<T>(L);
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  return FE_OK;
+}
+
+__global__ void k_commit(double* sc, int nb) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double* s = sc + (size_t)b * NSC;
+  s[SC_TIME] += s[SC_DT];
+  s[SC_DTPREV] = s[SC_DT];
+}
+
+template <typename T>
+static int step_once(fe_ctx* c) {
+  Launch L = c->L();
+  const int s = c->cur, ks = 1 - s, nc = c->prm.n_corr;
+  launch_dt<T>(L, s, 0);
+  launch_div<T>(L, S(s, F_U0));
+  launch_pred<T>(L, s, ks);
+  launch_fluxn<T>(L, s);
+  for (int kk = 0; kk < nc; ++kk) {
+    const int rhop = S(ks, F_RHO);
+    const int up0 = S(ks, F_U0);
+    const int php0 = kk == 0 ? S(s, F_PHI0) : S(ks, F_PHI0);
+    const int pp = kk == 0 ? S(s, F_P) : W_PW0 + ((kk - 1) & 1);
+    const int pn = W_PW0 + (kk & 1);
+    if (kk == 0) launch_div<T>(L, up0);
+    launch_asm<T>(L, s, up0, php0, rhop);
+    launch_rhs<T>(L, s, rhop, pp);
+    int rc = krylov<T>(c, c->prm.p_maxit);
+    if (rc != FE_OK) return rc;
+    launch_corr<T>(L, s, rhop, pp, pn, ks, kk);
+    launch_div<T>(L, S(ks, F_U0));
+    launch_accel<T>(L, ks, pn);
+    const bool last = kk == nc - 1;
+    const int yp0 = kk == 0 ? S(s, F_Y0) : W_YW0 + ((kk - 1) & 1) * MAXD;
+    const int yn0 = last ? S(ks, F_Y0) : W_YW0 + (kk & 1) * MAXD;
+    const int ep = kk == 0 ? -1 : W_EW0 + ((kk - 1) & 1);
+    const int en = last ? -1 : W_EW0 + (kk & 1);
+    launch_dust<T>(L, s, ks, pn, yp0, yn0, ep, en, last ? 1 : 0, kk == 0 ? 1 : 0);
+  }
+  CK(cudaGetLastError());
+  int rc = pull_scalars(c);
+  if (rc != FE_OK) return rc;
+  for (int b = 0; b < c->nb; ++b) {
+    const double* sc = c->hsc + (size_t)b * NSC;
+    if (sc[SC_BAD] > 0.0 || !std::isfinite(sc[SC_DT])) return FE_ERR_NONFINITE;
+    for (int kk = 0; kk < nc; ++kk)
+      if (!(sc[SC_RES0 + kk] <= c->prm.p_tol * (1.0 + 1e-6)) && sc[SC_IT0 + kk] >= c->prm.p_maxit)
+        return FE_ERR_NOT_CONVERGED;
+  }
+  {
+    Launch L2 = c->L();
+    FE_LAUNCH(L2, KID_COMMIT, (k_commit<<<(c->nb + 127) / 128, 128, 0, c->st>>>(c->dsc, c->nb)));
+  }
+  CK(cudaGetLastError());
+  c->cur = ks;
+  return FE_OK;
+}
+
+extern "C" int fe_step(fe_ctx* c, int nsteps, fe_step_info* info) {
+  if (!c || nsteps < 0) return FE_ERR_INVALID_ARG;
+  for (int n = 0; n < nsteps; ++n) {
+    int rc = c->fp64 ? step_once<double>(c) : step_once<float>(c);
+    if (rc != FE_OK) return rc;
+  }
+  if (info) {
+    int rc = pull_scalars(c);
+    if (rc != FE_OK) return rc;
+    for (int b = 0; b < c->nb; ++b) {
+      const double* sc = c->hsc + (size_t)b * NSC;
+      info[b].t = sc[SC_TIME];
+      info[b].dt = sc[SC_DTPREV];
+      for (int k = 0; k < 4; ++k) {
+        info[b].iters[k] = k < c->prm.n_corr ? (int)sc[SC_IT0 + k] : 0;
+        info[b].rel_res[k] = k < c->prm.n_corr ? sc[SC_RES0 + k] : 0.0;
+      }
+    }
+  }
+  return FE_OK;
+}
+
+extern "C" int fe_set_field(fe_ctx* c, int box, int field, const void* src, int is_dev) {
+  if (!c || !src || box < 0 || box >= c->nb) return FE_ERR_INVALID_ARG;
+  int slot = field_slot(c, field, c->cur);
+  if (slot < 0) return FE_ERR_INVALID_ARG;
+  const int N = c->N[box];
+  size_t bytes = (size_t)N * N * N * (c->fp64 ? 8 : 4);
+  CK(cudaMemcpyAsync(c->hbox[box].f[slot], src, bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+extern "C" int fe_get_field(fe_ctx* c, int box, int field, void* dst, int is_dev) {
+  if (!c || !dst || box < 0 || box >= c->nb) return FE_ERR_INVALID_ARG;
+  int slot = field_slot(c, field, c->cur);
+  if (slot < 0) return FE_ERR_INVALID_ARG;
+  const int N = c->N[box];
+  size_t bytes = (size_t)N * N * N * (c->fp64 ? 8 : 4);
+  CK(cudaMemcpyAsync(dst, c->hbox[box].f[slot], bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+extern "C" int fe_set_clock(fe_ctx* c, int box, double t, double dt_prev) {
+  if (!c || box < 0 || box >= c->nb) return FE_ERR_INVALID_ARG;
+  int rc = push_scalar(c, box, SC_TIME, t);
+  if (rc != FE_OK) return rc;
+  return push_scalar(c, box, SC_DTPREV, dt_prev > 0.0 ? dt_prev : 0.0);
+}
+
+template <typename T>
+static int init_box(fe_ctx* c, int b, int mode) {
+  BoxDev& B = c->hbox[b];
+  const int s = c->cur;
+  const long n = (long)B.N * B.N * B.N;
+  if (mode == FE_INIT_SPECTRAL) {
+    if (!fft_supported(B.N)) return FE_ERR_UNSUPPORTED;
+    int rc = ic_spectral<T>((T*)B.f[S(s, F_U0)], (T*)B.f[S(s, F_U1)], (T*)B.f[S(s, F_U2)], B.N, c->seed[b], c->k0[b],
+                            c->mach[b], c->st);
+    if (rc != FE_OK) return rc;
+    fill<T>((T*)B.f[S(s, F_RHO)], n, 1.0, c->st);
+    if (c->prm.closure == FE_FOURIER) fill<T>((T*)B.f[S(s, F_T)], n, 1.0, c->st);
+    for (int j = 0; j < B.nd; ++j) fill<T>((T*)B.f[S(s, F_Y0 + j)], n, c->Y0[(size_t)b * B.nd + j], c->st);
+  }
+  launch_derive_box<T>(c->L(), s, b);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  int rc = push_scalar(c, b, SC_TIME, 0.0);
+  if (rc != FE_OK) return rc;
+  return push_scalar(c, b, SC_DTPREV, 0.0);
+}
+
+extern "C" int fe_init_state(fe_ctx* c, int box, int mode) {
+  if (!c || box < -1 || box >= c->nb || (mode != FE_INIT_SPECTRAL && mode != FE_INIT_DERIVE))
+    return FE_ERR_INVALID_ARG;
+  for (int b = (box < 0 ? 0 : box); b < (box < 0 ? c->nb : box + 1); ++b) {
+    int rc = c->fp64 ? init_box<double>(c, b, mode) : init_box<float>(c, b, mode);
+    if (rc != FE_OK) return rc;
+  }
+  return FE_OK;
+}
+
+template <typename T>
+__global__ void k_psi_box(const BoxDev* boxes, int box, int s) {
+  const BoxDev& B = boxes[box];
+  const long n = (long)B.N * B.N * B.N;
+  const T* rho = (const T*)B.f[S(s, F_RHO)];
+  const T* p = (const T*)B.f[S(s, F_P)];
+  T* psi = (T*)B.f[W_PSI];
+  T* hb[3] = {(T*)B.f[W_HB0], (T*)B.f[W_HB1], (T*)B.f[W_HB2]};
+  const T* u[3] = {(const T*)B.f[S(s, F_U0)], (const T*)B.f[S(s, F_U1)], (const T*)B.f[S(s, F_U2)]};
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    psi[q] = rho[q] / ((T)B.gamma * p[q]);
+    for (int d = 0; d < 3; ++d) hb[d][q] = u[d][q];
+  }
+}
+
+template <typename T>
+static int solve_box(fe_ctx* c, int box, const void* b, void* x, double dt, double tol, int maxit,
+                     fe_solve_info* info) {
+  BoxDev& B = c->hbox[box];
+  const size_t bytes = (size_t)B.N * B.N * B.N * sizeof(T);
+  // other boxes stay idle: mark them done for this solve
+  int rc = pull_scalars(c);
+  if (rc != FE_OK) return rc;
+  std::vector<double> saved((size_t)c->nb * NSC);
+  memcpy(saved.data(), c->hsc, saved.size() * sizeof(double));
+  k_psi_box<T><<<1024, 256, 0, c->st>>>(c->dbox, box, c->cur);
+  CK(cudaMemcpyAsync(B.f[K_B], b, bytes, cudaMemcpyDeviceToDevice, c->st));
+  for (int q = 0; q < c->nb; ++q) {
+    double* s = c->hsc + (size_t)q * NSC;
+    s[SC_KDT] = dt;
+    s[SC_TOL] = tol;
+    s[SC_MAXIT] = maxit;
+  }
+  CK(cudaMemcpyAsync(c->dsc, c->hsc, (size_t)c->nb * NSC * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  // zero rhs of the other boxes so their solves end at once
+  for (int q = 0; q < c->nb; ++q)
+    if (q != box) CK(cudaMemsetAsync(c->hbox[q].f[K_B], 0, (size_t)c->N[q] * c->N[q] * c->N[q] * sizeof(T), c->st));
+  rc = krylov<T>(c, maxit);
+  if (rc != FE_OK) return rc;
+  launch_true_res<T>(c->L(), K_X);
+  CK(cudaMemcpyAsync(x, B.f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
+  rc = pull_scalars(c);
+  if (rc != FE_OK) return rc;
+  const double* s = c->hsc + (size_t)box * NSC;
+  fe_solve_info inf;
+  inf.iters = (int)s[SC_ITERS];
+  inf.rel_res_true = s[SC_BB] > 0 ? sqrt(s[SC_TRUE_RR] / s[SC_BB]) : 0.0;
+  bool conv = s[SC_CONV] != 0.0;
+  if (info) *info = inf;
+  // restore the step scalars (tolerance, cap, dt) of every box
+  memcpy(c->hsc, saved.data(), saved.size() * sizeof(double));
+  CK(cudaMemcpyAsync(c->dsc, c->hsc, (size_t)c->nb * NSC * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return conv ? FE_OK : FE_ERR_NOT_CONVERGED;
+}
+
+extern "C" int fe_solve_pressure(fe_ctx* c, int box, const void* b, void* x, double dt, double tol, int maxit,
+                                 fe_solve_info* info) {
+  if (!c || !b || !x || box < 0 || box >= c->nb || !(dt > 0.0) || !(tol > 0.0) || maxit < 1)
+    return FE_ERR_INVALID_ARG;
+  return c->fp64 ? solve_box<double>(c, box, b, x, dt, tol, maxit, info)
+                 : solve_box<float>(c, box, b, x, dt, tol, maxit, info);
+}
+
+template <typename T>
+static int diag_box(fe_ctx* c, int box, fe_diag* out, double* spec, int nbins) {
+  BoxDev& B = c->hbox[box];
+  double sums[7 + MAXD];
+  int rc = diag_sums<T>(c->L(), B, box, c->cur, sums);
+  if (rc != FE_OK) return rc;
+  const double n = (double)B.N * B.N * B.N, vol = B.h * B.h * B.h;
+  memset(out, 0, sizeof(*out));
+  out->ke = 0.5 * sums[0] / n;
+  out->ke_u = 0.5 * sums[1] / n;
+  out->enstrophy = 0.5 * sums[2] / n;
+  out->taylor = sums[3] > 0 ? sqrt(sums[1] / sums[3]) : 0.0;
+  out->rho_rms = sqrt(sums[5] / n);
+  out->mass = vol * sums[4];
+  out->energy = vol * sums[6];
+  for (int j = 0; j < B.nd; ++j) out->dust_mass[j] = vol * sums[7 + j];
+  rc = pull_scalars(c);
+  if (rc != FE_OK) return rc;
+  out->t = c->hsc[(size_t)box * NSC + SC_TIME];
+  out->dt_prev = c->hsc[(size_t)box * NSC + SC_DTPREV];
+  if (spec && nbins > 0) {
+    if (!fft_supported(B.N)) return FE_ERR_UNSUPPORTED;
+    const int s = c->cur;
+    rc = spectrum<T>((const T*)B.f[S(s, F_U0)], (const T*)B.f[S(s, F_U1)], (const T*)B.f[S(s, F_U2)], B.N, spec, nbins,
+                     c->st);
+    if (rc != FE_OK) return rc;
+  }
+  return FE_OK;
+}
+
+extern "C" int fe_diagnostics(fe_ctx* c, int box, fe_diag* out, double* spectrum_host, int nbins) {
+  if (!c || !out || box < 0 || box >= c->nb || nbins < 0 || (nbins > 0 && !spectrum_host)) return FE_ERR_INVALID_ARG;
+  return c->fp64 ? diag_box<double>(c, box, out, spectrum_host, nbins)
+                 : diag_box<float>(c, box, out, spectrum_host, nbins);
+}
+
+extern "C" int fe_q_criterion(fe_ctx* c, int box, void* q) {
+  if (!c || !q || box < 0 || box >= c->nb) return FE_ERR_INVALID_ARG;
+  if (c->fp64) qcrit<double>(c->L(), box, c->cur, (double*)q);
+  else qcrit<float>(c->L(), box, c->cur, (float*)q);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+extern "C" int fe_profile_start(fe_ctx* c, int kernel_id) {
+  if (!c || kernel_id < -1 || kernel_id >= KID_COUNT) return FE_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  c->prof.on = true;
+  c->prof.target = kernel_id;
+  c->prof.used = 0;
+  c->prof.failed = false;
+  for (int k = 0; k < KID_COUNT; ++k) c->prof.count[k] = 0;
+  return FE_OK;
+}
+
+extern "C" int fe_profile_stop(fe_ctx* c, fe_profile_info* out) {
+  if (!c || !out) return FE_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  memset(out, 0, sizeof(*out));
+  double ms = 0.0;
+  for (size_t i = 0; i < c->prof.used; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->prof.ev[2 * i], c->prof.ev[2 * i + 1]));
+    ms += t;
+  }
+  long long tot = 0;
+  for (int k = 0; k < KID_COUNT; ++k) {
+    tot += c->prof.count[k];
+    if (k < FE_PROFILE_MAX_KERNELS) out->counts[k] = c->prof.count[k];
+  }
+  out->launches = tot;
+  out->target_launches = (int64_t)c->prof.used;
+  out->target_ms = ms;
+  c->prof.on = false;
+  return c->prof.failed ? FE_ERR_CUDA : FE_OK;
+}
+
+extern "C" int fe_kernel_count(void) { return KID_COUNT; }
+
+extern "C" const char* fe_kernel_name(int id) {
+  if (id < 0 || id >= KID_COUNT) return "";
+  return kKernelNames[id];
+}

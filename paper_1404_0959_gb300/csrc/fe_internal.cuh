@@ -1,0 +1,306 @@
+// fe_internal.cuh -- device-side data model, stencils and reductions of libfe.
+//
+// Data model (one context = n_boxes independent periodic boxes):
+//  * every field of a box is an N^3 SoA array, x fastest; a face array of
+//    direction d stores at cell c the value on the face between c and c+e_d;
+//  * a box descriptor (BoxDev) holds the box constants and a table of field
+//    pointers indexed by slot; kernels name fields by slot so the host can
+//    swap time levels without moving data;
+//  * every stencil kernel is launched once for all boxes over a work list of
+//    (box, tile) pairs; a tile is 32 (x) x 8 (y) cells times tz z-planes and
+//    is processed by a 32 x 8 thread block that walks the z-planes;
+//  * reductions are deterministic: each block writes its partial sums to a
+//    fixed slot, the last block of a box (found with one atomic counter, no
+//    waiting) adds the partials in index order and updates the box scalars.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fe.h"
+
+namespace fe {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NTHR = TX * TY;
+constexpr int MAXD = FE_MAX_DUST;
+constexpr int MAXP = 16;  // partial sums per block
+
+// ---- field slots -----------------------------------------------------------
+// state set s (0 or 1): base s * NSF
+enum StateField { F_RHO = 0, F_U0, F_U1, F_U2, F_PHI0, F_PHI1, F_PHI2, F_P, F_T, F_Y0, NSF = F_Y0 + MAXD };
+__host__ __device__ constexpr int S(int set, int f) { return set * NSF + f; }
+enum WorkSlot {
+  W_BASE = 2 * NSF,
+  W_DIV = W_BASE,  // cell divergence of the velocity last differentiated
+  W_DIVPHI,        // D(phi^n)
+  W_RN0, W_RN1, W_RN2,    // R^n
+  W_AN0, W_AN1, W_AN2,    // Du/Dt (level n, then level k)
+  W_PSI,                  // rho^n / (gamma p^n)
+  W_HB0, W_HB1, W_HB2,    // HbyA
+  W_PS0, W_PS1, W_PS2,    // phi*
+  W_PW0, W_PW1,           // p^k ping-pong
+  W_EW0, W_EW1,           // E^k ping-pong (Fourier)
+  W_FEN,                  // D(F_E^n) (Fourier)
+  W_FYN0,                 // D(phi_p^n I4 Y^n), MAXD slots
+  W_YW0 = W_FYN0 + MAXD,  // Y^k ping 0, MAXD slots
+  W_YW1 = W_YW0 + MAXD,   // Y^k ping 1, MAXD slots
+  // Krylov vectors
+  K_B = W_YW1 + MAXD, K_X, K_R, K_PD, K_Q,
+  K_RHAT, K_V, K_S, K_T,  // BiCGStab
+  K_Z, K_PP, K_QP,        // flexible CG: preconditioned r, previous direction and its image
+  K_X64,                  // double accumulator (mixed precision refinement)
+  K_B64,                  // double right-hand side (mixed precision refinement)
+  K_AUX,                  // scratch (diagnostics, user solve)
+  NSLOT
+};
+
+// ---- per-box scalars (double) ---------------------------------------------
+enum Scalar {
+  SC_DT = 0, SC_DTPREV, SC_TIME, SC_UMAX,
+  SC_RZ, SC_ALPHA, SC_BETA, SC_PQ, SC_BB, SC_RR, SC_DONE, SC_ITERS, SC_CONV, SC_TRUE_RR,
+  SC_RHO_OLD, SC_OMEGA, SC_RV, SC_TS, SC_TT, SC_RHAT_R,  // BiCGStab
+  SC_ZQ, SC_PR,                                           // flexible CG
+  SC_TOL, SC_MAXIT, SC_KDT,   // Krylov tolerance, cap and the dt of its operator
+  SC_IT0, SC_IT1, SC_IT2, SC_IT3, SC_RES0, SC_RES1, SC_RES2, SC_RES3,
+  SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
+  NSC = SC_DUST0 + MAXD + 4
+};
+
+struct BoxDev {
+  int N, nd, closure, transonic;
+  int tnx, tny, tnz, tz;   // tile grid and planes per tile
+  int tile0, ntiles;       // this box's blocks in the work list
+  double h, ih, mu, gamma, R, cv, kappa, cfl, growth, dtmax;
+  double tau_p[MAXD];
+  void* f[NSLOT];
+  double* sc;   // NSC scalars
+  int* cnt;     // reduction counter (reset by the last block)
+};
+
+// ---- indexing ----------------------------------------------------------------
+__device__ __forceinline__ int wrapi(int v, int N) {
+  v += (v < 0) ? N : 0;
+  v -= (v >= N) ? N : 0;
+  return v;
+}
+
+// Wrapped flat offsets of the cells at -4..+4 along each axis.
+struct Nbr {
+  int x[9], y[9], z[9];
+  __device__ __forceinline__ Nbr(int i, int j, int k, int N) {
+#pragma unroll
+    for (int s = -4; s <= 4; ++s) {
+      x[s + 4] = wrapi(i + s, N);
+      y[s + 4] = wrapi(j + s, N) * N;
+      z[s + 4] = wrapi(k + s, N) * N * N;
+    }
+  }
+  __device__ __forceinline__ int operator()(int dx, int dy, int dz) const { return x[dx + 4] + y[dy + 4] + z[dz + 4]; }
+  // cell at offset o (given as a triple) shifted by s along d
+  __device__ __forceinline__ int at(int d, int ox, int oy, int oz, int s) const {
+    return (*this)(ox + (d == 0 ? s : 0), oy + (d == 1 ? s : 0), oz + (d == 2 ? s : 0));
+  }
+};
+
+// ---- stencils (value type T, arrays of type A) --------------------------------
+// I4 along d on the face between cell o and o+e_d
+template <typename T, typename A>
+__device__ __forceinline__ T I4f(const A* f, const Nbr& n, int d, int ox, int oy, int oz) {
+  T a = (T)f[n.at(d, ox, oy, oz, -1)], b = (T)f[n.at(d, ox, oy, oz, 0)];
+  T c = (T)f[n.at(d, ox, oy, oz, 1)], e = (T)f[n.at(d, ox, oy, oz, 2)];
+  return (T(9) * (b + c) - (a + e)) * T(0.0625);
+}
+// G4 along d on the face between o and o+e_d (times h: caller multiplies by ih)
+template <typename T, typename A>
+__device__ __forceinline__ T G4f_h(const A* f, const Nbr& n, int d, int ox, int oy, int oz) {
+  T a = (T)f[n.at(d, ox, oy, oz, -1)], b = (T)f[n.at(d, ox, oy, oz, 0)];
+  T c = (T)f[n.at(d, ox, oy, oz, 1)], e = (T)f[n.at(d, ox, oy, oz, 2)];
+  return (T(27) * (c - b) - (e - a)) * T(1.0 / 24.0);
+}
+// Gauss cell gradient along d at cell o (times h)
+template <typename T, typename A>
+__device__ __forceinline__ T Gc_h(const A* f, const Nbr& n, int d, int ox, int oy, int oz) {
+  T m2 = (T)f[n.at(d, ox, oy, oz, -2)], m1 = (T)f[n.at(d, ox, oy, oz, -1)];
+  T p1 = (T)f[n.at(d, ox, oy, oz, 1)], p2 = (T)f[n.at(d, ox, oy, oz, 2)];
+  return (T(10) * (p1 - m1) - (p2 - m2)) * T(0.0625);
+}
+// D o G4 along d at cell o (times h^2)
+template <typename T, typename A>
+__device__ __forceinline__ T DG4_h2(const A* f, const Nbr& n, int d, int ox, int oy, int oz) {
+  T m2 = (T)f[n.at(d, ox, oy, oz, -2)], m1 = (T)f[n.at(d, ox, oy, oz, -1)];
+  T c0 = (T)f[n.at(d, ox, oy, oz, 0)];
+  T p1 = (T)f[n.at(d, ox, oy, oz, 1)], p2 = (T)f[n.at(d, ox, oy, oz, 2)];
+  return (T(28) * (m1 + p1) - T(54) * c0 - (m2 + p2)) * T(1.0 / 24.0);
+}
+
+// ---- block prologue -----------------------------------------------------------
+struct Tile {
+  int box, i, j, k0, kend;
+  bool active;
+};
+__device__ __forceinline__ Tile tile_of(const BoxDev* boxes, const int2* work) {
+  int2 w = work[blockIdx.x];
+  const BoxDev& B = boxes[w.x];
+  Tile t;
+  t.box = w.x;
+  int tx = w.y % B.tnx;
+  int r = w.y / B.tnx;
+  int ty = r % B.tny;
+  int tzb = r / B.tny;
+  t.i = tx * TX + threadIdx.x;
+  t.j = ty * TY + threadIdx.y;
+  t.k0 = tzb * B.tz;
+  t.kend = min(t.k0 + B.tz, B.N);
+  t.active = (t.i < B.N) && (t.j < B.N);
+  return t;
+}
+
+// ---- deterministic reductions ----------------------------------------------------
+// Block-sum K doubles (fixed tree), write this block's partials, and report
+// whether this is the box's last block; if so `res` (shared) holds the box
+// totals (partials added in block order).  Must be called by all threads.
+template <int K>
+__device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res) {
+  __shared__ double red[K][NTHR / 32];
+  __shared__ int last;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[q][warp] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
+      part[(size_t)blockIdx.x * MAXP + q] = s;
+    }
+    __threadfence();
+    int prev = atomicAdd(B.cnt, 1);
+    last = (prev == B.ntiles - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = 0.0;
+    for (int b = tid; b < B.ntiles; b += NTHR) s += __ldcg(&part[(size_t)(B.tile0 + b) * MAXP + q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[q][warp] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
+      res[q] = s;
+    }
+    *B.cnt = 0;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Same for a maximum of one value.
+__device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double* part, double* res) {
+  __shared__ double red[NTHR / 32];
+  __shared__ int last;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  double s = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double m = red[0];
+    for (int w = 1; w < NTHR / 32; ++w) m = fmax(m, red[w]);
+    part[(size_t)blockIdx.x * MAXP] = m;
+    __threadfence();
+    int prev = atomicAdd(B.cnt, 1);
+    last = (prev == B.ntiles - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  s = 0.0;
+  for (int b = tid; b < B.ntiles; b += NTHR) s = fmax(s, __ldcg(&part[(size_t)(B.tile0 + b) * MAXP]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double m = red[0];
+    for (int w = 1; w < NTHR / 32; ++w) m = fmax(m, red[w]);
+    *res = m;
+    *B.cnt = 0;
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---- launch plumbing ------------------------------------------------------------
+// Kernel ids (instrumentation: launch counts and CUDA-event timing of one id).
+enum KernelId {
+  KID_DT = 0, KID_DIV, KID_PRED, KID_FLUXN, KID_ASM, KID_RHS, KID_CORR, KID_ACCEL, KID_DUST, KID_DERIVE,
+  KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
+  KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
+  KID_COMMIT, KID_OTHER, KID_COUNT
+};
+
+struct Prof;  // defined in fe_api.cu
+void prof_begin(Prof* p, int kid, cudaStream_t st);
+void prof_end(Prof* p, int kid, cudaStream_t st);
+
+struct Launch {
+  const BoxDev* boxes;
+  const int2* work;
+  int nblocks;
+  double* part;
+  int* active;  // number of boxes whose Krylov solve is running
+  cudaStream_t st;
+  Prof* prof;
+};
+
+// Launch `call` (a kernel launch statement) under instrumentation id kid.
+#define FE_LAUNCH(L, kid, call)          \
+  do {                                   \
+    prof_begin((L).prof, (kid), (L).st); \
+    call;                                \
+    prof_end((L).prof, (kid), (L).st);   \
+  } while (0)
+
+// Step kernels (step_kernels.cu); T = field type.
+template <typename T> void launch_dt(const Launch& L, int s, int first);
+template <typename T> void launch_div(const Launch& L, int uslot0);
+template <typename T> void launch_pred(const Launch& L, int s, int k);
+template <typename T> void launch_fluxn(const Launch& L, int s);
+template <typename T> void launch_asm(const Launch& L, int s, int uprev0, int phiprev0, int rhoprev);
+template <typename T> void launch_rhs(const Launch& L, int s, int rhoprev, int pprev);
+template <typename T> void launch_corr(const Launch& L, int s, int rhoprev, int pprev, int pnew, int kset, int kidx);
+template <typename T> void launch_accel(const Launch& L, int kset, int pk);
+template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yprev0, int ynew0, int eprev,
+                                      int enew, int last, int first);
+template <typename T> void launch_derive_box(const Launch& L, int s, int box);
+// Krylov kernels (krylov_kernels.cu); V = vector type.
+template <typename V> void launch_cg_init(const Launch& L, double dt_override);
+template <typename V> void launch_cg_matvec(const Launch& L);
+template <typename V> void launch_cg_update(const Launch& L);
+template <typename V> void launch_cg_dir(const Launch& L);
+template <typename V> void launch_true_res(const Launch& L, int xslot);
+template <typename V> void launch_bicg_init(const Launch& L);
+template <typename V> void launch_bicg_p(const Launch& L);
+template <typename V> void launch_bicg_v(const Launch& L);
+template <typename V> void launch_bicg_s(const Launch& L);
+template <typename V> void launch_bicg_x(const Launch& L);
+
+}  // namespace fe

@@ -1,0 +1,589 @@
+// step_kernels.cu -- the PISO step stencils (Sec. 2 par. 1 of arXiv:1404.0959:
+// PISO, fourth-order central interpolation, adaptive dt; Sec. 2 par. 2:
+// Equilibrium-Eulerian dust, Fourier / barotropic closure).
+//
+// One thread owns one (i, j) column of a tile and walks its z-planes; every
+// neighbour value is read through the read-only cache with periodic wrap.
+// The viscous term uses the identity D tau(u)_m = mu (sum_d D G4_d u_m +
+// Gc_m(div u)/3), which holds exactly for the stencils here because the Gauss
+// gradients along different axes commute on the periodic grid; the face
+// stress itself is formed only where the energy equation needs it.
+#include "fe_internal.cuh"
+
+namespace fe {
+
+template <typename T>
+__device__ __forceinline__ T* F(const BoxDev& B, int slot) {
+  return reinterpret_cast<T*>(B.f[slot]);
+}
+
+// offsets of "one cell back along d"
+__device__ __forceinline__ int bx(int d) { return d == 0 ? -1 : 0; }
+__device__ __forceinline__ int by(int d) { return d == 1 ? -1 : 0; }
+__device__ __forceinline__ int bz(int d) { return d == 2 ? -1 : 0; }
+
+// L_m(u, phi) = -D(phi_d I4_d u_m) + D tau_m and the viscous part D tau_m.
+template <typename T>
+__device__ __forceinline__ void eval_L(const T* const (&u)[3], const T* const (&phi)[3], const T* div,
+                                       const Nbr& n, T ih, T mu, T (&L)[3], T (&visc)[3]) {
+  const int c = n(0, 0, 0);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T conv = T(0), lap = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T fp = __ldg(&phi[d][c]) * I4f<T>(u[m], n, d, 0, 0, 0);
+      T fm = __ldg(&phi[d][n(bx(d), by(d), bz(d))]) * I4f<T>(u[m], n, d, bx(d), by(d), bz(d));
+      conv += fp - fm;
+      lap += DG4_h2<T>(u[m], n, d, 0, 0, 0);
+    }
+    T gdiv = Gc_h<T>(div, n, m, 0, 0, 0);
+    visc[m] = mu * (lap * ih * ih + gdiv * ih * T(1.0 / 3.0));
+    L[m] = visc[m] - conv * ih;
+  }
+}
+
+// Viscous face stress tau_dm on the d-face of cell offset o:
+// mu (G4_d u_m + I4_d Gc_m u_d - 2/3 delta_dm I4_d div).
+template <typename T>
+__device__ __forceinline__ T face_stress(const T* const (&u)[3], const T* div, const Nbr& n, int d, int m,
+                                         int ox, int oy, int oz, T ih, T mu) {
+  T g[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    int s = t - 1;
+    g[t] = Gc_h<T>(u[d], n, m, ox + (d == 0 ? s : 0), oy + (d == 1 ? s : 0), oz + (d == 2 ? s : 0));
+  }
+  T ig = (T(9) * (g[1] + g[2]) - (g[0] + g[3])) * T(0.0625);  // I4_d of h*Gc_m u_d
+  T tau = (G4f_h<T>(u[m], n, d, ox, oy, oz) + ig) * ih;
+  if (d == m) tau -= T(2.0 / 3.0) * I4f<T>(div, n, d, ox, oy, oz);  // W_DIV holds div u itself
+  return mu * tau;
+}
+
+// Total-energy face flux on the d-face of cell offset o:
+// phi I4(H) - sum_m tau_dm I4(u_m) - kappa G4(T), with H and T given per cell
+// by the functors.
+template <typename T, typename HF, typename TF>
+__device__ __forceinline__ T energy_face(const T* const (&u)[3], const T* const (&phi)[3], const T* div,
+                                         const Nbr& n, int d, int ox, int oy, int oz, T ih, T mu, T kappa,
+                                         HF Hat, TF Tat) {
+  T hq[4], tq[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    int s = t - 1;
+    int q = n.at(d, ox, oy, oz, s);
+    hq[t] = Hat(q);
+    tq[t] = Tat(q);
+  }
+  T IH = (T(9) * (hq[1] + hq[2]) - (hq[0] + hq[3])) * T(0.0625);
+  T G4T = (T(27) * (tq[2] - tq[1]) - (tq[3] - tq[0])) * T(1.0 / 24.0) * ih;
+  T work = T(0);
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    work += face_stress<T>(u, div, n, d, m, ox, oy, oz, ih, mu) * I4f<T>(u[m], n, d, ox, oy, oz);
+  T ph = __ldg(&phi[d][n(ox, oy, oz)]);
+  return ph * IH - work - kappa * G4T;
+}
+
+// ---------------------------------------------------------------------------------
+// a1: adaptive time step from max_i sum_d |u_d| of state s.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_dt(const BoxDev* boxes, const int2* work, double* part, int s) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  const T* u0 = F<T>(B, S(s, F_U0));
+  const T* u1 = F<T>(B, S(s, F_U1));
+  const T* u2 = F<T>(B, S(s, F_U2));
+  double m = 0.0;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      int c = t.i + B.N * (t.j + B.N * k);
+      double v = fabs((double)u0[c]) + fabs((double)u1[c]) + fabs((double)u2[c]);
+      m = fmax(m, v);
+    }
+  }
+  __shared__ double res;
+  if (block_max_last(m, B, part, &res)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double umax = res;
+      double dt = umax > 0.0 ? B.cfl * B.h / umax : HUGE_VAL;
+      double prev = B.sc[SC_DTPREV];
+      if (prev > 0.0) dt = fmin(dt, B.growth * prev);
+      dt = fmin(dt, B.dtmax);
+      B.sc[SC_UMAX] = umax;
+      B.sc[SC_DT] = dt;
+      B.sc[SC_KDT] = dt;
+    }
+  }
+}
+
+// cell divergence of a velocity (three consecutive slots from u0) -> W_DIV
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_div(const BoxDev* boxes, const int2* work, int u0) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* u[3] = {F<T>(B, u0), F<T>(B, u0 + 1), F<T>(B, u0 + 2)};
+  T* div = F<T>(B, W_DIV);
+  const T ih = (T)B.ih;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    T s = Gc_h<T>(u[0], n, 0, 0, 0, 0) + Gc_h<T>(u[1], n, 1, 0, 0, 0) + Gc_h<T>(u[2], n, 2, 0, 0, 0);
+    div[n(0, 0, 0)] = s * ih;
+  }
+}
+
+// a3: predictor.  Writes D(phi^n), R^n, Du/Dt at level n, psi, rho0 and u*
+// (rho0 and u* into state set kset).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  const T* u[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+  const T* phi[3] = {F<T>(B, S(s, F_PHI0)), F<T>(B, S(s, F_PHI1)), F<T>(B, S(s, F_PHI2))};
+  const T* p = F<T>(B, S(s, F_P));
+  const T* div = F<T>(B, W_DIV);
+  T* divphi = F<T>(B, W_DIVPHI);
+  T* Rn[3] = {F<T>(B, W_RN0), F<T>(B, W_RN1), F<T>(B, W_RN2)};
+  T* An[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
+  T* psi = F<T>(B, W_PSI);
+  T* rho0 = F<T>(B, S(kset, F_RHO));
+  T* us[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
+  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    T dph = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dph += __ldg(&phi[d][c]) - __ldg(&phi[d][n(bx(d), by(d), bz(d))]);
+    dph *= ih;
+    const T r = __ldg(&rho[c]);
+    const T r0 = r - dt * dph;
+    T L[3], visc[3];
+    eval_L<T>(u, phi, div, n, ih, mu, L, visc);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
+      us[m][c] = (r * __ldg(&u[m][c]) + dt * (L[m] - gp)) / r0;
+      Rn[m][c] = L[m];
+      An[m][c] = (visc[m] - gp) / r;
+    }
+    psi[c] = r / (gam * __ldg(&p[c]));
+    divphi[c] = dph;
+    rho0[c] = r0;
+  }
+}
+
+// n-level dust flux divergences D(phi_p^n I4 Y^n) and, Fourier, D(F_E^n).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fluxn(const BoxDev* boxes, const int2* work, int s) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  const T* u[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+  const T* phi[3] = {F<T>(B, S(s, F_PHI0)), F<T>(B, S(s, F_PHI1)), F<T>(B, S(s, F_PHI2))};
+  const T* a[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
+  const T ih = (T)B.ih;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    // mass-flux factor I4(rho) I4(a_d) per face, shared by all classes
+    T ra_p[3], ra_m[3], ph_p[3], ph_m[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ra_p[d] = I4f<T>(rho, n, d, 0, 0, 0) * I4f<T>(a[d], n, d, 0, 0, 0);
+      ra_m[d] = I4f<T>(rho, n, d, bx(d), by(d), bz(d)) * I4f<T>(a[d], n, d, bx(d), by(d), bz(d));
+      ph_p[d] = __ldg(&phi[d][c]);
+      ph_m[d] = __ldg(&phi[d][n(bx(d), by(d), bz(d))]);
+    }
+    for (int j = 0; j < B.nd; ++j) {
+      const T* Y = F<T>(B, S(s, F_Y0 + j));
+      const T tp = (T)B.tau_p[j];
+      T acc = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T fp = (ph_p[d] - tp * ra_p[d]) * I4f<T>(Y, n, d, 0, 0, 0);
+        T fm = (ph_m[d] - tp * ra_m[d]) * I4f<T>(Y, n, d, bx(d), by(d), bz(d));
+        acc += fp - fm;
+      }
+      F<T>(B, W_FYN0 + j)[c] = acc * ih;
+    }
+    if (B.closure == FE_FOURIER) {
+      const T* Tf = F<T>(B, S(s, F_T));
+      const T* p = F<T>(B, S(s, F_P));
+      const T* div = F<T>(B, W_DIV);
+      const T cv = (T)B.cv;
+      auto Hat = [&](int q) {
+        T uu = __ldg(&u[0][q]) * __ldg(&u[0][q]) + __ldg(&u[1][q]) * __ldg(&u[1][q]) + __ldg(&u[2][q]) * __ldg(&u[2][q]);
+        return cv * __ldg(&Tf[q]) + T(0.5) * uu + __ldg(&p[q]) / __ldg(&rho[q]);
+      };
+      auto Tat = [&](int q) { return __ldg(&Tf[q]); };
+      T acc = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        acc += energy_face<T>(u, phi, div, n, d, 0, 0, 0, ih, (T)B.mu, (T)B.kappa, Hat, Tat) -
+               energy_face<T>(u, phi, div, n, d, bx(d), by(d), bz(d), ih, (T)B.mu, (T)B.kappa, Hat, Tat);
+      }
+      F<T>(B, W_FEN)[c] = acc * ih;
+    }
+  }
+}
+
+// a4: HbyA = (rho^n u^n + dt (R^n + L(u^{k-1}, phi^{k-1}))/2) / rho^{k-1}
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
+                                               int rhop) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  const T* un[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+  const T* u[3] = {F<T>(B, up0), F<T>(B, up0 + 1), F<T>(B, up0 + 2)};
+  const T* phi[3] = {F<T>(B, php0), F<T>(B, php0 + 1), F<T>(B, php0 + 2)};
+  const T* rp = F<T>(B, rhop);
+  const T* div = F<T>(B, W_DIV);
+  const T* Rn[3] = {F<T>(B, W_RN0), F<T>(B, W_RN1), F<T>(B, W_RN2)};
+  T* hb[3] = {F<T>(B, W_HB0), F<T>(B, W_HB1), F<T>(B, W_HB2)};
+  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    T L[3], visc[3];
+    eval_L<T>(u, phi, div, n, ih, mu, L, visc);
+    const T r = __ldg(&rho[c]);
+    const T rpc = __ldg(&rp[c]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      T R = T(0.5) * (__ldg(&Rn[m][c]) + L[m]);
+      hb[m][c] = (r * __ldg(&un[m][c]) + dt * R) / rpc;
+    }
+  }
+}
+
+// a4: phi* = I4(rho^{k-1}) I4(HbyA) - dt G2(p^{k-1}); right-hand side b.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_rhs(const BoxDev* boxes, const int2* work, int s, int rhop, int pp) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  const T* rp = F<T>(B, rhop);
+  const T* p = F<T>(B, pp);
+  const T* hb[3] = {F<T>(B, W_HB0), F<T>(B, W_HB1), F<T>(B, W_HB2)};
+  const T* divphi = F<T>(B, W_DIVPHI);
+  T* ps[3] = {F<T>(B, W_PS0), F<T>(B, W_PS1), F<T>(B, W_PS2)};
+  T* b = F<T>(B, K_B);
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    T dsum = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T fp = I4f<T>(rp, n, d, 0, 0, 0) * I4f<T>(hb[d], n, d, 0, 0, 0) -
+             dt * (__ldg(&p[n.at(d, 0, 0, 0, 1)]) - __ldg(&p[c])) * ih;
+      T fm = I4f<T>(rp, n, d, bx(d), by(d), bz(d)) * I4f<T>(hb[d], n, d, bx(d), by(d), bz(d)) -
+             dt * (__ldg(&p[c]) - __ldg(&p[n.at(d, 0, 0, 0, -1)])) * ih;
+      ps[d][c] = fp;
+      dsum += fp - fm;
+    }
+    b[c] = -((__ldg(&rp[c]) - __ldg(&rho[c])) / dt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
+  }
+}
+
+// a6: p^k, phi^k, u^k, rho^k from the correction x = p'; the true residual
+// ||b - M x||^2 of the solve is accumulated on the way (same stencil reads).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_corr(const BoxDev* boxes, const int2* work, double* part, int s,
+                                                int rhop, int pp, int pnew, int kset, int kidx) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  T* rk = F<T>(B, rhop);  // rho^{k-1} in, rho^k out (own cell only)
+  const T* p = F<T>(B, pp);
+  T* pn = F<T>(B, pnew);
+  const T* x = F<T>(B, K_X);
+  const T* b = F<T>(B, K_B);
+  const T* psi = F<T>(B, W_PSI);
+  const T* hb[3] = {F<T>(B, W_HB0), F<T>(B, W_HB1), F<T>(B, W_HB2)};
+  const T* ps[3] = {F<T>(B, W_PS0), F<T>(B, W_PS1), F<T>(B, W_PS2)};
+  const T* divphi = F<T>(B, W_DIVPHI);
+  T* phk[3] = {F<T>(B, S(kset, F_PHI0)), F<T>(B, S(kset, F_PHI1)), F<T>(B, S(kset, F_PHI2))};
+  T* uk[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  const bool tr = B.transonic != 0;
+  double rr = 0.0;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      Nbr n(t.i, t.j, k, B.N);
+      const int c = n(0, 0, 0);
+      const T xc = __ldg(&x[c]);
+      const T psic = __ldg(&psi[c]);
+      T dsum = T(0), lap = T(0), trd = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T xp = __ldg(&x[n.at(d, 0, 0, 0, 1)]), xm = __ldg(&x[n.at(d, 0, 0, 0, -1)]);
+        T fp = __ldg(&ps[d][c]) - dt * (xp - xc) * ih;
+        T fm = __ldg(&ps[d][n(bx(d), by(d), bz(d))]) - dt * (xc - xm) * ih;
+        lap += (xp - xc) - (xc - xm);
+        if (tr) {
+          auto I4px = [&](int ox, int oy, int oz) {
+            T v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              int id = n.at(d, ox, oy, oz, q - 1);
+              v[q] = __ldg(&psi[id]) * __ldg(&x[id]);
+            }
+            return (T(9) * (v[1] + v[2]) - (v[0] + v[3])) * T(0.0625);
+          };
+          T tp = I4px(0, 0, 0) * I4f<T>(hb[d], n, d, 0, 0, 0);
+          T tm = I4px(bx(d), by(d), bz(d)) * I4f<T>(hb[d], n, d, bx(d), by(d), bz(d));
+          fp += tp;
+          fm += tm;
+          trd += tp - tm;
+        }
+        phk[d][c] = fp;
+        dsum += fp - fm;
+      }
+      const T rpc = rk[c];
+      pn[c] = __ldg(&p[c]) + xc;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        T g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int sft = q < 2 ? q - 2 : q - 1;  // -2, -1, +1, +2
+          int id = n.at(m, 0, 0, 0, sft);
+          g[q] = __ldg(&p[id]) + __ldg(&x[id]);
+        }
+        T gp = (T(10) * (g[2] - g[1]) - (g[3] - g[0])) * T(0.0625) * ih;
+        uk[m][c] = __ldg(&hb[m][c]) - dt / rpc * gp;
+      }
+      rk[c] = __ldg(&rho[c]) - T(0.5) * dt * (__ldg(&divphi[c]) + dsum * ih);
+      T Mx = psic * xc / dt - T(0.5) * dt * lap * ih * ih + T(0.5) * trd * ih;
+      double r = (double)__ldg(&b[c]) - (double)Mx;
+      rr += r * r;
+    }
+  }
+  double v[1] = {rr};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double bb = B.sc[SC_BB];
+      B.sc[SC_RES0 + kidx] = bb > 0.0 ? sqrt(res[0] / bb) : 0.0;
+      B.sc[SC_IT0 + kidx] = B.sc[SC_ITERS];
+    }
+  }
+}
+
+// a7: Du/Dt at level k = (-Gc p^k + D tau(u^k)) / rho^k  (W_DIV holds div u^k)
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(kset, F_RHO));
+  const T* u[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
+  const T* p = F<T>(B, pk);
+  const T* div = F<T>(B, W_DIV);
+  T* a[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
+  const T ih = (T)B.ih, mu = (T)B.mu;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    const T r = __ldg(&rho[c]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      T lap = DG4_h2<T>(u[m], n, 0, 0, 0, 0) + DG4_h2<T>(u[m], n, 1, 0, 0, 0) + DG4_h2<T>(u[m], n, 2, 0, 0, 0);
+      T visc = mu * (lap * ih * ih + Gc_h<T>(div, n, m, 0, 0, 0) * ih * T(1.0 / 3.0));
+      T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
+      a[m][c] = (visc - gp) / r;
+    }
+  }
+}
+
+// a7/a8: dust transport at level k, Fourier energy, and on the last
+// corrector the closure plus the conserved totals and a non-finite count.
+// eprev < 0: E^{k-1} = E^n from state s; enew < 0: last corrector (write T, p).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* work, double* part, int s,
+                                                int kset, int pk, int yp0, int yn0, int eprev, int enew,
+                                                int last) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  const T* rhon = F<T>(B, S(s, F_RHO));
+  const T* rho = F<T>(B, S(kset, F_RHO));
+  const T* u[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
+  const T* phi[3] = {F<T>(B, S(kset, F_PHI0)), F<T>(B, S(kset, F_PHI1)), F<T>(B, S(kset, F_PHI2))};
+  const T* a[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
+  const T* p = F<T>(B, pk);
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  const bool fourier = B.closure == FE_FOURIER;
+  double acc[3 + MAXD];
+#pragma unroll
+  for (int q = 0; q < 3 + MAXD; ++q) acc[q] = 0.0;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      Nbr n(t.i, t.j, k, B.N);
+      const int c = n(0, 0, 0);
+      const T rk = __ldg(&rho[c]);
+      const T rn = __ldg(&rhon[c]);
+      T ra_p[3], ra_m[3], ph_p[3], ph_m[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        ra_p[d] = I4f<T>(rho, n, d, 0, 0, 0) * I4f<T>(a[d], n, d, 0, 0, 0);
+        ra_m[d] = I4f<T>(rho, n, d, bx(d), by(d), bz(d)) * I4f<T>(a[d], n, d, bx(d), by(d), bz(d));
+        ph_p[d] = __ldg(&phi[d][c]);
+        ph_m[d] = __ldg(&phi[d][n(bx(d), by(d), bz(d))]);
+      }
+      for (int j = 0; j < B.nd; ++j) {
+        const T* Yp = F<T>(B, yp0 + j);
+        const T tp = (T)B.tau_p[j];
+        T fl = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T fp = (ph_p[d] - tp * ra_p[d]) * I4f<T>(Yp, n, d, 0, 0, 0);
+          T fm = (ph_m[d] - tp * ra_m[d]) * I4f<T>(Yp, n, d, bx(d), by(d), bz(d));
+          fl += fp - fm;
+        }
+        T rY = rn * __ldg(&F<T>(B, S(s, F_Y0 + j))[c]) - T(0.5) * dt * (__ldg(&F<T>(B, W_FYN0 + j)[c]) + fl * ih);
+        T Yk = rY / rk;
+        F<T>(B, yn0 + j)[c] = Yk;
+        if (last) {
+          acc[3 + j] += (double)rk * (double)Yk;
+          if (!isfinite((double)Yk)) acc[2] += 1.0;
+        }
+      }
+      T Ek = T(0);
+      if (fourier) {
+        const T* div = F<T>(B, W_DIV);
+        const T cv = (T)B.cv, Rg = (T)B.R;
+        const T* un[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+        const T* Tn = F<T>(B, S(s, F_T));
+        auto En_at = [&](int q) {
+          T uu = __ldg(&un[0][q]) * __ldg(&un[0][q]) + __ldg(&un[1][q]) * __ldg(&un[1][q]) +
+                 __ldg(&un[2][q]) * __ldg(&un[2][q]);
+          return cv * __ldg(&Tn[q]) + T(0.5) * uu;
+        };
+        const T* Ep = eprev >= 0 ? F<T>(B, eprev) : nullptr;
+        auto Hat = [&](int q) {
+          T e = Ep ? __ldg(&Ep[q]) : En_at(q);
+          return e + __ldg(&p[q]) / __ldg(&rho[q]);
+        };
+        auto Tat = [&](int q) { return __ldg(&p[q]) / (__ldg(&rho[q]) * Rg); };
+        T fl = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          fl += energy_face<T>(u, phi, div, n, d, 0, 0, 0, ih, (T)B.mu, (T)B.kappa, Hat, Tat) -
+                energy_face<T>(u, phi, div, n, d, bx(d), by(d), bz(d), ih, (T)B.mu, (T)B.kappa, Hat, Tat);
+        }
+        T rE = rn * En_at(c) - T(0.5) * dt * (__ldg(&F<T>(B, W_FEN)[c]) + fl * ih);
+        Ek = rE / rk;
+        if (enew >= 0) F<T>(B, enew)[c] = Ek;
+      }
+      if (last) {
+        T u0 = __ldg(&u[0][c]), u1 = __ldg(&u[1][c]), u2 = __ldg(&u[2][c]);
+        T uu = u0 * u0 + u1 * u1 + u2 * u2;
+        T pf;
+        if (fourier) {
+          T Tk = (Ek - T(0.5) * uu) / (T)B.cv;
+          F<T>(B, S(kset, F_T))[c] = Tk;
+          pf = rk * (T)B.R * Tk;
+          acc[1] += (double)rk * (double)Ek;
+        } else {
+          pf = pow(rk, (T)B.gamma) / (T)B.gamma;
+          acc[1] += 0.5 * (double)rk * (double)uu;
+        }
+        F<T>(B, S(kset, F_P))[c] = pf;
+        acc[0] += (double)rk;
+        if (!(isfinite((double)rk) && isfinite((double)uu) && isfinite((double)pf))) acc[2] += 1.0;
+      }
+    }
+  }
+  if (!last) return;
+  __shared__ double res[3 + MAXD];
+  if (block_sum_last<3 + MAXD>(acc, B, part, res)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_MASS] = res[0];
+      B.sc[SC_ENERGY] = res[1];
+      B.sc[SC_BAD] = res[2];
+      for (int j = 0; j < MAXD; ++j) B.sc[SC_DUST0 + j] = res[3 + j];
+    }
+  }
+}
+
+// p from the closure and phi = I4(rho) I4(u_d) for state set s.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_derive(const BoxDev* boxes, const int2* work, int s, int only_box) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active || (only_box >= 0 && t.box != only_box)) return;
+  const BoxDev& B = boxes[t.box];
+  const T* rho = F<T>(B, S(s, F_RHO));
+  const T* u[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+  T* phi[3] = {F<T>(B, S(s, F_PHI0)), F<T>(B, S(s, F_PHI1)), F<T>(B, S(s, F_PHI2))};
+  T* p = F<T>(B, S(s, F_P));
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    const T r = __ldg(&rho[c]);
+    if (B.closure == FE_FOURIER)
+      p[c] = r * (T)B.R * __ldg(&F<T>(B, S(s, F_T))[c]);
+    else
+      p[c] = pow(r, (T)B.gamma) / (T)B.gamma;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) phi[d][c] = I4f<T>(rho, n, d, 0, 0, 0) * I4f<T>(u[d], n, d, 0, 0, 0);
+  }
+}
+
+// ---- launchers --------------------------------------------------------------------
+#define GRID L.nblocks, dim3(TX, TY), 0, L.st
+template <typename T> void launch_dt(const Launch& L, int s, int) {
+  FE_LAUNCH(L, KID_DT, (k_dt<T><<<GRID>>>(L.boxes, L.work, L.part, s)));
+}
+template <typename T> void launch_div(const Launch& L, int u0) {
+  FE_LAUNCH(L, KID_DIV, (k_div<T><<<GRID>>>(L.boxes, L.work, u0)));
+}
+template <typename T> void launch_pred(const Launch& L, int s, int k) {
+  FE_LAUNCH(L, KID_PRED, (k_pred<T><<<GRID>>>(L.boxes, L.work, s, k)));
+}
+template <typename T> void launch_fluxn(const Launch& L, int s) {
+  FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T><<<GRID>>>(L.boxes, L.work, s)));
+}
+template <typename T> void launch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
+  FE_LAUNCH(L, KID_ASM, (k_asm<T><<<GRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
+}
+template <typename T> void launch_rhs(const Launch& L, int s, int rhop, int pp) {
+  FE_LAUNCH(L, KID_RHS, (k_rhs<T><<<GRID>>>(L.boxes, L.work, s, rhop, pp)));
+}
+template <typename T> void launch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx) {
+  FE_LAUNCH(L, KID_CORR, (k_corr<T><<<GRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
+}
+template <typename T> void launch_accel(const Launch& L, int kset, int pk) {
+  FE_LAUNCH(L, KID_ACCEL, (k_accel<T><<<GRID>>>(L.boxes, L.work, kset, pk)));
+}
+template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yp0, int yn0, int eprev, int enew,
+                                       int last, int) {
+  FE_LAUNCH(L, KID_DUST, (k_dust<T><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
+}
+template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
+  FE_LAUNCH(L, KID_DERIVE, (k_derive<T><<<GRID>>>(L.boxes, L.work, s, box)));
+}
+
+#define INST(T)                                                                              \
+  template void launch_dt<T>(const Launch&, int, int);                                       \
+  template void launch_div<T>(const Launch&, int);                                           \
+  template void launch_pred<T>(const Launch&, int, int);                                     \
+  template void launch_fluxn<T>(const Launch&, int);                                         \
+  template void launch_asm<T>(const Launch&, int, int, int, int);                            \
+  template void launch_rhs<T>(const Launch&, int, int, int);                                 \
+  template void launch_corr<T>(const Launch&, int, int, int, int, int, int);                 \
+  template void launch_accel<T>(const Launch&, int, int);                                    \
+  template void launch_dust<T>(const Launch&, int, int, int, int, int, int, int, int, int);  \
+  template void launch_derive_box<T>(const Launch&, int, int);
+INST(double)
+INST(float)
+
+}  // namespace fe
