@@ -48,6 +48,7 @@ extern "C" {
 #define FE_ERR_NONFINITE      -4
 #define FE_ERR_OOM            -5
 #define FE_ERR_UNSUPPORTED    -6
+#define FE_ERR_TOO_LARGE      -7   /* grid larger than a fixed static buffer */
 
 /* precision */
 #define FE_FP64        0
@@ -222,6 +223,29 @@ int fe_profile_start(fe_ctx* ctx, int kernel_id);
 int fe_profile_stop(fe_ctx* ctx, fe_profile_info* out);
 int fe_kernel_count(void);
 const char* fe_kernel_name(int kernel_id);
+
+/* Allocation-free pressure solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (for example
+ * code running while another framework owns the device allocator, or
+ * real-time loops that must not allocate).  It solves, for one box of N^3
+ * cells (8 <= N <= FE_NOALLOC_MAX_N), the same equation and with the same
+ * Jacobi-PCG as fe_solve_pressure, in FP64:
+ *     psi x / dt - dt/2 D(G2 x) = b,   x starts at 0,
+ * stopping at ||r|| <= tol ||b|| or maxit.  psi, b, x: device arrays of N^3
+ * doubles owned by the caller (flat index i + N*(j + N*k)); stream: a
+ * cudaStream_t or NULL.  No context is needed and nothing is allocated: the
+ * Krylov vectors and reduction scratch live in one static device array of
+ * about 6.3 MB per device (sized for N = 64), held from library load until
+ * process exit.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) and caches it, so make that first call
+ * before capturing a stream.  All calls on a device share the array and it
+ * keeps the previous call's contents (each call clears its counters and
+ * flags); calls that overlap on the GPU race with each other.  Returns
+ * FE_ERR_TOO_LARGE for N > FE_NOALLOC_MAX_N, FE_ERR_NOT_CONVERGED if maxit
+ * was reached, FE_ERR_INVALID_ARG for other bad arguments. */
+#define FE_NOALLOC_MAX_N 64
+int fe_solve_pressure_noalloc(int N, const double* psi, const double* b, double* x, double dt, double tol,
+                              int maxit, void* stream, fe_solve_info* info);
 
 void fe_destroy(fe_ctx* ctx);
 const char* fe_strerror(int code);

@@ -279,6 +279,7 @@ extern "C" const char* fe_strerror(int code) {
     case FE_ERR_NONFINITE: return "non-finite value in the new state";
     case FE_ERR_OOM: return "out of device memory";
     case FE_ERR_UNSUPPORTED: return "unsupported configuration";
+    case FE_ERR_TOO_LARGE: return "grid larger than the fixed static buffer of the allocation-free entry point";
     default: return "unknown error";
   }
 }

@@ -22,6 +22,8 @@ FE_ERR_NOT_CONVERGED = -3
 FE_ERR_NONFINITE = -4
 FE_ERR_OOM = -5
 FE_ERR_UNSUPPORTED = -6
+FE_ERR_TOO_LARGE = -7
+FE_NOALLOC_MAX_N = 64
 
 FE_FP64 = 0
 FE_FP32_MIXED = 1
@@ -67,7 +69,7 @@ class fe_profile_info(ctypes.Structure):
 
 EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_clock", "fe_step",
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
-           "fe_kernel_count", "fe_kernel_name", "fe_destroy", "fe_strerror"]
+           "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -89,6 +91,8 @@ def load_library(path=LIB_PATH):
     lib.fe_kernel_count.argtypes = []
     lib.fe_kernel_name.argtypes = [c_int]
     lib.fe_kernel_name.restype = ctypes.c_char_p
+    lib.fe_solve_pressure_noalloc.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
+                                              c_void_p, POINTER(fe_solve_info)]
     lib.fe_destroy.argtypes = [c_void_p]
     lib.fe_destroy.restype = None
     lib.fe_strerror.argtypes = [c_int]
@@ -194,6 +198,16 @@ def kernel_id(name):
         if fe_kernel_name(k) == name:
             return k
     raise KeyError(name)
+
+
+def fe_solve_pressure_noalloc(N, psi_ptr, b_ptr, x_ptr, dt, tol, maxit, stream=None):
+    """Allocation-free FP64 pressure solve (for callers that cannot allocate device memory)."""
+    info = fe_solve_info()
+    code = lib().fe_solve_pressure_noalloc(N, c_void_p(psi_ptr), c_void_p(b_ptr), c_void_p(x_ptr), dt, tol, maxit,
+                                           c_void_p(stream or 0), byref(info))
+    if code not in (FE_OK, FE_ERR_NOT_CONVERGED):
+        raise FeError(code, "fe_solve_pressure_noalloc")
+    return code, info
 
 
 def fe_destroy(ctx):
