@@ -39,6 +39,8 @@ def alg_words(kernel, nd):
         "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4, "corr": 21, "accel": 9,
         "dust": 8 + 4 * nd + 2,  # last corrector adds u reads and p write; averaged over 2 correctors
         "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
+        # refinement (field word = 4 bytes; x64 counts as two words)
+        "mix_residual": 6, "mix_accum": 5, "mix_finish": 3, "commit": 0,
     }
     return table[kernel]
 
@@ -145,6 +147,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default=None, help="kernel timed live for the roofline (default: largest share)")
+    ap.add_argument("--no-breakdown", action="store_true", help="skip the untimed per-kernel pass")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile depth")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -184,19 +188,20 @@ def main():
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
                   p_maxit=1000, stream=stream.cuda_stream)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
+    tz = s.autotune(2) if not args.no_tune else 0
     code, _ = s.step(args.warmup)
     assert code == fe.FE_OK, fe.fe_strerror(code)
 
     # untimed pass: per-kernel device time over one step, one kernel id at a time
     names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir", "corr",
-             "accel", "dust"]
+             "accel", "dust", "mix_residual", "mix_accum", "mix_finish", "commit"]
     share = {}
-    for k in names:
+    for k in ([] if args.no_breakdown else names):
         s.profile_start(k)
         s.step(1)
         p = s.profile_stop()
         share[k] = (p["target_ms"], p["target_launches"])
-    kernel = args.kernel or max(share, key=lambda k: share[k][0])
+    kernel = args.kernel or (max(share, key=lambda k: share[k][0]) if share else "cg_update")
 
     # timed region
     clocks = Clocks(local)
@@ -274,7 +279,7 @@ def main():
                 "config": {"workload": WORKLOAD, "N": N, "closure": "barotropic", "mach_rms": cfg["mach_rms"],
                            "k0": cfg["k0"], "nu": cfg["nu"], "tau_p": cfg["tau_p"], "Y0": cfg["Y0"],
                            "p_tol": cfg["p_tol"], "solver": "jacobi-pcg", "precision": args.precision,
-                           "n_corr": 2, "krylov_iters_last_step": iters,
+                           "n_corr": 2, "krylov_iters_last_step": iters, "tile": "32x8x%d" % tz if tz else "default",
                            "l2": "state of %.1f GB >> 126 MB L2, no flush needed" % (
                                (40 + 4 * nd) * cells * w / 1e9),
                            "parallelism": "replicas" if world > 1 else "single box"},

@@ -205,6 +205,15 @@ int fe_diagnostics(fe_ctx* ctx, int box, fe_diag* out, double* spectrum, int nbi
  * Q iso-surfaces). */
 int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
 
+/* Tile depth of the stencil kernels: every kernel launch covers all boxes
+ * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz
+ * (0 = built-in default: 8 for N >= 128, else 4).  fe_autotune times `trials`
+ * trial steps (computed from the current state and discarded: the state and
+ * clock are unchanged) for tz in {1, 2, 4, 8, 16}, keeps the fastest and
+ * returns it in *best_tz.  Not part of the method. */
+int fe_set_tiling(fe_ctx* ctx, int tz);
+int fe_autotune(fe_ctx* ctx, int trials, int* best_tz);
+
 /* Instrumentation (not part of the method).  fe_profile_start resets the
  * counters of the context and, when kernel_id >= 0, brackets every later
  * launch of that kernel with CUDA events on the context's stream;

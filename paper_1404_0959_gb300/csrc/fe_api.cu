@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -56,7 +57,8 @@ void prof_end(Prof* p, int kid, cudaStream_t st) {
 static const char* kKernelNames[KID_COUNT] = {
     "dt",      "div",       "pred",      "fluxn",  "asm",      "rhs",       "corr",    "accel",
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
-    "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "other"};
+    "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
+    "mix_residual", "mix_accum", "mix_finish", "other"};
 
 struct fe_ctx {
   fe_params prm;
@@ -71,16 +73,23 @@ struct fe_ctx {
   BoxDev* dbox = nullptr;
   int2* dwork = nullptr;
   int nblocks = 0;
+  int2* dework = nullptr;
+  int neblocks = 0;
+  int tz_override = 0;     // 0: default tile depth per N
+  int nsm = 152;           // multiprocessors of the device
   double* dpart = nullptr;
   double* dsc = nullptr;
   int* dcnt = nullptr;
   int* dactive = nullptr;
+  int* douter = nullptr;   // boxes whose refinement loop is running
   int* hactive = nullptr;  // pinned
   double* hsc = nullptr;   // pinned copy of all box scalars
   int cur = 0;             // state set holding the current state
-  int poll = 1;            // Krylov iterations between convergence polls
+  int hint[16] = {};       // iterations of the previous Krylov solve, per solve key
   Prof prof;
-  Launch L() { return Launch{dbox, dwork, nblocks, dpart, dactive, st, &prof}; }
+  Launch L() {
+    return Launch{dbox, dwork, nblocks, dework, neblocks, dpart, dactive, st, &prof, prm.closure == FE_FOURIER};
+  }
 };
 
 #define CK(x)                                     \
@@ -104,7 +113,7 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
     if (fourier) plan.push_back({S(set, F_T), e});
     for (int j = 0; j < nd; ++j) plan.push_back({S(set, F_Y0 + j), e});
   }
-  int w[] = {W_DIV, W_DIVPHI, W_RN0, W_RN1, W_RN2, W_AN0, W_AN1, W_AN2, W_PSI, W_HB0, W_HB1, W_HB2,
+  int w[] = {W_DIV, W_DIVPHI, W_RN0, W_RN1, W_RN2, W_AN0, W_AN1, W_AN2, W_PSI, W_DINV, W_HB0, W_HB1, W_HB2,
              W_PS0, W_PS1, W_PS2, W_PW0, W_PW1, K_B, K_X, K_R, K_PD, K_Q, K_AUX};
   for (int s : w) plan.push_back({s, e});
   if (fourier)
@@ -116,10 +125,7 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   }
   if (c->prm.solver == FE_BICGSTAB_JACOBI)
     for (int s : {K_RHAT, K_V, K_S, K_T}) plan.push_back({s, e});
-  if (!c->fp64) {
-    plan.push_back({K_X64, 8});
-    plan.push_back({K_B64, 8});
-  }
+  if (!c->fp64) plan.push_back({K_X64, 8});
 }
 
 static int validate(const fe_params* p) {
@@ -142,6 +148,56 @@ static int validate(const fe_params* p) {
 
 static int tz_for(int N) { return N >= 128 ? 8 : 4; }
 
+// (Re)build both work lists for tile depth tz (0: default per N) and upload the
+// descriptors.  Grows the partial-sum buffer when needed.
+static int set_tiling(fe_ctx* c, int tz) {
+  std::vector<int2> work, ework;
+  // element-wise chunk: about two waves of 8 blocks per SM over all boxes, so
+  // the per-block reduction tail (fence + counter) is paid rarely
+  long total = 0;
+  for (int b = 0; b < c->nb; ++b) total += (long)c->hbox[b].N * c->hbox[b].N * c->hbox[b].N;
+  const long quantum = 4L * NTHR;
+  long chunk = (total + 2L * 8 * c->nsm - 1) / (2L * 8 * c->nsm);
+  chunk = std::max(quantum, (chunk + quantum - 1) / quantum * quantum);
+  for (int b = 0; b < c->nb; ++b) {
+    BoxDev& B = c->hbox[b];
+    const int N = B.N;
+    B.tz = tz > 0 ? (tz < N ? tz : N) : tz_for(N);
+    B.tnx = (N + TX - 1) / TX;
+    B.tny = (N + TY - 1) / TY;
+    B.tnz = (N + B.tz - 1) / B.tz;
+    B.ntiles = B.tnx * B.tny * B.tnz;
+    B.tile0 = (int)work.size();
+    for (int q = 0; q < B.ntiles; ++q) work.push_back(make_int2(b, q));
+    const long n = (long)N * N * N;
+    B.echunk = (int)chunk;
+    B.entiles = (int)((n + chunk - 1) / chunk);
+    B.etile0 = (int)ework.size();
+    for (int q = 0; q < B.entiles; ++q) ework.push_back(make_int2(b, q));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  const int need = (int)std::max(work.size(), ework.size());
+  if ((int)work.size() != c->nblocks || (int)ework.size() != c->neblocks || !c->dpart) {
+    cudaFree(c->dwork);
+    cudaFree(c->dework);
+    cudaFree(c->dpart);
+    c->dwork = c->dework = nullptr;
+    c->dpart = nullptr;
+    if (cudaMalloc(&c->dwork, work.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&c->dework, ework.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&c->dpart, (size_t)need * MAXP * sizeof(double)) != cudaSuccess)
+      return FE_ERR_OOM;
+  }
+  c->nblocks = (int)work.size();
+  c->neblocks = (int)ework.size();
+  c->tz_override = tz;
+  CK(cudaMemcpyAsync(c->dwork, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dework, ework.data(), ework.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dbox, c->hbox.data(), c->nb * sizeof(BoxDev), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
 extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
   if (!out) return FE_ERR_INVALID_ARG;
   *out = nullptr;
@@ -153,6 +209,12 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
   c->nb = prm->n_boxes;
   c->fp64 = prm->precision == FE_FP64;
   c->st = (cudaStream_t)stream;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      c->nsm = nsm;
+  }
   const int nb = c->nb, nd = prm->n_dust;
   c->N.assign(prm->N, prm->N + nb);
   c->nu.assign(prm->nu, prm->nu + nb);
@@ -171,8 +233,7 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
   c->prm.tau_p = nd ? c->tau_p.data() : nullptr;
   c->prm.Y0 = nd ? c->Y0.data() : nullptr;
 
-  // work list and descriptors
-  std::vector<int2> work;
+  // descriptors (work lists are built by set_tiling)
   c->hbox.resize(nb);
   std::vector<std::pair<int, size_t>> plan;
   slot_plan(c, plan);
@@ -185,13 +246,6 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
     B.nd = nd;
     B.closure = prm->closure;
     B.transonic = prm->transonic;
-    B.tz = tz_for(N);
-    B.tnx = (N + TX - 1) / TX;
-    B.tny = (N + TY - 1) / TY;
-    B.tnz = (N + B.tz - 1) / B.tz;
-    B.ntiles = B.tnx * B.tny * B.tnz;
-    B.tile0 = (int)work.size();
-    for (int q = 0; q < B.ntiles; ++q) work.push_back(make_int2(b, q));
     B.h = 2.0 * M_PI / N;
     B.ih = 1.0 / B.h;
     B.mu = c->nu[b];
@@ -219,12 +273,10 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
     }
   }
   if (rc == FE_OK) {
-    c->nblocks = (int)work.size();
     if (cudaMalloc(&c->dbox, nb * sizeof(BoxDev)) != cudaSuccess ||
-        cudaMalloc(&c->dwork, work.size() * sizeof(int2)) != cudaSuccess ||
-        cudaMalloc(&c->dpart, (size_t)c->nblocks * MAXP * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->dsc, (size_t)nb * NSC * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->dcnt, nb * sizeof(int)) != cudaSuccess || cudaMalloc(&c->dactive, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->douter, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->hactive, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->hsc, (size_t)nb * NSC * sizeof(double)) != cudaSuccess)
       rc = FE_ERR_OOM;
@@ -236,15 +288,15 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
       c->hbox[b].cnt = c->dcnt + b;
       double* s = c->hsc + (size_t)b * NSC;
       s[SC_TOL] = prm->p_tol;
+      s[SC_OTOL] = prm->p_tol;
       s[SC_MAXIT] = prm->p_maxit;
       s[SC_DONE] = 1.0;
     }
-    cudaMemcpyAsync(c->dbox, c->hbox.data(), nb * sizeof(BoxDev), cudaMemcpyHostToDevice, c->st);
-    cudaMemcpyAsync(c->dwork, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->dsc, c->hsc, (size_t)nb * NSC * sizeof(double), cudaMemcpyHostToDevice, c->st);
     cudaMemsetAsync(c->dcnt, 0, nb * sizeof(int), c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = FE_ERR_CUDA;
   }
+  if (rc == FE_OK) rc = set_tiling(c, 0);
   if (rc != FE_OK) {
     fe_destroy(c);
     return rc;
@@ -261,10 +313,12 @@ extern "C" void fe_destroy(fe_ctx* c) {
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   cudaFree(c->dbox);
   cudaFree(c->dwork);
+  cudaFree(c->dework);
   cudaFree(c->dpart);
   cudaFree(c->dsc);
   cudaFree(c->dcnt);
   cudaFree(c->dactive);
+  cudaFree(c->douter);
   if (c->hactive) cudaFreeHost(c->hactive);
   if (c->hsc) cudaFreeHost(c->hsc);
   delete c;
@@ -309,19 +363,27 @@ static int push_scalar(fe_ctx* c, int box, int idx, double v) {
 }
 
 // Krylov driver for all boxes: operator/psi/dt already in place, rhs in K_B.
+// The host reads the number of running solves only after `batch` iterations
+// have been queued: the first batch is one less than the iteration count of
+// the previous solve with the same key (boxes that finish early skip the
+// surplus launches on the device), later batches are single iterations.
 template <typename T>
-static int krylov(fe_ctx* c, int maxit) {
+static int krylov(fe_ctx* c, int maxit, int key) {
   Launch L = c->L();
   CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
   const bool bicg = c->prm.solver == FE_BICGSTAB_JACOBI;
   if (bicg) launch_bicg_init<T>(L);
   else launch_cg_init<T>(L, 0.0);
   int it = 0;
+  int batch = c->hint[key] > 1 ? c->hint[key] - 1 : 1;
   while (true) {
-    CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    if (*c->hactive == 0 || it >= maxit) break;
-    for (int q = 0; q < c->poll && it < maxit; ++q, ++it) {
+    if (it > 0 || batch == 1) {
+      CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (*c->hactive == 0 || it >= maxit) break;
+    }
+    const int n = it == 0 ? batch : 1;
+    for (int q = 0; q < n && it < maxit; ++q, ++it) {
       if (bicg) {
         launch_bicg_p<T>(L);
         launch_bicg_v<T>(L);
@@ -334,6 +396,31 @@ static int krylov(fe_ctx* c, int maxit) {
       }
     }
   }
+  c->hint[key] = it;
+  CK(cudaGetLastError());
+  return FE_OK;
+}
+
+// Pressure solve of every box with the right-hand side in K_B: one Krylov
+// solve in FP64 mode; in mixed mode FP64 iterative refinement (residual
+// b - M x64 in FP64, inner solves in FP32, x64 += x) until the FP64 residual
+// meets the tolerance, then x = (float) x64.
+template <typename T>
+static int pressure_solve(fe_ctx* c) {
+  if (c->fp64) return krylov<T>(c, c->prm.p_maxit, 0);
+  Launch L = c->L();
+  CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
+  launch_mix_residual<T>(L, 1, c->douter);
+  for (int outer = 0; outer < 8; ++outer) {
+    CK(cudaMemcpyAsync(c->hactive, c->douter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (*c->hactive == 0) break;
+    int rc = krylov<T>(c, c->prm.p_maxit, 1 + outer);
+    if (rc != FE_OK) return rc;
+    launch_mix_accum<T>(L);
+    launch_mix_residual<T>(L, 0, c->douter);
+  }
+  launch_mix_finish<T>(L);
   CK(cudaGetLastError());
   return FE_OK;
 }
@@ -346,8 +433,10 @@ __global__ void k_commit(double* sc, int nb) {
   s[SC_DTPREV] = s[SC_DT];
 }
 
+// One PISO step of every box.  commit = false runs a trial step (autotuning):
+// the new state is computed into the other state set but not adopted.
 template <typename T>
-static int step_once(fe_ctx* c) {
+static int step_once(fe_ctx* c, bool commit = true) {
   Launch L = c->L();
   const int s = c->cur, ks = 1 - s, nc = c->prm.n_corr;
   launch_dt<T>(L, s, 0);
@@ -363,9 +452,9 @@ static int step_once(fe_ctx* c) {
     if (kk == 0) launch_div<T>(L, up0);
     launch_asm<T>(L, s, up0, php0, rhop);
     launch_rhs<T>(L, s, rhop, pp);
-    int rc = krylov<T>(c, c->prm.p_maxit);
+    int rc = pressure_solve<T>(c);
     if (rc != FE_OK) return rc;
-    launch_corr<T>(L, s, rhop, pp, pn, ks, kk);
+    launch_corr<T>(L, s, rhop, pp, pn, ks, kk, c->fp64 ? 0 : 1);
     launch_div<T>(L, S(ks, F_U0));
     launch_accel<T>(L, ks, pn);
     const bool last = kk == nc - 1;
@@ -376,14 +465,14 @@ static int step_once(fe_ctx* c) {
     launch_dust<T>(L, s, ks, pn, yp0, yn0, ep, en, last ? 1 : 0, kk == 0 ? 1 : 0);
   }
   CK(cudaGetLastError());
+  if (!commit) return FE_OK;
   int rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   for (int b = 0; b < c->nb; ++b) {
     const double* sc = c->hsc + (size_t)b * NSC;
     if (sc[SC_BAD] > 0.0 || !std::isfinite(sc[SC_DT])) return FE_ERR_NONFINITE;
     for (int kk = 0; kk < nc; ++kk)
-      if (!(sc[SC_RES0 + kk] <= c->prm.p_tol * (1.0 + 1e-6)) && sc[SC_IT0 + kk] >= c->prm.p_maxit)
-        return FE_ERR_NOT_CONVERGED;
+      if (!(sc[SC_RES0 + kk] <= c->prm.p_tol * (1.0 + 1e-3))) return FE_ERR_NOT_CONVERGED;
   }
   {
     Launch L2 = c->L();
@@ -480,8 +569,10 @@ extern "C" int fe_init_state(fe_ctx* c, int box, int mode) {
 }
 
 template <typename T>
-__global__ void k_psi_box(const BoxDev* boxes, int box, int s) {
+__global__ void k_psi_box(const BoxDev* boxes, int box, int s, double dt) {
   const BoxDev& B = boxes[box];
+  T* dinv = (T*)B.f[W_DINV];
+  const T idt = (T)(1.0 / dt), c3 = (T)(3.0 * dt * B.ih * B.ih);
   const long n = (long)B.N * B.N * B.N;
   const T* rho = (const T*)B.f[S(s, F_RHO)];
   const T* p = (const T*)B.f[S(s, F_P)];
@@ -489,7 +580,9 @@ __global__ void k_psi_box(const BoxDev* boxes, int box, int s) {
   T* hb[3] = {(T*)B.f[W_HB0], (T*)B.f[W_HB1], (T*)B.f[W_HB2]};
   const T* u[3] = {(const T*)B.f[S(s, F_U0)], (const T*)B.f[S(s, F_U1)], (const T*)B.f[S(s, F_U2)]};
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    psi[q] = rho[q] / ((T)B.gamma * p[q]);
+    T ps = rho[q] / ((T)B.gamma * p[q]);
+    psi[q] = ps;
+    dinv[q] = T(1) / (ps * idt + c3);
     for (int d = 0; d < 3; ++d) hb[d][q] = u[d][q];
   }
 }
@@ -504,28 +597,37 @@ static int solve_box(fe_ctx* c, int box, const void* b, void* x, double dt, doub
   if (rc != FE_OK) return rc;
   std::vector<double> saved((size_t)c->nb * NSC);
   memcpy(saved.data(), c->hsc, saved.size() * sizeof(double));
-  k_psi_box<T><<<1024, 256, 0, c->st>>>(c->dbox, box, c->cur);
+  k_psi_box<T><<<1024, 256, 0, c->st>>>(c->dbox, box, c->cur, dt);
   CK(cudaMemcpyAsync(B.f[K_B], b, bytes, cudaMemcpyDeviceToDevice, c->st));
   for (int q = 0; q < c->nb; ++q) {
     double* s = c->hsc + (size_t)q * NSC;
     s[SC_KDT] = dt;
     s[SC_TOL] = tol;
+    s[SC_OTOL] = tol;
     s[SC_MAXIT] = maxit;
   }
   CK(cudaMemcpyAsync(c->dsc, c->hsc, (size_t)c->nb * NSC * sizeof(double), cudaMemcpyHostToDevice, c->st));
   // zero rhs of the other boxes so their solves end at once
   for (int q = 0; q < c->nb; ++q)
     if (q != box) CK(cudaMemsetAsync(c->hbox[q].f[K_B], 0, (size_t)c->N[q] * c->N[q] * c->N[q] * sizeof(T), c->st));
-  rc = krylov<T>(c, maxit);
+  const int save_maxit = c->prm.p_maxit;
+  c->prm.p_maxit = maxit;
+  rc = pressure_solve<T>(c);
+  c->prm.p_maxit = save_maxit;
   if (rc != FE_OK) return rc;
-  launch_true_res<T>(c->L(), K_X);
+  if (c->fp64) launch_true_res<T>(c->L(), K_X);
   CK(cudaMemcpyAsync(x, B.f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
   rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   const double* s = c->hsc + (size_t)box * NSC;
   fe_solve_info inf;
-  inf.iters = (int)s[SC_ITERS];
-  inf.rel_res_true = s[SC_BB] > 0 ? sqrt(s[SC_TRUE_RR] / s[SC_BB]) : 0.0;
+  if (c->fp64) {
+    inf.iters = (int)s[SC_ITERS];
+    inf.rel_res_true = s[SC_BB] > 0 ? sqrt(s[SC_TRUE_RR] / s[SC_BB]) : 0.0;
+  } else {
+    inf.iters = (int)s[SC_ITSUM];
+    inf.rel_res_true = s[SC_ORES];
+  }
   bool conv = s[SC_CONV] != 0.0;
   if (info) *info = inf;
   // restore the step scalars (tolerance, cap, dt) of every box
@@ -626,4 +728,47 @@ extern "C" int fe_kernel_count(void) { return KID_COUNT; }
 extern "C" const char* fe_kernel_name(int id) {
   if (id < 0 || id >= KID_COUNT) return "";
   return kKernelNames[id];
+}
+
+extern "C" int fe_set_tiling(fe_ctx* c, int tz) {
+  if (!c || tz < 0 || tz > 512) return FE_ERR_INVALID_ARG;
+  return set_tiling(c, tz);
+}
+
+extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
+  if (!c || trials < 1) return FE_ERR_INVALID_ARG;
+  int rc = pull_scalars(c);
+  if (rc != FE_OK) return rc;
+  std::vector<double> saved(c->hsc, c->hsc + (size_t)c->nb * NSC);
+  const int cand[] = {1, 2, 4, 8, 16};
+  int best = 0;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int tz : cand) {
+    rc = set_tiling(c, tz);
+    if (rc != FE_OK) break;
+    rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
+    if (rc != FE_OK) break;
+    cudaEventRecord(e0, c->st);
+    for (int t = 0; t < trials && rc == FE_OK; ++t)
+      rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
+    cudaEventRecord(e1, c->st);
+    if (rc != FE_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tz;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc2 = set_tiling(c, best);
+  memcpy(c->hsc, saved.data(), saved.size() * sizeof(double));
+  CK(cudaMemcpyAsync(c->dsc, c->hsc, saved.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (best_tz) *best_tz = best;
+  return rc != FE_OK ? rc : rc2;
 }

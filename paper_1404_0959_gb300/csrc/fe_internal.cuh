@@ -37,6 +37,7 @@ enum WorkSlot {
   W_RN0, W_RN1, W_RN2,    // R^n
   W_AN0, W_AN1, W_AN2,    // Du/Dt (level n, then level k)
   W_PSI,                  // rho^n / (gamma p^n)
+  W_DINV,                 // 1 / Jacobi diagonal (psi/dt + 3 dt/h^2)
   W_HB0, W_HB1, W_HB2,    // HbyA
   W_PS0, W_PS1, W_PS2,    // phi*
   W_PW0, W_PW1,           // p^k ping-pong
@@ -63,6 +64,7 @@ enum Scalar {
   SC_ZQ, SC_PR,                                           // flexible CG
   SC_TOL, SC_MAXIT, SC_KDT,   // Krylov tolerance, cap and the dt of its operator
   SC_IT0, SC_IT1, SC_IT2, SC_IT3, SC_RES0, SC_RES1, SC_RES2, SC_RES3,
+  SC_ODONE, SC_OBB, SC_ORR, SC_ORES, SC_ITSUM, SC_OTOL, SC_OUTER,  // mixed-precision refinement
   SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
   NSC = SC_DUST0 + MAXD + 4
 };
@@ -70,7 +72,9 @@ enum Scalar {
 struct BoxDev {
   int N, nd, closure, transonic;
   int tnx, tny, tnz, tz;   // tile grid and planes per tile
-  int tile0, ntiles;       // this box's blocks in the work list
+  int tile0, ntiles;       // this box's blocks in the stencil work list
+  int etile0, entiles;     // this box's blocks in the element-wise work list
+  int echunk;              // cells per element-wise block (multiple of 4 * NTHR)
   double h, ih, mu, gamma, R, cv, kappa, cfl, growth, dtmax;
   double tau_p[MAXD];
   void* f[NSLOT];
@@ -134,6 +138,78 @@ __device__ __forceinline__ T DG4_h2(const A* f, const Nbr& n, int d, int ox, int
   return (T(28) * (m1 + p1) - T(54) * c0 - (m2 + p2)) * T(1.0 / 24.0);
 }
 
+// ---- inner-product accumulation ----------------------------------------------------
+// double vectors: FP64 fused multiply-add.  float vectors: the compensated
+// "Dot2" scheme of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): each product is split exactly into
+// rounded product + error with one FMA (TwoProduct) and added to a float
+// pair with Knuth's error-free TwoSum, so the pair carries about 48
+// significant bits -- FP64-class accuracy computed on the FP32 pipe, which on
+// this GPU is far wider than the FP64 pipe.  The pair is converted to double
+// once per thread before the block tree.  The _rn intrinsics keep the
+// compiler from contracting the error-free steps.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float z = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---- double-float arithmetic ---------------------------------------------------
+// An unevaluated pair hi + lo of floats (about 48 significant bits), with the
+// error-free TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and FMA-based TwoProduct, and
+// the pair addition and multiplication built on them (Dekker 1971).  Used for
+// the refinement residual b - M x of the mixed-precision pressure solve: on
+// this GPU the FP32 pipe is far wider than the FP64 pipe.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  DF t = df_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_from_double(double d) {
+  const float hi = (float)d;
+  return DF{hi, (float)(d - (double)hi)};
+}
+
 // ---- block prologue -----------------------------------------------------------
 struct Tile {
   int box, i, j, k0, kend;
@@ -156,12 +232,52 @@ __device__ __forceinline__ Tile tile_of(const BoxDev* boxes, const int2* work) {
   return t;
 }
 
+// Element-wise kernels ignore the tile geometry: block w.y of a box takes the
+// w.y-th of ntiles equal chunks of its N^3 cells (chunk length a multiple of
+// 4 so that 16-byte vector accesses stay aligned).
+struct Chunk {
+  int box;
+  int begin, end;
+};
+__device__ __forceinline__ Chunk chunk_of(const BoxDev* boxes, const int2* ework) {
+  int2 w = ework[blockIdx.x];
+  const BoxDev& B = boxes[w.x];
+  const int n = B.N * B.N * B.N;
+  Chunk c;
+  c.box = w.x;
+  c.begin = min(w.y * B.echunk, n);
+  c.end = min(c.begin + B.echunk, n);
+  return c;
+}
+
+// four consecutive elements as one (float4) or two (double2) 16-byte accesses
+template <typename T>
+struct V4 {
+  T v[4];
+};
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  float4 a = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& a) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
+
 // ---- deterministic reductions ----------------------------------------------------
 // Block-sum K doubles (fixed tree), write this block's partials, and report
 // whether this is the box's last block; if so `res` (shared) holds the box
 // totals (partials added in block order).  Must be called by all threads.
+// tile0/ntiles: the box's block range in the work list of this launch.
 template <int K>
-__device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res) {
+__device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
   __shared__ double red[K][NTHR / 32];
   __shared__ int last;
   const int tid = threadIdx.x + TX * threadIdx.y;
@@ -183,7 +299,7 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
     }
     __threadfence();
     int prev = atomicAdd(B.cnt, 1);
-    last = (prev == B.ntiles - 1);
+    last = (prev == ntiles - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -191,7 +307,7 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     double s = 0.0;
-    for (int b = tid; b < B.ntiles; b += NTHR) s += __ldcg(&part[(size_t)(B.tile0 + b) * MAXP + q]);
+    for (int b = tid; b < ntiles; b += NTHR) s += __ldcg(&part[(size_t)(tile0 + b) * MAXP + q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) red[q][warp] = s;
@@ -211,7 +327,8 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
 }
 
 // Same for a maximum of one value.
-__device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double* part, double* res) {
+__device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double* part, double* res, int tile0,
+                                               int ntiles) {
   __shared__ double red[NTHR / 32];
   __shared__ int last;
   const int tid = threadIdx.x + TX * threadIdx.y;
@@ -227,13 +344,13 @@ __device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double
     part[(size_t)blockIdx.x * MAXP] = m;
     __threadfence();
     int prev = atomicAdd(B.cnt, 1);
-    last = (prev == B.ntiles - 1);
+    last = (prev == ntiles - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
   s = 0.0;
-  for (int b = tid; b < B.ntiles; b += NTHR) s = fmax(s, __ldcg(&part[(size_t)(B.tile0 + b) * MAXP]));
+  for (int b = tid; b < ntiles; b += NTHR) s = fmax(s, __ldcg(&part[(size_t)(tile0 + b) * MAXP]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
   if (lane == 0) red[warp] = s;
@@ -254,7 +371,7 @@ enum KernelId {
   KID_DT = 0, KID_DIV, KID_PRED, KID_FLUXN, KID_ASM, KID_RHS, KID_CORR, KID_ACCEL, KID_DUST, KID_DERIVE,
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
-  KID_COMMIT, KID_OTHER, KID_COUNT
+  KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_OTHER, KID_COUNT
 };
 
 struct Prof;  // defined in fe_api.cu
@@ -263,12 +380,15 @@ void prof_end(Prof* p, int kid, cudaStream_t st);
 
 struct Launch {
   const BoxDev* boxes;
-  const int2* work;
+  const int2* work;   // stencil tiles (box, tile)
   int nblocks;
+  const int2* ework;  // element-wise chunks (box, chunk)
+  int neblocks;
   double* part;
   int* active;  // number of boxes whose Krylov solve is running
   cudaStream_t st;
   Prof* prof;
+  int fourier;  // closure of the context (selects kernel variants)
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -286,7 +406,8 @@ template <typename T> void launch_pred(const Launch& L, int s, int k);
 template <typename T> void launch_fluxn(const Launch& L, int s);
 template <typename T> void launch_asm(const Launch& L, int s, int uprev0, int phiprev0, int rhoprev);
 template <typename T> void launch_rhs(const Launch& L, int s, int rhoprev, int pprev);
-template <typename T> void launch_corr(const Launch& L, int s, int rhoprev, int pprev, int pnew, int kset, int kidx);
+template <typename T> void launch_corr(const Launch& L, int s, int rhoprev, int pprev, int pnew, int kset, int kidx,
+                                      int mixed);
 template <typename T> void launch_accel(const Launch& L, int kset, int pk);
 template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yprev0, int ynew0, int eprev,
                                       int enew, int last, int first);
@@ -302,5 +423,8 @@ template <typename V> void launch_bicg_p(const Launch& L);
 template <typename V> void launch_bicg_v(const Launch& L);
 template <typename V> void launch_bicg_s(const Launch& L);
 template <typename V> void launch_bicg_x(const Launch& L);
+template <typename V> void launch_mix_residual(const Launch& L, int first, int* outer_active);
+template <typename V> void launch_mix_accum(const Launch& L);
+template <typename V> void launch_mix_finish(const Launch& L);
 
 }  // namespace fe

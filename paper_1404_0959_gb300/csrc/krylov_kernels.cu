@@ -21,23 +21,24 @@ __device__ __forceinline__ T* F(const BoxDev& B, int slot) {
 
 __device__ __forceinline__ bool box_done(const BoxDev& B) { return B.sc[SC_DONE] != 0.0; }
 
-// (M v)_c.  `scale` multiplies v element-wise first (the Jacobi
-// preconditioner applied on the fly: pass inverse-diagonal mode).
+// (M v)_c with v read through `val` (PRE: v scaled by the inverse Jacobi
+// diagonal first, i.e. M D^{-1} v for right preconditioning).
 template <typename T, bool PRE>
 __device__ __forceinline__ T applyM(const BoxDev& B, const T* v, const Nbr& n, T dt, T ih) {
   const T* psi = F<T>(B, W_PSI);
-  const T c3 = T(3) * dt * ih * ih;
+  const T* dinv = F<T>(B, W_DINV);
   auto val = [&](int q) {
     T x = __ldg(&v[q]);
-    if (PRE) x /= __ldg(&psi[q]) / dt + c3;
+    if (PRE) x *= __ldg(&dinv[q]);
     return x;
   };
+  const T idt = T(1) / dt;
   const int c = n(0, 0, 0);
   const T vc = val(c);
   T lap = T(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) lap += (val(n.at(d, 0, 0, 0, 1)) - vc) - (vc - val(n.at(d, 0, 0, 0, -1)));
-  T y = __ldg(&psi[c]) * vc / dt - T(0.5) * dt * lap * ih * ih;
+  T y = __ldg(&psi[c]) * vc * idt - T(0.5) * dt * lap * ih * ih;
   if (B.transonic) {
     T trd = T(0);
 #pragma unroll
@@ -62,38 +63,99 @@ __device__ __forceinline__ T applyM(const BoxDev& B, const T* v, const Nbr& n, T
   return y;
 }
 
+// The operator in FP64 on the double-float correction (transonic refinement residuals).
 template <typename T>
-__device__ __forceinline__ T jacobi_diag(const BoxDev& B, T psic, T dt) {
-  return psic / dt + T(3) * dt * (T)B.ih * (T)B.ih;
+__device__ __forceinline__ double applyM64_pairs(const BoxDev& B, const float2* xs, const Nbr& n, double dt) {
+  const T* psi = F<T>(B, W_PSI);
+  const double ih = B.ih, idt = 1.0 / dt;
+  auto v = [&](int q) {
+    const float2 a = xs[q];
+    return (double)a.x + (double)a.y;
+  };
+  const int c = n(0, 0, 0);
+  const double vc = v(c);
+  double lap = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lap += (v(n.at(d, 0, 0, 0, 1)) - vc) - (vc - v(n.at(d, 0, 0, 0, -1)));
+  double y = (double)__ldg(&psi[c]) * vc * idt - 0.5 * dt * lap * ih * ih;
+  if (B.transonic) {
+    double trd = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* hb = F<T>(B, W_HB0 + d);
+      auto I4pv = [&](int ox, int oy, int oz) {
+        double w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int id = n.at(d, ox, oy, oz, q - 1);
+          w[q] = (double)__ldg(&psi[id]) * v(id);
+        }
+        return (9.0 * (w[1] + w[2]) - (w[0] + w[3])) * 0.0625;
+      };
+      double tp = I4pv(0, 0, 0) * I4f<double>(hb, n, d, 0, 0, 0);
+      double tm = I4pv(d == 0 ? -1 : 0, d == 1 ? -1 : 0, d == 2 ? -1 : 0) *
+                  I4f<double>(hb, n, d, d == 0 ? -1 : 0, d == 1 ? -1 : 0, d == 2 ? -1 : 0);
+      trd += tp - tm;
+    }
+    y += 0.5 * trd * ih;
+  }
+  return y;
 }
 
 // ---- CG ------------------------------------------------------------------------------
+// Element-wise CG kernels walk a flat chunk of the box with 16-byte accesses;
+// each thread keeps two vectors of four cells in flight.
+template <typename F4, typename F1>
+__device__ __forceinline__ void chunk_loop(const Chunk& ch, int tid, F4 f4, F1 f1) {
+  for (int q0 = ch.begin + 4 * tid; q0 < ch.end; q0 += 4 * NTHR) {
+    if (q0 + 4 <= ch.end) {
+      f4(q0);
+    } else {
+      for (int c = q0; c < ch.end; ++c) f1(c);
+    }
+  }
+}
+
 // r = b, x = 0, pd = z = b / diag; rz = <r, z>, bb = <b, b>.
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int2* work, double* part, int* active) {
-  Tile t = tile_of(boxes, work);
-  const BoxDev& B = boxes[t.box];
-  const T* b = F<T>(B, K_B);
-  const T* psi = F<T>(B, W_PSI);
-  T* r = F<T>(B, K_R);
-  T* x = F<T>(B, K_X);
-  T* pd = F<T>(B, K_PD);
-  const T dt = (T)B.sc[SC_KDT];
-  double v[2] = {0.0, 0.0};
-  if (t.active) {
-    for (int k = t.k0; k < t.kend; ++k) {
-      int c = t.i + B.N * (t.j + B.N * k);
-      T bc = b[c];
-      T z = bc / jacobi_diag<T>(B, psi[c], dt);
-      r[c] = bc;
-      x[c] = T(0);
-      pd[c] = z;
-      v[0] += (double)bc * (double)z;
-      v[1] += (double)bc * (double)bc;
-    }
-  }
+  const Chunk ch = chunk_of(boxes, work);
+  const BoxDev& B = boxes[ch.box];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ b = F<T>(B, K_B);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ r = F<T>(B, K_R);
+  T* __restrict__ x = F<T>(B, K_X);
+  T* __restrict__ pd = F<T>(B, K_PD);
+  const T keep = B.sc[SC_ODONE] != 0.0 ? T(0) : T(1);  // refinement already converged for this box
+  DotAcc<T> a0, a1;
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        V4<T> bv = ld4(b + q0), dv = ld4(dinv + q0), zv, zero{{T(0), T(0), T(0), T(0)}};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          bv.v[e] *= keep;
+          zv.v[e] = bv.v[e] * dv.v[e];
+          a0.add(bv.v[e], zv.v[e]);
+          a1.add(bv.v[e], bv.v[e]);
+        }
+        st4(r + q0, bv);
+        st4(x + q0, zero);
+        st4(pd + q0, zv);
+      },
+      [&](int c) {
+        T bc = b[c] * keep;
+        T z = bc * dinv[c];
+        r[c] = bc;
+        x[c] = T(0);
+        pd[c] = z;
+        a0.add(bc, z);
+        a1.add(bc, bc);
+      });
+  double v[2] = {a0.value(), a1.value()};
   __shared__ double res[2];
-  if (block_sum_last<2>(v, B, part, res)) {
+  if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_RZ] = res[0];
       B.sc[SC_BB] = res[1];
@@ -106,27 +168,56 @@ __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int
   }
 }
 
-// q = M pd; alpha = rz / <pd, q>
+// q = M pd; alpha = rz / <pd, q>.  Symmetric operator: each thread walks its
+// (i, j) column through the tile's z-planes keeping pd at k-1, k, k+1 in
+// registers; x and y neighbours come through the read-only cache.
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const int2* work, double* part) {
   Tile t = tile_of(boxes, work);
   const BoxDev& B = boxes[t.box];
   if (box_done(B)) return;
-  const T* pd = F<T>(B, K_PD);
-  T* q = F<T>(B, K_Q);
-  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
-  double v[1] = {0.0};
+  const T* __restrict__ pd = F<T>(B, K_PD);
+  const T* __restrict__ psi = F<T>(B, W_PSI);
+  T* __restrict__ q = F<T>(B, K_Q);
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  DotAcc<T> a0;
   if (t.active) {
-    for (int k = t.k0; k < t.kend; ++k) {
-      Nbr n(t.i, t.j, k, B.N);
-      int c = n(0, 0, 0);
-      T y = applyM<T, false>(B, pd, n, dt, ih);
-      q[c] = y;
-      v[0] += (double)__ldg(&pd[c]) * (double)y;
+    const int N = B.N, NN = N * N;
+    if (!B.transonic) {
+      const int col = t.i + N * t.j;
+      const int xm = (t.i == 0 ? N - 1 : t.i - 1) + N * t.j - col;
+      const int xp = (t.i == N - 1 ? 0 : t.i + 1) + N * t.j - col;
+      const int ym = t.i + N * (t.j == 0 ? N - 1 : t.j - 1) - col;
+      const int yp = t.i + N * (t.j == N - 1 ? 0 : t.j + 1) - col;
+      int km = t.k0 == 0 ? N - 1 : t.k0 - 1;
+      T vm = __ldg(&pd[col + NN * km]);
+      T vc = __ldg(&pd[col + NN * t.k0]);
+#pragma unroll 2
+      for (int k = t.k0; k < t.kend; ++k) {
+        const int kp = k == N - 1 ? 0 : k + 1;
+        const int c = col + NN * k;
+        const T vp = __ldg(&pd[col + NN * kp]);
+        const T nb = (__ldg(&pd[c + xm]) + __ldg(&pd[c + xp])) + (__ldg(&pd[c + ym]) + __ldg(&pd[c + yp])) + (vm + vp);
+        const T y = __ldg(&psi[c]) * vc * idt - lapc * (nb - T(6) * vc);
+        q[c] = y;
+        a0.add(vc, y);
+        vm = vc;
+        vc = vp;
+      }
+    } else {
+      for (int k = t.k0; k < t.kend; ++k) {
+        Nbr n(t.i, t.j, k, N);
+        int c = n(0, 0, 0);
+        T y = applyM<T, false>(B, pd, n, dt, ih);
+        q[c] = y;
+        a0.add(__ldg(&pd[c]), y);
+      }
     }
   }
+  double v[1] = {a0.value()};
   __shared__ double res[1];
-  if (block_sum_last<1>(v, B, part, res)) {
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_PQ] = res[0];
       B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
@@ -137,30 +228,41 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
 // x += alpha pd; r -= alpha q; z = r / diag; convergence test on ||r||.
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const int2* work, double* part, int* active) {
-  Tile t = tile_of(boxes, work);
-  const BoxDev& B = boxes[t.box];
+  const Chunk ch = chunk_of(boxes, work);
+  const BoxDev& B = boxes[ch.box];
   if (box_done(B)) return;
-  const T* pd = F<T>(B, K_PD);
-  const T* q = F<T>(B, K_Q);
-  const T* psi = F<T>(B, W_PSI);
-  T* x = F<T>(B, K_X);
-  T* r = F<T>(B, K_R);
-  const T dt = (T)B.sc[SC_KDT];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ pd = F<T>(B, K_PD);
+  const T* __restrict__ qv = F<T>(B, K_Q);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ x = F<T>(B, K_X);
+  T* __restrict__ r = F<T>(B, K_R);
   const T alpha = (T)B.sc[SC_ALPHA];
-  double v[2] = {0.0, 0.0};
-  if (t.active) {
-    for (int k = t.k0; k < t.kend; ++k) {
-      int c = t.i + B.N * (t.j + B.N * k);
-      x[c] = x[c] + alpha * pd[c];
-      T rc = r[c] - alpha * q[c];
-      r[c] = rc;
-      T z = rc / jacobi_diag<T>(B, psi[c], dt);
-      v[0] += (double)rc * (double)z;
-      v[1] += (double)rc * (double)rc;
-    }
-  }
+  DotAcc<T> a0, a1;
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        V4<T> xv = ld4(x + q0), pv = ld4(pd + q0), rv = ld4(r + q0), qq = ld4(qv + q0), dv = ld4(dinv + q0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xv.v[e] += alpha * pv.v[e];
+          rv.v[e] -= alpha * qq.v[e];
+          a0.add(rv.v[e], rv.v[e] * dv.v[e]);
+          a1.add(rv.v[e], rv.v[e]);
+        }
+        st4(x + q0, xv);
+        st4(r + q0, rv);
+      },
+      [&](int c) {
+        x[c] = x[c] + alpha * pd[c];
+        T rc = r[c] - alpha * qv[c];
+        r[c] = rc;
+        a0.add(rc, rc * dinv[c]);
+        a1.add(rc, rc);
+      });
+  double v[2] = {a0.value(), a1.value()};
   __shared__ double res[2];
-  if (block_sum_last<2>(v, B, part, res)) {
+  if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double it = B.sc[SC_ITERS] + 1.0;
       B.sc[SC_ITERS] = it;
@@ -184,18 +286,23 @@ __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const i
 // pd = r / diag + beta pd
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_cg_dir(const BoxDev* boxes, const int2* work) {
-  Tile t = tile_of(boxes, work);
-  const BoxDev& B = boxes[t.box];
-  if (box_done(B) || !t.active) return;
-  const T* r = F<T>(B, K_R);
-  const T* psi = F<T>(B, W_PSI);
-  T* pd = F<T>(B, K_PD);
-  const T dt = (T)B.sc[SC_KDT];
+  const Chunk ch = chunk_of(boxes, work);
+  const BoxDev& B = boxes[ch.box];
+  if (box_done(B)) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ pd = F<T>(B, K_PD);
   const T beta = (T)B.sc[SC_BETA];
-  for (int k = t.k0; k < t.kend; ++k) {
-    int c = t.i + B.N * (t.j + B.N * k);
-    pd[c] = r[c] / jacobi_diag<T>(B, psi[c], dt) + beta * pd[c];
-  }
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        V4<T> rv = ld4(r + q0), dv = ld4(dinv + q0), pv = ld4(pd + q0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pv.v[e] = rv.v[e] * dv.v[e] + beta * pv.v[e];
+        st4(pd + q0, pv);
+      },
+      [&](int c) { pd[c] = r[c] * dinv[c] + beta * pd[c]; });
 }
 
 // ||b - M x||^2 -> SC_TRUE_RR (x in slot xs)
@@ -216,7 +323,7 @@ __global__ void __launch_bounds__(NTHR) k_true_res(const BoxDev* boxes, const in
     }
   }
   __shared__ double res[1];
-  if (block_sum_last<1>(v, B, part, res)) {
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) B.sc[SC_TRUE_RR] = res[0];
   }
 }
@@ -234,6 +341,7 @@ __global__ void __launch_bounds__(NTHR) k_bicg_init(const BoxDev* boxes, const i
   T* p = F<T>(B, K_PD);
   T* v = F<T>(B, K_V);
   double a[1] = {0.0};
+  DotAcc<T> acc;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
       int c = t.i + B.N * (t.j + B.N * k);
@@ -243,11 +351,12 @@ __global__ void __launch_bounds__(NTHR) k_bicg_init(const BoxDev* boxes, const i
       x[c] = T(0);
       p[c] = T(0);
       v[c] = T(0);
-      a[0] += (double)bc * (double)bc;
+      acc.add(bc, bc);
     }
   }
+  a[0] = acc.value();
   __shared__ double res[1];
-  if (block_sum_last<1>(a, B, part, res)) {
+  if (block_sum_last<1>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_BB] = res[0];
       B.sc[SC_RZ] = res[0];  // rho_i
@@ -291,17 +400,19 @@ __global__ void __launch_bounds__(NTHR) k_bicg_v(const BoxDev* boxes, const int2
   T* v = F<T>(B, K_V);
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
   double a[1] = {0.0};
+  DotAcc<T> acc;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
       Nbr n(t.i, t.j, k, B.N);
       int c = n(0, 0, 0);
       T y = applyM<T, true>(B, p, n, dt, ih);
       v[c] = y;
-      a[0] += (double)rh[c] * (double)y;
+      acc.add(rh[c], y);
     }
   }
+  a[0] = acc.value();
   __shared__ double res[1];
-  if (block_sum_last<1>(a, B, part, res)) {
+  if (block_sum_last<1>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_RV] = res[0];
       B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
@@ -334,18 +445,21 @@ __global__ void __launch_bounds__(NTHR) k_bicg_t(const BoxDev* boxes, const int2
   T* tv = F<T>(B, K_T);
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
   double a[2] = {0.0, 0.0};
+  DotAcc<T> acc0, acc1;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
       Nbr n(t.i, t.j, k, B.N);
       int c = n(0, 0, 0);
       T y = applyM<T, true>(B, s, n, dt, ih);
       tv[c] = y;
-      a[0] += (double)y * (double)__ldg(&s[c]);
-      a[1] += (double)y * (double)y;
+      acc0.add(y, __ldg(&s[c]));
+      acc1.add(y, y);
     }
   }
+  a[0] = acc0.value();
+  a[1] = acc1.value();
   __shared__ double res[2];
-  if (block_sum_last<2>(a, B, part, res)) {
+  if (block_sum_last<2>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_TS] = res[0];
       B.sc[SC_TT] = res[1];
@@ -364,26 +478,28 @@ __global__ void __launch_bounds__(NTHR) k_bicg_x(const BoxDev* boxes, const int2
   const T* s = F<T>(B, K_S);
   const T* tv = F<T>(B, K_T);
   const T* rh = F<T>(B, K_RHAT);
-  const T* psi = F<T>(B, W_PSI);
+  const T* dinv = F<T>(B, W_DINV);
   T* x = F<T>(B, K_X);
   T* r = F<T>(B, K_R);
-  const T dt = (T)B.sc[SC_KDT];
   const T alpha = (T)B.sc[SC_ALPHA], om = (T)B.sc[SC_OMEGA];
   double a[2] = {0.0, 0.0};
+  DotAcc<T> acc0, acc1;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
       int c = t.i + B.N * (t.j + B.N * k);
-      T dg = jacobi_diag<T>(B, psi[c], dt);
+      T di = dinv[c];
       T sc = s[c];
-      x[c] = x[c] + alpha * (p[c] / dg) + om * (sc / dg);
+      x[c] = x[c] + alpha * (p[c] * di) + om * (sc * di);
       T rc = sc - om * tv[c];
       r[c] = rc;
-      a[0] += (double)rc * (double)rc;
-      a[1] += (double)rh[c] * (double)rc;
+      acc0.add(rc, rc);
+      acc1.add(rh[c], rc);
     }
   }
+  a[0] = acc0.value();
+  a[1] = acc1.value();
   __shared__ double res[2];
-  if (block_sum_last<2>(a, B, part, res)) {
+  if (block_sum_last<2>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double it = B.sc[SC_ITERS] + 1.0;
       B.sc[SC_ITERS] = it;
@@ -403,19 +519,144 @@ __global__ void __launch_bounds__(NTHR) k_bicg_x(const BoxDev* boxes, const int2
   }
 }
 
+// ---- mixed precision: iterative refinement around the field-precision solve -----------
+// The accumulated correction x is kept as a double-float pair per cell (slot
+// K_X64, 8 bytes).  first: keep b in K_AUX, x = 0, ||b||^2.  Otherwise the
+// residual r = b - M x in double-float arithmetic (FP64 for the transonic
+// operator), stored in K_B as the next inner right-hand side.  The last block
+// records the residual, the convergence of the box and the inner tolerance
+// that the next inner solve needs (just enough to reach the target).
+template <typename T>
+__device__ __forceinline__ DF residual_df(const BoxDev& B, const float2* __restrict__ xs, const T* __restrict__ psi,
+                                          T bc, const Nbr& n, DF idt, DF kl, DF k6) {
+  const int c = n(0, 0, 0);
+  auto X = [&](int q) {
+    const float2 v = xs[q];
+    return DF{v.x, v.y};
+  };
+  DF nb = df_add(X(n(1, 0, 0)), X(n(-1, 0, 0)));
+  nb = df_add(nb, df_add(X(n(0, 1, 0)), X(n(0, -1, 0))));
+  nb = df_add(nb, df_add(X(n(0, 0, 1)), X(n(0, 0, -1))));
+  // a_c = psi_c / dt + 6 k,  M x = a_c x_c - k sum_nb
+  const DF a = df_add(df_mul(idt, DF{(float)psi[c], 0.f}), k6);
+  const DF mx = df_add(df_mul(a, X(c)), df_neg(df_mul(kl, nb)));
+  return df_add(DF{(float)bc, 0.f}, df_neg(mx));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_mix_residual(const BoxDev* boxes, const int2* work, double* part, int first,
+                                                       int* outer_active) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  T* __restrict__ b = F<T>(B, K_B);
+  T* __restrict__ borig = F<T>(B, K_AUX);
+  float2* __restrict__ xs = F<float2>(B, K_X64);
+  const T* __restrict__ psi = F<T>(B, W_PSI);
+  const double dt = B.sc[SC_KDT];
+  const DF idt = df_from_double(1.0 / dt), kl = df_from_double(0.5 * dt * B.ih * B.ih),
+           k6 = df_from_double(3.0 * dt * B.ih * B.ih);
+  DotAcc<float> acc;
+  double acc64 = 0.0;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      Nbr n(t.i, t.j, k, B.N);
+      const int c = n(0, 0, 0);
+      if (first) {
+        T bc = b[c];
+        borig[c] = bc;
+        xs[c] = make_float2(0.f, 0.f);
+        acc.add((float)bc, (float)bc);
+      } else if (!B.transonic) {
+        DF r = residual_df<T>(B, xs, psi, borig[c], n, idt, kl, k6);
+        b[c] = (T)r.hi;
+        acc.add(r.hi, r.hi);
+      } else {
+        // transonic operator: FP64 on the pair values
+        double r = (double)borig[c] - applyM64_pairs<T>(B, xs, n, dt);
+        b[c] = (T)r;
+        acc64 += r * r;
+      }
+    }
+  }
+  double v[1] = {acc.value() + acc64};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double* sc = B.sc;
+      const double rr = res[0];
+      if (first) {
+        sc[SC_OBB] = rr;
+        sc[SC_ITSUM] = 0.0;
+        sc[SC_OUTER] = 0.0;
+        bool zero = !(rr > 0.0);
+        sc[SC_ODONE] = zero ? 1.0 : 0.0;
+        sc[SC_CONV] = zero ? 1.0 : 0.0;
+        if (!zero) atomicAdd(outer_active, 1);
+      } else if (sc[SC_ODONE] == 0.0) {
+        sc[SC_ITSUM] += sc[SC_ITERS];
+        sc[SC_OUTER] += 1.0;
+        if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
+          sc[SC_ODONE] = 1.0;
+          sc[SC_CONV] = 1.0;
+          atomicSub(outer_active, 1);
+        } else if (sc[SC_OUTER] >= 8.0) {
+          sc[SC_ODONE] = 1.0;
+          sc[SC_CONV] = 0.0;
+          atomicSub(outer_active, 1);
+        }
+      }
+      sc[SC_ORR] = rr;
+      sc[SC_ORES] = sc[SC_OBB] > 0.0 ? sqrt(rr / sc[SC_OBB]) : 0.0;
+      // inner tolerance: reach the outer target with a factor 2 margin, within FP32 reach
+      double need = rr > 0.0 ? 0.5 * sc[SC_OTOL] * sqrt(sc[SC_OBB] / rr) : 0.5;
+      sc[SC_TOL] = fmin(0.5, fmax(need, 1e-6));
+    }
+  }
+}
+
+// x (double-float pair) += inner correction
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_mix_accum(const BoxDev* boxes, const int2* ework) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ x = F<T>(B, K_X);
+  float2* __restrict__ xs = F<float2>(B, K_X64);
+  for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
+    const float2 a = xs[c];
+    const DF s = df_add(DF{a.x, a.y}, DF{(float)x[c], 0.f});
+    xs[c] = make_float2(s.hi, s.lo);
+  }
+}
+
+// x = the pair rounded to the field precision
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const int2* ework) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  T* __restrict__ x = F<T>(B, K_X);
+  const float2* __restrict__ xs = F<float2>(B, K_X64);
+  for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
+    const float2 a = xs[c];
+    x[c] = (T)__fadd_rn(a.x, a.y);
+  }
+}
+
 // ---- launchers ------------------------------------------------------------------------
 #define GRID L.nblocks, dim3(TX, TY), 0, L.st
+#define EGRID L.neblocks, dim3(TX, TY), 0, L.st
 template <typename T> void launch_cg_init(const Launch& L, double) {
-  FE_LAUNCH(L, KID_CG_INIT, (k_cg_init<T><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_INIT, (k_cg_init<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_matvec(const Launch& L) {
   FE_LAUNCH(L, KID_CG_MATVEC, (k_cg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
 }
 template <typename T> void launch_cg_update(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_dir(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_DIR, (k_cg_dir<T><<<GRID>>>(L.boxes, L.work)));
+  FE_LAUNCH(L, KID_CG_DIR, (k_cg_dir<T><<<EGRID>>>(L.boxes, L.ework)));
 }
 template <typename T> void launch_true_res(const Launch& L, int xs) {
   FE_LAUNCH(L, KID_TRUE_RES, (k_true_res<T><<<GRID>>>(L.boxes, L.work, L.part, xs)));
@@ -436,6 +677,15 @@ template <typename T> void launch_bicg_s(const Launch& L) {
 template <typename T> void launch_bicg_x(const Launch& L) {
   FE_LAUNCH(L, KID_BICG_X, (k_bicg_x<T><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
 }
+template <typename T> void launch_mix_residual(const Launch& L, int first, int* outer_active) {
+  FE_LAUNCH(L, KID_MIX_RES, (k_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, first, outer_active)));
+}
+template <typename T> void launch_mix_accum(const Launch& L) {
+  FE_LAUNCH(L, KID_MIX_ACC, (k_mix_accum<T><<<EGRID>>>(L.boxes, L.ework)));
+}
+template <typename T> void launch_mix_finish(const Launch& L) {
+  FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework)));
+}
 
 #define INST(T)                                                  \
   template void launch_cg_init<T>(const Launch&, double);        \
@@ -447,7 +697,10 @@ template <typename T> void launch_bicg_x(const Launch& L) {
   template void launch_bicg_p<T>(const Launch&);                 \
   template void launch_bicg_v<T>(const Launch&);                 \
   template void launch_bicg_s<T>(const Launch&);                 \
-  template void launch_bicg_x<T>(const Launch&);
+  template void launch_bicg_x<T>(const Launch&);                 \
+  template void launch_mix_residual<T>(const Launch&, int, int*); \
+  template void launch_mix_accum<T>(const Launch&);              \
+  template void launch_mix_finish<T>(const Launch&);
 INST(double)
 INST(float)
 

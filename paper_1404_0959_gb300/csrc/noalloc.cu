@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NTHR) na_init(BoxDev B) {
     }
   }
   __shared__ double res[2];
-  if (block_sum_last<2>(v, B, part, res)) {
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_RZ] = res[0];
       B.sc[SC_BB] = res[1];
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NTHR) na_matvec(BoxDev B) {
     }
   }
   __shared__ double res[1];
-  if (block_sum_last<1>(v, B, part, res)) {
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
   }
 }
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(NTHR) na_update(BoxDev B) {
     }
   }
   __shared__ double res[2];
-  if (block_sum_last<2>(v, B, part, res)) {
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double it = B.sc[SC_ITERS] + 1.0;
       B.sc[SC_ITERS] = it;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(NTHR) na_true_res(BoxDev B) {
     }
   }
   __shared__ double res[1];
-  if (block_sum_last<1>(v, B, part, res)) {
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) B.sc[SC_TRUE_RR] = res[0];
   }
 }

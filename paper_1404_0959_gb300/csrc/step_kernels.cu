@@ -88,22 +88,25 @@ __device__ __forceinline__ T energy_face(const T* const (&u)[3], const T* const 
 // ---------------------------------------------------------------------------------
 // a1: adaptive time step from max_i sum_d |u_d| of state s.
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_dt(const BoxDev* boxes, const int2* work, double* part, int s) {
-  Tile t = tile_of(boxes, work);
-  const BoxDev& B = boxes[t.box];
-  const T* u0 = F<T>(B, S(s, F_U0));
-  const T* u1 = F<T>(B, S(s, F_U1));
-  const T* u2 = F<T>(B, S(s, F_U2));
-  double m = 0.0;
-  if (t.active) {
-    for (int k = t.k0; k < t.kend; ++k) {
-      int c = t.i + B.N * (t.j + B.N * k);
-      double v = fabs((double)u0[c]) + fabs((double)u1[c]) + fabs((double)u2[c]);
-      m = fmax(m, v);
+__global__ void __launch_bounds__(NTHR) k_dt(const BoxDev* boxes, const int2* ework, double* part, int s) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  const T* __restrict__ u0 = F<T>(B, S(s, F_U0));
+  const T* __restrict__ u1 = F<T>(B, S(s, F_U1));
+  const T* __restrict__ u2 = F<T>(B, S(s, F_U2));
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  T m = T(0);
+  for (int q0 = ch.begin + 4 * tid; q0 < ch.end; q0 += 4 * NTHR) {
+    if (q0 + 4 <= ch.end) {
+      V4<T> a = ld4(u0 + q0), b = ld4(u1 + q0), c = ld4(u2 + q0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) m = fmax(m, fabs(a.v[e]) + fabs(b.v[e]) + fabs(c.v[e]));
+    } else {
+      for (int c = q0; c < ch.end; ++c) m = fmax(m, fabs(u0[c]) + fabs(u1[c]) + fabs(u2[c]));
     }
   }
   __shared__ double res;
-  if (block_max_last(m, B, part, &res)) {
+  if (block_max_last((double)m, B, part, &res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       double umax = res;
       double dt = umax > 0.0 ? B.cfl * B.h / umax : HUGE_VAL;
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(NTHR) k_div(const BoxDev* boxes, const int2* w
 // a3: predictor.  Writes D(phi^n), R^n, Du/Dt at level n, psi, rho0 and u*
 // (rho0 and u* into state set kset).
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
+__global__ void __launch_bounds__(NTHR, 3) k_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
   Tile t = tile_of(boxes, work);
   if (!t.active) return;
   const BoxDev& B = boxes[t.box];
@@ -149,9 +152,11 @@ __global__ void __launch_bounds__(NTHR) k_pred(const BoxDev* boxes, const int2* 
   T* Rn[3] = {F<T>(B, W_RN0), F<T>(B, W_RN1), F<T>(B, W_RN2)};
   T* An[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
   T* psi = F<T>(B, W_PSI);
+  T* dinv = F<T>(B, W_DINV);
   T* rho0 = F<T>(B, S(kset, F_RHO));
   T* us[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
   for (int k = t.k0; k < t.kend; ++k) {
     Nbr n(t.i, t.j, k, B.N);
     const int c = n(0, 0, 0);
@@ -161,24 +166,27 @@ __global__ void __launch_bounds__(NTHR) k_pred(const BoxDev* boxes, const int2* 
     dph *= ih;
     const T r = __ldg(&rho[c]);
     const T r0 = r - dt * dph;
+    const T ir0 = T(1) / r0, ir = T(1) / r;
     T L[3], visc[3];
     eval_L<T>(u, phi, div, n, ih, mu, L, visc);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
-      us[m][c] = (r * __ldg(&u[m][c]) + dt * (L[m] - gp)) / r0;
+      us[m][c] = (r * __ldg(&u[m][c]) + dt * (L[m] - gp)) * ir0;
       Rn[m][c] = L[m];
-      An[m][c] = (visc[m] - gp) / r;
+      An[m][c] = (visc[m] - gp) * ir;
     }
-    psi[c] = r / (gam * __ldg(&p[c]));
+    const T ps = r / (gam * __ldg(&p[c]));
+    psi[c] = ps;
+    dinv[c] = T(1) / (ps * idt + c3);
     divphi[c] = dph;
     rho0[c] = r0;
   }
 }
 
 // n-level dust flux divergences D(phi_p^n I4 Y^n) and, Fourier, D(F_E^n).
-template <typename T>
-__global__ void __launch_bounds__(NTHR) k_fluxn(const BoxDev* boxes, const int2* work, int s) {
+template <typename T, bool FOURIER>
+__global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_fluxn(const BoxDev* boxes, const int2* work, int s) {
   Tile t = tile_of(boxes, work);
   if (!t.active) return;
   const BoxDev& B = boxes[t.box];
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(NTHR) k_fluxn(const BoxDev* boxes, const int2*
       }
       F<T>(B, W_FYN0 + j)[c] = acc * ih;
     }
-    if (B.closure == FE_FOURIER) {
+    if (FOURIER) {
       const T* Tf = F<T>(B, S(s, F_T));
       const T* p = F<T>(B, S(s, F_P));
       const T* div = F<T>(B, W_DIV);
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(NTHR) k_fluxn(const BoxDev* boxes, const int2*
 
 // a4: HbyA = (rho^n u^n + dt (R^n + L(u^{k-1}, phi^{k-1}))/2) / rho^{k-1}
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
+__global__ void __launch_bounds__(NTHR, 3) k_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
                                                int rhop) {
   Tile t = tile_of(boxes, work);
   if (!t.active) return;
@@ -254,11 +262,11 @@ __global__ void __launch_bounds__(NTHR) k_asm(const BoxDev* boxes, const int2* w
     T L[3], visc[3];
     eval_L<T>(u, phi, div, n, ih, mu, L, visc);
     const T r = __ldg(&rho[c]);
-    const T rpc = __ldg(&rp[c]);
+    const T irp = T(1) / __ldg(&rp[c]);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       T R = T(0.5) * (__ldg(&Rn[m][c]) + L[m]);
-      hb[m][c] = (r * __ldg(&un[m][c]) + dt * R) / rpc;
+      hb[m][c] = (r * __ldg(&un[m][c]) + dt * R) * irp;
     }
   }
 }
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(NTHR) k_rhs(const BoxDev* boxes, const int2* w
   const T* divphi = F<T>(B, W_DIVPHI);
   T* ps[3] = {F<T>(B, W_PS0), F<T>(B, W_PS1), F<T>(B, W_PS2)};
   T* b = F<T>(B, K_B);
-  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
   for (int k = t.k0; k < t.kend; ++k) {
     Nbr n(t.i, t.j, k, B.N);
     const int c = n(0, 0, 0);
@@ -290,15 +298,15 @@ __global__ void __launch_bounds__(NTHR) k_rhs(const BoxDev* boxes, const int2* w
       ps[d][c] = fp;
       dsum += fp - fm;
     }
-    b[c] = -((__ldg(&rp[c]) - __ldg(&rho[c])) / dt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
+    b[c] = -((__ldg(&rp[c]) - __ldg(&rho[c])) * idt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
   }
 }
 
 // a6: p^k, phi^k, u^k, rho^k from the correction x = p'; the true residual
 // ||b - M x||^2 of the solve is accumulated on the way (same stencil reads).
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_corr(const BoxDev* boxes, const int2* work, double* part, int s,
-                                                int rhop, int pp, int pnew, int kset, int kidx) {
+__global__ void __launch_bounds__(NTHR, 2) k_corr(const BoxDev* boxes, const int2* work, double* part, int s,
+                                                int rhop, int pp, int pnew, int kset, int kidx, int mixed) {
   Tile t = tile_of(boxes, work);
   const BoxDev& B = boxes[t.box];
   const T* rho = F<T>(B, S(s, F_RHO));
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(NTHR) k_corr(const BoxDev* boxes, const int2* 
   const T* divphi = F<T>(B, W_DIVPHI);
   T* phk[3] = {F<T>(B, S(kset, F_PHI0)), F<T>(B, S(kset, F_PHI1)), F<T>(B, S(kset, F_PHI2))};
   T* uk[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
-  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
   const bool tr = B.transonic != 0;
   double rr = 0.0;
   if (t.active) {
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(NTHR) k_corr(const BoxDev* boxes, const int2* 
         phk[d][c] = fp;
         dsum += fp - fm;
       }
-      const T rpc = rk[c];
+      const T dtr = dt / rk[c];
       pn[c] = __ldg(&p[c]) + xc;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
@@ -360,21 +368,28 @@ __global__ void __launch_bounds__(NTHR) k_corr(const BoxDev* boxes, const int2* 
           g[q] = __ldg(&p[id]) + __ldg(&x[id]);
         }
         T gp = (T(10) * (g[2] - g[1]) - (g[3] - g[0])) * T(0.0625) * ih;
-        uk[m][c] = __ldg(&hb[m][c]) - dt / rpc * gp;
+        uk[m][c] = __ldg(&hb[m][c]) - dtr * gp;
       }
       rk[c] = __ldg(&rho[c]) - T(0.5) * dt * (__ldg(&divphi[c]) + dsum * ih);
-      T Mx = psic * xc / dt - T(0.5) * dt * lap * ih * ih + T(0.5) * trd * ih;
-      double r = (double)__ldg(&b[c]) - (double)Mx;
-      rr += r * r;
+      if (!mixed) {
+        T Mx = psic * xc * idt - T(0.5) * dt * lap * ih * ih + T(0.5) * trd * ih;
+        double r = (double)__ldg(&b[c]) - (double)Mx;
+        rr += r * r;
+      }
     }
   }
   double v[1] = {rr};
   __shared__ double res[1];
-  if (block_sum_last<1>(v, B, part, res)) {
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double bb = B.sc[SC_BB];
-      B.sc[SC_RES0 + kidx] = bb > 0.0 ? sqrt(res[0] / bb) : 0.0;
-      B.sc[SC_IT0 + kidx] = B.sc[SC_ITERS];
+      if (mixed) {  // FP64 refinement residual and total inner iterations
+        B.sc[SC_RES0 + kidx] = B.sc[SC_ORES];
+        B.sc[SC_IT0 + kidx] = B.sc[SC_ITSUM];
+      } else {
+        double bb = B.sc[SC_BB];
+        B.sc[SC_RES0 + kidx] = bb > 0.0 ? sqrt(res[0] / bb) : 0.0;
+        B.sc[SC_IT0 + kidx] = B.sc[SC_ITERS];
+      }
     }
   }
 }
@@ -394,13 +409,13 @@ __global__ void __launch_bounds__(NTHR) k_accel(const BoxDev* boxes, const int2*
   for (int k = t.k0; k < t.kend; ++k) {
     Nbr n(t.i, t.j, k, B.N);
     const int c = n(0, 0, 0);
-    const T r = __ldg(&rho[c]);
+    const T ir = T(1) / __ldg(&rho[c]);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       T lap = DG4_h2<T>(u[m], n, 0, 0, 0, 0) + DG4_h2<T>(u[m], n, 1, 0, 0, 0) + DG4_h2<T>(u[m], n, 2, 0, 0, 0);
       T visc = mu * (lap * ih * ih + Gc_h<T>(div, n, m, 0, 0, 0) * ih * T(1.0 / 3.0));
       T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
-      a[m][c] = (visc - gp) / r;
+      a[m][c] = (visc - gp) * ir;
     }
   }
 }
@@ -408,8 +423,8 @@ __global__ void __launch_bounds__(NTHR) k_accel(const BoxDev* boxes, const int2*
 // a7/a8: dust transport at level k, Fourier energy, and on the last
 // corrector the closure plus the conserved totals and a non-finite count.
 // eprev < 0: E^{k-1} = E^n from state s; enew < 0: last corrector (write T, p).
-template <typename T>
-__global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* work, double* part, int s,
+template <typename T, bool FOURIER>
+__global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* boxes, const int2* work, double* part, int s,
                                                 int kset, int pk, int yp0, int yn0, int eprev, int enew,
                                                 int last) {
   Tile t = tile_of(boxes, work);
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* 
   const T* a[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
   const T* p = F<T>(B, pk);
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
-  const bool fourier = B.closure == FE_FOURIER;
+  constexpr bool fourier = FOURIER;
   double acc[3 + MAXD];
 #pragma unroll
   for (int q = 0; q < 3 + MAXD; ++q) acc[q] = 0.0;
@@ -430,6 +445,7 @@ __global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* 
       Nbr n(t.i, t.j, k, B.N);
       const int c = n(0, 0, 0);
       const T rk = __ldg(&rho[c]);
+      const T irk = T(1) / rk;
       const T rn = __ldg(&rhon[c]);
       T ra_p[3], ra_m[3], ph_p[3], ph_m[3];
 #pragma unroll
@@ -450,7 +466,7 @@ __global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* 
           fl += fp - fm;
         }
         T rY = rn * __ldg(&F<T>(B, S(s, F_Y0 + j))[c]) - T(0.5) * dt * (__ldg(&F<T>(B, W_FYN0 + j)[c]) + fl * ih);
-        T Yk = rY / rk;
+        T Yk = rY * irk;
         F<T>(B, yn0 + j)[c] = Yk;
         if (last) {
           acc[3 + j] += (double)rk * (double)Yk;
@@ -481,7 +497,7 @@ __global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* 
                 energy_face<T>(u, phi, div, n, d, bx(d), by(d), bz(d), ih, (T)B.mu, (T)B.kappa, Hat, Tat);
         }
         T rE = rn * En_at(c) - T(0.5) * dt * (__ldg(&F<T>(B, W_FEN)[c]) + fl * ih);
-        Ek = rE / rk;
+        Ek = rE * irk;
         if (enew >= 0) F<T>(B, enew)[c] = Ek;
       }
       if (last) {
@@ -505,7 +521,7 @@ __global__ void __launch_bounds__(NTHR) k_dust(const BoxDev* boxes, const int2* 
   }
   if (!last) return;
   __shared__ double res[3 + MAXD];
-  if (block_sum_last<3 + MAXD>(acc, B, part, res)) {
+  if (block_sum_last<3 + MAXD>(acc, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_MASS] = res[0];
       B.sc[SC_ENERGY] = res[1];
@@ -541,7 +557,7 @@ __global__ void __launch_bounds__(NTHR) k_derive(const BoxDev* boxes, const int2
 // ---- launchers --------------------------------------------------------------------
 #define GRID L.nblocks, dim3(TX, TY), 0, L.st
 template <typename T> void launch_dt(const Launch& L, int s, int) {
-  FE_LAUNCH(L, KID_DT, (k_dt<T><<<GRID>>>(L.boxes, L.work, L.part, s)));
+  FE_LAUNCH(L, KID_DT, (k_dt<T><<<L.neblocks, dim3(TX, TY), 0, L.st>>>(L.boxes, L.ework, L.part, s)));
 }
 template <typename T> void launch_div(const Launch& L, int u0) {
   FE_LAUNCH(L, KID_DIV, (k_div<T><<<GRID>>>(L.boxes, L.work, u0)));
@@ -550,7 +566,8 @@ template <typename T> void launch_pred(const Launch& L, int s, int k) {
   FE_LAUNCH(L, KID_PRED, (k_pred<T><<<GRID>>>(L.boxes, L.work, s, k)));
 }
 template <typename T> void launch_fluxn(const Launch& L, int s) {
-  FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T><<<GRID>>>(L.boxes, L.work, s)));
+  if (L.fourier) FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
+  else FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, false><<<GRID>>>(L.boxes, L.work, s)));
 }
 template <typename T> void launch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
   FE_LAUNCH(L, KID_ASM, (k_asm<T><<<GRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
@@ -558,15 +575,19 @@ template <typename T> void launch_asm(const Launch& L, int s, int up0, int php0,
 template <typename T> void launch_rhs(const Launch& L, int s, int rhop, int pp) {
   FE_LAUNCH(L, KID_RHS, (k_rhs<T><<<GRID>>>(L.boxes, L.work, s, rhop, pp)));
 }
-template <typename T> void launch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx) {
-  FE_LAUNCH(L, KID_CORR, (k_corr<T><<<GRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
+template <typename T> void launch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
+                                       int mixed) {
+  FE_LAUNCH(L, KID_CORR, (k_corr<T><<<GRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx, mixed)));
 }
 template <typename T> void launch_accel(const Launch& L, int kset, int pk) {
   FE_LAUNCH(L, KID_ACCEL, (k_accel<T><<<GRID>>>(L.boxes, L.work, kset, pk)));
 }
 template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yp0, int yn0, int eprev, int enew,
                                        int last, int) {
-  FE_LAUNCH(L, KID_DUST, (k_dust<T><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
+  if (L.fourier)
+    FE_LAUNCH(L, KID_DUST, (k_dust<T, true><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
+  else
+    FE_LAUNCH(L, KID_DUST, (k_dust<T, false><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
 }
 template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
   FE_LAUNCH(L, KID_DERIVE, (k_derive<T><<<GRID>>>(L.boxes, L.work, s, box)));
@@ -579,7 +600,7 @@ template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
   template void launch_fluxn<T>(const Launch&, int);                                         \
   template void launch_asm<T>(const Launch&, int, int, int, int);                            \
   template void launch_rhs<T>(const Launch&, int, int, int);                                 \
-  template void launch_corr<T>(const Launch&, int, int, int, int, int, int);                 \
+  template void launch_corr<T>(const Launch&, int, int, int, int, int, int, int);            \
   template void launch_accel<T>(const Launch&, int, int);                                    \
   template void launch_dust<T>(const Launch&, int, int, int, int, int, int, int, int, int);  \
   template void launch_derive_box<T>(const Launch&, int, int);

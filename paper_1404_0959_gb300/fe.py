@@ -69,7 +69,8 @@ class fe_profile_info(ctypes.Structure):
 
 EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_clock", "fe_step",
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
-           "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_destroy", "fe_strerror"]
+           "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
+           "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -93,6 +94,8 @@ def load_library(path=LIB_PATH):
     lib.fe_kernel_name.restype = ctypes.c_char_p
     lib.fe_solve_pressure_noalloc.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                               c_void_p, POINTER(fe_solve_info)]
+    lib.fe_set_tiling.argtypes = [c_void_p, c_int]
+    lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
     lib.fe_destroy.restype = None
     lib.fe_strerror.argtypes = [c_int]
@@ -210,6 +213,16 @@ def fe_solve_pressure_noalloc(N, psi_ptr, b_ptr, x_ptr, dt, tol, maxit, stream=N
     return code, info
 
 
+def fe_set_tiling(ctx, tz):
+    return _check(lib().fe_set_tiling(ctx, tz), "fe_set_tiling")
+
+
+def fe_autotune(ctx, trials=2):
+    best = c_int(0)
+    _check(lib().fe_autotune(ctx, trials, byref(best)), "fe_autotune")
+    return best.value
+
+
 def fe_destroy(ctx):
     lib().fe_destroy(ctx)
 
@@ -304,6 +317,19 @@ class Solver:
             self.set_field(box, FE_T, T)
         self.init_state(box, FE_INIT_DERIVE)
 
+    def load_state(self, box, st, t=0.0, dt_prev=0.0):
+        """Set every state field (rho, u, phi, p, Y, T) as given, then the clock (checkpoint restore)."""
+        self.set_field(box, FE_RHO, st["rho"])
+        for d in range(3):
+            self.set_field(box, FE_UX + d, st["u"][d])
+            self.set_field(box, FE_PHIX + d, st["phi"][d])
+        self.set_field(box, FE_P, st["p"])
+        for j, y in enumerate(st["Y"]):
+            self.set_field(box, FE_Y0 + j, y)
+        if st.get("T") is not None:
+            self.set_field(box, FE_T, st["T"])
+        fe_set_clock(self.ctx, box, t, dt_prev)
+
     def get_state(self, box=0):
         g = self.get_field
         st = {"rho": g(box, FE_RHO), "u": [g(box, FE_UX + d) for d in range(3)],
@@ -334,6 +360,12 @@ class Solver:
         if nbins > 0:
             out["spectrum"] = spec
         return out
+
+    def autotune(self, trials=2):
+        return fe_autotune(self.ctx, trials)
+
+    def set_tiling(self, tz):
+        fe_set_tiling(self.ctx, tz)
 
     def profile_start(self, kernel=None):
         fe_profile_start(self.ctx, -1 if kernel is None else kernel_id(kernel))
