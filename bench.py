@@ -134,13 +134,56 @@ def run_reference(args, cfg, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_path(fe, box, cfg, precision, solver, args, stream):
+    """Steps/s of one solver path on the same workload (untimed set-up excluded)."""
+    import torch
+    from paper_1404_0959_gb300 import learned
+    N = box["N"]
+    s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
+                  p_maxit=1000, solver=solver, learned_every=0, stream=stream.cuda_stream)
+    s.init_state(0, fe.FE_INIT_SPECTRAL)
+    out = {"precision": "fp64" if precision == fe.FE_FP64 else "mixed",
+           "solver": "jacobi-pcg" if solver == fe.FE_PCG_JACOBI else "fcg, learned first direction"}
+    if solver == fe.FE_FCG_LEARNED:
+        fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
+        bank = learned.PairBank(s, 12)
+        bank.harvest(s, args.learn_steps)
+        t0 = time.perf_counter()
+        hist = learned.train(s, bank, args.learn_iters, lr=1e-3)
+        torch.cuda.synchronize()
+        out.update(train_pairs=bank.n, train_iters=args.learn_iters, train_s=time.perf_counter() - t0,
+                   loss_first=hist[0], loss_last=hist[-1])
+        s.profile_start("unet")
+        s.step(1)
+        prof = s.profile_stop()
+        out["net_ms_per_apply"] = prof["target_ms"] / max(prof["target_launches"], 1)
+        out["net_applies_per_step"] = prof["target_launches"]
+    s.autotune(1)
+    code, _ = s.step(args.warmup)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    K = max(2, args.steps // 2)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    code, info = s.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    t = ev0.elapsed_time(ev1) / 1e3
+    out.update(steps=K, ms_per_step=1e3 * t / K, value=float(N) ** 3 * K / t, krylov_iters_last_step=info[0]["iters"],
+               rel_res_last_step=info[0]["rel_res"])
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--cpu-n", type=int, default=128)
@@ -149,6 +192,9 @@ def main():
     ap.add_argument("--kernel", default=None, help="kernel timed live for the roofline (default: largest share)")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the untimed per-kernel pass")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile depth")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and learned comparison paths")
+    ap.add_argument("--learn-steps", type=int, default=2, help="steps harvested for training (learned path)")
+    ap.add_argument("--learn-iters", type=int, default=60, help="training iterations (learned path)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -263,6 +309,16 @@ def main():
         e2e = {"value": cells * args.steps * world / te, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(nbytes)}
 
+    s.close()
+
+    # the same workload on the other two solver paths of the metric: plain FP64
+    # Jacobi-PCG, and FP32 steps whose pressure solve starts from the learned
+    # network's direction (trained first on this run's own pressure pairs)
+    extra = {}
+    if not args.no_compare:
+        extra["plain_fp64"] = time_path(fe, box, cfg, fe.FE_FP64, fe.FE_PCG_JACOBI, args, stream)
+        extra["learned_fp32"] = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         tc = oracle_sample(args.cpu_n, 1, cfg)
@@ -288,10 +344,10 @@ def main():
                              "alg_bytes_per_launch": alg_bytes, "launches": prof["target_launches"],
                              "ms_per_launch": per_launch_ms},
                 "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items()},
+                "paths": extra,
                 "gpu_launches": prof["launches"],
                 "clocks": ck, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
 

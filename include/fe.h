@@ -106,6 +106,9 @@ typedef struct {
     double p_tol;               /* ||b - M x||_2 <= p_tol ||b||_2                */
     int32_t p_maxit;            /* Krylov iteration cap per solve                */
     int32_t transonic;          /* 1: add the psi-convection term (non-symmetric) */
+    int32_t learned_every;      /* FE_FCG_LEARNED: network direction at iterations it with
+                                 * it % learned_every == 0 (1 = every iteration), Jacobi
+                                 * direction otherwise; 0 = first iteration only */
 } fe_params;
 
 typedef struct {
@@ -204,6 +207,44 @@ int fe_diagnostics(fe_ctx* ctx, int box, fe_diag* out, double* spectrum, int nbi
  * device array of N^3 context-precision values (Fig. 3 of the paper shows
  * Q iso-surfaces). */
 int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
+
+/* Learned preconditioner (extension of the paper's pressure solve, Sec. 2
+ * par. 1): a 3-level 3D-conv U-Net (16/32/64 channels, 3x3x3 kernels,
+ * periodic padding, ReLU; BF16 weights and activations, FP32 accumulation on
+ * the tensor cores) maps the residual r to a search direction of flexible CG
+ * (solver FE_FCG_LEARNED; one box, N divisible by 4).  When <z, r> <= 0 the
+ * Jacobi direction is used instead, so plain preconditioned CG remains the
+ * fallback.  Network input: channel 0 = r / rms(r), channel 1 = psi - 1.
+ * Layers, in parameter order: e1a 2->16, e1b 16->16, d1 16->32 (stride 2),
+ * e2 32->32, d2 32->64 (stride 2), e3 64->64, u2 [up2(e3), e2] 96->32,
+ * u1 [up2(u2), e1b] 48->16, out 16->1 (linear).  Parameter layout (FP32,
+ * host): per layer W[27][cin][cout] (tap index (dz+1)*9 + (dy+1)*3 + (dx+1)
+ * of a weight applied to x(v + (dx, dy, dz))) followed by b[cout]. */
+long fe_preconditioner_size(void);   /* number of floats of the layout above */
+/* Copy weights in (Adam state reset).  Allocates the network buffers on first use. */
+int fe_load_preconditioner(fe_ctx* ctx, const float* weights, size_t count);
+/* Copy the weights (gradients = 0) or the last training step's gradients (1) out. */
+int fe_get_preconditioner(fe_ctx* ctx, float* out, size_t count, int gradients);
+/* z (device, N^3 FP32) = network(r) for device r (context precision), psi of the current state. */
+int fe_precond_apply(fe_ctx* ctx, int box, const void* r, float* z);
+/* One training step on a pair (r, e) with M e = r (device arrays, context
+ * precision; psi of the current state): input r / rms(r), target e / rms(e),
+ * loss ||y - t||^2 / ||t||^2,
+ * then Adam (Kingma and Ba 2015) with learning rate lr (lr <= 0: gradients
+ * only).  *loss receives the loss before the update. */
+int fe_precond_train_step(fe_ctx* ctx, int box, const void* r, const void* e, double lr, double* loss);
+/* Activations of the last network pass (inspection): layer 0..7 = e1a, e1b,
+ * d1, e2, d2, e3, u2, u1 (after ReLU, channels-last, n_l^3 * C_l floats, n_l
+ * = N, N/2 or N/4), 8 = output (N^3 floats), 9 = packed input (N^3 * 16). */
+int fe_precond_activation(fe_ctx* ctx, int layer, float* out, size_t count);
+/* Advance the context by one step with the plain Jacobi-PCG solver and copy
+ * (residual, correction) pairs of box 0 into b_out[i], x_out[i] (device
+ * arrays of N^3 values of the context precision), per corrector: the
+ * residuals r_k and corrections x* - x_k after Krylov iterations 2 and 5 (when
+ * reached), then the right-hand side b with its converged solution x*.
+ * *npairs = pairs written (<= max_pairs).  These are the training pairs of
+ * this run; fe_precond_train_step uses the psi of the current state. */
+int fe_harvest_pressure(fe_ctx* ctx, void* const* b_out, void* const* x_out, int max_pairs, int* npairs);
 
 /* Tile depth of the stencil kernels: every kernel launch covers all boxes
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz

@@ -22,6 +22,17 @@ template <typename T> void fill(T*, long, double, cudaStream_t);
 template <typename T> int spectrum(const T*, const T*, const T*, int, double*, int, cudaStream_t);
 template <typename T> int diag_sums(const Launch&, const BoxDev&, int, int, double*);
 template <typename T> void qcrit(const Launch&, int, int, T*);
+struct UNet;
+UNet* unet_create(int N, bool training, int* rc);
+void unet_destroy(UNet* U);
+long unet_param_count();
+int unet_set_weights(UNet* U, const float* host, cudaStream_t st);
+int unet_get_weights(UNet* U, float* host, int which, cudaStream_t st);
+template <typename T> void unet_apply_sc(UNet*, const T*, const T*, const double*, int, cudaStream_t);
+template <typename T> int unet_apply(UNet*, const T*, const T*, float*, cudaStream_t);
+template <typename T> int unet_train_step(UNet*, const T*, const T*, const T*, double, double*, cudaStream_t);
+float* unet_output(UNet* U);
+int unet_activation(UNet* U, int l, float* host, long count, cudaStream_t st);
 }  // namespace fe
 
 namespace fe {
@@ -54,11 +65,12 @@ void prof_end(Prof* p, int kid, cudaStream_t st) {
 }
 }  // namespace fe
 
-static const char* kKernelNames[KID_COUNT] = {
+static const char* kKernelNames[] = {
     "dt",      "div",       "pred",      "fluxn",  "asm",      "rhs",       "corr",    "accel",
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
-    "mix_residual", "mix_accum", "mix_finish", "other"};
+    "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec", "unet", "other"};
+static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
 
 struct fe_ctx {
   fe_params prm;
@@ -86,6 +98,11 @@ struct fe_ctx {
   double* hsc = nullptr;   // pinned copy of all box scalars
   int cur = 0;             // state set holding the current state
   int hint[16] = {};       // iterations of the previous Krylov solve, per solve key
+  UNet* unet = nullptr;    // learned preconditioner (FE_FCG_LEARNED)
+  bool unet_ready = false;
+  void* const* harvest_b = nullptr;  // fe_harvest_pressure: per-corrector copies of b and x
+  void* const* harvest_x = nullptr;
+  int harvest_max = 0, harvest_n = 0;
   Prof prof;
   Launch L() {
     return Launch{dbox, dwork, nblocks, dework, neblocks, dpart, dactive, st, &prof, prm.closure == FE_FOURIER};
@@ -140,7 +157,9 @@ static int validate(const fe_params* p) {
   if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED)
     return FE_ERR_INVALID_ARG;
   if (p->transonic && p->solver == FE_PCG_JACOBI) return FE_ERR_INVALID_ARG;
-  if (p->solver == FE_FCG_LEARNED) return FE_ERR_UNSUPPORTED;
+  if (p->solver == FE_FCG_LEARNED && (p->n_boxes != 1 || p->N[0] % 4 != 0 || p->transonic))
+    return FE_ERR_UNSUPPORTED;
+  if (p->learned_every < 0) return FE_ERR_INVALID_ARG;
   for (int b = 0; b < p->n_boxes; ++b)
     if (p->N[b] < 8 || p->N[b] > 512 || !(p->nu[b] >= 0.0)) return FE_ERR_INVALID_ARG;
   return FE_OK;
@@ -311,6 +330,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   else cudaDeviceSynchronize();
   for (void* s : c->slabs) cudaFree(s);
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  unet_destroy(c->unet);
   cudaFree(c->dbox);
   cudaFree(c->dwork);
   cudaFree(c->dework);
@@ -363,6 +383,12 @@ static int push_scalar(fe_ctx* c, int box, int idx, double v) {
 }
 
 // Krylov driver for all boxes: operator/psi/dt already in place, rhs in K_B.
+// y = a - y (harvested snapshot targets)
+template <typename T>
+__global__ void k_sub_from(const T* a, T* y, long n) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) y[q] = a[q] - y[q];
+}
+
 // The host reads the number of running solves only after `batch` iterations
 // have been queued: the first batch is one less than the iteration count of
 // the previous solve with the same key (boxes that finish early skip the
@@ -376,7 +402,18 @@ static int krylov(fe_ctx* c, int maxit, int key) {
   else launch_cg_init<T>(L, 0.0);
   int it = 0;
   int batch = c->hint[key] > 1 ? c->hint[key] - 1 : 1;
+  // harvesting: snapshots (r_k, x_k) of box 0 after iterations 2 and 5 of the first solve
+  const bool snap = c->harvest_b && key <= 1;
+  const int snap_at[2] = {2, 5};
+  int nsnap = 0, snap_slot[2] = {-1, -1};
+  if (snap) batch = 1;
   while (true) {
+    if (snap && nsnap < 2 && it == snap_at[nsnap] && c->harvest_n < c->harvest_max) {
+      const size_t bytes = (size_t)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N * sizeof(T);
+      CK(cudaMemcpyAsync(c->harvest_b[c->harvest_n], c->hbox[0].f[K_R], bytes, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(c->harvest_x[c->harvest_n], c->hbox[0].f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
+      snap_slot[nsnap++] = c->harvest_n++;
+    }
     if (it > 0 || batch == 1) {
       CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
@@ -397,8 +434,48 @@ static int krylov(fe_ctx* c, int maxit, int key) {
     }
   }
   c->hint[key] = it;
+  // snapshot targets: e_k = x* - x_k
+  for (int q = 0; q < nsnap; ++q) {
+    const long n = (long)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N;
+    k_sub_from<T><<<(int)std::min<long>((n + 255) / 256, 4096), 256, 0, c->st>>>(
+        (const T*)c->hbox[0].f[K_X], (T*)c->harvest_x[snap_slot[q]], n);
+  }
   CK(cudaGetLastError());
   return FE_OK;
+}
+
+// Flexible CG with the network direction (box 0; one network application per
+// iteration).  The host polls convergence after every iteration: each one
+// already costs a full network pass.
+template <typename T>
+static int fcg_learned(fe_ctx* c, int maxit) {
+  Launch L = c->L();
+  BoxDev& B = c->hbox[0];
+  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
+  launch_cg_init<T>(L, 0.0);
+  for (int it = 0; it < maxit; ++it) {
+    CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (*c->hactive == 0) break;
+    const int every = c->prm.learned_every;
+    const bool net = every > 0 ? (it % every == 0) : (it == 0);
+    if (net)
+      FE_LAUNCH(L, KID_UNET,
+                (unet_apply_sc<T>(c->unet, (const T*)B.f[K_R], (const T*)B.f[W_PSI], B.sc,
+                                  it == 0 ? SC_BB : SC_RR, c->st)));
+    launch_fcg<T>(L, net ? unet_output(c->unet) : nullptr);
+  }
+  CK(cudaGetLastError());
+  return FE_OK;
+}
+
+template <typename T>
+static int inner_solve(fe_ctx* c, int maxit, int key) {
+  if (c->prm.solver == FE_FCG_LEARNED) {
+    if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
+    return fcg_learned<T>(c, maxit);
+  }
+  return krylov<T>(c, maxit, key);
 }
 
 // Pressure solve of every box with the right-hand side in K_B: one Krylov
@@ -407,7 +484,7 @@ static int krylov(fe_ctx* c, int maxit, int key) {
 // meets the tolerance, then x = (float) x64.
 template <typename T>
 static int pressure_solve(fe_ctx* c) {
-  if (c->fp64) return krylov<T>(c, c->prm.p_maxit, 0);
+  if (c->fp64) return inner_solve<T>(c, c->prm.p_maxit, 0);
   Launch L = c->L();
   CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
   launch_mix_residual<T>(L, 1, c->douter);
@@ -415,7 +492,7 @@ static int pressure_solve(fe_ctx* c) {
     CK(cudaMemcpyAsync(c->hactive, c->douter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (*c->hactive == 0) break;
-    int rc = krylov<T>(c, c->prm.p_maxit, 1 + outer);
+    int rc = inner_solve<T>(c, c->prm.p_maxit, 1 + outer);
     if (rc != FE_OK) return rc;
     launch_mix_accum<T>(L);
     launch_mix_residual<T>(L, 0, c->douter);
@@ -454,6 +531,13 @@ static int step_once(fe_ctx* c, bool commit = true) {
     launch_rhs<T>(L, s, rhop, pp);
     int rc = pressure_solve<T>(c);
     if (rc != FE_OK) return rc;
+    if (c->harvest_b && c->harvest_n < c->harvest_max) {
+      const size_t bytes = (size_t)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N * sizeof(T);
+      CK(cudaMemcpyAsync(c->harvest_b[c->harvest_n], c->hbox[0].f[c->fp64 ? K_B : K_AUX], bytes,
+                         cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(c->harvest_x[c->harvest_n], c->hbox[0].f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
+      c->harvest_n++;
+    }
     launch_corr<T>(L, s, rhop, pp, pn, ks, kk, c->fp64 ? 0 : 1);
     launch_div<T>(L, S(ks, F_U0));
     launch_accel<T>(L, ks, pn);
@@ -771,4 +855,78 @@ extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   CK(cudaStreamSynchronize(c->st));
   if (best_tz) *best_tz = best;
   return rc != FE_OK ? rc : rc2;
+}
+
+// ---- learned preconditioner --------------------------------------------------------------
+extern "C" long fe_preconditioner_size(void) { return unet_param_count(); }
+
+extern "C" int fe_load_preconditioner(fe_ctx* c, const float* w, size_t count) {
+  if (!c || !w || (long)count != unet_param_count()) return FE_ERR_INVALID_ARG;
+  if (c->hbox[0].N % 4 != 0) return FE_ERR_UNSUPPORTED;
+  if (!c->unet) {
+    int rc = FE_OK;
+    c->unet = unet_create(c->hbox[0].N, true, &rc);
+    if (!c->unet) return rc;
+  }
+  int rc = unet_set_weights(c->unet, w, c->st);
+  c->unet_ready = rc == FE_OK;
+  return rc;
+}
+
+extern "C" int fe_get_preconditioner(fe_ctx* c, float* w, size_t count, int gradients) {
+  if (!c || !w || (long)count != unet_param_count()) return FE_ERR_INVALID_ARG;
+  if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
+  return unet_get_weights(c->unet, w, gradients ? 1 : 0, c->st);
+}
+
+extern "C" int fe_precond_apply(fe_ctx* c, int box, const void* r, float* z) {
+  if (!c || box != 0 || !r || !z) return FE_ERR_INVALID_ARG;
+  if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
+  const int s = c->cur;
+  BoxDev& B = c->hbox[0];
+  // psi of the current state (dt does not enter the network input)
+  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, s, 1.0);
+  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, s, 1.0);
+  int rc;
+  if (c->fp64) {
+    rc = unet_apply<double>(c->unet, (const double*)r, (const double*)B.f[W_PSI], z, c->st);
+  } else {
+    rc = unet_apply<float>(c->unet, (const float*)r, (const float*)B.f[W_PSI], z, c->st);
+  }
+  (void)s;
+  return rc;
+}
+
+extern "C" int fe_precond_train_step(fe_ctx* c, int box, const void* r, const void* e, double lr, double* loss) {
+  if (!c || box != 0 || !r || !e || !loss) return FE_ERR_INVALID_ARG;
+  if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
+  BoxDev& B = c->hbox[0];
+  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, 1.0);
+  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, 1.0);
+  if (c->fp64)
+    return unet_train_step<double>(c->unet, (const double*)r, (const double*)e, (const double*)B.f[W_PSI], lr, loss,
+                                   c->st);
+  return unet_train_step<float>(c->unet, (const float*)r, (const float*)e, (const float*)B.f[W_PSI], lr, loss, c->st);
+}
+
+extern "C" int fe_harvest_pressure(fe_ctx* c, void* const* b_out, void* const* x_out, int max_pairs, int* npairs) {
+  if (!c || !b_out || !x_out || max_pairs < 1 || !npairs) return FE_ERR_INVALID_ARG;
+  const int solver = c->prm.solver;
+  c->prm.solver = FE_PCG_JACOBI;
+  c->harvest_b = b_out;
+  c->harvest_x = x_out;
+  c->harvest_max = max_pairs;
+  c->harvest_n = 0;
+  int rc = c->fp64 ? step_once<double>(c) : step_once<float>(c);
+  c->prm.solver = solver;
+  c->harvest_b = c->harvest_x = nullptr;
+  *npairs = c->harvest_n;
+  if (rc == FE_OK) CK(cudaStreamSynchronize(c->st));
+  return rc;
+}
+
+extern "C" int fe_precond_activation(fe_ctx* c, int layer, float* out, size_t count) {
+  if (!c || !out) return FE_ERR_INVALID_ARG;
+  if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
+  return unet_activation(c->unet, layer, out, (long)count, c->st);
 }

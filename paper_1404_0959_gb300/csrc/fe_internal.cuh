@@ -65,6 +65,7 @@ enum Scalar {
   SC_TOL, SC_MAXIT, SC_KDT,   // Krylov tolerance, cap and the dt of its operator
   SC_IT0, SC_IT1, SC_IT2, SC_IT3, SC_RES0, SC_RES1, SC_RES2, SC_RES3,
   SC_ODONE, SC_OBB, SC_ORR, SC_ORES, SC_ITSUM, SC_OTOL, SC_OUTER,  // mixed-precision refinement
+  SC_FB, SC_NFB,                                                    // flexible CG: Jacobi fallback flag, count
   SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
   NSC = SC_DUST0 + MAXD + 4
 };
@@ -371,7 +372,8 @@ enum KernelId {
   KID_DT = 0, KID_DIV, KID_PRED, KID_FLUXN, KID_ASM, KID_RHS, KID_CORR, KID_ACCEL, KID_DUST, KID_DERIVE,
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
-  KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_OTHER, KID_COUNT
+  KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
+  KID_UNET, KID_OTHER, KID_COUNT
 };
 
 struct Prof;  // defined in fe_api.cu
@@ -426,5 +428,6 @@ template <typename V> void launch_bicg_x(const Launch& L);
 template <typename V> void launch_mix_residual(const Launch& L, int first, int* outer_active);
 template <typename V> void launch_mix_accum(const Launch& L);
 template <typename V> void launch_mix_finish(const Launch& L);
+template <typename V> void launch_fcg(const Launch& L, const float* z);
 
 }  // namespace fe

@@ -643,6 +643,89 @@ __global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const 
   }
 }
 
+// ---- flexible CG (learned preconditioner) ------------------------------------------------
+// Direction candidates: z (network output, FP32) or the Jacobi direction
+// r / diag when <z, r> <= 0.  p = z' - beta p_prev with
+// beta = <z', q_prev> / <p_prev, q_prev> (Notay 2000, truncation 1).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fcg_dots(const BoxDev* boxes, const int2* ework, double* part,
+                                                   const float* z) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  if (box_done(B)) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ q = F<T>(B, K_Q);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  DotAcc<T> zr, zq, dq;
+  for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
+    const T rc = r[c], qc = q[c], rd = rc * dinv[c];
+    const T zc = z ? (T)z[c] : rd;  // no network output: Jacobi direction
+    zr.add(zc, rc);
+    zq.add(zc, qc);
+    dq.add(rd, qc);
+  }
+  double v[3] = {zr.value(), zq.value(), dq.value()};
+  __shared__ double res[3];
+  if (block_sum_last<3>(v, B, part, res, B.etile0, B.entiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const bool fb = !(res[0] > 0.0);
+      B.sc[SC_FB] = fb ? 1.0 : 0.0;
+      if (fb) B.sc[SC_NFB] += 1.0;
+      const double pq = B.sc[SC_PQ];
+      B.sc[SC_BETA] = (B.sc[SC_ITERS] == 0.0 || !(pq != 0.0)) ? 0.0 : (fb ? res[2] : res[1]) / pq;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fcg_dir(const BoxDev* boxes, const int2* ework, const float* z) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  if (box_done(B)) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ p = F<T>(B, K_PD);
+  const bool fb = B.sc[SC_FB] != 0.0;
+  const T beta = (T)B.sc[SC_BETA];
+  for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
+    const T zc = (fb || !z) ? r[c] * dinv[c] : (T)z[c];
+    p[c] = zc - beta * p[c];
+  }
+}
+
+// q = M p; alpha = <p, r> / <p, q>
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fcg_matvec(const BoxDev* boxes, const int2* work, double* part) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (box_done(B)) return;
+  const T* __restrict__ p = F<T>(B, K_PD);
+  const T* __restrict__ r = F<T>(B, K_R);
+  T* __restrict__ q = F<T>(B, K_Q);
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
+  DotAcc<T> pq, pr;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      Nbr n(t.i, t.j, k, B.N);
+      const int c = n(0, 0, 0);
+      const T y = applyM<T, false>(B, p, n, dt, ih);
+      q[c] = y;
+      pq.add(p[c], y);
+      pr.add(p[c], r[c]);
+    }
+  }
+  double v[2] = {pq.value(), pr.value()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_PQ] = res[0];
+      B.sc[SC_ALPHA] = res[1] / res[0];
+    }
+  }
+}
+
 // ---- launchers ------------------------------------------------------------------------
 #define GRID L.nblocks, dim3(TX, TY), 0, L.st
 #define EGRID L.neblocks, dim3(TX, TY), 0, L.st
@@ -677,6 +760,12 @@ template <typename T> void launch_bicg_s(const Launch& L) {
 template <typename T> void launch_bicg_x(const Launch& L) {
   FE_LAUNCH(L, KID_BICG_X, (k_bicg_x<T><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
 }
+template <typename T> void launch_fcg(const Launch& L, const float* z) {
+  FE_LAUNCH(L, KID_FCG_DOTS, (k_fcg_dots<T><<<EGRID>>>(L.boxes, L.ework, L.part, z)));
+  FE_LAUNCH(L, KID_FCG_DIR, (k_fcg_dir<T><<<EGRID>>>(L.boxes, L.ework, z)));
+  FE_LAUNCH(L, KID_FCG_MATVEC, (k_fcg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+}
 template <typename T> void launch_mix_residual(const Launch& L, int first, int* outer_active) {
   FE_LAUNCH(L, KID_MIX_RES, (k_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, first, outer_active)));
 }
@@ -700,7 +789,8 @@ template <typename T> void launch_mix_finish(const Launch& L) {
   template void launch_bicg_x<T>(const Launch&);                 \
   template void launch_mix_residual<T>(const Launch&, int, int*); \
   template void launch_mix_accum<T>(const Launch&);              \
-  template void launch_mix_finish<T>(const Launch&);
+  template void launch_mix_finish<T>(const Launch&);              \
+  template void launch_fcg<T>(const Launch&, const float*);
 INST(double)
 INST(float)
 

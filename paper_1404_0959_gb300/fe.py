@@ -45,7 +45,7 @@ class fe_params(ctypes.Structure):
                 ("tau_p", POINTER(c_double)), ("Y0", POINTER(c_double)), ("mach_rms", POINTER(c_double)),
                 ("k0", POINTER(c_double)), ("seed", POINTER(c_uint64)), ("cfl", c_double),
                 ("dt_growth_max", c_double), ("dt_max", c_double), ("n_corr", c_int32), ("solver", c_int32),
-                ("p_tol", c_double), ("p_maxit", c_int32), ("transonic", c_int32)]
+                ("p_tol", c_double), ("p_maxit", c_int32), ("transonic", c_int32), ("learned_every", c_int32)]
 
 
 class fe_step_info(ctypes.Structure):
@@ -70,7 +70,8 @@ class fe_profile_info(ctypes.Structure):
 EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_clock", "fe_step",
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
-           "fe_destroy", "fe_strerror"]
+           "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
+           "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -94,6 +95,14 @@ def load_library(path=LIB_PATH):
     lib.fe_kernel_name.restype = ctypes.c_char_p
     lib.fe_solve_pressure_noalloc.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                               c_void_p, POINTER(fe_solve_info)]
+    lib.fe_preconditioner_size.argtypes = []
+    lib.fe_preconditioner_size.restype = ctypes.c_long
+    lib.fe_load_preconditioner.argtypes = [c_void_p, c_void_p, ctypes.c_size_t]
+    lib.fe_get_preconditioner.argtypes = [c_void_p, c_void_p, ctypes.c_size_t, c_int]
+    lib.fe_precond_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
+    lib.fe_precond_train_step.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_double, POINTER(c_double)]
+    lib.fe_precond_activation.argtypes = [c_void_p, c_int, c_void_p, ctypes.c_size_t]
+    lib.fe_harvest_pressure.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_int)]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
@@ -101,7 +110,7 @@ def load_library(path=LIB_PATH):
     lib.fe_strerror.argtypes = [c_int]
     lib.fe_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("fe_destroy", "fe_strerror", "fe_kernel_name"):
+        if name not in ("fe_destroy", "fe_strerror", "fe_kernel_name", "fe_preconditioner_size"):
             getattr(lib, name).restype = c_int
     return lib
 
@@ -213,6 +222,49 @@ def fe_solve_pressure_noalloc(N, psi_ptr, b_ptr, x_ptr, dt, tol, maxit, stream=N
     return code, info
 
 
+def fe_preconditioner_size():
+    return int(lib().fe_preconditioner_size())
+
+
+def fe_load_preconditioner(ctx, weights):
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
+    return _check(lib().fe_load_preconditioner(ctx, w.ctypes.data, w.size), "fe_load_preconditioner")
+
+
+def fe_get_preconditioner(ctx, gradients=False):
+    w = np.empty(fe_preconditioner_size(), dtype=np.float32)
+    _check(lib().fe_get_preconditioner(ctx, w.ctypes.data, w.size, int(gradients)), "fe_get_preconditioner")
+    return w
+
+
+def fe_precond_apply(ctx, box, r_ptr, z_ptr):
+    return _check(lib().fe_precond_apply(ctx, box, c_void_p(r_ptr), c_void_p(z_ptr)), "fe_precond_apply")
+
+
+def fe_precond_train_step(ctx, box, r_ptr, e_ptr, lr):
+    loss = c_double(0.0)
+    _check(lib().fe_precond_train_step(ctx, box, c_void_p(r_ptr), c_void_p(e_ptr), lr, byref(loss)),
+           "fe_precond_train_step")
+    return loss.value
+
+
+def fe_precond_activation(ctx, layer, count):
+    out = np.empty(count, dtype=np.float32)
+    _check(lib().fe_precond_activation(ctx, layer, out.ctypes.data, count), "fe_precond_activation")
+    return out
+
+
+def fe_harvest_pressure(ctx, b_ptrs, x_ptrs):
+    n = len(b_ptrs)
+    bb = (c_void_p * n)(*[c_void_p(p) for p in b_ptrs])
+    xx = (c_void_p * n)(*[c_void_p(p) for p in x_ptrs])
+    got = c_int(0)
+    code = lib().fe_harvest_pressure(ctx, bb, xx, n, byref(got))
+    if code not in (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_NONFINITE):
+        raise FeError(code, "fe_harvest_pressure")
+    return code, got.value
+
+
 def fe_set_tiling(ctx, tz):
     return _check(lib().fe_set_tiling(ctx, tz), "fe_set_tiling")
 
@@ -241,7 +293,7 @@ class Solver:
 
     def __init__(self, boxes, precision=FE_FP64, closure=FE_BAROTROPIC, gamma=1.4, Pr=0.7, cfl=0.5,
                  dt_growth_max=1.2, dt_max=float("inf"), n_corr=2, solver=FE_PCG_JACOBI, p_tol=1e-10,
-                 p_maxit=500, transonic=False, stream=None):
+                 p_maxit=500, transonic=False, learned_every=1, stream=None):
         import torch
         self.torch = torch
         nb = len(boxes)
@@ -263,7 +315,7 @@ class Solver:
         self.params = fe_params(nb, self._N, precision, closure, gamma, Pr, self._nu, nd, self._tau, self._y0,
                                 self._mach, self._k0, self._seed, cfl, dt_growth_max,
                                 dt_max if np.isfinite(dt_max) else 0.0, n_corr, solver, p_tol, p_maxit,
-                                int(bool(transonic)))
+                                int(bool(transonic)), int(learned_every))
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream

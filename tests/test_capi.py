@@ -61,7 +61,7 @@ def _params(**kw):
     tau = (ctypes.c_double * 1)(0.05)
     y0 = (ctypes.c_double * 1)(0.01)
     keep += [N, nu, mach, k0, seed, tau, y0]
-    p = fe.fe_params(1, N, 0, 0, 1.4, 0.7, nu, 1, tau, y0, mach, k0, seed, 0.5, 1.2, 0.0, 2, 0, 1e-10, 100, 0)
+    p = fe.fe_params(1, N, 0, 0, 1.4, 0.7, nu, 1, tau, y0, mach, k0, seed, 0.5, 1.2, 0.0, 2, 0, 1e-10, 100, 0, 1)
     for k, v in kw.items():
         setattr(p, k, v)
     return p, keep
