@@ -105,7 +105,8 @@ struct fe_ctx {
   int harvest_max = 0, harvest_n = 0;
   Prof prof;
   Launch L() {
-    return Launch{dbox, dwork, nblocks, dework, neblocks, dpart, dactive, st, &prof, prm.closure == FE_FOURIER};
+    return Launch{dbox,  dwork, nblocks, dework, neblocks, dpart, dactive, st, &prof, prm.closure == FE_FOURIER,
+                  prm.transonic, prm.n_dust};
   }
 };
 

@@ -390,7 +390,9 @@ struct Launch {
   int* active;  // number of boxes whose Krylov solve is running
   cudaStream_t st;
   Prof* prof;
-  int fourier;  // closure of the context (selects kernel variants)
+  int fourier;    // closure of the context (selects kernel variants)
+  int transonic;  // transonic pressure operator
+  int nd;         // dust classes
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.

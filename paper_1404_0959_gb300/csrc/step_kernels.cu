@@ -12,6 +12,17 @@
 
 namespace fe {
 
+// z-marching shared-memory variants (step_zkernels.cu)
+template <typename T> void zlaunch_div(const Launch& L, int u0);
+template <typename T> void zlaunch_pred(const Launch& L, int s, int k);
+template <typename T> void zlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop);
+template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp);
+template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
+                                        int mixed);
+template <typename T> void zlaunch_accel(const Launch& L, int kset, int pk);
+template <typename T> void zlaunch_fluxn(const Launch& L, int s, int nd);
+template <typename T> void zlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd);
+
 template <typename T>
 __device__ __forceinline__ T* F(const BoxDev& B, int slot) {
   return reinterpret_cast<T*>(B.f[slot]);
@@ -559,32 +570,28 @@ __global__ void __launch_bounds__(NTHR) k_derive(const BoxDev* boxes, const int2
 template <typename T> void launch_dt(const Launch& L, int s, int) {
   FE_LAUNCH(L, KID_DT, (k_dt<T><<<L.neblocks, dim3(TX, TY), 0, L.st>>>(L.boxes, L.ework, L.part, s)));
 }
-template <typename T> void launch_div(const Launch& L, int u0) {
-  FE_LAUNCH(L, KID_DIV, (k_div<T><<<GRID>>>(L.boxes, L.work, u0)));
-}
-template <typename T> void launch_pred(const Launch& L, int s, int k) {
-  FE_LAUNCH(L, KID_PRED, (k_pred<T><<<GRID>>>(L.boxes, L.work, s, k)));
-}
+template <typename T> void launch_div(const Launch& L, int u0) { zlaunch_div<T>(L, u0); }
+template <typename T> void launch_pred(const Launch& L, int s, int k) { zlaunch_pred<T>(L, s, k); }
 template <typename T> void launch_fluxn(const Launch& L, int s) {
-  if (L.fourier) FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
+  if (!L.fourier && L.nd >= 1 && L.nd <= 3) zlaunch_fluxn<T>(L, s, L.nd);
+  else if (L.fourier) FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
   else FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, false><<<GRID>>>(L.boxes, L.work, s)));
 }
 template <typename T> void launch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
-  FE_LAUNCH(L, KID_ASM, (k_asm<T><<<GRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
+  zlaunch_asm<T>(L, s, up0, php0, rhop);
 }
-template <typename T> void launch_rhs(const Launch& L, int s, int rhop, int pp) {
-  FE_LAUNCH(L, KID_RHS, (k_rhs<T><<<GRID>>>(L.boxes, L.work, s, rhop, pp)));
-}
+template <typename T> void launch_rhs(const Launch& L, int s, int rhop, int pp) { zlaunch_rhs<T>(L, s, rhop, pp); }
 template <typename T> void launch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
                                        int mixed) {
-  FE_LAUNCH(L, KID_CORR, (k_corr<T><<<GRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx, mixed)));
+  if (!L.transonic) zlaunch_corr<T>(L, s, rhop, pp, pnew, kset, kidx, mixed);
+  else FE_LAUNCH(L, KID_CORR, (k_corr<T><<<GRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx, mixed)));
 }
-template <typename T> void launch_accel(const Launch& L, int kset, int pk) {
-  FE_LAUNCH(L, KID_ACCEL, (k_accel<T><<<GRID>>>(L.boxes, L.work, kset, pk)));
-}
+template <typename T> void launch_accel(const Launch& L, int kset, int pk) { zlaunch_accel<T>(L, kset, pk); }
 template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yp0, int yn0, int eprev, int enew,
                                        int last, int) {
-  if (L.fourier)
+  if (!L.fourier && L.nd >= 1 && L.nd <= 3)
+    zlaunch_dust<T>(L, s, kset, yp0, yn0, last, L.nd);
+  else if (L.fourier)
     FE_LAUNCH(L, KID_DUST, (k_dust<T, true><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
   else
     FE_LAUNCH(L, KID_DUST, (k_dust<T, false><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));

@@ -1,0 +1,114 @@
+// zmarch.cuh -- z-marching star-stencil machinery for the step kernels.
+//
+// A 32 x 8 thread block owns a 32 x 8 column tile and walks tz z-planes.  For
+// every field read with a star stencil of radius R (offsets along one axis at
+// a time) each thread keeps its column's values at z-offsets -R..R in a
+// register queue (one new global load per plane), and the block stages the
+// current plane of the field with an R-wide x/y halo in shared memory (one
+// interior store per thread plus (4 R TY + 4 R TX) / (TX TY) halo loads per
+// cell).  The tile is "wrapped": thread columns beyond the box edge hold the
+// periodic continuation, so ragged tiles and N < 32 need no special cases;
+// only threads inside the box store results.
+#pragma once
+#include "fe_internal.cuh"
+
+namespace fe {
+
+template <int R>
+struct ZGeom {
+  static constexpr int W = TX + 2 * R, H = TY + 2 * R;
+  int N, NN;
+  int col;         // flat (x, y) index of this thread's column
+  int csm;         // its smem position
+  int hcol, hsm;   // halo cell this thread stages (hcol < 0: none)
+  bool active;     // column inside the box
+  __device__ __forceinline__ ZGeom(int x0, int y0, int N_) {
+    N = N_;
+    NN = N * N;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int gx = (x0 + tx) % N, gy = (y0 + ty) % N;
+    active = (x0 + tx < N) && (y0 + ty < N);
+    col = gx + N * gy;
+    csm = (ty + R) * W + tx + R;
+    hcol = -1;
+    hsm = 0;
+    int lx = 0, ly = 0;
+    if (tid < 2 * R * TY) {  // x halo: 2R cells on each of TY rows
+      const int row = tid / (2 * R), k = tid % (2 * R);
+      lx = k < R ? k - R : TX + (k - R);
+      ly = row;
+      hcol = 0;
+    } else if (tid < 2 * R * TY + 2 * R * TX) {  // y halo: 2R rows of TX cells
+      const int q = tid - 2 * R * TY;
+      const int rowi = q / TX, cx = q % TX;
+      lx = cx;
+      ly = rowi < R ? rowi - R : TY + (rowi - R);
+      hcol = 0;
+    }
+    if (hcol == 0) {
+      const int hx = ((x0 + lx) % N + N) % N, hy = ((y0 + ly) % N + N) % N;
+      hcol = hx + N * hy;
+      hsm = (ly + R) * W + lx + R;
+    }
+  }
+  __device__ __forceinline__ int plane(int k) const { return NN * k; }
+  __device__ __forceinline__ int wrapz(int k) const { return k < 0 ? k + N : (k >= N ? k - N : k); }
+};
+
+// One field read with a radius-R star stencil.  Loads run one plane ahead:
+// the z-queue value and the halo value needed at plane k + 1 are requested
+// while plane k is computed.
+template <typename T, int R>
+struct ZField {
+  const T* __restrict__ g;
+  T q[2 * R + 1];  // q[R + s] = value at z-offset s of the current plane
+  T nq;            // next queue entry (plane k + R + 1)
+  T nh;            // next halo value (plane k + 1)
+  T* sm;           // shared plane (H x W)
+  __device__ __forceinline__ void init(const T* gp, T* smem, const ZGeom<R>& G, int k0) {
+    g = gp;
+    sm = smem;
+#pragma unroll
+    for (int s = -R; s < R; ++s) q[R + s + 1] = __ldg(&g[G.col + G.plane(G.wrapz(k0 + s))]);
+    nq = __ldg(&g[G.col + G.plane(G.wrapz(k0 + R))]);
+    nh = G.hcol >= 0 ? __ldg(&g[G.hcol + G.plane(k0)]) : T(0);
+  }
+  // move to plane k: shift the queue in, request plane k + R + 1
+  __device__ __forceinline__ void advance(const ZGeom<R>& G, int k) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) q[s] = q[s + 1];
+    q[2 * R] = nq;
+    nq = __ldg(&g[G.col + G.plane(G.wrapz(k + R + 1))]);
+  }
+  // stage the current plane (call between two __syncthreads), request the next halo
+  __device__ __forceinline__ void stage(const ZGeom<R>& G, int k) {
+    sm[G.csm] = q[R];
+    if (G.hcol >= 0) {
+      sm[G.hsm] = nh;
+      nh = __ldg(&g[G.hcol + G.plane(G.wrapz(k + 1))]);
+    }
+  }
+  // value at offset s along axis d from this thread's cell
+  __device__ __forceinline__ T at(const ZGeom<R>& G, int d, int s) const {
+    if (d == 2) return q[R + s];
+    return d == 0 ? sm[G.csm + s] : sm[G.csm + s * ZGeom<R>::W];
+  }
+  __device__ __forceinline__ T c() const { return q[R]; }
+};
+
+// ---- star stencils on a ZField (same arithmetic as the global-memory helpers) ----
+template <typename T, int R>
+__device__ __forceinline__ T zI4(const ZField<T, R>& f, const ZGeom<R>& G, int d, int o) {
+  return (T(9) * (f.at(G, d, o) + f.at(G, d, o + 1)) - (f.at(G, d, o - 1) + f.at(G, d, o + 2))) * T(0.0625);
+}
+template <typename T, int R>
+__device__ __forceinline__ T zGc_h(const ZField<T, R>& f, const ZGeom<R>& G, int d) {
+  return (T(10) * (f.at(G, d, 1) - f.at(G, d, -1)) - (f.at(G, d, 2) - f.at(G, d, -2))) * T(0.0625);
+}
+template <typename T, int R>
+__device__ __forceinline__ T zDG4_h2(const ZField<T, R>& f, const ZGeom<R>& G, int d) {
+  return (T(28) * (f.at(G, d, -1) + f.at(G, d, 1)) - T(54) * f.c() - (f.at(G, d, -2) + f.at(G, d, 2))) *
+         T(1.0 / 24.0);
+}
+
+}  // namespace fe
