@@ -246,6 +246,17 @@ int fe_precond_activation(fe_ctx* ctx, int layer, float* out, size_t count);
  * this run; fe_precond_train_step uses the psi of the current state. */
 int fe_harvest_pressure(fe_ctx* ctx, void* const* b_out, void* const* x_out, int max_pairs, int* npairs);
 
+/* Run each step as one CUDA graph (on = 1): the step's kernels plus the
+ * Krylov iterations and the mixed-precision refinement as conditional WHILE
+ * nodes evaluated on the device (each loop also stops at its iteration cap),
+ * so the host waits once per step instead of once per Krylov iteration.  The
+ * graphs are built on first use for each parity of the state set and rebuilt
+ * after fe_set_tiling / fe_autotune / fe_load_preconditioner.  Results are
+ * identical to the host-driven path (same kernels, same order).  Off by
+ * default; not used during fe_harvest_pressure, profiling, or with
+ * learned_every > 1. */
+int fe_use_graphs(fe_ctx* ctx, int on);
+
 /* Tile depth of the stencil kernels: every kernel launch covers all boxes
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz
  * (0 = built-in default: 8 for N >= 128, else 4).  fe_autotune times `trials`

@@ -99,6 +99,10 @@ struct fe_ctx {
   int cur = 0;             // state set holding the current state
   int hint[16] = {};       // iterations of the previous Krylov solve, per solve key
   UNet* unet = nullptr;    // learned preconditioner (FE_FCG_LEARNED)
+  bool use_graphs = false;           // step as one CUDA graph with WHILE nodes for the solves
+  cudaGraphExec_t gexec[2] = {};     // per parity of the current state set
+  cudaStream_t cap[3] = {};          // capture streams (loop nesting levels)
+  int* dloop = nullptr;              // loop iteration counters
   bool unet_ready = false;
   void* const* harvest_b = nullptr;  // fe_harvest_pressure: per-corrector copies of b and x
   void* const* harvest_x = nullptr;
@@ -109,6 +113,8 @@ struct fe_ctx {
                   prm.transonic, prm.n_dust};
   }
 };
+
+static void drop_graphs(fe_ctx* c);
 
 #define CK(x)                                     \
   do {                                            \
@@ -211,6 +217,7 @@ static int set_tiling(fe_ctx* c, int tz) {
   c->nblocks = (int)work.size();
   c->neblocks = (int)ework.size();
   c->tz_override = tz;
+  drop_graphs(c);
   CK(cudaMemcpyAsync(c->dwork, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->dework, ework.data(), ework.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->dbox, c->hbox.data(), c->nb * sizeof(BoxDev), cudaMemcpyHostToDevice, c->st));
@@ -331,6 +338,10 @@ extern "C" void fe_destroy(fe_ctx* c) {
   else cudaDeviceSynchronize();
   for (void* s : c->slabs) cudaFree(s);
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  drop_graphs(c);
+  for (int q = 0; q < 3; ++q)
+    if (c->cap[q]) cudaStreamDestroy(c->cap[q]);
+  cudaFree(c->dloop);
   unet_destroy(c->unet);
   cudaFree(c->dbox);
   cudaFree(c->dwork);
@@ -511,12 +522,125 @@ __global__ void k_commit(double* sc, int nb) {
   s[SC_DTPREV] = s[SC_DT];
 }
 
-// One PISO step of every box.  commit = false runs a trial step (autotuning):
-// the new state is computed into the other state set but not adopted.
+// ---- CUDA-graph form of the pressure solves --------------------------------------------------
+// A Krylov loop becomes a conditional WHILE node whose body ends with a
+// one-thread kernel that keeps the loop alive while some box is still
+// iterating and an iteration counter is below its cap, so the graph always
+// terminates on its own.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* active, int* counter, int cap) {
+  const int n = ++(*counter);
+  cudaGraphSetConditional(h, (*active > 0 && n < cap) ? 1u : 0u);
+}
+
+__global__ void k_cond_set(cudaGraphConditionalHandle h, unsigned v) { cudaGraphSetConditional(h, v); }
+
+// Open a WHILE node at the capture point of `cs`; its body is captured on `bs`.
+// The condition is set to 1 right before the node (a handle's default value
+// applies only at graph launch, which would skip a nested loop's later passes).
+static int while_begin(cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, &deps, nullptr, &nd));
+  CK(cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
+  k_cond_set<<<1, 1, 0, cs>>>(*h, 1u);
+  CK(cudaGetLastError());
+  CK(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = *h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(bs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  return FE_OK;
+}
+
+static int while_end(cudaStream_t bs) {
+  cudaGraph_t body;
+  CK(cudaStreamEndCapture(bs, &body));
+  return FE_OK;
+}
+
+// Krylov solve of every box captured on stream level `lev` (loop body on lev + 1).
 template <typename T>
-static int step_once(fe_ctx* c, bool commit = true) {
+static int krylov_graph(fe_ctx* c, int lev) {
+  cudaStream_t cs = c->cap[lev], bs = c->cap[lev + 1];
   Launch L = c->L();
-  const int s = c->cur, ks = 1 - s, nc = c->prm.n_corr;
+  L.st = cs;
+  const int maxit = c->prm.p_maxit;
+  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), cs));
+  const bool bicg = c->prm.solver == FE_BICGSTAB_JACOBI;
+  const bool learned = c->prm.solver == FE_FCG_LEARNED;
+  BoxDev& B0 = c->hbox[0];
+  if (bicg) launch_bicg_init<T>(L);
+  else launch_cg_init<T>(L, 0.0);
+  if (learned) {  // first iteration with the network direction
+    unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_PSI], B0.sc, SC_BB, cs);
+    launch_fcg<T>(L, unet_output(c->unet));
+  }
+  CK(cudaMemsetAsync(c->dloop + lev, 0, sizeof(int), cs));
+  cudaGraphConditionalHandle h;
+  int rc = while_begin(cs, bs, &h);
+  if (rc != FE_OK) return rc;
+  Launch Lb = L;
+  Lb.st = bs;
+  if (bicg) {
+    launch_bicg_p<T>(Lb);
+    launch_bicg_v<T>(Lb);
+    launch_bicg_s<T>(Lb);
+    launch_bicg_x<T>(Lb);
+  } else if (learned) {
+    if (c->prm.learned_every == 1)
+      unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_PSI], B0.sc, SC_RR, bs);
+    launch_fcg<T>(Lb, c->prm.learned_every == 1 ? unet_output(c->unet) : nullptr);
+  } else {
+    launch_cg_matvec<T>(Lb);
+    launch_cg_update<T>(Lb);
+    launch_cg_dir<T>(Lb);
+  }
+  k_loop_cond<<<1, 1, 0, bs>>>(h, c->dactive, c->dloop + lev, maxit + 1);
+  return while_end(bs);
+}
+
+// Pressure solve captured on stream level 0 (mixed precision adds the
+// refinement loop as an outer WHILE node).
+template <typename T>
+static int pressure_graph(fe_ctx* c) {
+  if (c->fp64) return krylov_graph<T>(c, 0);
+  cudaStream_t cs = c->cap[0], bs = c->cap[1];
+  Launch L = c->L();
+  L.st = cs;
+  CK(cudaMemsetAsync(c->douter, 0, sizeof(int), cs));
+  launch_mix_residual<T>(L, 1, c->douter);
+  CK(cudaMemsetAsync(c->dloop + 3, 0, sizeof(int), cs));
+  cudaGraphConditionalHandle h;
+  int rc = while_begin(cs, bs, &h);
+  if (rc != FE_OK) return rc;
+  rc = krylov_graph<T>(c, 1);
+  if (rc != FE_OK) return rc;
+  Launch Lb = L;
+  Lb.st = bs;
+  launch_mix_accum<T>(Lb);
+  launch_mix_residual<T>(Lb, 0, c->douter);
+  k_loop_cond<<<1, 1, 0, bs>>>(h, c->douter, c->dloop + 3, 8);
+  rc = while_end(bs);
+  if (rc != FE_OK) return rc;
+  launch_mix_finish<T>(L);
+  return FE_OK;
+}
+
+// The kernel sequence of one PISO step (state set s -> 1 - s).  graph = true:
+// issued into the capture on stream level 0 with the solves as WHILE nodes.
+template <typename T>
+static int issue_step(fe_ctx* c, int s, bool graph) {
+  Launch L = c->L();
+  if (graph) L.st = c->cap[0];
+  const int ks = 1 - s, nc = c->prm.n_corr;
   launch_dt<T>(L, s, 0);
   launch_div<T>(L, S(s, F_U0));
   launch_pred<T>(L, s, ks);
@@ -530,9 +654,9 @@ static int step_once(fe_ctx* c, bool commit = true) {
     if (kk == 0) launch_div<T>(L, up0);
     launch_asm<T>(L, s, up0, php0, rhop);
     launch_rhs<T>(L, s, rhop, pp);
-    int rc = pressure_solve<T>(c);
+    int rc = graph ? pressure_graph<T>(c) : pressure_solve<T>(c);
     if (rc != FE_OK) return rc;
-    if (c->harvest_b && c->harvest_n < c->harvest_max) {
+    if (!graph && c->harvest_b && c->harvest_n < c->harvest_max) {
       const size_t bytes = (size_t)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N * sizeof(T);
       CK(cudaMemcpyAsync(c->harvest_b[c->harvest_n], c->hbox[0].f[c->fp64 ? K_B : K_AUX], bytes,
                          cudaMemcpyDeviceToDevice, c->st));
@@ -550,6 +674,57 @@ static int step_once(fe_ctx* c, bool commit = true) {
     launch_dust<T>(L, s, ks, pn, yp0, yn0, ep, en, last ? 1 : 0, kk == 0 ? 1 : 0);
   }
   CK(cudaGetLastError());
+  return FE_OK;
+}
+
+static void drop_graphs(fe_ctx* c) {
+  for (int q = 0; q < 2; ++q)
+    if (c->gexec[q]) {
+      cudaGraphExecDestroy(c->gexec[q]);
+      c->gexec[q] = nullptr;
+    }
+}
+
+template <typename T>
+static int build_graph(fe_ctx* c, int s) {
+  for (int q = 0; q < 3; ++q)
+    if (!c->cap[q]) CK(cudaStreamCreateWithFlags(&c->cap[q], cudaStreamNonBlocking));
+  if (!c->dloop) CK(cudaMalloc(&c->dloop, 8 * sizeof(int)));
+  CK(cudaStreamBeginCapture(c->cap[0], cudaStreamCaptureModeRelaxed));
+  int rc = issue_step<T>(c, s, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap[0], &g);
+  if (rc != FE_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != FE_OK ? rc : FE_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&c->gexec[s], g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
+
+static bool graph_ok(const fe_ctx* c) {
+  if (!c->use_graphs || c->harvest_b || c->prof.on) return false;
+  if (c->prm.solver == FE_FCG_LEARNED && (!c->unet_ready || c->prm.learned_every > 1)) return false;
+  return true;
+}
+
+// One PISO step of every box.  commit = false runs a trial step (autotuning):
+// the new state is computed into the other state set but not adopted.
+template <typename T>
+static int step_once(fe_ctx* c, bool commit = true) {
+  const int s = c->cur, ks = 1 - s, nc = c->prm.n_corr;
+  if (graph_ok(c)) {
+    if (!c->gexec[s]) {
+      int rc = build_graph<T>(c, s);
+      if (rc != FE_OK) return rc;
+    }
+    CK(cudaGraphLaunch(c->gexec[s], c->st));
+  } else {
+    int rc = issue_step<T>(c, s, false);
+    if (rc != FE_OK) return rc;
+  }
   if (!commit) return FE_OK;
   int rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
@@ -871,6 +1046,7 @@ extern "C" int fe_load_preconditioner(fe_ctx* c, const float* w, size_t count) {
   }
   int rc = unet_set_weights(c->unet, w, c->st);
   c->unet_ready = rc == FE_OK;
+  drop_graphs(c);
   return rc;
 }
 
@@ -930,4 +1106,11 @@ extern "C" int fe_precond_activation(fe_ctx* c, int layer, float* out, size_t co
   if (!c || !out) return FE_ERR_INVALID_ARG;
   if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
   return unet_activation(c->unet, layer, out, (long)count, c->st);
+}
+
+extern "C" int fe_use_graphs(fe_ctx* c, int on) {
+  if (!c) return FE_ERR_INVALID_ARG;
+  c->use_graphs = on != 0;
+  if (!c->use_graphs) drop_graphs(c);
+  return FE_OK;
 }
