@@ -36,7 +36,8 @@ UNIT = "cell-steps/s"
 def alg_words(kernel, nd):
     table = {
         "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 11,
-        "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4, "corr": 21, "accel": 9,
+        "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4,
+        "cg_dirmatvec": 8, "cg_rupdate": 4, "cg_xfinal": 3, "corr": 21, "accel": 9,
         "dust": 8 + 4 * nd + 2,  # last corrector adds u reads and p write; averaged over 2 correctors
         "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
         # refinement (field word = 4 bytes; x64 counts as two words)
@@ -241,8 +242,9 @@ def main():
     assert code == fe.FE_OK, fe.fe_strerror(code)
 
     # untimed pass: per-kernel device time over one step, one kernel id at a time
-    names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir", "corr",
-             "accel", "dust", "mix_residual", "mix_accum", "mix_finish", "commit"]
+    names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir",
+             "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "corr", "accel", "dust", "mix_residual", "mix_accum",
+             "mix_finish", "commit"]
     share = {}
     for k in ([] if args.no_breakdown else names):
         s.profile_start(k)
@@ -357,7 +359,7 @@ def main():
                              "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
                              "alg_bytes_per_launch": alg_bytes, "launches": prof["target_launches"],
                              "ms_per_launch": per_launch_ms},
-                "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items()},
+                "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items() if v[1] > 0},
                 "paths": extra,
                 "gpu_launches": prof["launches"],
                 "gpu_launches_note": "kernel launches of %d host-driven steps (the graph steps run the same kernels "

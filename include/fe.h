@@ -273,7 +273,7 @@ int fe_autotune(fe_ctx* ctx, int trials, int* best_tz);
  * launches since the start (total and per kernel id) and the summed device
  * time of the bracketed launches.  Kernel ids run 0 .. fe_kernel_count()-1,
  * fe_kernel_name() gives their names. */
-#define FE_PROFILE_MAX_KERNELS 32
+#define FE_PROFILE_MAX_KERNELS 64
 typedef struct {
     int64_t launches;                          /* all kernels of this context */
     int64_t target_launches;                   /* launches of kernel_id       */

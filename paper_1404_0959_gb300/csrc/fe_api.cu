@@ -69,8 +69,10 @@ static const char* kKernelNames[] = {
     "dt",      "div",       "pred",      "fluxn",  "asm",      "rhs",       "corr",    "accel",
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
-    "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec", "unet", "other"};
+    "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec",
+    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "unet", "other"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
+static_assert(KID_COUNT <= FE_PROFILE_MAX_KERNELS, "profile counters");
 
 struct fe_ctx {
   fe_params prm;
@@ -149,6 +151,8 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   }
   if (c->prm.solver == FE_BICGSTAB_JACOBI)
     for (int s : {K_RHAT, K_V, K_S, K_T}) plan.push_back({s, e});
+  // second CG direction buffer (the learned solver's harvest runs plain CG)
+  if (c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_PP, e});
   if (!c->fp64) plan.push_back({K_X64, 8});
 }
 
@@ -416,6 +420,7 @@ static int krylov(fe_ctx* c, int maxit, int key) {
   int batch = c->hint[key] > 1 ? c->hint[key] - 1 : 1;
   // harvesting: snapshots (r_k, x_k) of box 0 after iterations 2 and 5 of the first solve
   const bool snap = c->harvest_b && key <= 1;
+  const bool fused = !bicg && !snap && c->hbox[0].f[K_PP] != nullptr;
   const int snap_at[2] = {2, 5};
   int nsnap = 0, snap_slot[2] = {-1, -1};
   if (snap) batch = 1;
@@ -438,6 +443,8 @@ static int krylov(fe_ctx* c, int maxit, int key) {
         launch_bicg_v<T>(L);
         launch_bicg_s<T>(L);
         launch_bicg_x<T>(L);
+      } else if (fused) {
+        launch_cg_fused<T>(L);
       } else {
         launch_cg_matvec<T>(L);
         launch_cg_update<T>(L);
@@ -445,6 +452,7 @@ static int krylov(fe_ctx* c, int maxit, int key) {
       }
     }
   }
+  if (fused) launch_cg_xfinal<T>(L);
   c->hint[key] = it;
   // snapshot targets: e_k = x* - x_k
   for (int q = 0; q < nsnap; ++q) {
@@ -599,12 +607,12 @@ static int krylov_graph(fe_ctx* c, int lev) {
       unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_PSI], B0.sc, SC_RR, bs);
     launch_fcg<T>(Lb, c->prm.learned_every == 1 ? unet_output(c->unet) : nullptr);
   } else {
-    launch_cg_matvec<T>(Lb);
-    launch_cg_update<T>(Lb);
-    launch_cg_dir<T>(Lb);
+    launch_cg_fused<T>(Lb);
   }
   k_loop_cond<<<1, 1, 0, bs>>>(h, c->dactive, c->dloop + lev, maxit + 1);
-  return while_end(bs);
+  rc = while_end(bs);
+  if (rc == FE_OK && !bicg && !learned) launch_cg_xfinal<T>(L);
+  return rc;
 }
 
 // Pressure solve captured on stream level 0 (mixed precision adds the

@@ -373,7 +373,7 @@ enum KernelId {
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
   KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
-  KID_UNET, KID_OTHER, KID_COUNT
+  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_UNET, KID_OTHER, KID_COUNT
 };
 
 struct Prof;  // defined in fe_api.cu
@@ -420,6 +420,8 @@ template <typename T> void launch_derive_box(const Launch& L, int s, int box);
 template <typename V> void launch_cg_init(const Launch& L, double dt_override);
 template <typename V> void launch_cg_matvec(const Launch& L);
 template <typename V> void launch_cg_update(const Launch& L);
+template <typename V> void launch_cg_fused(const Launch& L);   // symmetric operator: dir + matvec, then update
+template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
 template <typename V> void launch_cg_dir(const Launch& L);
 template <typename V> void launch_true_res(const Launch& L, int xslot);
 template <typename V> void launch_bicg_init(const Launch& L);

@@ -10,7 +10,7 @@
 // (per-thread, then a fixed-order warp/block tree, then the box's last block
 // adds the block partials in order).  A box whose solve has finished skips
 // every later launch, so one launch serves all boxes of an ensemble.
-#include "fe_internal.cuh"
+#include "zmarch.cuh"
 
 namespace fe {
 
@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int
       B.sc[SC_RZ] = res[0];
       B.sc[SC_BB] = res[1];
       B.sc[SC_ITERS] = 0.0;
+      B.sc[SC_ALPHA] = 0.0;
+      B.sc[SC_BETA] = 0.0;
       bool zero = !(res[1] > 0.0);
       B.sc[SC_DONE] = zero ? 1.0 : 0.0;
       B.sc[SC_CONV] = zero ? 1.0 : 0.0;
@@ -225,8 +227,177 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
   }
 }
 
-// x += alpha pd; r -= alpha q; z = r / diag; convergence test on ||r||.
+// Planes requested ahead by the z-marching Krylov kernels.
+constexpr int KPF = 2;
+
+// q = M pd; alpha = rz / <pd, q> (symmetric operator): z-marching form, pd
+// staged per plane in shared memory with a 1-cell halo, z-neighbours in
+// registers, loads issued KPF planes ahead.
 template <typename T>
+__global__ void __launch_bounds__(NTHR) kz_cg_matvec(const BoxDev* boxes, const int2* work, double* part) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (box_done(B)) return;
+  const ZGeom<1> G(t.x0, t.y0, B.N);
+  __shared__ T sm[ZGeom<1>::H * ZGeom<1>::W];
+  ZField<T, 1, KPF> p;
+  p.init(F<T>(B, K_PD), sm, G, t.k0);
+  ZStream<T, KPF> psi;
+  psi.init(F<T>(B, W_PSI), G, t.k0);
+  T* __restrict__ q = F<T>(B, K_Q);
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  DotAcc<T> a0;
+  for (int k = t.k0; k < t.kend; ++k) {
+    p.advance(G, k);
+    const T ps = psi.next(G, k);
+    __syncthreads();
+    p.stage(G, k);
+    __syncthreads();
+    if (!G.active) continue;
+    const T vc = p.c();
+    const T nb = (p.at(G, 0, -1) + p.at(G, 0, 1)) + (p.at(G, 1, -1) + p.at(G, 1, 1)) + (p.at(G, 2, -1) + p.at(G, 2, 1));
+    const T y = ps * vc * idt - lapc * (nb - T(6) * vc);
+    q[G.col + G.plane(k)] = y;
+    a0.add(vc, y);
+  }
+  double v[1] = {a0.value()};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_PQ] = res[0];
+      B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
+    }
+  }
+}
+
+// One CG iteration's direction and operator in one pass (symmetric operator):
+//   pd_new = D^{-1} r + beta pd_old,  x += alpha pd_old,  q = M pd_new,
+//   alpha = rz / <pd_new, q>.
+// x therefore lags one direction behind; k_cg_xfinal adds the last one.
+// pd_old and pd_new alternate between slots K_PD and K_PP with the parity of
+// the iteration counter (neighbouring tiles still read pd_old as halo).  At
+// iteration 0 alpha = beta = 0 (set by k_cg_init) and pd_new = D^{-1} b.
+template <typename T>
+__global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? 4 : 2) kz_cg_dirmatvec(const BoxDev* boxes, const int2* work, double* part) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (box_done(B)) return;
+  const ZGeom<1> G(t.x0, t.y0, B.N);
+  __shared__ T sm[ZGeom<1>::H * ZGeom<1>::W];
+  const int odd = ((int)B.sc[SC_ITERS]) & 1;
+  const T* __restrict__ po = F<T>(B, odd ? K_PP : K_PD);
+  T* __restrict__ pn = F<T>(B, odd ? K_PD : K_PP);
+  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ x = F<T>(B, K_X);
+  T* __restrict__ q = F<T>(B, K_Q);
+  const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  auto dir = [&](T rv, T dv, T pv) { return rv * dv + beta * pv; };
+  auto ld = [&](const T* f, int col, int k) { return __ldg(&f[col + G.plane(G.wrapz(k))]); };
+  // centre column: r, dinv, pd_old for planes k + 1 .. k + KPF in flight
+  T cr[KPF], cd[KPF], cp[KPF];
+  // halo cell: r, dinv, pd_old for planes k .. k + KPF - 1
+  T hr[KPF], hd[KPF], hp[KPF];
+  ZStream<T, KPF> psi, xs;
+  psi.init(F<T>(B, W_PSI), G, t.k0);
+  xs.init(x, G, t.k0);
+#pragma unroll
+  for (int j = 0; j < KPF; ++j) {
+    cr[j] = ld(r, G.col, t.k0 + 1 + j);
+    cd[j] = ld(dinv, G.col, t.k0 + 1 + j);
+    cp[j] = ld(po, G.col, t.k0 + 1 + j);
+    if (G.hcol >= 0) {
+      hr[j] = ld(r, G.hcol, t.k0 + j);
+      hd[j] = ld(dinv, G.hcol, t.k0 + j);
+      hp[j] = ld(po, G.hcol, t.k0 + j);
+    }
+  }
+  // z-queue of pd_new at k - 1, k; pd_old at k (for the x update)
+  T zm = dir(ld(r, G.col, t.k0 - 1), ld(dinv, G.col, t.k0 - 1), ld(po, G.col, t.k0 - 1));
+  T oc = ld(po, G.col, t.k0);
+  T zc = dir(ld(r, G.col, t.k0), ld(dinv, G.col, t.k0), oc);
+  DotAcc<T> a0;
+  for (int k = t.k0; k < t.kend; ++k) {
+    const T op = cp[0];
+    const T zp = dir(cr[0], cd[0], cp[0]);
+#pragma unroll
+    for (int j = 0; j + 1 < KPF; ++j) {
+      cr[j] = cr[j + 1];
+      cd[j] = cd[j + 1];
+      cp[j] = cp[j + 1];
+    }
+    cr[KPF - 1] = ld(r, G.col, k + 1 + KPF);
+    cd[KPF - 1] = ld(dinv, G.col, k + 1 + KPF);
+    cp[KPF - 1] = ld(po, G.col, k + 1 + KPF);
+    const T ps = psi.next(G, k);
+    const T xv = xs.next(G, k);
+    __syncthreads();
+    sm[G.csm] = zc;
+    if (G.hcol >= 0) {
+      sm[G.hsm] = dir(hr[0], hd[0], hp[0]);
+#pragma unroll
+      for (int j = 0; j + 1 < KPF; ++j) {
+        hr[j] = hr[j + 1];
+        hd[j] = hd[j + 1];
+        hp[j] = hp[j + 1];
+      }
+      hr[KPF - 1] = ld(r, G.hcol, k + KPF);
+      hd[KPF - 1] = ld(dinv, G.hcol, k + KPF);
+      hp[KPF - 1] = ld(po, G.hcol, k + KPF);
+    }
+    __syncthreads();
+    if (G.active) {
+      const int c = G.col + G.plane(k);
+      const T* s = sm + G.csm;
+      const T nb = (s[-1] + s[1]) + (s[-ZGeom<1>::W] + s[ZGeom<1>::W]) + (zm + zp);
+      const T y = ps * zc * idt - lapc * (nb - T(6) * zc);
+      q[c] = y;
+      pn[c] = zc;
+      x[c] = xv + alpha * oc;
+      a0.add(zc, y);
+    }
+    zm = zc;
+    zc = zp;
+    oc = op;
+  }
+  double v[1] = {a0.value()};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_PQ] = res[0];
+      B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
+    }
+  }
+}
+
+// x += alpha pd for the direction of the last iteration (after kz_cg_dirmatvec).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_cg_xfinal(const BoxDev* boxes, const int2* work) {
+  const Chunk ch = chunk_of(boxes, work);
+  const BoxDev& B = boxes[ch.box];
+  const int it = (int)B.sc[SC_ITERS];
+  if (it == 0) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ pd = F<T>(B, (it & 1) ? K_PP : K_PD);
+  T* __restrict__ x = F<T>(B, K_X);
+  const T alpha = (T)B.sc[SC_ALPHA];
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        V4<T> xv = ld4(x + q0), pv = ld4(pd + q0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xv.v[e] += alpha * pv.v[e];
+        st4(x + q0, xv);
+      },
+      [&](int c) { x[c] = x[c] + alpha * pd[c]; });
+}
+
+// x += alpha pd (XU; otherwise x is updated by kz_cg_dirmatvec); r -= alpha q;
+// rz = <r, D^{-1} r>; convergence test on ||r||.
+template <typename T, bool XU>
 __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const int2* work, double* part, int* active) {
   const Chunk ch = chunk_of(boxes, work);
   const BoxDev& B = boxes[ch.box];
@@ -242,19 +413,23 @@ __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const i
   chunk_loop(
       ch, tid,
       [&](int q0) {
-        V4<T> xv = ld4(x + q0), pv = ld4(pd + q0), rv = ld4(r + q0), qq = ld4(qv + q0), dv = ld4(dinv + q0);
+        V4<T> rv = ld4(r + q0), qq = ld4(qv + q0), dv = ld4(dinv + q0);
+        if (XU) {
+          V4<T> xv = ld4(x + q0), pv = ld4(pd + q0);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) xv.v[e] += alpha * pv.v[e];
+          st4(x + q0, xv);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          xv.v[e] += alpha * pv.v[e];
           rv.v[e] -= alpha * qq.v[e];
           a0.add(rv.v[e], rv.v[e] * dv.v[e]);
           a1.add(rv.v[e], rv.v[e]);
         }
-        st4(x + q0, xv);
         st4(r + q0, rv);
       },
       [&](int c) {
-        x[c] = x[c] + alpha * pd[c];
+        if (XU) x[c] = x[c] + alpha * pd[c];
         T rc = r[c] - alpha * qv[c];
         r[c] = rc;
         a0.add(rc, rc * dinv[c]);
@@ -543,6 +718,81 @@ __device__ __forceinline__ DF residual_df(const BoxDev& B, const float2* __restr
   return df_add(DF{(float)bc, 0.f}, df_neg(mx));
 }
 
+// Box bookkeeping after a refinement residual: convergence, counters, the FP64
+// residual report and the next inner tolerance.
+__device__ void mix_finish_scalars(const BoxDev& B, double rr, int first, int* outer_active) {
+  double* sc = B.sc;
+  if (first) {
+    sc[SC_OBB] = rr;
+    sc[SC_ITSUM] = 0.0;
+    sc[SC_OUTER] = 0.0;
+    bool zero = !(rr > 0.0);
+    sc[SC_ODONE] = zero ? 1.0 : 0.0;
+    sc[SC_CONV] = zero ? 1.0 : 0.0;
+    if (!zero) atomicAdd(outer_active, 1);
+  } else if (sc[SC_ODONE] == 0.0) {
+    sc[SC_ITSUM] += sc[SC_ITERS];
+    sc[SC_OUTER] += 1.0;
+    if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
+      sc[SC_ODONE] = 1.0;
+      sc[SC_CONV] = 1.0;
+      atomicSub(outer_active, 1);
+    } else if (sc[SC_OUTER] >= 8.0) {
+      sc[SC_ODONE] = 1.0;
+      sc[SC_CONV] = 0.0;
+      atomicSub(outer_active, 1);
+    }
+  }
+  sc[SC_ORR] = rr;
+  sc[SC_ORES] = sc[SC_OBB] > 0.0 ? sqrt(rr / sc[SC_OBB]) : 0.0;
+  // inner tolerance: reach the outer target with a factor 2 margin, within FP32 reach
+  double need = rr > 0.0 ? 0.5 * sc[SC_OTOL] * sqrt(sc[SC_OBB] / rr) : 0.5;
+  sc[SC_TOL] = fmin(0.5, fmax(need, 1e-6));
+}
+
+// Refinement residual r = b - M x (x as double-float pairs) for the symmetric
+// operator, z-marching form (pairs staged with a 1-cell halo).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kz_mix_residual(const BoxDev* boxes, const int2* work, double* part,
+                                                        int* outer_active) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  const ZGeom<1> G(t.x0, t.y0, B.N);
+  __shared__ float2 sm[ZGeom<1>::H * ZGeom<1>::W];
+  ZField<float2, 1, KPF> xs;
+  xs.init(F<float2>(B, K_X64), sm, G, t.k0);
+  ZStream<T, KPF> borig, psi;
+  borig.init(F<T>(B, K_AUX), G, t.k0);
+  psi.init(F<T>(B, W_PSI), G, t.k0);
+  T* __restrict__ b = F<T>(B, K_B);
+  const double dt = B.sc[SC_KDT];
+  const DF idt = df_from_double(1.0 / dt), kl = df_from_double(0.5 * dt * B.ih * B.ih),
+           k6 = df_from_double(3.0 * dt * B.ih * B.ih);
+  DotAcc<float> acc;
+  auto X = [&](const float2 v) { return DF{v.x, v.y}; };
+  for (int k = t.k0; k < t.kend; ++k) {
+    xs.advance(G, k);
+    const T bc = borig.next(G, k), pc = psi.next(G, k);
+    __syncthreads();
+    xs.stage(G, k);
+    __syncthreads();
+    if (!G.active) continue;
+    DF nb = df_add(X(xs.at(G, 0, 1)), X(xs.at(G, 0, -1)));
+    nb = df_add(nb, df_add(X(xs.at(G, 1, 1)), X(xs.at(G, 1, -1))));
+    nb = df_add(nb, df_add(X(xs.at(G, 2, 1)), X(xs.at(G, 2, -1))));
+    const DF a = df_add(df_mul(idt, DF{(float)pc, 0.f}), k6);
+    const DF mx = df_add(df_mul(a, X(xs.c())), df_neg(df_mul(kl, nb)));
+    const DF r = df_add(DF{(float)bc, 0.f}, df_neg(mx));
+    b[G.col + G.plane(k)] = (T)r.hi;
+    acc.add(r.hi, r.hi);
+  }
+  double v[1] = {acc.value()};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) mix_finish_scalars(B, res[0], 0, outer_active);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_mix_residual(const BoxDev* boxes, const int2* work, double* part, int first,
                                                        int* outer_active) {
@@ -581,36 +831,7 @@ __global__ void __launch_bounds__(NTHR) k_mix_residual(const BoxDev* boxes, cons
   double v[1] = {acc.value() + acc64};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double* sc = B.sc;
-      const double rr = res[0];
-      if (first) {
-        sc[SC_OBB] = rr;
-        sc[SC_ITSUM] = 0.0;
-        sc[SC_OUTER] = 0.0;
-        bool zero = !(rr > 0.0);
-        sc[SC_ODONE] = zero ? 1.0 : 0.0;
-        sc[SC_CONV] = zero ? 1.0 : 0.0;
-        if (!zero) atomicAdd(outer_active, 1);
-      } else if (sc[SC_ODONE] == 0.0) {
-        sc[SC_ITSUM] += sc[SC_ITERS];
-        sc[SC_OUTER] += 1.0;
-        if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
-          sc[SC_ODONE] = 1.0;
-          sc[SC_CONV] = 1.0;
-          atomicSub(outer_active, 1);
-        } else if (sc[SC_OUTER] >= 8.0) {
-          sc[SC_ODONE] = 1.0;
-          sc[SC_CONV] = 0.0;
-          atomicSub(outer_active, 1);
-        }
-      }
-      sc[SC_ORR] = rr;
-      sc[SC_ORES] = sc[SC_OBB] > 0.0 ? sqrt(rr / sc[SC_OBB]) : 0.0;
-      // inner tolerance: reach the outer target with a factor 2 margin, within FP32 reach
-      double need = rr > 0.0 ? 0.5 * sc[SC_OTOL] * sqrt(sc[SC_OBB] / rr) : 0.5;
-      sc[SC_TOL] = fmin(0.5, fmax(need, 1e-6));
-    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) mix_finish_scalars(B, res[0], first, outer_active);
   }
 }
 
@@ -733,10 +954,18 @@ template <typename T> void launch_cg_init(const Launch& L, double) {
   FE_LAUNCH(L, KID_CG_INIT, (k_cg_init<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_matvec(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_MATVEC, (k_cg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+  if (L.transonic) FE_LAUNCH(L, KID_CG_MATVEC, (k_cg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+  else FE_LAUNCH(L, KID_CG_MATVEC, (kz_cg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
 }
 template <typename T> void launch_cg_update(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T, true><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+}
+template <typename T> void launch_cg_fused(const Launch& L) {
+  FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+  FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_update<T, false><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+}
+template <typename T> void launch_cg_xfinal(const Launch& L) {
+  FE_LAUNCH(L, KID_CG_XFINAL, (k_cg_xfinal<T><<<EGRID>>>(L.boxes, L.ework)));
 }
 template <typename T> void launch_cg_dir(const Launch& L) {
   FE_LAUNCH(L, KID_CG_DIR, (k_cg_dir<T><<<EGRID>>>(L.boxes, L.ework)));
@@ -764,10 +993,13 @@ template <typename T> void launch_fcg(const Launch& L, const float* z) {
   FE_LAUNCH(L, KID_FCG_DOTS, (k_fcg_dots<T><<<EGRID>>>(L.boxes, L.ework, L.part, z)));
   FE_LAUNCH(L, KID_FCG_DIR, (k_fcg_dir<T><<<EGRID>>>(L.boxes, L.ework, z)));
   FE_LAUNCH(L, KID_FCG_MATVEC, (k_fcg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
-  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T, true><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_mix_residual(const Launch& L, int first, int* outer_active) {
-  FE_LAUNCH(L, KID_MIX_RES, (k_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, first, outer_active)));
+  if (first || L.transonic)
+    FE_LAUNCH(L, KID_MIX_RES, (k_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, first, outer_active)));
+  else
+    FE_LAUNCH(L, KID_MIX_RES, (kz_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active)));
 }
 template <typename T> void launch_mix_accum(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_ACC, (k_mix_accum<T><<<EGRID>>>(L.boxes, L.ework)));
@@ -780,6 +1012,8 @@ template <typename T> void launch_mix_finish(const Launch& L) {
   template void launch_cg_init<T>(const Launch&, double);        \
   template void launch_cg_matvec<T>(const Launch&);              \
   template void launch_cg_update<T>(const Launch&);              \
+  template void launch_cg_fused<T>(const Launch&);               \
+  template void launch_cg_xfinal<T>(const Launch&);              \
   template void launch_cg_dir<T>(const Launch&);                 \
   template void launch_true_res<T>(const Launch&, int);          \
   template void launch_bicg_init<T>(const Launch&);              \

@@ -13,22 +13,6 @@ __device__ __forceinline__ T* Fz(const BoxDev& B, int slot) {
   return reinterpret_cast<T*>(B.f[slot]);
 }
 
-struct TileXYZ {
-  int box, x0, y0, k0, kend;
-};
-__device__ __forceinline__ TileXYZ tile_xyz(const BoxDev* boxes, const int2* work) {
-  const int2 w = work[blockIdx.x];
-  const BoxDev& B = boxes[w.x];
-  TileXYZ t;
-  t.box = w.x;
-  const int tx = w.y % B.tnx, r = w.y / B.tnx, ty = r % B.tny, tzb = r / B.tny;
-  t.x0 = tx * TX;
-  t.y0 = ty * TY;
-  t.k0 = tzb * B.tz;
-  t.kend = min(t.k0 + B.tz, B.N);
-  return t;
-}
-
 // Face values of a face array at this cell's +1/2 face and at its -1/2 face
 // (the neighbour's +1/2 face) along x, y, z; the z one is carried over planes.
 template <typename T>
@@ -259,20 +243,20 @@ struct ZSum2 {
     g2 = b2;
 #pragma unroll
     for (int s = -2; s < 2; ++s) f.q[2 + s + 1] = ld(G.col + G.plane(G.wrapz(k0 + s)));
-    f.nq = ld(G.col + G.plane(G.wrapz(k0 + 2)));
-    f.nh = G.hcol >= 0 ? ld(G.hcol + G.plane(k0)) : T(0);
+    f.nq[0] = ld(G.col + G.plane(G.wrapz(k0 + 2)));
+    f.nh[0] = G.hcol >= 0 ? ld(G.hcol + G.plane(k0)) : T(0);
   }
   __device__ __forceinline__ void advance(const ZGeom<2>& G, int k) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) f.q[s] = f.q[s + 1];
-    f.q[4] = f.nq;
-    f.nq = ld(G.col + G.plane(G.wrapz(k + 3)));
+    f.q[4] = f.nq[0];
+    f.nq[0] = ld(G.col + G.plane(G.wrapz(k + 3)));
   }
   __device__ __forceinline__ void stage(const ZGeom<2>& G, int k) {
     f.sm[G.csm] = f.q[2];
     if (G.hcol >= 0) {
-      f.sm[G.hsm] = f.nh;
-      f.nh = ld(G.hcol + G.plane(G.wrapz(k + 1)));
+      f.sm[G.hsm] = f.nh[0];
+      f.nh[0] = ld(G.hcol + G.plane(G.wrapz(k + 1)));
     }
   }
 };

@@ -55,37 +55,44 @@ struct ZGeom {
   __device__ __forceinline__ int wrapz(int k) const { return k < 0 ? k + N : (k >= N ? k - N : k); }
 };
 
-// One field read with a radius-R star stencil.  Loads run one plane ahead:
-// the z-queue value and the halo value needed at plane k + 1 are requested
-// while plane k is computed.
-template <typename T, int R>
+// One field read with a radius-R star stencil.  Loads run PF planes ahead:
+// the z-queue values and the halo values needed at planes k + 1 .. k + PF are
+// in flight while plane k is computed.
+template <typename T, int R, int PF = 1>
 struct ZField {
   const T* __restrict__ g;
   T q[2 * R + 1];  // q[R + s] = value at z-offset s of the current plane
-  T nq;            // next queue entry (plane k + R + 1)
-  T nh;            // next halo value (plane k + 1)
+  T nq[PF];        // pending queue entries (planes k + R + 1 .. k + R + PF)
+  T nh[PF];        // pending halo values (planes k + 1 .. k + PF)
   T* sm;           // shared plane (H x W)
   __device__ __forceinline__ void init(const T* gp, T* smem, const ZGeom<R>& G, int k0) {
     g = gp;
     sm = smem;
 #pragma unroll
     for (int s = -R; s < R; ++s) q[R + s + 1] = __ldg(&g[G.col + G.plane(G.wrapz(k0 + s))]);
-    nq = __ldg(&g[G.col + G.plane(G.wrapz(k0 + R))]);
-    nh = G.hcol >= 0 ? __ldg(&g[G.hcol + G.plane(k0)]) : T(0);
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      nq[j] = __ldg(&g[G.col + G.plane(G.wrapz(k0 + R + j))]);
+      nh[j] = G.hcol >= 0 ? __ldg(&g[G.hcol + G.plane(G.wrapz(k0 + j))]) : T{};
+    }
   }
-  // move to plane k: shift the queue in, request plane k + R + 1
+  // move to plane k: shift the queue in, request plane k + R + PF
   __device__ __forceinline__ void advance(const ZGeom<R>& G, int k) {
 #pragma unroll
     for (int s = 0; s < 2 * R; ++s) q[s] = q[s + 1];
-    q[2 * R] = nq;
-    nq = __ldg(&g[G.col + G.plane(G.wrapz(k + R + 1))]);
+    q[2 * R] = nq[0];
+#pragma unroll
+    for (int j = 0; j + 1 < PF; ++j) nq[j] = nq[j + 1];
+    nq[PF - 1] = __ldg(&g[G.col + G.plane(G.wrapz(k + R + PF))]);
   }
-  // stage the current plane (call between two __syncthreads), request the next halo
+  // stage the current plane (call between two __syncthreads), request halo plane k + PF
   __device__ __forceinline__ void stage(const ZGeom<R>& G, int k) {
     sm[G.csm] = q[R];
     if (G.hcol >= 0) {
-      sm[G.hsm] = nh;
-      nh = __ldg(&g[G.hcol + G.plane(G.wrapz(k + 1))]);
+      sm[G.hsm] = nh[0];
+#pragma unroll
+      for (int j = 0; j + 1 < PF; ++j) nh[j] = nh[j + 1];
+      nh[PF - 1] = __ldg(&g[G.hcol + G.plane(G.wrapz(k + PF))]);
     }
   }
   // value at offset s along axis d from this thread's cell
@@ -95,6 +102,45 @@ struct ZField {
   }
   __device__ __forceinline__ T c() const { return q[R]; }
 };
+
+// A field read at this thread's own cell only, PF planes ahead.
+template <typename T, int PF>
+struct ZStream {
+  const T* __restrict__ g;
+  T v[PF];  // planes k .. k + PF - 1
+  template <int R>
+  __device__ __forceinline__ void init(const T* gp, const ZGeom<R>& G, int k0) {
+    g = gp;
+#pragma unroll
+    for (int j = 0; j < PF; ++j) v[j] = __ldg(&g[G.col + G.plane(G.wrapz(k0 + j))]);
+  }
+  // value at plane k; requests plane k + PF
+  template <int R>
+  __device__ __forceinline__ T next(const ZGeom<R>& G, int k) {
+    const T out = v[0];
+#pragma unroll
+    for (int j = 0; j + 1 < PF; ++j) v[j] = v[j + 1];
+    v[PF - 1] = __ldg(&g[G.col + G.plane(G.wrapz(k + PF))]);
+    return out;
+  }
+};
+
+// Tile origin of this block's (box, tile) work item.
+struct TileXYZ {
+  int box, x0, y0, k0, kend;
+};
+__device__ __forceinline__ TileXYZ tile_xyz(const BoxDev* boxes, const int2* work) {
+  const int2 w = work[blockIdx.x];
+  const BoxDev& B = boxes[w.x];
+  TileXYZ t;
+  t.box = w.x;
+  const int tx = w.y % B.tnx, r = w.y / B.tnx, ty = r % B.tny, tzb = r / B.tny;
+  t.x0 = tx * TX;
+  t.y0 = ty * TY;
+  t.k0 = tzb * B.tz;
+  t.kend = min(t.k0 + B.tz, B.N);
+  return t;
+}
 
 // ---- star stencils on a ZField (same arithmetic as the global-memory helpers) ----
 template <typename T, int R>

@@ -24,6 +24,7 @@ FE_ERR_OOM = -5
 FE_ERR_UNSUPPORTED = -6
 FE_ERR_TOO_LARGE = -7
 FE_NOALLOC_MAX_N = 64
+FE_PROFILE_MAX_KERNELS = 64
 
 FE_FP64 = 0
 FE_FP32_MIXED = 1
@@ -64,7 +65,7 @@ class fe_diag(ctypes.Structure):
 
 class fe_profile_info(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("target_launches", ctypes.c_int64), ("target_ms", c_double),
-                ("counts", ctypes.c_int64 * 32)]
+                ("counts", ctypes.c_int64 * FE_PROFILE_MAX_KERNELS)]
 
 
 EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_clock", "fe_step",
@@ -433,7 +434,7 @@ class Solver:
 
     def profile_stop(self):
         info = fe_profile_stop(self.ctx)
-        n = fe_kernel_count()
+        n = min(fe_kernel_count(), FE_PROFILE_MAX_KERNELS)
         return dict(launches=info.launches, target_launches=info.target_launches, target_ms=info.target_ms,
                     counts={fe_kernel_name(k): info.counts[k] for k in range(n) if info.counts[k]})
 

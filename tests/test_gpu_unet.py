@@ -301,3 +301,23 @@ def test_trained_network_gain(fe):
     assert sum(b[1] for b in trained) < sum(a[1] for a in untrained)
     s.close()
     plain.close()
+
+
+def test_harvest_in_mixed_precision_learned_context(fe):
+    """A mixed-precision learned-solver context harvests one (b, x) pair per
+    corrector through the plain-CG path (inner solves and refinement alike)."""
+    import torch
+    from paper_1404_0959_gb300 import learned
+    N = 16
+    rho, u, Y, T = random_fields(N, 1, False, seed=4, noise=0.0)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])], precision=fe.FE_FP32_MIXED,
+                  solver=fe.FE_FCG_LEARNED, p_tol=1e-8)
+    s.set_state(0, rho, u, Y)
+    fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
+    bank = learned.PairBank(s, 8)
+    assert bank.harvest(s, 2) >= 4
+    for k in range(bank.n):
+        b, x = bank.b[k].double(), bank.x[k].double()
+        assert torch.isfinite(b).all() and torch.isfinite(x).all()
+        assert b.norm() > 0 and x.norm() > 0
+    s.close()
