@@ -251,7 +251,7 @@ def main():
         s.step(1)
         p = s.profile_stop()
         share[k] = (p["target_ms"], p["target_launches"])
-    kernel = args.kernel or (max(share, key=lambda k: share[k][0]) if share else "cg_update")
+    kernel = args.kernel or (max(share, key=lambda k: share[k][0]) if share else "cg_dirmatvec")
 
     # kernel-level timed region: host-driven steps with CUDA events around
     # every launch of the dominant kernel, and the launch count
@@ -293,7 +293,7 @@ def main():
     hbm, peak_kind = peaks()
     per_launch_ms = prof["target_ms"] / max(prof["target_launches"], 1)
     alg_bytes = alg_words(kernel, nd) * w * cells
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     iters = info[0]["iters"]
 
     # end to end through the public API: state from pinned host, step, state back

@@ -139,39 +139,6 @@ __device__ __forceinline__ T DG4_h2(const A* f, const Nbr& n, int d, int ox, int
   return (T(28) * (m1 + p1) - T(54) * c0 - (m2 + p2)) * T(1.0 / 24.0);
 }
 
-// ---- inner-product accumulation ----------------------------------------------------
-// double vectors: FP64 fused multiply-add.  float vectors: the compensated
-// "Dot2" scheme of Ogita, Rump and Oishi ("Accurate sum and dot product",
-// SIAM J. Sci. Comput. 26, 2005): each product is split exactly into
-// rounded product + error with one FMA (TwoProduct) and added to a float
-// pair with Knuth's error-free TwoSum, so the pair carries about 48
-// significant bits -- FP64-class accuracy computed on the FP32 pipe, which on
-// this GPU is far wider than the FP64 pipe.  The pair is converted to double
-// once per thread before the block tree.  The _rn intrinsics keep the
-// compiler from contracting the error-free steps.
-template <typename T>
-struct DotAcc;
-template <>
-struct DotAcc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-  __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct DotAcc<float> {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float pe = __fmaf_rn(a, b, -p);
-    const float s = __fadd_rn(hi, p);
-    const float z = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(e, pe));
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // ---- double-float arithmetic ---------------------------------------------------
 // An unevaluated pair hi + lo of floats (about 48 significant bits), with the
 // error-free TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and FMA-based TwoProduct, and
@@ -209,6 +176,87 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 __device__ __forceinline__ DF df_from_double(double d) {
   const float hi = (float)d;
   return DF{hi, (float)(d - (double)hi)};
+}
+
+// ---- inner-product accumulation ----------------------------------------------------
+// double vectors: FP64 fused multiply-add.  float vectors: the compensated
+// "Dot2" scheme of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): each product is split exactly into
+// rounded product + error with one FMA (TwoProduct) and added to a float
+// pair with Knuth's error-free TwoSum, so the pair carries about 48
+// significant bits -- FP64-class accuracy computed on the FP32 pipe, which on
+// this GPU is far wider than the FP64 pipe.  The pairs stay pairs through the
+// warp and block trees (double-float additions) and become a double once per
+// block: on this GPU even a few FP64 additions per thread cost more than the
+// block's memory traffic.  The _rn intrinsics keep the compiler from
+// contracting the error-free steps.  red() gives the value to reduce (a double
+// or a float pair).
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ double red() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float z = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ DF red() const { return DF{hi, lo}; }
+};
+
+// Plain sums with the same accuracy: FP64, or a float pair with TwoSum.
+template <typename T>
+struct SumAcc;
+template <>
+struct SumAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a) { s += a; }
+  __device__ __forceinline__ double red() const { return s; }
+};
+template <>
+struct SumAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a) {
+    const DF t = df_two_sum(hi, a);
+    hi = t.hi;
+    lo = __fadd_rn(lo, t.lo);
+  }
+  __device__ __forceinline__ DF red() const { return DF{hi, lo}; }
+};
+
+// The reduced type of a field precision: double for FP64 fields, a float pair
+// for FP32 fields.
+template <typename T>
+struct RedSel {
+  using type = double;
+};
+template <>
+struct RedSel<float> {
+  using type = DF;
+};
+template <typename T>
+using Red = typename RedSel<T>::type;
+template <typename T>
+__device__ __forceinline__ Red<T> red_from(double v);
+template <>
+__device__ __forceinline__ double red_from<double>(double v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ DF red_from<float>(double v) {
+  return df_from_double(v);
 }
 
 // ---- block prologue -----------------------------------------------------------
@@ -273,31 +321,15 @@ __device__ __forceinline__ void st4(double* p, const V4<double>& a) {
 }
 
 // ---- deterministic reductions ----------------------------------------------------
-// Block-sum K doubles (fixed tree), write this block's partials, and report
-// whether this is the box's last block; if so `res` (shared) holds the box
-// totals (partials added in block order).  Must be called by all threads.
-// tile0/ntiles: the box's block range in the work list of this launch.
+// Last-block phase of the block sums: the box's last block to finish adds the
+// partials of all its blocks in block order.
 template <int K>
-__device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
+__device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
   __shared__ double red[K][NTHR / 32];
   __shared__ int last;
   const int tid = threadIdx.x + TX * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    double s = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[q][warp] = s;
-  }
-  __syncthreads();
   if (tid == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
-      part[(size_t)blockIdx.x * MAXP + q] = s;
-    }
     __threadfence();
     int prev = atomicAdd(B.cnt, 1);
     last = (prev == ntiles - 1);
@@ -325,6 +357,61 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
   }
   __syncthreads();
   return true;
+}
+
+// Block-sum K values (fixed tree), write this block's partials, and report
+// whether this is the box's last block; if so `res` (shared) holds the box
+// totals (partials added in block order).  Must be called by all threads.
+// tile0/ntiles: the box's block range in the work list of this launch.
+template <int K>
+__device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
+  __shared__ double red[K][NTHR / 32];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[q][warp] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
+      part[(size_t)blockIdx.x * MAXP + q] = s;
+    }
+  }
+  return sum_partials_last<K>(B, part, res, tile0, ntiles);
+}
+// Float-pair values: the warp and block trees add pairs on the FP32 pipe.
+template <int K>
+__device__ bool block_sum_last(DF (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
+  __shared__ DF red[K][NTHR / 32];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    DF s = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DF t{__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)};
+      s = df_add(s, t);
+    }
+    if (lane == 0) red[q][warp] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      DF s = red[q][0];
+      for (int w = 1; w < NTHR / 32; ++w) s = df_add(s, red[q][w]);
+      part[(size_t)blockIdx.x * MAXP + q] = (double)s.hi + (double)s.lo;
+    }
+  }
+  return sum_partials_last<K>(B, part, res, tile0, ntiles);
 }
 
 // Same for a maximum of one value.

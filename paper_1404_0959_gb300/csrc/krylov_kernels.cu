@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int
         a0.add(bc, z);
         a1.add(bc, bc);
       });
-  double v[2] = {a0.value(), a1.value()};
+  Red<T> v[2] = {a0.red(), a1.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
       }
     }
   }
-  double v[1] = {a0.value()};
+  Red<T> v[1] = {a0.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NTHR) kz_cg_matvec(const BoxDev* boxes, const 
     q[G.col + G.plane(k)] = y;
     a0.add(vc, y);
   }
-  double v[1] = {a0.value()};
+  Red<T> v[1] = {a0.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? 4 : 2) kz_cg_dirmatvec(
     zc = zp;
     oc = op;
   }
-  double v[1] = {a0.value()};
+  Red<T> v[1] = {a0.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -395,9 +395,66 @@ __global__ void __launch_bounds__(NTHR) k_cg_xfinal(const BoxDev* boxes, const i
       [&](int c) { x[c] = x[c] + alpha * pd[c]; });
 }
 
-// x += alpha pd (XU; otherwise x is updated by kz_cg_dirmatvec); r -= alpha q;
-// rz = <r, D^{-1} r>; convergence test on ||r||.
-template <typename T, bool XU>
+// Iteration count, convergence test on ||r|| and the next beta (last block of
+// a CG update).
+__device__ void cg_update_scalars(const BoxDev& B, double rz, double rr, int* active) {
+  double it = B.sc[SC_ITERS] + 1.0;
+  B.sc[SC_ITERS] = it;
+  B.sc[SC_RR] = rr;
+  if (sqrt(rr) <= B.sc[SC_TOL] * sqrt(B.sc[SC_BB])) {
+    B.sc[SC_DONE] = 1.0;
+    B.sc[SC_CONV] = 1.0;
+    atomicSub(active, 1);
+  } else if (it >= B.sc[SC_MAXIT]) {
+    B.sc[SC_DONE] = 1.0;
+    B.sc[SC_CONV] = 0.0;
+    atomicSub(active, 1);
+  } else {
+    B.sc[SC_BETA] = rz / B.sc[SC_RZ];
+    B.sc[SC_RZ] = rz;
+  }
+}
+
+// r -= alpha q; rz = <r, D^{-1} r>; convergence test on ||r|| (the update of
+// the fused iteration: x is advanced by kz_cg_dirmatvec).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_cg_rupdate(const BoxDev* boxes, const int2* work, double* part, int* active) {
+  const Chunk ch = chunk_of(boxes, work);
+  const BoxDev& B = boxes[ch.box];
+  if (box_done(B)) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ qv = F<T>(B, K_Q);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ r = F<T>(B, K_R);
+  const T alpha = (T)B.sc[SC_ALPHA];
+  DotAcc<T> a0, a1;
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        V4<T> rv = ld4(r + q0), qq = ld4(qv + q0), dv = ld4(dinv + q0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          rv.v[e] -= alpha * qq.v[e];
+          a0.add(rv.v[e], rv.v[e] * dv.v[e]);
+          a1.add(rv.v[e], rv.v[e]);
+        }
+        st4(r + q0, rv);
+      },
+      [&](int c) {
+        T rc = r[c] - alpha * qv[c];
+        r[c] = rc;
+        a0.add(rc, rc * dinv[c]);
+        a1.add(rc, rc);
+      });
+  Red<T> v[2] = {a0.red(), a1.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) cg_update_scalars(B, res[0], res[1], active);
+  }
+}
+
+// x += alpha pd; r -= alpha q; rz = <r, D^{-1} r>; convergence test on ||r||.
+template <typename T>
 __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const int2* work, double* part, int* active) {
   const Chunk ch = chunk_of(boxes, work);
   const BoxDev& B = boxes[ch.box];
@@ -414,12 +471,10 @@ __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const i
       ch, tid,
       [&](int q0) {
         V4<T> rv = ld4(r + q0), qq = ld4(qv + q0), dv = ld4(dinv + q0);
-        if (XU) {
-          V4<T> xv = ld4(x + q0), pv = ld4(pd + q0);
+        V4<T> xv = ld4(x + q0), pv = ld4(pd + q0);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) xv.v[e] += alpha * pv.v[e];
-          st4(x + q0, xv);
-        }
+        for (int e = 0; e < 4; ++e) xv.v[e] += alpha * pv.v[e];
+        st4(x + q0, xv);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           rv.v[e] -= alpha * qq.v[e];
@@ -429,32 +484,16 @@ __global__ void __launch_bounds__(NTHR) k_cg_update(const BoxDev* boxes, const i
         st4(r + q0, rv);
       },
       [&](int c) {
-        if (XU) x[c] = x[c] + alpha * pd[c];
+        x[c] = x[c] + alpha * pd[c];
         T rc = r[c] - alpha * qv[c];
         r[c] = rc;
         a0.add(rc, rc * dinv[c]);
         a1.add(rc, rc);
       });
-  double v[2] = {a0.value(), a1.value()};
+  Red<T> v[2] = {a0.red(), a1.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double it = B.sc[SC_ITERS] + 1.0;
-      B.sc[SC_ITERS] = it;
-      B.sc[SC_RR] = res[1];
-      if (sqrt(res[1]) <= B.sc[SC_TOL] * sqrt(B.sc[SC_BB])) {
-        B.sc[SC_DONE] = 1.0;
-        B.sc[SC_CONV] = 1.0;
-        atomicSub(active, 1);
-      } else if (it >= B.sc[SC_MAXIT]) {
-        B.sc[SC_DONE] = 1.0;
-        B.sc[SC_CONV] = 0.0;
-        atomicSub(active, 1);
-      } else {
-        B.sc[SC_BETA] = res[0] / B.sc[SC_RZ];
-        B.sc[SC_RZ] = res[0];
-      }
-    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) cg_update_scalars(B, res[0], res[1], active);
   }
 }
 
@@ -515,7 +554,6 @@ __global__ void __launch_bounds__(NTHR) k_bicg_init(const BoxDev* boxes, const i
   T* x = F<T>(B, K_X);
   T* p = F<T>(B, K_PD);
   T* v = F<T>(B, K_V);
-  double a[1] = {0.0};
   DotAcc<T> acc;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
@@ -529,7 +567,7 @@ __global__ void __launch_bounds__(NTHR) k_bicg_init(const BoxDev* boxes, const i
       acc.add(bc, bc);
     }
   }
-  a[0] = acc.value();
+  Red<T> a[1] = {acc.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -574,7 +612,6 @@ __global__ void __launch_bounds__(NTHR) k_bicg_v(const BoxDev* boxes, const int2
   const T* rh = F<T>(B, K_RHAT);
   T* v = F<T>(B, K_V);
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
-  double a[1] = {0.0};
   DotAcc<T> acc;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
@@ -585,7 +622,7 @@ __global__ void __launch_bounds__(NTHR) k_bicg_v(const BoxDev* boxes, const int2
       acc.add(rh[c], y);
     }
   }
-  a[0] = acc.value();
+  Red<T> a[1] = {acc.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -619,7 +656,6 @@ __global__ void __launch_bounds__(NTHR) k_bicg_t(const BoxDev* boxes, const int2
   const T* s = F<T>(B, K_S);
   T* tv = F<T>(B, K_T);
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih;
-  double a[2] = {0.0, 0.0};
   DotAcc<T> acc0, acc1;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
@@ -631,8 +667,7 @@ __global__ void __launch_bounds__(NTHR) k_bicg_t(const BoxDev* boxes, const int2
       acc1.add(y, y);
     }
   }
-  a[0] = acc0.value();
-  a[1] = acc1.value();
+  Red<T> a[2] = {acc0.red(), acc1.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -657,7 +692,6 @@ __global__ void __launch_bounds__(NTHR) k_bicg_x(const BoxDev* boxes, const int2
   T* x = F<T>(B, K_X);
   T* r = F<T>(B, K_R);
   const T alpha = (T)B.sc[SC_ALPHA], om = (T)B.sc[SC_OMEGA];
-  double a[2] = {0.0, 0.0};
   DotAcc<T> acc0, acc1;
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
@@ -671,8 +705,7 @@ __global__ void __launch_bounds__(NTHR) k_bicg_x(const BoxDev* boxes, const int2
       acc1.add(rh[c], rc);
     }
   }
-  a[0] = acc0.value();
-  a[1] = acc1.value();
+  Red<T> a[2] = {acc0.red(), acc1.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(a, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -786,7 +819,7 @@ __global__ void __launch_bounds__(NTHR) kz_mix_residual(const BoxDev* boxes, con
     b[G.col + G.plane(k)] = (T)r.hi;
     acc.add(r.hi, r.hi);
   }
-  double v[1] = {acc.value()};
+  DF v[1] = {acc.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) mix_finish_scalars(B, res[0], 0, outer_active);
@@ -828,7 +861,7 @@ __global__ void __launch_bounds__(NTHR) k_mix_residual(const BoxDev* boxes, cons
       }
     }
   }
-  double v[1] = {acc.value() + acc64};
+  DF v[1] = {B.transonic ? df_add(acc.red(), df_from_double(acc64)) : acc.red()};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) mix_finish_scalars(B, res[0], first, outer_active);
@@ -886,7 +919,7 @@ __global__ void __launch_bounds__(NTHR) k_fcg_dots(const BoxDev* boxes, const in
     zq.add(zc, qc);
     dq.add(rd, qc);
   }
-  double v[3] = {zr.value(), zq.value(), dq.value()};
+  Red<T> v[3] = {zr.red(), zq.red(), dq.red()};
   __shared__ double res[3];
   if (block_sum_last<3>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -937,7 +970,7 @@ __global__ void __launch_bounds__(NTHR) k_fcg_matvec(const BoxDev* boxes, const 
       pr.add(p[c], r[c]);
     }
   }
-  double v[2] = {pq.value(), pr.value()};
+  Red<T> v[2] = {pq.red(), pr.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -958,11 +991,11 @@ template <typename T> void launch_cg_matvec(const Launch& L) {
   else FE_LAUNCH(L, KID_CG_MATVEC, (kz_cg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
 }
 template <typename T> void launch_cg_update(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T, true><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_fused(const Launch& L) {
   FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
-  FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_update<T, false><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_xfinal(const Launch& L) {
   FE_LAUNCH(L, KID_CG_XFINAL, (k_cg_xfinal<T><<<EGRID>>>(L.boxes, L.ework)));
@@ -993,7 +1026,7 @@ template <typename T> void launch_fcg(const Launch& L, const float* z) {
   FE_LAUNCH(L, KID_FCG_DOTS, (k_fcg_dots<T><<<EGRID>>>(L.boxes, L.ework, L.part, z)));
   FE_LAUNCH(L, KID_FCG_DIR, (k_fcg_dir<T><<<EGRID>>>(L.boxes, L.ework, z)));
   FE_LAUNCH(L, KID_FCG_MATVEC, (k_fcg_matvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
-  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T, true><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+  FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_mix_residual(const Launch& L, int first, int* outer_active) {
   if (first || L.transonic)

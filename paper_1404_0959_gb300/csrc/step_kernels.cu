@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_corr(const BoxDev* boxes, const int
       }
     }
   }
-  double v[1] = {rr};
+  Red<T> v[1] = {mixed ? Red<T>{} : red_from<T>(rr)};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -448,9 +448,10 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* bo
   const T* p = F<T>(B, pk);
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
   constexpr bool fourier = FOURIER;
-  double acc[3 + MAXD];
-#pragma unroll
-  for (int q = 0; q < 3 + MAXD; ++q) acc[q] = 0.0;
+  // totals of the last corrector: mass, energy (barotropic: 2 x kinetic),
+  // non-finite count, dust mass per class
+  SumAcc<T> amass, abad;
+  DotAcc<T> aen, ady[MAXD];
   if (t.active) {
     for (int k = t.k0; k < t.kend; ++k) {
       Nbr n(t.i, t.j, k, B.N);
@@ -480,8 +481,8 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* bo
         T Yk = rY * irk;
         F<T>(B, yn0 + j)[c] = Yk;
         if (last) {
-          acc[3 + j] += (double)rk * (double)Yk;
-          if (!isfinite((double)Yk)) acc[2] += 1.0;
+          ady[j].add(rk, Yk);
+          if (!isfinite(Yk)) abad.add(T(1));
         }
       }
       T Ek = T(0);
@@ -519,23 +520,29 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* bo
           T Tk = (Ek - T(0.5) * uu) / (T)B.cv;
           F<T>(B, S(kset, F_T))[c] = Tk;
           pf = rk * (T)B.R * Tk;
-          acc[1] += (double)rk * (double)Ek;
+          aen.add(rk, Ek);
         } else {
           pf = pow(rk, (T)B.gamma) / (T)B.gamma;
-          acc[1] += 0.5 * (double)rk * (double)uu;
+          aen.add(rk, uu);
         }
         F<T>(B, S(kset, F_P))[c] = pf;
-        acc[0] += (double)rk;
-        if (!(isfinite((double)rk) && isfinite((double)uu) && isfinite((double)pf))) acc[2] += 1.0;
+        amass.add(rk);
+        if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
       }
     }
   }
   if (!last) return;
+  Red<T> acc[3 + MAXD];
+  acc[0] = amass.red();
+  acc[1] = aen.red();
+  acc[2] = abad.red();
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) acc[3 + j] = ady[j].red();
   __shared__ double res[3 + MAXD];
   if (block_sum_last<3 + MAXD>(acc, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_MASS] = res[0];
-      B.sc[SC_ENERGY] = res[1];
+      B.sc[SC_ENERGY] = fourier ? res[1] : 0.5 * res[1];
       B.sc[SC_BAD] = res[2];
       for (int j = 0; j < MAXD; ++j) B.sc[SC_DUST0 + j] = res[3 + j];
     }

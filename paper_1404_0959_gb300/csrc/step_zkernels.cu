@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(NTHR, 2) kz_corr(const BoxDev* boxes, const in
       rr += r * r;
     }
   }
-  double v[1] = {rr};
+  Red<T> v[1] = {mixed ? Red<T>{} : red_from<T>(rr)};
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -389,6 +389,13 @@ __global__ void __launch_bounds__(NTHR) kz_fluxn(const BoxDev* boxes, const int2
   FaceBack<T> phi;
   phi.init(Fz<T>(B, S(s, F_PHI0)), Fz<T>(B, S(s, F_PHI1)), Fz<T>(B, S(s, F_PHI2)), G, t.k0);
   const T ih = (T)B.ih;
+  T taup[ND];
+  T* fyn[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    taup[j] = (T)B.tau_p[j];
+    fyn[j] = Fz<T>(B, W_FYN0 + j);
+  }
   for (int k = t.k0; k < t.kend; ++k) {
     rho.advance(G, k);
 #pragma unroll
@@ -414,12 +421,12 @@ __global__ void __launch_bounds__(NTHR) kz_fluxn(const BoxDev* boxes, const int2
     }
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
-      const T tp = (T)B.tau_p[j];
+      const T tp = taup[j];
       T acc = T(0);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
         acc += (php[d] - tp * ra_p[d]) * zI4(Y[j], G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y[j], G, d, -1);
-      Fz<T>(B, W_FYN0 + j)[c] = acc * ih;
+      fyn[j][c] = acc * ih;
     }
   }
 }
@@ -443,10 +450,23 @@ __global__ void __launch_bounds__(NTHR, 2) kz_dust(const BoxDev* boxes, const in
   phi.init(Fz<T>(B, S(kset, F_PHI0)), Fz<T>(B, S(kset, F_PHI1)), Fz<T>(B, S(kset, F_PHI2)), G, t.k0);
   const T* __restrict__ rhon = Fz<T>(B, S(s, F_RHO));
   const T* __restrict__ u[3] = {Fz<T>(B, S(kset, F_U0)), Fz<T>(B, S(kset, F_U1)), Fz<T>(B, S(kset, F_U2))};
-  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
-  double acc[3 + ND];
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  T taup[ND];
+  const T* yold[ND];
+  const T* fyn[ND];
+  T* ynew[ND];
 #pragma unroll
-  for (int q = 0; q < 3 + ND; ++q) acc[q] = 0.0;
+  for (int j = 0; j < ND; ++j) {
+    taup[j] = (T)B.tau_p[j];
+    yold[j] = Fz<T>(B, S(s, F_Y0 + j));
+    fyn[j] = Fz<T>(B, W_FYN0 + j);
+    ynew[j] = Fz<T>(B, yn0 + j);
+  }
+  T* __restrict__ pout = Fz<T>(B, S(kset, F_P));
+  // totals of the last corrector: mass, 2 x kinetic energy, non-finite count,
+  // dust mass per class
+  SumAcc<T> amass, abad;
+  DotAcc<T> aen, ady[ND];
   for (int k = t.k0; k < t.kend; ++k) {
     rho.advance(G, k);
 #pragma unroll
@@ -475,35 +495,41 @@ __global__ void __launch_bounds__(NTHR, 2) kz_dust(const BoxDev* boxes, const in
     }
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
-      const T tp = (T)B.tau_p[j];
+      const T tp = taup[j];
       T fl = T(0);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
         fl += (php[d] - tp * ra_p[d]) * zI4(Y[j], G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y[j], G, d, -1);
-      const T rY = rn * __ldg(&Fz<T>(B, S(s, F_Y0 + j))[c]) - T(0.5) * dt * (__ldg(&Fz<T>(B, W_FYN0 + j)[c]) + fl * ih);
+      const T rY = rn * __ldg(&yold[j][c]) - T(0.5) * dt * (__ldg(&fyn[j][c]) + fl * ih);
       const T Yk = rY * irk;
-      Fz<T>(B, yn0 + j)[c] = Yk;
+      ynew[j][c] = Yk;
       if (last) {
-        acc[3 + j] += (double)rk * (double)Yk;
-        if (!isfinite((double)Yk)) acc[2] += 1.0;
+        ady[j].add(rk, Yk);
+        if (!isfinite(Yk)) abad.add(T(1));
       }
     }
     if (last) {
       const T u0 = __ldg(&u[0][c]), u1 = __ldg(&u[1][c]), u2 = __ldg(&u[2][c]);
       const T uu = u0 * u0 + u1 * u1 + u2 * u2;
-      const T pf = pow(rk, (T)B.gamma) / (T)B.gamma;
-      Fz<T>(B, S(kset, F_P))[c] = pf;
-      acc[0] += (double)rk;
-      acc[1] += 0.5 * (double)rk * (double)uu;
-      if (!(isfinite((double)rk) && isfinite((double)uu) && isfinite((double)pf))) acc[2] += 1.0;
+      const T pf = pow(rk, gam) / gam;
+      pout[c] = pf;
+      amass.add(rk);
+      aen.add(rk, uu);
+      if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
     }
   }
   if (!last) return;
+  Red<T> acc[3 + ND];
+  acc[0] = amass.red();
+  acc[1] = aen.red();
+  acc[2] = abad.red();
+#pragma unroll
+  for (int j = 0; j < ND; ++j) acc[3 + j] = ady[j].red();
   __shared__ double res[3 + ND];
   if (block_sum_last<3 + ND>(acc, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_MASS] = res[0];
-      B.sc[SC_ENERGY] = res[1];
+      B.sc[SC_ENERGY] = 0.5 * res[1];
       B.sc[SC_BAD] = res[2];
       for (int j = 0; j < MAXD; ++j) B.sc[SC_DUST0 + j] = j < ND ? res[3 + j] : 0.0;
     }
