@@ -257,6 +257,15 @@ int fe_harvest_pressure(fe_ctx* ctx, void* const* b_out, void* const* x_out, int
  * learned_every > 1. */
 int fe_use_graphs(fe_ctx* ctx, int on);
 
+/* Plane streaming for the fused CG iteration (on by default).  For boxes
+ * with N in {64, 128, 256, 512} and the symmetric operator, the kernel that
+ * forms the new direction and applies M to it streams whole x-rows of each
+ * z-plane into shared memory with bulk asynchronous copies instead of
+ * z-marching 32 x 8 column tiles; the arithmetic per cell is the same, the
+ * order of the partial sums of <pd, M pd> differs.  Off: the z-marching
+ * kernel for every box.  Not part of the method. */
+int fe_use_plane_streaming(fe_ctx* ctx, int on);
+
 /* Tile depth of the stencil kernels: every kernel launch covers all boxes
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz
  * (0 = built-in default: 8 for N >= 128, else 4).  fe_autotune times `trials`

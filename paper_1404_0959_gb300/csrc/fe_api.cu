@@ -88,6 +88,9 @@ struct fe_ctx {
   int2* dwork = nullptr;
   int nblocks = 0;
   int2* dework = nullptr;
+  int2* dbwork = nullptr;   // plane-streaming blocks (box, block of box)
+  int nbblocks = 0, bsmem = 0, npart = 0;
+  bool use_bulk = true;     // streamed CG kernel where the boxes allow it
   int neblocks = 0;
   int tz_override = 0;     // 0: default tile depth per N
   int nsm = 152;           // multiprocessors of the device
@@ -111,8 +114,9 @@ struct fe_ctx {
   int harvest_max = 0, harvest_n = 0;
   Prof prof;
   Launch L() {
-    return Launch{dbox,  dwork, nblocks, dework, neblocks, dpart, dactive, st, &prof, prm.closure == FE_FOURIER,
-                  prm.transonic, prm.n_dust};
+    return Launch{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
+                  prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, use_bulk && nbblocks > 0 ? dbwork : nullptr,
+                  nbblocks, bsmem};
   }
 };
 
@@ -205,18 +209,60 @@ static int set_tiling(fe_ctx* c, int tz) {
     B.etile0 = (int)ework.size();
     for (int q = 0; q < B.entiles; ++q) ework.push_back(make_int2(b, q));
   }
+  // plane-streaming blocks: every box with N in {64, 128, 256, 512}, a
+  // persistent grid of the resident blocks per SM x SMs shared out by cells
+  std::vector<int2> bwork;
+  int bsmem = 0;
+  bool stream = !c->prm.transonic;
+  long scells = 0;
+  for (int b = 0; b < c->nb && stream; ++b) {
+    const int N = c->hbox[b].N;
+    stream = N >= 64 && N <= 512 && (N & (N - 1)) == 0;
+    scells += (long)N * N * N;
+  }
+  if (stream) {
+    int maxN = 0;
+    for (int b = 0; b < c->nb; ++b) maxN = std::max(maxN, c->hbox[b].N);
+    bsmem = c->fp64 ? bulk_cg_prepare<double>(maxN) : bulk_cg_prepare<float>(maxN);
+    const int per_sm = bsmem <= 0 ? 0 : c->fp64 ? bulk_cg_blocks_per_sm<double>(bsmem) : bulk_cg_blocks_per_sm<float>(bsmem);
+    stream = per_sm > 0;
+    const long grid = (long)per_sm * c->nsm;
+    for (int b = 0; b < c->nb && stream; ++b) {
+      BoxDev& B = c->hbox[b];
+      const long N = B.N, planes = bulk_cg_pairs(B.N);
+      long nb = (grid * N * N * N + scells - 1) / scells;
+      nb = std::max(1L, std::min(nb, planes / 4));
+      B.btile0 = (int)bwork.size();
+      B.bntiles = (int)nb;
+      for (int q = 0; q < B.bntiles; ++q) bwork.push_back(make_int2(b, q));
+    }
+  }
+  if (!stream) {
+    bwork.clear();
+    bsmem = 0;
+    for (int b = 0; b < c->nb; ++b) c->hbox[b].btile0 = c->hbox[b].bntiles = 0;
+  }
   CK(cudaStreamSynchronize(c->st));
-  const int need = (int)std::max(work.size(), ework.size());
-  if ((int)work.size() != c->nblocks || (int)ework.size() != c->neblocks || !c->dpart) {
+  const int need = (int)std::max(std::max(work.size(), ework.size()), bwork.size());
+  cudaFree(c->dbwork);
+  c->dbwork = nullptr;
+  if (!bwork.empty() && cudaMalloc(&c->dbwork, bwork.size() * sizeof(int2)) != cudaSuccess) return FE_ERR_OOM;
+  if (!bwork.empty())
+    CK(cudaMemcpyAsync(c->dbwork, bwork.data(), bwork.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
+  c->nbblocks = (int)bwork.size();
+  c->bsmem = bsmem;
+  if ((int)work.size() != c->nblocks || (int)ework.size() != c->neblocks || !c->dpart || need > c->npart) {
     cudaFree(c->dwork);
     cudaFree(c->dework);
     cudaFree(c->dpart);
     c->dwork = c->dework = nullptr;
     c->dpart = nullptr;
+    c->npart = 0;
     if (cudaMalloc(&c->dwork, work.size() * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&c->dework, ework.size() * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&c->dpart, (size_t)need * MAXP * sizeof(double)) != cudaSuccess)
       return FE_ERR_OOM;
+    c->npart = need;
   }
   c->nblocks = (int)work.size();
   c->neblocks = (int)ework.size();
@@ -350,6 +396,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->dbox);
   cudaFree(c->dwork);
   cudaFree(c->dework);
+  cudaFree(c->dbwork);
   cudaFree(c->dpart);
   cudaFree(c->dsc);
   cudaFree(c->dcnt);
@@ -738,6 +785,7 @@ static int step_once(fe_ctx* c, bool commit = true) {
   if (rc != FE_OK) return rc;
   for (int b = 0; b < c->nb; ++b) {
     const double* sc = c->hsc + (size_t)b * NSC;
+    if (sc[SC_KERR] != 0.0) return FE_ERR_CUDA;
     if (sc[SC_BAD] > 0.0 || !std::isfinite(sc[SC_DT])) return FE_ERR_NONFINITE;
     for (int kk = 0; kk < nc; ++kk)
       if (!(sc[SC_RES0 + kk] <= c->prm.p_tol * (1.0 + 1e-3))) return FE_ERR_NOT_CONVERGED;
@@ -1114,6 +1162,13 @@ extern "C" int fe_precond_activation(fe_ctx* c, int layer, float* out, size_t co
   if (!c || !out) return FE_ERR_INVALID_ARG;
   if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
   return unet_activation(c->unet, layer, out, (long)count, c->st);
+}
+
+extern "C" int fe_use_plane_streaming(fe_ctx* c, int on) {
+  if (!c) return FE_ERR_INVALID_ARG;
+  if (c->use_bulk != (on != 0)) drop_graphs(c);
+  c->use_bulk = on != 0;
+  return FE_OK;
 }
 
 extern "C" int fe_use_graphs(fe_ctx* c, int on) {

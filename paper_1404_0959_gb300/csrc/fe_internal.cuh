@@ -66,6 +66,7 @@ enum Scalar {
   SC_IT0, SC_IT1, SC_IT2, SC_IT3, SC_RES0, SC_RES1, SC_RES2, SC_RES3,
   SC_ODONE, SC_OBB, SC_ORR, SC_ORES, SC_ITSUM, SC_OTOL, SC_OUTER,  // mixed-precision refinement
   SC_FB, SC_NFB,                                                    // flexible CG: Jacobi fallback flag, count
+  SC_KERR,  // a kernel gave up a bounded wait (bulk-copy completion)
   SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
   NSC = SC_DUST0 + MAXD + 4
 };
@@ -76,6 +77,7 @@ struct BoxDev {
   int tile0, ntiles;       // this box's blocks in the stencil work list
   int etile0, entiles;     // this box's blocks in the element-wise work list
   int echunk;              // cells per element-wise block (multiple of 4 * NTHR)
+  int btile0, bntiles;     // this box's blocks in the plane-streaming work list (0: not streamed)
   double h, ih, mu, gamma, R, cv, kappa, cfl, growth, dtmax;
   double tau_p[MAXD];
   void* f[NSLOT];
@@ -480,6 +482,9 @@ struct Launch {
   int fourier;    // closure of the context (selects kernel variants)
   int transonic;  // transonic pressure operator
   int nd;         // dust classes
+  const int2* bwork;  // plane-streaming blocks (box, block of box); null: z-marching kernels
+  int nbblocks;
+  int bsmem;          // dynamic shared memory of the streamed CG kernel
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -509,6 +514,9 @@ template <typename V> void launch_cg_matvec(const Launch& L);
 template <typename V> void launch_cg_update(const Launch& L);
 template <typename V> void launch_cg_fused(const Launch& L);   // symmetric operator: dir + matvec, then update
 template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
+template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
+template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);
+int bulk_cg_pairs(int N);  // (row group, plane) pairs of the streamed CG kernel for an N^3 box
 template <typename V> void launch_cg_dir(const Launch& L);
 template <typename V> void launch_true_res(const Launch& L, int xslot);
 template <typename V> void launch_bicg_init(const Launch& L);

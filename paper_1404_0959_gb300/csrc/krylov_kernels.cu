@@ -10,6 +10,7 @@
 // (per-thread, then a fixed-order warp/block tree, then the box's last block
 // adds the block partials in order).  A box whose solve has finished skips
 // every later launch, so one launch serves all boxes of an ensemble.
+#include "zbulk.cuh"
 #include "zmarch.cuh"
 
 namespace fe {
@@ -227,8 +228,21 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
   }
 }
 
-// Planes requested ahead by the z-marching Krylov kernels.
-constexpr int KPF = 2;
+// Planes requested ahead by the z-marching Krylov kernels, minimum resident
+// blocks per SM of the fused CG kernel (FP32), and shared-memory plane
+// buffers (2: the next plane is staged while the current one is read, one
+// barrier per plane).
+#ifndef FE_KPF
+#define FE_KPF 2
+#endif
+#ifndef FE_DM_MINB
+#define FE_DM_MINB 4
+#endif
+#ifndef FE_DM_NBUF
+#define FE_DM_NBUF 2
+#endif
+constexpr int KPF = FE_KPF;
+constexpr int kDmBuf = FE_DM_NBUF;
 
 // q = M pd; alpha = rz / <pd, q> (symmetric operator): z-marching form, pd
 // staged per plane in shared memory with a 1-cell halo, z-neighbours in
@@ -279,12 +293,12 @@ __global__ void __launch_bounds__(NTHR) kz_cg_matvec(const BoxDev* boxes, const 
 // the iteration counter (neighbouring tiles still read pd_old as halo).  At
 // iteration 0 alpha = beta = 0 (set by k_cg_init) and pd_new = D^{-1} b.
 template <typename T>
-__global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? 4 : 2) kz_cg_dirmatvec(const BoxDev* boxes, const int2* work, double* part) {
+__global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_dirmatvec(const BoxDev* boxes, const int2* work, double* part) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   if (box_done(B)) return;
   const ZGeom<1> G(t.x0, t.y0, B.N);
-  __shared__ T sm[ZGeom<1>::H * ZGeom<1>::W];
+  __shared__ T smb[kDmBuf][ZGeom<1>::H * ZGeom<1>::W];
   const int odd = ((int)B.sc[SC_ITERS]) & 1;
   const T* __restrict__ po = F<T>(B, odd ? K_PP : K_PD);
   T* __restrict__ pn = F<T>(B, odd ? K_PD : K_PP);
@@ -334,7 +348,8 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? 4 : 2) kz_cg_dirmatvec(
     cp[KPF - 1] = ld(po, G.col, k + 1 + KPF);
     const T ps = psi.next(G, k);
     const T xv = xs.next(G, k);
-    __syncthreads();
+    T* sm = smb[kDmBuf == 2 ? (k & 1) : 0];
+    if (kDmBuf == 1) __syncthreads();
     sm[G.csm] = zc;
     if (G.hcol >= 0) {
       sm[G.hsm] = dir(hr[0], hd[0], hp[0]);
@@ -367,6 +382,192 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? 4 : 2) kz_cg_dirmatvec(
   __shared__ double res[1];
   if (block_sum_last<1>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_PQ] = res[0];
+      B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
+    }
+  }
+}
+
+// ---- kz_cg_dirmatvec on streamed planes --------------------------------------------
+// The same iteration (identical per-cell arithmetic) for boxes with N in
+// {64, 128, 256, 512}: raw planes of r, D^{-1}, pd_old (with y-halo rows),
+// psi and x (own rows) arrive by bulk copy in a ring of kBulkStages stages;
+// pd_new of each plane (own and halo rows) goes to a 4-slot ring, and the
+// operator is applied one plane behind, once pd_new of the plane above is
+// there.  One barrier per plane.
+#ifndef FE_BULK_STAGES
+#define FE_BULK_STAGES 2
+#endif
+constexpr int kBulkStages = FE_BULK_STAGES;
+
+template <typename T>
+__host__ __device__ constexpr int bulk_stage_elems(int N) {
+  return 3 * (kBulkCells + 2 * N) + 2 * kBulkCells;
+}
+template <typename T>
+__host__ __device__ constexpr int bulk_ring_elems(int N) {
+  return 4 * (kBulkCells + 2 * N);
+}
+// dynamic shared memory of kb_cg_dirmatvec for edge N
+template <typename T>
+int bulk_smem_bytes(int N) {
+  return 128 + (kBulkStages * bulk_stage_elems<T>(N) + bulk_ring_elems<T>(N)) * (int)sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, const int2* bwork, double* part) {
+  const int2 w = bwork[blockIdx.x];
+  const BoxDev& B = boxes[w.x];
+  if (box_done(B)) return;
+  extern __shared__ __align__(128) unsigned char zsm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(zsm);
+  const int N = B.N;
+  const BulkGeom Gm(N, w.y, B.bntiles);
+  const int R = Gm.R, RN = R * N, HN = (R + 2) * N;
+  T* stage0 = reinterpret_cast<T*>(zsm + 128);
+  const int SE = bulk_stage_elems<T>(N);
+  T* ring = stage0 + kBulkStages * SE;
+  const int tid = threadIdx.x;
+  const int odd = ((int)B.sc[SC_ITERS]) & 1;
+  const T* __restrict__ po = F<T>(B, odd ? K_PP : K_PD);
+  T* __restrict__ pn = F<T>(B, odd ? K_PD : K_PP);
+  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  const T* __restrict__ psi = F<T>(B, W_PSI);
+  T* __restrict__ x = F<T>(B, K_X);
+  T* __restrict__ q = F<T>(B, K_Q);
+  const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  const int nseq = Gm.count();
+  const size_t NN = (size_t)N * N;
+
+  // stage layout: r | dinv | pd_old (R + 2 rows each, halo rows first and last) | psi | x (R rows)
+  auto issue = [&](int j) {
+    const BulkPos P = bulk_pos(Gm, j);
+    T* st = stage0 + (j % kBulkStages) * SE;
+    uint64_t* bj = bar + (j % kBulkStages);
+    const int y0 = P.g * R;
+    const int ym = y0 == 0 ? N - 1 : y0 - 1, yp = y0 + R == N ? 0 : y0 + R;
+    const size_t pl = (size_t)P.m * NN;
+    const bool comp = P.pos >= 1 && P.pos <= P.len;
+    const unsigned row = (unsigned)(N * sizeof(T)), rows = (unsigned)(RN * sizeof(T));
+    mbar_expect_tx(bj, 3 * (rows + 2 * row) + (comp ? 2 * rows : 0));
+    const T* src[3] = {r, dinv, po};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      T* d = st + f * HN;
+      bulk_g2s(d, src[f] + pl + (size_t)ym * N, row, bj);
+      bulk_g2s(d + N, src[f] + pl + (size_t)y0 * N, rows, bj);
+      bulk_g2s(d + N + RN, src[f] + pl + (size_t)yp * N, row, bj);
+    }
+    if (comp) {
+      bulk_g2s(st + 3 * HN, psi + pl + (size_t)y0 * N, rows, bj);
+      bulk_g2s(st + 3 * HN + RN, x + pl + (size_t)y0 * N, rows, bj);
+    }
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < kBulkStages; ++s) mbar_init(bar + s, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < kBulkStages && j < nseq; ++j) issue(j);
+
+  const int Q = Gm.Q;
+  const int x4 = (tid % Q) * 4;                                // first x of this thread
+  const int RS = R / kBulkRows;                                // own rows: tid / Q + RS * u
+  const int hr = tid < Q ? 0 : R + 1;                          // halo row handled (tid < 2Q)
+  const bool halo = tid < 2 * Q;
+  const int xm1 = x4 == 0 ? N - 1 : x4 - 1, xp4 = x4 + 4 == N ? 0 : x4 + 4;
+  V4<T> sv_psi[kBulkRows], sv_x[kBulkRows], sv_po[kBulkRows], cu_psi[kBulkRows], cu_x[kBulkRows], cu_po[kBulkRows];
+  DotAcc<T> a0;
+  bool failed = false;
+  for (int i = 0; i < nseq; ++i) {
+    const BulkPos P = bulk_pos(Gm, i);
+    const bool ok = mbar_wait(bar + (i % kBulkStages), (unsigned)((i / kBulkStages) & 1));
+    const T* st = stage0 + (i % kBulkStages) * SE;
+    T* slot = ring + (i & 3) * HN;
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < kBulkRows; ++u) {  // own rows: pd_new, and the centre values needed one plane later
+        const int jr = tid / Q + RS * u;
+        const int o = (jr + 1) * N + x4;
+        const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
+        V4<T> nv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) nv.v[e] = rv.v[e] * dv.v[e] + beta * pv.v[e];
+        st4(slot + o, nv);
+        cu_po[u] = pv;
+        if (P.pos >= 1 && P.pos <= P.len) {
+          cu_psi[u] = ld4(st + 3 * HN + jr * N + x4);
+          cu_x[u] = ld4(st + 3 * HN + RN + jr * N + x4);
+        }
+      }
+      if (halo) {
+        const int o = hr * N + x4;
+        const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
+        V4<T> nv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) nv.v[e] = rv.v[e] * dv.v[e] + beta * pv.v[e];
+        st4(slot + o, nv);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && i + kBulkStages < nseq) issue(i + kBulkStages);
+    if (P.pos >= 2) {  // operator for the plane below (pos - 1 in 1..len)
+      const int mo = P.m == 0 ? N - 1 : P.m - 1;
+      const T* c = ring + ((i - 1) & 3) * HN;
+      const T* zm = ring + ((i - 2) & 3) * HN;
+      const T* zp = slot;
+#pragma unroll
+      for (int u = 0; u < kBulkRows; ++u) {
+        const int jr = tid / Q + RS * u;
+        const int o = (jr + 1) * N;
+        const size_t gbase = (size_t)mo * NN + (size_t)(P.g * R + jr) * N + x4;
+        const V4<T> cc = ld4(c + o + x4), cs = ld4(c + o - N + x4), cn = ld4(c + o + N + x4);
+        const V4<T> cb = ld4(zm + o + x4), ca = ld4(zp + o + x4);
+        const T left = c[o + xm1], right = c[o + xp4];
+        V4<T> yv, xn;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T vc = cc.v[e];
+          const T vxm = e == 0 ? left : cc.v[e == 0 ? 0 : e - 1];
+          const T vxp = e == 3 ? right : cc.v[e == 3 ? 3 : e + 1];
+          const T nb = (vxm + vxp) + (cs.v[e] + cn.v[e]) + (cb.v[e] + ca.v[e]);
+          const T y = sv_psi[u].v[e] * vc * idt - lapc * (nb - T(6) * vc);
+          yv.v[e] = y;
+          xn.v[e] = sv_x[u].v[e] + alpha * sv_po[u].v[e];
+          a0.add(vc, y);
+        }
+        st4(q + gbase, yv);
+        st4(pn + gbase, cc);
+        st4(x + gbase, xn);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBulkRows; ++u) {
+      sv_psi[u] = cu_psi[u];
+      sv_x[u] = cu_x[u];
+      sv_po[u] = cu_po[u];
+    }
+  }
+  if (failed) {
+    // drain the copies still in flight (bounded), record the failure, leave
+    if (tid == 0) {
+      for (int s = 0; s < kBulkStages; ++s) mbar_wait(bar + s, 0u, 1 << 16), mbar_wait(bar + s, 1u, 1 << 16);
+      B.sc[SC_KERR] = 1.0;
+    }
+    return;
+  }
+  Red<T> v[1] = {a0.red()};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.btile0, B.bntiles)) {
+    if (tid == 0) {
       B.sc[SC_PQ] = res[0];
       B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
     }
@@ -994,7 +1195,11 @@ template <typename T> void launch_cg_update(const Launch& L) {
   FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_fused(const Launch& L) {
-  FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+  if (L.bwork)
+    FE_LAUNCH(L, KID_CG_DIRMATVEC,
+              (kb_cg_dirmatvec<T><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+  else
+    FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
   FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_xfinal(const Launch& L) {
@@ -1041,12 +1246,33 @@ template <typename T> void launch_mix_finish(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework)));
 }
 
+// Dynamic shared memory of the streamed CG kernel for edge N (sets the
+// kernel's opt-in limit); 0 if it does not fit.
+template <typename T>
+int bulk_cg_prepare(int N) {
+  const int bytes = bulk_smem_bytes<T>(N);
+  if (bytes > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(kb_cg_dirmatvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    return 0;
+  return bytes;
+}
+// (row group, plane) pairs of an N^3 box
+int bulk_cg_pairs(int N) { return N * (N / (kBulkCells / N)); }
+template <typename T>
+int bulk_cg_blocks_per_sm(int bytes) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T>, NTHR, bytes) != cudaSuccess) return 0;
+  return nb;
+}
+
 #define INST(T)                                                  \
   template void launch_cg_init<T>(const Launch&, double);        \
   template void launch_cg_matvec<T>(const Launch&);              \
   template void launch_cg_update<T>(const Launch&);              \
   template void launch_cg_fused<T>(const Launch&);               \
   template void launch_cg_xfinal<T>(const Launch&);              \
+  template int bulk_cg_prepare<T>(int);                          \
+  template int bulk_cg_blocks_per_sm<T>(int);                    \
   template void launch_cg_dir<T>(const Launch&);                 \
   template void launch_true_res<T>(const Launch&, int);          \
   template void launch_bicg_init<T>(const Launch&);              \

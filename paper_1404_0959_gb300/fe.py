@@ -72,8 +72,8 @@ EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
-           "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs", "fe_destroy",
-           "fe_strerror"]
+           "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
+           "fe_use_plane_streaming", "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -106,6 +106,7 @@ def load_library(path=LIB_PATH):
     lib.fe_precond_activation.argtypes = [c_void_p, c_int, c_void_p, ctypes.c_size_t]
     lib.fe_harvest_pressure.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_int)]
     lib.fe_use_graphs.argtypes = [c_void_p, c_int]
+    lib.fe_use_plane_streaming.argtypes = [c_void_p, c_int]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
@@ -272,6 +273,10 @@ def fe_use_graphs(ctx, on=True):
     return _check(lib().fe_use_graphs(ctx, int(bool(on))), "fe_use_graphs")
 
 
+def fe_use_plane_streaming(ctx, on=True):
+    return _check(lib().fe_use_plane_streaming(ctx, int(bool(on))), "fe_use_plane_streaming")
+
+
 def fe_set_tiling(ctx, tz):
     return _check(lib().fe_set_tiling(ctx, tz), "fe_set_tiling")
 
@@ -422,6 +427,9 @@ class Solver:
 
     def use_graphs(self, on=True):
         fe_use_graphs(self.ctx, on)
+
+    def use_plane_streaming(self, on=True):
+        fe_use_plane_streaming(self.ctx, on)
 
     def autotune(self, trials=2):
         return fe_autotune(self.ctx, trials)

@@ -1,0 +1,120 @@
+"""Plane-streamed fused CG kernel (bulk asynchronous copies, N in {64, 128,
+256, 512}) against the FP64 oracle and against the z-marching kernel.
+
+The two kernels do the same per-cell arithmetic; only the order of the
+partial sums of <pd, M pd> differs, so steps agree to the Krylov tolerance
+(FP64 bar 1e-11 relative L2 per field and step against the oracle, as for
+the z-marching path).
+"""
+import numpy as np
+import pytest
+
+from oracle import piso
+from paper_1404_0959_gb300.inputs import random_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1404_0959_gb300 import build
+    build.build()
+    from paper_1404_0959_gb300 import fe as fe_mod
+    return fe_mod
+
+
+def rel(a, b):
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / (nb if nb > 0 else 1.0)
+
+
+def fields(st):
+    out = {"rho": st["rho"], "p": st["p"]}
+    for d in range(3):
+        out["u%d" % d] = st["u"][d]
+        out["phi%d" % d] = st["phi"][d]
+    for j, y in enumerate(st["Y"]):
+        out["Y%d" % j] = y
+    return out
+
+
+def worst(got, ref):
+    g, r = fields(got), fields(ref)
+    return max(rel(g[k], r[k]) for k in r)
+
+
+def solver(fe, N, precision, streaming, seed=1, p_tol=1e-10):
+    rho, u, Y, _ = random_fields(N, 1, False, seed=seed, mach=0.3, noise=0.02)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])], precision=precision, p_tol=p_tol)
+    s.set_state(0, rho, u, Y)
+    s.use_plane_streaming(streaming)
+    return s, (rho, u, Y)
+
+
+def test_streamed_fp64_step_matches_oracle(fe):
+    N = 64
+    s, (rho, u, Y) = solver(fe, N, fe.FE_FP64, True)
+    prm = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], p_tol=1e-10)
+    st = piso.make_state(prm, rho, u, Y)
+    s.profile_start("cg_dirmatvec")
+    code, ginf = s.step(1)
+    prof = s.profile_stop()
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    assert prof["target_launches"] > 0
+    ref, info = piso.step(prm, st)
+    got = s.get_state(0)
+    s.close()
+    assert worst(got, ref) <= 1e-11
+    assert all(abs(a - b) <= 1 for a, b in zip(ginf[0]["iters"], info["iters"]))
+
+
+@pytest.mark.parametrize("N,precision,tol", [(128, 0, 1e-10), (256, 1, 1e-5)])
+def test_streamed_matches_zmarching(fe, N, precision, tol):
+    out = []
+    for streaming in (True, False):
+        s, _ = solver(fe, N, precision, streaming, seed=2, p_tol=1e-10 if precision == 0 else 1e-8)
+        code, info = s.step(2)
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        out.append((s.get_state(0), info[0]))
+        s.close()
+    (a, ia), (b, ib) = out
+    assert worst(a, b) <= tol
+    assert all(abs(x - y) <= 1 for x, y in zip(ia["iters"], ib["iters"]))
+
+
+def test_streamed_ensemble_matches_single_boxes(fe):
+    boxes = [dict(N=64, nu=0.005, tau_p=[0.05], Y0=[0.01], seed=3),
+             dict(N=128, nu=0.002, tau_p=[0.05], Y0=[0.01], seed=4)]
+    ens = fe.Solver(boxes)
+    ens.init_state(-1, fe.FE_INIT_SPECTRAL)
+    code, _ = ens.step(2)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    for b, box in enumerate(boxes):
+        one = fe.Solver([box])
+        one.init_state(0, fe.FE_INIT_SPECTRAL)
+        code, _ = one.step(2)
+        assert code == fe.FE_OK
+        assert worst(ens.get_state(b), one.get_state(0)) <= 1e-10
+        one.close()
+    ens.close()
+
+
+def test_streamed_512_mixed_matches_zmarching(fe):
+    N = 512
+    out = []
+    for streaming in (True, False):
+        s = fe.Solver([dict(N=N, nu=0.001, tau_p=[0.05], Y0=[0.01], mach_rms=0.2, k0=8.0, seed=5)],
+                      precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+        s.init_state(0, fe.FE_INIT_SPECTRAL)
+        s.use_plane_streaming(streaming)
+        code, info = s.step(1)
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        st = s.get_state(0)
+        out.append({k: st[k] for k in ("rho", "p")} | {"u0": st["u"][0]})
+        s.close()
+    for k in out[0]:
+        assert rel(out[0][k], out[1][k]) <= 1e-5, k
