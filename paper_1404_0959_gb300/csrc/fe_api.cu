@@ -291,6 +291,9 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
       c->nsm = nsm;
+    // ring kernels need their shared-memory limits set before any capture (else z-marching kernels run)
+    if (c->fp64) rprepare<double>();
+    else rprepare<float>();
   }
   const int nb = c->nb, nd = prm->n_dust;
   c->N.assign(prm->N, prm->N + nb);

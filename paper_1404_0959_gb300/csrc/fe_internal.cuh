@@ -514,6 +514,9 @@ template <typename V> void launch_cg_matvec(const Launch& L);
 template <typename V> void launch_cg_update(const Launch& L);
 template <typename V> void launch_cg_fused(const Launch& L);   // symmetric operator: dir + matvec, then update
 template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
+// PISO kernels on asynchronous-copy rings (return 0: not launched, use the z-marching kernel)
+template <typename V> int rprepare();  // shared-memory limits of the ring kernels on the current device
+template <typename V> int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
 template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);
 int bulk_cg_pairs(int N);  // (row group, plane) pairs of the streamed CG kernel for an N^3 box

@@ -552,6 +552,7 @@ template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp)
 }
 template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
                                         int mixed) {
+  if (rlaunch_corr<T>(L, s, rhop, pp, pnew, kset, kidx, mixed)) return;
   FE_LAUNCH(L, KID_CORR, (kz_corr<T><<<ZGRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx, mixed)));
 }
 template <typename T> void zlaunch_accel(const Launch& L, int kset, int pk) {

@@ -142,17 +142,21 @@ __device__ __forceinline__ TileXYZ tile_xyz(const BoxDev* boxes, const int2* wor
   return t;
 }
 
-// ---- star stencils on a ZField (same arithmetic as the global-memory helpers) ----
-template <typename T, int R>
-__device__ __forceinline__ T zI4(const ZField<T, R>& f, const ZGeom<R>& G, int d, int o) {
+// ---- star stencils on a staged field (same arithmetic as the global-memory helpers) ----
+// FV: any view with at(G, d, s) and c() (ZField, ZView, ZView2).
+template <typename FV, typename GT>
+__device__ __forceinline__ auto zI4(const FV& f, const GT& G, int d, int o) -> decltype(f.c()) {
+  using T = decltype(f.c());
   return (T(9) * (f.at(G, d, o) + f.at(G, d, o + 1)) - (f.at(G, d, o - 1) + f.at(G, d, o + 2))) * T(0.0625);
 }
-template <typename T, int R>
-__device__ __forceinline__ T zGc_h(const ZField<T, R>& f, const ZGeom<R>& G, int d) {
+template <typename FV, typename GT>
+__device__ __forceinline__ auto zGc_h(const FV& f, const GT& G, int d) -> decltype(f.c()) {
+  using T = decltype(f.c());
   return (T(10) * (f.at(G, d, 1) - f.at(G, d, -1)) - (f.at(G, d, 2) - f.at(G, d, -2))) * T(0.0625);
 }
-template <typename T, int R>
-__device__ __forceinline__ T zDG4_h2(const ZField<T, R>& f, const ZGeom<R>& G, int d) {
+template <typename FV, typename GT>
+__device__ __forceinline__ auto zDG4_h2(const FV& f, const GT& G, int d) -> decltype(f.c()) {
+  using T = decltype(f.c());
   return (T(28) * (f.at(G, d, -1) + f.at(G, d, 1)) - T(54) * f.c() - (f.at(G, d, -2) + f.at(G, d, 2))) *
          T(1.0 / 24.0);
 }
