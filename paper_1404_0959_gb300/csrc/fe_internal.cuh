@@ -517,6 +517,11 @@ template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_c
 // PISO kernels on asynchronous-copy rings (return 0: not launched, use the z-marching kernel)
 template <typename V> int rprepare();  // shared-memory limits of the ring kernels on the current device
 template <typename V> int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed);
+template <typename V> int rlaunch_pred(const Launch& L, int s, int kset);
+template <typename V> int rlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop);
+template <typename V> int rlaunch_accel(const Launch& L, int kset, int pk);
+template <typename V> int rlaunch_fluxn(const Launch& L, int s, int nd);
+template <typename V> int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
 template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);
 int bulk_cg_pairs(int N);  // (row group, plane) pairs of the streamed CG kernel for an N^3 box

@@ -8,6 +8,21 @@
 
 namespace fe {
 
+// Lookahead planes of each ring kernel (shared memory per block grows with
+// it; measured at 256^3 FP32: the corrector and the dust update run best
+// with one plane, the others with two).  The divergence and the right-hand
+// side keep their register-queue z-marching kernels, which measured faster.
+#ifndef FE_RING_A
+#define FE_RING_A 2
+#endif
+#ifndef FE_RING_A_LIGHT
+#define FE_RING_A_LIGHT 1
+#endif
+#ifndef FE_RING_OFF
+#define FE_RING_OFF 0u  // ring kernels left out (bits of RingKernel): their z-marching versions run
+#endif
+constexpr int kA = FE_RING_A, kA1 = FE_RING_A_LIGHT;
+
 template <typename T>
 __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
   return reinterpret_cast<T*>(B.f[slot]);
@@ -17,21 +32,24 @@ __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
 // (outside any stream capture); the launchers run a ring kernel only on a
 // prepared device.
 constexpr int kMaxDev = 64;
+// per device, one bit per ring kernel (set when its shared-memory limit was accepted)
+enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
+                  RK_DUST3 };
 template <typename T>
 struct RingReady {
-  static bool ok[kMaxDev];
+  static unsigned ok[kMaxDev];
 };
 template <typename T>
-bool RingReady<T>::ok[kMaxDev] = {};
+unsigned RingReady<T>::ok[kMaxDev] = {};
 static int current_device() {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return -1;
   return dev;
 }
 template <typename T>
-static bool ring_ready() {
+static bool ring_ready(int kernel) {
   const int dev = current_device();
-  return dev >= 0 && RingReady<T>::ok[dev];
+  return dev >= 0 && (RingReady<T>::ok[dev] >> kernel & 1u);
 }
 template <typename K>
 static bool set_smem(K kernel, int bytes) {
@@ -42,7 +60,7 @@ static bool set_smem(K kernel, int bytes) {
 // p^k = p^{k-1} + x staged as the sum of two rings; fluxes phi^k = phi* - dt G2 x,
 // u^k = HbyA - dt/rho^{k-1} Gc p^k, rho^k = rho^n - dt/2 (div phi^n + D phi^k);
 // FP64 path: ||b - M x||^2 for the reported residual.
-constexpr int kCorrA = 2;
+constexpr int kCorrA = kA1;
 template <typename T, bool MIXED>
 struct CorrRing {
   static constexpr int A = kCorrA, NCEN = MIXED ? 6 : 8;
@@ -183,11 +201,305 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
   }
 }
 
+
+template <typename P>
+struct Unparen;
+template <typename P>
+struct Unparen<void(P)> {
+  using type = P;
+};
+#define RING_PROLOGUE(P)                                   \
+  const TileXYZ t = tile_xyz(boxes, work);                 \
+  const BoxDev& B = boxes[t.box];                          \
+  const ZGeom<2> G(t.x0, t.y0, B.N);                       \
+  const int tid = threadIdx.x + TX * threadIdx.y;          \
+  extern __shared__ __align__(16) unsigned char rsm[];     \
+  typename Unparen<void(P)>::type R;                       \
+  R.init(rsm, t.k0, t.kend)
+
+// ---- predictor ------------------------------------------------------------------------------------
+template <typename T>
+using PredPlan = RingPlan<T, kA, 5, 3, 1>;  // u0..2, div, p | phi | rho
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kr_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
+  RING_PROLOGUE(PredPlan<T>);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(s, F_U0 + m));
+  R.gs[3] = Fr<T>(B, W_DIV);
+  R.gs[4] = Fr<T>(B, S(s, F_P));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, S(s, F_PHI0 + d));
+  R.gc[0] = Fr<T>(B, S(s, F_RHO));
+  T* __restrict__ divphi = Fr<T>(B, W_DIVPHI);
+  T* __restrict__ Rn[3] = {Fr<T>(B, W_RN0), Fr<T>(B, W_RN1), Fr<T>(B, W_RN2)};
+  T* __restrict__ An[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
+  T* __restrict__ psi = Fr<T>(B, W_PSI);
+  T* __restrict__ dinv = Fr<T>(B, W_DINV);
+  T* __restrict__ rho0 = Fr<T>(B, S(kset, F_RHO));
+  T* __restrict__ us[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
+  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
+  R.prologue(G, tid);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, tid, i);
+    if (!G.active) continue;
+    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
+    const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
+    T php[3], phm[3];
+    R.faces(0, k, G, php, phm);
+    const int c = G.col + G.plane(k);
+    const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
+    const T r = R.cen(0, k, tid);
+    const T r0 = r - dt * dph;
+    const T ir0 = T(1) / r0, ir = T(1) / r;
+    T L[3], visc[3];
+    zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const T gp = zGc_h(p, G, m) * ih;
+      us[m][c] = (r * u[m].c() + dt * (L[m] - gp)) * ir0;
+      Rn[m][c] = L[m];
+      An[m][c] = (visc[m] - gp) * ir;
+    }
+    const T ps = r / (gam * p.c());
+    psi[c] = ps;
+    dinv[c] = T(1) / (ps * idt + c3);
+    divphi[c] = dph;
+    rho0[c] = r0;
+  }
+  cp_async_wait<0>();
+}
+
+// ---- corrector assembly ------------------------------------------------------------------------------
+template <typename T>
+using AsmPlan = RingPlan<T, kA, 4, 3, 8>;  // u0..2 (level k-1), div | phi | rho, un0..2, rho', Rn0..2
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kr_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
+                                                int rhop) {
+  RING_PROLOGUE(AsmPlan<T>);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, up0 + m);
+  R.gs[3] = Fr<T>(B, W_DIV);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, php0 + d);
+  R.gc[0] = Fr<T>(B, S(s, F_RHO));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[1 + m] = Fr<T>(B, S(s, F_U0 + m));
+  R.gc[4] = Fr<T>(B, rhop);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[5 + m] = Fr<T>(B, W_RN0 + m);
+  T* __restrict__ hb[3] = {Fr<T>(B, W_HB0), Fr<T>(B, W_HB1), Fr<T>(B, W_HB2)};
+  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
+  R.prologue(G, tid);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, tid, i);
+    if (!G.active) continue;
+    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
+    const ZView<T> div = R.view(3, k, G);
+    T php[3], phm[3];
+    R.faces(0, k, G, php, phm);
+    const int c = G.col + G.plane(k);
+    T L[3], visc[3];
+    zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+    const T r = R.cen(0, k, tid);
+    const T irp = T(1) / R.cen(4, k, tid);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const T Rm = T(0.5) * (R.cen(5 + m, k, tid) + L[m]);
+      hb[m][c] = (r * R.cen(1 + m, k, tid) + dt * Rm) * irp;
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---- Du/Dt at level k -----------------------------------------------------------------------------------
+template <typename T>
+using AccelPlan = RingPlan<T, kA, 5, 0, 1>;  // u0..2, div, p | | rho
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kr_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
+  RING_PROLOGUE(AccelPlan<T>);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(kset, F_U0 + m));
+  R.gs[3] = Fr<T>(B, W_DIV);
+  R.gs[4] = Fr<T>(B, pk);
+  R.gc[0] = Fr<T>(B, S(kset, F_RHO));
+  T* __restrict__ a[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
+  const T ih = (T)B.ih, mu = (T)B.mu;
+  R.prologue(G, tid);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, tid, i);
+    if (!G.active) continue;
+    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
+    const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
+    const int c = G.col + G.plane(k);
+    const T ir = T(1) / R.cen(0, k, tid);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
+      const T visc = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
+      a[m][c] = (visc - zGc_h(p, G, m) * ih) * ir;
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---- dust: n-level flux divergences FYN_j = D(phi_p^n I4 Y_j^n) --------------------------------------------
+template <typename T, int ND>
+using FluxPlan = RingPlan<T, kA, 4 + ND, 3, 0>;  // rho, a0..2, Y_j | phi
+template <typename T, int ND>
+__global__ void __launch_bounds__(NTHR) kr_fluxn(const BoxDev* boxes, const int2* work, int s) {
+  RING_PROLOGUE((FluxPlan<T, ND>));
+  R.gs[0] = Fr<T>(B, S(s, F_RHO));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gs[1 + d] = Fr<T>(B, W_AN0 + d);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) R.gs[4 + j] = Fr<T>(B, S(s, F_Y0 + j));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, S(s, F_PHI0 + d));
+  const T ih = (T)B.ih;
+  T taup[ND];
+  T* fyn[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    taup[j] = (T)B.tau_p[j];
+    fyn[j] = Fr<T>(B, W_FYN0 + j);
+  }
+  R.prologue(G, tid);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, tid, i);
+    if (!G.active) continue;
+    const ZView<T> rho = R.view(0, k, G);
+    const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
+    T php[3], phm[3];
+    R.faces(0, k, G, php, phm);
+    const int c = G.col + G.plane(k);
+    T ra_p[3], ra_m[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
+      ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const ZView<T> Y = R.view(4 + j, k, G);
+      const T tp = taup[j];
+      T acc = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        acc += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
+      fyn[j][c] = acc * ih;
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---- dust: level k, (rho Y)^k and Y^k; on the last corrector the barotropic closure and totals -----------------
+template <typename T, int ND>
+using DustPlan = RingPlan<T, kA1, 4 + ND, 3, 4 + 2 * ND>;  // rho^k, a0..2, Y_j^{k-1} | phi^k | rho^n, Y^n, FYN, u0..2
+template <typename T, int ND>
+__global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2* work, double* part, int s, int kset,
+                                                 int yp0, int yn0, int last) {
+  RING_PROLOGUE((DustPlan<T, ND>));
+  R.gs[0] = Fr<T>(B, S(kset, F_RHO));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gs[1 + d] = Fr<T>(B, W_AN0 + d);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) R.gs[4 + j] = Fr<T>(B, yp0 + j);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, S(kset, F_PHI0 + d));
+  R.gc[0] = Fr<T>(B, S(s, F_RHO));
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    R.gc[1 + j] = Fr<T>(B, S(s, F_Y0 + j));
+    R.gc[1 + ND + j] = Fr<T>(B, W_FYN0 + j);
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[1 + 2 * ND + m] = Fr<T>(B, S(kset, F_U0 + m));
+  if (!last) R.ncf = 1 + 2 * ND;  // u^k is read on the last corrector only
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  T taup[ND];
+  T* ynew[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    taup[j] = (T)B.tau_p[j];
+    ynew[j] = Fr<T>(B, yn0 + j);
+  }
+  T* __restrict__ pout = Fr<T>(B, S(kset, F_P));
+  SumAcc<T> amass, abad;
+  DotAcc<T> aen, ady[ND];
+  R.prologue(G, tid);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, tid, i);
+    if (!G.active) continue;
+    const ZView<T> rho = R.view(0, k, G);
+    const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
+    T php[3], phm[3];
+    R.faces(0, k, G, php, phm);
+    const int c = G.col + G.plane(k);
+    const T rk = rho.c();
+    const T irk = T(1) / rk;
+    const T rn = R.cen(0, k, tid);
+    T ra_p[3], ra_m[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
+      ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const ZView<T> Y = R.view(4 + j, k, G);
+      const T tp = taup[j];
+      T fl = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        fl += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
+      const T rY = rn * R.cen(1 + j, k, tid) - T(0.5) * dt * (R.cen(1 + ND + j, k, tid) + fl * ih);
+      const T Yk = rY * irk;
+      ynew[j][c] = Yk;
+      if (last) {
+        ady[j].add(rk, Yk);
+        if (!isfinite(Yk)) abad.add(T(1));
+      }
+    }
+    if (last) {
+      const T u0 = R.cen(1 + 2 * ND, k, tid), u1 = R.cen(2 + 2 * ND, k, tid), u2 = R.cen(3 + 2 * ND, k, tid);
+      const T uu = u0 * u0 + u1 * u1 + u2 * u2;
+      const T pf = pow(rk, gam) / gam;
+      pout[c] = pf;
+      amass.add(rk);
+      aen.add(rk, uu);
+      if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
+    }
+  }
+  cp_async_wait<0>();
+  if (!last) return;
+  Red<T> acc[3 + ND];
+  acc[0] = amass.red();
+  acc[1] = aen.red();
+  acc[2] = abad.red();
+#pragma unroll
+  for (int j = 0; j < ND; ++j) acc[3 + j] = ady[j].red();
+  __shared__ double res[3 + ND];
+  if (block_sum_last<3 + ND>(acc, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_MASS] = res[0];
+      B.sc[SC_ENERGY] = 0.5 * res[1];
+      B.sc[SC_BAD] = res[2];
+      for (int j = 0; j < MAXD; ++j) B.sc[SC_DUST0 + j] = j < ND ? res[3 + j] : 0.0;
+    }
+  }
+}
+
 // ---- launchers (0: the ring kernel could not be prepared) --------------------------------------
 #define RGRID(bytes) L.nblocks, dim3(TX, TY), (bytes), L.st
 template <typename T>
 int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed) {
-  if (!ring_ready<T>()) return 0;
+  if (!ring_ready<T>(mixed ? RK_CORR_M : RK_CORR_F)) return 0;
   constexpr int bm = CorrRing<T, true>::bytes, bf = CorrRing<T, false>::bytes;
   if (mixed)
     FE_LAUNCH(L, KID_CORR, (kr_corr<T, true><<<RGRID(bm)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
@@ -197,16 +509,85 @@ int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, i
 }
 
 template <typename T>
+int rlaunch_pred(const Launch& L, int s, int kset) {
+  if (!ring_ready<T>(RK_PRED)) return 0;
+  FE_LAUNCH(L, KID_PRED, (kr_pred<T><<<RGRID(PredPlan<T>::bytes)>>>(L.boxes, L.work, s, kset)));
+  return 1;
+}
+template <typename T>
+int rlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
+  if (!ring_ready<T>(RK_ASM)) return 0;
+  FE_LAUNCH(L, KID_ASM, (kr_asm<T><<<RGRID(AsmPlan<T>::bytes)>>>(L.boxes, L.work, s, up0, php0, rhop)));
+  return 1;
+}
+template <typename T>
+int rlaunch_accel(const Launch& L, int kset, int pk) {
+  if (!ring_ready<T>(RK_ACCEL)) return 0;
+  FE_LAUNCH(L, KID_ACCEL, (kr_accel<T><<<RGRID(AccelPlan<T>::bytes)>>>(L.boxes, L.work, kset, pk)));
+  return 1;
+}
+template <typename T>
+int rlaunch_fluxn(const Launch& L, int s, int nd) {
+  if (nd < 1 || nd > 3 || !ring_ready<T>(RK_FLUX1 + nd - 1)) return 0;
+  switch (nd) {
+    case 1: FE_LAUNCH(L, KID_FLUXN, (kr_fluxn<T, 1><<<RGRID((FluxPlan<T, 1>::bytes))>>>(L.boxes, L.work, s))); break;
+    case 2: FE_LAUNCH(L, KID_FLUXN, (kr_fluxn<T, 2><<<RGRID((FluxPlan<T, 2>::bytes))>>>(L.boxes, L.work, s))); break;
+    case 3: FE_LAUNCH(L, KID_FLUXN, (kr_fluxn<T, 3><<<RGRID((FluxPlan<T, 3>::bytes))>>>(L.boxes, L.work, s))); break;
+    default: return 0;
+  }
+  return 1;
+}
+template <typename T>
+int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd) {
+  if (nd < 1 || nd > 3 || !ring_ready<T>(RK_DUST1 + nd - 1)) return 0;
+  switch (nd) {
+    case 1:
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 1><<<RGRID((DustPlan<T, 1>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
+                                                                                 yn0, last)));
+      break;
+    case 2:
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 2><<<RGRID((DustPlan<T, 2>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
+                                                                                 yn0, last)));
+      break;
+    case 3:
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 3><<<RGRID((DustPlan<T, 3>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
+                                                                                 yn0, last)));
+      break;
+    default: return 0;
+  }
+  return 1;
+}
+
+template <typename T>
 int rprepare() {
   const int dev = current_device();
   if (dev < 0) return 0;
-  bool ok = set_smem(kr_corr<T, true>, CorrRing<T, true>::bytes) && set_smem(kr_corr<T, false>, CorrRing<T, false>::bytes);
+  unsigned ok = 0;
+  auto set = [&](int bit, bool accepted) { ok |= accepted ? 1u << bit : 0u; };
+  set(RK_CORR_M, set_smem(kr_corr<T, true>, CorrRing<T, true>::bytes));
+  set(RK_CORR_F, set_smem(kr_corr<T, false>, CorrRing<T, false>::bytes));
+  set(RK_PRED, set_smem(kr_pred<T>, PredPlan<T>::bytes));
+  set(RK_ASM, set_smem(kr_asm<T>, AsmPlan<T>::bytes));
+  set(RK_ACCEL, set_smem(kr_accel<T>, AccelPlan<T>::bytes));
+  set(RK_FLUX1, set_smem(kr_fluxn<T, 1>, FluxPlan<T, 1>::bytes));
+  set(RK_FLUX2, set_smem(kr_fluxn<T, 2>, FluxPlan<T, 2>::bytes));
+  set(RK_FLUX3, set_smem(kr_fluxn<T, 3>, FluxPlan<T, 3>::bytes));
+  set(RK_DUST1, set_smem(kr_dust<T, 1>, DustPlan<T, 1>::bytes));
+  set(RK_DUST2, set_smem(kr_dust<T, 2>, DustPlan<T, 2>::bytes));
+  set(RK_DUST3, set_smem(kr_dust<T, 3>, DustPlan<T, 3>::bytes));
+  cudaGetLastError();  // a refused limit is not an error of the context
+  ok &= ~(unsigned)(FE_RING_OFF);
   RingReady<T>::ok[dev] = ok;
-  return ok ? 1 : 0;
+  return ok != 0;
 }
 
 #define RINST(T)                                                                \
   template int rlaunch_corr<T>(const Launch&, int, int, int, int, int, int, int); \
+  template int rlaunch_pred<T>(const Launch&, int, int);                          \
+  template int rlaunch_asm<T>(const Launch&, int, int, int, int);                 \
+  template int rlaunch_accel<T>(const Launch&, int, int);                         \
+  template int rlaunch_fluxn<T>(const Launch&, int, int);                         \
+  template int rlaunch_dust<T>(const Launch&, int, int, int, int, int, int);      \
   template int rprepare<T>();
 RINST(double)
 RINST(float)

@@ -42,24 +42,6 @@ struct FaceBack {
   }
 };
 
-// L_m = -D(phi I4 u_m) + mu (sum_d D G4_d u_m + Gc_m(div)/3), and the viscous part
-template <typename T>
-__device__ __forceinline__ void zeval_L(const ZField<T, 2> (&u)[3], const ZField<T, 2>& div, const T (&php)[3],
-                                        const T (&phm)[3], const ZGeom<2>& G, T ih, T mu, T (&L)[3],
-                                        T (&visc)[3]) {
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    T conv = T(0), lap = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      conv += php[d] * zI4(u[m], G, d, 0) - phm[d] * zI4(u[m], G, d, -1);
-      lap += zDG4_h2(u[m], G, d);
-    }
-    visc[m] = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
-    L[m] = visc[m] - conv * ih;
-  }
-}
-
 // ---- div -----------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(NTHR) kz_div(const BoxDev* boxes, const int2* work, int u0) {
@@ -542,9 +524,11 @@ template <typename T> void zlaunch_div(const Launch& L, int u0) {
   FE_LAUNCH(L, KID_DIV, (kz_div<T><<<ZGRID>>>(L.boxes, L.work, u0)));
 }
 template <typename T> void zlaunch_pred(const Launch& L, int s, int k) {
+  if (rlaunch_pred<T>(L, s, k)) return;
   FE_LAUNCH(L, KID_PRED, (kz_pred<T><<<ZGRID>>>(L.boxes, L.work, s, k)));
 }
 template <typename T> void zlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
+  if (rlaunch_asm<T>(L, s, up0, php0, rhop)) return;
   FE_LAUNCH(L, KID_ASM, (kz_asm<T><<<ZGRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
 }
 template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
@@ -556,9 +540,11 @@ template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp
   FE_LAUNCH(L, KID_CORR, (kz_corr<T><<<ZGRID>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx, mixed)));
 }
 template <typename T> void zlaunch_accel(const Launch& L, int kset, int pk) {
+  if (rlaunch_accel<T>(L, kset, pk)) return;
   FE_LAUNCH(L, KID_ACCEL, (kz_accel<T><<<ZGRID>>>(L.boxes, L.work, kset, pk)));
 }
 template <typename T> void zlaunch_fluxn(const Launch& L, int s, int nd) {
+  if (rlaunch_fluxn<T>(L, s, nd)) return;
   switch (nd) {
     case 1: FE_LAUNCH(L, KID_FLUXN, (kz_fluxn<T, 1><<<ZGRID>>>(L.boxes, L.work, s))); break;
     case 2: FE_LAUNCH(L, KID_FLUXN, (kz_fluxn<T, 2><<<ZGRID>>>(L.boxes, L.work, s))); break;
@@ -566,6 +552,7 @@ template <typename T> void zlaunch_fluxn(const Launch& L, int s, int nd) {
   }
 }
 template <typename T> void zlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd) {
+  if (rlaunch_dust<T>(L, s, kset, yp0, yn0, last, nd)) return;
   switch (nd) {
     case 1: FE_LAUNCH(L, KID_DUST, (kz_dust<T, 1><<<ZGRID>>>(L.boxes, L.work, L.part, s, kset, yp0, yn0, last))); break;
     case 2: FE_LAUNCH(L, KID_DUST, (kz_dust<T, 2><<<ZGRID>>>(L.boxes, L.work, L.part, s, kset, yp0, yn0, last))); break;

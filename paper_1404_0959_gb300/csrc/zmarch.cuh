@@ -161,4 +161,21 @@ __device__ __forceinline__ auto zDG4_h2(const FV& f, const GT& G, int d) -> decl
          T(1.0 / 24.0);
 }
 
+// L_m = -D(phi I4 u_m) + mu (sum_d D G4_d u_m + Gc_m(div)/3), and the viscous part
+template <typename T, typename FV>
+__device__ __forceinline__ void zeval_L(const FV (&u)[3], const FV& div, const T (&php)[3], const T (&phm)[3],
+                                        const ZGeom<2>& G, T ih, T mu, T (&L)[3], T (&visc)[3]) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T conv = T(0), lap = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      conv += php[d] * zI4(u[m], G, d, 0) - phm[d] * zI4(u[m], G, d, -1);
+      lap += zDG4_h2(u[m], G, d);
+    }
+    visc[m] = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
+    L[m] = visc[m] - conv * ih;
+  }
+}
+
 }  // namespace fe
