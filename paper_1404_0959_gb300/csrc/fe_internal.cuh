@@ -167,6 +167,13 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   s.lo = __fadd_rn(s.lo, t.lo);
   return df_fast_two_sum(s.hi, s.lo);
 }
+// Pair addition without the second TwoSum (Dekker's original): accurate to
+// about 2^-44 relative to |a| + |b|, for operands of one sign.
+__device__ __forceinline__ DF df_add_same_sign(DF a, DF b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
   const float p = __fmul_rn(a.hi, b.hi);

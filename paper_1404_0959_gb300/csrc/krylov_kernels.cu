@@ -984,6 +984,40 @@ __device__ void mix_finish_scalars(const BoxDev& B, double rr, int first, int* o
   sc[SC_TOL] = fmin(0.5, fmax(need, 1e-6));
 }
 
+// First refinement step (element-wise): keep b in K_AUX, x pairs = 0, ||b||^2.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_mix_first(const BoxDev* boxes, const int2* ework, double* part,
+                                                    int* outer_active) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ b = F<T>(B, K_B);
+  T* __restrict__ borig = F<T>(B, K_AUX);
+  float2* __restrict__ xs = F<float2>(B, K_X64);
+  DotAcc<float> acc;
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        const V4<T> bv = ld4(b + q0);
+        st4(borig + q0, bv);
+        reinterpret_cast<float4*>(xs + q0)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(xs + q0)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc.add((float)bv.v[e], (float)bv.v[e]);
+      },
+      [&](int c) {
+        const T bc = b[c];
+        borig[c] = bc;
+        xs[c] = make_float2(0.f, 0.f);
+        acc.add((float)bc, (float)bc);
+      });
+  DF v[1] = {acc.red()};
+  __shared__ double res[1];
+  if (block_sum_last<1>(v, B, part, res, B.etile0, B.entiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) mix_finish_scalars(B, res[0], 1, outer_active);
+  }
+}
+
 // Refinement residual r = b - M x (x as double-float pairs) for the symmetric
 // operator, z-marching form (pairs staged with a 1-cell halo).
 template <typename T>
@@ -1011,10 +1045,22 @@ __global__ void __launch_bounds__(NTHR) kz_mix_residual(const BoxDev* boxes, con
     xs.stage(G, k);
     __syncthreads();
     if (!G.active) continue;
-    DF nb = df_add(X(xs.at(G, 0, 1)), X(xs.at(G, 0, -1)));
-    nb = df_add(nb, df_add(X(xs.at(G, 1, 1)), X(xs.at(G, 1, -1))));
-    nb = df_add(nb, df_add(X(xs.at(G, 2, 1)), X(xs.at(G, 2, -1))));
-    const DF a = df_add(df_mul(idt, DF{(float)pc, 0.f}), k6);
+    // neighbour sum: hi parts by a TwoSum chain (error terms kept), lo parts plainly
+    const float2 n0 = xs.at(G, 0, 1), n1 = xs.at(G, 0, -1), n2 = xs.at(G, 1, 1), n3 = xs.at(G, 1, -1),
+                 n4 = xs.at(G, 2, 1), n5 = xs.at(G, 2, -1);
+    DF nb = df_two_sum(n0.x, n1.x);
+    {
+      const float h[4] = {n2.x, n3.x, n4.x, n5.x};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const DF u = df_two_sum(nb.hi, h[j]);
+        nb.hi = u.hi;
+        nb.lo = __fadd_rn(nb.lo, u.lo);
+      }
+      nb.lo = __fadd_rn(nb.lo, __fadd_rn(__fadd_rn(__fadd_rn(n0.y, n1.y), __fadd_rn(n2.y, n3.y)), __fadd_rn(n4.y, n5.y)));
+      nb = df_fast_two_sum(nb.hi, nb.lo);
+    }
+    const DF a = df_add_same_sign(df_mul(idt, DF{(float)pc, 0.f}), k6);
     const DF mx = df_add(df_mul(a, X(xs.c())), df_neg(df_mul(kl, nb)));
     const DF r = df_add(DF{(float)bc, 0.f}, df_neg(mx));
     b[G.col + G.plane(k)] = (T)r.hi;
@@ -1234,7 +1280,9 @@ template <typename T> void launch_fcg(const Launch& L, const float* z) {
   FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_mix_residual(const Launch& L, int first, int* outer_active) {
-  if (first || L.transonic)
+  if (first)
+    FE_LAUNCH(L, KID_MIX_RES, (k_mix_first<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active)));
+  else if (L.transonic)
     FE_LAUNCH(L, KID_MIX_RES, (k_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, first, outer_active)));
   else
     FE_LAUNCH(L, KID_MIX_RES, (kz_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active)));
