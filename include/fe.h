@@ -257,6 +257,14 @@ int fe_harvest_pressure(fe_ctx* ctx, void* const* b_out, void* const* x_out, int
  * learned_every > 1. */
 int fe_use_graphs(fe_ctx* ctx, int on);
 
+/* Convolution kernels of the learned preconditioner: mode 1 (default) runs
+ * the stride-1 layers whose output grid is a multiple of 128 on the
+ * fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+ * memory); mode 0 runs every layer on warp-level MMA.  Both accumulate in
+ * FP32 from BF16 operands; the order of the partial sums differs.  Not part
+ * of the method. */
+int fe_precond_kernels(fe_ctx* ctx, int mode);
+
 /* Plane streaming for the fused CG iteration (on by default).  For boxes
  * with N in {64, 128, 256, 512} and the symmetric operator, the kernel that
  * forms the new direction and applies M to it streams whole x-rows of each

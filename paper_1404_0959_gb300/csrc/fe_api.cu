@@ -33,6 +33,7 @@ template <typename T> int unet_apply(UNet*, const T*, const T*, float*, cudaStre
 template <typename T> int unet_train_step(UNet*, const T*, const T*, const T*, double, double*, cudaStream_t);
 float* unet_output(UNet* U);
 int unet_activation(UNet* U, int l, float* host, long count, cudaStream_t st);
+void unet_set_kernels(UNet* U, int tc);
 }  // namespace fe
 
 namespace fe {
@@ -91,6 +92,7 @@ struct fe_ctx {
   int2* dbwork = nullptr;   // plane-streaming blocks (box, block of box)
   int nbblocks = 0, bsmem = 0, npart = 0;
   bool use_bulk = true;     // streamed CG kernel where the boxes allow it
+  int unet_tc = 1;          // U-Net stride-1 layers on tcgen05 (1) or warp-level MMA (0)
   int neblocks = 0;
   int tz_override = 0;     // 0: default tile depth per N
   int nsm = 152;           // multiprocessors of the device
@@ -1101,6 +1103,7 @@ extern "C" int fe_load_preconditioner(fe_ctx* c, const float* w, size_t count) {
   if (!c->unet) {
     int rc = FE_OK;
     c->unet = unet_create(c->hbox[0].N, true, &rc);
+    if (c->unet) unet_set_kernels(c->unet, c->unet_tc);
     if (!c->unet) return rc;
   }
   int rc = unet_set_weights(c->unet, w, c->st);
@@ -1165,6 +1168,14 @@ extern "C" int fe_precond_activation(fe_ctx* c, int layer, float* out, size_t co
   if (!c || !out) return FE_ERR_INVALID_ARG;
   if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
   return unet_activation(c->unet, layer, out, (long)count, c->st);
+}
+
+extern "C" int fe_precond_kernels(fe_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 1) return FE_ERR_INVALID_ARG;
+  c->unet_tc = mode;
+  if (c->unet) unet_set_kernels(c->unet, mode);
+  drop_graphs(c);
+  return FE_OK;
 }
 
 extern "C" int fe_use_plane_streaming(fe_ctx* c, int on) {

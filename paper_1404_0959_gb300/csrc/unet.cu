@@ -355,14 +355,20 @@ __global__ void k_slice(const float* src, long n, int Cf, int c0, int C, float* 
 }
 
 // Network input: channel 0 = r / rms(r), channel 1 = psi / mean(psi) - 1, channels 2..15 = 0.
+// 16-channel input voxel: (c0, c1, 0, ..., 0) in two 16-byte stores
+__device__ __forceinline__ void pack_voxel(bf16* o, float c0, float c1) {
+  __nv_bfloat162 p = __floats2bfloat162_rn(c0, c1);
+  uint4 a;
+  a.x = *reinterpret_cast<uint32_t*>(&p);
+  a.y = a.z = a.w = 0u;
+  reinterpret_cast<uint4*>(o)[0] = a;
+  reinterpret_cast<uint4*>(o)[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 template <typename T>
 __global__ void k_pack_input(const T* r, const T* psi, long n, double rinv, double pinv, bf16* in16) {
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    bf16* o = in16 + q * 16;
-    o[0] = __float2bfloat16((float)((double)r[q] * rinv));
-    o[1] = __float2bfloat16(psi ? (float)((double)psi[q] * pinv - 1.0) : 0.f);
-    for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16(0.f);
-  }
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    pack_voxel(in16 + q * 16, (float)((double)r[q] * rinv), psi ? (float)((double)psi[q] * pinv - 1.0) : 0.f);
 }
 
 // Adam (Kingma and Ba 2015) on the FP32 master weights; refreshes the BF16
@@ -456,7 +462,24 @@ struct UNet {
   int adam_step = 0;
   std::vector<void*> allocs;
   bool trained = false;
+  int use_tc = 1;      // stride-1 layers on the fifth-generation tensor cores where they fit
+  int* err = nullptr;  // device flag: a tensor-core convolution gave up a bounded wait
+  int nsm = 152;
 };
+
+struct TcConvArgs {
+  const bf16* s0;
+  const bf16* s1;
+  int c0, c1, m0, m1;
+  int No;
+  const bf16* W;
+  const float* bias;
+  bf16* out;
+  float* out32;
+  int relu;
+  int* err;
+};
+int conv_tc(const TcConvArgs& a, int Cout, int nsm, cudaStream_t st);
 
 static long cube(long n) { return n * n * n; }
 
@@ -479,7 +502,15 @@ static int unet_alloc(UNet& U, int N, bool training) {
   U.u2 = (bf16*)A(n1 * 32 * 2);
   U.u1 = (bf16*)A(n0 * 16 * 2);
   U.out32 = (float*)A(n0 * 4);
-  if (!U.in16 || !U.e1a || !U.e1b || !U.d1 || !U.e2 || !U.d2 || !U.e3 || !U.u2 || !U.u1 || !U.out32)
+  U.err = (int*)A(sizeof(int));
+  if (U.err) cudaMemset(U.err, 0, sizeof(int));
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      U.nsm = nsm;
+  }
+  if (!U.in16 || !U.e1a || !U.e1b || !U.d1 || !U.e2 || !U.d2 || !U.e3 || !U.u2 || !U.u1 || !U.out32 || !U.err)
     return FE_ERR_OOM;
   size_t wtotal = 0;
   for (int l = 0; l < kNL; ++l) {
@@ -539,7 +570,20 @@ static int ew(long n) {
   return (int)(g < 152L * 8 ? g : 152L * 8);
 }
 
-static void launch_conv(const ConvArgs& a, cudaStream_t st) {
+static void launch_conv(const UNet& U, const ConvArgs& a, cudaStream_t st) {
+  // stride-1 gathers (same grid, nearest upsampling) go to the tensor-memory kernel when it fits
+  auto tc_mode = [&](const Src& s, int& m) {
+    if (s.C == 0) return true;
+    if (s.mode == G_SAME && s.n == a.No) return (m = 0, true);
+    if (s.mode == G_UP && 2 * s.n == a.No) return (m = 1, true);
+    return false;
+  };
+  int m0 = 0, m1 = 0;
+  if (U.use_tc && !a.accumulate && (a.out32 == nullptr || a.out32_ch == 1) && tc_mode(a.s0, m0) &&
+      tc_mode(a.s1, m1)) {
+    TcConvArgs t{a.s0.ptr, a.s1.ptr, a.s0.C, a.s1.C, m0, m1, a.No, a.W, a.bias, a.out, a.out32, a.relu, U.err};
+    if (conv_tc(t, a.Cout, U.nsm, st)) return;
+  }
   const long nvox = cube(a.No);
   const int grid = (int)((nvox + 16 * CONV_MT * CONV_WARPS - 1) / (16 * CONV_MT * CONV_WARPS));
   switch (a.Cout / 8) {
@@ -570,7 +614,7 @@ static void fwd(UNet& U, int l, Src s0, Src s1, bf16* out, float* out32, int rel
   a.out32 = out32;
   a.out32_ch = 1;
   a.relu = relu;
-  launch_conv(a, st);
+  launch_conv(U, a, st);
 }
 
 // Forward pass on the packed input; output channel 0 in U.out32.
@@ -602,7 +646,7 @@ static void bwd_data(UNet& U, int l, int n_in, float* dIn, cudaStream_t st) {
   a.W = y.wt;  // [27][cin][cout]: rows = input channels, k = output channels
   a.out32 = dIn;
   a.out32_ch = y.cin;
-  launch_conv(a, st);
+  launch_conv(U, a, st);
 }
 
 static void wgrad(UNet& U, int l, Src s0, Src s1, cudaStream_t st) {
@@ -637,12 +681,8 @@ template <typename T>
 __global__ void k_pack_fcg(const T* r, const T* psi, long n, const double* sc, int rr_slot, bf16* in16) {
   const double rr = sc[rr_slot];
   const double rinv = rr > 0.0 ? sqrt((double)n / rr) : 0.0;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    bf16* o = in16 + q * 16;
-    o[0] = __float2bfloat16((float)((double)r[q] * rinv));
-    o[1] = __float2bfloat16((float)psi[q] - 1.f);
-    for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16(0.f);
-  }
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    pack_voxel(in16 + q * 16, (float)((double)r[q] * rinv), (float)psi[q] - 1.f);
 }
 
 // mean-square of a field (two-level, fixed order): part[block] partial sums
@@ -773,8 +813,14 @@ int unet_apply(UNet* U, const T* r, const T* psi, float* z, cudaStream_t st) {
   k_pack_input<T><<<ew(n), 256, 0, st>>>(r, psi, n, rinv, 1.0, U->in16);
   unet_forward(*U, st);
   cudaMemcpyAsync(z, U->out32, n * 4, cudaMemcpyDeviceToDevice, st);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, U->err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   if (tmp) cudaFree(tmp);
+  if (herr) {
+    cudaMemsetAsync(U->err, 0, sizeof(int), st);
+    return FE_ERR_CUDA;
+  }
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
@@ -863,6 +909,7 @@ int unet_train_step(UNet* U, const T* r, const T* e, const T* psi, double lr, do
 
 float* unet_output(UNet* U) { return U->out32; }
 int unet_N(const UNet* U) { return U->N; }
+void unet_set_kernels(UNet* U, int tc) { U->use_tc = tc; }
 
 #define INST(T)                                                                                         \
   template void unet_apply_sc<T>(UNet*, const T*, const T*, const double*, int, cudaStream_t);          \

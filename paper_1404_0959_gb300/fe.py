@@ -73,7 +73,7 @@ EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
            "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
-           "fe_use_plane_streaming", "fe_destroy", "fe_strerror"]
+           "fe_use_plane_streaming", "fe_precond_kernels", "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -107,6 +107,7 @@ def load_library(path=LIB_PATH):
     lib.fe_harvest_pressure.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_int)]
     lib.fe_use_graphs.argtypes = [c_void_p, c_int]
     lib.fe_use_plane_streaming.argtypes = [c_void_p, c_int]
+    lib.fe_precond_kernels.argtypes = [c_void_p, c_int]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
@@ -271,6 +272,10 @@ def fe_harvest_pressure(ctx, b_ptrs, x_ptrs):
 
 def fe_use_graphs(ctx, on=True):
     return _check(lib().fe_use_graphs(ctx, int(bool(on))), "fe_use_graphs")
+
+
+def fe_precond_kernels(ctx, mode):
+    return _check(lib().fe_precond_kernels(ctx, int(mode)), "fe_precond_kernels")
 
 
 def fe_use_plane_streaming(ctx, on=True):
