@@ -55,6 +55,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from profiles/traffic_<workload>.txt (an
+    ncu capture), or None when absent or when the kernel sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % workload)
+    srcs = [os.path.join(ROOT, "paper_1404_0959_gb300", "csrc", f)
+            for f in ("krylov_kernels.cu", "zbulk.cuh", "fe_internal.cuh")]
+    try:
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        digest = h.hexdigest()[:16]
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel:
+                    return float(parts[1]) if parts[2] == digest else None
+    except OSError:
+        return None
+    return None
+
+
 class Clocks:
     """nvidia-smi sampler (200 ms) running during the timed region."""
 
@@ -179,6 +202,50 @@ def time_path(fe, box, cfg, precision, solver, args, stream):
     return out
 
 
+# FLOPs of one network application at N^3 (2 x MACs; 27-tap convolutions over
+# the padded channel counts the kernels compute): e1a, e1b, out at N (16 -> 16),
+# d1 (N/2, 16 -> 32), e2 (N/2, 32 -> 32), d2 (N/4, 32 -> 64), e3 (N/4, 64 -> 64),
+# u2 (N/2, 96 -> 32), u1 (N, 48 -> 16).
+def unet_flops(N):
+    n0, n1, n2 = N ** 3, (N // 2) ** 3, (N // 4) ** 3
+    macs = 27 * (3 * n0 * 16 * 16 + n1 * 16 * 32 + n1 * 32 * 32 + n2 * 32 * 64 + n2 * 64 * 64 +
+                 n1 * 96 * 32 + n0 * 48 * 16)
+    return 2.0 * macs
+
+
+def unet_only(args):
+    """--unet: CUDA-event time of fe_precond_apply on a random residual (He-initialised weights)."""
+    import torch
+    from paper_1404_0959_gb300 import fe, learned
+    from paper_1404_0959_gb300.inputs import WORKLOADS
+    fe.load_library()
+    w = WORKLOADS[WORKLOAD]
+    N = args.N
+    box = dict(N=N, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], mach_rms=w["mach_rms"], k0=w["k0"], seed=0)
+    s = fe.Solver([box], precision=fe.FE_FP32_MIXED, solver=fe.FE_FCG_LEARNED, p_tol=1e-8)
+    s.init_state(0, fe.FE_INIT_SPECTRAL)
+    fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    r = torch.randn(N, N, N, device="cuda", generator=g)
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), z.data_ptr())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), z.data_ptr())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fl = unet_flops(N)
+    print(json.dumps({"metric": "learned-preconditioner network applications/s at %d^3" % N, "value": 1e3 / ms,
+                      "unit": "applications/s", "ms_per_apply": ms, "tflops": fl / ms / 1e9,
+                      "flops_per_apply": fl, "steps": args.steps, "warmup": args.warmup,
+                      "note": "includes the host read of the error flag after every application"}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,8 +265,12 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="host-driven steps in the headline region")
     ap.add_argument("--learn-steps", type=int, default=2, help="steps harvested for training (learned path)")
     ap.add_argument("--learn-iters", type=int, default=60, help="training iterations (learned path)")
+    ap.add_argument("--unet", action="store_true",
+                    help="time only the learned preconditioner's network pass (K applications at N^3)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.unet:
+        return unet_only(args)
 
     from paper_1404_0959_gb300.inputs import WORKLOADS
     cfg = dict(WORKLOADS[WORKLOAD])
@@ -356,7 +427,8 @@ def main():
                                (40 + 4 * nd) * cells * w / 1e9),
                            "parallelism": "replicas" if world > 1 else "single box"},
                 "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                             "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                             "frac": achieved / hbm, "peak_kind": peak_kind,
+                             "traffic": recorded_traffic(kernel, WORKLOAD) if N == 256 else None,
                              "alg_bytes_per_launch": alg_bytes, "launches": prof["target_launches"],
                              "ms_per_launch": per_launch_ms},
                 "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items() if v[1] > 0},

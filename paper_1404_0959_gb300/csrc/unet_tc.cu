@@ -202,13 +202,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_conv_tc(TcConvArgs a) {
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // tiles march in z for a fixed (x segment, row group): consecutive tiles of
+  // a CTA share two of their three z-planes of input rows, so the re-reads hit L2
   auto tile_of = [&](int i, int& x0, int& y0, int& z) {
     const long t = t0 + i;
-    const int xs = (int)(t % nseg);
-    const long r = t / nseg;
-    y0 = R * (int)(r % (No / R));
-    z = (int)(r / (No / R));
-    x0 = 128 * xs;
+    z = (int)(t % No);
+    const long r = t / No;
+    x0 = 128 * (int)(r % nseg);
+    y0 = R * (int)(r / nseg);
   };
   auto fail = [&]() { atomicExch(abort_flag, 1); };
   auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
