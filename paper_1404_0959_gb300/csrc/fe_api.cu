@@ -91,6 +91,7 @@ struct fe_ctx {
   int2* dework = nullptr;
   int2* dbwork = nullptr;   // plane-streaming blocks (box, block of box)
   int nbblocks = 0, bsmem = 0, npart = 0;
+  int ring_ok = 0;          // all N multiples of the 16-byte chunk of the ring kernels
   bool use_bulk = true;     // streamed CG kernel where the boxes allow it
   int unet_tc = 1;          // U-Net stride-1 layers on tcgen05 (1) or warp-level MMA (0)
   int neblocks = 0;
@@ -117,7 +118,7 @@ struct fe_ctx {
   Prof prof;
   Launch L() {
     return Launch{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
-                  prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, use_bulk && nbblocks > 0 ? dbwork : nullptr,
+                  prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
                   nbblocks, bsmem};
   }
 };
@@ -211,6 +212,9 @@ static int set_tiling(fe_ctx* c, int tz) {
     B.etile0 = (int)ework.size();
     for (int q = 0; q < B.entiles; ++q) ework.push_back(make_int2(b, q));
   }
+  c->ring_ok = 1;
+  for (int b = 0; b < c->nb; ++b)
+    if (c->hbox[b].N % (c->fp64 ? 2 : 4)) c->ring_ok = 0;
   // plane-streaming blocks: every box with N in {64, 128, 256, 512}, a
   // persistent grid of the resident blocks per SM x SMs shared out by cells
   std::vector<int2> bwork;

@@ -489,6 +489,7 @@ struct Launch {
   int fourier;    // closure of the context (selects kernel variants)
   int transonic;  // transonic pressure operator
   int nd;         // dust classes
+  int ring_ok;        // every box's N is a multiple of the 16-byte chunk (ring kernels usable)
   const int2* bwork;  // plane-streaming blocks (box, block of box); null: z-marching kernels
   int nbblocks;
   int bsmem;          // dynamic shared memory of the streamed CG kernel

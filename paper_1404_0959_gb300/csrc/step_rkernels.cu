@@ -56,111 +56,61 @@ static bool set_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
 }
 
+template <typename P>
+struct Unparen;
+template <typename P>
+struct Unparen<void(P)> {
+  using type = P;
+};
+#define RING_PROLOGUE(P)                                   \
+  const TileXYZ t = tile_xyz(boxes, work);                 \
+  const BoxDev& B = boxes[t.box];                          \
+  const RGeom<T> G(t.x0, t.y0, B.N);                       \
+  const int tid = threadIdx.x + TX * threadIdx.y;          \
+  extern __shared__ __align__(16) unsigned char rsm[];     \
+  typename Unparen<void(P)>::type R;                       \
+  R.init(rsm, t.k0, t.kend)
+
 // ---- correction (symmetric operator) ----------------------------------------------------------
 // p^k = p^{k-1} + x staged as the sum of two rings; fluxes phi^k = phi* - dt G2 x,
 // u^k = HbyA - dt/rho^{k-1} Gc p^k, rho^k = rho^n - dt/2 (div phi^n + D phi^k);
 // FP64 path: ||b - M x||^2 for the reported residual.
-constexpr int kCorrA = kA1;
 template <typename T, bool MIXED>
-struct CorrRing {
-  static constexpr int A = kCorrA, NCEN = MIXED ? 6 : 8;
-  static constexpr int elems = 2 * ZSlots<A>::NS * kZHW + 3 * ZSlots<A>::NF * kZHW + NCEN * ZSlots<A>::NC * NTHR;
-  static constexpr int bytes = elems * (int)sizeof(T);
-};
+using CorrPlan = RingPlan<T, kA1, 2, 3, MIXED ? 6 : 8>;  // p^{k-1}, x | phi* | rho^n, rho^{k-1}, HbyA0..2, D phi^n [, psi, b]
 
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2* work, double* part, int s, int rhop,
                                                 int pp, int pnew, int kset, int kidx) {
-  using CR = CorrRing<T, MIXED>;
-  constexpr int A = CR::A;
-  using SL = ZSlots<A>;
-  const TileXYZ t = tile_xyz(boxes, work);
-  const BoxDev& B = boxes[t.box];
-  const ZGeom<2> G(t.x0, t.y0, B.N);
-  const int tid = threadIdx.x + TX * threadIdx.y;
-  extern __shared__ __align__(16) unsigned char rsm[];
-  T* base = reinterpret_cast<T*>(rsm);
-  T* r_pp = base;
-  T* r_x = r_pp + SL::NS * kZHW;
-  T* r_ps = r_x + SL::NS * kZHW;  // 3 face rings
-  T* r_c = r_ps + 3 * SL::NF * kZHW;  // centre rings: rho, rk, hb0..2, divphi [, psi, b]
-  const T* g_pp = Fr<T>(B, pp);
-  const T* g_x = Fr<T>(B, K_X);
-  const T* g_ps[3] = {Fr<T>(B, W_PS0), Fr<T>(B, W_PS1), Fr<T>(B, W_PS2)};
-  const T* g_c[8] = {Fr<T>(B, S(s, F_RHO)), Fr<T>(B, rhop), Fr<T>(B, W_HB0), Fr<T>(B, W_HB1),
-                     Fr<T>(B, W_HB2),      Fr<T>(B, W_DIVPHI), Fr<T>(B, W_PSI), Fr<T>(B, K_B)};
-  T* rk = Fr<T>(B, rhop);
+  constexpr int NC = MIXED ? 6 : 8;
+  RING_PROLOGUE((CorrPlan<T, MIXED>));
+  R.gs[0] = Fr<T>(B, pp);
+  R.gs[1] = Fr<T>(B, K_X);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, W_PS0 + d);
+  R.gc[0] = Fr<T>(B, S(s, F_RHO));
+  R.gc[1] = Fr<T>(B, rhop);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[2 + m] = Fr<T>(B, W_HB0 + m);
+  R.gc[5] = Fr<T>(B, W_DIVPHI);
+  if (NC == 8) {
+    R.gc[6 % NC] = Fr<T>(B, W_PSI);
+    R.gc[7 % NC] = Fr<T>(B, K_B);
+  }
+  T* rk = Fr<T>(B, rhop);  // rho^{k-1} in (through the ring), rho^k out (own cell only)
   T* __restrict__ pn = Fr<T>(B, pnew);
   T* __restrict__ phk[3] = {Fr<T>(B, S(kset, F_PHI0)), Fr<T>(B, S(kset, F_PHI1)), Fr<T>(B, S(kset, F_PHI2))};
   T* __restrict__ uk[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
-  const SL sl{t.k0};
-  const int nk = t.kend - t.k0;
-  // copies of the planes needed first: stencil k0-2..k0+2, faces k0-1..k0, centre k0
-  auto issue = [&](int q) {  // group q >= 1: stencil k0+2+q, face k0+q, centre k0+q (within range)
-    const int ms = t.k0 + 2 + q, mf = t.k0 + q, mc = t.k0 + q;
-    if (ms <= t.kend + 1) {
-      const int w = G.wrapz(ms);
-      zr_issue_halo(G, g_pp, r_pp + sl.s(ms) * kZHW, w);
-      zr_issue_halo(G, g_x, r_x + sl.s(ms) * kZHW, w);
-    }
-    if (mf < t.kend) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) zr_issue_halo(G, g_ps[d], r_ps + (d * SL::NF + sl.f(mf)) * kZHW, mf);
-    }
-    if (mc < t.kend) {
-#pragma unroll
-      for (int j = 0; j < CR::NCEN; ++j) zr_issue_centre(G, g_c[j], r_c + (j * SL::NC + sl.c(mc)) * NTHR, tid, mc);
-    }
-  };
-  for (int m = t.k0 - 2; m <= t.k0 + 2; ++m) {
-    const int w = G.wrapz(m);
-    zr_issue_halo(G, g_pp, r_pp + sl.s(m) * kZHW, w);
-    zr_issue_halo(G, g_x, r_x + sl.s(m) * kZHW, w);
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    zr_issue_halo(G, g_ps[d], r_ps + (d * SL::NF + sl.f(t.k0 - 1)) * kZHW, G.wrapz(t.k0 - 1));
-    zr_issue_halo(G, g_ps[d], r_ps + (d * SL::NF + sl.f(t.k0)) * kZHW, t.k0);
-  }
-#pragma unroll
-  for (int j = 0; j < CR::NCEN; ++j) zr_issue_centre(G, g_c[j], r_c + (j * SL::NC + sl.c(t.k0)) * NTHR, tid, t.k0);
-  cp_async_commit();
-#pragma unroll
-  for (int q = 1; q < A; ++q) {
-    issue(q);
-    cp_async_commit();
-  }
   double rr = 0.0;
-  for (int i = 0; i < nk; ++i) {
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    cp_async_wait<A - 1>();
-    __syncthreads();
-    issue(A + i);
-    cp_async_commit();
+    R.next(G, i);
     if (!G.active) continue;
-    ZView<T> vp, vx;
-    vp.csm = vx.csm = G.csm;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      vp.p[j] = r_pp + sl.s(k - 2 + j) * kZHW;
-      vx.p[j] = r_x + sl.s(k - 2 + j) * kZHW;
-    }
+    const ZView<T> vp = R.view(0, k, G), vx = R.view(1, k, G);
     const ZView2<T> pk{vp, vx};
     T psp[3], psm[3];
-    {
-      const T* f0 = r_ps + (0 * SL::NF + sl.f(k)) * kZHW;
-      const T* f1 = r_ps + (1 * SL::NF + sl.f(k)) * kZHW;
-      const T* f2 = r_ps + (2 * SL::NF + sl.f(k)) * kZHW;
-      const T* f2m = r_ps + (2 * SL::NF + sl.f(k - 1)) * kZHW;
-      psp[0] = f0[G.csm];
-      psm[0] = f0[G.csm - 1];
-      psp[1] = f1[G.csm];
-      psm[1] = f1[G.csm - ZGeom<2>::W];
-      psp[2] = f2[G.csm];
-      psm[2] = f2m[G.csm];
-    }
-    auto cen = [&](int j) { return r_c[(j * SL::NC + sl.c(k)) * NTHR + tid]; };
+    R.faces(0, k, G, psp, psm);
     const int c = G.col + G.plane(k);
     const T xc = vx.c();
     T dsum = T(0), lap = T(0);
@@ -173,14 +123,14 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
       phk[d][c] = fp;
       dsum += fp - fm;
     }
-    const T dtr = dt / cen(1);
+    const T dtr = dt / R.cen(1, k, tid);
     pn[c] = pk.c();
 #pragma unroll
-    for (int m = 0; m < 3; ++m) uk[m][c] = cen(2 + m) - dtr * (zGc_h(pk, G, m) * ih);
-    rk[c] = cen(0) - T(0.5) * dt * (cen(5) + dsum * ih);
+    for (int m = 0; m < 3; ++m) uk[m][c] = R.cen(2 + m, k, tid) - dtr * (zGc_h(pk, G, m) * ih);
+    rk[c] = R.cen(0, k, tid) - T(0.5) * dt * (R.cen(5, k, tid) + dsum * ih);
     if (!MIXED) {
-      const T Mx = cen(6) * xc * idt - T(0.5) * dt * lap * ih * ih;
-      const double r = (double)cen(7) - (double)Mx;
+      const T Mx = R.cen(6 % NC, k, tid) * xc * idt - T(0.5) * dt * lap * ih * ih;
+      const double r = (double)R.cen(7 % NC, k, tid) - (double)Mx;
       rr += r * r;
     }
   }
@@ -201,23 +151,6 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
   }
 }
 
-
-template <typename P>
-struct Unparen;
-template <typename P>
-struct Unparen<void(P)> {
-  using type = P;
-};
-#define RING_PROLOGUE(P)                                   \
-  const TileXYZ t = tile_xyz(boxes, work);                 \
-  const BoxDev& B = boxes[t.box];                          \
-  const ZGeom<2> G(t.x0, t.y0, B.N);                       \
-  const int tid = threadIdx.x + TX * threadIdx.y;          \
-  extern __shared__ __align__(16) unsigned char rsm[];     \
-  typename Unparen<void(P)>::type R;                       \
-  R.init(rsm, t.k0, t.kend)
-
-// ---- predictor ------------------------------------------------------------------------------------
 template <typename T>
 using PredPlan = RingPlan<T, kA, 5, 3, 1>;  // u0..2, div, p | phi | rho
 template <typename T>
@@ -239,10 +172,10 @@ __global__ void __launch_bounds__(NTHR) kr_pred(const BoxDev* boxes, const int2*
   T* __restrict__ us[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
   const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
-  R.prologue(G, tid);
+  R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    R.next(G, tid, i);
+    R.next(G, i);
     if (!G.active) continue;
     const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
     const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
@@ -291,10 +224,10 @@ __global__ void __launch_bounds__(NTHR) kr_asm(const BoxDev* boxes, const int2* 
   for (int m = 0; m < 3; ++m) R.gc[5 + m] = Fr<T>(B, W_RN0 + m);
   T* __restrict__ hb[3] = {Fr<T>(B, W_HB0), Fr<T>(B, W_HB1), Fr<T>(B, W_HB2)};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
-  R.prologue(G, tid);
+  R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    R.next(G, tid, i);
+    R.next(G, i);
     if (!G.active) continue;
     const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
     const ZView<T> div = R.view(3, k, G);
@@ -327,10 +260,10 @@ __global__ void __launch_bounds__(NTHR) kr_accel(const BoxDev* boxes, const int2
   R.gc[0] = Fr<T>(B, S(kset, F_RHO));
   T* __restrict__ a[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
   const T ih = (T)B.ih, mu = (T)B.mu;
-  R.prologue(G, tid);
+  R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    R.next(G, tid, i);
+    R.next(G, i);
     if (!G.active) continue;
     const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
     const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
@@ -367,10 +300,10 @@ __global__ void __launch_bounds__(NTHR) kr_fluxn(const BoxDev* boxes, const int2
     taup[j] = (T)B.tau_p[j];
     fyn[j] = Fr<T>(B, W_FYN0 + j);
   }
-  R.prologue(G, tid);
+  R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    R.next(G, tid, i);
+    R.next(G, i);
     if (!G.active) continue;
     const ZView<T> rho = R.view(0, k, G);
     const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
@@ -431,10 +364,10 @@ __global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2*
   T* __restrict__ pout = Fr<T>(B, S(kset, F_P));
   SumAcc<T> amass, abad;
   DotAcc<T> aen, ady[ND];
-  R.prologue(G, tid);
+  R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
-    R.next(G, tid, i);
+    R.next(G, i);
     if (!G.active) continue;
     const ZView<T> rho = R.view(0, k, G);
     const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
@@ -499,8 +432,8 @@ __global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2*
 #define RGRID(bytes) L.nblocks, dim3(TX, TY), (bytes), L.st
 template <typename T>
 int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed) {
-  if (!ring_ready<T>(mixed ? RK_CORR_M : RK_CORR_F)) return 0;
-  constexpr int bm = CorrRing<T, true>::bytes, bf = CorrRing<T, false>::bytes;
+  if (!L.ring_ok || !ring_ready<T>(mixed ? RK_CORR_M : RK_CORR_F)) return 0;
+  constexpr int bm = CorrPlan<T, true>::bytes, bf = CorrPlan<T, false>::bytes;
   if (mixed)
     FE_LAUNCH(L, KID_CORR, (kr_corr<T, true><<<RGRID(bm)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
   else
@@ -510,25 +443,25 @@ int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, i
 
 template <typename T>
 int rlaunch_pred(const Launch& L, int s, int kset) {
-  if (!ring_ready<T>(RK_PRED)) return 0;
+  if (!L.ring_ok || !ring_ready<T>(RK_PRED)) return 0;
   FE_LAUNCH(L, KID_PRED, (kr_pred<T><<<RGRID(PredPlan<T>::bytes)>>>(L.boxes, L.work, s, kset)));
   return 1;
 }
 template <typename T>
 int rlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
-  if (!ring_ready<T>(RK_ASM)) return 0;
+  if (!L.ring_ok || !ring_ready<T>(RK_ASM)) return 0;
   FE_LAUNCH(L, KID_ASM, (kr_asm<T><<<RGRID(AsmPlan<T>::bytes)>>>(L.boxes, L.work, s, up0, php0, rhop)));
   return 1;
 }
 template <typename T>
 int rlaunch_accel(const Launch& L, int kset, int pk) {
-  if (!ring_ready<T>(RK_ACCEL)) return 0;
+  if (!L.ring_ok || !ring_ready<T>(RK_ACCEL)) return 0;
   FE_LAUNCH(L, KID_ACCEL, (kr_accel<T><<<RGRID(AccelPlan<T>::bytes)>>>(L.boxes, L.work, kset, pk)));
   return 1;
 }
 template <typename T>
 int rlaunch_fluxn(const Launch& L, int s, int nd) {
-  if (nd < 1 || nd > 3 || !ring_ready<T>(RK_FLUX1 + nd - 1)) return 0;
+  if (nd < 1 || nd > 3 || !L.ring_ok || !ring_ready<T>(RK_FLUX1 + nd - 1)) return 0;
   switch (nd) {
     case 1: FE_LAUNCH(L, KID_FLUXN, (kr_fluxn<T, 1><<<RGRID((FluxPlan<T, 1>::bytes))>>>(L.boxes, L.work, s))); break;
     case 2: FE_LAUNCH(L, KID_FLUXN, (kr_fluxn<T, 2><<<RGRID((FluxPlan<T, 2>::bytes))>>>(L.boxes, L.work, s))); break;
@@ -539,7 +472,7 @@ int rlaunch_fluxn(const Launch& L, int s, int nd) {
 }
 template <typename T>
 int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd) {
-  if (nd < 1 || nd > 3 || !ring_ready<T>(RK_DUST1 + nd - 1)) return 0;
+  if (nd < 1 || nd > 3 || !L.ring_ok || !ring_ready<T>(RK_DUST1 + nd - 1)) return 0;
   switch (nd) {
     case 1:
       FE_LAUNCH(L, KID_DUST, (kr_dust<T, 1><<<RGRID((DustPlan<T, 1>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
@@ -564,8 +497,8 @@ int rprepare() {
   if (dev < 0) return 0;
   unsigned ok = 0;
   auto set = [&](int bit, bool accepted) { ok |= accepted ? 1u << bit : 0u; };
-  set(RK_CORR_M, set_smem(kr_corr<T, true>, CorrRing<T, true>::bytes));
-  set(RK_CORR_F, set_smem(kr_corr<T, false>, CorrRing<T, false>::bytes));
+  set(RK_CORR_M, set_smem(kr_corr<T, true>, CorrPlan<T, true>::bytes));
+  set(RK_CORR_F, set_smem(kr_corr<T, false>, CorrPlan<T, false>::bytes));
   set(RK_PRED, set_smem(kr_pred<T>, PredPlan<T>::bytes));
   set(RK_ASM, set_smem(kr_asm<T>, AsmPlan<T>::bytes));
   set(RK_ACCEL, set_smem(kr_accel<T>, AccelPlan<T>::bytes));

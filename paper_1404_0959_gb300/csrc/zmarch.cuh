@@ -162,9 +162,9 @@ __device__ __forceinline__ auto zDG4_h2(const FV& f, const GT& G, int d) -> decl
 }
 
 // L_m = -D(phi I4 u_m) + mu (sum_d D G4_d u_m + Gc_m(div)/3), and the viscous part
-template <typename T, typename FV>
+template <typename T, typename FV, typename GT>
 __device__ __forceinline__ void zeval_L(const FV (&u)[3], const FV& div, const T (&php)[3], const T (&phm)[3],
-                                        const ZGeom<2>& G, T ih, T mu, T (&L)[3], T (&visc)[3]) {
+                                        const GT& G, T ih, T mu, T (&L)[3], T (&visc)[3]) {
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T conv = T(0), lap = T(0);

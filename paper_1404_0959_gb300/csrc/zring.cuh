@@ -1,9 +1,9 @@
 // zring.cuh -- z-marching with asynchronous copies into shared-memory rings.
 //
-// Same 32 x 8 column tiles and radius-2 halo geometry as zmarch.cuh (ZGeom<2>),
-// but every streamed plane -- the z-neighbours included -- lives in a shared
-// ring filled by cp.async (global -> shared without registers), A planes ahead
-// of the plane being computed.  Three ring kinds:
+// Same 32 x 8 column tiles as zmarch.cuh, but every streamed plane -- the
+// z-neighbours included -- lives in a shared ring filled by 16-byte cp.async
+// chunks (global -> shared without registers), A planes ahead of the plane
+// being computed.  Three ring kinds:
 //   stencil field  planes k-2 .. k+2 in use           (5 + A slots, tile + halo)
 //   face array     planes k-1 .. k (own, x-1, y-1)    (2 + A slots, tile + halo)
 //   centre field   plane k, own cells                  (1 + A slots, tile only)
@@ -30,19 +30,70 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-constexpr int kZHW = ZGeom<2>::H * ZGeom<2>::W;  // tile + radius-2 halo, elements
-
-// Plane m of a tile-with-halo field into a ring slot.
-template <typename T>
-__device__ __forceinline__ void zr_issue_halo(const ZGeom<2>& G, const T* g, T* slot, int m) {
-  const int pl = G.plane(m);
-  cp_async(slot + G.csm, g + G.col + pl);
-  if (G.hcol >= 0) cp_async(slot + G.hsm, g + G.hcol + pl);
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-// Plane m of a centre-only field (own cells) into a ring slot.
+
+// Tile geometry of the ring kernels: 32 x 8 columns, y-halo 2, x-halo XH (2
+// cells rounded up to one 16-byte chunk), copied in 16-byte chunks: one chunk
+// per thread and field for the tile with its star halo (corners are not
+// needed), one per thread for a centre-only plane.  Needs N % CE == 0 so no
+// chunk straddles the periodic seam; wrapped columns beyond a ragged box edge
+// hold the periodic continuation as in ZGeom.
 template <typename T>
-__device__ __forceinline__ void zr_issue_centre(const ZGeom<2>& G, const T* g, T* slot, int tid, int m) {
-  cp_async(slot + tid, g + G.col + G.plane(m));
+struct RGeom {
+  static constexpr int CE = 16 / (int)sizeof(T);  // cells per chunk
+  static constexpr int XH = CE > 2 ? CE : 2;      // x-halo
+  static constexpr int W = TX + 2 * XH, H = TY + 4, HW = H * W;
+  static constexpr int ROWC = W / CE, MIDC = TX / CE;
+  static constexpr int NCH = TY * ROWC + 4 * MIDC;  // chunks of a tile-with-halo plane
+  static constexpr int NCC = TX * TY / CE;          // chunks of a centre plane
+  static_assert(NCH <= NTHR && NCC <= NTHR, "one chunk per thread");
+  int N, NN, col, csm;
+  bool active;
+  int ch_g, ch_s;  // this thread's halo-plane chunk: global column (-1: none), shared offset
+  int cc_g, cc_s;  // this thread's centre-plane chunk
+  __device__ __forceinline__ static int wrap(int v, int n) { return ((v % n) + n) % n; }
+  __device__ __forceinline__ RGeom(int x0, int y0, int N_) {
+    N = N_;
+    NN = N * N;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    active = (x0 + tx < N) && (y0 + ty < N);
+    col = wrap(x0 + tx, N) + N * wrap(y0 + ty, N);
+    csm = (ty + 2) * W + tx + XH;
+    ch_g = cc_g = -1;
+    ch_s = cc_s = 0;
+    if (tid < NCH) {
+      int lx, ly;
+      if (tid < TY * ROWC) {
+        ly = tid / ROWC;
+        lx = (tid % ROWC) * CE - XH;
+      } else {
+        const int h = tid - TY * ROWC, hr = h / MIDC;
+        ly = hr < 2 ? hr - 2 : TY + hr - 2;
+        lx = (h % MIDC) * CE;
+      }
+      ch_g = wrap(x0 + lx, N) + N * wrap(y0 + ly, N);
+      ch_s = (ly + 2) * W + lx + XH;
+    }
+    if (tid < NCC) {
+      const int row = tid / (TX / CE), x = (tid % (TX / CE)) * CE;
+      cc_g = wrap(x0 + x, N) + N * wrap(y0 + row, N);
+      cc_s = row * TX + x;
+    }
+  }
+  __device__ __forceinline__ int plane(int k) const { return NN * k; }
+  __device__ __forceinline__ int wrapz(int k) const { return k < 0 ? k + N : (k >= N ? k - N : k); }
+};
+
+// Plane m of a tile-with-halo field / of a centre-only field into a ring slot.
+template <typename T>
+__device__ __forceinline__ void zr_issue_halo(const RGeom<T>& G, const T* g, T* slot, int m) {
+  if (G.ch_g >= 0) cp_async16(slot + G.ch_s, g + G.ch_g + G.plane(m));
+}
+template <typename T>
+__device__ __forceinline__ void zr_issue_centre(const RGeom<T>& G, const T* g, T* slot, int m) {
+  if (G.cc_g >= 0) cp_async16(slot + G.cc_s, g + G.cc_g + G.plane(m));
 }
 
 // Stencil view of one field at plane k: five ring slots k-2 .. k+2.
@@ -50,9 +101,10 @@ template <typename T>
 struct ZView {
   const T* p[5];
   int csm;
-  __device__ __forceinline__ T at(const ZGeom<2>&, int d, int s) const {
+  template <typename GT>
+  __device__ __forceinline__ T at(const GT&, int d, int s) const {
     if (d == 2) return p[2 + s][csm];
-    return d == 0 ? p[2][csm + s] : p[2][csm + s * ZGeom<2>::W];
+    return d == 0 ? p[2][csm + s] : p[2][csm + s * RGeom<T>::W];
   }
   __device__ __forceinline__ T c() const { return p[2][csm]; }
 };
@@ -60,7 +112,8 @@ struct ZView {
 template <typename T>
 struct ZView2 {
   ZView<T> a, b;
-  __device__ __forceinline__ T at(const ZGeom<2>& G, int d, int s) const { return a.at(G, d, s) + b.at(G, d, s); }
+  template <typename GT>
+  __device__ __forceinline__ T at(const GT& G, int d, int s) const { return a.at(G, d, s) + b.at(G, d, s); }
   __device__ __forceinline__ T c() const { return a.c() + b.c(); }
 };
 
@@ -81,7 +134,9 @@ struct ZSlots {
 template <typename T, int A, int NSF, int NFF, int NCF>
 struct RingPlan {
   using SL = ZSlots<A>;
-  static constexpr int elems = NSF * SL::NS * kZHW + NFF * SL::NF * kZHW + NCF * SL::NC * NTHR;
+  using G_ = RGeom<T>;
+  static constexpr int HW = G_::HW;
+  static constexpr int elems = NSF * SL::NS * HW + NFF * SL::NF * HW + NCF * SL::NC * NTHR;
   static constexpr int bytes = (elems > 0 ? elems : 1) * (int)sizeof(T);
   T* rs;
   T* rf;
@@ -94,72 +149,72 @@ struct RingPlan {
   int ncf = NCF;  // centre fields copied (the first ncf of gc)
   __device__ __forceinline__ void init(unsigned char* smem, int k0_, int kend_) {
     rs = reinterpret_cast<T*>(smem);
-    rf = rs + NSF * SL::NS * kZHW;
-    rc = rf + NFF * SL::NF * kZHW;
+    rf = rs + NSF * SL::NS * HW;
+    rc = rf + NFF * SL::NF * HW;
     k0 = k0_;
     kend = kend_;
     sl.k0 = k0_;
   }
-  __device__ __forceinline__ void stencil_plane(const ZGeom<2>& G, int m) {
+  __device__ __forceinline__ void stencil_plane(const G_& G, int m) {
     const int w = G.wrapz(m);
 #pragma unroll
-    for (int f = 0; f < NSF; ++f) zr_issue_halo(G, gs[f], rs + (f * SL::NS + sl.s(m)) * kZHW, w);
+    for (int f = 0; f < NSF; ++f) zr_issue_halo(G, gs[f], rs + (f * SL::NS + sl.s(m)) * HW, w);
   }
-  __device__ __forceinline__ void face_plane(const ZGeom<2>& G, int m) {
+  __device__ __forceinline__ void face_plane(const G_& G, int m) {
     const int w = G.wrapz(m);
 #pragma unroll
-    for (int f = 0; f < NFF; ++f) zr_issue_halo(G, gf[f], rf + (f * SL::NF + sl.f(m)) * kZHW, w);
+    for (int f = 0; f < NFF; ++f) zr_issue_halo(G, gf[f], rf + (f * SL::NF + sl.f(m)) * HW, w);
   }
-  __device__ __forceinline__ void centre_plane(const ZGeom<2>& G, int tid, int m) {
+  __device__ __forceinline__ void centre_plane(const G_& G, int m) {
 #pragma unroll
     for (int f = 0; f < NCF; ++f)
-      if (f < ncf) zr_issue_centre(G, gc[f], rc + (f * SL::NC + sl.c(m)) * NTHR, tid, m);
+      if (f < ncf) zr_issue_centre(G, gc[f], rc + (f * SL::NC + sl.c(m)) * NTHR, m);
   }
   // group q >= 1: stencil plane k0+2+q, face and centre planes k0+q (skipped beyond the tile)
-  __device__ __forceinline__ void issue(const ZGeom<2>& G, int tid, int q) {
+  __device__ __forceinline__ void issue(const G_& G, int q) {
     if (k0 + 2 + q <= kend + 1) stencil_plane(G, k0 + 2 + q);
     if (k0 + q < kend) {
       face_plane(G, k0 + q);
-      centre_plane(G, tid, k0 + q);
+      centre_plane(G, k0 + q);
     }
   }
   // group 0 (stencil k0-2..k0+2, faces k0-1..k0, centre k0) and groups 1..A-1
-  __device__ __forceinline__ void prologue(const ZGeom<2>& G, int tid) {
+  __device__ __forceinline__ void prologue(const G_& G) {
     for (int m = k0 - 2; m <= k0 + 2; ++m) stencil_plane(G, m);
     face_plane(G, k0 - 1);
     face_plane(G, k0);
-    centre_plane(G, tid, k0);
+    centre_plane(G, k0);
     cp_async_commit();
 #pragma unroll
     for (int q = 1; q < A; ++q) {
-      issue(G, tid, q);
+      issue(G, q);
       cp_async_commit();
     }
   }
   // before plane k = k0 + i: wait for its copies, make them visible, start plane group A + i
-  __device__ __forceinline__ void next(const ZGeom<2>& G, int tid, int i) {
+  __device__ __forceinline__ void next(const G_& G, int i) {
     cp_async_wait<A - 1>();
     __syncthreads();
-    issue(G, tid, A + i);
+    issue(G, A + i);
     cp_async_commit();
   }
-  __device__ __forceinline__ ZView<T> view(int f, int k, const ZGeom<2>& G) const {
+  __device__ __forceinline__ ZView<T> view(int f, int k, const G_& G) const {
     ZView<T> v;
     v.csm = G.csm;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) v.p[j] = rs + (f * SL::NS + sl.s(k - 2 + j)) * kZHW;
+    for (int j = 0; j < 5; ++j) v.p[j] = rs + (f * SL::NS + sl.s(k - 2 + j)) * HW;
     return v;
   }
   // faces f0, f0+1, f0+2 (x, y, z arrays): values at the +1/2 and -1/2 faces of the cell
-  __device__ __forceinline__ void faces(int f0, int k, const ZGeom<2>& G, T (&plus)[3], T (&minus)[3]) const {
-    const T* fx = rf + (f0 * SL::NF + sl.f(k)) * kZHW;
-    const T* fy = rf + ((f0 + 1) * SL::NF + sl.f(k)) * kZHW;
-    const T* fz = rf + ((f0 + 2) * SL::NF + sl.f(k)) * kZHW;
-    const T* fzm = rf + ((f0 + 2) * SL::NF + sl.f(k - 1)) * kZHW;
+  __device__ __forceinline__ void faces(int f0, int k, const G_& G, T (&plus)[3], T (&minus)[3]) const {
+    const T* fx = rf + (f0 * SL::NF + sl.f(k)) * HW;
+    const T* fy = rf + ((f0 + 1) * SL::NF + sl.f(k)) * HW;
+    const T* fz = rf + ((f0 + 2) * SL::NF + sl.f(k)) * HW;
+    const T* fzm = rf + ((f0 + 2) * SL::NF + sl.f(k - 1)) * HW;
     plus[0] = fx[G.csm];
     minus[0] = fx[G.csm - 1];
     plus[1] = fy[G.csm];
-    minus[1] = fy[G.csm - ZGeom<2>::W];
+    minus[1] = fy[G.csm - G_::W];
     plus[2] = fz[G.csm];
     minus[2] = fzm[G.csm];
   }
