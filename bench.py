@@ -42,6 +42,8 @@ def alg_words(kernel, nd):
         "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
         # refinement (field word = 4 bytes; x64 counts as two words)
         "mix_residual": 6, "mix_accum": 5, "mix_finish": 3, "commit": 0,
+        # fused refinement: pairs read and written, x, pd, b, psi, dinv read, r written
+        "refine": 10,
     }
     return table[kernel]
 
@@ -315,7 +317,7 @@ def main():
     # untimed pass: per-kernel device time over one step, one kernel id at a time
     names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir",
              "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "corr", "accel", "dust", "mix_residual", "mix_accum",
-             "mix_finish", "commit"]
+             "refine", "mix_finish", "commit"]
     share = {}
     for k in ([] if args.no_breakdown else names):
         s.profile_start(k)

@@ -71,7 +71,7 @@ static const char* kKernelNames[] = {
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
     "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec",
-    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "unet", "other"};
+    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "other"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
 static_assert(KID_COUNT <= FE_PROFILE_MAX_KERNELS, "profile counters");
 
@@ -161,6 +161,7 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   // second CG direction buffer (the learned solver's harvest runs plain CG)
   if (c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_PP, e});
   if (!c->fp64) plan.push_back({K_X64, 8});
+  if (!c->fp64 && c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_X64B, 8});
 }
 
 static int validate(const fe_params* p) {
@@ -558,9 +559,57 @@ static int inner_solve(fe_ctx* c, int maxit, int key) {
 // solve in FP64 mode; in mixed mode FP64 iterative refinement (residual
 // b - M x64 in FP64, inner solves in FP32, x64 += x) until the FP64 residual
 // meets the tolerance, then x = (float) x64.
+// Mixed precision with the fused plain-CG iteration: the refinement boundary
+// (last direction, pair accumulation, double-float residual, next start) is
+// one kernel.
+static bool fused_refine(const fe_ctx* c) {
+  return !c->fp64 && c->prm.solver == FE_PCG_JACOBI && !c->prm.transonic && !c->harvest_b &&
+         c->hbox[0].f[K_PP] != nullptr && c->hbox[0].f[K_X64B] != nullptr;
+}
+
+// Fused CG iterations of an already started solve (host-driven, batched as in krylov()).
+template <typename T>
+static int cg_iterate(fe_ctx* c, int maxit, int key) {
+  Launch L = c->L();
+  int it = 0;
+  const int batch = c->hint[key] > 1 ? c->hint[key] - 1 : 1;
+  while (true) {
+    if (it > 0 || batch == 1) {
+      CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (*c->hactive == 0 || it >= maxit) break;
+    }
+    const int n = it == 0 ? batch : 1;
+    for (int q = 0; q < n && it < maxit; ++q, ++it) launch_cg_fused<T>(L);
+  }
+  c->hint[key] = it;
+  return FE_OK;
+}
+
+template <typename T>
+static int refine_solve(fe_ctx* c) {
+  Launch L = c->L();
+  CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
+  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
+  launch_mix_first_init<T>(L, c->douter);
+  for (int outer = 0; outer < 8; ++outer) {
+    CK(cudaMemcpyAsync(c->hactive, c->douter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (*c->hactive == 0) break;
+    int rc = cg_iterate<T>(c, c->prm.p_maxit, 1 + outer);
+    if (rc != FE_OK) return rc;
+    CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
+    launch_refine<T>(L, c->douter);
+  }
+  launch_mix_finish_pp<T>(L);
+  CK(cudaGetLastError());
+  return FE_OK;
+}
+
 template <typename T>
 static int pressure_solve(fe_ctx* c) {
   if (c->fp64) return inner_solve<T>(c, c->prm.p_maxit, 0);
+  if (fused_refine(c)) return refine_solve<T>(c);
   Launch L = c->L();
   CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
   launch_mix_residual<T>(L, 1, c->douter);
@@ -679,6 +728,34 @@ static int pressure_graph(fe_ctx* c) {
   cudaStream_t cs = c->cap[0], bs = c->cap[1];
   Launch L = c->L();
   L.st = cs;
+  if (fused_refine(c)) {
+    CK(cudaMemsetAsync(c->douter, 0, sizeof(int), cs));
+    CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), cs));
+    launch_mix_first_init<T>(L, c->douter);
+    CK(cudaMemsetAsync(c->dloop + 3, 0, sizeof(int), cs));
+    cudaGraphConditionalHandle ho, hi;
+    int rc = while_begin(cs, bs, &ho);  // refinement steps
+    if (rc != FE_OK) return rc;
+    cudaStream_t is = c->cap[2];
+    CK(cudaMemsetAsync(c->dloop + 1, 0, sizeof(int), bs));
+    rc = while_begin(bs, is, &hi);  // fused CG iterations of one inner solve
+    if (rc != FE_OK) return rc;
+    Launch Li = L;
+    Li.st = is;
+    launch_cg_fused<T>(Li);
+    k_loop_cond<<<1, 1, 0, is>>>(hi, c->dactive, c->dloop + 1, c->prm.p_maxit + 1);
+    rc = while_end(is);
+    if (rc != FE_OK) return rc;
+    Launch Lb = L;
+    Lb.st = bs;
+    CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), bs));
+    launch_refine<T>(Lb, c->douter);
+    k_loop_cond<<<1, 1, 0, bs>>>(ho, c->douter, c->dloop + 3, 8);
+    rc = while_end(bs);
+    if (rc != FE_OK) return rc;
+    launch_mix_finish_pp<T>(L);
+    return FE_OK;
+  }
   CK(cudaMemsetAsync(c->douter, 0, sizeof(int), cs));
   launch_mix_residual<T>(L, 1, c->douter);
   CK(cudaMemsetAsync(c->dloop + 3, 0, sizeof(int), cs));

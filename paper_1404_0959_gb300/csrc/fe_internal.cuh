@@ -51,6 +51,7 @@ enum WorkSlot {
   K_RHAT, K_V, K_S, K_T,  // BiCGStab
   K_Z, K_PP, K_QP,        // flexible CG: preconditioned r, previous direction and its image
   K_X64,                  // double accumulator (mixed precision refinement)
+  K_X64B,                 // its ping-pong partner (fused refinement of plain CG)
   K_B64,                  // double right-hand side (mixed precision refinement)
   K_AUX,                  // scratch (diagnostics, user solve)
   NSLOT
@@ -469,7 +470,7 @@ enum KernelId {
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
   KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
-  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_UNET, KID_OTHER, KID_COUNT
+  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_OTHER, KID_COUNT
 };
 
 struct Prof;  // defined in fe_api.cu
@@ -522,6 +523,9 @@ template <typename V> void launch_cg_matvec(const Launch& L);
 template <typename V> void launch_cg_update(const Launch& L);
 template <typename V> void launch_cg_fused(const Launch& L);   // symmetric operator: dir + matvec, then update
 template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
+template <typename V> void launch_mix_first_init(const Launch& L, int* outer_active);  // fused refinement: start
+template <typename V> void launch_refine(const Launch& L, int* outer_active);          // fused refinement: boundary
+template <typename V> void launch_mix_finish_pp(const Launch& L);  // final x from the ping-ponged pairs
 // PISO kernels on asynchronous-copy rings (return 0: not launched, use the z-marching kernel)
 template <typename V> int rprepare();  // shared-memory limits of the ring kernels on the current device
 template <typename V> int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed);

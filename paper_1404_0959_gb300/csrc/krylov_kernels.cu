@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int
       B.sc[SC_BETA] = 0.0;
       bool zero = !(res[1] > 0.0);
       B.sc[SC_DONE] = zero ? 1.0 : 0.0;
-      B.sc[SC_CONV] = zero ? 1.0 : 0.0;
+      if (B.sc[SC_ODONE] == 0.0) B.sc[SC_CONV] = zero ? 1.0 : 0.0;  // a finished refinement keeps its verdict
       if (!zero) atomicAdd(active, 1);
     }
   }
@@ -309,7 +309,9 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
   const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
   const T lapc = T(0.5) * dt * ih * ih;
-  auto dir = [&](T rv, T dv, T pv) { return rv * dv + beta * pv; };
+  // first iteration of a solve: pd_new = D^{-1} r and x = 0 whatever pd_old and x hold
+  const bool first = B.sc[SC_ITERS] == 0.0;
+  auto dir = [&](T rv, T dv, T pv) { return first ? rv * dv : rv * dv + beta * pv; };
   auto ld = [&](const T* f, int col, int k) { return __ldg(&f[col + G.plane(G.wrapz(k))]); };
   // centre column: r, dinv, pd_old for planes k + 1 .. k + KPF in flight
   T cr[KPF], cd[KPF], cp[KPF];
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
       const T y = ps * zc * idt - lapc * (nb - T(6) * zc);
       q[c] = y;
       pn[c] = zc;
-      x[c] = xv + alpha * oc;
+      x[c] = first ? T(0) : xv + alpha * oc;
       a0.add(zc, y);
     }
     zm = zc;
@@ -439,6 +441,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
   const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
   const T lapc = T(0.5) * dt * ih * ih;
+  const bool first = B.sc[SC_ITERS] == 0.0;  // pd_new = D^{-1} r, x = 0 whatever pd_old and x hold
   const int nseq = Gm.count();
   const size_t NN = (size_t)N * N;
 
@@ -497,7 +500,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
         const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
         V4<T> nv;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) nv.v[e] = rv.v[e] * dv.v[e] + beta * pv.v[e];
+        for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
         st4(slot + o, nv);
         cu_po[u] = pv;
         if (P.pos >= 1 && P.pos <= P.len) {
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
         const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
         V4<T> nv;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) nv.v[e] = rv.v[e] * dv.v[e] + beta * pv.v[e];
+        for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
         st4(slot + o, nv);
       }
     }
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
           const T nb = (vxm + vxp) + (cs.v[e] + cn.v[e]) + (cb.v[e] + ca.v[e]);
           const T y = sv_psi[u].v[e] * vc * idt - lapc * (nb - T(6) * vc);
           yv.v[e] = y;
-          xn.v[e] = sv_x[u].v[e] + alpha * sv_po[u].v[e];
+          xn.v[e] = first ? T(0) : sv_x[u].v[e] + alpha * sv_po[u].v[e];
           a0.add(vc, y);
         }
         st4(q + gbase, yv);
@@ -1073,6 +1076,201 @@ __global__ void __launch_bounds__(NTHR) kz_mix_residual(const BoxDev* boxes, con
   }
 }
 
+// ---- fused refinement of the plain-CG mixed-precision solve -----------------------------------
+// The CG scalars of a new inner solve from its right-hand side r: rz, ||r||^2,
+// counters, and whether it runs (not for a box whose refinement has converged).
+__device__ void cg_start_scalars(const BoxDev& B, double rz, double rr, int* active) {
+  double* sc = B.sc;
+  sc[SC_ITERS] = 0.0;
+  sc[SC_ALPHA] = 0.0;
+  sc[SC_BETA] = 0.0;
+  sc[SC_RZ] = rz;
+  sc[SC_BB] = rr;
+  const bool run = sc[SC_ODONE] == 0.0 && rr > 0.0;
+  sc[SC_DONE] = run ? 0.0 : 1.0;
+  if (run) atomicAdd(active, 1);
+  else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;  // a finished refinement keeps its verdict
+}
+
+// Start: keep b in K_AUX, x pairs = 0, r = b; ||b||^2 and <b, D^{-1} b> (the
+// first CG iteration forms pd = D^{-1} r itself and treats x as 0).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_mix_first_init(const BoxDev* boxes, const int2* ework, double* part,
+                                                         int* outer_active, int* active) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const T* __restrict__ b = F<T>(B, K_B);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ borig = F<T>(B, K_AUX);
+  T* __restrict__ r = F<T>(B, K_R);
+  float2* __restrict__ xs = F<float2>(B, K_X64);
+  DotAcc<float> arr, arz;
+  chunk_loop(
+      ch, tid,
+      [&](int q0) {
+        const V4<T> bv = ld4(b + q0), dv = ld4(dinv + q0);
+        st4(borig + q0, bv);
+        st4(r + q0, bv);
+        reinterpret_cast<float4*>(xs + q0)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(xs + q0)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          arr.add((float)bv.v[e], (float)bv.v[e]);
+          arz.add((float)bv.v[e], (float)(bv.v[e] * dv.v[e]));
+        }
+      },
+      [&](int c) {
+        const T bc = b[c];
+        borig[c] = bc;
+        r[c] = bc;
+        xs[c] = make_float2(0.f, 0.f);
+        arr.add((float)bc, (float)bc);
+        arz.add((float)bc, (float)(bc * dinv[c]));
+      });
+  DF v[2] = {arr.red(), arz.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      mix_finish_scalars(B, res[0], 1, outer_active);
+      cg_start_scalars(B, res[1], res[0], active);
+    }
+  }
+}
+
+// Boundary between inner solves, one pass: x pairs' = x pairs + (x + alpha pd)
+// (the last direction the fused iteration has not added yet; nothing when the
+// solve did not iterate), r = b - M x pairs' in double-float arithmetic, the
+// refinement bookkeeping, and the start of the next inner solve from r.  The
+// pairs ping-pong between K_X64 and K_X64B with the parity of the outer step
+// (neighbouring tiles read the old pairs as halo).  Symmetric operator.
+//
+// The residual is written as r = b - (psi/dt) x - kl (6 x - sum of the six
+// neighbours), kl = dt/(2 h^2): the neighbour sum of the high parts is exact
+// (TwoSum), 6 x and the two products are split exactly by FMA (TwoProduct),
+// and the three large terms b, (psi/dt) x, kl (6x - sum) meet in two TwoSums,
+// so the cancellation between them loses nothing; every low-order part is
+// carried in plain FP32 (its rounding is about 2^-48 of the terms).  Loads
+// run KPF planes ahead, halo cells included.
+template <typename T>
+struct PairRaw {
+  float2 a;  // old pair
+  T x, p;    // FP32 iterate and last direction (zero when the solve did not move)
+};
+template <typename T>
+struct PairSrc {
+  const float2* __restrict__ xo;
+  const T* __restrict__ x;
+  const T* __restrict__ pd;
+  T alpha;
+  bool moved;
+  __device__ __forceinline__ PairRaw<T> load(int q) const {
+    PairRaw<T> v;
+    v.a = __ldg(&xo[q]);
+    v.x = moved ? __ldg(&x[q]) : T(0);
+    v.p = moved ? __ldg(&pd[q]) : T(0);
+    return v;
+  }
+  // pair + (x + alpha pd) as a pair (the FP32 sum rounds as the field update would)
+  __device__ __forceinline__ float2 make(const PairRaw<T>& v) const {
+    if (!moved) return v.a;
+    const float d = (float)(v.x + alpha * v.p);
+    const DF s = df_two_sum(v.a.x, d);
+    const DF t = df_fast_two_sum(s.hi, __fadd_rn(s.lo, v.a.y));
+    return make_float2(t.hi, t.lo);
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int2* work, double* part,
+                                                  int* outer_active, int* active) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (B.sc[SC_ODONE] != 0.0) return;
+  const ZGeom<1> G(t.x0, t.y0, B.N);
+  __shared__ float2 sm[ZGeom<1>::H * ZGeom<1>::W];
+  const int par = ((int)B.sc[SC_OUTER]) & 1, it = (int)B.sc[SC_ITERS];
+  PairSrc<T> src;
+  src.xo = F<float2>(B, par ? K_X64B : K_X64);
+  src.x = F<T>(B, K_X);
+  src.pd = F<T>(B, (it & 1) ? K_PP : K_PD);
+  src.alpha = (T)B.sc[SC_ALPHA];
+  src.moved = it > 0;
+  float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
+  T* __restrict__ r = F<T>(B, K_R);
+  const double dt = B.sc[SC_KDT];
+  const DF idt = df_from_double(1.0 / dt), kl = df_from_double(0.5 * dt * B.ih * B.ih);
+  // pairs at planes k-1, k, k+1 of the own column; raw loads of later planes
+  auto cq = [&](int k) { return G.col + G.plane(G.wrapz(k)); };
+  auto hq = [&](int k) { return G.hcol + G.plane(G.wrapz(k)); };
+  float2 zm, zc = src.make(src.load(cq(t.k0 - 1))), zp = src.make(src.load(cq(t.k0)));
+  PairRaw<T> nq[KPF], nh[KPF];  // own column planes k+2.., halo planes k..
+#pragma unroll
+  for (int j = 0; j < KPF; ++j) {
+    nq[j] = src.load(cq(t.k0 + 1 + j));
+    if (G.hcol >= 0) nh[j] = src.load(hq(t.k0 + j));
+  }
+  ZStream<T, KPF> borig, psi, dinv;
+  borig.init(F<T>(B, K_AUX), G, t.k0);
+  psi.init(F<T>(B, W_PSI), G, t.k0);
+  dinv.init(F<T>(B, W_DINV), G, t.k0);
+  DotAcc<float> arr, arz;
+  for (int k = t.k0; k < t.kend; ++k) {
+    zm = zc;
+    zc = zp;
+    zp = src.make(nq[0]);
+#pragma unroll
+    for (int j = 0; j + 1 < KPF; ++j) nq[j] = nq[j + 1];
+    nq[KPF - 1] = src.load(cq(k + 2 + KPF - 1));
+    const T bc = borig.next(G, k), pc = psi.next(G, k), dc = dinv.next(G, k);
+    __syncthreads();
+    sm[G.csm] = zc;
+    if (G.hcol >= 0) {
+      sm[G.hsm] = src.make(nh[0]);
+#pragma unroll
+      for (int j = 0; j + 1 < KPF; ++j) nh[j] = nh[j + 1];
+      nh[KPF - 1] = src.load(hq(k + KPF));
+    }
+    __syncthreads();
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+    xn[c] = zc;
+    const float2* s = sm + G.csm;
+    const float2 n0 = s[1], n1 = s[-1], n2 = s[ZGeom<1>::W], n3 = s[-ZGeom<1>::W], n4 = zp, n5 = zm;
+    // sum of the neighbours: high parts exactly (pairwise TwoSums), low parts plainly
+    const DF s01 = df_two_sum(n0.x, n1.x), s23 = df_two_sum(n2.x, n3.x), s45 = df_two_sum(n4.x, n5.x);
+    const DF u = df_two_sum(s01.hi, s23.hi), v = df_two_sum(u.hi, s45.hi);
+    const float nlo = __fadd_rn(__fadd_rn(__fadd_rn(s01.lo, s23.lo), __fadd_rn(s45.lo, u.lo)),
+                                __fadd_rn(v.lo, __fadd_rn(__fadd_rn(__fadd_rn(n0.y, n1.y), __fadd_rn(n2.y, n3.y)),
+                                                          __fadd_rn(n4.y, n5.y))));
+    // S = 6 x - sum (6 x_hi split exactly)
+    const float p6 = __fmul_rn(6.f, zc.x), e6 = __fmaf_rn(6.f, zc.x, -p6);
+    const DF sh = df_two_sum(p6, -v.hi);
+    const float slo = __fadd_rn(__fadd_rn(sh.lo, e6), __fsub_rn(__fmul_rn(6.f, zc.y), nlo));
+    // K = kl S and A = (psi/dt) x as unnormalised pairs (product + exact error + low terms)
+    const float kp = __fmul_rn(kl.hi, sh.hi);
+    const float ke = __fmaf_rn(kl.lo, sh.hi, __fmaf_rn(kl.hi, slo, __fmaf_rn(kl.hi, sh.hi, -kp)));
+    const float wp = __fmul_rn(idt.hi, (float)pc);
+    const float we = __fmaf_rn(idt.lo, (float)pc, __fmaf_rn(idt.hi, (float)pc, -wp));
+    const float ap = __fmul_rn(wp, zc.x);
+    const float ae = __fmaf_rn(we, zc.x, __fmaf_rn(wp, zc.y, __fmaf_rn(wp, zc.x, -ap)));
+    // r = b - A - K: the large parts in two TwoSums, the rest in FP32
+    const DF t1 = df_two_sum((float)bc, -ap), t2 = df_two_sum(t1.hi, -kp);
+    const float rv = __fadd_rn(t2.hi, __fsub_rn(__fadd_rn(t2.lo, t1.lo), __fadd_rn(ae, ke)));
+    r[c] = (T)rv;
+    arr.add(rv, rv);
+    arz.add(rv, (float)((T)rv * dc));
+  }
+  DF v[2] = {arr.red(), arz.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      mix_finish_scalars(B, res[0], 0, outer_active);
+      cg_start_scalars(B, res[1], res[0], active);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_mix_residual(const BoxDev* boxes, const int2* work, double* part, int first,
                                                        int* outer_active) {
@@ -1132,12 +1330,13 @@ __global__ void __launch_bounds__(NTHR) k_mix_accum(const BoxDev* boxes, const i
 
 // x = the pair rounded to the field precision
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const int2* ework) {
+__global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const int2* ework, int pingpong) {
   const Chunk ch = chunk_of(boxes, ework);
   const BoxDev& B = boxes[ch.box];
   const int tid = threadIdx.x + TX * threadIdx.y;
   T* __restrict__ x = F<T>(B, K_X);
-  const float2* __restrict__ xs = F<float2>(B, K_X64);
+  const bool second = pingpong && (((int)B.sc[SC_OUTER]) & 1);
+  const float2* __restrict__ xs = F<float2>(B, second ? K_X64B : K_X64);
   for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
     const float2 a = xs[c];
     x[c] = (T)__fadd_rn(a.x, a.y);
@@ -1287,11 +1486,20 @@ template <typename T> void launch_mix_residual(const Launch& L, int first, int* 
   else
     FE_LAUNCH(L, KID_MIX_RES, (kz_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active)));
 }
+template <typename T> void launch_mix_first_init(const Launch& L, int* outer_active) {
+  FE_LAUNCH(L, KID_MIX_RES, (k_mix_first_init<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active, L.active)));
+}
+template <typename T> void launch_refine(const Launch& L, int* outer_active) {
+  FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+}
+template <typename T> void launch_mix_finish_pp(const Launch& L) {
+  FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework, 1)));
+}
 template <typename T> void launch_mix_accum(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_ACC, (k_mix_accum<T><<<EGRID>>>(L.boxes, L.ework)));
 }
 template <typename T> void launch_mix_finish(const Launch& L) {
-  FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework)));
+  FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework, 0)));
 }
 
 // Dynamic shared memory of the streamed CG kernel for edge N (sets the
@@ -1330,6 +1538,9 @@ int bulk_cg_blocks_per_sm(int bytes) {
   template void launch_bicg_x<T>(const Launch&);                 \
   template void launch_mix_residual<T>(const Launch&, int, int*); \
   template void launch_mix_accum<T>(const Launch&);              \
+  template void launch_mix_first_init<T>(const Launch&, int*);   \
+  template void launch_refine<T>(const Launch&, int*);           \
+  template void launch_mix_finish_pp<T>(const Launch&);          \
   template void launch_mix_finish<T>(const Launch&);              \
   template void launch_fcg<T>(const Launch&, const float*);
 INST(double)
