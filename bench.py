@@ -263,6 +263,7 @@ def main():
     ap.add_argument("--kernel", default=None, help="kernel timed live for the roofline (default: largest share)")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the untimed per-kernel pass")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile depth")
+    ap.add_argument("--tile", type=int, default=0, help="fixed tile depth (no autotuning)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and learned comparison paths")
     ap.add_argument("--no-graphs", action="store_true", help="host-driven steps in the headline region")
     ap.add_argument("--learn-steps", type=int, default=2, help="steps harvested for training (learned path)")
@@ -310,7 +311,11 @@ def main():
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
                   p_maxit=1000, stream=stream.cuda_stream)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
-    tz = s.autotune(2) if not args.no_tune else 0
+    if args.tile > 0:
+        s.set_tiling(args.tile)
+        tz = args.tile
+    else:
+        tz = s.autotune(2) if not args.no_tune else 0
     code, _ = s.step(args.warmup)
     assert code == fe.FE_OK, fe.fe_strerror(code)
 

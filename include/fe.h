@@ -278,7 +278,7 @@ int fe_use_plane_streaming(fe_ctx* ctx, int on);
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz
  * (0 = built-in default: 8 for N >= 128, else 4).  fe_autotune times `trials`
  * trial steps (computed from the current state and discarded: the state and
- * clock are unchanged) for tz in {1, 2, 4, 8, 16}, keeps the fastest and
+ * clock are unchanged) for tz in {4, 8, 16, 32}, keeps the fastest and
  * returns it in *best_tz.  Not part of the method. */
 int fe_set_tiling(fe_ctx* ctx, int tz);
 int fe_autotune(fe_ctx* ctx, int trials, int* best_tz);

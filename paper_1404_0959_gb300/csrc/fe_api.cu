@@ -1142,7 +1142,7 @@ extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   int rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   std::vector<double> saved(c->hsc, c->hsc + (size_t)c->nb * NSC);
-  const int cand[] = {1, 2, 4, 8, 16};
+  const int cand[] = {4, 8, 16, 32};
   int best = 0;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;

@@ -1,7 +1,8 @@
 // step_rkernels.cu -- the PISO stencil kernels on asynchronous-copy rings
 // (zring.cuh): every streamed plane reaches shared memory by cp.async A
-// planes ahead, so no register holds data in flight and the z-neighbours are
-// read from the ring.  Same per-cell arithmetic as step_zkernels.cu (and as
+// planes ahead, so no register holds data in flight; the z-neighbours come
+// from per-thread register queues fed from the ring.  Same per-cell
+// arithmetic as step_zkernels.cu (and as
 // the general kernels of step_kernels.cu, which carry the formulas of Sec. 2
 // of arXiv:1404.0959).
 #include "zring.cuh"

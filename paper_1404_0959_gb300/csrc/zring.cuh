@@ -1,15 +1,18 @@
 // zring.cuh -- z-marching with asynchronous copies into shared-memory rings.
 //
-// Same 32 x 8 column tiles as zmarch.cuh, but every streamed plane -- the
-// z-neighbours included -- lives in a shared ring filled by 16-byte cp.async
-// chunks (global -> shared without registers), A planes ahead of the plane
-// being computed.  Three ring kinds:
-//   stencil field  planes k-2 .. k+2 in use           (5 + A slots, tile + halo)
-//   face array     planes k-1 .. k (own, x-1, y-1)    (2 + A slots, tile + halo)
-//   centre field   plane k, own cells                  (1 + A slots, tile only)
-// One group of copies per plane; before plane k a thread waits until its own
-// copies of plane k (+2 for stencils) have landed, then one barrier makes
-// all threads' copies visible and frees the slots of plane k - 3 for reuse.
+// Same 32 x 8 column tiles as zmarch.cuh, but every streamed plane lives in a
+// shared ring filled by 16-byte cp.async chunks (global -> shared without
+// registers), A planes ahead of the plane being computed.  Three ring kinds:
+//   stencil field  planes k .. k+2 in use               (3 + A slots, tile + halo)
+//   face array     planes k-1 .. k (own, x-1, y-1)      (2 + A slots, tile + halo)
+//   centre field   plane k, own cells                    (1 + A slots, tile only)
+// The z-neighbours of a stencil field come from a per-thread register queue
+// (planes k-2 .. k+2 of the own column): each plane is read from shared
+// memory once for the queue, when it is two planes ahead, and once per x/y
+// neighbour while it is the current plane.  One group of copies per plane;
+// before plane k a thread waits until its own copies of plane k (+2 for
+// stencils) have landed, then one barrier makes all threads' copies visible
+// and frees the slots of plane k - 1 for reuse.
 #pragma once
 #include "zbulk.cuh"
 #include "zmarch.cuh"
@@ -96,17 +99,19 @@ __device__ __forceinline__ void zr_issue_centre(const RGeom<T>& G, const T* g, T
   if (G.cc_g >= 0) cp_async16(slot + G.cc_s, g + G.cc_g + G.plane(m));
 }
 
-// Stencil view of one field at plane k: five ring slots k-2 .. k+2.
+// Stencil view of one field at plane k: the current ring slot (x/y
+// neighbours) and the register queue (z-neighbours and the cell itself).
 template <typename T>
 struct ZView {
-  const T* p[5];
+  const T* p;
+  T z[5];  // own column, planes k-2 .. k+2
   int csm;
   template <typename GT>
   __device__ __forceinline__ T at(const GT&, int d, int s) const {
-    if (d == 2) return p[2 + s][csm];
-    return d == 0 ? p[2][csm + s] : p[2][csm + s * RGeom<T>::W];
+    if (d == 2) return z[2 + s];
+    return d == 0 ? p[csm + s] : p[csm + s * RGeom<T>::W];
   }
-  __device__ __forceinline__ T c() const { return p[2][csm]; }
+  __device__ __forceinline__ T c() const { return z[2]; }
 };
 // Sum of two stencil views (a + b per cell, the same rounding as staging the sum).
 template <typename T>
@@ -117,13 +122,13 @@ struct ZView2 {
   __device__ __forceinline__ T c() const { return a.c() + b.c(); }
 };
 
-// Ring slot bookkeeping of one tile: stencil slots (5 + A), face slots (2 + A),
-// centre slots (1 + A), indexed from the tile's first plane k0.
+// Ring slot bookkeeping of one tile: stencil slots (3 + A, from plane k0),
+// face slots (2 + A, from plane k0 - 1), centre slots (1 + A, from plane k0).
 template <int A>
 struct ZSlots {
-  static constexpr int NS = 5 + A, NF = 2 + A, NC = 1 + A;
+  static constexpr int NS = 3 + A, NF = 2 + A, NC = 1 + A;
   int k0;
-  __device__ __forceinline__ int s(int m) const { return (m - k0 + 2) % NS; }  // stencil plane m
+  __device__ __forceinline__ int s(int m) const { return (m - k0) % NS; }      // stencil plane m
   __device__ __forceinline__ int f(int m) const { return (m - k0 + 1) % NF; }  // face plane m
   __device__ __forceinline__ int c(int m) const { return (m - k0) % NC; }      // centre plane m
 };
@@ -144,6 +149,7 @@ struct RingPlan {
   const T* gs[NSF > 0 ? NSF : 1];
   const T* gf[NFF > 0 ? NFF : 1];
   const T* gc[NCF > 0 ? NCF : 1];
+  T zq[NSF > 0 ? NSF : 1][5];  // z-queues of the stencil fields (own column, planes k-2 .. k+2)
   SL sl;
   int k0, kend;
   int ncf = NCF;  // centre fields copied (the first ncf of gc)
@@ -155,6 +161,7 @@ struct RingPlan {
     kend = kend_;
     sl.k0 = k0_;
   }
+  __device__ __forceinline__ const T* sslot(int f, int m) const { return rs + (f * SL::NS + sl.s(m)) * HW; }
   __device__ __forceinline__ void stencil_plane(const G_& G, int m) {
     const int w = G.wrapz(m);
 #pragma unroll
@@ -178,9 +185,10 @@ struct RingPlan {
       centre_plane(G, k0 + q);
     }
   }
-  // group 0 (stencil k0-2..k0+2, faces k0-1..k0, centre k0) and groups 1..A-1
+  // group 0 (stencil k0..k0+2, faces k0-1..k0, centre k0) and groups 1..A-1;
+  // the queue entries below the tile (planes k0-2, k0-1) straight from global memory
   __device__ __forceinline__ void prologue(const G_& G) {
-    for (int m = k0 - 2; m <= k0 + 2; ++m) stencil_plane(G, m);
+    for (int m = k0; m <= k0 + 2; ++m) stencil_plane(G, m);
     face_plane(G, k0 - 1);
     face_plane(G, k0);
     centre_plane(G, k0);
@@ -190,19 +198,43 @@ struct RingPlan {
       issue(G, q);
       cp_async_commit();
     }
+    const int m2 = G.plane(G.wrapz(k0 - 2)), m1 = G.plane(G.wrapz(k0 - 1));
+#pragma unroll
+    for (int f = 0; f < NSF; ++f) {
+      zq[f][0] = __ldg(gs[f] + G.col + m2);
+      zq[f][1] = __ldg(gs[f] + G.col + m1);
+    }
   }
-  // before plane k = k0 + i: wait for its copies, make them visible, start plane group A + i
+  // before plane k = k0 + i: wait for its copies, make them visible, start plane group
+  // A + i, and move the z-queues to plane k (plane k+2 read from its slot)
   __device__ __forceinline__ void next(const G_& G, int i) {
     cp_async_wait<A - 1>();
     __syncthreads();
     issue(G, A + i);
     cp_async_commit();
+    const int k = k0 + i;
+    if (i == 0) {
+#pragma unroll
+      for (int f = 0; f < NSF; ++f) {
+        zq[f][2] = sslot(f, k)[G.csm];
+        zq[f][3] = sslot(f, k + 1)[G.csm];
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < NSF; ++f) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zq[f][j] = zq[f][j + 1];
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NSF; ++f) zq[f][4] = sslot(f, k + 2)[G.csm];
   }
   __device__ __forceinline__ ZView<T> view(int f, int k, const G_& G) const {
     ZView<T> v;
     v.csm = G.csm;
+    v.p = sslot(f, k);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) v.p[j] = rs + (f * SL::NS + sl.s(k - 2 + j)) * HW;
+    for (int j = 0; j < 5; ++j) v.z[j] = zq[f][j];
     return v;
   }
   // faces f0, f0+1, f0+2 (x, y, z arrays): values at the +1/2 and -1/2 faces of the cell
