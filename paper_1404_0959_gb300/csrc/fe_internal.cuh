@@ -332,12 +332,13 @@ __device__ __forceinline__ void st4(double* p, const V4<double>& a) {
 
 // ---- deterministic reductions ----------------------------------------------------
 // Last-block phase of the block sums: the box's last block to finish adds the
-// partials of all its blocks in block order.
+// partials of all its blocks in block order.  Blocks of up to NTHR threads
+// (a multiple of 32), 1-D or 2-D.
 template <int K>
 __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
   __shared__ double red[K][NTHR / 32];
   __shared__ int last;
-  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     __threadfence();
@@ -350,7 +351,7 @@ __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, in
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     double s = 0.0;
-    for (int b = tid; b < ntiles; b += NTHR) s += __ldcg(&part[(size_t)(tile0 + b) * MAXP + q]);
+    for (int b = tid; b < ntiles; b += nt) s += __ldcg(&part[(size_t)(tile0 + b) * MAXP + q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) red[q][warp] = s;
@@ -360,7 +361,7 @@ __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, in
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       double s = 0.0;
-      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
+      for (int w = 0; w < nt / 32; ++w) s += red[q][w];
       res[q] = s;
     }
     *B.cnt = 0;
@@ -376,7 +377,7 @@ __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, in
 template <int K>
 __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
   __shared__ double red[K][NTHR / 32];
-  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < K; ++q) {
@@ -390,7 +391,7 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       double s = 0.0;
-      for (int w = 0; w < NTHR / 32; ++w) s += red[q][w];
+      for (int w = 0; w < nt / 32; ++w) s += red[q][w];
       part[(size_t)blockIdx.x * MAXP + q] = s;
     }
   }
@@ -400,7 +401,7 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
 template <int K>
 __device__ bool block_sum_last(DF (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
   __shared__ DF red[K][NTHR / 32];
-  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < K; ++q) {
@@ -417,7 +418,7 @@ __device__ bool block_sum_last(DF (&v)[K], const BoxDev& B, double* part, double
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       DF s = red[q][0];
-      for (int w = 1; w < NTHR / 32; ++w) s = df_add(s, red[q][w]);
+      for (int w = 1; w < nt / 32; ++w) s = df_add(s, red[q][w]);
       part[(size_t)blockIdx.x * MAXP + q] = (double)s.hi + (double)s.lo;
     }
   }
@@ -429,7 +430,7 @@ __device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double
                                                int ntiles) {
   __shared__ double red[NTHR / 32];
   __shared__ int last;
-  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
   double s = v;
 #pragma unroll
@@ -438,7 +439,7 @@ __device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double
   __syncthreads();
   if (tid == 0) {
     double m = red[0];
-    for (int w = 1; w < NTHR / 32; ++w) m = fmax(m, red[w]);
+    for (int w = 1; w < nt / 32; ++w) m = fmax(m, red[w]);
     part[(size_t)blockIdx.x * MAXP] = m;
     __threadfence();
     int prev = atomicAdd(B.cnt, 1);
@@ -448,14 +449,14 @@ __device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double
   if (!last) return false;
   __threadfence();
   s = 0.0;
-  for (int b = tid; b < ntiles; b += NTHR) s = fmax(s, __ldcg(&part[(size_t)(tile0 + b) * MAXP]));
+  for (int b = tid; b < ntiles; b += nt) s = fmax(s, __ldcg(&part[(size_t)(tile0 + b) * MAXP]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
   if (lane == 0) red[warp] = s;
   __syncthreads();
   if (tid == 0) {
     double m = red[0];
-    for (int w = 1; w < NTHR / 32; ++w) m = fmax(m, red[w]);
+    for (int w = 1; w < nt / 32; ++w) m = fmax(m, red[w]);
     *res = m;
     *B.cnt = 0;
   }

@@ -10,14 +10,23 @@
 namespace fe {
 
 // Lookahead planes of each ring kernel (shared memory per block grows with
-// it; measured at 256^3 FP32: the corrector and the dust update run best
-// with one plane, the others with two).  The divergence and the right-hand
-// side keep their register-queue z-marching kernels, which measured faster.
+// it; measured at 256^3 FP32 with column-pair threads: the corrector, the
+// predictor and Du/Dt run best with two planes, the assembly and the dust
+// kernels with one), and the predictor's register cap (three resident blocks
+// per SM in FP32: its 174-register build left it at two and ran 25 % slower).  The
+// divergence and the right-hand side keep their register-queue z-marching
+// kernels, which measured faster.
 #ifndef FE_RING_A
 #define FE_RING_A 2
 #endif
 #ifndef FE_RING_A_LIGHT
 #define FE_RING_A_LIGHT 1
+#endif
+#ifndef FE_RING_MINB
+#define FE_RING_MINB 1  // minimum resident blocks per SM asked of the register allocator
+#endif
+#ifndef FE_RING_MINB_PRED
+#define FE_RING_MINB_PRED 3
 #endif
 #ifndef FE_RING_OFF
 #define FE_RING_OFF 0u  // ring kernels left out (bits of RingKernel): their z-marching versions run
@@ -67,7 +76,7 @@ struct Unparen<void(P)> {
   const TileXYZ t = tile_xyz(boxes, work);                 \
   const BoxDev& B = boxes[t.box];                          \
   const RGeom<T> G(t.x0, t.y0, B.N);                       \
-  const int tid = threadIdx.x + TX * threadIdx.y;          \
+  const int tid = threadIdx.x + RTX * threadIdx.y;         \
   extern __shared__ __align__(16) unsigned char rsm[];     \
   typename Unparen<void(P)>::type R;                       \
   R.init(rsm, t.k0, t.kend)
@@ -77,10 +86,10 @@ struct Unparen<void(P)> {
 // u^k = HbyA - dt/rho^{k-1} Gc p^k, rho^k = rho^n - dt/2 (div phi^n + D phi^k);
 // FP64 path: ||b - M x||^2 for the reported residual.
 template <typename T, bool MIXED>
-using CorrPlan = RingPlan<T, kA1, 2, 3, MIXED ? 6 : 8>;  // p^{k-1}, x | phi* | rho^n, rho^{k-1}, HbyA0..2, D phi^n [, psi, b]
+using CorrPlan = RingPlan<T, kA, 2, 3, MIXED ? 6 : 8>;  // p^{k-1}, x | phi* | rho^n, rho^{k-1}, HbyA0..2, D phi^n [, psi, b]
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2* work, double* part, int s, int rhop,
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_corr(const BoxDev* boxes, const int2* work, double* part, int s, int rhop,
                                                 int pp, int pnew, int kset, int kidx) {
   constexpr int NC = MIXED ? 6 : 8;
   RING_PROLOGUE((CorrPlan<T, MIXED>));
@@ -97,7 +106,7 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
     R.gc[6 % NC] = Fr<T>(B, W_PSI);
     R.gc[7 % NC] = Fr<T>(B, K_B);
   }
-  T* rk = Fr<T>(B, rhop);  // rho^{k-1} in (through the ring), rho^k out (own cell only)
+  T* rk = Fr<T>(B, rhop);  // rho^{k-1} in (through the ring), rho^k out (own cells only)
   T* __restrict__ pn = Fr<T>(B, pnew);
   T* __restrict__ phk[3] = {Fr<T>(B, S(kset, F_PHI0)), Fr<T>(B, S(kset, F_PHI1)), Fr<T>(B, S(kset, F_PHI2))};
   T* __restrict__ uk[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
@@ -108,32 +117,44 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> vp = R.view(0, k, G), vx = R.view(1, k, G);
-    const ZView2<T> pk{vp, vx};
-    T psp[3], psm[3];
-    R.faces(0, k, G, psp, psm);
     const int c = G.col + G.plane(k);
-    const T xc = vx.c();
-    T dsum = T(0), lap = T(0);
+    const P2<T> crn = R.cen(0, k, tid), crp = R.cen(1, k, tid), cdp = R.cen(5, k, tid);
+    const P2<T> chb[3] = {R.cen(2, k, tid), R.cen(3, k, tid), R.cen(4, k, tid)};
+    T oph[3][2], opn[2], ou[3][2], ork[2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T xp = vx.at(G, d, 1), xm = vx.at(G, d, -1);
-      const T fp = psp[d] - dt * (xp - xc) * ih;
-      const T fm = psm[d] - dt * (xc - xm) * ih;
-      lap += (xp - xc) - (xc - xm);
-      phk[d][c] = fp;
-      dsum += fp - fm;
-    }
-    const T dtr = dt / R.cen(1, k, tid);
-    pn[c] = pk.c();
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> vp = R.view(0, k, G, r), vx = R.view(1, k, G, r);
+      const ZView2<T> pk{vp, vx};
+      T psp[3], psm[3];
+      R.faces(0, k, G, r, psp, psm);
+      const T xc = vx.c();
+      T dsum = T(0), lap = T(0);
 #pragma unroll
-    for (int m = 0; m < 3; ++m) uk[m][c] = R.cen(2 + m, k, tid) - dtr * (zGc_h(pk, G, m) * ih);
-    rk[c] = R.cen(0, k, tid) - T(0.5) * dt * (R.cen(5, k, tid) + dsum * ih);
-    if (!MIXED) {
-      const T Mx = R.cen(6 % NC, k, tid) * xc * idt - T(0.5) * dt * lap * ih * ih;
-      const double r = (double)R.cen(7 % NC, k, tid) - (double)Mx;
-      rr += r * r;
+      for (int d = 0; d < 3; ++d) {
+        const T xp = vx.at(G, d, 1), xm = vx.at(G, d, -1);
+        const T fp = psp[d] - dt * (xp - xc) * ih;
+        const T fm = psm[d] - dt * (xc - xm) * ih;
+        lap += (xp - xc) - (xc - xm);
+        oph[d][r] = fp;
+        dsum += fp - fm;
+      }
+      const T dtr = dt / pc<T>(crp, r);
+      opn[r] = pk.c();
+#pragma unroll
+      for (int m = 0; m < 3; ++m) ou[m][r] = pc<T>(chb[m], r) - dtr * (zGc_h(pk, G, m) * ih);
+      ork[r] = pc<T>(crn, r) - T(0.5) * dt * (pc<T>(cdp, r) + dsum * ih);
+      if (!MIXED) {
+        const T Mx = pc<T>(R.cen(6 % NC, k, tid), r) * xc * idt - T(0.5) * dt * lap * ih * ih;
+        const double e = (double)pc<T>(R.cen(7 % NC, k, tid), r) - (double)Mx;
+        rr += e * e;
+      }
     }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) stp(phk[d] + c, oph[d][0], oph[d][1]);
+    stp(pn + c, opn[0], opn[1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) stp(uk[m] + c, ou[m][0], ou[m][1]);
+    stp(rk + c, ork[0], ork[1]);
   }
   cp_async_wait<0>();
   Red<T> v[1] = {MIXED ? Red<T>{} : red_from<T>(rr)};
@@ -155,7 +176,7 @@ __global__ void __launch_bounds__(NTHR) kr_corr(const BoxDev* boxes, const int2*
 template <typename T>
 using PredPlan = RingPlan<T, kA, 5, 3, 1>;  // u0..2, div, p | phi | rho
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kr_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
+__global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_RING_MINB) kr_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
   RING_PROLOGUE(PredPlan<T>);
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(s, F_U0 + m));
@@ -178,39 +199,54 @@ __global__ void __launch_bounds__(NTHR) kr_pred(const BoxDev* boxes, const int2*
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
-    const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
-    T php[3], phm[3];
-    R.faces(0, k, G, php, phm);
     const int c = G.col + G.plane(k);
-    const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
-    const T r = R.cen(0, k, tid);
-    const T r0 = r - dt * dph;
-    const T ir0 = T(1) / r0, ir = T(1) / r;
-    T L[3], visc[3];
-    zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+    const P2<T> crho = R.cen(0, k, tid);
+    T ous[3][2], oRn[3][2], oAn[3][2], ops[2], odi[2], odp[2], or0[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
+      const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
+      T php[3], phm[3];
+      R.faces(0, k, G, r, php, phm);
+      const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
+      const T rc = pc<T>(crho, r);
+      const T r0 = rc - dt * dph;
+      const T ir0 = T(1) / r0, ir = T(1) / rc;
+      T L[3], visc[3];
+      zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T gp = zGc_h(p, G, m) * ih;
+        ous[m][r] = (rc * u[m].c() + dt * (L[m] - gp)) * ir0;
+        oRn[m][r] = L[m];
+        oAn[m][r] = (visc[m] - gp) * ir;
+      }
+      const T ps = rc / (gam * p.c());
+      ops[r] = ps;
+      odi[r] = T(1) / (ps * idt + c3);
+      odp[r] = dph;
+      or0[r] = r0;
+    }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const T gp = zGc_h(p, G, m) * ih;
-      us[m][c] = (r * u[m].c() + dt * (L[m] - gp)) * ir0;
-      Rn[m][c] = L[m];
-      An[m][c] = (visc[m] - gp) * ir;
+      stp(us[m] + c, ous[m][0], ous[m][1]);
+      stp(Rn[m] + c, oRn[m][0], oRn[m][1]);
+      stp(An[m] + c, oAn[m][0], oAn[m][1]);
     }
-    const T ps = r / (gam * p.c());
-    psi[c] = ps;
-    dinv[c] = T(1) / (ps * idt + c3);
-    divphi[c] = dph;
-    rho0[c] = r0;
+    stp(psi + c, ops[0], ops[1]);
+    stp(dinv + c, odi[0], odi[1]);
+    stp(divphi + c, odp[0], odp[1]);
+    stp(rho0 + c, or0[0], or0[1]);
   }
   cp_async_wait<0>();
 }
 
 // ---- corrector assembly ------------------------------------------------------------------------------
 template <typename T>
-using AsmPlan = RingPlan<T, kA, 4, 3, 8>;  // u0..2 (level k-1), div | phi | rho, un0..2, rho', Rn0..2
+using AsmPlan = RingPlan<T, kA1, 4, 3, 8>;  // u0..2 (level k-1), div | phi | rho, un0..2, rho', Rn0..2
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kr_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
-                                                int rhop) {
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
+                                               int rhop) {
   RING_PROLOGUE(AsmPlan<T>);
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, up0 + m);
@@ -230,20 +266,27 @@ __global__ void __launch_bounds__(NTHR) kr_asm(const BoxDev* boxes, const int2* 
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
-    const ZView<T> div = R.view(3, k, G);
-    T php[3], phm[3];
-    R.faces(0, k, G, php, phm);
     const int c = G.col + G.plane(k);
-    T L[3], visc[3];
-    zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
-    const T r = R.cen(0, k, tid);
-    const T irp = T(1) / R.cen(4, k, tid);
+    const P2<T> crho = R.cen(0, k, tid), crp = R.cen(4, k, tid);
+    T ohb[3][2];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const T Rm = T(0.5) * (R.cen(5 + m, k, tid) + L[m]);
-      hb[m][c] = (r * R.cen(1 + m, k, tid) + dt * Rm) * irp;
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
+      const ZView<T> div = R.view(3, k, G, r);
+      T php[3], phm[3];
+      R.faces(0, k, G, r, php, phm);
+      T L[3], visc[3];
+      zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+      const T rc = pc<T>(crho, r);
+      const T irp = T(1) / pc<T>(crp, r);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T Rm = T(0.5) * (pc<T>(R.cen(5 + m, k, tid), r) + L[m]);
+        ohb[m][r] = (rc * pc<T>(R.cen(1 + m, k, tid), r) + dt * Rm) * irp;
+      }
     }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) stp(hb[m] + c, ohb[m][0], ohb[m][1]);
   }
   cp_async_wait<0>();
 }
@@ -252,7 +295,7 @@ __global__ void __launch_bounds__(NTHR) kr_asm(const BoxDev* boxes, const int2* 
 template <typename T>
 using AccelPlan = RingPlan<T, kA, 5, 0, 1>;  // u0..2, div, p | | rho
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kr_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
   RING_PROLOGUE(AccelPlan<T>);
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(kset, F_U0 + m));
@@ -266,25 +309,32 @@ __global__ void __launch_bounds__(NTHR) kr_accel(const BoxDev* boxes, const int2
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> u[3] = {R.view(0, k, G), R.view(1, k, G), R.view(2, k, G)};
-    const ZView<T> div = R.view(3, k, G), p = R.view(4, k, G);
     const int c = G.col + G.plane(k);
-    const T ir = T(1) / R.cen(0, k, tid);
+    const P2<T> crho = R.cen(0, k, tid);
+    T oa[3][2];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
-      const T visc = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
-      a[m][c] = (visc - zGc_h(p, G, m) * ih) * ir;
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
+      const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
+      const T ir = T(1) / pc<T>(crho, r);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
+        const T visc = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
+        oa[m][r] = (visc - zGc_h(p, G, m) * ih) * ir;
+      }
     }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) stp(a[m] + c, oa[m][0], oa[m][1]);
   }
   cp_async_wait<0>();
 }
 
 // ---- dust: n-level flux divergences FYN_j = D(phi_p^n I4 Y_j^n) --------------------------------------------
 template <typename T, int ND>
-using FluxPlan = RingPlan<T, kA, 4 + ND, 3, 0>;  // rho, a0..2, Y_j | phi
+using FluxPlan = RingPlan<T, kA1, 4 + ND, 3, 0>;  // rho, a0..2, Y_j | phi
 template <typename T, int ND>
-__global__ void __launch_bounds__(NTHR) kr_fluxn(const BoxDev* boxes, const int2* work, int s) {
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fluxn(const BoxDev* boxes, const int2* work, int s) {
   RING_PROLOGUE((FluxPlan<T, ND>));
   R.gs[0] = Fr<T>(B, S(s, F_RHO));
 #pragma unroll
@@ -306,27 +356,33 @@ __global__ void __launch_bounds__(NTHR) kr_fluxn(const BoxDev* boxes, const int2
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> rho = R.view(0, k, G);
-    const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
-    T php[3], phm[3];
-    R.faces(0, k, G, php, phm);
     const int c = G.col + G.plane(k);
-    T ra_p[3], ra_m[3];
+    T of[ND][2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
-      ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> rho = R.view(0, k, G, r);
+      const ZView<T> a[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
+      T php[3], phm[3];
+      R.faces(0, k, G, r, php, phm);
+      T ra_p[3], ra_m[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
+        ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
+      }
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const ZView<T> Y = R.view(4 + j, k, G, r);
+        const T tp = taup[j];
+        T acc = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          acc += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
+        of[j][r] = acc * ih;
+      }
     }
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      const ZView<T> Y = R.view(4 + j, k, G);
-      const T tp = taup[j];
-      T acc = T(0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        acc += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
-      fyn[j][c] = acc * ih;
-    }
+    for (int j = 0; j < ND; ++j) stp(fyn[j] + c, of[j][0], of[j][1]);
   }
   cp_async_wait<0>();
 }
@@ -335,8 +391,8 @@ __global__ void __launch_bounds__(NTHR) kr_fluxn(const BoxDev* boxes, const int2
 template <typename T, int ND>
 using DustPlan = RingPlan<T, kA1, 4 + ND, 3, 4 + 2 * ND>;  // rho^k, a0..2, Y_j^{k-1} | phi^k | rho^n, Y^n, FYN, u0..2
 template <typename T, int ND>
-__global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2* work, double* part, int s, int kset,
-                                                 int yp0, int yn0, int last) {
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes, const int2* work, double* part, int s, int kset,
+                                                int yp0, int yn0, int last) {
   RING_PROLOGUE((DustPlan<T, ND>));
   R.gs[0] = Fr<T>(B, S(kset, F_RHO));
 #pragma unroll
@@ -370,45 +426,55 @@ __global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2*
     const int k = t.k0 + i;
     R.next(G, i);
     if (!G.active) continue;
-    const ZView<T> rho = R.view(0, k, G);
-    const ZView<T> a[3] = {R.view(1, k, G), R.view(2, k, G), R.view(3, k, G)};
-    T php[3], phm[3];
-    R.faces(0, k, G, php, phm);
     const int c = G.col + G.plane(k);
-    const T rk = rho.c();
-    const T irk = T(1) / rk;
-    const T rn = R.cen(0, k, tid);
-    T ra_p[3], ra_m[3];
+    const P2<T> crn = R.cen(0, k, tid);
+    T oy[ND][2], op[2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
-      ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
-    }
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> rho = R.view(0, k, G, r);
+      const ZView<T> a[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
+      T php[3], phm[3];
+      R.faces(0, k, G, r, php, phm);
+      const T rk = rho.c();
+      const T irk = T(1) / rk;
+      const T rn = pc<T>(crn, r);
+      T ra_p[3], ra_m[3];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      const ZView<T> Y = R.view(4 + j, k, G);
-      const T tp = taup[j];
-      T fl = T(0);
+      for (int d = 0; d < 3; ++d) {
+        ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
+        ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
+      }
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        fl += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
-      const T rY = rn * R.cen(1 + j, k, tid) - T(0.5) * dt * (R.cen(1 + ND + j, k, tid) + fl * ih);
-      const T Yk = rY * irk;
-      ynew[j][c] = Yk;
+      for (int j = 0; j < ND; ++j) {
+        const ZView<T> Y = R.view(4 + j, k, G, r);
+        const T tp = taup[j];
+        T fl = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          fl += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
+        const T rY = rn * pc<T>(R.cen(1 + j, k, tid), r) - T(0.5) * dt * (pc<T>(R.cen(1 + ND + j, k, tid), r) + fl * ih);
+        const T Yk = rY * irk;
+        oy[j][r] = Yk;
+        if (last) {
+          ady[j].add(rk, Yk);
+          if (!isfinite(Yk)) abad.add(T(1));
+        }
+      }
+      op[r] = T(0);
       if (last) {
-        ady[j].add(rk, Yk);
-        if (!isfinite(Yk)) abad.add(T(1));
+        const T u0 = pc<T>(R.cen(1 + 2 * ND, k, tid), r), u1 = pc<T>(R.cen(2 + 2 * ND, k, tid), r),
+                u2 = pc<T>(R.cen(3 + 2 * ND, k, tid), r);
+        const T uu = u0 * u0 + u1 * u1 + u2 * u2;
+        const T pf = pow(rk, gam) / gam;
+        op[r] = pf;
+        amass.add(rk);
+        aen.add(rk, uu);
+        if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
       }
     }
-    if (last) {
-      const T u0 = R.cen(1 + 2 * ND, k, tid), u1 = R.cen(2 + 2 * ND, k, tid), u2 = R.cen(3 + 2 * ND, k, tid);
-      const T uu = u0 * u0 + u1 * u1 + u2 * u2;
-      const T pf = pow(rk, gam) / gam;
-      pout[c] = pf;
-      amass.add(rk);
-      aen.add(rk, uu);
-      if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
-    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) stp(ynew[j] + c, oy[j][0], oy[j][1]);
+    if (last) stp(pout + c, op[0], op[1]);
   }
   cp_async_wait<0>();
   if (!last) return;
@@ -430,7 +496,7 @@ __global__ void __launch_bounds__(NTHR) kr_dust(const BoxDev* boxes, const int2*
 }
 
 // ---- launchers (0: the ring kernel could not be prepared) --------------------------------------
-#define RGRID(bytes) L.nblocks, dim3(TX, TY), (bytes), L.st
+#define RGRID(bytes) L.nblocks, dim3(RTX, TY), (bytes), L.st
 template <typename T>
 int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx, int mixed) {
   if (!L.ring_ok || !ring_ready<T>(mixed ? RK_CORR_M : RK_CORR_F)) return 0;

@@ -1,13 +1,17 @@
 // zring.cuh -- z-marching with asynchronous copies into shared-memory rings.
 //
-// Same 32 x 8 column tiles as zmarch.cuh, but every streamed plane lives in a
+// A block of 16 x 8 threads owns a 32 x 8 column tile and walks its z-planes;
+// each thread computes the two x-neighbouring cells (x, x+1) of its column
+// pair, so every shared-memory read, copy, slot computation and loop step
+// serves two cells, and the x-neighbours of both cells come from three
+// 8-byte (16-byte in FP64) pair reads.  Every streamed plane lives in a
 // shared ring filled by 16-byte cp.async chunks (global -> shared without
 // registers), A planes ahead of the plane being computed.  Three ring kinds:
 //   stencil field  planes k .. k+2 in use               (3 + A slots, tile + halo)
 //   face array     planes k-1 .. k (own, x-1, y-1)      (2 + A slots, tile + halo)
 //   centre field   plane k, own cells                    (1 + A slots, tile only)
 // The z-neighbours of a stencil field come from a per-thread register queue
-// (planes k-2 .. k+2 of the own column): each plane is read from shared
+// (planes k-2 .. k+2 of the own column pair): each plane is read from shared
 // memory once for the queue, when it is two planes ahead, and once per x/y
 // neighbour while it is the current plane.  One group of copies per plane;
 // before plane k a thread waits until its own copies of plane k (+2 for
@@ -37,12 +41,45 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// Threads of a ring block: 16 column pairs x 8 rows.
+constexpr int RTX = TX / 2, RNT = RTX * TY;
+
+// Two neighbouring cells of one field (x, x+1).
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <typename T>
+using P2 = typename Pair<T>::type;
+template <typename T>
+__device__ __forceinline__ T pc(const P2<T>& v, int r) {
+  return r ? v.y : v.x;
+}
+template <typename T>
+__device__ __forceinline__ P2<T> ldp(const T* p) {
+  return *reinterpret_cast<const P2<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void stp(T* p, T a, T b) {
+  P2<T> v;
+  v.x = a;
+  v.y = b;
+  *reinterpret_cast<P2<T>*>(p) = v;
+}
+
 // Tile geometry of the ring kernels: 32 x 8 columns, y-halo 2, x-halo XH (2
-// cells rounded up to one 16-byte chunk), copied in 16-byte chunks: one chunk
-// per thread and field for the tile with its star halo (corners are not
-// needed), one per thread for a centre-only plane.  Needs N % CE == 0 so no
-// chunk straddles the periodic seam; wrapped columns beyond a ragged box edge
-// hold the periodic continuation as in ZGeom.
+// cells rounded up to one 16-byte chunk), copied in 16-byte chunks: at most
+// two chunks per thread and field for the tile with its star halo (corners
+// are not needed), at most one per thread for a centre-only plane.  Needs
+// N % CE == 0 so no chunk straddles the periodic seam (and N even, so a
+// column pair is inside the box or outside it as a whole); wrapped columns
+// beyond a ragged box edge hold the periodic continuation as in ZGeom.
 template <typename T>
 struct RGeom {
   static constexpr int CE = 16 / (int)sizeof(T);  // cells per chunk
@@ -51,34 +88,40 @@ struct RGeom {
   static constexpr int ROWC = W / CE, MIDC = TX / CE;
   static constexpr int NCH = TY * ROWC + 4 * MIDC;  // chunks of a tile-with-halo plane
   static constexpr int NCC = TX * TY / CE;          // chunks of a centre plane
-  static_assert(NCH <= NTHR && NCC <= NTHR, "one chunk per thread");
+  static_assert(NCH <= 2 * RNT && NCC <= RNT, "two halo chunks and one centre chunk per thread");
   int N, NN, col, csm;
   bool active;
-  int ch_g, ch_s;  // this thread's halo-plane chunk: global column (-1: none), shared offset
-  int cc_g, cc_s;  // this thread's centre-plane chunk
+  int ch_g[2], ch_s[2];  // this thread's halo-plane chunks: global column (-1: none), shared offset
+  int cc_g, cc_s;        // this thread's centre-plane chunk
   __device__ __forceinline__ static int wrap(int v, int n) { return ((v % n) + n) % n; }
   __device__ __forceinline__ RGeom(int x0, int y0, int N_) {
     N = N_;
     NN = N * N;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
-    active = (x0 + tx < N) && (y0 + ty < N);
-    col = wrap(x0 + tx, N) + N * wrap(y0 + ty, N);
-    csm = (ty + 2) * W + tx + XH;
-    ch_g = cc_g = -1;
-    ch_s = cc_s = 0;
-    if (tid < NCH) {
-      int lx, ly;
-      if (tid < TY * ROWC) {
-        ly = tid / ROWC;
-        lx = (tid % ROWC) * CE - XH;
-      } else {
-        const int h = tid - TY * ROWC, hr = h / MIDC;
-        ly = hr < 2 ? hr - 2 : TY + hr - 2;
-        lx = (h % MIDC) * CE;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + RTX * ty;
+    active = (x0 + 2 * tx < N) && (y0 + ty < N);
+    col = wrap(x0 + 2 * tx, N) + N * wrap(y0 + ty, N);
+    csm = (ty + 2) * W + 2 * tx + XH;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int ch = tid + j * RNT;
+      ch_g[j] = -1;
+      ch_s[j] = 0;
+      if (ch < NCH) {
+        int lx, ly;
+        if (ch < TY * ROWC) {
+          ly = ch / ROWC;
+          lx = (ch % ROWC) * CE - XH;
+        } else {
+          const int h = ch - TY * ROWC, hr = h / MIDC;
+          ly = hr < 2 ? hr - 2 : TY + hr - 2;
+          lx = (h % MIDC) * CE;
+        }
+        ch_g[j] = wrap(x0 + lx, N) + N * wrap(y0 + ly, N);
+        ch_s[j] = (ly + 2) * W + lx + XH;
       }
-      ch_g = wrap(x0 + lx, N) + N * wrap(y0 + ly, N);
-      ch_s = (ly + 2) * W + lx + XH;
     }
+    cc_g = -1;
+    cc_s = 0;
     if (tid < NCC) {
       const int row = tid / (TX / CE), x = (tid % (TX / CE)) * CE;
       cc_g = wrap(x0 + x, N) + N * wrap(y0 + row, N);
@@ -92,26 +135,31 @@ struct RGeom {
 // Plane m of a tile-with-halo field / of a centre-only field into a ring slot.
 template <typename T>
 __device__ __forceinline__ void zr_issue_halo(const RGeom<T>& G, const T* g, T* slot, int m) {
-  if (G.ch_g >= 0) cp_async16(slot + G.ch_s, g + G.ch_g + G.plane(m));
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    if (G.ch_g[j] >= 0) cp_async16(slot + G.ch_s[j], g + G.ch_g[j] + G.plane(m));
 }
 template <typename T>
 __device__ __forceinline__ void zr_issue_centre(const RGeom<T>& G, const T* g, T* slot, int m) {
   if (G.cc_g >= 0) cp_async16(slot + G.cc_s, g + G.cc_g + G.plane(m));
 }
 
-// Stencil view of one field at plane k: the current ring slot (x/y
-// neighbours) and the register queue (z-neighbours and the cell itself).
+// Stencil view of one field at plane k for cell r (0: x, 1: x+1) of the
+// thread's pair: the current ring slot (x/y neighbours, read as pairs) and the
+// register queue (z-neighbours and the cell itself).
 template <typename T>
 struct ZView {
   const T* p;
-  T z[5];  // own column, planes k-2 .. k+2
-  int csm;
+  P2<T> z[5];  // own column pair, planes k-2 .. k+2
+  int csm, r;
   template <typename GT>
   __device__ __forceinline__ T at(const GT&, int d, int s) const {
-    if (d == 2) return z[2 + s];
-    return d == 0 ? p[csm + s] : p[csm + s * RGeom<T>::W];
+    if (d == 2) return pc<T>(z[2 + s], r);
+    if (d == 1) return pc<T>(ldp(p + csm + s * RGeom<T>::W), r);
+    const int o = r + s;  // -2 .. 3: pair (o >> 1), component (o & 1)
+    return pc<T>(ldp(p + csm + 2 * (o >> 1)), o & 1);
   }
-  __device__ __forceinline__ T c() const { return z[2]; }
+  __device__ __forceinline__ T c() const { return pc<T>(z[2], r); }
 };
 // Sum of two stencil views (a + b per cell, the same rounding as staging the sum).
 template <typename T>
@@ -149,7 +197,7 @@ struct RingPlan {
   const T* gs[NSF > 0 ? NSF : 1];
   const T* gf[NFF > 0 ? NFF : 1];
   const T* gc[NCF > 0 ? NCF : 1];
-  T zq[NSF > 0 ? NSF : 1][5];  // z-queues of the stencil fields (own column, planes k-2 .. k+2)
+  P2<T> zq[NSF > 0 ? NSF : 1][5];  // z-queues of the stencil fields (own pair, planes k-2 .. k+2)
   SL sl;
   int k0, kend;
   int ncf = NCF;  // centre fields copied (the first ncf of gc)
@@ -201,8 +249,8 @@ struct RingPlan {
     const int m2 = G.plane(G.wrapz(k0 - 2)), m1 = G.plane(G.wrapz(k0 - 1));
 #pragma unroll
     for (int f = 0; f < NSF; ++f) {
-      zq[f][0] = __ldg(gs[f] + G.col + m2);
-      zq[f][1] = __ldg(gs[f] + G.col + m1);
+      zq[f][0] = ldp(gs[f] + G.col + m2);
+      zq[f][1] = ldp(gs[f] + G.col + m1);
     }
   }
   // before plane k = k0 + i: wait for its copies, make them visible, start plane group
@@ -216,8 +264,8 @@ struct RingPlan {
     if (i == 0) {
 #pragma unroll
       for (int f = 0; f < NSF; ++f) {
-        zq[f][2] = sslot(f, k)[G.csm];
-        zq[f][3] = sslot(f, k + 1)[G.csm];
+        zq[f][2] = ldp(sslot(f, k) + G.csm);
+        zq[f][3] = ldp(sslot(f, k + 1) + G.csm);
       }
     } else {
 #pragma unroll
@@ -227,30 +275,35 @@ struct RingPlan {
       }
     }
 #pragma unroll
-    for (int f = 0; f < NSF; ++f) zq[f][4] = sslot(f, k + 2)[G.csm];
+    for (int f = 0; f < NSF; ++f) zq[f][4] = ldp(sslot(f, k + 2) + G.csm);
   }
-  __device__ __forceinline__ ZView<T> view(int f, int k, const G_& G) const {
+  __device__ __forceinline__ ZView<T> view(int f, int k, const G_& G, int r) const {
     ZView<T> v;
     v.csm = G.csm;
+    v.r = r;
     v.p = sslot(f, k);
 #pragma unroll
     for (int j = 0; j < 5; ++j) v.z[j] = zq[f][j];
     return v;
   }
-  // faces f0, f0+1, f0+2 (x, y, z arrays): values at the +1/2 and -1/2 faces of the cell
-  __device__ __forceinline__ void faces(int f0, int k, const G_& G, T (&plus)[3], T (&minus)[3]) const {
+  // faces f0, f0+1, f0+2 (x, y, z arrays) of cell r: values at its +1/2 and -1/2 faces
+  __device__ __forceinline__ void faces(int f0, int k, const G_& G, int r, T (&plus)[3], T (&minus)[3]) const {
     const T* fx = rf + (f0 * SL::NF + sl.f(k)) * HW;
     const T* fy = rf + ((f0 + 1) * SL::NF + sl.f(k)) * HW;
     const T* fz = rf + ((f0 + 2) * SL::NF + sl.f(k)) * HW;
     const T* fzm = rf + ((f0 + 2) * SL::NF + sl.f(k - 1)) * HW;
-    plus[0] = fx[G.csm];
-    minus[0] = fx[G.csm - 1];
-    plus[1] = fy[G.csm];
-    minus[1] = fy[G.csm - G_::W];
-    plus[2] = fz[G.csm];
-    minus[2] = fzm[G.csm];
+    const P2<T> xc = ldp(fx + G.csm), xl = ldp(fx + G.csm - 2);
+    plus[0] = pc<T>(xc, r);
+    minus[0] = r ? xc.x : xl.y;
+    plus[1] = pc<T>(ldp(fy + G.csm), r);
+    minus[1] = pc<T>(ldp(fy + G.csm - G_::W), r);
+    plus[2] = pc<T>(ldp(fz + G.csm), r);
+    minus[2] = pc<T>(ldp(fzm + G.csm), r);
   }
-  __device__ __forceinline__ T cen(int f, int k, int tid) const { return rc[(f * SL::NC + sl.c(k)) * NTHR + tid]; }
+  // centre field f at plane k, both cells of the pair
+  __device__ __forceinline__ P2<T> cen(int f, int k, int tid) const {
+    return ldp(rc + (f * SL::NC + sl.c(k)) * NTHR + 2 * tid);
+  }
 };
 
 }  // namespace fe
