@@ -535,6 +535,8 @@ template <typename V> int rlaunch_asm(const Launch& L, int s, int up0, int php0,
 template <typename V> int rlaunch_accel(const Launch& L, int kset, int pk);
 template <typename V> int rlaunch_fluxn(const Launch& L, int s, int nd);
 template <typename V> int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd);
+template <typename V> int rlaunch_div(const Launch& L, int u0);
+template <typename V> int rlaunch_rhs(const Launch& L, int s, int rhop, int pp);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
 template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);
 int bulk_cg_pairs(int N);  // (row group, plane) pairs of the streamed CG kernel for an N^3 box

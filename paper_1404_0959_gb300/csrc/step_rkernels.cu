@@ -11,11 +11,10 @@ namespace fe {
 
 // Lookahead planes of each ring kernel (shared memory per block grows with
 // it; measured at 256^3 FP32 with column-pair threads: the corrector, the
-// predictor and Du/Dt run best with two planes, the assembly and the dust
-// kernels with one), and the predictor's register cap (three resident blocks
-// per SM in FP32: its 174-register build left it at two and ran 25 % slower).  The
-// divergence and the right-hand side keep their register-queue z-marching
-// kernels, which measured faster.
+// predictor, Du/Dt, the divergence and the right-hand side run best with two
+// planes, the assembly and the dust kernels with one), and the predictor's
+// register cap (three resident blocks per SM in FP32: its 174-register build
+// left it at two and ran 25 % slower).
 #ifndef FE_RING_A
 #define FE_RING_A 2
 #endif
@@ -44,7 +43,7 @@ __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
 constexpr int kMaxDev = 64;
 // per device, one bit per ring kernel (set when its shared-memory limit was accepted)
 enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
-                  RK_DUST3 };
+                  RK_DUST3, RK_DIV, RK_RHS };
 template <typename T>
 struct RingReady {
   static unsigned ok[kMaxDev];
@@ -495,6 +494,77 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
   }
 }
 
+// ---- velocity divergence div = sum_m Gc_m(u_m) --------------------------------------------------------
+template <typename T>
+using DivPlan = RingPlan<T, kA, 3, 0, 0>;  // u0..2
+template <typename T>
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes, const int2* work, int u0) {
+  RING_PROLOGUE(DivPlan<T>);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, u0 + m);
+  T* __restrict__ div = Fr<T>(B, W_DIV);
+  const T ih = (T)B.ih;
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    T od[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
+      od[r] = (zGc_h(u[0], G, 0) + zGc_h(u[1], G, 1) + zGc_h(u[2], G, 2)) * ih;
+    }
+    stp(div + G.col + G.plane(k), od[0], od[1]);
+  }
+  cp_async_wait<0>();
+}
+
+// ---- phi* and the pressure right-hand side --------------------------------------------------------------
+template <typename T>
+using RhsPlan = RingPlan<T, kA, 5, 0, 2>;  // rho', HbyA0..2, p | | rho^n, D phi^n
+template <typename T>
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
+                                                            int pp) {
+  RING_PROLOGUE(RhsPlan<T>);
+  R.gs[0] = Fr<T>(B, rhop);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gs[1 + d] = Fr<T>(B, W_HB0 + d);
+  R.gs[4] = Fr<T>(B, pp);
+  R.gc[0] = Fr<T>(B, S(s, F_RHO));
+  R.gc[1] = Fr<T>(B, W_DIVPHI);
+  T* __restrict__ ps[3] = {Fr<T>(B, W_PS0), Fr<T>(B, W_PS1), Fr<T>(B, W_PS2)};
+  T* __restrict__ b = Fr<T>(B, K_B);
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+    const P2<T> crho = R.cen(0, k, tid), cdp = R.cen(1, k, tid);
+    T ops[3][2], ob[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const ZView<T> rp = R.view(0, k, G, r), p = R.view(4, k, G, r);
+      const ZView<T> hb[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
+      T dsum = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T fp = zI4(rp, G, d, 0) * zI4(hb[d], G, d, 0) - dt * (p.at(G, d, 1) - p.c()) * ih;
+        const T fm = zI4(rp, G, d, -1) * zI4(hb[d], G, d, -1) - dt * (p.c() - p.at(G, d, -1)) * ih;
+        ops[d][r] = fp;
+        dsum += fp - fm;
+      }
+      ob[r] = -((rp.c() - pc<T>(crho, r)) * idt + T(0.5) * pc<T>(cdp, r) + T(0.5) * dsum * ih);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) stp(ps[d] + c, ops[d][0], ops[d][1]);
+    stp(b + c, ob[0], ob[1]);
+  }
+  cp_async_wait<0>();
+}
+
 // ---- launchers (0: the ring kernel could not be prepared) --------------------------------------
 #define RGRID(bytes) L.nblocks, dim3(RTX, TY), (bytes), L.st
 template <typename T>
@@ -559,6 +629,19 @@ int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, i
 }
 
 template <typename T>
+int rlaunch_div(const Launch& L, int u0) {
+  if (!L.ring_ok || !ring_ready<T>(RK_DIV)) return 0;
+  FE_LAUNCH(L, KID_DIV, (kr_div<T><<<RGRID(DivPlan<T>::bytes)>>>(L.boxes, L.work, u0)));
+  return 1;
+}
+template <typename T>
+int rlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
+  if (!L.ring_ok || !ring_ready<T>(RK_RHS)) return 0;
+  FE_LAUNCH(L, KID_RHS, (kr_rhs<T><<<RGRID(RhsPlan<T>::bytes)>>>(L.boxes, L.work, s, rhop, pp)));
+  return 1;
+}
+
+template <typename T>
 int rprepare() {
   const int dev = current_device();
   if (dev < 0) return 0;
@@ -575,6 +658,8 @@ int rprepare() {
   set(RK_DUST1, set_smem(kr_dust<T, 1>, DustPlan<T, 1>::bytes));
   set(RK_DUST2, set_smem(kr_dust<T, 2>, DustPlan<T, 2>::bytes));
   set(RK_DUST3, set_smem(kr_dust<T, 3>, DustPlan<T, 3>::bytes));
+  set(RK_DIV, set_smem(kr_div<T>, DivPlan<T>::bytes));
+  set(RK_RHS, set_smem(kr_rhs<T>, RhsPlan<T>::bytes));
   cudaGetLastError();  // a refused limit is not an error of the context
   ok &= ~(unsigned)(FE_RING_OFF);
   RingReady<T>::ok[dev] = ok;
@@ -588,6 +673,8 @@ int rprepare() {
   template int rlaunch_accel<T>(const Launch&, int, int);                         \
   template int rlaunch_fluxn<T>(const Launch&, int, int);                         \
   template int rlaunch_dust<T>(const Launch&, int, int, int, int, int, int);      \
+  template int rlaunch_div<T>(const Launch&, int);                                \
+  template int rlaunch_rhs<T>(const Launch&, int, int, int);                      \
   template int rprepare<T>();
 RINST(double)
 RINST(float)

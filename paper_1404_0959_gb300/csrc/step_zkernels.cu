@@ -521,6 +521,7 @@ __global__ void __launch_bounds__(NTHR, 2) kz_dust(const BoxDev* boxes, const in
 // ---- launchers ---------------------------------------------------------------------------------
 #define ZGRID L.nblocks, dim3(TX, TY), 0, L.st
 template <typename T> void zlaunch_div(const Launch& L, int u0) {
+  if (rlaunch_div<T>(L, u0)) return;
   FE_LAUNCH(L, KID_DIV, (kz_div<T><<<ZGRID>>>(L.boxes, L.work, u0)));
 }
 template <typename T> void zlaunch_pred(const Launch& L, int s, int k) {
@@ -532,6 +533,7 @@ template <typename T> void zlaunch_asm(const Launch& L, int s, int up0, int php0
   FE_LAUNCH(L, KID_ASM, (kz_asm<T><<<ZGRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
 }
 template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
+  if (rlaunch_rhs<T>(L, s, rhop, pp)) return;
   FE_LAUNCH(L, KID_RHS, (kz_rhs<T><<<ZGRID>>>(L.boxes, L.work, s, rhop, pp)));
 }
 template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
