@@ -974,7 +974,7 @@ template <typename T>
 __global__ void k_psi_box(const BoxDev* boxes, int box, int s, double dt) {
   const BoxDev& B = boxes[box];
   T* dinv = (T*)B.f[W_DINV];
-  const T idt = (T)(1.0 / dt), c3 = (T)(3.0 * dt * B.ih * B.ih);
+  const JacobiDiag<T> jd(dt, B.ih);
   const long n = (long)B.N * B.N * B.N;
   const T* rho = (const T*)B.f[S(s, F_RHO)];
   const T* p = (const T*)B.f[S(s, F_P)];
@@ -984,7 +984,7 @@ __global__ void k_psi_box(const BoxDev* boxes, int box, int s, double dt) {
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     T ps = rho[q] / ((T)B.gamma * p[q]);
     psi[q] = ps;
-    dinv[q] = T(1) / (ps * idt + c3);
+    dinv[q] = jd.inv(ps);
     for (int d = 0; d < 3; ++d) hb[d][q] = u[d][q];
   }
 }

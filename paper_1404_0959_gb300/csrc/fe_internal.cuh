@@ -188,6 +188,24 @@ __device__ __forceinline__ DF df_from_double(double d) {
   return DF{hi, (float)(d - (double)hi)};
 }
 
+// ---- Jacobi preconditioner ---------------------------------------------------------
+// 1 / diag(M) = 1 / (psi/dt + 3 dt/h^2) in the field precision, with one fused
+// multiply-add: every kernel that stores it and every kernel that forms it on
+// the fly gets the same bits.
+template <typename T>
+struct JacobiDiag {
+  T idt, c3;
+  __device__ __forceinline__ JacobiDiag(double dt, double ih) {
+    const T d = (T)dt, h = (T)ih;
+    idt = T(1) / d;
+    c3 = T(3) * d * h * h;
+  }
+  __device__ __forceinline__ T inv(T psi) const { return rcp_rn(fma(psi, idt, c3)); }
+  // correctly rounded reciprocal (the same value as 1 / v in IEEE division)
+  __device__ __forceinline__ static float rcp_rn(float v) { return __frcp_rn(v); }
+  __device__ __forceinline__ static double rcp_rn(double v) { return __drcp_rn(v); }
+};
+
 // ---- inner-product accumulation ----------------------------------------------------
 // double vectors: FP64 fused multiply-add.  float vectors: the compensated
 // "Dot2" scheme of Ogita, Rump and Oishi ("Accurate sum and dot product",
@@ -332,11 +350,12 @@ __device__ __forceinline__ void st4(double* p, const V4<double>& a) {
 
 // ---- deterministic reductions ----------------------------------------------------
 // Last-block phase of the block sums: the box's last block to finish adds the
-// partials of all its blocks in block order.  Blocks of up to NTHR threads
-// (a multiple of 32), 1-D or 2-D.
+// partials of all its blocks in block order.  Blocks of up to 32 warps
+// (a multiple of 32 threads), 1-D or 2-D.
+constexpr int kMaxWarps = 32;
 template <int K>
 __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
-  __shared__ double red[K][NTHR / 32];
+  __shared__ double red[K][kMaxWarps];
   __shared__ int last;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
@@ -376,7 +395,7 @@ __device__ bool sum_partials_last(const BoxDev& B, double* part, double* res, in
 // tile0/ntiles: the box's block range in the work list of this launch.
 template <int K>
 __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
-  __shared__ double red[K][NTHR / 32];
+  __shared__ double red[K][kMaxWarps];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -400,7 +419,7 @@ __device__ bool block_sum_last(double (&v)[K], const BoxDev& B, double* part, do
 // Float-pair values: the warp and block trees add pairs on the FP32 pipe.
 template <int K>
 __device__ bool block_sum_last(DF (&v)[K], const BoxDev& B, double* part, double* res, int tile0, int ntiles) {
-  __shared__ DF red[K][NTHR / 32];
+  __shared__ DF red[K][kMaxWarps];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -428,7 +447,7 @@ __device__ bool block_sum_last(DF (&v)[K], const BoxDev& B, double* part, double
 // Same for a maximum of one value.
 __device__ __forceinline__ bool block_max_last(double v, const BoxDev& B, double* part, double* res, int tile0,
                                                int ntiles) {
-  __shared__ double red[NTHR / 32];
+  __shared__ double red[kMaxWarps];
   __shared__ int last;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;

@@ -451,18 +451,19 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
     T* st = stage0 + (j % kBulkStages) * SE;
     uint64_t* bj = bar + (j % kBulkStages);
     const int y0 = P.g * R;
-    const int ym = y0 == 0 ? N - 1 : y0 - 1, yp = y0 + R == N ? 0 : y0 + R;
+    const int ym = y0 == 0 ? N - 1 : y0 - 1;
     const size_t pl = (size_t)P.m * NN;
     const bool comp = P.pos >= 1 && P.pos <= P.len;
     const unsigned row = (unsigned)(N * sizeof(T)), rows = (unsigned)(RN * sizeof(T));
     mbar_expect_tx(bj, 3 * (rows + 2 * row) + (comp ? 2 * rows : 0));
     const T* src[3] = {r, dinv, po};
+    // rows ym .. ym + R + 1 of each stream: one copy, two where they wrap in y
+    const int n0 = min(R + 2, N - ym);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       T* d = st + f * HN;
-      bulk_g2s(d, src[f] + pl + (size_t)ym * N, row, bj);
-      bulk_g2s(d + N, src[f] + pl + (size_t)y0 * N, rows, bj);
-      bulk_g2s(d + N + RN, src[f] + pl + (size_t)yp * N, row, bj);
+      bulk_g2s(d, src[f] + pl + (size_t)ym * N, (unsigned)n0 * row, bj);
+      if (n0 < R + 2) bulk_g2s(d + n0 * N, src[f] + pl, (unsigned)(R + 2 - n0) * row, bj);
     }
     if (comp) {
       bulk_g2s(st + 3 * HN, psi + pl + (size_t)y0 * N, rows, bj);

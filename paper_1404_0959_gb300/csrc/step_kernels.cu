@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NTHR, 3) k_pred(const BoxDev* boxes, const int
   T* rho0 = F<T>(B, S(kset, F_RHO));
   T* us[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
-  const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
+  const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
   for (int k = t.k0; k < t.kend; ++k) {
     Nbr n(t.i, t.j, k, B.N);
     const int c = n(0, 0, 0);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(NTHR, 3) k_pred(const BoxDev* boxes, const int
     }
     const T ps = r / (gam * __ldg(&p[c]));
     psi[c] = ps;
-    dinv[c] = T(1) / (ps * idt + c3);
+    dinv[c] = jd.inv(ps);
     divphi[c] = dph;
     rho0[c] = r0;
   }

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
   T* __restrict__ rho0 = Fr<T>(B, S(kset, F_RHO));
   T* __restrict__ us[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
-  const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
+  const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
       }
       const T ps = rc / (gam * p.c());
       ops[r] = ps;
-      odi[r] = T(1) / (ps * idt + c3);
+      odi[r] = jd.inv(ps);
       odp[r] = dph;
       or0[r] = r0;
     }

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
   T* __restrict__ rho0 = Fz<T>(B, S(kset, F_RHO));
   T* __restrict__ us[3] = {Fz<T>(B, S(kset, F_U0)), Fz<T>(B, S(kset, F_U1)), Fz<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
-  const T idt = T(1) / dt, c3 = T(3) * dt * ih * ih;
+  const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
   for (int k = t.k0; k < t.kend; ++k) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) u[m].advance(G, k);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
     }
     const T ps = r / (gam * p.c());
     psi[c] = ps;
-    dinv[c] = T(1) / (ps * idt + c3);
+    dinv[c] = jd.inv(ps);
     divphi[c] = dph;
     rho0[c] = r0;
   }
