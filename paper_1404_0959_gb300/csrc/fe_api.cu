@@ -586,12 +586,16 @@ static int cg_iterate(fe_ctx* c, int maxit, int key) {
   return FE_OK;
 }
 
+// started: the right-hand-side kernel of the step already started the refined
+// solve (K_AUX, K_R and the scalars); otherwise start it from K_B here.
 template <typename T>
-static int refine_solve(fe_ctx* c) {
+static int refine_solve(fe_ctx* c, bool started) {
   Launch L = c->L();
-  CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
-  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
-  launch_mix_first_init<T>(L, c->douter);
+  if (!started) {
+    CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
+    CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
+    launch_refine_start<T>(L, c->douter);
+  }
   for (int outer = 0; outer < 8; ++outer) {
     CK(cudaMemcpyAsync(c->hactive, c->douter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -607,9 +611,9 @@ static int refine_solve(fe_ctx* c) {
 }
 
 template <typename T>
-static int pressure_solve(fe_ctx* c) {
+static int pressure_solve(fe_ctx* c, bool started = false) {
   if (c->fp64) return inner_solve<T>(c, c->prm.p_maxit, 0);
-  if (fused_refine(c)) return refine_solve<T>(c);
+  if (fused_refine(c)) return refine_solve<T>(c, started);
   Launch L = c->L();
   CK(cudaMemsetAsync(c->douter, 0, sizeof(int), c->st));
   launch_mix_residual<T>(L, 1, c->douter);
@@ -728,10 +732,7 @@ static int pressure_graph(fe_ctx* c) {
   cudaStream_t cs = c->cap[0], bs = c->cap[1];
   Launch L = c->L();
   L.st = cs;
-  if (fused_refine(c)) {
-    CK(cudaMemsetAsync(c->douter, 0, sizeof(int), cs));
-    CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), cs));
-    launch_mix_first_init<T>(L, c->douter);
+  if (fused_refine(c)) {  // the right-hand-side kernel started the refined solve
     CK(cudaMemsetAsync(c->dloop + 3, 0, sizeof(int), cs));
     cudaGraphConditionalHandle ho, hi;
     int rc = while_begin(cs, bs, &ho);  // refinement steps
@@ -794,8 +795,16 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
     const int pn = W_PW0 + (kk & 1);
     if (kk == 0) launch_div<T>(L, up0);
     launch_asm<T>(L, s, up0, php0, rhop);
-    launch_rhs<T>(L, s, rhop, pp);
-    int rc = graph ? pressure_graph<T>(c) : pressure_solve<T>(c);
+    if (fused_refine(c)) {  // b, the first inner right-hand side and the solve's start in one pass
+      CK(cudaMemsetAsync(c->douter, 0, sizeof(int), L.st));
+      CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), L.st));
+      Launch Lr = L;
+      Lr.rstart = c->douter;
+      launch_rhs<T>(Lr, s, rhop, pp);
+    } else {
+      launch_rhs<T>(L, s, rhop, pp);
+    }
+    int rc = graph ? pressure_graph<T>(c) : pressure_solve<T>(c, true);
     if (rc != FE_OK) return rc;
     if (!graph && c->harvest_b && c->harvest_n < c->harvest_max) {
       const size_t bytes = (size_t)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N * sizeof(T);

@@ -287,6 +287,62 @@ __device__ __forceinline__ DF red_from<float>(double v) {
   return df_from_double(v);
 }
 
+// ---- mixed-precision refinement and CG start bookkeeping (last block of a reduction) ----
+// Refinement scalars after a residual evaluation, ||r||^2 = rr (first: of the
+// right-hand side itself), and the tolerance of the next inner solve: the
+// outer target with a safety margin, never below what an FP32 Krylov
+// recurrence resolves.
+#ifndef FE_INNER_MARGIN
+#define FE_INNER_MARGIN 0.5
+#endif
+#ifndef FE_INNER_FLOOR
+#define FE_INNER_FLOOR 1e-6
+#endif
+__device__ inline void mix_finish_scalars(const BoxDev& B, double rr, int first, int* outer_active) {
+  double* sc = B.sc;
+  if (first) {
+    sc[SC_OBB] = rr;
+    sc[SC_ITSUM] = 0.0;
+    sc[SC_OUTER] = 0.0;
+    bool zero = !(rr > 0.0);
+    sc[SC_ODONE] = zero ? 1.0 : 0.0;
+    sc[SC_CONV] = zero ? 1.0 : 0.0;
+    if (!zero) atomicAdd(outer_active, 1);
+  } else if (sc[SC_ODONE] == 0.0) {
+    sc[SC_ITSUM] += sc[SC_ITERS];
+    sc[SC_OUTER] += 1.0;
+    if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
+      sc[SC_ODONE] = 1.0;
+      sc[SC_CONV] = 1.0;
+      atomicSub(outer_active, 1);
+    } else if (sc[SC_OUTER] >= 8.0) {
+      sc[SC_ODONE] = 1.0;
+      sc[SC_CONV] = 0.0;
+      atomicSub(outer_active, 1);
+    }
+  }
+  sc[SC_ORR] = rr;
+  sc[SC_ORES] = sc[SC_OBB] > 0.0 ? sqrt(rr / sc[SC_OBB]) : 0.0;
+  // inner tolerance: reach the outer target with a factor 2 margin, within FP32 reach
+  double need = rr > 0.0 ? FE_INNER_MARGIN * sc[SC_OTOL] * sqrt(sc[SC_OBB] / rr) : 0.5;
+  sc[SC_TOL] = fmin(0.5, fmax(need, FE_INNER_FLOOR));
+}
+
+// The CG scalars of a new inner solve from its right-hand side r: rz, ||r||^2,
+// counters, and whether it runs (not for a box whose refinement has converged).
+__device__ inline void cg_start_scalars(const BoxDev& B, double rz, double rr, int* active) {
+  double* sc = B.sc;
+  sc[SC_ITERS] = 0.0;
+  sc[SC_ALPHA] = 0.0;
+  sc[SC_BETA] = 0.0;
+  sc[SC_RZ] = rz;
+  sc[SC_BB] = rr;
+  const bool run = sc[SC_ODONE] == 0.0 && rr > 0.0;
+  sc[SC_DONE] = run ? 0.0 : 1.0;
+  if (run) atomicAdd(active, 1);
+  else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;  // a finished refinement keeps its verdict
+}
+
 // ---- block prologue -----------------------------------------------------------
 struct Tile {
   int box, i, j, k0, kend;
@@ -514,6 +570,7 @@ struct Launch {
   const int2* bwork;  // plane-streaming blocks (box, block of box); null: z-marching kernels
   int nbblocks;
   int bsmem;          // dynamic shared memory of the streamed CG kernel
+  int* rstart = nullptr;  // right-hand-side kernels: also start the refined solve (outer counter)
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -543,7 +600,7 @@ template <typename V> void launch_cg_matvec(const Launch& L);
 template <typename V> void launch_cg_update(const Launch& L);
 template <typename V> void launch_cg_fused(const Launch& L);   // symmetric operator: dir + matvec, then update
 template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
-template <typename V> void launch_mix_first_init(const Launch& L, int* outer_active);  // fused refinement: start
+template <typename V> void launch_refine_start(const Launch& L, int* outer_active);  // fused refinement: start from K_B
 template <typename V> void launch_refine(const Launch& L, int* outer_active);          // fused refinement: boundary
 template <typename V> void launch_mix_finish_pp(const Launch& L);  // final x from the ping-ponged pairs
 // PISO kernels on asynchronous-copy rings (return 0: not launched, use the z-marching kernel)

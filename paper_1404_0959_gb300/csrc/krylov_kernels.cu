@@ -958,35 +958,6 @@ __device__ __forceinline__ DF residual_df(const BoxDev& B, const float2* __restr
 
 // Box bookkeeping after a refinement residual: convergence, counters, the FP64
 // residual report and the next inner tolerance.
-__device__ void mix_finish_scalars(const BoxDev& B, double rr, int first, int* outer_active) {
-  double* sc = B.sc;
-  if (first) {
-    sc[SC_OBB] = rr;
-    sc[SC_ITSUM] = 0.0;
-    sc[SC_OUTER] = 0.0;
-    bool zero = !(rr > 0.0);
-    sc[SC_ODONE] = zero ? 1.0 : 0.0;
-    sc[SC_CONV] = zero ? 1.0 : 0.0;
-    if (!zero) atomicAdd(outer_active, 1);
-  } else if (sc[SC_ODONE] == 0.0) {
-    sc[SC_ITSUM] += sc[SC_ITERS];
-    sc[SC_OUTER] += 1.0;
-    if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
-      sc[SC_ODONE] = 1.0;
-      sc[SC_CONV] = 1.0;
-      atomicSub(outer_active, 1);
-    } else if (sc[SC_OUTER] >= 8.0) {
-      sc[SC_ODONE] = 1.0;
-      sc[SC_CONV] = 0.0;
-      atomicSub(outer_active, 1);
-    }
-  }
-  sc[SC_ORR] = rr;
-  sc[SC_ORES] = sc[SC_OBB] > 0.0 ? sqrt(rr / sc[SC_OBB]) : 0.0;
-  // inner tolerance: reach the outer target with a factor 2 margin, within FP32 reach
-  double need = rr > 0.0 ? 0.5 * sc[SC_OTOL] * sqrt(sc[SC_OBB] / rr) : 0.5;
-  sc[SC_TOL] = fmin(0.5, fmax(need, 1e-6));
-}
 
 // First refinement step (element-wise): keep b in K_AUX, x pairs = 0, ||b||^2.
 template <typename T>
@@ -1078,26 +1049,16 @@ __global__ void __launch_bounds__(NTHR) kz_mix_residual(const BoxDev* boxes, con
 }
 
 // ---- fused refinement of the plain-CG mixed-precision solve -----------------------------------
-// The CG scalars of a new inner solve from its right-hand side r: rz, ||r||^2,
-// counters, and whether it runs (not for a box whose refinement has converged).
-__device__ void cg_start_scalars(const BoxDev& B, double rz, double rr, int* active) {
-  double* sc = B.sc;
-  sc[SC_ITERS] = 0.0;
-  sc[SC_ALPHA] = 0.0;
-  sc[SC_BETA] = 0.0;
-  sc[SC_RZ] = rz;
-  sc[SC_BB] = rr;
-  const bool run = sc[SC_ODONE] == 0.0 && rr > 0.0;
-  sc[SC_DONE] = run ? 0.0 : 1.0;
-  if (run) atomicAdd(active, 1);
-  else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;  // a finished refinement keeps its verdict
-}
 
-// Start: keep b in K_AUX, x pairs = 0, r = b; ||b||^2 and <b, D^{-1} b> (the
-// first CG iteration forms pd = D^{-1} r itself and treats x as 0).
+
+// Start of a refined solve whose right-hand side is in K_B (the standalone
+// pressure solve; in a step the right-hand-side kernel does this itself):
+// b to K_AUX and to the first inner right-hand side K_R, ||b||^2 and
+// <b, D^{-1} b> into the refinement and CG scalars.  The solution pairs start
+// as zero by the outer-step count (nothing is written to them).
 template <typename T>
-__global__ void __launch_bounds__(NTHR) k_mix_first_init(const BoxDev* boxes, const int2* ework, double* part,
-                                                         int* outer_active, int* active) {
+__global__ void __launch_bounds__(NTHR) k_refine_start(const BoxDev* boxes, const int2* ework, double* part,
+                                                       int* outer_active, int* active) {
   const Chunk ch = chunk_of(boxes, ework);
   const BoxDev& B = boxes[ch.box];
   const int tid = threadIdx.x + TX * threadIdx.y;
@@ -1105,31 +1066,27 @@ __global__ void __launch_bounds__(NTHR) k_mix_first_init(const BoxDev* boxes, co
   const T* __restrict__ dinv = F<T>(B, W_DINV);
   T* __restrict__ borig = F<T>(B, K_AUX);
   T* __restrict__ r = F<T>(B, K_R);
-  float2* __restrict__ xs = F<float2>(B, K_X64);
-  DotAcc<float> arr, arz;
+  DotAcc<T> arr, arz;
   chunk_loop(
       ch, tid,
       [&](int q0) {
         const V4<T> bv = ld4(b + q0), dv = ld4(dinv + q0);
         st4(borig + q0, bv);
         st4(r + q0, bv);
-        reinterpret_cast<float4*>(xs + q0)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        reinterpret_cast<float4*>(xs + q0)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          arr.add((float)bv.v[e], (float)bv.v[e]);
-          arz.add((float)bv.v[e], (float)(bv.v[e] * dv.v[e]));
+          arr.add(bv.v[e], bv.v[e]);
+          arz.add(bv.v[e], bv.v[e] * dv.v[e]);
         }
       },
       [&](int c) {
         const T bc = b[c];
         borig[c] = bc;
         r[c] = bc;
-        xs[c] = make_float2(0.f, 0.f);
-        arr.add((float)bc, (float)bc);
-        arz.add((float)bc, (float)(bc * dinv[c]));
+        arr.add(bc, bc);
+        arz.add(bc, bc * dinv[c]);
       });
-  DF v[2] = {arr.red(), arz.red()};
+  Red<T> v[2] = {arr.red(), arz.red()};
   __shared__ double res[2];
   if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -1164,10 +1121,10 @@ struct PairSrc {
   const T* __restrict__ x;
   const T* __restrict__ pd;
   T alpha;
-  bool moved;
+  bool moved, fresh;
   __device__ __forceinline__ PairRaw<T> load(int q) const {
     PairRaw<T> v;
-    v.a = __ldg(&xo[q]);
+    v.a = fresh ? make_float2(0.f, 0.f) : __ldg(&xo[q]);
     v.x = moved ? __ldg(&x[q]) : T(0);
     v.p = moved ? __ldg(&pd[q]) : T(0);
     return v;
@@ -1192,6 +1149,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
   __shared__ float2 sm[ZGeom<1>::H * ZGeom<1>::W];
   const int par = ((int)B.sc[SC_OUTER]) & 1, it = (int)B.sc[SC_ITERS];
   PairSrc<T> src;
+  src.fresh = B.sc[SC_OUTER] == 0.0;  // first boundary: the pairs start as zero
   src.xo = F<float2>(B, par ? K_X64B : K_X64);
   src.x = F<T>(B, K_X);
   src.pd = F<T>(B, (it & 1) ? K_PP : K_PD);
@@ -1337,9 +1295,10 @@ __global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const 
   const int tid = threadIdx.x + TX * threadIdx.y;
   T* __restrict__ x = F<T>(B, K_X);
   const bool second = pingpong && (((int)B.sc[SC_OUTER]) & 1);
+  const bool zero = pingpong && B.sc[SC_OUTER] == 0.0;  // no boundary pass ran: the pairs are zero
   const float2* __restrict__ xs = F<float2>(B, second ? K_X64B : K_X64);
   for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
-    const float2 a = xs[c];
+    const float2 a = zero ? make_float2(0.f, 0.f) : xs[c];
     x[c] = (T)__fadd_rn(a.x, a.y);
   }
 }
@@ -1487,8 +1446,8 @@ template <typename T> void launch_mix_residual(const Launch& L, int first, int* 
   else
     FE_LAUNCH(L, KID_MIX_RES, (kz_mix_residual<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active)));
 }
-template <typename T> void launch_mix_first_init(const Launch& L, int* outer_active) {
-  FE_LAUNCH(L, KID_MIX_RES, (k_mix_first_init<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active, L.active)));
+template <typename T> void launch_refine_start(const Launch& L, int* outer_active) {
+  FE_LAUNCH(L, KID_MIX_RES, (k_refine_start<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active, L.active)));
 }
 template <typename T> void launch_refine(const Launch& L, int* outer_active) {
   FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
@@ -1539,8 +1498,8 @@ int bulk_cg_blocks_per_sm(int bytes) {
   template void launch_bicg_x<T>(const Launch&);                 \
   template void launch_mix_residual<T>(const Launch&, int, int*); \
   template void launch_mix_accum<T>(const Launch&);              \
-  template void launch_mix_first_init<T>(const Launch&, int*);   \
   template void launch_refine<T>(const Launch&, int*);           \
+  template void launch_refine_start<T>(const Launch&, int*);     \
   template void launch_mix_finish_pp<T>(const Launch&);          \
   template void launch_mix_finish<T>(const Launch&);              \
   template void launch_fcg<T>(const Launch&, const float*);

@@ -521,11 +521,15 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes,
 }
 
 // ---- phi* and the pressure right-hand side --------------------------------------------------------------
+// With rstart (mixed-precision plain CG) b goes straight to the refinement's
+// copy (K_AUX) and to the first inner right-hand side (K_R), and the kernel
+// starts the refined solve: ||b||^2 and <b, D^{-1} b> into the refinement and
+// CG scalars (the solution pairs start as zero by the outer-step count).
 template <typename T>
-using RhsPlan = RingPlan<T, kA, 5, 0, 2>;  // rho', HbyA0..2, p | | rho^n, D phi^n
+using RhsPlan = RingPlan<T, kA, 5, 0, 3>;  // rho', HbyA0..2, p | | rho^n, D phi^n [, D^{-1}]
 template <typename T>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
-                                                            int pp) {
+                                                            int pp, double* part, int* rstart, int* active) {
   RING_PROLOGUE(RhsPlan<T>);
   R.gs[0] = Fr<T>(B, rhop);
 #pragma unroll
@@ -533,9 +537,14 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
   R.gs[4] = Fr<T>(B, pp);
   R.gc[0] = Fr<T>(B, S(s, F_RHO));
   R.gc[1] = Fr<T>(B, W_DIVPHI);
+  R.gc[2] = Fr<T>(B, W_DINV);
+  const bool start = rstart != nullptr;
+  if (!start) R.ncf = 2;
   T* __restrict__ ps[3] = {Fr<T>(B, W_PS0), Fr<T>(B, W_PS1), Fr<T>(B, W_PS2)};
-  T* __restrict__ b = Fr<T>(B, K_B);
+  T* __restrict__ b = Fr<T>(B, start ? K_AUX : K_B);
+  T* __restrict__ r0 = Fr<T>(B, K_R);
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
+  DotAcc<T> abb, abz;
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
@@ -561,8 +570,26 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
 #pragma unroll
     for (int d = 0; d < 3; ++d) stp(ps[d] + c, ops[d][0], ops[d][1]);
     stp(b + c, ob[0], ob[1]);
+    if (start) {
+      const P2<T> cd = R.cen(2, k, tid);
+      stp(r0 + c, ob[0], ob[1]);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        abb.add(ob[r], ob[r]);
+        abz.add(ob[r], ob[r] * pc<T>(cd, r));
+      }
+    }
   }
   cp_async_wait<0>();
+  if (!start) return;
+  Red<T> v[2] = {abb.red(), abz.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      mix_finish_scalars(B, res[0], 1, rstart);
+      cg_start_scalars(B, res[1], res[0], active);
+    }
+  }
 }
 
 // ---- launchers (0: the ring kernel could not be prepared) --------------------------------------
@@ -637,7 +664,8 @@ int rlaunch_div(const Launch& L, int u0) {
 template <typename T>
 int rlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (!L.ring_ok || !ring_ready<T>(RK_RHS)) return 0;
-  FE_LAUNCH(L, KID_RHS, (kr_rhs<T><<<RGRID(RhsPlan<T>::bytes)>>>(L.boxes, L.work, s, rhop, pp)));
+  FE_LAUNCH(L, KID_RHS,
+            (kr_rhs<T><<<RGRID(RhsPlan<T>::bytes)>>>(L.boxes, L.work, s, rhop, pp, L.part, L.rstart, L.active)));
   return 1;
 }
 

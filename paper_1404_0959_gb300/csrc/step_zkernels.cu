@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(NTHR) kz_asm(const BoxDev* boxes, const int2* 
 
 // ---- phi*, right-hand side ---------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kz_rhs(const BoxDev* boxes, const int2* work, int s, int rhop, int pp) {
+__global__ void __launch_bounds__(NTHR) kz_rhs(const BoxDev* boxes, const int2* work, int s, int rhop, int pp,
+                                                double* part, int* rstart, int* active) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   const ZGeom<2> G(t.x0, t.y0, B.N);
@@ -185,8 +186,14 @@ __global__ void __launch_bounds__(NTHR) kz_rhs(const BoxDev* boxes, const int2* 
   const T* __restrict__ rho = Fz<T>(B, S(s, F_RHO));
   const T* __restrict__ divphi = Fz<T>(B, W_DIVPHI);
   T* __restrict__ ps[3] = {Fz<T>(B, W_PS0), Fz<T>(B, W_PS1), Fz<T>(B, W_PS2)};
-  T* __restrict__ b = Fz<T>(B, K_B);
+  // rstart: b to the refinement's copy and the first inner right-hand side, and the
+  // refined solve started (as in kr_rhs)
+  const bool start = rstart != nullptr;
+  T* __restrict__ b = Fz<T>(B, start ? K_AUX : K_B);
+  T* __restrict__ r0 = Fz<T>(B, K_R);
+  const T* __restrict__ dinv = Fz<T>(B, W_DINV);
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
+  DotAcc<T> abb, abz;
   for (int k = t.k0; k < t.kend; ++k) {
     rp.advance(G, k);
 #pragma unroll
@@ -208,7 +215,22 @@ __global__ void __launch_bounds__(NTHR) kz_rhs(const BoxDev* boxes, const int2* 
       ps[d][c] = fp;
       dsum += fp - fm;
     }
-    b[c] = -((rp.c() - __ldg(&rho[c])) * idt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
+    const T bc = -((rp.c() - __ldg(&rho[c])) * idt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
+    b[c] = bc;
+    if (start) {
+      r0[c] = bc;
+      abb.add(bc, bc);
+      abz.add(bc, bc * __ldg(&dinv[c]));
+    }
+  }
+  if (!start) return;
+  Red<T> v[2] = {abb.red(), abz.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      mix_finish_scalars(B, res[0], 1, rstart);
+      cg_start_scalars(B, res[1], res[0], active);
+    }
   }
 }
 
@@ -534,7 +556,7 @@ template <typename T> void zlaunch_asm(const Launch& L, int s, int up0, int php0
 }
 template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (rlaunch_rhs<T>(L, s, rhop, pp)) return;
-  FE_LAUNCH(L, KID_RHS, (kz_rhs<T><<<ZGRID>>>(L.boxes, L.work, s, rhop, pp)));
+  FE_LAUNCH(L, KID_RHS, (kz_rhs<T><<<ZGRID>>>(L.boxes, L.work, s, rhop, pp, L.part, L.rstart, L.active)));
 }
 template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, int kidx,
                                         int mixed) {
