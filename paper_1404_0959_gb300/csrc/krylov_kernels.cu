@@ -12,6 +12,7 @@
 // every later launch, so one launch serves all boxes of an ensemble.
 #include "zbulk.cuh"
 #include "zmarch.cuh"
+#include "zring.cuh"
 
 namespace fe {
 
@@ -1102,14 +1103,8 @@ __global__ void __launch_bounds__(NTHR) k_refine_start(const BoxDev* boxes, cons
 // refinement bookkeeping, and the start of the next inner solve from r.  The
 // pairs ping-pong between K_X64 and K_X64B with the parity of the outer step
 // (neighbouring tiles read the old pairs as halo).  Symmetric operator.
-//
-// The residual is written as r = b - (psi/dt) x - kl (6 x - sum of the six
-// neighbours), kl = dt/(2 h^2): the neighbour sum of the high parts is exact
-// (TwoSum), 6 x and the two products are split exactly by FMA (TwoProduct),
-// and the three large terms b, (psi/dt) x, kl (6x - sum) meet in two TwoSums,
-// so the cancellation between them loses nothing; every low-order part is
-// carried in plain FP32 (its rounding is about 2^-48 of the terms).  Loads
-// run KPF planes ahead, halo cells included.
+// Loads run KPF planes ahead, halo cells included.  kp_refine is the same
+// pass on column pairs (two x-neighbouring cells per thread, vector loads).
 template <typename T>
 struct PairRaw {
   float2 a;  // old pair
@@ -1138,6 +1133,33 @@ struct PairSrc {
     return make_float2(t.hi, t.lo);
   }
 };
+
+// One cell of r = b - M x for x as double-float pairs (symmetric operator):
+// r = b - (psi/dt) x - kl (6 x - sum of the six neighbours n0..n5),
+// kl = dt/(2 h^2).  The neighbour sum of the high parts is exact (TwoSum),
+// 6 x and the two products are split exactly by FMA (TwoProduct), and the
+// three large terms meet in two TwoSums, so the cancellation between them
+// loses nothing; every low-order part is carried in plain FP32 (its rounding
+// is about 2^-48 of the terms).
+__device__ __forceinline__ float refine_residual(float2 zc, float2 n0, float2 n1, float2 n2, float2 n3, float2 n4,
+                                                 float2 n5, float bc, float pc, DF idt, DF kl) {
+  const DF s01 = df_two_sum(n0.x, n1.x), s23 = df_two_sum(n2.x, n3.x), s45 = df_two_sum(n4.x, n5.x);
+  const DF u = df_two_sum(s01.hi, s23.hi), v = df_two_sum(u.hi, s45.hi);
+  const float nlo = __fadd_rn(__fadd_rn(__fadd_rn(s01.lo, s23.lo), __fadd_rn(s45.lo, u.lo)),
+                              __fadd_rn(v.lo, __fadd_rn(__fadd_rn(__fadd_rn(n0.y, n1.y), __fadd_rn(n2.y, n3.y)),
+                                                        __fadd_rn(n4.y, n5.y))));
+  const float p6 = __fmul_rn(6.f, zc.x), e6 = __fmaf_rn(6.f, zc.x, -p6);
+  const DF sh = df_two_sum(p6, -v.hi);
+  const float slo = __fadd_rn(__fadd_rn(sh.lo, e6), __fsub_rn(__fmul_rn(6.f, zc.y), nlo));
+  const float kp = __fmul_rn(kl.hi, sh.hi);
+  const float ke = __fmaf_rn(kl.lo, sh.hi, __fmaf_rn(kl.hi, slo, __fmaf_rn(kl.hi, sh.hi, -kp)));
+  const float wp = __fmul_rn(idt.hi, pc);
+  const float we = __fmaf_rn(idt.lo, pc, __fmaf_rn(idt.hi, pc, -wp));
+  const float ap = __fmul_rn(wp, zc.x);
+  const float ae = __fmaf_rn(we, zc.x, __fmaf_rn(wp, zc.y, __fmaf_rn(wp, zc.x, -ap)));
+  const DF t1 = df_two_sum(bc, -ap), t2 = df_two_sum(t1.hi, -kp);
+  return __fadd_rn(t2.hi, __fsub_rn(__fadd_rn(t2.lo, t1.lo), __fadd_rn(ae, ke)));
+}
 
 template <typename T>
 __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int2* work, double* part,
@@ -1195,30 +1217,150 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
     const int c = G.col + G.plane(k);
     xn[c] = zc;
     const float2* s = sm + G.csm;
-    const float2 n0 = s[1], n1 = s[-1], n2 = s[ZGeom<1>::W], n3 = s[-ZGeom<1>::W], n4 = zp, n5 = zm;
-    // sum of the neighbours: high parts exactly (pairwise TwoSums), low parts plainly
-    const DF s01 = df_two_sum(n0.x, n1.x), s23 = df_two_sum(n2.x, n3.x), s45 = df_two_sum(n4.x, n5.x);
-    const DF u = df_two_sum(s01.hi, s23.hi), v = df_two_sum(u.hi, s45.hi);
-    const float nlo = __fadd_rn(__fadd_rn(__fadd_rn(s01.lo, s23.lo), __fadd_rn(s45.lo, u.lo)),
-                                __fadd_rn(v.lo, __fadd_rn(__fadd_rn(__fadd_rn(n0.y, n1.y), __fadd_rn(n2.y, n3.y)),
-                                                          __fadd_rn(n4.y, n5.y))));
-    // S = 6 x - sum (6 x_hi split exactly)
-    const float p6 = __fmul_rn(6.f, zc.x), e6 = __fmaf_rn(6.f, zc.x, -p6);
-    const DF sh = df_two_sum(p6, -v.hi);
-    const float slo = __fadd_rn(__fadd_rn(sh.lo, e6), __fsub_rn(__fmul_rn(6.f, zc.y), nlo));
-    // K = kl S and A = (psi/dt) x as unnormalised pairs (product + exact error + low terms)
-    const float kp = __fmul_rn(kl.hi, sh.hi);
-    const float ke = __fmaf_rn(kl.lo, sh.hi, __fmaf_rn(kl.hi, slo, __fmaf_rn(kl.hi, sh.hi, -kp)));
-    const float wp = __fmul_rn(idt.hi, (float)pc);
-    const float we = __fmaf_rn(idt.lo, (float)pc, __fmaf_rn(idt.hi, (float)pc, -wp));
-    const float ap = __fmul_rn(wp, zc.x);
-    const float ae = __fmaf_rn(we, zc.x, __fmaf_rn(wp, zc.y, __fmaf_rn(wp, zc.x, -ap)));
-    // r = b - A - K: the large parts in two TwoSums, the rest in FP32
-    const DF t1 = df_two_sum((float)bc, -ap), t2 = df_two_sum(t1.hi, -kp);
-    const float rv = __fadd_rn(t2.hi, __fsub_rn(__fadd_rn(t2.lo, t1.lo), __fadd_rn(ae, ke)));
+    const float rv = refine_residual(zc, s[1], s[-1], s[ZGeom<1>::W], s[-ZGeom<1>::W], zp, zm, (float)bc, (float)pc,
+                                     idt, kl);
     r[c] = (T)rv;
     arr.add(rv, rv);
     arz.add(rv, (float)((T)rv * dc));
+  }
+  DF v[2] = {arr.red(), arz.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      mix_finish_scalars(B, res[0], 0, outer_active);
+      cg_start_scalars(B, res[1], res[0], active);
+    }
+  }
+}
+
+// kz_refine on column pairs: 16 x 8 threads per 32 x 8 tile, each thread the
+// cells (x, x+1) of its column pair (N even), pair loads and stores; the
+// inner x-neighbours come from registers, the outer ones and the y-neighbours
+// from the staged plane of updated pairs.
+template <typename T>
+__global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2* work, double* part,
+                                                 int* outer_active, int* active) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (B.sc[SC_ODONE] != 0.0) return;
+  constexpr int SW = TX + 2, SH = TY + 2;  // staged plane: tile + one-cell halo
+  __shared__ __align__(16) float2 sm[SH * SW];
+  const int N = B.N, NN = N * N;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + RTX * ty;
+  auto wrap = [&](int v) { return ((v % N) + N) % N; };  // tiles wider than a small box wrap more than once
+  const bool act = (t.x0 + 2 * tx < N) && (t.y0 + ty < N);
+  const int col = wrap(t.x0 + 2 * tx) + N * wrap(t.y0 + ty);
+  const int csm = (ty + 1) * SW + 2 * tx + 1;
+  int hcol = -1, hsm = 0;  // the halo cell this thread stages (80 of them: x-halo 2 x 8, y-halo 2 x 32)
+  if (tid < 2 * TY + 2 * TX) {
+    int lx, ly;
+    if (tid < 2 * TY) {
+      ly = tid >> 1;
+      lx = (tid & 1) ? TX : -1;
+    } else {
+      const int h = tid - 2 * TY;
+      ly = h < TX ? -1 : TY;
+      lx = h % TX;
+    }
+    hcol = wrap(t.x0 + lx) + N * wrap(t.y0 + ly);
+    hsm = (ly + 1) * SW + lx + 1;
+  }
+  auto plane = [&](int k) { return NN * (k < 0 ? k + N : (k >= N ? k - N : k)); };
+  const int par = ((int)B.sc[SC_OUTER]) & 1, it = (int)B.sc[SC_ITERS];
+  PairSrc<T> src;
+  src.fresh = B.sc[SC_OUTER] == 0.0;
+  src.xo = F<float2>(B, par ? K_X64B : K_X64);
+  src.x = F<T>(B, K_X);
+  src.pd = F<T>(B, (it & 1) ? K_PP : K_PD);
+  src.alpha = (T)B.sc[SC_ALPHA];
+  src.moved = it > 0;
+  float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
+  T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ borig = F<T>(B, K_AUX);
+  const T* __restrict__ psi = F<T>(B, W_PSI);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  const double dt = B.sc[SC_KDT];
+  const DF idt = df_from_double(1.0 / dt), kl = df_from_double(0.5 * dt * B.ih * B.ih);
+  // raw values of the own pair at one plane
+  struct Raw2 {
+    float4 a;  // old pairs of both cells
+    P2<T> x, p;
+  };
+  auto load2 = [&](int q) {
+    Raw2 v;
+    v.a = src.fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(reinterpret_cast<const float4*>(src.xo + q));
+    if (src.moved) {
+      v.x = ldp(src.x + q);
+      v.p = ldp(src.pd + q);
+    } else {
+      v.x.x = v.x.y = v.p.x = v.p.y = T(0);
+    }
+    return v;
+  };
+  auto make2 = [&](const Raw2& v, float2& c0, float2& c1) {
+    c0 = src.make(PairRaw<T>{make_float2(v.a.x, v.a.y), v.x.x, v.p.x});
+    c1 = src.make(PairRaw<T>{make_float2(v.a.z, v.a.w), v.x.y, v.p.y});
+  };
+  float2 zm[2], zc[2], zp[2];
+  make2(load2(col + plane(t.k0 - 1)), zc[0], zc[1]);
+  make2(load2(col + plane(t.k0)), zp[0], zp[1]);
+  Raw2 nq[KPF];            // own pair, planes k+2 ..
+  PairRaw<T> nh[KPF];      // halo cell, planes k ..
+  P2<T> nb_[KPF], np_[KPF], nd_[KPF];  // b, psi, D^{-1} of the own pair, planes k ..
+#pragma unroll
+  for (int j = 0; j < KPF; ++j) {
+    nq[j] = load2(col + plane(t.k0 + 1 + j));
+    if (hcol >= 0) nh[j] = src.load(hcol + plane(t.k0 + j));
+    const int q = col + plane(t.k0 + j);
+    nb_[j] = ldp(borig + q);
+    np_[j] = ldp(psi + q);
+    nd_[j] = ldp(dinv + q);
+  }
+  DotAcc<float> arr, arz;
+  for (int k = t.k0; k < t.kend; ++k) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      zm[e] = zc[e];
+      zc[e] = zp[e];
+    }
+    make2(nq[0], zp[0], zp[1]);
+    const P2<T> bc = nb_[0], pcv = np_[0], dc = nd_[0];
+#pragma unroll
+    for (int j = 0; j + 1 < KPF; ++j) {
+      nq[j] = nq[j + 1];
+      nb_[j] = nb_[j + 1];
+      np_[j] = np_[j + 1];
+      nd_[j] = nd_[j + 1];
+    }
+    nq[KPF - 1] = load2(col + plane(k + 1 + KPF));
+    {
+      const int q = col + plane(k + KPF);
+      nb_[KPF - 1] = ldp(borig + q);
+      np_[KPF - 1] = ldp(psi + q);
+      nd_[KPF - 1] = ldp(dinv + q);
+    }
+    __syncthreads();
+    sm[csm] = zc[0];
+    sm[csm + 1] = zc[1];
+    if (hcol >= 0) {
+      sm[hsm] = src.make(nh[0]);
+#pragma unroll
+      for (int j = 0; j + 1 < KPF; ++j) nh[j] = nh[j + 1];
+      nh[KPF - 1] = src.load(hcol + plane(k + KPF));
+    }
+    __syncthreads();
+    if (!act) continue;
+    const int c = col + NN * k;
+    *reinterpret_cast<float4*>(xn + c) = make_float4(zc[0].x, zc[0].y, zc[1].x, zc[1].y);
+    const float r0 = refine_residual(zc[0], zc[1], sm[csm - 1], sm[csm + SW], sm[csm - SW], zp[0], zm[0],
+                                     (float)bc.x, (float)pcv.x, idt, kl);
+    const float r1 = refine_residual(zc[1], sm[csm + 2], zc[0], sm[csm + 1 + SW], sm[csm + 1 - SW], zp[1], zm[1],
+                                     (float)bc.y, (float)pcv.y, idt, kl);
+    stp(r + c, (T)r0, (T)r1);
+    arr.add(r0, r0);
+    arr.add(r1, r1);
+    arz.add(r0, (float)((T)r0 * dc.x));
+    arz.add(r1, (float)((T)r1 * dc.y));
   }
   DF v[2] = {arr.red(), arz.red()};
   __shared__ double res[2];
@@ -1450,7 +1592,11 @@ template <typename T> void launch_refine_start(const Launch& L, int* outer_activ
   FE_LAUNCH(L, KID_MIX_RES, (k_refine_start<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active, L.active)));
 }
 template <typename T> void launch_refine(const Launch& L, int* outer_active) {
-  FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+  if (L.ring_ok)  // every box's N a multiple of the 16-byte chunk, so even: column pairs
+    FE_LAUNCH(L, KID_REFINE,
+              (kp_refine<T><<<L.nblocks, dim3(RTX, TY), 0, L.st>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+  else
+    FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
 }
 template <typename T> void launch_mix_finish_pp(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework, 1)));
