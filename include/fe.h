@@ -157,6 +157,14 @@ int fe_init_state(fe_ctx* ctx, int box, int mode);
 int fe_set_field(fe_ctx* ctx, int box, int field, const void* src, int src_is_device);
 int fe_get_field(fe_ctx* ctx, int box, int field, void* dst, int dst_is_device);
 
+/* The same for n fields at once: fields[q] is copied from src[q] (to
+ * dst[q]); all n copies are queued before the one synchronisation at the end
+ * (with pinned host memory they run back to back at the host link's rate).
+ * Every id and pointer is checked first; on FE_ERR_INVALID_ARG nothing is
+ * copied.  The arrays are the caller's and are not kept. */
+int fe_set_fields(fe_ctx* ctx, int box, int n, const int* fields, const void* const* src, int src_is_device);
+int fe_get_fields(fe_ctx* ctx, int box, int n, const int* fields, void* const* dst, int dst_is_device);
+
 /* Time and previous step of a box (checkpoint restore; dt_prev <= 0 means none). */
 int fe_set_clock(fe_ctx* ctx, int box, double t, double dt_prev);
 

@@ -940,6 +940,33 @@ extern "C" int fe_get_field(fe_ctx* c, int box, int field, void* dst, int is_dev
   return FE_OK;
 }
 
+// Several fields in one call: every copy queued on the context stream, one
+// synchronisation at the end (all arguments are checked before any copy).
+static int copy_fields(fe_ctx* c, int box, int n, const int* fields, void* const* ptrs, int is_dev, bool in) {
+  if (!c || box < 0 || box >= c->nb || n < 0 || (n > 0 && (!fields || !ptrs))) return FE_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q)
+    if (!ptrs[q] || field_slot(c, fields[q], c->cur) < 0) return FE_ERR_INVALID_ARG;
+  const int N = c->N[box];
+  const size_t bytes = (size_t)N * N * N * (c->fp64 ? 8 : 4);
+  for (int q = 0; q < n; ++q) {
+    void* dev = c->hbox[box].f[field_slot(c, fields[q], c->cur)];
+    if (in)
+      CK(cudaMemcpyAsync(dev, ptrs[q], bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    else
+      CK(cudaMemcpyAsync(ptrs[q], dev, bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return FE_OK;
+}
+
+extern "C" int fe_set_fields(fe_ctx* c, int box, int n, const int* fields, const void* const* src, int is_dev) {
+  return copy_fields(c, box, n, fields, const_cast<void* const*>(src), is_dev, true);
+}
+
+extern "C" int fe_get_fields(fe_ctx* c, int box, int n, const int* fields, void* const* dst, int is_dev) {
+  return copy_fields(c, box, n, fields, dst, is_dev, false);
+}
+
 extern "C" int fe_set_clock(fe_ctx* c, int box, double t, double dt_prev) {
   if (!c || box < 0 || box >= c->nb) return FE_ERR_INVALID_ARG;
   int rc = push_scalar(c, box, SC_TIME, t);

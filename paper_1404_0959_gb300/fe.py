@@ -68,7 +68,8 @@ class fe_profile_info(ctypes.Structure):
                 ("counts", ctypes.c_int64 * FE_PROFILE_MAX_KERNELS)]
 
 
-EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_clock", "fe_step",
+EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_fields", "fe_get_fields",
+           "fe_set_clock", "fe_step",
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
@@ -84,6 +85,8 @@ def load_library(path=LIB_PATH):
     lib.fe_init_state.argtypes = [c_void_p, c_int, c_int]
     lib.fe_set_field.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int]
     lib.fe_get_field.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int]
+    lib.fe_set_fields.argtypes = [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_void_p), c_int]
+    lib.fe_get_fields.argtypes = [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_void_p), c_int]
     lib.fe_set_clock.argtypes = [c_void_p, c_int, c_double, c_double]
     lib.fe_step.argtypes = [c_void_p, c_int, POINTER(fe_step_info)]
     lib.fe_solve_pressure.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_double, c_double, c_int,
@@ -159,6 +162,23 @@ def fe_set_field(ctx, box, field, ptr, is_device):
 
 def fe_get_field(ctx, box, field, ptr, is_device):
     return _check(lib().fe_get_field(ctx, box, field, c_void_p(ptr), int(is_device)), "fe_get_field")
+
+
+def _field_arrays(fields, ptrs):
+    n = len(fields)
+    if len(ptrs) != n:
+        raise ValueError("one pointer per field")
+    return n, (c_int * n)(*fields), (c_void_p * n)(*[c_void_p(p) for p in ptrs])
+
+
+def fe_set_fields(ctx, box, fields, ptrs, is_device):
+    n, f, p = _field_arrays(fields, ptrs)
+    return _check(lib().fe_set_fields(ctx, box, n, f, p, int(is_device)), "fe_set_fields")
+
+
+def fe_get_fields(ctx, box, fields, ptrs, is_device):
+    n, f, p = _field_arrays(fields, ptrs)
+    return _check(lib().fe_get_fields(ctx, box, n, f, p, int(is_device)), "fe_get_fields")
 
 
 def fe_set_clock(ctx, box, t, dt_prev):

@@ -135,3 +135,29 @@ def test_conservation_on_gpu(fe):
     assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
     assert abs(d1["dust_mass"][0] - d0["dust_mass"][0]) <= 1e-13 * d0["dust_mass"][0]
     s.close()
+
+
+def test_batched_field_copies(fe):
+    # fe_set_fields / fe_get_fields move the same bytes as one call per field,
+    # from host and from device memory; a bad id copies nothing
+    import torch
+    N = 24
+    rho, u, Y, _ = random_fields(N, 1, False, seed=21, noise=0.02)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])])
+    s.set_state(0, rho, u, Y)
+    ids = [fe.FE_RHO, fe.FE_UX, fe.FE_UY, fe.FE_UZ, fe.FE_P, fe.FE_PHIX, fe.FE_PHIY, fe.FE_PHIZ, fe.FE_Y0]
+    single = {f: s.get_field(0, f) for f in ids}
+    host = [np.empty((N, N, N)) for _ in ids]
+    fe.fe_get_fields(s.ctx, 0, ids, [h.ctypes.data for h in host], 0)
+    for f, h in zip(ids, host):
+        assert np.array_equal(h, single[f])
+    # write scaled copies back from device memory, read them again
+    dev = [torch.tensor(2.0 * h, device="cuda") for h in host]
+    fe.fe_set_fields(s.ctx, 0, ids, [d.data_ptr() for d in dev], 1)
+    for f, h in zip(ids, host):
+        assert np.array_equal(s.get_field(0, f), 2.0 * h)
+    before = s.get_field(0, fe.FE_RHO)
+    with pytest.raises(fe.FeError):
+        fe.fe_set_fields(s.ctx, 0, [fe.FE_RHO, 999], [dev[0].data_ptr(), dev[1].data_ptr()], 1)
+    assert np.array_equal(s.get_field(0, fe.FE_RHO), before)
+    s.close()
