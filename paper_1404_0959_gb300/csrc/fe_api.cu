@@ -184,6 +184,10 @@ static int validate(const fe_params* p) {
   return FE_OK;
 }
 
+// Element-wise kernels: chunks per SM over all boxes (each block one chunk).
+#ifndef FE_ECHUNKS
+#define FE_ECHUNKS 8  // one wave of eight 256-thread blocks per SM (measured: the residual update 57 -> 54 us at 256^3)
+#endif
 static int tz_for(int N) { return N >= 128 ? 8 : 4; }
 
 // (Re)build both work lists for tile depth tz (0: default per N) and upload the
@@ -195,7 +199,7 @@ static int set_tiling(fe_ctx* c, int tz) {
   long total = 0;
   for (int b = 0; b < c->nb; ++b) total += (long)c->hbox[b].N * c->hbox[b].N * c->hbox[b].N;
   const long quantum = 4L * NTHR;
-  long chunk = (total + 2L * 8 * c->nsm - 1) / (2L * 8 * c->nsm);
+  long chunk = (total + (long)FE_ECHUNKS * c->nsm - 1) / ((long)FE_ECHUNKS * c->nsm);
   chunk = std::max(quantum, (chunk + quantum - 1) / quantum * quantum);
   for (int b = 0; b < c->nb; ++b) {
     BoxDev& B = c->hbox[b];
