@@ -68,7 +68,6 @@ enum Scalar {
   SC_ODONE, SC_OBB, SC_ORR, SC_ORES, SC_ITSUM, SC_OTOL, SC_OUTER,  // mixed-precision refinement
   SC_FB, SC_NFB,                                                    // flexible CG: Jacobi fallback flag, count
   SC_KERR,  // a kernel gave up a bounded wait (bulk-copy completion)
-  SC_ITBASE, SC_XRESET,  // refined plain CG: iteration count at the last boundary; x restarts from 0
   SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
   NSC = SC_DUST0 + MAXD + 4
 };
@@ -310,7 +309,7 @@ __device__ inline void mix_finish_scalars(const BoxDev& B, double rr, int first,
     sc[SC_CONV] = zero ? 1.0 : 0.0;
     if (!zero) atomicAdd(outer_active, 1);
   } else if (sc[SC_ODONE] == 0.0) {
-    sc[SC_ITSUM] += sc[SC_ITERS] - sc[SC_ITBASE];
+    sc[SC_ITSUM] += sc[SC_ITERS];
     sc[SC_OUTER] += 1.0;
     if (sqrt(rr) <= sc[SC_OTOL] * sqrt(sc[SC_OBB])) {
       sc[SC_ODONE] = 1.0;
@@ -334,8 +333,6 @@ __device__ inline void mix_finish_scalars(const BoxDev& B, double rr, int first,
 __device__ inline void cg_start_scalars(const BoxDev& B, double rz, double rr, int* active) {
   double* sc = B.sc;
   sc[SC_ITERS] = 0.0;
-  sc[SC_ITBASE] = 0.0;
-  sc[SC_XRESET] = 0.0;
   sc[SC_ALPHA] = 0.0;
   sc[SC_BETA] = 0.0;
   sc[SC_RZ] = rz;
@@ -344,35 +341,6 @@ __device__ inline void cg_start_scalars(const BoxDev& B, double rz, double rr, i
   sc[SC_DONE] = run ? 0.0 : 1.0;
   if (run) atomicAdd(active, 1);
   else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;  // a finished refinement keeps its verdict
-}
-
-// The next inner solve of a refined plain CG continued from the last one
-// (reliable update, van der Vorst and Ye, SIAM J. Sci. Comput. 22, 2000): the
-// recursively updated residual is replaced by the true one r (its <r, D^{-1} r>
-// = rz, ||r||^2 = rr), the direction recurrence goes on with
-// beta = rz / <r_old, D^{-1} r_old>, and the FP32 iterate restarts from zero
-// (the boundary pass added it to the pairs).  Before any iteration it is the
-// plain start.
-#ifndef FE_RELIABLE
-#define FE_RELIABLE 1
-#endif
-__device__ inline void cg_continue_scalars(const BoxDev& B, double rz, double rr, int* active) {
-  double* sc = B.sc;
-  const double it = sc[SC_ITERS], rz_old = sc[SC_RZ];
-  if (!FE_RELIABLE || it == 0.0 || !(rz_old > 0.0)) {
-    cg_start_scalars(B, rz, rr, active);
-    return;
-  }
-  sc[SC_ITBASE] = it;
-  sc[SC_XRESET] = 1.0;
-  sc[SC_ALPHA] = 0.0;
-  sc[SC_BETA] = rz / rz_old;
-  sc[SC_RZ] = rz;
-  sc[SC_BB] = rr;
-  const bool run = sc[SC_ODONE] == 0.0 && rr > 0.0;
-  sc[SC_DONE] = run ? 0.0 : 1.0;
-  if (run) atomicAdd(active, 1);
-  else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;
 }
 
 // ---- block prologue -----------------------------------------------------------

@@ -162,8 +162,6 @@ __global__ void __launch_bounds__(NTHR) k_cg_init(const BoxDev* boxes, const int
       B.sc[SC_RZ] = res[0];
       B.sc[SC_BB] = res[1];
       B.sc[SC_ITERS] = 0.0;
-      B.sc[SC_ITBASE] = 0.0;
-      B.sc[SC_XRESET] = 0.0;
       B.sc[SC_ALPHA] = 0.0;
       B.sc[SC_BETA] = 0.0;
       bool zero = !(res[1] > 0.0);
@@ -314,7 +312,6 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
   const T lapc = T(0.5) * dt * ih * ih;
   // first iteration of a solve: pd_new = D^{-1} r and x = 0 whatever pd_old and x hold
   const bool first = B.sc[SC_ITERS] == 0.0;
-  const bool xzero = first || B.sc[SC_XRESET] != 0.0;  // x restarts: the previous direction is in the pairs
   auto dir = [&](T rv, T dv, T pv) { return first ? rv * dv : rv * dv + beta * pv; };
   auto ld = [&](const T* f, int col, int k) { return __ldg(&f[col + G.plane(G.wrapz(k))]); };
   // centre column: r, dinv, pd_old for planes k + 1 .. k + KPF in flight
@@ -377,7 +374,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
       const T y = ps * zc * idt - lapc * (nb - T(6) * zc);
       q[c] = y;
       pn[c] = zc;
-      x[c] = xzero ? T(0) : xv + alpha * oc;
+      x[c] = first ? T(0) : xv + alpha * oc;
       a0.add(zc, y);
     }
     zm = zc;
@@ -390,7 +387,6 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_PQ] = res[0];
       B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
-      B.sc[SC_XRESET] = 0.0;
     }
   }
 }
@@ -447,7 +443,6 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
   const T lapc = T(0.5) * dt * ih * ih;
   const bool first = B.sc[SC_ITERS] == 0.0;  // pd_new = D^{-1} r, x = 0 whatever pd_old and x hold
-  const bool xzero = first || B.sc[SC_XRESET] != 0.0;  // x restarts: the previous direction is in the pairs
   const int nseq = Gm.count();
   const size_t NN = (size_t)N * N;
 
@@ -551,7 +546,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
           const T nb = (vxm + vxp) + (cs.v[e] + cn.v[e]) + (cb.v[e] + ca.v[e]);
           const T y = sv_psi[u].v[e] * vc * idt - lapc * (nb - T(6) * vc);
           yv.v[e] = y;
-          xn.v[e] = xzero ? T(0) : sv_x[u].v[e] + alpha * sv_po[u].v[e];
+          xn.v[e] = first ? T(0) : sv_x[u].v[e] + alpha * sv_po[u].v[e];
           a0.add(vc, y);
         }
         st4(q + gbase, yv);
@@ -580,7 +575,6 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
     if (tid == 0) {
       B.sc[SC_PQ] = res[0];
       B.sc[SC_ALPHA] = B.sc[SC_RZ] / res[0];
-      B.sc[SC_XRESET] = 0.0;
     }
   }
 }
@@ -617,7 +611,7 @@ __device__ void cg_update_scalars(const BoxDev& B, double rz, double rr, int* ac
     B.sc[SC_DONE] = 1.0;
     B.sc[SC_CONV] = 1.0;
     atomicSub(active, 1);
-  } else if (it - B.sc[SC_ITBASE] >= B.sc[SC_MAXIT]) {
+  } else if (it >= B.sc[SC_MAXIT]) {
     B.sc[SC_DONE] = 1.0;
     B.sc[SC_CONV] = 0.0;
     atomicSub(active, 1);
@@ -1182,7 +1176,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
   src.x = F<T>(B, K_X);
   src.pd = F<T>(B, (it & 1) ? K_PP : K_PD);
   src.alpha = (T)B.sc[SC_ALPHA];
-  src.moved = it > (int)B.sc[SC_ITBASE];  // the inner solve iterated since the last boundary
+  src.moved = it > 0;
   float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
   T* __restrict__ r = F<T>(B, K_R);
   const double dt = B.sc[SC_KDT];
@@ -1234,7 +1228,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
   if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       mix_finish_scalars(B, res[0], 0, outer_active);
-      cg_continue_scalars(B, res[1], res[0], active);
+      cg_start_scalars(B, res[1], res[0], active);
     }
   }
 }
@@ -1279,7 +1273,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
   src.x = F<T>(B, K_X);
   src.pd = F<T>(B, (it & 1) ? K_PP : K_PD);
   src.alpha = (T)B.sc[SC_ALPHA];
-  src.moved = it > (int)B.sc[SC_ITBASE];  // the inner solve iterated since the last boundary
+  src.moved = it > 0;
   float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
   T* __restrict__ r = F<T>(B, K_R);
   const T* __restrict__ borig = F<T>(B, K_AUX);
@@ -1373,7 +1367,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
   if (block_sum_last<2>(v, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       mix_finish_scalars(B, res[0], 0, outer_active);
-      cg_continue_scalars(B, res[1], res[0], active);
+      cg_start_scalars(B, res[1], res[0], active);
     }
   }
 }
