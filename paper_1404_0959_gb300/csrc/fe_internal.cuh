@@ -188,6 +188,11 @@ __device__ __forceinline__ DF df_from_double(double d) {
   return DF{hi, (float)(d - (double)hi)};
 }
 
+// Correctly rounded reciprocal: the value of 1 / v in IEEE division, without
+// the general division sequence.
+__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
+
 // ---- Jacobi preconditioner ---------------------------------------------------------
 // 1 / diag(M) = 1 / (psi/dt + 3 dt/h^2) in the field precision, with one fused
 // multiply-add: every kernel that stores it and every kernel that forms it on
@@ -201,9 +206,6 @@ struct JacobiDiag {
     c3 = T(3) * d * h * h;
   }
   __device__ __forceinline__ T inv(T psi) const { return rcp_rn(fma(psi, idt, c3)); }
-  // correctly rounded reciprocal (the same value as 1 / v in IEEE division)
-  __device__ __forceinline__ static float rcp_rn(float v) { return __frcp_rn(v); }
-  __device__ __forceinline__ static double rcp_rn(double v) { return __drcp_rn(v); }
 };
 
 // ---- inner-product accumulation ----------------------------------------------------

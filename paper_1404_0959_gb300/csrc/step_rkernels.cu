@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
       const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
       const T rc = pc<T>(crho, r);
       const T r0 = rc - dt * dph;
-      const T ir0 = T(1) / r0, ir = T(1) / rc;
+      const T ir0 = rcp_rn(r0), ir = rcp_rn(rc);
       T L[3], visc[3];
       zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
 #pragma unroll
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes,
       T L[3], visc[3];
       zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
       const T rc = pc<T>(crho, r);
-      const T irp = T(1) / pc<T>(crp, r);
+      const T irp = rcp_rn(pc<T>(crp, r));
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const T Rm = T(0.5) * (pc<T>(R.cen(5 + m, k, tid), r) + L[m]);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxe
     for (int r = 0; r < 2; ++r) {
       const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
       const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
-      const T ir = T(1) / pc<T>(crho, r);
+      const T ir = rcp_rn(pc<T>(crho, r));
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
       T php[3], phm[3];
       R.faces(0, k, G, r, php, phm);
       const T rk = rho.c();
-      const T irk = T(1) / rk;
+      const T irk = rcp_rn(rk);
       const T rn = pc<T>(crn, r);
       T ra_p[3], ra_m[3];
 #pragma unroll

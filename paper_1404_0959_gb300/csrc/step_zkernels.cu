@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
     const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
     const T r = __ldg(&rho[c]);
     const T r0 = r - dt * dph;
-    const T ir0 = T(1) / r0, ir = T(1) / r;
+    const T ir0 = rcp_rn(r0), ir = rcp_rn(r);
     T L[3], visc[3];
     zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
 #pragma unroll
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(NTHR) kz_asm(const BoxDev* boxes, const int2* 
     T L[3], visc[3];
     zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
     const T r = __ldg(&rho[c]);
-    const T irp = T(1) / __ldg(&rp[c]);
+    const T irp = rcp_rn(__ldg(&rp[c]));
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T R = T(0.5) * (__ldg(&Rn[m][c]) + L[m]);
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(NTHR) kz_accel(const BoxDev* boxes, const int2
     __syncthreads();
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
-    const T ir = T(1) / __ldg(&rho[c]);
+    const T ir = rcp_rn(__ldg(&rho[c]));
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(NTHR, 2) kz_dust(const BoxDev* boxes, const in
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     const T rk = rho.c();
-    const T irk = T(1) / rk;
+    const T irk = rcp_rn(rk);
     const T rn = __ldg(&rhon[c]);
     T ra_p[3], ra_m[3];
 #pragma unroll
