@@ -32,12 +32,14 @@ METRIC = "cell-steps/s at 256^3 (learned vs plain solve, same residual); % of HB
 UNIT = "cell-steps/s"
 
 # Algorithmic words per cell (one N^3 array element read or written once) per
-# launch of each kernel, barotropic closure, nd dust classes.
-def alg_words(kernel, nd):
+# launch of each kernel, barotropic closure, nd dust classes.  Mixed precision:
+# the right-hand side also writes the first inner right-hand side and reads
+# D^{-1} (it starts the refined solve); the corrector reads neither psi nor b.
+def alg_words(kernel, nd, mixed=False):
     table = {
-        "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 11,
+        "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 13 if mixed else 11,
         "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4,
-        "cg_dirmatvec": 8, "cg_rupdate": 4, "cg_xfinal": 3, "corr": 21, "accel": 9,
+        "cg_dirmatvec": 8, "cg_rupdate": 4, "cg_xfinal": 3, "corr": 19 if mixed else 21, "accel": 9,
         "dust": 8 + 4 * nd + 2,  # last corrector adds u reads and p write; averaged over 2 correctors
         "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
         # refinement (field word = 4 bytes; x64 counts as two words)
@@ -388,7 +390,10 @@ def main():
     w = 8 if precision == fe.FE_FP64 else 4
     hbm, peak_kind = peaks()
     per_launch_ms = prof["target_ms"] / max(prof["target_launches"], 1)
-    alg_bytes = alg_words(kernel, nd) * w * cells
+    mixed = precision == fe.FE_FP32_MIXED
+    alg_bytes = alg_words(kernel, nd, mixed) * w * cells
+    # whole step: algorithmic bytes of every launch of the breakdown step over the headline step time
+    step_bytes = sum(n * alg_words(k, nd, mixed) * w * cells for k, (_, n) in share.items()) if share else None
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     iters = info[0]["iters"]
 
@@ -452,6 +457,9 @@ def main():
                            "l2": "state of %.1f GB >> 126 MB L2, no flush needed" % (
                                (40 + 4 * nd) * cells * w / 1e9),
                            "parallelism": "replicas" if world > 1 else "single box"},
+                "step_roofline": None if step_bytes is None else {
+                    "alg_bytes_per_step": step_bytes, "achieved": step_bytes / t * args.steps / 1e9, "peak": hbm,
+                    "unit": "GB/s", "frac": step_bytes / t * args.steps / 1e9 / hbm},
                 "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "peak_kind": peak_kind,
                              "traffic": recorded_traffic(kernel, WORKLOAD) if N == 256 else None,
