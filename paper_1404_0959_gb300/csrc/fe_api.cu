@@ -161,7 +161,10 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   // second CG direction buffer (the learned solver's harvest runs plain CG)
   if (c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_PP, e});
   if (!c->fp64) plan.push_back({K_X64, 8});
-  if (!c->fp64 && c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_X64B, 8});
+  if (!c->fp64 && c->prm.solver != FE_BICGSTAB_JACOBI) {
+    plan.push_back({K_X64B, 8});
+    plan.push_back({K_XH, e});
+  }
 }
 
 static int validate(const fe_params* p) {
@@ -817,7 +820,7 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
       CK(cudaMemcpyAsync(c->harvest_x[c->harvest_n], c->hbox[0].f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
       c->harvest_n++;
     }
-    launch_corr<T>(L, s, rhop, pp, pn, ks, kk, c->fp64 ? 0 : 1);
+    launch_corr<T>(L, s, rhop, pp, pn, ks, kk, c->fp64 ? 0 : (fused_refine(c) ? 2 : 1));
     launch_div<T>(L, S(ks, F_U0));
     launch_accel<T>(L, ks, pn);
     const bool last = kk == nc - 1;
@@ -1058,7 +1061,7 @@ static int solve_box(fe_ctx* c, int box, const void* b, void* x, double dt, doub
   c->prm.p_maxit = save_maxit;
   if (rc != FE_OK) return rc;
   if (c->fp64) launch_true_res<T>(c->L(), K_X);
-  CK(cudaMemcpyAsync(x, B.f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(x, B.f[fused_refine(c) ? K_XH : K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
   rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   const double* s = c->hsc + (size_t)box * NSC;

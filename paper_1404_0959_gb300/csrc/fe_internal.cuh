@@ -52,6 +52,7 @@ enum WorkSlot {
   K_Z, K_PP, K_QP,        // flexible CG: preconditioned r, previous direction and its image
   K_X64,                  // double accumulator (mixed precision refinement)
   K_X64B,                 // its ping-pong partner (fused refinement of plain CG)
+  K_XH,                   // fused refinement: high parts of the pairs = the FP32 solution the corrector reads
   K_B64,                  // double right-hand side (mixed precision refinement)
   K_AUX,                  // scratch (diagnostics, user solve)
   NSLOT

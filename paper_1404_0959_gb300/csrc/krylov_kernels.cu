@@ -1178,6 +1178,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
   src.alpha = (T)B.sc[SC_ALPHA];
   src.moved = it > 0;
   float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
+  T* __restrict__ xh = F<T>(B, K_XH);
   T* __restrict__ r = F<T>(B, K_R);
   const double dt = B.sc[SC_KDT];
   const DF idt = df_from_double(1.0 / dt), kl = df_from_double(0.5 * dt * B.ih * B.ih);
@@ -1216,6 +1217,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     xn[c] = zc;
+    xh[c] = (T)zc.x;  // the high part is the pair rounded to FP32
     const float2* s = sm + G.csm;
     const float rv = refine_residual(zc, s[1], s[-1], s[ZGeom<1>::W], s[-ZGeom<1>::W], zp, zm, (float)bc, (float)pc,
                                      idt, kl);
@@ -1275,6 +1277,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
   src.alpha = (T)B.sc[SC_ALPHA];
   src.moved = it > 0;
   float2* __restrict__ xn = F<float2>(B, par ? K_X64 : K_X64B);
+  T* __restrict__ xh = F<T>(B, K_XH);
   T* __restrict__ r = F<T>(B, K_R);
   const T* __restrict__ borig = F<T>(B, K_AUX);
   const T* __restrict__ psi = F<T>(B, W_PSI);
@@ -1352,6 +1355,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
     if (!act) continue;
     const int c = col + NN * k;
     *reinterpret_cast<float4*>(xn + c) = make_float4(zc[0].x, zc[0].y, zc[1].x, zc[1].y);
+    stp(xh + c, (T)zc[0].x, (T)zc[1].x);  // the high parts are the pairs rounded to FP32
     const float r0 = refine_residual(zc[0], zc[1], sm[csm - 1], sm[csm + SW], sm[csm - SW], zp[0], zm[0],
                                      (float)bc.x, (float)pcv.x, idt, kl);
     const float r1 = refine_residual(zc[1], sm[csm + 2], zc[0], sm[csm + 1 + SW], sm[csm + 1 - SW], zp[1], zm[1],
@@ -1436,11 +1440,17 @@ __global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const 
   const BoxDev& B = boxes[ch.box];
   const int tid = threadIdx.x + TX * threadIdx.y;
   T* __restrict__ x = F<T>(B, K_X);
-  const bool second = pingpong && (((int)B.sc[SC_OUTER]) & 1);
-  const bool zero = pingpong && B.sc[SC_OUTER] == 0.0;  // no boundary pass ran: the pairs are zero
-  const float2* __restrict__ xs = F<float2>(B, second ? K_X64B : K_X64);
+  if (pingpong) {
+    // fused refinement: every boundary pass wrote the high parts (the pairs rounded to
+    // FP32) to K_XH; only a solve that never reached a boundary (b = 0) leaves zero there
+    if (B.sc[SC_OUTER] != 0.0) return;
+    T* __restrict__ xh = F<T>(B, K_XH);
+    for (int c = ch.begin + tid; c < ch.end; c += NTHR) xh[c] = T(0);
+    return;
+  }
+  const float2* __restrict__ xs = F<float2>(B, K_X64);
   for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
-    const float2 a = zero ? make_float2(0.f, 0.f) : xs[c];
+    const float2 a = xs[c];
     x[c] = (T)__fadd_rn(a.x, a.y);
   }
 }

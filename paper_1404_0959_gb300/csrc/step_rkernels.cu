@@ -89,11 +89,11 @@ using CorrPlan = RingPlan<T, kA, 2, 3, MIXED ? 6 : 8>;  // p^{k-1}, x | phi* | r
 
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_corr(const BoxDev* boxes, const int2* work, double* part, int s, int rhop,
-                                                int pp, int pnew, int kset, int kidx) {
+                                                int pp, int pnew, int kset, int kidx, int xslot) {
   constexpr int NC = MIXED ? 6 : 8;
   RING_PROLOGUE((CorrPlan<T, MIXED>));
   R.gs[0] = Fr<T>(B, pp);
-  R.gs[1] = Fr<T>(B, K_X);
+  R.gs[1] = Fr<T>(B, xslot);  // the pressure correction (FP32 solution, or the high parts of its pairs)
 #pragma unroll
   for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, W_PS0 + d);
   R.gc[0] = Fr<T>(B, S(s, F_RHO));
@@ -599,9 +599,11 @@ int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, i
   if (!L.ring_ok || !ring_ready<T>(mixed ? RK_CORR_M : RK_CORR_F)) return 0;
   constexpr int bm = CorrPlan<T, true>::bytes, bf = CorrPlan<T, false>::bytes;
   if (mixed)
-    FE_LAUNCH(L, KID_CORR, (kr_corr<T, true><<<RGRID(bm)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
+    FE_LAUNCH(L, KID_CORR, (kr_corr<T, true><<<RGRID(bm)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx,
+                                                             mixed == 2 ? K_XH : K_X)));
   else
-    FE_LAUNCH(L, KID_CORR, (kr_corr<T, false><<<RGRID(bf)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx)));
+    FE_LAUNCH(L, KID_CORR, (kr_corr<T, false><<<RGRID(bf)>>>(L.boxes, L.work, L.part, s, rhop, pp, pnew, kset, kidx,
+                                                              K_X)));
   return 1;
 }
 

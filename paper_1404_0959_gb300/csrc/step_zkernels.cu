@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(NTHR, 2) kz_corr(const BoxDev* boxes, const in
   __shared__ T sm[2][ZGeom<2>::H * ZGeom<2>::W];
   ZSum2<T> pk;
   ZField<T, 2> x;
-  pk.init(Fz<T>(B, pp), Fz<T>(B, K_X), sm[0], G, t.k0);
-  x.init(Fz<T>(B, K_X), sm[1], G, t.k0);
+  const int xs = mixed == 2 ? K_XH : K_X;  // the pressure correction (or the high parts of its pairs)
+  pk.init(Fz<T>(B, pp), Fz<T>(B, xs), sm[0], G, t.k0);
+  x.init(Fz<T>(B, xs), sm[1], G, t.k0);
   FaceBack<T> ps;
   ps.init(Fz<T>(B, W_PS0), Fz<T>(B, W_PS1), Fz<T>(B, W_PS2), G, t.k0);
   const T* __restrict__ rho = Fz<T>(B, S(s, F_RHO));
