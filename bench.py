@@ -44,8 +44,8 @@ def alg_words(kernel, nd, mixed=False):
         "bicg_p": 4, "bicg_v": 4, "bicg_s": 3, "bicg_t": 3, "bicg_x": 8, "true_res": 3,
         # refinement (field word = 4 bytes; x64 counts as two words)
         "mix_residual": 6, "mix_accum": 5, "mix_finish": 3, "commit": 0,
-        # fused refinement: pairs read and written, x, pd, b, psi, dinv read, r written
-        "refine": 10,
+        # fused refinement: pairs read and written, x, pd, b, psi, dinv read, r and the FP32 solution written
+        "refine": 11,
     }
     return table[kernel]
 
