@@ -790,8 +790,7 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
   Launch L = c->L();
   if (graph) L.st = c->cap[0];
   const int ks = 1 - s, nc = c->prm.n_corr;
-  launch_dt<T>(L, s, 0);
-  launch_div<T>(L, S(s, F_U0));
+  launch_dt_div<T>(L, s);
   launch_pred<T>(L, s, ks);
   launch_fluxn<T>(L, s);
   for (int kk = 0; kk < nc; ++kk) {

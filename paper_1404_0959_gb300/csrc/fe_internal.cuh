@@ -346,6 +346,18 @@ __device__ inline void cg_start_scalars(const BoxDev& B, double rz, double rr, i
   else if (sc[SC_ODONE] == 0.0) sc[SC_CONV] = 1.0;  // a finished refinement keeps its verdict
 }
 
+// Adaptive time step from the box's max_i sum_d |u_d| (last block of the max
+// reduction): CFL rule, growth limit against the previous step, cap.
+__device__ inline void finish_dt(const BoxDev& B, double umax) {
+  double dt = umax > 0.0 ? B.cfl * B.h / umax : HUGE_VAL;
+  const double prev = B.sc[SC_DTPREV];
+  if (prev > 0.0) dt = fmin(dt, B.growth * prev);
+  dt = fmin(dt, B.dtmax);
+  B.sc[SC_UMAX] = umax;
+  B.sc[SC_DT] = dt;
+  B.sc[SC_KDT] = dt;
+}
+
 // ---- block prologue -----------------------------------------------------------
 struct Tile {
   int box, i, j, k0, kend;
@@ -587,6 +599,7 @@ struct Launch {
 // Step kernels (step_kernels.cu); T = field type.
 template <typename T> void launch_dt(const Launch& L, int s, int first);
 template <typename T> void launch_div(const Launch& L, int uslot0);
+template <typename T> void launch_dt_div(const Launch& L, int s);  // adaptive dt and div u^n (one pass where it can)
 template <typename T> void launch_pred(const Launch& L, int s, int k);
 template <typename T> void launch_fluxn(const Launch& L, int s);
 template <typename T> void launch_asm(const Launch& L, int s, int uprev0, int phiprev0, int rhoprev);
@@ -614,7 +627,7 @@ template <typename V> int rlaunch_asm(const Launch& L, int s, int up0, int php0,
 template <typename V> int rlaunch_accel(const Launch& L, int kset, int pk);
 template <typename V> int rlaunch_fluxn(const Launch& L, int s, int nd);
 template <typename V> int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd);
-template <typename V> int rlaunch_div(const Launch& L, int u0);
+template <typename V> int rlaunch_div(const Launch& L, int u0, int with_dt = 0);
 template <typename V> int rlaunch_rhs(const Launch& L, int s, int rhop, int pp);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
 template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);

@@ -118,16 +118,7 @@ __global__ void __launch_bounds__(NTHR) k_dt(const BoxDev* boxes, const int2* ew
   }
   __shared__ double res;
   if (block_max_last((double)m, B, part, &res, B.etile0, B.entiles)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double umax = res;
-      double dt = umax > 0.0 ? B.cfl * B.h / umax : HUGE_VAL;
-      double prev = B.sc[SC_DTPREV];
-      if (prev > 0.0) dt = fmin(dt, B.growth * prev);
-      dt = fmin(dt, B.dtmax);
-      B.sc[SC_UMAX] = umax;
-      B.sc[SC_DT] = dt;
-      B.sc[SC_KDT] = dt;
-    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) finish_dt(B, res);
   }
 }
 
@@ -578,6 +569,11 @@ template <typename T> void launch_dt(const Launch& L, int s, int) {
   FE_LAUNCH(L, KID_DT, (k_dt<T><<<L.neblocks, dim3(TX, TY), 0, L.st>>>(L.boxes, L.ework, L.part, s)));
 }
 template <typename T> void launch_div(const Launch& L, int u0) { zlaunch_div<T>(L, u0); }
+template <typename T> void launch_dt_div(const Launch& L, int s) {
+  if (rlaunch_div<T>(L, S(s, F_U0), 1)) return;  // the ring divergence also takes the max for dt
+  launch_dt<T>(L, s, 0);
+  launch_div<T>(L, S(s, F_U0));
+}
 template <typename T> void launch_pred(const Launch& L, int s, int k) { zlaunch_pred<T>(L, s, k); }
 template <typename T> void launch_fluxn(const Launch& L, int s) {
   if (!L.fourier && L.nd >= 1 && L.nd <= 3) zlaunch_fluxn<T>(L, s, L.nd);
@@ -610,6 +606,7 @@ template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
 #define INST(T)                                                                              \
   template void launch_dt<T>(const Launch&, int, int);                                       \
   template void launch_div<T>(const Launch&, int);                                           \
+  template void launch_dt_div<T>(const Launch&, int);                                        \
   template void launch_pred<T>(const Launch&, int, int);                                     \
   template void launch_fluxn<T>(const Launch&, int);                                         \
   template void launch_asm<T>(const Launch&, int, int, int, int);                            \

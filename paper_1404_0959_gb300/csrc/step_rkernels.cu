@@ -497,13 +497,17 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
 // ---- velocity divergence div = sum_m Gc_m(u_m) --------------------------------------------------------
 template <typename T>
 using DivPlan = RingPlan<T, kA, 3, 0, 0>;  // u0..2
+// with_dt: also max_i sum_d |u_d| over the box and the adaptive time step
+// from it (the first divergence of a step reads u^n, the field k_dt reads).
 template <typename T>
-__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes, const int2* work, int u0) {
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes, const int2* work, int u0,
+                                                            double* part, int with_dt) {
   RING_PROLOGUE(DivPlan<T>);
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, u0 + m);
   T* __restrict__ div = Fr<T>(B, W_DIV);
   const T ih = (T)B.ih;
+  T umax = T(0);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
@@ -514,10 +518,15 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes,
     for (int r = 0; r < 2; ++r) {
       const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
       od[r] = (zGc_h(u[0], G, 0) + zGc_h(u[1], G, 1) + zGc_h(u[2], G, 2)) * ih;
+      if (with_dt) umax = fmax(umax, fabs(u[0].c()) + fabs(u[1].c()) + fabs(u[2].c()));
     }
     stp(div + G.col + G.plane(k), od[0], od[1]);
   }
   cp_async_wait<0>();
+  if (!with_dt) return;
+  __shared__ double res;
+  if (block_max_last((double)umax, B, part, &res, B.tile0, B.ntiles))
+    if (threadIdx.x == 0 && threadIdx.y == 0) finish_dt(B, res);
 }
 
 // ---- phi* and the pressure right-hand side --------------------------------------------------------------
@@ -658,9 +667,9 @@ int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, i
 }
 
 template <typename T>
-int rlaunch_div(const Launch& L, int u0) {
+int rlaunch_div(const Launch& L, int u0, int with_dt) {
   if (!L.ring_ok || !ring_ready<T>(RK_DIV)) return 0;
-  FE_LAUNCH(L, KID_DIV, (kr_div<T><<<RGRID(DivPlan<T>::bytes)>>>(L.boxes, L.work, u0)));
+  FE_LAUNCH(L, KID_DIV, (kr_div<T><<<RGRID(DivPlan<T>::bytes)>>>(L.boxes, L.work, u0, L.part, with_dt)));
   return 1;
 }
 template <typename T>
@@ -703,7 +712,7 @@ int rprepare() {
   template int rlaunch_accel<T>(const Launch&, int, int);                         \
   template int rlaunch_fluxn<T>(const Launch&, int, int);                         \
   template int rlaunch_dust<T>(const Launch&, int, int, int, int, int, int);      \
-  template int rlaunch_div<T>(const Launch&, int);                                \
+  template int rlaunch_div<T>(const Launch&, int, int);                           \
   template int rlaunch_rhs<T>(const Launch&, int, int, int);                      \
   template int rprepare<T>();
 RINST(double)
