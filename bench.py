@@ -217,6 +217,47 @@ def unet_flops(N):
     return 2.0 * macs
 
 
+def ensemble_only(args):
+    """--ensemble: the 64-box ensemble of uneven boxes (N in {32, 48, 64, 96}, FP32 fields) stepped in
+    one context -- one launch per stage over every box, CUDA graph, autotuned tiles -- against the
+    same boxes each in a context of its own stepped one after the other (same steps, same state)."""
+    import torch
+    from paper_1404_0959_gb300 import build, fe
+    from paper_1404_0959_gb300.inputs import ensemble64_boxes
+    build.build()
+    boxes = ensemble64_boxes(64)
+    cells = float(sum(b["N"] ** 3 for b in boxes))
+    K, W = args.steps, args.warmup
+
+    def timed(solver_boxes):
+        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+        s.init_state(-1, fe.FE_INIT_SPECTRAL)
+        s.autotune(2)
+        s.use_graphs(True)
+        code, _ = s.step(W)
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        code, _ = s.step(K)
+        ev1.record()
+        torch.cuda.synchronize()
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        s.close()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    t_ens = timed(boxes)
+    t_one = sum(timed([b]) for b in boxes)
+    line = {"metric": "cell-steps/s, 64-box ensemble of uneven boxes (one context vs one context per box)",
+            "value": cells * K / t_ens, "unit": "cell-steps/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * t_ens / K, "higher_is_better": True, "dtype": "f32 fields, f64 reductions",
+            "data": "synthetic spectral HIT boxes (seed = box index), no dataset",
+            "config": {"workload": "ensemble64", "boxes": len(boxes), "cells": int(cells), "p_tol": 1e-8,
+                       "cuda_graphs": True},
+            "per_box_contexts": {"value": cells * K / t_one, "ms_per_step": 1e3 * t_one / K}}
+    print(json.dumps(line), flush=True)
+
+
 def unet_only(args):
     """--unet: CUDA-event time of fe_precond_apply on a random residual (He-initialised weights)."""
     import torch
@@ -270,12 +311,16 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="host-driven steps in the headline region")
     ap.add_argument("--learn-steps", type=int, default=2, help="steps harvested for training (learned path)")
     ap.add_argument("--learn-iters", type=int, default=60, help="training iterations (learned path)")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="time the 64-box ensemble in one context against one context per box")
     ap.add_argument("--unet", action="store_true",
                     help="time only the learned preconditioner's network pass (K applications at N^3)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.unet:
         return unet_only(args)
+    if args.ensemble:
+        return ensemble_only(args)
 
     from paper_1404_0959_gb300.inputs import WORKLOADS
     cfg = dict(WORKLOADS[WORKLOAD])
