@@ -82,6 +82,29 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+# ---- multi-rank aggregation (replicas: one box per rank, no data-path collective) ----
+def rank_box(cfg, rank):
+    """The box of one rank: the workload's parameters with seed + rank (independent replicas)."""
+    return dict(N=cfg["N"], nu=cfg["nu"], tau_p=list(cfg["tau_p"]), Y0=list(cfg["Y0"]), mach_rms=cfg["mach_rms"],
+                k0=cfg["k0"], seed=cfg["seed"] + rank)
+
+
+def max_over_ranks(t, world, device="cuda"):
+    """The slowest rank's time (every rank returns it); t itself on one rank."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(cells_per_rank, steps, world, t):
+    """Whole-job throughput: the cells all ranks stepped over the slowest rank's time."""
+    return cells_per_rank * steps * world / t
+
+
 class Clocks:
     """nvidia-smi sampler (200 ms) running during the timed region."""
 
@@ -352,8 +375,7 @@ def main():
     precision = fe.FE_FP64 if args.precision == "fp64" else fe.FE_FP32_MIXED
     N = cfg["N"]
     nd = len(cfg["tau_p"])
-    box = dict(N=N, nu=cfg["nu"], tau_p=list(cfg["tau_p"]), Y0=list(cfg["Y0"]), mach_rms=cfg["mach_rms"],
-               k0=cfg["k0"], seed=cfg["seed"] + rank)
+    box = rank_box(cfg, rank)
     stream = torch.cuda.current_stream()
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
                   p_maxit=1000, stream=stream.cuda_stream)
@@ -425,13 +447,9 @@ def main():
     barrier()
     ck = clocks.stop()
     assert code == fe.FE_OK, fe.fe_strerror(code)
-    t = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
     cells = float(N) ** 3
-    value = cells * args.steps * world / t
+    value = job_rate(cells, args.steps, world, t)
     w = 8 if precision == fe.FE_FP64 else 4
     hbm, peak_kind = peaks()
     per_launch_ms = prof["target_ms"] / max(prof["target_launches"], 1)
@@ -461,13 +479,9 @@ def main():
             code, _ = s.step(1)
             fe.fe_get_fields(s.ctx, 0, fields, ptrs, 0)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0, world)
         nbytes = len(fields) * cells * w
-        e2e = {"value": cells * args.steps * world / te, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
+        e2e = {"value": job_rate(cells, args.steps, world, te), "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(nbytes)}
 
     s.close()
