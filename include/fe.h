@@ -273,14 +273,18 @@ int fe_use_graphs(fe_ctx* ctx, int on);
  * of the method. */
 int fe_precond_kernels(fe_ctx* ctx, int mode);
 
-/* Plane streaming for the fused CG iteration (on by default).  For boxes
- * with N in {64, 128, 256, 512} and the symmetric operator, the kernel that
- * forms the new direction and applies M to it streams whole x-rows of each
- * z-plane into shared memory with bulk asynchronous copies instead of
- * z-marching 32 x 8 column tiles; the arithmetic per cell is the same, the
- * order of the partial sums of <pd, M pd> differs.  Off: the z-marching
- * kernel for every box.  Not part of the method. */
+/* Plane streaming for the fused CG iteration (on by default).  For FP32
+ * contexts whose boxes all have N in {64, 128, 256, 512} and the symmetric
+ * operator, the kernel that forms the new direction and applies M to it
+ * streams whole x-rows of each z-plane into shared memory with bulk
+ * asynchronous copies instead of z-marching 32 x 8 column tiles; the
+ * arithmetic per cell is the same, the order of the partial sums of
+ * <pd, M pd> differs.  (FP64 rings do not fit in shared memory: FP64
+ * contexts always z-march.)  Off: the z-marching kernel for every box.
+ * fe_plane_streaming_active returns 1 when the next step streams, 0 when it
+ * z-marches, FE_ERR_INVALID_ARG for a null context.  Not part of the method. */
 int fe_use_plane_streaming(fe_ctx* ctx, int on);
+int fe_plane_streaming_active(const fe_ctx* ctx);
 
 /* Tile depth of the stencil kernels: every kernel launch covers all boxes
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz

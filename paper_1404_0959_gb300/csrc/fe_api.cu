@@ -1308,6 +1308,11 @@ extern "C" int fe_use_plane_streaming(fe_ctx* c, int on) {
   return FE_OK;
 }
 
+extern "C" int fe_plane_streaming_active(const fe_ctx* c) {
+  if (!c) return FE_ERR_INVALID_ARG;
+  return c->use_bulk && c->nbblocks > 0 ? 1 : 0;
+}
+
 extern "C" int fe_use_graphs(fe_ctx* c, int on) {
   if (!c) return FE_ERR_INVALID_ARG;
   c->use_graphs = on != 0;

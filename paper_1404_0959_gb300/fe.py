@@ -74,7 +74,8 @@ EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
            "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
-           "fe_use_plane_streaming", "fe_precond_kernels", "fe_destroy", "fe_strerror"]
+           "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_destroy",
+           "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -110,6 +111,7 @@ def load_library(path=LIB_PATH):
     lib.fe_harvest_pressure.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_int)]
     lib.fe_use_graphs.argtypes = [c_void_p, c_int]
     lib.fe_use_plane_streaming.argtypes = [c_void_p, c_int]
+    lib.fe_plane_streaming_active.argtypes = [c_void_p]
     lib.fe_precond_kernels.argtypes = [c_void_p, c_int]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
@@ -302,6 +304,13 @@ def fe_use_plane_streaming(ctx, on=True):
     return _check(lib().fe_use_plane_streaming(ctx, int(bool(on))), "fe_use_plane_streaming")
 
 
+def fe_plane_streaming_active(ctx):
+    code = lib().fe_plane_streaming_active(ctx)
+    if code < 0:
+        raise FeError(code, "fe_plane_streaming_active")
+    return bool(code)
+
+
 def fe_set_tiling(ctx, tz):
     return _check(lib().fe_set_tiling(ctx, tz), "fe_set_tiling")
 
@@ -455,6 +464,9 @@ class Solver:
 
     def use_plane_streaming(self, on=True):
         fe_use_plane_streaming(self.ctx, on)
+
+    def plane_streaming_active(self):
+        return fe_plane_streaming_active(self.ctx)
 
     def autotune(self, trials=2):
         return fe_autotune(self.ctx, trials)

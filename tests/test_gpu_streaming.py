@@ -1,10 +1,12 @@
-"""Plane-streamed fused CG kernel (bulk asynchronous copies, N in {64, 128,
-256, 512}) against the FP64 oracle and against the z-marching kernel.
+"""Plane-streamed fused CG kernel (bulk asynchronous copies, FP32 boxes with N
+in {64, 128, 256, 512}) against the FP64 oracle and against the z-marching
+kernel.
 
 The two kernels do the same per-cell arithmetic; only the order of the
-partial sums of <pd, M pd> differs, so steps agree to the Krylov tolerance
-(FP64 bar 1e-11 relative L2 per field and step against the oracle, as for
-the z-marching path).
+partial sums of <pd, M pd> differs, so mixed-precision steps agree to the
+reduced-precision bar (1e-5 relative L2 per field and step) and Krylov
+iteration counts to within one.  FP64 contexts always z-march (their rings do
+not fit in shared memory) and meet the FP64 bar (1e-11).
 """
 import numpy as np
 import pytest
@@ -55,50 +57,65 @@ def solver(fe, N, precision, streaming, seed=1, p_tol=1e-10):
     return s, (rho, u, Y)
 
 
-def test_streamed_fp64_step_matches_oracle(fe):
+def test_streamed_mixed_step_matches_oracle(fe):
     N = 64
-    s, (rho, u, Y) = solver(fe, N, fe.FE_FP64, True)
+    s, (rho, u, Y) = solver(fe, N, fe.FE_FP32_MIXED, True, p_tol=1e-8)
+    assert s.plane_streaming_active()
     prm = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], p_tol=1e-10)
     st = piso.make_state(prm, rho, u, Y)
-    s.profile_start("cg_dirmatvec")
     code, ginf = s.step(1)
-    prof = s.profile_stop()
     assert code == fe.FE_OK, fe.fe_strerror(code)
-    assert prof["target_launches"] > 0
     ref, info = piso.step(prm, st)
+    got = s.get_state(0)
+    s.close()
+    assert worst(got, ref) <= 1e-5
+
+
+def test_fp64_contexts_zmarch(fe):
+    # FP64 rings do not fit in shared memory: the request is accepted, the z-marching kernel runs,
+    # and the step meets the FP64 bar
+    N = 64
+    s, (rho, u, Y) = solver(fe, N, fe.FE_FP64, True)
+    assert not s.plane_streaming_active()
+    prm = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], p_tol=1e-10)
+    code, ginf = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    ref, info = piso.step(prm, piso.make_state(prm, rho, u, Y))
     got = s.get_state(0)
     s.close()
     assert worst(got, ref) <= 1e-11
     assert all(abs(a - b) <= 1 for a, b in zip(ginf[0]["iters"], info["iters"]))
 
 
-@pytest.mark.parametrize("N,precision,tol", [(128, 0, 1e-10), (256, 1, 1e-5)])
-def test_streamed_matches_zmarching(fe, N, precision, tol):
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_streamed_matches_zmarching(fe, N):
     out = []
     for streaming in (True, False):
-        s, _ = solver(fe, N, precision, streaming, seed=2, p_tol=1e-10 if precision == 0 else 1e-8)
+        s, _ = solver(fe, N, fe.FE_FP32_MIXED, streaming, seed=2, p_tol=1e-8)
+        assert s.plane_streaming_active() == streaming
         code, info = s.step(2)
         assert code == fe.FE_OK, fe.fe_strerror(code)
         out.append((s.get_state(0), info[0]))
         s.close()
     (a, ia), (b, ib) = out
-    assert worst(a, b) <= tol
+    assert worst(a, b) <= 1e-5
     assert all(abs(x - y) <= 1 for x, y in zip(ia["iters"], ib["iters"]))
 
 
 def test_streamed_ensemble_matches_single_boxes(fe):
     boxes = [dict(N=64, nu=0.005, tau_p=[0.05], Y0=[0.01], seed=3),
              dict(N=128, nu=0.002, tau_p=[0.05], Y0=[0.01], seed=4)]
-    ens = fe.Solver(boxes)
+    ens = fe.Solver(boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8)
     ens.init_state(-1, fe.FE_INIT_SPECTRAL)
+    assert ens.plane_streaming_active()
     code, _ = ens.step(2)
     assert code == fe.FE_OK, fe.fe_strerror(code)
     for b, box in enumerate(boxes):
-        one = fe.Solver([box])
+        one = fe.Solver([box], precision=fe.FE_FP32_MIXED, p_tol=1e-8)
         one.init_state(0, fe.FE_INIT_SPECTRAL)
         code, _ = one.step(2)
         assert code == fe.FE_OK
-        assert worst(ens.get_state(b), one.get_state(0)) <= 1e-10
+        assert worst(ens.get_state(b), one.get_state(0)) <= 1e-5
         one.close()
     ens.close()
 
@@ -111,6 +128,7 @@ def test_streamed_512_mixed_matches_zmarching(fe):
                       precision=fe.FE_FP32_MIXED, p_tol=1e-8)
         s.init_state(0, fe.FE_INIT_SPECTRAL)
         s.use_plane_streaming(streaming)
+        assert s.plane_streaming_active() == streaming
         code, info = s.step(1)
         assert code == fe.FE_OK, fe.fe_strerror(code)
         st = s.get_state(0)
