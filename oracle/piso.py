@@ -1,8 +1,9 @@
 """One compressible PISO step of Equilibrium-Eulerian dusty decaying HIT (FP64).
 
-Test infrastructure (see ``oracle/__init__``).  Parity unpinned as a whole:
-this function *is* the definition of the discrete step; its parts are pinned
-by the tests listed at the end of this header.
+Test infrastructure (see ``oracle/__init__``).  A nonlinear step has no
+closed form, so this function is the definition of the discrete step; every
+term of it is pinned by at least one of the tests listed at the end of this
+header.
 
 Paper passages it restates (arXiv:1404.0959):
 
@@ -56,7 +57,9 @@ Pins (tests/test_oracle_piso.py): Taylor-Green viscous decay rate against the
 discrete and the analytic rate; exact conservation of mass, dust mass and
 total energy; uniform state stays uniform; tau_p = 0 passive tracer; first
 order response in tau_p; closed-form initial dust drift for a pressure and
-for a dilatational velocity perturbation; isobaric heat-conduction decay.
+for a dilatational velocity perturbation; isobaric heat-conduction decay;
+acoustic wave speed c = 1; psi c^2 = 1 with c^2 the isentropic derivative of
+the closure's EOS; the adaptive step's Courant number, growth limit and cap.
 """
 import math
 from dataclasses import dataclass, field
@@ -124,6 +127,11 @@ def eos_pressure(prm, rho, T=None):
     if prm.closure == BAROTROPIC:
         return rho ** prm.gamma / prm.gamma
     return rho * prm.R * T
+
+
+def compressibility(prm, rho, p):
+    """psi = rho/(gamma p) = 1/c^2, the isentropic compressibility (both closures)."""
+    return rho / (prm.gamma * p)
 
 
 def face_flux(rho, u):
@@ -227,7 +235,7 @@ def step(prm, state, precond=None, dt=None):
     # a1: adaptive time step, psi frozen at level n
     if dt is None:
         dt = time_step(prm, u_n, state["dt_prev"])
-    psi = rho_n / (prm.gamma * p_n)
+    psi = compressibility(prm, rho_n, p_n)
 
     # a3: predictor
     divphi_n = ops.D(phi_n, h)

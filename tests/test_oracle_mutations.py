@@ -66,6 +66,15 @@ def _energy_no_pressure_work(prm, phi, u, rho, p, E, T):
     return F
 
 
+def _dt_euclidean(prm, u, dt_prev):
+    umax = float(np.max(np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)))
+    return min(prm.cfl * prm.h / umax, prm.dt_growth_max * dt_prev, prm.dt_max)
+
+
+def _psi_isothermal(prm, rho, p):
+    return rho / p
+
+
 CASES = [
     ("I4 normalisation", ops, "I4", _bad_I4, lambda: t_ops.test_symbols(16, 1, 0)),
     ("G4 normalisation", ops, "G4", _bad_G4, lambda: t_ops.test_order_G4()),
@@ -76,6 +85,10 @@ CASES = [
     ("convection sign", ops, "L", _L_wrong_sign, lambda: t_ops.test_convection_closed_form()),
     ("barotropic EOS without 1/gamma", piso, "eos_pressure", _eos_no_gamma_division,
      lambda: t_piso.test_acoustic_wave_speed()),
+    ("Euclidean Courant number", piso, "time_step", _dt_euclidean,
+     lambda: t_piso.test_adaptive_time_step_courant_number_and_growth()),
+    ("isothermal compressibility", piso, "compressibility", _psi_isothermal,
+     lambda: t_piso.test_psi_is_inverse_isentropic_sound_speed_squared(piso.FOURIER)),
     ("Du/Dt pressure sign", piso, "accel", _accel_wrong_sign,
      lambda: t_piso.test_dust_drift_pressure_closed_form()),
     ("enthalpy flux without p/rho", piso, "energy_flux", _energy_no_pressure_work,

@@ -220,10 +220,73 @@ def _acoustic_omega(N, dt=0.01):
 def test_acoustic_wave_speed():
     """A k = 1 density wave oscillates at omega = c k with c^2 = gamma p / rho = 1.
 
-    Pins psi = rho/(gamma p) and the EOS: a missing gamma moves c by
-    sqrt(1.4).  Discretisation error converges at second order or better.
+    Pins the EOS: a missing gamma moves c by sqrt(1.4).  (psi enters the
+    wave only at O(dt^2) per step; its value has its own pin below.)
+    Discretisation error converges at second order or better.
     """
     w8 = _acoustic_omega(8)
     w16 = _acoustic_omega(16)
     assert abs(w16 - 1) < 1e-2
     assert abs(w16 - 1) < abs(w8 - 1) / 3
+
+
+def _isentropic_c2(prm, rho, T, delta=1e-6):
+    """dp/drho at constant entropy, by central differences of the oracle's EOS.
+
+    Barotropic: p = p(rho) is itself isentropic.  Fourier: an ideal gas with
+    constant c_v keeps c_v ln T - R ln rho fixed, so T scales as rho^(R/c_v)
+    along the isentrope.
+    """
+    def p_at(s):
+        r = rho * (1 + s)
+        if prm.closure == piso.BAROTROPIC:
+            return piso.eos_pressure(prm, r)
+        return piso.eos_pressure(prm, r, T * (1 + s) ** (prm.R / prm.cv))
+    return (p_at(delta) - p_at(-delta)) / (2 * delta * rho)
+
+
+@pytest.mark.parametrize("closure", [piso.BAROTROPIC, piso.FOURIER])
+def test_psi_is_inverse_isentropic_sound_speed_squared(closure):
+    """psi (the step's compressibility, frozen at level n) times the isentropic
+    c^2 = dp/drho|_s of the closure is 1 at every cell.
+
+    An isothermal psi = 1/(R T) would give 1/gamma under the Fourier closure,
+    a missing gamma gives gamma, an inverted ratio gives c^4.
+    """
+    N = 8
+    prm = piso.Params(N=N, closure=closure, tau_p=[0.05], Y0=[0.01], dt_max=0.01)
+    st = random_state(prm, 11, amp=0.2)
+    _new, info = piso.step(prm, st)
+    c2 = _isentropic_c2(prm, st["rho"], st["T"])
+    assert np.max(np.abs(info["psi"] * c2 - 1)) < 1e-8
+
+
+def test_adaptive_time_step_courant_number_and_growth():
+    """a1: the step taken is the largest with Courant number
+    dt * max_i sum_d |u_d| / h <= CFL (0.5), grown by at most 1.2 per step.
+
+    A diagonal velocity (1, -1, 1) u0 has sum_d |u_d| = 3 u0 but |u| = sqrt(3) u0,
+    so a Euclidean Courant number would give a step sqrt(3) times larger.
+    """
+    N = 8
+    prm = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])
+    h = 2 * math.pi / N
+    ones = np.ones((N, N, N))
+    u0 = 0.3
+    u = [u0 * ones, -u0 * ones, u0 * ones]
+    u[0][3, 2, 5] = 2 * u0                     # the most restrictive cell: 4 u0
+    st = piso.make_state(prm, ones, u, [0.01 * ones])
+    assert st["dt_prev"] == math.inf
+    new, info = piso.step(prm, st)
+    assert abs(info["dt"] - 0.5 * h / (4 * u0)) <= 1e-15 * info["dt"]
+    assert new["dt_prev"] == info["dt"] and abs(new["t"] - info["dt"]) <= 1e-15
+
+    # growth limit: a slower flow may take at most 1.2 times the previous step
+    st2 = piso.make_state(prm, ones, [0.1 * c for c in u], [0.01 * ones])
+    st2["dt_prev"] = info["dt"]
+    _n2, info2 = piso.step(prm, st2)
+    assert abs(info2["dt"] / info["dt"] - 1.2) < 1e-14
+    # and the optional cap
+    prm3 = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], dt_max=0.01)
+    _n3, info3 = piso.step(prm3, st)
+    assert info3["dt"] == 0.01
