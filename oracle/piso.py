@@ -59,7 +59,8 @@ total energy; uniform state stays uniform; tau_p = 0 passive tracer; first
 order response in tau_p; closed-form initial dust drift for a pressure and
 for a dilatational velocity perturbation; isobaric heat-conduction decay;
 acoustic wave speed c = 1; psi c^2 = 1 with c^2 the isentropic derivative of
-the closure's EOS; the adaptive step's Courant number, growth limit and cap.
+the closure's EOS; the adaptive step's Courant number, growth limit and cap;
+with one corrector, sum rho^0 u^{n+1} = sum rho^n u^n exactly.
 """
 import math
 from dataclasses import dataclass, field

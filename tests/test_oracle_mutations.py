@@ -66,6 +66,16 @@ def _energy_no_pressure_work(prm, phi, u, rho, p, E, T):
     return F
 
 
+def _L_advective(u, phi, mu, h):
+    # convection as (face flux averaged to the cell) . Gc(u): not a divergence
+    visc = ops.div_stress(u, mu, h)
+    out = []
+    for m in range(3):
+        adv = sum(0.5 * (phi[d] + ops.at(phi[d], d, -1)) * ops.Gc(u[m], d, h) for d in range(3))
+        out.append(-adv + visc[m])
+    return out
+
+
 def _dt_euclidean(prm, u, dt_prev):
     umax = float(np.max(np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)))
     return min(prm.cfl * prm.h / umax, prm.dt_growth_max * dt_prev, prm.dt_max)
@@ -83,6 +93,8 @@ CASES = [
     ("stress transposed gradient", ops, "stress", _stress_transposed,
      lambda: t_ops.test_viscous_stress_closed_form()),
     ("convection sign", ops, "L", _L_wrong_sign, lambda: t_ops.test_convection_closed_form()),
+    ("advective convection", ops, "L", _L_advective,
+     lambda: t_piso.test_single_corrector_momentum_identity(piso.BAROTROPIC, 0)),
     ("barotropic EOS without 1/gamma", piso, "eos_pressure", _eos_no_gamma_division,
      lambda: t_piso.test_acoustic_wave_speed()),
     ("Euclidean Courant number", piso, "time_step", _dt_euclidean,

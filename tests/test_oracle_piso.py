@@ -290,3 +290,27 @@ def test_adaptive_time_step_courant_number_and_growth():
     prm3 = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], dt_max=0.01)
     _n3, info3 = piso.step(prm3, st)
     assert info3["dt"] == 0.01
+
+
+@pytest.mark.parametrize("closure,transonic", [(piso.BAROTROPIC, 0), (piso.FOURIER, 1)])
+def test_single_corrector_momentum_identity(closure, transonic):
+    """With one corrector, sum_i rho^0 u^{n+1} = sum_i rho^n u^n exactly,
+    rho^0 = rho^n - dt D(phi^n).
+
+    The corrected velocity is HbyA - (dt/rho^0) Gc(p^1) and HbyA = (rho^n u^n +
+    dt R^1)/rho^0, so rho^0 u^1 = rho^n u^n + dt (R^1 - Gc p^1): R in divergence
+    form and Gc a periodic difference sum to zero.  Pins the momentum numerator,
+    the common divisor rho^{k-1} of HbyA and the velocity correction, and the
+    conservative form of convection and viscous stress.
+    """
+    from oracle import ops
+    N = 8
+    prm = piso.Params(N=N, closure=closure, transonic=transonic, n_corr=1, tau_p=[0.05], Y0=[0.01])
+    st = random_state(prm, 3, amp=0.1)
+    dt = 0.02
+    new, _info = piso.step(prm, st, dt=dt)
+    rho0 = st["rho"] - dt * ops.D(st["phi"], prm.h)
+    for m in range(3):
+        got = np.sum(rho0 * new["u"][m])
+        want = np.sum(st["rho"] * st["u"][m])
+        assert abs(got - want) <= 1e-13 * np.sum(np.abs(st["rho"] * st["u"][m]))
