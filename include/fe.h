@@ -279,8 +279,8 @@ int fe_precond_kernels(fe_ctx* ctx, int mode);
  * streams whole x-rows of each z-plane into shared memory with bulk
  * asynchronous copies instead of z-marching 32 x 8 column tiles; the
  * arithmetic per cell is the same, the order of the partial sums of
- * <pd, M pd> differs.  (FP64 rings do not fit in shared memory: FP64
- * contexts always z-march.)  Off: the z-marching kernel for every box.
+ * <pd, M pd> differs.  (FP64 contexts, bound by the FP64 pipe rather than
+ * by memory, always z-march.)  Off: the z-marching kernel for every box.
  * fe_plane_streaming_active returns 1 when the next step streams, 0 when it
  * z-marches, FE_ERR_INVALID_ARG for a null context.  Not part of the method. */
 int fe_use_plane_streaming(fe_ctx* ctx, int on);

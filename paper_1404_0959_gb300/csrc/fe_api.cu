@@ -223,11 +223,12 @@ static int set_tiling(fe_ctx* c, int tz) {
   c->ring_ok = 1;
   for (int b = 0; b < c->nb; ++b)
     if (c->hbox[b].N % (c->fp64 ? 2 : 4)) c->ring_ok = 0;
-  // plane-streaming blocks: every box with N in {64, 128, 256, 512}, a
-  // persistent grid of the resident blocks per SM x SMs shared out by cells
+  // plane-streaming blocks (FP32 fields; FP64 contexts are bound by the FP64
+  // pipe and keep the z-marching kernel): every box with N in {64, 128, 256,
+  // 512}, a persistent grid of the resident blocks per SM x SMs shared out by cells
   std::vector<int2> bwork;
   int bsmem = 0;
-  bool stream = !c->prm.transonic;
+  bool stream = !c->prm.transonic && !c->fp64;
   long scells = 0;
   for (int b = 0; b < c->nb && stream; ++b) {
     const int N = c->hbox[b].N;

@@ -72,8 +72,8 @@ def test_streamed_mixed_step_matches_oracle(fe):
 
 
 def test_fp64_contexts_zmarch(fe):
-    # FP64 rings do not fit in shared memory: the request is accepted, the z-marching kernel runs,
-    # and the step meets the FP64 bar
+    # FP64 contexts keep the z-marching kernel (the streamed one serves FP32 fields): the request
+    # is accepted, the z-marching kernel runs, and the step meets the FP64 bar
     N = 64
     s, (rho, u, Y) = solver(fe, N, fe.FE_FP64, True)
     assert not s.plane_streaming_active()
