@@ -6,7 +6,7 @@ Each case names the mistake and the pin expected to catch it.
 import numpy as np
 import pytest
 
-from oracle import ops, piso
+from oracle import krylov, ops, piso
 
 from . import test_oracle_ops as t_ops
 from . import test_oracle_piso as t_piso
@@ -76,6 +76,13 @@ def _L_advective(u, phi, mu, h):
     return out
 
 
+def _givens_transposed(a, b):
+    if b == 0.0:
+        return 1.0, 0.0
+    h = float(np.hypot(a, b))
+    return b / h, a / h
+
+
 def _dt_euclidean(prm, u, dt_prev):
     umax = float(np.max(np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)))
     return min(prm.cfl * prm.h / umax, prm.dt_growth_max * dt_prev, prm.dt_max)
@@ -99,6 +106,8 @@ CASES = [
      lambda: t_piso.test_acoustic_wave_speed()),
     ("Euclidean Courant number", piso, "time_step", _dt_euclidean,
      lambda: t_piso.test_adaptive_time_step_courant_number_and_growth()),
+    ("Givens rotation with swapped entries", krylov, "_givens", _givens_transposed,
+     lambda: t_solve.test_fgmres_minimises_residual_over_its_directions(3)),
     ("isothermal compressibility", piso, "compressibility", _psi_isothermal,
      lambda: t_piso.test_psi_is_inverse_isentropic_sound_speed_squared(piso.FOURIER)),
     ("Du/Dt pressure sign", piso, "accel", _accel_wrong_sign,
