@@ -63,6 +63,10 @@ extern "C" {
 #define FE_BICGSTAB_JACOBI  1   /* any operator (required for transonic = 1) */
 #define FE_FCG_LEARNED      2   /* flexible CG, learned preconditioner with  *
                                  * Jacobi fallback (needs fe_load_preconditioner) */
+#define FE_FGMRES_LEARNED   3   /* flexible GMRES(20) (Saad 1993), any operator  *
+                                 * (transonic included): learned directions when *
+                                 * a network is loaded, Jacobi otherwise; one box, *
+                                 * N divisible by 4; host-driven (no CUDA graph)  */
 
 /* field ids for fe_set_field / fe_get_field */
 #define FE_RHO   0
@@ -102,13 +106,15 @@ typedef struct {
     double dt_growth_max;       /* max dt ratio between steps (1.2)              */
     double dt_max;              /* upper bound on dt (use HUGE_VAL for none)     */
     int32_t n_corr;             /* PISO correctors, >= 1 (2 recommended)         */
-    int32_t solver;             /* FE_PCG_JACOBI | FE_BICGSTAB_JACOBI | FE_FCG_LEARNED */
+    int32_t solver;             /* FE_PCG_JACOBI | FE_BICGSTAB_JACOBI | FE_FCG_LEARNED |
+                                 * FE_FGMRES_LEARNED */
     double p_tol;               /* ||b - M x||_2 <= p_tol ||b||_2                */
     int32_t p_maxit;            /* Krylov iteration cap per solve                */
     int32_t transonic;          /* 1: add the psi-convection term (non-symmetric) */
-    int32_t learned_every;      /* FE_FCG_LEARNED: network direction at iterations it with
-                                 * it % learned_every == 0 (1 = every iteration), Jacobi
-                                 * direction otherwise; 0 = first iteration only */
+    int32_t learned_every;      /* FE_FCG_LEARNED, FE_FGMRES_LEARNED: network direction at
+                                 * iterations it with it % learned_every == 0 (1 = every
+                                 * iteration), Jacobi direction otherwise; 0 = first
+                                 * iteration only */
 } fe_params;
 
 typedef struct {
@@ -222,7 +228,14 @@ int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
  * the tensor cores) maps the residual r to a search direction of flexible CG
  * (solver FE_FCG_LEARNED; one box, N divisible by 4).  When <z, r> <= 0 the
  * Jacobi direction is used instead, so plain preconditioned CG remains the
- * fallback.  Network input: channel 0 = r / rms(r), channel 1 = psi - 1.
+ * fallback.  With FE_FGMRES_LEARNED the network maps each unit Arnoldi
+ * vector v_j to the direction z_j of flexible GMRES(20) (right
+ * preconditioning, M Z_k = V_{k+1} H_k; x minimises ||b - M x|| over the
+ * span of Z_k), which needs no symmetry and so also serves the transonic
+ * operator; a network direction that is not finite, is zero, has an image
+ * already in the span of the basis (new component below 1e-5 of its norm),
+ * or shrinks the least-squares residual by less than 10 % is replaced by the
+ * Jacobi direction, and without a loaded network every direction is Jacobi's.  Network input: channel 0 = r / rms(r), channel 1 = psi - 1.
  * Layers, in parameter order: e1a 2->16, e1b 16->16, d1 16->32 (stride 2),
  * e2 32->32, d2 32->64 (stride 2), e3 64->64, u2 [up2(e3), e2] 96->32,
  * u1 [up2(u2), e1b] 48->16, out 16->1 (linear).  Parameter layout (FP32,

@@ -153,16 +153,21 @@ def _givens(a, b):
     return a / h, b / h
 
 
-def fgmres(matvec, b, precond, diag, tol, maxit, m=20):
+def fgmres(matvec, b, precond, diag, tol, maxit, m=20, keep=0.9):
     """Flexible GMRES(m), right-preconditioned, x0 = 0.
 
     precond(v, it) returns the direction z_j for the unit Arnoldi vector v_j
     at overall iteration `it`, or None for the Jacobi direction v_j / diag
-    (``precond`` None: always Jacobi).  Directions that are not finite or are
-    zero fall back to Jacobi.  After each cycle of at most m directions,
-    x += Z y with y the least-squares solution of the Hessenberg system; the
-    next cycle starts from the true residual.  Same returns as ``pcg``
-    (the recurrence residual is the least-squares residual |g_{j+1}|).
+    (``precond`` None: always Jacobi).  A preconditioner direction is kept
+    only if it is finite and non-zero, its image M z is not (to 1e-5 of its
+    norm) in the span of the basis so far (which would make the Hessenberg
+    matrix singular and the residual estimate meaningless), and its Arnoldi
+    column shrinks the least-squares residual to at most ``keep`` times its
+    previous value; otherwise the column is recomputed with the Jacobi
+    direction (so a poor network cannot stall or fool the solve).  After each cycle of at most m
+    directions, x += Z y with y the least-squares solution of the Hessenberg
+    system; the next cycle starts from the true residual.  Same returns as
+    ``pcg`` (the recurrence residual is the least-squares residual |g_{j+1}|).
     """
     x = np.zeros_like(b)
     bnorm = _norm(b)
@@ -173,6 +178,9 @@ def fgmres(matvec, b, precond, diag, tol, maxit, m=20):
     res = bnorm
     while True:
         beta = _norm(r)
+        if beta <= tol * bnorm:  # a restart's true residual already meets the tolerance
+            res = beta
+            break
         V = [r / beta]
         Z = []
         H = np.zeros((m + 1, m))
@@ -181,21 +189,38 @@ def fgmres(matvec, b, precond, diag, tol, maxit, m=20):
         g = np.zeros(m + 1)
         g[0] = beta
         k = 0
+
+        def column(z, j):
+            """Arnoldi column of direction z (modified Gram-Schmidt), its next
+            basis vector, the column after the previous rotations, and ||M z||."""
+            w = matvec(z)
+            wn = _norm(w)
+            h = np.zeros(j + 2)
+            for i in range(j + 1):
+                h[i] = float(np.sum(w * V[i]))
+                w = w - h[i] * V[i]
+            h[j + 1] = _norm(w)
+            v = w / h[j + 1] if h[j + 1] > 0.0 else w
+            for i in range(j):
+                a, c = h[i], h[i + 1]
+                h[i] = cs[i] * a + sn[i] * c
+                h[i + 1] = -sn[i] * a + cs[i] * c
+            return h, v, wn
+
         for j in range(m):
             z = precond(V[j], it) if precond is not None else None
-            if z is None or not np.all(np.isfinite(z)) or _norm(z) == 0.0:
+            h = None
+            if z is not None and np.all(np.isfinite(z)) and _norm(z) > 0.0:
+                h, v, wn = column(z, j)
+                c, s = _givens(h[j], h[j + 1])
+                if not float(np.hypot(h[j], h[j + 1])) > 1e-5 * wn or abs(s) > keep:
+                    h = None  # degenerate, or too little progress: the Jacobi direction instead
+            if h is None:
                 z = V[j] / diag
+                h, v, _ = column(z, j)
             Z.append(z)
-            w = matvec(z)
-            for i in range(j + 1):
-                H[i, j] = float(np.sum(w * V[i]))
-                w = w - H[i, j] * V[i]
-            H[j + 1, j] = _norm(w)
-            V.append(w / H[j + 1, j] if H[j + 1, j] > 0.0 else w)
-            for i in range(j):
-                a, c = H[i, j], H[i + 1, j]
-                H[i, j] = cs[i] * a + sn[i] * c
-                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            V.append(v)
+            H[: j + 2, j] = h
             cs[j], sn[j] = _givens(H[j, j], H[j + 1, j])
             H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
             H[j + 1, j] = 0.0

@@ -35,6 +35,8 @@ frozen at level n; mu = nu (reference density 1).
      b     = -[(rho^{k-1} - rho^n)/dt + D(phi^n)/2 + D(phi*)/2]
  a5  M p' = b,  M p' = psi p'/dt - (dt/2) D(G2 p')
                 [+ (1/2) D(I4(psi p') I4(HbyA))  when transonic]
+     (Jacobi-PCG; BiCGStab when transonic; flexible CG with a given
+      preconditioner; flexible GMRES(20) for either operator when fgmres)
  a6  p^k   = p^{k-1} + p'
      phi^k = phi* - dt G2(p')  [+ I4(psi p') I4(HbyA) when transonic]
      u^k   = HbyA - (dt / rho^{k-1}) Gc(p^k)
@@ -68,7 +70,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import ops
-from .krylov import bicgstab, fcg, pcg
+from .krylov import bicgstab, fcg, fgmres, pcg
 
 BAROTROPIC = 0
 FOURIER = 1
@@ -93,6 +95,7 @@ class Params:
     p_tol: float = 1e-10
     p_maxit: int = 500
     transonic: bool = False
+    fgmres: bool = False  # flexible GMRES(20) for every solve (any operator)
 
     @property
     def h(self):
@@ -214,6 +217,9 @@ def helmholtz(prm, psi, dt, HbyA=None):
 
 
 def solve(prm, matvec, b, diag, precond=None):
+    if prm.fgmres:
+        pre = None if precond is None else (lambda v, it: precond(v))
+        return fgmres(matvec, b, pre, diag, prm.p_tol, prm.p_maxit, m=20)
     if precond is not None:
         return fcg(matvec, b, precond, diag, prm.p_tol, prm.p_maxit)
     if prm.transonic:

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fe_internal.cuh"
+#include "fgmres.cuh"
 
 using namespace fe;
 
@@ -106,7 +107,11 @@ struct fe_ctx {
   double* hsc = nullptr;   // pinned copy of all box scalars
   int cur = 0;             // state set holding the current state
   int hint[16] = {};       // iterations of the previous Krylov solve, per solve key
-  UNet* unet = nullptr;    // learned preconditioner (FE_FCG_LEARNED)
+  UNet* unet = nullptr;    // learned preconditioner (FE_FCG_LEARNED, FE_FGMRES_LEARNED)
+  void* gm_basis = nullptr;   // FE_FGMRES_LEARNED: Arnoldi basis V (m + 1 vectors), directions Z (m)
+  double* gm_part = nullptr;  // its block partial sums (device) ...
+  double* gm_hpart = nullptr; // ... and their pinned host copy
+  int gm_blocks = 0;
   bool use_graphs = false;           // step as one CUDA graph with WHILE nodes for the solves
   cudaGraphExec_t gexec[2] = {};     // per parity of the current state set
   cudaStream_t cap[3] = {};          // capture streams (loop nesting levels)
@@ -176,11 +181,13 @@ static int validate(const fe_params* p) {
   if (p->n_corr < 1 || p->n_corr > 4) return FE_ERR_INVALID_ARG;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->p_tol > 0.0) || p->p_maxit < 1) return FE_ERR_INVALID_ARG;
   if (p->closure == FE_FOURIER && !(p->Pr > 0.0)) return FE_ERR_INVALID_ARG;
-  if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED)
+  if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED &&
+      p->solver != FE_FGMRES_LEARNED)
     return FE_ERR_INVALID_ARG;
   if (p->transonic && p->solver == FE_PCG_JACOBI) return FE_ERR_INVALID_ARG;
   if (p->solver == FE_FCG_LEARNED && (p->n_boxes != 1 || p->N[0] % 4 != 0 || p->transonic))
     return FE_ERR_UNSUPPORTED;
+  if (p->solver == FE_FGMRES_LEARNED && (p->n_boxes != 1 || p->N[0] % 4 != 0)) return FE_ERR_UNSUPPORTED;
   if (p->learned_every < 0) return FE_ERR_INVALID_ARG;
   for (int b = 0; b < p->n_boxes; ++b)
     if (p->N[b] < 8 || p->N[b] > 512 || !(p->nu[b] >= 0.0)) return FE_ERR_INVALID_ARG;
@@ -391,6 +398,16 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
     cudaMemsetAsync(c->dcnt, 0, nb * sizeof(int), c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = FE_ERR_CUDA;
   }
+  if (rc == FE_OK && prm->solver == FE_FGMRES_LEARNED) {
+    const long n = (long)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N;
+    const size_t esz = c->fp64 ? 8 : 4;
+    c->gm_blocks = (int)std::min<long>((n + 255) / 256, 8L * c->nsm);
+    const size_t parts = std::max<size_t>((size_t)c->gm_blocks * kGmPart, NSC);
+    if (cudaMalloc(&c->gm_basis, (size_t)(2 * kGmRestart + 1) * n * esz) != cudaSuccess ||
+        cudaMalloc(&c->gm_part, parts * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->gm_hpart, parts * sizeof(double)) != cudaSuccess)
+      rc = FE_ERR_OOM;
+  }
   if (rc == FE_OK) rc = set_tiling(c, 0);
   if (rc != FE_OK) {
     fe_destroy(c);
@@ -420,6 +437,9 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->dcnt);
   cudaFree(c->dactive);
   cudaFree(c->douter);
+  cudaFree(c->gm_basis);
+  cudaFree(c->gm_part);
+  if (c->gm_hpart) cudaFreeHost(c->gm_hpart);
   if (c->hactive) cudaFreeHost(c->hactive);
   if (c->hsc) cudaFreeHost(c->hsc);
   delete c;
@@ -554,12 +574,177 @@ static int fcg_learned(fe_ctx* c, int maxit) {
   return FE_OK;
 }
 
+// Block partial sums of the FGMRES kernels, added on the host in block order.
+static int gm_sums(fe_ctx* c, int stride, double* out) {
+  const size_t cnt = (size_t)c->gm_blocks * stride;
+  CK(cudaMemcpyAsync(c->gm_hpart, c->gm_part, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < stride; ++i) out[i] = 0.0;
+  for (int bl = 0; bl < c->gm_blocks; ++bl)
+    for (int i = 0; i < stride; ++i) out[i] += c->gm_hpart[(size_t)bl * stride + i];
+  return FE_OK;
+}
+
+// Flexible GMRES(m) (Saad 1993) on box 0, any operator: right
+// preconditioning with the network direction (learned_every as for flexible
+// CG) or the Jacobi one (no network loaded, or a network output that is not
+// finite or is zero), Arnoldi by classical Gram-Schmidt with one
+// reorthogonalisation, Givens rotations and the least-squares update in FP64
+// on the host, restart after kGmRestart directions from the true residual.
+// Stops when the least-squares residual meets SC_TOL ||b|| or at the
+// iteration cap; x0 = 0 (the refinement's correction starts from zero).
+template <typename T>
+static int fgmres_learned(fe_ctx* c, int maxit) {
+  Launch L = c->L();
+  BoxDev& B = c->hbox[0];
+  cudaStream_t st = c->st;
+  const long n = (long)B.N * B.N * B.N;
+  const int m = kGmRestart, nb = c->gm_blocks;
+  CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), st));
+  launch_cg_init<T>(L, 0.0);  // x = 0, r = b, ||b||^2, the solve's scalars and counter
+  double* hs = c->gm_hpart;
+  CK(cudaMemcpyAsync(hs, B.sc, NSC * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hs[SC_DONE] != 0.0) return FE_OK;  // zero right-hand side, or the refinement has converged
+  const double bnorm = std::sqrt(hs[SC_BB]), tol = hs[SC_TOL];
+  const int cap = std::min(maxit, (int)hs[SC_MAXIT]);
+  T* V = (T*)c->gm_basis;
+  T* Z = V + (size_t)(m + 1) * n;
+  const T* b = (const T*)B.f[K_B];
+  T* r = (T*)B.f[K_R];
+  T* x = (T*)B.f[K_X];
+  T* pd = (T*)B.f[K_PD];
+  const T* q = (const T*)B.f[K_Q];
+  const T* dinv = (const T*)B.f[W_DINV];
+  const T* psi = (const T*)B.f[W_PSI];
+  const int every = c->prm.learned_every;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  double d[kGmPart], e[kGmPart];
+  GmCoef co{};
+  int it = 0, rc = FE_OK;
+  double res = bnorm;
+  bool conv = false;
+  while (true) {
+    gm_dots<T>(V, n, 0, r, c->gm_part, nb, st);  // ||r||^2
+    if ((rc = gm_sums(c, kGmPart, d)) != FE_OK) return rc;
+    const double beta = std::sqrt(d[kGmMax + 1]);
+    if (!(beta > tol * bnorm)) {  // the restart's true residual already meets the tolerance
+      res = beta;
+      conv = true;
+      break;
+    }
+    gm_combine<T>(V, r, 1.0 / beta, nullptr, n, 0, co, nb, st);  // v_0 = r / beta
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (size_t)j * n;
+      T* vn = V + (size_t)(j + 1) * n;
+      // Arnoldi column of the direction in pd: q = M z, w = q - V h twice
+      // (classical Gram-Schmidt with one reorthogonalisation) into vn,
+      // col[j + 1] = ||w||, col[0..j] = h after the previous rotations
+      double col[kGmMax + 2], qn = 0.0;
+      auto column = [&]() -> int {
+        launch_cg_matvec<T>(L);
+        gm_dots<T>(V, n, j + 1, q, c->gm_part, nb, st);
+        int e1 = gm_sums(c, kGmPart, d);
+        if (e1 != FE_OK) return e1;
+        qn = std::sqrt(d[kGmMax + 1]);
+        for (int i = 0; i <= j; ++i) co.h[i] = -d[i];
+        gm_combine<T>(vn, q, 1.0, V, n, j + 1, co, nb, st);
+        gm_dots<T>(V, n, j + 1, vn, c->gm_part, nb, st);
+        if ((e1 = gm_sums(c, kGmPart, e)) != FE_OK) return e1;
+        for (int i = 0; i <= j; ++i) {
+          co.h[i] = -e[i];
+          col[i] = d[i] + e[i];
+        }
+        gm_combine<T>(vn, vn, 1.0, V, n, j + 1, co, nb, st);
+        gm_dots<T>(V, n, 0, vn, c->gm_part, nb, st);
+        if ((e1 = gm_sums(c, kGmPart, d)) != FE_OK) return e1;
+        col[j + 1] = std::sqrt(d[kGmMax + 1]);
+        for (int i = 0; i < j; ++i) {
+          const double a0 = col[i], a1 = col[i + 1];
+          col[i] = cs[i] * a0 + sn[i] * a1;
+          col[i + 1] = -sn[i] * a0 + cs[i] * a1;
+        }
+        return FE_OK;
+      };
+      // the network's direction for v_j, kept if finite and non-zero, if its
+      // image is not (to kGmNetFresh of its norm) in the span of the basis (a
+      // singular Hessenberg matrix would fake convergence), and if it shrinks
+      // the least-squares residual to at most kGmNetKeep of its value;
+      // otherwise (or without a network) the Jacobi direction
+      bool have = false;
+      if (c->unet_ready && (every > 0 ? it % every == 0 : it == 0)) {
+        gm_set_scalar(B.sc, SC_PR, 1.0, st);  // ||v_j||^2: the network input is v_j / rms(v_j)
+        FE_LAUNCH(L, KID_UNET, (unet_apply_sc<T>(c->unet, vj, psi, B.sc, SC_PR, st)));
+        gm_from_net<T>(pd, unet_output(c->unet), n, c->gm_part, nb, st);
+        double zz = 0.0;
+        if ((rc = gm_sums(c, 1, &zz)) != FE_OK) return rc;
+        if (std::isfinite(zz) && zz > 0.0) {
+          if ((rc = column()) != FE_OK) return rc;
+          const double hyp = std::hypot(col[j], col[j + 1]);
+          have = std::isfinite(hyp) && hyp > kGmNetFresh * qn && std::fabs(col[j + 1] / hyp) <= kGmNetKeep;
+        }
+      }
+      if (!have) {
+        gm_jacobi<T>(pd, vj, dinv, n, nb, st);
+        if ((rc = column()) != FE_OK) return rc;
+      }
+      CK(cudaMemcpyAsync(Z + (size_t)j * n, pd, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      const double hn = col[j + 1];
+      if (hn > 0.0) gm_combine<T>(vn, vn, 1.0 / hn, nullptr, n, 0, co, nb, st);
+      for (int i = 0; i <= j + 1; ++i) Hij(i, j) = col[i];
+      // the rotation that zeroes H(j+1, j)
+      const double a0 = Hij(j, j), a1 = Hij(j + 1, j), hyp = std::hypot(a0, a1);
+      cs[j] = a1 == 0.0 ? 1.0 : a0 / hyp;
+      sn[j] = a1 == 0.0 ? 0.0 : a1 / hyp;
+      Hij(j, j) = cs[j] * a0 + sn[j] * a1;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      k = j + 1;
+      res = std::fabs(g[j + 1]);
+      if (res <= tol * bnorm) {
+        conv = true;
+        stop = true;
+        break;
+      }
+      if (it >= cap || !(hn > 0.0)) {
+        stop = true;
+        break;
+      }
+    }
+    // y from the rotated upper triangle; x += Z y
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+      y[i] = Hij(i, i) != 0.0 ? t / Hij(i, i) : 0.0;
+    }
+    for (int i = 0; i < k; ++i) co.h[i] = y[i];
+    gm_combine<T>(x, x, 1.0, Z, n, k, co, nb, st);
+    if (stop) break;
+    // restart from the true residual r = b - M x
+    CK(cudaMemcpyAsync(pd, x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    launch_cg_matvec<T>(L);
+    co.h[0] = -1.0;
+    gm_combine<T>(r, b, 1.0, q, n, 1, co, nb, st);
+  }
+  gm_finish(B.sc, c->dactive, (double)it, res * res, conv ? 1 : 0, st);
+  CK(cudaGetLastError());
+  return FE_OK;
+}
+
 template <typename T>
 static int inner_solve(fe_ctx* c, int maxit, int key) {
   if (c->prm.solver == FE_FCG_LEARNED) {
     if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
     return fcg_learned<T>(c, maxit);
   }
+  if (c->prm.solver == FE_FGMRES_LEARNED) return fgmres_learned<T>(c, maxit);
   return krylov<T>(c, maxit, key);
 }
 
@@ -864,6 +1049,7 @@ static int build_graph(fe_ctx* c, int s) {
 static bool graph_ok(const fe_ctx* c) {
   if (!c->use_graphs || c->harvest_b || c->prof.on) return false;
   if (c->prm.solver == FE_FCG_LEARNED && (!c->unet_ready || c->prm.learned_every > 1)) return false;
+  if (c->prm.solver == FE_FGMRES_LEARNED) return false;  // host-driven: the Arnoldi step reads its dots
   return true;
 }
 
@@ -1275,7 +1461,7 @@ extern "C" int fe_precond_train_step(fe_ctx* c, int box, const void* r, const vo
 extern "C" int fe_harvest_pressure(fe_ctx* c, void* const* b_out, void* const* x_out, int max_pairs, int* npairs) {
   if (!c || !b_out || !x_out || max_pairs < 1 || !npairs) return FE_ERR_INVALID_ARG;
   const int solver = c->prm.solver;
-  c->prm.solver = FE_PCG_JACOBI;
+  c->prm.solver = c->prm.transonic ? FE_BICGSTAB_JACOBI : FE_PCG_JACOBI;
   c->harvest_b = b_out;
   c->harvest_x = x_out;
   c->harvest_max = max_pairs;

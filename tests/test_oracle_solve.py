@@ -179,7 +179,7 @@ def test_fgmres_minimises_residual_over_its_directions(k):
         seen.append(z)
         return z
 
-    x, it, rec, true = krylov.fgmres(matvec, b, prec, diag, 0.0, k, m=20)
+    x, it, rec, true = krylov.fgmres(matvec, b, prec, diag, 0.0, k, m=20, keep=1.0)
     assert it == k and len(seen) == k
     xs = _min_residual_over(matvec, b, seen)
     assert np.max(np.abs(x - xs)) < 1e-9 * np.max(np.abs(xs))
@@ -220,3 +220,24 @@ def test_fgmres_restarts_and_falls_back():
     assert np.max(np.abs(x - x0)) < 1e-10 * np.max(np.abs(x0))
     z, it0, _, _ = krylov.fgmres(matvec, np.zeros_like(b), None, diag, 1e-12, 10)
     assert it0 == 0 and not np.any(z)
+
+
+def test_fgmres_replaces_directions_that_make_no_progress():
+    """Directions that add nothing are replaced by Jacobi's: one fixed vector
+    returned every time (degenerate after its first use: its image is already
+    in the basis), and fresh random vectors (non-degenerate but nearly
+    useless).  Both solves converge in about the Jacobi-only iteration count;
+    without the progress rule the random directions stall."""
+    matvec, diag, b = _transonic_system(8, 0.2, 10)
+    fixed = np.random.default_rng(11).standard_normal(b.shape)
+    _, it_j, _, _ = krylov.fgmres(matvec, b, None, diag, 1e-12, 500, m=20)
+    x, it, rec, true = krylov.fgmres(matvec, b, lambda v, k: fixed, diag, 1e-12, 500, m=20)
+    assert true < 1e-12 * 1.01 and abs(rec - true) < 1e-12
+    assert it <= it_j + 2
+    rnd = np.random.default_rng(12)
+    x, it, rec, true = krylov.fgmres(matvec, b, lambda v, k: rnd.standard_normal(v.shape), diag, 1e-12, 500, m=20)
+    assert true < 1e-12 * 1.01 and it <= it_j + 4
+    rnd = np.random.default_rng(12)
+    _, it_s, rec_s, _ = krylov.fgmres(matvec, b, lambda v, k: rnd.standard_normal(v.shape), diag, 1e-12, 60,
+                                      m=20, keep=1.0)
+    assert it_s == 60 and rec_s > 1e-6
