@@ -92,3 +92,32 @@ def test_null_arguments(lib):
     assert lib.fe_step(None, 1, None) == fe.FE_ERR_INVALID_ARG
     assert lib.fe_init_state(None, 0, 0) == fe.FE_ERR_INVALID_ARG
     lib.fe_destroy(None)
+
+
+@pytest.mark.parametrize("solver", ["FE_FCG_LEARNED", "FE_FGMRES_LEARNED"])
+def test_learned_solvers_need_one_box_with_n_divisible_by_four(lib, solver):
+    """The U-Net halves the grid twice, so the learned solvers take one box
+    with N % 4 == 0; other grids are refused before any CUDA call."""
+    from paper_1404_0959_gb300 import fe
+    p, keep = _params(N=18, solver=getattr(fe, solver))
+    ctx = ctypes.c_void_p()
+    assert lib.fe_create(ctypes.byref(p), None, ctypes.byref(ctx)) == fe.FE_ERR_UNSUPPORTED
+    assert not ctx.value
+
+
+def test_fgmres_accepts_the_transonic_operator_and_fcg_does_not(lib):
+    """Flexible CG needs a symmetric operator; flexible GMRES does not.  The
+    FCG refusal comes from validation (no CUDA call); the FGMRES parameters
+    pass validation, so on a machine without a GPU fe_create fails later, at
+    its first CUDA call, with FE_ERR_CUDA rather than a parameter error."""
+    import torch
+    from paper_1404_0959_gb300 import fe
+    p, keep = _params(N=16, solver=fe.FE_FCG_LEARNED, transonic=1)
+    ctx = ctypes.c_void_p()
+    assert lib.fe_create(ctypes.byref(p), None, ctypes.byref(ctx)) == fe.FE_ERR_UNSUPPORTED
+    if torch.cuda.is_available():
+        pytest.skip("the no-GPU branch of this check needs a machine without a GPU")
+    p, keep = _params(N=16, solver=fe.FE_FGMRES_LEARNED, transonic=1)
+    rc = lib.fe_create(ctypes.byref(p), None, ctypes.byref(ctx))
+    assert rc not in (fe.FE_ERR_INVALID_ARG, fe.FE_ERR_UNSUPPORTED, fe.FE_OK)
+    assert not ctx.value
