@@ -26,7 +26,7 @@ here is this project's reading of those passages.  Modules:
 ``ops``     fourth-order face interpolation and the face/cell stencils
 ``ic``      SplitMix64 counter RNG, Box-Muller, spectral solenoidal field
 ``piso``    one PISO step (predictor, two correctors, closures, dust)
-``krylov``  Jacobi-PCG, Jacobi-BiCGStab, flexible CG
+``krylov``  Jacobi-PCG, Jacobi-BiCGStab, flexible CG, flexible GMRES
 ``diag``    kinetic energy, enstrophy, Taylor microscale, spectrum, totals
 ``unet``    FP64 3D-conv U-Net forward/backward (learned preconditioner)
 
