@@ -161,7 +161,9 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
     plan.push_back({W_YW0 + j, e});
     plan.push_back({W_YW1 + j, e});
   }
-  if (c->prm.solver == FE_BICGSTAB_JACOBI)
+  // BiCGStab vectors: its own solver, and the harvest of a transonic flexible-GMRES context (which
+  // generates its training pairs with BiCGStab)
+  if (c->prm.solver == FE_BICGSTAB_JACOBI || (c->prm.solver == FE_FGMRES_LEARNED && c->prm.transonic))
     for (int s : {K_RHAT, K_V, K_S, K_T}) plan.push_back({s, e});
   // second CG direction buffer (the learned solver's harvest runs plain CG)
   if (c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_PP, e});
@@ -1461,7 +1463,9 @@ extern "C" int fe_precond_train_step(fe_ctx* c, int box, const void* r, const vo
 extern "C" int fe_harvest_pressure(fe_ctx* c, void* const* b_out, void* const* x_out, int max_pairs, int* npairs) {
   if (!c || !b_out || !x_out || max_pairs < 1 || !npairs) return FE_ERR_INVALID_ARG;
   const int solver = c->prm.solver;
-  c->prm.solver = c->prm.transonic ? FE_BICGSTAB_JACOBI : FE_PCG_JACOBI;
+  const int plain = c->prm.transonic ? FE_BICGSTAB_JACOBI : FE_PCG_JACOBI;
+  if (plain == FE_BICGSTAB_JACOBI && !c->hbox[0].f[K_RHAT]) return FE_ERR_UNSUPPORTED;  // no BiCGStab vectors
+  c->prm.solver = plain;
   c->harvest_b = b_out;
   c->harvest_x = x_out;
   c->harvest_max = max_pairs;
