@@ -76,6 +76,11 @@ def _L_advective(u, phi, mu, h):
     return out
 
 
+def _energy_no_viscous_work(prm, phi, u, rho, p, E, T):
+    H = E + p / rho
+    return [phi[d] * ops.I4(H, d) - prm.kappa * ops.G4(T, d, prm.h) for d in range(3)]
+
+
 def _givens_transposed(a, b):
     if b == 0.0:
         return 1.0, 0.0
@@ -112,6 +117,8 @@ CASES = [
      lambda: t_piso.test_psi_is_inverse_isentropic_sound_speed_squared(piso.FOURIER)),
     ("Du/Dt pressure sign", piso, "accel", _accel_wrong_sign,
      lambda: t_piso.test_dust_drift_pressure_closed_form()),
+    ("energy flux without viscous work", piso, "energy_flux", _energy_no_viscous_work,
+     lambda: t_piso.test_viscous_heating_pattern()),
     ("enthalpy flux without p/rho", piso, "energy_flux", _energy_no_pressure_work,
      lambda: t_piso.test_isobaric_heat_conduction_rate()),
 ]

@@ -314,3 +314,26 @@ def test_single_corrector_momentum_identity(closure, transonic):
         got = np.sum(rho0 * new["u"][m])
         want = np.sum(st["rho"] * st["u"][m])
         assert abs(got - want) <= 1e-13 * np.sum(np.abs(st["rho"] * st["u"][m]))
+
+
+def _viscous_heating_ratio(N, eps=1e-2, nu=0.05, dt=1e-3):
+    x, y, z, h = grid(N)
+    prm = piso.Params(N=N, closure=piso.FOURIER, nu=nu, tau_p=[0.0], Y0=[0.0], dt_max=dt)
+    st = piso.make_state(prm, np.ones_like(x), [eps * np.sin(y), 0 * x, 0 * x], [0 * x], np.ones_like(x))
+    new, _info = piso.step(prm, st, dt=dt)
+    e = new["rho"] * prm.cv * (new["T"] - 1.0)  # internal energy gained
+    c2 = np.sum(e * np.cos(2 * y)) / np.sum(np.cos(2 * y) ** 2)
+    return c2 / (0.5 * nu * eps ** 2 * dt)
+
+
+def test_viscous_heating_pattern():
+    """Fourier closure: a shear wave u_x = eps sin y heats the gas where it
+    dissipates, at mu (du_x/dy)^2 = mu eps^2 cos^2 y = (mu eps^2 / 2)(1 + cos 2y)
+    per unit volume and time.  The cos 2y part of the internal energy gained
+    in a short step matches mu eps^2 dt / 2, converging at second order.  An
+    energy flux without the viscous work -tau.u would put the heat where the
+    kinetic energy was lost instead, (mu eps^2 / 2)(1 - cos 2y): the opposite
+    sign of this coefficient."""
+    r8, r16 = _viscous_heating_ratio(8), _viscous_heating_ratio(16)
+    assert abs(r16 - 1) < 0.06
+    assert 3.5 < abs(r8 - 1) / abs(r16 - 1) < 4.5
