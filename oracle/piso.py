@@ -60,7 +60,8 @@ discrete and the analytic rate; exact conservation of mass, dust mass and
 total energy; uniform state stays uniform; tau_p = 0 passive tracer; first
 order response in tau_p; closed-form initial dust drift for a pressure and
 for a dilatational velocity perturbation; isobaric heat-conduction decay;
-viscous heating of a shear wave where it dissipates (Fourier);
+viscous heating of a shear wave where it dissipates (Fourier); passive dust
+advection at second order in time;
 acoustic wave speed c = 1; psi c^2 = 1 with c^2 the isentropic derivative of
 the closure's EOS; the adaptive step's Courant number, growth limit and cap;
 with one corrector, sum rho^0 u^{n+1} = sum rho^n u^n exactly.
