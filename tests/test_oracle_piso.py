@@ -363,3 +363,24 @@ def test_dust_advection_second_order_in_time():
     e1, e2 = _advected_dust_error(16, 0.1), _advected_dust_error(16, 0.05)
     assert e1 < 5e-4
     assert 3.5 < e1 / e2 < 4.5
+
+
+@pytest.mark.parametrize("closure", [piso.BAROTROPIC, piso.FOURIER])
+def test_totals_closed_form(closure):
+    """a9 totals are volume integrals over the (2 pi)^3 box: a uniform state
+    rho, u, Y, T has mass rho (2 pi)^3, dust mass rho Y (2 pi)^3 and energy
+    (rho c_v T [Fourier] + rho |u|^2 / 2)(2 pi)^3."""
+    N = 8
+    prm = piso.Params(N=N, closure=closure, tau_p=[0.05, 0.2], Y0=[0.01, 0.03])
+    ones = np.ones((N, N, N))
+    rho, u, Y, T = 1.3, (0.2, -0.1, 0.05), (0.01, 0.03), 1.1
+    st = piso.make_state(prm, rho * ones, [c * ones for c in u], [y * ones for y in Y],
+                         T * ones if closure == piso.FOURIER else None)
+    tot = piso.totals(prm, st)
+    vol = (2 * math.pi) ** 3
+    ke = 0.5 * rho * sum(c * c for c in u)
+    assert abs(tot["mass"] - rho * vol) <= 1e-13 * rho * vol
+    for j in range(2):
+        assert abs(tot["dust"][j] - rho * Y[j] * vol) <= 1e-13 * rho * Y[j] * vol
+    e = (rho * prm.cv * T + ke if closure == piso.FOURIER else ke) * vol
+    assert abs(tot["energy"] - e) <= 1e-13 * e
