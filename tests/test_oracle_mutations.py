@@ -183,3 +183,31 @@ def test_solver_pin_catches_wrong_laplacian(monkeypatch):
     monkeypatch.setattr(piso, "helmholtz", helm_bad)
     with pytest.raises(AssertionError):
         t_solve.test_pcg_uniform_psi_matches_fourier()
+
+
+def test_rng_pin_catches_wrong_mixer_shift(monkeypatch):
+    from oracle import ic
+
+    from . import test_oracle_ic as t_ic
+
+    def bad(seed, m):
+        m = np.asarray(m, dtype=np.uint64)
+        z = np.uint64(seed) + (m + np.uint64(1)) * ic.GOLDEN
+        z = (z ^ (z >> np.uint64(31))) * ic.MIX1   # 30 in the published mixer
+        z = (z ^ (z >> np.uint64(27))) * ic.MIX2
+        return z ^ (z >> np.uint64(31))
+
+    monkeypatch.setattr(ic, "splitmix64", bad)
+    t_ic.test_uniform_moments()  # the statistical pins still pass
+    with pytest.raises(AssertionError):
+        t_ic.test_splitmix64_published_outputs()
+
+
+def test_rng_pin_catches_zero_based_counter(monkeypatch):
+    from oracle import ic
+
+    from . import test_oracle_ic as t_ic
+    orig = ic.splitmix64
+    monkeypatch.setattr(ic, "splitmix64", lambda seed, m: orig(seed, np.asarray(m, dtype=np.uint64) - np.uint64(1)))
+    with pytest.raises(AssertionError):
+        t_ic.test_splitmix64_published_outputs()
