@@ -164,6 +164,46 @@ def oracle_sample(N, steps, cfg):
     return time.perf_counter() - t0
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+def _oracle_worker(args):
+    N, cfg = args
+    return oracle_sample(N, 1, cfg)
+
+
+def oracle_all_cores(N, cfg, procs):
+    """Wall time of `procs` independent one-step oracle samples run at once in
+    spawned processes (one per core): the oracle as it stands, replicated."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [(8, cfg)] * procs)  # start-up (imports) outside the timed region
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, [(N, cfg)] * procs)
+        return time.perf_counter() - t0
+
+
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
@@ -175,12 +215,15 @@ def run_reference(args, cfg, rank):
             times.append(t)
     total = sum(times)
     value = N ** 3 * len(times) / total
+    cpu = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample_N": N},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: one oracle PISO step of the %s physics on a %d^3 box" % (WORKLOAD, N)},
+                             "cpu_model": cpu["model"], "nproc": cpu["nproc"],
+                             "sample": "each step: one oracle PISO step of the %s physics on a %d^3 box "
+                                       "(single-threaded numpy)" % (WORKLOAD, N)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -273,7 +316,8 @@ def ensemble_only(args):
     t_one = sum(timed([b]) for b in boxes)
     line = {"metric": "cell-steps/s, 64-box ensemble of uneven boxes (one context vs one context per box)",
             "value": cells * K / t_ens, "unit": "cell-steps/s", "n_gpus": 1, "steps": K, "warmup": W,
-            "ms_per_step": 1e3 * t_ens / K, "higher_is_better": True, "dtype": "f32 fields, f64 reductions",
+            "ms_per_step": 1e3 * t_ens / K, "higher_is_better": True,
+            "dtype": "f32 fields, FP64-class float-pair reductions and refinement",
             "data": "synthetic spectral HIT boxes (seed = box index), no dataset",
             "config": {"workload": "ensemble64", "boxes": len(boxes), "cells": int(cells), "p_tol": 1e-8,
                        "cuda_graphs": True},
@@ -324,6 +368,7 @@ def main():
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--cpu-procs", type=int, default=16, help="oracle processes of the all-cores CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default=None, help="kernel timed live for the roofline (default: largest share)")
@@ -496,16 +541,23 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        host = host_cpu()
         tc = oracle_sample(args.cpu_n, 1, cfg)
-        cpu = {"value": args.cpu_n ** 3 / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one FP64 oracle PISO step of the %s physics on a %d^3 box (spectral IC, same seed)"
-                         % (WORKLOAD, args.cpu_n)}
+        procs = max(1, min(host["nproc"] or 1, args.cpu_procs))
+        tp = oracle_all_cores(args.cpu_n, cfg, procs) if procs > 1 else tc
+        cpu = {"value": procs * args.cpu_n ** 3 / tp, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "cpu_model": host["model"], "nproc": host["nproc"],
+               "sample": "%d independent one-step FP64 oracle runs of the %s physics on %d^3 boxes (spectral IC, "
+                         "same seed), one spawned single-threaded process per core, run at once"
+                         % (procs, WORKLOAD, args.cpu_n),
+               "single_core": {"value": args.cpu_n ** 3 / tc, "unit": UNIT, "cores": 1,
+                               "sample": "one oracle step on a %d^3 box in this process" % args.cpu_n}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if w == 8 else "f32 fields, f64 reductions",
+                "dtype": "f64" if w == 8 else "f32 fields, FP64-class float-pair reductions and refinement",
                 "data": "synthetic spectral HIT field (seed per rank), no dataset",
                 "config": {"workload": WORKLOAD, "N": N, "closure": "barotropic", "mach_rms": cfg["mach_rms"],
                            "k0": cfg["k0"], "nu": cfg["nu"], "tau_p": cfg["tau_p"], "Y0": cfg["Y0"],

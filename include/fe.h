@@ -339,13 +339,18 @@ const char* fe_kernel_name(int kernel_id);
  * cudaStream_t or NULL.  No context is needed and nothing is allocated: the
  * Krylov vectors and reduction scratch live in one static device array of
  * about 6.3 MB per device (sized for N = 64), held from library load until
- * process exit.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) and caches it, so make that first call
- * before capturing a stream.  All calls on a device share the array and it
- * keeps the previous call's contents (each call clears its counters and
- * flags); calls that overlap on the GPU race with each other.  Returns
- * FE_ERR_TOO_LARGE for N > FE_NOALLOC_MAX_N, FE_ERR_NOT_CONVERGED if maxit
- * was reached, FE_ERR_INVALID_ARG for other bad arguments. */
+ * process exit.  The entry point looks up that array's device address
+ * (cudaGetSymbolAddress) in the current CUDA context and caches it per
+ * context.  The solve is host-polled: it reads the convergence flag back
+ * every four iterations and synchronises the stream, so it cannot be
+ * recorded into a CUDA graph; on a stream that is being captured it returns
+ * FE_ERR_UNSUPPORTED before enqueueing anything.  All calls on a device
+ * share the array and it keeps the previous call's contents (each call
+ * clears its counters and flags); calls that overlap on the GPU race with
+ * each other.  A launch error left by earlier unrelated work is cleared on
+ * entry and not reported by this call.  Returns FE_ERR_TOO_LARGE for
+ * N > FE_NOALLOC_MAX_N, FE_ERR_NOT_CONVERGED if maxit was reached,
+ * FE_ERR_INVALID_ARG for other bad arguments. */
 #define FE_NOALLOC_MAX_N 64
 int fe_solve_pressure_noalloc(int N, const double* psi, const double* b, double* x, double dt, double tol,
                               int maxit, void* stream, fe_solve_info* info);

@@ -17,10 +17,16 @@
 // array and race; serialise them.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// names a host-side stand-in), so the first call on each device looks up the
-// device address with cudaGetSymbolAddress while that device is current and
-// caches it.  That first call must therefore happen before any stream
-// capture that wants to record this entry point.
+// names a host-side stand-in), so the entry point looks up the device address
+// with cudaGetSymbolAddress while the caller's device is current and caches
+// it per CUDA context: a context that is destroyed and created again (after
+// cudaDeviceReset, for instance) loads the module afresh, and its address is
+// looked up again.
+//
+// The solve is driven from the host: it reads the convergence flag back
+// every few iterations and waits for the stream, so it cannot be recorded
+// into a CUDA graph.  A call on a stream that is being captured returns
+// FE_ERR_UNSUPPORTED before it enqueues anything.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -204,20 +210,62 @@ __global__ void __launch_bounds__(NTHR) na_true_res(BoxDev B) {
   }
 }
 
-// per-device cache of the scratch array's device address
+// Cache of the scratch array's device address, keyed by (device, context id).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+struct NaSlot {
+  int dev;
+  unsigned long long ctx;
+  double* ptr;
+};
 static std::mutex g_na_mutex;
-static double* g_na_ptr[64] = {};
+static NaSlot g_na_cache[16];
+static int g_na_used = 0;
+
+// Unique id of the context current on this thread (0 if it cannot be told).
+static unsigned long long na_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_cur = (CtxGetCurrentFn)f1;
+      get_id = (CtxGetIdFn)f2;
+    }
+  }
+  if (!get_cur || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 static int na_scratch(double** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FE_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return FE_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, fe_noalloc_scratch) != cudaSuccess || !p) return FE_ERR_CUDA;
-    g_na_ptr[dev] = (double*)p;
+  const unsigned long long ctx = na_context_id();
+  if (ctx != 0)
+    for (int q = 0; q < g_na_used; ++q)
+      if (g_na_cache[q].dev == dev && g_na_cache[q].ctx == ctx) {
+        *out = g_na_cache[q].ptr;
+        return FE_OK;
+      }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, fe_noalloc_scratch) != cudaSuccess || !p) return FE_ERR_CUDA;
+  if (ctx != 0) {  // without a context id the address is looked up on every call
+    const int q = g_na_used < 16 ? g_na_used++ : (int)(ctx % 16);
+    g_na_cache[q] = NaSlot{dev, ctx, (double*)p};
   }
-  *out = g_na_ptr[dev];
+  *out = (double*)p;
   return FE_OK;
 }
 
@@ -229,10 +277,15 @@ extern "C" int fe_solve_pressure_noalloc(int N, const double* psi, const double*
                                          int maxit, void* stream, fe_solve_info* info) {
   if (N > FE_NOALLOC_MAX_N) return FE_ERR_TOO_LARGE;
   if (N < 8 || !psi || !b || !x || !(dt > 0.0) || !(tol > 0.0) || maxit < 1) return FE_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // a stale launch error left by earlier, unrelated work is not this call's
+  (void)cudaGetLastError();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return FE_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return FE_ERR_UNSUPPORTED;  // host-polled: cannot be captured
   double* base = nullptr;
   int rc = na_scratch(&base);
   if (rc != FE_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   BoxDev B;
   memset(&B, 0, sizeof(B));
   B.N = N;
@@ -259,6 +312,7 @@ extern "C" int fe_solve_pressure_noalloc(int N, const double* psi, const double*
   if (cudaMemcpyAsync(B.sc + SC_TOL, hs, sizeof(hs), cudaMemcpyHostToDevice, st) != cudaSuccess) return FE_ERR_CUDA;
   const dim3 blk(TX, TY);
   na_init<<<B.ntiles, blk, 0, st>>>(B);
+  if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
   const int poll = 4;
   double done = 0.0;
   for (int it = 0; it < maxit;) {
@@ -271,11 +325,13 @@ extern "C" int fe_solve_pressure_noalloc(int N, const double* psi, const double*
       na_update<<<B.ntiles, blk, 0, st>>>(B);
       na_dir<<<B.ntiles, blk, 0, st>>>(B);
     }
+    if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
   }
   na_true_res<<<B.ntiles, blk, 0, st>>>(B);
+  if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
   double sc[NSC];
   if (cudaMemcpyAsync(sc, B.sc, NSC * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      cudaStreamSynchronize(st) != cudaSuccess)
     return FE_ERR_CUDA;
   if (info) {
     info->iters = (int)sc[SC_ITERS];
