@@ -512,16 +512,18 @@ static int krylov(fe_ctx* c, int maxit, int key) {
   int nsnap = 0, snap_slot[2] = {-1, -1};
   if (snap) batch = 1;
   while (true) {
+    if (it > 0 || batch == 1) {
+      CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (*c->hactive == 0 || it >= maxit) break;
+    }
+    // snapshots only of a solve that is still running: the iterate at which the
+    // solve stops is x* itself and would give the degenerate pair (r*, 0)
     if (snap && nsnap < 2 && it == snap_at[nsnap] && c->harvest_n < c->harvest_max) {
       const size_t bytes = (size_t)c->hbox[0].N * c->hbox[0].N * c->hbox[0].N * sizeof(T);
       CK(cudaMemcpyAsync(c->harvest_b[c->harvest_n], c->hbox[0].f[K_R], bytes, cudaMemcpyDeviceToDevice, c->st));
       CK(cudaMemcpyAsync(c->harvest_x[c->harvest_n], c->hbox[0].f[K_X], bytes, cudaMemcpyDeviceToDevice, c->st));
       snap_slot[nsnap++] = c->harvest_n++;
-    }
-    if (it > 0 || batch == 1) {
-      CK(cudaMemcpyAsync(c->hactive, c->dactive, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      if (*c->hactive == 0 || it >= maxit) break;
     }
     const int n = it == 0 ? batch : 1;
     for (int q = 0; q < n && it < maxit; ++q, ++it) {

@@ -151,7 +151,7 @@ def check_layer(name, P, acts, out, N, nsample, rng):
 
 def test_every_layer_at_128_matches_the_oracle_convolution(fe):
     N = 128
-    P, acts, out, r, psi = network_run(fe, N, 3, set(range(10)))
+    P, acts, out, r, psi = network_run(fe, N, 3, set(range(8)) | {9})
     # the packed input: BF16 of r / rms(r) and psi - 1
     rms = np.sqrt(np.mean(f32(r) ** 2))
     assert rel(acts[9][..., 0], bf16(f32(r) / rms)) < 1e-5
@@ -165,7 +165,7 @@ def test_half_grid_tensor_memory_layers_at_256_match_the_oracle_convolution(fe):
     """At 256^3 the half-grid layers e2 (from d1) and u2 (from up2(e3) and e2)
     also have 128-cell output grids and run on tcgen05."""
     N = 256
-    P, acts, out, r, psi = network_run(fe, N, 5, {2, 3, 5, 6})
+    P, acts, out, r, psi = network_run(fe, N, 5, {2, 3, 4, 5, 6})
     rng = np.random.default_rng(256)
     errs = {name: check_layer(name, P, acts, out, N, 4096, rng) for name in ("e2", "u2", "e3")}
     print("N=256 relative L2 vs the oracle convolution:", {k: "%.2e" % v for k, v in errs.items()})
