@@ -336,17 +336,17 @@ def unet_only(args):
     box = dict(N=N, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], mach_rms=w["mach_rms"], k0=w["k0"], seed=0)
     s = fe.Solver([box], precision=fe.FE_FP32_MIXED, solver=fe.FE_FCG_LEARNED, p_tol=1e-8)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
-    fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
+    fe.fe_load_preconditioner(s.ctx, learned.he_init(0, zero_last=False))
     g = torch.Generator(device="cuda").manual_seed(0)
     r = torch.randn(N, N, N, device="cuda", generator=g)
     z = torch.empty_like(r)
     for _ in range(args.warmup):
-        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), z.data_ptr())
+        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), 0.01, z.data_ptr())
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), z.data_ptr())
+        fe.fe_precond_apply(s.ctx, 0, r.data_ptr(), 0.01, z.data_ptr())
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps

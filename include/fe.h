@@ -113,8 +113,10 @@ typedef struct {
     int32_t transonic;          /* 1: add the psi-convection term (non-symmetric) */
     int32_t learned_every;      /* FE_FCG_LEARNED, FE_FGMRES_LEARNED: network direction at
                                  * iterations it with it % learned_every == 0 (1 = every
-                                 * iteration), Jacobi direction otherwise; 0 = first
-                                 * iteration only */
+                                 * iteration), Jacobi direction otherwise; 0 = the first
+                                 * direction of each corrector's solve only (mixed
+                                 * precision: of its first refinement solve; such steps
+                                 * are host-driven, not CUDA graphs) */
 } fe_params;
 
 typedef struct {
@@ -225,17 +227,23 @@ int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
 /* Learned preconditioner (extension of the paper's pressure solve, Sec. 2
  * par. 1): a 3-level 3D-conv U-Net (16/32/64 channels, 3x3x3 kernels,
  * periodic padding, ReLU; BF16 weights and activations, FP32 accumulation on
- * the tensor cores) maps the residual r to a search direction of flexible CG
- * (solver FE_FCG_LEARNED; one box, N divisible by 4).  When <z, r> <= 0 the
- * Jacobi direction is used instead, so plain preconditioned CG remains the
- * fallback.  With FE_FGMRES_LEARNED the network maps each unit Arnoldi
- * vector v_j to the direction z_j of flexible GMRES(20) (right
+ * the tensor cores) that corrects the Jacobi direction of flexible CG
+ * (solver FE_FCG_LEARNED; one box, N divisible by 4).  For a residual r of
+ * the operator M = diag(psi/dt) - dt/2 D(G2 .), whose Jacobi diagonal is
+ * d = psi/dt + 3 dt/h^2, with rms(r) = sqrt(mean r^2) and d0 = 1/(1/dt +
+ * 3 dt/h^2) (d at psi = 1):
+ *     input channel 0 = (r/d) / (rms(r) d0),  channel 1 = (3 dt/h^2) / d,
+ *     direction z = r/d + rms(r) d0 y,  y = network(input).
+ * A network whose last layer is zero gives exactly the Jacobi direction.
+ * When <z, r> <= 0 the Jacobi direction is used instead, so plain
+ * preconditioned CG remains the fallback.  With FE_FGMRES_LEARNED the same
+ * direction is formed for each unit Arnoldi vector v_j (right
  * preconditioning, M Z_k = V_{k+1} H_k; x minimises ||b - M x|| over the
  * span of Z_k), which needs no symmetry and so also serves the transonic
  * operator; a network direction that is not finite, is zero, has an image
  * already in the span of the basis (new component below 1e-5 of its norm),
  * or shrinks the least-squares residual by less than 10 % is replaced by the
- * Jacobi direction, and without a loaded network every direction is Jacobi's.  Network input: channel 0 = r / rms(r), channel 1 = psi - 1.
+ * Jacobi direction, and without a loaded network every direction is Jacobi's.
  * Layers, in parameter order: e1a 2->16, e1b 16->16, d1 16->32 (stride 2),
  * e2 32->32, d2 32->64 (stride 2), e3 64->64, u2 [up2(e3), e2] 96->32,
  * u1 [up2(u2), e1b] 48->16, out 16->1 (linear).  Parameter layout (FP32,
@@ -246,25 +254,32 @@ long fe_preconditioner_size(void);   /* number of floats of the layout above */
 int fe_load_preconditioner(fe_ctx* ctx, const float* weights, size_t count);
 /* Copy the weights (gradients = 0) or the last training step's gradients (1) out. */
 int fe_get_preconditioner(fe_ctx* ctx, float* out, size_t count, int gradients);
-/* z (device, N^3 FP32) = network(r) for device r (context precision), psi of the current state. */
-int fe_precond_apply(fe_ctx* ctx, int box, const void* r, float* z);
-/* One training step on a pair (r, e) with M e = r (device arrays, context
- * precision; psi of the current state): input r / rms(r), target e / rms(e),
- * loss ||y - t||^2 / ||t||^2,
- * then Adam (Kingma and Ba 2015) with learning rate lr (lr <= 0: gradients
- * only).  *loss receives the loss before the update. */
-int fe_precond_train_step(fe_ctx* ctx, int box, const void* r, const void* e, double lr, double* loss);
+/* z (device, N^3 FP32) = the direction above for the device residual r
+ * (context precision), the operator with time step dt > 0 and psi of the
+ * current state.  The raw network output y is activation 8. */
+int fe_precond_apply(fe_ctx* ctx, int box, const void* r, double dt, float* z);
+/* One training step on a pair (r, e) with M e = r, M the operator with time
+ * step dt > 0 and psi of the current state (device arrays, context
+ * precision): input as fe_precond_apply, target t = (e - r/d) / (rms(r) d0)
+ * (the part of M^{-1} r the Jacobi direction misses), loss ||y - t||^2 /
+ * ||t||^2, then Adam (Kingma and Ba 2015) with learning rate lr (lr <= 0:
+ * gradients only).  *loss receives the loss before the update.
+ * FE_ERR_INVALID_ARG when r = 0 or e = r/d (nothing to learn). */
+int fe_precond_train_step(fe_ctx* ctx, int box, const void* r, const void* e, double dt, double lr, double* loss);
 /* Activations of the last network pass (inspection): layer 0..7 = e1a, e1b,
  * d1, e2, d2, e3, u2, u1 (after ReLU, channels-last, n_l^3 * C_l floats, n_l
- * = N, N/2 or N/4), 8 = output (N^3 floats), 9 = packed input (N^3 * 16). */
+ * = N, N/2 or N/4), 8 = network output y (N^3 floats), 9 = packed input
+ * (N^3 * 16). */
 int fe_precond_activation(fe_ctx* ctx, int layer, float* out, size_t count);
 /* Advance the context by one step with the plain Jacobi-PCG solver and copy
  * (residual, correction) pairs of box 0 into b_out[i], x_out[i] (device
  * arrays of N^3 values of the context precision), per corrector: the
  * residuals r_k and corrections x* - x_k after Krylov iterations 2 and 5 (when
- * reached), then the right-hand side b with its converged solution x*.
- * *npairs = pairs written (<= max_pairs).  These are the training pairs of
- * this run; fe_precond_train_step uses the psi of the current state. */
+ * the solve is still running there), then the right-hand side b with its
+ * converged solution x*.  *npairs = pairs written (<= max_pairs).  These are
+ * the training pairs of this run; all pairs of one call belong to operators
+ * with the step's dt (fe_diagnostics dt_prev after the call), which
+ * fe_precond_train_step takes, with the psi of the then current state. */
 int fe_harvest_pressure(fe_ctx* ctx, void* const* b_out, void* const* x_out, int max_pairs, int* npairs);
 
 /* Run each step as one CUDA graph (on = 1): the step's kernels plus the

@@ -20,9 +20,27 @@ A stride-2 convolution is the stride-1 convolution sampled at even cells.
 Convolution (definition): y[co](v) = b[co] + sum_{t in {-1,0,1}^3} sum_ci
 W[t, ci, co] x[ci](v + t), periodic.  Arrays: (C, N, N, N), [z, y, x].
 
+Preconditioner (residual form).  The pressure-correction operator of the
+PISO corrector (Sec. 2 par. 1) is M = diag(psi/dt) - dt/2 D(G2 .), whose
+Jacobi diagonal is d = psi/dt + 3 dt/h^2.  For a residual r the network
+corrects the Jacobi direction r/d instead of replacing it:
+
+  rho   = rms(r) = sqrt(mean(r^2));  d0 = 1 / (1/dt + 3 dt/h^2)  (d at psi = 1)
+  input = [ (r/d) / (rho d0),  (3 dt/h^2) / d ]   (second channel in (0, 1):
+          the share of the diagonal that comes from the Laplacian, i.e. six
+          times the Jacobi neighbour weight; it carries dt and psi)
+  z     = r/d + rho d0 net(input)
+
+so that a network whose last layer is zero is exactly Jacobi, and z scales
+with r.  A training pair (r, e) with M e = r has the target
+t = (e - r/d) / (rho d0): the part of M^{-1} r that Jacobi misses, in the
+same units as the network output; loss ||y - t||^2 / ||t||^2.
+
 Parity pins (tests/test_oracle_unet.py): the convolution against a brute
 force loop on a tiny grid; every parameter and input gradient against
-centred finite differences; translation equivariance.
+centred finite differences; translation equivariance; a zero last layer
+gives the Jacobi direction; the direction of the exact correction target
+solves M z = r; direction and input scale with r.
 """
 import numpy as np
 
@@ -152,3 +170,41 @@ def adam_update(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** step)
     vh = v / (1 - b2 ** step)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def jacobi_diag(psi, dt, h):
+    """Diagonal of M = diag(psi/dt) - dt/2 D(G2 .): psi/dt + 3 dt/h^2."""
+    return psi / dt + 3.0 * dt / (h * h)
+
+
+def precond_scales(r, dt, h):
+    """(rho, d0): r.m.s. of r and the Jacobi inverse of the uniform state psi = 1."""
+    rho = float(np.sqrt(np.mean(r * r)))
+    d0 = 1.0 / (1.0 / dt + 3.0 * dt / (h * h))
+    return rho, d0
+
+
+def network_input(r, psi, dt, h):
+    """The two input channels: Jacobi direction r/d over rho d0, and (3 dt/h^2)/d."""
+    d = jacobi_diag(psi, dt, h)
+    rho, d0 = precond_scales(r, dt, h)
+    s = (r / d) / (rho * d0) if rho > 0.0 else np.zeros_like(r)
+    w = (3.0 * dt / (h * h)) / d
+    return np.stack([s, w])
+
+
+def direction(P, r, psi, dt, h):
+    """Preconditioned direction z = r/d + rho d0 net(input) for residual r."""
+    d = jacobi_diag(psi, dt, h)
+    rho, d0 = precond_scales(r, dt, h)
+    if rho == 0.0:
+        return np.zeros_like(r)
+    y, _ = forward(P, network_input(r, psi, dt, h))
+    return r / d + rho * d0 * y[0]
+
+
+def training_target(r, e, psi, dt, h):
+    """Target of the network output for a pair (r, e) with M e = r."""
+    d = jacobi_diag(psi, dt, h)
+    rho, d0 = precond_scales(r, dt, h)
+    return ((e - r / d) / (rho * d0))[None]

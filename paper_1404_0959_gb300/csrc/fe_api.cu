@@ -29,9 +29,10 @@ void unet_destroy(UNet* U);
 long unet_param_count();
 int unet_set_weights(UNet* U, const float* host, cudaStream_t st);
 int unet_get_weights(UNet* U, float* host, int which, cudaStream_t st);
-template <typename T> void unet_apply_sc(UNet*, const T*, const T*, const double*, int, cudaStream_t);
-template <typename T> int unet_apply(UNet*, const T*, const T*, float*, cudaStream_t);
-template <typename T> int unet_train_step(UNet*, const T*, const T*, const T*, double, double*, cudaStream_t);
+template <typename T> void unet_apply_sc(UNet*, const T*, const T*, double*, int, double, cudaStream_t);
+template <typename T> int unet_apply(UNet*, const T*, const T*, double, double, float*, cudaStream_t);
+template <typename T>
+int unet_train_step(UNet*, const T*, const T*, const T*, double, double, double, double*, cudaStream_t);
 float* unet_output(UNet* U);
 int unet_activation(UNet* U, int l, float* host, long count, cudaStream_t st);
 void unet_set_kernels(UNet* U, int tc);
@@ -555,9 +556,10 @@ static int krylov(fe_ctx* c, int maxit, int key) {
 
 // Flexible CG with the network direction (box 0; one network application per
 // iteration).  The host polls convergence after every iteration: each one
-// already costs a full network pass.
+// already costs a full network pass.  allow_net = false: Jacobi directions
+// only (a later refinement solve of a corrector with learned_every = 0).
 template <typename T>
-static int fcg_learned(fe_ctx* c, int maxit) {
+static int fcg_learned(fe_ctx* c, int maxit, bool allow_net) {
   Launch L = c->L();
   BoxDev& B = c->hbox[0];
   CK(cudaMemsetAsync(c->dactive, 0, sizeof(int), c->st));
@@ -567,11 +569,11 @@ static int fcg_learned(fe_ctx* c, int maxit) {
     CK(cudaStreamSynchronize(c->st));
     if (*c->hactive == 0) break;
     const int every = c->prm.learned_every;
-    const bool net = every > 0 ? (it % every == 0) : (it == 0);
+    const bool net = allow_net && (every > 0 ? (it % every == 0) : (it == 0));
     if (net)
       FE_LAUNCH(L, KID_UNET,
-                (unet_apply_sc<T>(c->unet, (const T*)B.f[K_R], (const T*)B.f[W_PSI], B.sc,
-                                  it == 0 ? SC_BB : SC_RR, c->st)));
+                (unet_apply_sc<T>(c->unet, (const T*)B.f[K_R], (const T*)B.f[W_DINV], B.sc,
+                                  it == 0 ? SC_BB : SC_RR, B.ih, c->st)));
     launch_fcg<T>(L, net ? unet_output(c->unet) : nullptr);
   }
   CK(cudaGetLastError());
@@ -598,7 +600,7 @@ static int gm_sums(fe_ctx* c, int stride, double* out) {
 // Stops when the least-squares residual meets SC_TOL ||b|| or at the
 // iteration cap; x0 = 0 (the refinement's correction starts from zero).
 template <typename T>
-static int fgmres_learned(fe_ctx* c, int maxit) {
+static int fgmres_learned(fe_ctx* c, int maxit, bool allow_net) {
   Launch L = c->L();
   BoxDev& B = c->hbox[0];
   cudaStream_t st = c->st;
@@ -681,10 +683,10 @@ static int fgmres_learned(fe_ctx* c, int maxit) {
       // the least-squares residual to at most kGmNetKeep of its value;
       // otherwise (or without a network) the Jacobi direction
       bool have = false;
-      if (c->unet_ready && (every > 0 ? it % every == 0 : it == 0)) {
-        gm_set_scalar(B.sc, SC_PR, 1.0, st);  // ||v_j||^2: the network input is v_j / rms(v_j)
-        FE_LAUNCH(L, KID_UNET, (unet_apply_sc<T>(c->unet, vj, psi, B.sc, SC_PR, st)));
-        gm_from_net<T>(pd, unet_output(c->unet), n, c->gm_part, nb, st);
+      if (allow_net && c->unet_ready && (every > 0 ? it % every == 0 : it == 0)) {
+        gm_set_scalar(B.sc, SC_PR, 1.0, st);  // ||v_j||^2 = 1: the input scale of the unit vector v_j
+        FE_LAUNCH(L, KID_UNET, (unet_apply_sc<T>(c->unet, vj, dinv, B.sc, SC_PR, B.ih, st)));
+        gm_from_net<T>(pd, vj, dinv, unet_output(c->unet), B.sc, n, c->gm_part, nb, st);
         double zz = 0.0;
         if ((rc = gm_sums(c, 1, &zz)) != FE_OK) return rc;
         if (std::isfinite(zz) && zz > 0.0) {
@@ -742,13 +744,17 @@ static int fgmres_learned(fe_ctx* c, int maxit) {
   return FE_OK;
 }
 
+// outer: index of the refinement solve within the corrector (0 in FP64).  With
+// learned_every = 0 the network gives only the first direction of the
+// corrector's first solve: once per corrector, not once per refinement step.
 template <typename T>
-static int inner_solve(fe_ctx* c, int maxit, int key) {
+static int inner_solve(fe_ctx* c, int maxit, int key, int outer = 0) {
+  const bool allow_net = c->prm.learned_every != 0 || outer == 0;
   if (c->prm.solver == FE_FCG_LEARNED) {
     if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
-    return fcg_learned<T>(c, maxit);
+    return fcg_learned<T>(c, maxit, allow_net);
   }
-  if (c->prm.solver == FE_FGMRES_LEARNED) return fgmres_learned<T>(c, maxit);
+  if (c->prm.solver == FE_FGMRES_LEARNED) return fgmres_learned<T>(c, maxit, allow_net);
   return krylov<T>(c, maxit, key);
 }
 
@@ -818,7 +824,7 @@ static int pressure_solve(fe_ctx* c, bool started = false) {
     CK(cudaMemcpyAsync(c->hactive, c->douter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (*c->hactive == 0) break;
-    int rc = inner_solve<T>(c, c->prm.p_maxit, 1 + outer);
+    int rc = inner_solve<T>(c, c->prm.p_maxit, 1 + outer, outer);
     if (rc != FE_OK) return rc;
     launch_mix_accum<T>(L);
     launch_mix_residual<T>(L, 0, c->douter);
@@ -894,7 +900,7 @@ static int krylov_graph(fe_ctx* c, int lev) {
   if (bicg) launch_bicg_init<T>(L);
   else launch_cg_init<T>(L, 0.0);
   if (learned) {  // first iteration with the network direction
-    unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_PSI], B0.sc, SC_BB, cs);
+    unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_DINV], B0.sc, SC_BB, B0.ih, cs);
     launch_fcg<T>(L, unet_output(c->unet));
   }
   CK(cudaMemsetAsync(c->dloop + lev, 0, sizeof(int), cs));
@@ -910,7 +916,7 @@ static int krylov_graph(fe_ctx* c, int lev) {
     launch_bicg_x<T>(Lb);
   } else if (learned) {
     if (c->prm.learned_every == 1)
-      unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_PSI], B0.sc, SC_RR, bs);
+      unet_apply_sc<T>(c->unet, (const T*)B0.f[K_R], (const T*)B0.f[W_DINV], B0.sc, SC_RR, B0.ih, bs);
     launch_fcg<T>(Lb, c->prm.learned_every == 1 ? unet_output(c->unet) : nullptr);
   } else {
     launch_cg_fused<T>(Lb);
@@ -1053,6 +1059,9 @@ static int build_graph(fe_ctx* c, int s) {
 static bool graph_ok(const fe_ctx* c) {
   if (!c->use_graphs || c->harvest_b || c->prof.on) return false;
   if (c->prm.solver == FE_FCG_LEARNED && (!c->unet_ready || c->prm.learned_every > 1)) return false;
+  // mixed precision, network once per corrector: host-driven (the refinement
+  // loop's later solves skip the network, which the graph's loop body cannot)
+  if (c->prm.solver == FE_FCG_LEARNED && !c->fp64 && c->prm.learned_every == 0) return false;
   if (c->prm.solver == FE_FGMRES_LEARNED) return false;  // host-driven: the Arnoldi step reads its dots
   return true;
 }
@@ -1432,34 +1441,30 @@ extern "C" int fe_get_preconditioner(fe_ctx* c, float* w, size_t count, int grad
   return unet_get_weights(c->unet, w, gradients ? 1 : 0, c->st);
 }
 
-extern "C" int fe_precond_apply(fe_ctx* c, int box, const void* r, float* z) {
-  if (!c || box != 0 || !r || !z) return FE_ERR_INVALID_ARG;
+extern "C" int fe_precond_apply(fe_ctx* c, int box, const void* r, double dt, float* z) {
+  if (!c || box != 0 || !r || !z || !(dt > 0.0)) return FE_ERR_INVALID_ARG;
   if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
-  const int s = c->cur;
   BoxDev& B = c->hbox[0];
-  // psi of the current state (dt does not enter the network input)
-  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, s, 1.0);
-  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, s, 1.0);
-  int rc;
-  if (c->fp64) {
-    rc = unet_apply<double>(c->unet, (const double*)r, (const double*)B.f[W_PSI], z, c->st);
-  } else {
-    rc = unet_apply<float>(c->unet, (const float*)r, (const float*)B.f[W_PSI], z, c->st);
-  }
-  (void)s;
-  return rc;
+  // psi of the current state and the Jacobi inverse of the operator with this dt
+  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, dt);
+  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, dt);
+  if (c->fp64)
+    return unet_apply<double>(c->unet, (const double*)r, (const double*)B.f[W_DINV], dt, B.ih, z, c->st);
+  return unet_apply<float>(c->unet, (const float*)r, (const float*)B.f[W_DINV], dt, B.ih, z, c->st);
 }
 
-extern "C" int fe_precond_train_step(fe_ctx* c, int box, const void* r, const void* e, double lr, double* loss) {
-  if (!c || box != 0 || !r || !e || !loss) return FE_ERR_INVALID_ARG;
+extern "C" int fe_precond_train_step(fe_ctx* c, int box, const void* r, const void* e, double dt, double lr,
+                                     double* loss) {
+  if (!c || box != 0 || !r || !e || !loss || !(dt > 0.0)) return FE_ERR_INVALID_ARG;
   if (!c->unet_ready) return FE_ERR_UNSUPPORTED;
   BoxDev& B = c->hbox[0];
-  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, 1.0);
-  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, 1.0);
+  if (c->fp64) k_psi_box<double><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, dt);
+  else k_psi_box<float><<<1024, 256, 0, c->st>>>(c->dbox, 0, c->cur, dt);
   if (c->fp64)
-    return unet_train_step<double>(c->unet, (const double*)r, (const double*)e, (const double*)B.f[W_PSI], lr, loss,
-                                   c->st);
-  return unet_train_step<float>(c->unet, (const float*)r, (const float*)e, (const float*)B.f[W_PSI], lr, loss, c->st);
+    return unet_train_step<double>(c->unet, (const double*)r, (const double*)e, (const double*)B.f[W_DINV], dt, B.ih,
+                                   lr, loss, c->st);
+  return unet_train_step<float>(c->unet, (const float*)r, (const float*)e, (const float*)B.f[W_DINV], dt, B.ih, lr,
+                                loss, c->st);
 }
 
 extern "C" int fe_harvest_pressure(fe_ctx* c, void* const* b_out, void* const* x_out, int max_pairs, int* npairs) {

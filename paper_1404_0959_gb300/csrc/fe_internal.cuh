@@ -68,6 +68,7 @@ enum Scalar {
   SC_IT0, SC_IT1, SC_IT2, SC_IT3, SC_RES0, SC_RES1, SC_RES2, SC_RES3,
   SC_ODONE, SC_OBB, SC_ORR, SC_ORES, SC_ITSUM, SC_OTOL, SC_OUTER,  // mixed-precision refinement
   SC_FB, SC_NFB,                                                    // flexible CG: Jacobi fallback flag, count
+  SC_NSCALE,  // learned preconditioner: scale rms(r) d0 of the network's correction of the Jacobi direction
   SC_KERR,  // a kernel gave up a bounded wait (bulk-copy completion)
   SC_MASS, SC_ENERGY, SC_BAD, SC_DUST0,
   NSC = SC_DUST0 + MAXD + 4

@@ -65,15 +65,20 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jacobi(T* __restrict__ z, con
     z[c] = v[c] * dinv[c];
 }
 
+// z = v dinv + sc[SC_NSCALE] y: the residual-form direction of the network
+// output y for the unit Arnoldi vector v; block partial sums of ||z||^2
 template <typename T>
-__global__ void __launch_bounds__(kGmThreads) k_gm_from_net(T* __restrict__ z, const float* __restrict__ net, long n,
+__global__ void __launch_bounds__(kGmThreads) k_gm_from_net(T* __restrict__ z, const T* __restrict__ v,
+                                                            const T* __restrict__ dinv, const float* __restrict__ net,
+                                                            const double* __restrict__ sc, long n,
                                                             double* __restrict__ part) {
   __shared__ double red[kGmThreads / 32];
+  const T scale = (T)sc[SC_NSCALE];
   double s = 0.0;
   for (long c = blockIdx.x * (long)kGmThreads + threadIdx.x; c < n; c += (long)gridDim.x * kGmThreads) {
-    const float v = net[c];
-    z[c] = (T)v;
-    s += (double)v * (double)v;
+    const T zc = v[c] * dinv[c] + scale * (T)net[c];
+    z[c] = zc;
+    s += (double)zc * (double)zc;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -112,8 +117,9 @@ void gm_jacobi(T* z, const T* v, const T* dinv, long n, int nblk, cudaStream_t s
   k_gm_jacobi<T><<<nblk, kGmThreads, 0, st>>>(z, v, dinv, n);
 }
 template <typename T>
-void gm_from_net(T* z, const float* net, long n, double* part, int nblk, cudaStream_t st) {
-  k_gm_from_net<T><<<nblk, kGmThreads, 0, st>>>(z, net, n, part);
+void gm_from_net(T* z, const T* v, const T* dinv, const float* net, const double* sc, long n, double* part, int nblk,
+                 cudaStream_t st) {
+  k_gm_from_net<T><<<nblk, kGmThreads, 0, st>>>(z, v, dinv, net, sc, n, part);
 }
 void gm_set_scalar(double* sc, int slot, double v, cudaStream_t st) { k_gm_set<<<1, 1, 0, st>>>(sc, slot, v); }
 void gm_finish(double* sc, int* active, double iters, double rr, int conv, cudaStream_t st) {
@@ -124,7 +130,7 @@ void gm_finish(double* sc, int* active, double iters, double rr, int conv, cudaS
   template void gm_dots<T>(const T*, long, int, const T*, double*, int, cudaStream_t);                 \
   template void gm_combine<T>(T*, const T*, double, const T*, long, int, const GmCoef&, int, cudaStream_t); \
   template void gm_jacobi<T>(T*, const T*, const T*, long, int, cudaStream_t);                          \
-  template void gm_from_net<T>(T*, const float*, long, double*, int, cudaStream_t);
+  template void gm_from_net<T>(T*, const T*, const T*, const float*, const double*, long, double*, int, cudaStream_t);
 INST(double)
 INST(float)
 

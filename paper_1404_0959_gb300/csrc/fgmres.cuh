@@ -43,9 +43,11 @@ void gm_combine(T* out, const T* a, double sa, const T* V, long n, int nv, const
 // z = dinv v.
 template <typename T>
 void gm_jacobi(T* z, const T* v, const T* dinv, long n, int nblk, cudaStream_t st);
-// z = (T) net; part[b] = block b's share of sum net^2 (not finite if any net value is not).
+// z = dinv v + sc[SC_NSCALE] net (residual-form network direction for v); part[b] = block b's
+// share of ||z||^2 (not finite if any net value is not).
 template <typename T>
-void gm_from_net(T* z, const float* net, long n, double* part, int nblk, cudaStream_t st);
+void gm_from_net(T* z, const T* v, const T* dinv, const float* net, const double* sc, long n, double* part, int nblk,
+                 cudaStream_t st);
 // sc[slot] = v (one thread).
 void gm_set_scalar(double* sc, int slot, double v, cudaStream_t st);
 // End of a solve: iteration count, squared residual, verdict; marks the box

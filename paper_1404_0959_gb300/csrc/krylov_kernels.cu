@@ -1456,9 +1456,11 @@ __global__ void __launch_bounds__(NTHR) k_mix_finish(const BoxDev* boxes, const 
 }
 
 // ---- flexible CG (learned preconditioner) ------------------------------------------------
-// Direction candidates: z (network output, FP32) or the Jacobi direction
-// r / diag when <z, r> <= 0.  p = z' - beta p_prev with
-// beta = <z', q_prev> / <p_prev, q_prev> (Notay 2000, truncation 1).
+// Direction candidates: the residual-form network direction
+// z = r dinv + sc[SC_NSCALE] y (y the network output, FP32) or the Jacobi
+// direction r dinv when <z, r> <= 0 or without a network output.
+// p = z' - beta p_prev with beta = <z', q_prev> / <p_prev, q_prev>
+// (Notay 2000, truncation 1).
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_fcg_dots(const BoxDev* boxes, const int2* ework, double* part,
                                                    const float* z) {
@@ -1469,10 +1471,11 @@ __global__ void __launch_bounds__(NTHR) k_fcg_dots(const BoxDev* boxes, const in
   const T* __restrict__ r = F<T>(B, K_R);
   const T* __restrict__ q = F<T>(B, K_Q);
   const T* __restrict__ dinv = F<T>(B, W_DINV);
+  const T zs = z ? (T)B.sc[SC_NSCALE] : T(0);
   DotAcc<T> zr, zq, dq;
   for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
     const T rc = r[c], qc = q[c], rd = rc * dinv[c];
-    const T zc = z ? (T)z[c] : rd;  // no network output: Jacobi direction
+    const T zc = z ? rd + zs * (T)z[c] : rd;  // no network output: Jacobi direction
     zr.add(zc, rc);
     zq.add(zc, qc);
     dq.add(rd, qc);
@@ -1501,8 +1504,10 @@ __global__ void __launch_bounds__(NTHR) k_fcg_dir(const BoxDev* boxes, const int
   T* __restrict__ p = F<T>(B, K_PD);
   const bool fb = B.sc[SC_FB] != 0.0;
   const T beta = (T)B.sc[SC_BETA];
+  const T zs = z ? (T)B.sc[SC_NSCALE] : T(0);
   for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
-    const T zc = (fb || !z) ? r[c] * dinv[c] : (T)z[c];
+    const T rd = r[c] * dinv[c];
+    const T zc = (fb || !z) ? rd : rd + zs * (T)z[c];
     p[c] = zc - beta * p[c];
   }
 }

@@ -354,7 +354,12 @@ __global__ void k_slice(const float* src, long n, int Cf, int c0, int C, float* 
     dst[q] = src[(q / C) * Cf + c0 + q % C];
 }
 
-// Network input: channel 0 = r / rms(r), channel 1 = psi / mean(psi) - 1, channels 2..15 = 0.
+// Network input of the residual-form preconditioner, for a residual r of the
+// operator M = diag(psi/dt) - dt/2 D(G2 .) with Jacobi inverse dinv = 1/d,
+// d = psi/dt + 3 dt/h^2: channel 0 = (r dinv) / (rms(r) d0) with d0 the
+// Jacobi inverse at psi = 1, channel 1 = (3 dt/h^2) dinv (the Laplacian's
+// share of the diagonal, which carries dt and psi), channels 2..15 = 0.  The
+// direction is z = r dinv + rms(r) d0 y for the network output y.
 // 16-channel input voxel: (c0, c1, 0, ..., 0) in two 16-byte stores
 __device__ __forceinline__ void pack_voxel(bf16* o, float c0, float c1) {
   __nv_bfloat162 p = __floats2bfloat162_rn(c0, c1);
@@ -365,10 +370,39 @@ __device__ __forceinline__ void pack_voxel(bf16* o, float c0, float c1) {
   reinterpret_cast<uint4*>(o)[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// a = 1 / (rms(r) d0), w = 3 dt / h^2
 template <typename T>
-__global__ void k_pack_input(const T* r, const T* psi, long n, double rinv, double pinv, bf16* in16) {
+__global__ void k_pack_input(const T* r, const T* dinv, long n, double a, double w, bf16* in16) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const double dq = (double)dinv[q];
+    pack_voxel(in16 + q * 16, (float)((double)r[q] * dq * a), (float)(dq * w));
+  }
+}
+
+// z = r dinv + scale y (the residual-form direction, FP32)
+template <typename T>
+__global__ void k_direction(const T* r, const T* dinv, const float* y, double scale, long n, float* z) {
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
-    pack_voxel(in16 + q * 16, (float)((double)r[q] * rinv), psi ? (float)((double)psi[q] * pinv - 1.0) : 0.f);
+    z[q] = (float)((double)r[q] * (double)dinv[q] + scale * (double)y[q]);
+}
+
+// training target t = (e - r dinv) * inv_scale into tgt; block partial sums of t^2
+template <typename T>
+__global__ void k_target(const T* r, const T* e, const T* dinv, long n, double inv_scale, float* tgt, double* part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const float t = (float)(((double)e[q] - (double)r[q] * (double)dinv[q]) * inv_scale);
+    tgt[q] = t;
+    s += (double)t * (double)t;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // Adam (Kingma and Ba 2015) on the FP32 master weights; refreshes the BF16
@@ -675,14 +709,20 @@ static void wgrad(UNet& U, int l, Src s0, Src s1, cudaStream_t st) {
 
 namespace fe {
 
-// Network input for the current residual: channel 0 = r / rms(r) where
-// rms(r)^2 = rr / n is read from the box scalars, channel 1 = psi - 1.
+// Network input for the current residual of a solve: rms(r)^2 = rr / n with
+// rr read from the box scalar rr_slot, dt from SC_KDT (the solve's operator);
+// the output scale rms(r) d0 of the direction goes to SC_NSCALE.
 template <typename T>
-__global__ void k_pack_fcg(const T* r, const T* psi, long n, const double* sc, int rr_slot, bf16* in16) {
-  const double rr = sc[rr_slot];
-  const double rinv = rr > 0.0 ? sqrt((double)n / rr) : 0.0;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
-    pack_voxel(in16 + q * 16, (float)((double)r[q] * rinv), (float)psi[q] - 1.f);
+__global__ void k_pack_fcg(const T* r, const T* dinv, long n, double* sc, int rr_slot, double ih, bf16* in16) {
+  const double rr = sc[rr_slot], dt = sc[SC_KDT];
+  const double c3 = 3.0 * dt * ih * ih, d0 = 1.0 / (1.0 / dt + c3);
+  const double rms = rr > 0.0 ? sqrt(rr / (double)n) : 0.0;
+  const double a = rms > 0.0 ? 1.0 / (rms * d0) : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_NSCALE] = rms * d0;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const double dq = (double)dinv[q];
+    pack_voxel(in16 + q * 16, (float)((double)r[q] * dq * a), (float)(dq * c3));
+  }
 }
 
 // mean-square of a field (two-level, fixed order): part[block] partial sums
@@ -788,35 +828,40 @@ int unet_get_weights(UNet* U, float* host, int which, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
-// z (fp32 [N^3]) = net(r / rms(r), psi - 1); rms taken from the box scalar rr_slot
+// Network pass for the current residual of a solve (input as k_pack_fcg);
+// the output y stays in U->out32 and its scale in sc[SC_NSCALE].
 template <typename T>
-void unet_apply_sc(UNet* U, const T* r, const T* psi, const double* sc, int rr_slot, cudaStream_t st) {
+void unet_apply_sc(UNet* U, const T* r, const T* dinv, double* sc, int rr_slot, double ih, cudaStream_t st) {
   const long n = cube(U->N);
-  k_pack_fcg<T><<<ew(n), 256, 0, st>>>(r, psi, n, sc, rr_slot, U->in16);
+  k_pack_fcg<T><<<ew(n), 256, 0, st>>>(r, dinv, n, sc, rr_slot, ih, U->in16);
   unet_forward(*U, st);
 }
 
-// z = net(r / rms(r), psi - 1) with rms computed here
+// Preconditioner scales of a residual: rms(r) from a fixed-order reduction, d0 from dt.
 template <typename T>
-int unet_apply(UNet* U, const T* r, const T* psi, float* z, cudaStream_t st) {
+static void precond_scales(UNet* U, const T* r, double dt, double ih, cudaStream_t st, double* rms, double* d0) {
   const long n = cube(U->N);
-  double* part = U->part;
-  double* tmp = nullptr;
-  if (!part) {
-    if (cudaMalloc(&tmp, 4096 * 8) != cudaSuccess) return FE_ERR_OOM;
-    part = tmp;
-  }
   const int nb = ew(n);
-  k_sumsq<T><<<nb, 256, 0, st>>>(r, n, part);
-  const double rr = host_sum(part, nb, st);
-  const double rinv = rr > 0.0 ? sqrt((double)n / rr) : 0.0;
-  k_pack_input<T><<<ew(n), 256, 0, st>>>(r, psi, n, rinv, 1.0, U->in16);
+  k_sumsq<T><<<nb, 256, 0, st>>>(r, n, U->part);
+  const double rr = host_sum(U->part, nb, st);
+  *rms = rr > 0.0 ? sqrt(rr / (double)n) : 0.0;
+  *d0 = 1.0 / (1.0 / dt + 3.0 * dt * ih * ih);
+}
+
+// z = r dinv + rms(r) d0 net(input): the residual-form direction.
+template <typename T>
+int unet_apply(UNet* U, const T* r, const T* dinv, double dt, double ih, float* z, cudaStream_t st) {
+  const long n = cube(U->N);
+  if (!U->part) return FE_ERR_UNSUPPORTED;
+  double rms, d0;
+  precond_scales<T>(U, r, dt, ih, st, &rms, &d0);
+  k_pack_input<T><<<ew(n), 256, 0, st>>>(r, dinv, n, rms > 0.0 ? 1.0 / (rms * d0) : 0.0, 3.0 * dt * ih * ih,
+                                         U->in16);
   unet_forward(*U, st);
-  cudaMemcpyAsync(z, U->out32, n * 4, cudaMemcpyDeviceToDevice, st);
+  k_direction<T><<<ew(n), 256, 0, st>>>(r, dinv, U->out32, rms * d0, n, z);
   int herr = 0;
   cudaMemcpyAsync(&herr, U->err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  if (tmp) cudaFree(tmp);
   if (herr) {
     cudaMemsetAsync(U->err, 0, sizeof(int), st);
     return FE_ERR_CUDA;
@@ -824,28 +869,28 @@ int unet_apply(UNet* U, const T* r, const T* psi, float* z, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
-// One training step on the pair (r, e): input r / rms(r), target e / rms(e),
-// loss ||y - t||^2 / ||t||^2, backward through every layer, Adam.
-// lr <= 0: gradients only (no update).
+// One training step on the pair (r, e) with M e = r (M of this dt): input as
+// unet_apply, target t = (e - r dinv) / (rms(r) d0), loss ||y - t||^2 /
+// ||t||^2, backward through every layer, Adam.  lr <= 0: gradients only.
 template <typename T>
-int unet_train_step(UNet* U, const T* r, const T* e, const T* psi, double lr, double* loss, cudaStream_t st) {
+int unet_train_step(UNet* U, const T* r, const T* e, const T* dinv, double dt, double ih, double lr, double* loss,
+                    cudaStream_t st) {
   if (!U->g0) return FE_ERR_UNSUPPORTED;
   const int n0 = U->N, n1 = U->N / 2, n2 = U->N / 4;
   const long v0 = cube(n0), v1 = cube(n1), v2 = cube(n2);
   const int nb = ew(v0);
-  k_sumsq<T><<<nb, 256, 0, st>>>(r, v0, U->part);
-  const double rr = host_sum(U->part, nb, st);
-  k_sumsq<T><<<nb, 256, 0, st>>>(e, v0, U->part);
-  const double ee = host_sum(U->part, nb, st);
-  if (!(rr > 0.0) || !(ee > 0.0)) return FE_ERR_INVALID_ARG;
-  k_pack_input<T><<<ew(v0), 256, 0, st>>>(r, psi, v0, sqrt((double)v0 / rr), 1.0, U->in16);
+  double rms, d0;
+  precond_scales<T>(U, r, dt, ih, st, &rms, &d0);
+  if (!(rms > 0.0)) return FE_ERR_INVALID_ARG;
+  k_pack_input<T><<<ew(v0), 256, 0, st>>>(r, dinv, v0, 1.0 / (rms * d0), 3.0 * dt * ih * ih, U->in16);
   unet_forward(*U, st);
-  // target e / rms(e) into gsk0 (fp32 scratch), loss and dL/dy
+  // target into gsk0 (fp32 scratch), its norm, then loss and dL/dy
   float* tgt = U->gsk0;
-  k_scale_to_f32<T><<<ew(v0), 256, 0, st>>>(e, v0, sqrt((double)v0 / ee), tgt);
-  // ||t||^2 = v0 by construction
-  k_loss_grad<<<nb, 256, 0, st>>>(U->out32, tgt, v0, 1.0 / (double)v0, U->dy8, U->part);
-  *loss = host_sum(U->part, nb, st) / (double)v0;
+  k_target<T><<<nb, 256, 0, st>>>(r, e, dinv, v0, 1.0 / (rms * d0), tgt, U->part);
+  const double tt = host_sum(U->part, nb, st);
+  if (!(tt > 0.0)) return FE_ERR_INVALID_ARG;
+  k_loss_grad<<<nb, 256, 0, st>>>(U->out32, tgt, v0, 1.0 / tt, U->dy8, U->part);
+  *loss = host_sum(U->part, nb, st) / tt;
   for (int l = 0; l < kNL; ++l) {
     cudaMemsetAsync(U->L[l].gw, 0, 27L * U->L[l].cin * U->L[l].cout * 4, st);
     cudaMemsetAsync(U->L[l].gb, 0, U->L[l].cout * 4, st);
@@ -912,9 +957,10 @@ int unet_N(const UNet* U) { return U->N; }
 void unet_set_kernels(UNet* U, int tc) { U->use_tc = tc; }
 
 #define INST(T)                                                                                         \
-  template void unet_apply_sc<T>(UNet*, const T*, const T*, const double*, int, cudaStream_t);          \
-  template int unet_apply<T>(UNet*, const T*, const T*, float*, cudaStream_t);                          \
-  template int unet_train_step<T>(UNet*, const T*, const T*, const T*, double, double*, cudaStream_t);
+  template void unet_apply_sc<T>(UNet*, const T*, const T*, double*, int, double, cudaStream_t);         \
+  template int unet_apply<T>(UNet*, const T*, const T*, double, double, float*, cudaStream_t);          \
+  template int unet_train_step<T>(UNet*, const T*, const T*, const T*, double, double, double, double*, \
+                                  cudaStream_t);
 INST(double)
 INST(float)
 

@@ -106,8 +106,8 @@ def load_library(path=LIB_PATH):
     lib.fe_preconditioner_size.restype = ctypes.c_long
     lib.fe_load_preconditioner.argtypes = [c_void_p, c_void_p, ctypes.c_size_t]
     lib.fe_get_preconditioner.argtypes = [c_void_p, c_void_p, ctypes.c_size_t, c_int]
-    lib.fe_precond_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
-    lib.fe_precond_train_step.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_double, POINTER(c_double)]
+    lib.fe_precond_apply.argtypes = [c_void_p, c_int, c_void_p, c_double, c_void_p]
+    lib.fe_precond_train_step.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_double, c_double, POINTER(c_double)]
     lib.fe_precond_activation.argtypes = [c_void_p, c_int, c_void_p, ctypes.c_size_t]
     lib.fe_harvest_pressure.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_int)]
     lib.fe_use_graphs.argtypes = [c_void_p, c_int]
@@ -265,13 +265,13 @@ def fe_get_preconditioner(ctx, gradients=False):
     return w
 
 
-def fe_precond_apply(ctx, box, r_ptr, z_ptr):
-    return _check(lib().fe_precond_apply(ctx, box, c_void_p(r_ptr), c_void_p(z_ptr)), "fe_precond_apply")
+def fe_precond_apply(ctx, box, r_ptr, dt, z_ptr):
+    return _check(lib().fe_precond_apply(ctx, box, c_void_p(r_ptr), dt, c_void_p(z_ptr)), "fe_precond_apply")
 
 
-def fe_precond_train_step(ctx, box, r_ptr, e_ptr, lr):
+def fe_precond_train_step(ctx, box, r_ptr, e_ptr, dt, lr):
     loss = c_double(0.0)
-    _check(lib().fe_precond_train_step(ctx, box, c_void_p(r_ptr), c_void_p(e_ptr), lr, byref(loss)),
+    _check(lib().fe_precond_train_step(ctx, box, c_void_p(r_ptr), c_void_p(e_ptr), dt, lr, byref(loss)),
            "fe_precond_train_step")
     return loss.value
 

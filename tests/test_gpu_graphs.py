@@ -72,7 +72,7 @@ def test_graph_learned_first_direction(fe):
     for graphs in (False, True):
         s = fe.Solver(box, solver=fe.FE_FCG_LEARNED, p_tol=1e-8, learned_every=0)
         s.init_state(0, fe.FE_INIT_SPECTRAL)
-        fe.fe_load_preconditioner(s.ctx, learned.he_init(5))
+        fe.fe_load_preconditioner(s.ctx, learned.he_init(5, zero_last=False))
         s.use_graphs(graphs)
         code, info = s.step(2)
         assert code == fe.FE_OK

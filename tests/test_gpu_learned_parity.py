@@ -39,6 +39,7 @@ SOURCES = {"e1a": [(9, "same", 2)], "e1b": [(0, "same", 16)], "d1": [(1, "down",
 OUT_LEVEL = {"e1a": 0, "e1b": 0, "d1": 1, "e2": 1, "d2": 2, "e3": 2, "u2": 1, "u1": 0, "out": 0}
 FIXTURE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hit256_step.json")
 BF16_ULP = 2.0 ** -7
+DT = 0.02
 
 
 @pytest.fixture(scope="module")
@@ -107,12 +108,13 @@ def network_run(fe, N, seed, want):
                   solver=fe.FE_FCG_LEARNED, p_tol=1e-8)
     s.set_state(0, rho, u, Y)
     P = ounet.init_params(2, seed=seed + 100)
+    P["out.W"] *= 0.1  # a correction smaller than the Jacobi direction, as after training
     fe.fe_load_preconditioner(s.ctx, flat(P))
     r = smooth_field(N, seed + 7, 1.0) + 0.1 * np.random.default_rng(seed).standard_normal((N, N, N))
     rt = torch.tensor(r, dtype=torch.float32, device="cuda")
     z = torch.empty_like(rt)
-    fe.fe_precond_apply(s.ctx, 0, rt.data_ptr(), z.data_ptr())
-    acts = {}
+    fe.fe_precond_apply(s.ctx, 0, rt.data_ptr(), DT, z.data_ptr())
+    acts = {8: fe.fe_precond_activation(s.ctx, 8, N ** 3).reshape(N, N, N).astype(np.float64)}
     for l in sorted(want):
         if l == 9:
             acts[9] = fe.fe_precond_activation(s.ctx, 9, N ** 3 * 16).reshape(N, N, N, 16).astype(np.float64)
@@ -133,7 +135,7 @@ def check_layer(name, P, acts, out, N, nsample, rng):
     vox[:4] = [[0, 0, 0], [No - 1, No - 1, No - 1], [0, No - 1, 0], [No - 1, 0, No - 1]]
     y = oracle_layer(name, P, acts, vox, No)
     if name == "out":
-        g = out[vox[:, 0], vox[:, 1], vox[:, 2]]
+        g = acts[8][vox[:, 0], vox[:, 1], vox[:, 2]]
         e = y[:, 0]
         err = rel(g, e)
         assert err < 1e-4, (name, err)
@@ -152,10 +154,14 @@ def check_layer(name, P, acts, out, N, nsample, rng):
 def test_every_layer_at_128_matches_the_oracle_convolution(fe):
     N = 128
     P, acts, out, r, psi = network_run(fe, N, 3, set(range(8)) | {9})
-    # the packed input: BF16 of r / rms(r) and psi - 1
-    rms = np.sqrt(np.mean(f32(r) ** 2))
-    assert rel(acts[9][..., 0], bf16(f32(r) / rms)) < 1e-5
-    assert rel(acts[9][..., 1], bf16(f32(psi) - 1.0)) < 1e-2
+    # the packed input (BF16) and the direction r/d + rms(r) d0 y against the oracle's definitions
+    h = 2 * np.pi / N
+    x = ounet.network_input(f32(r), psi, DT, h)
+    assert rel(acts[9][..., 0], bf16(x[0])) < 1e-2
+    assert rel(acts[9][..., 1], bf16(x[1])) < 1e-2
+    rho, d0 = ounet.precond_scales(f32(r), DT, h)
+    z = f32(r) / ounet.jacobi_diag(psi, DT, h) + rho * d0 * acts[8]
+    assert rel(out, z) < 1e-5
     rng = np.random.default_rng(128)
     errs = {name: check_layer(name, P, acts, out, N, 4096, rng) for name in NAMES}
     print("N=128 relative L2 vs the oracle convolution per layer:", {k: "%.2e" % v for k, v in errs.items()})

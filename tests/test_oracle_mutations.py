@@ -211,3 +211,26 @@ def test_rng_pin_catches_zero_based_counter(monkeypatch):
     monkeypatch.setattr(ic, "splitmix64", lambda seed, m: orig(seed, np.asarray(m, dtype=np.uint64) - np.uint64(1)))
     with pytest.raises(AssertionError):
         t_ic.test_splitmix64_published_outputs()
+
+
+def test_precond_pins_catch_a_wrong_jacobi_diagonal(monkeypatch):
+    from oracle import unet
+
+    from . import test_oracle_unet as t_unet
+    monkeypatch.setattr(unet, "jacobi_diag", lambda psi, dt, h: psi / dt + 6.0 * dt / (h * h))
+    with pytest.raises(AssertionError):
+        t_unet.test_jacobi_diag_and_weight_channel_are_the_operators_entries()
+
+
+def test_precond_pins_catch_a_target_without_the_jacobi_part(monkeypatch):
+    from oracle import unet
+
+    from . import test_oracle_unet as t_unet
+
+    def bad_target(r, e, psi, dt, h):
+        rho, d0 = unet.precond_scales(r, dt, h)
+        return (e / (rho * d0))[None]
+
+    monkeypatch.setattr(unet, "training_target", bad_target)
+    with pytest.raises(AssertionError):
+        t_unet.test_target_direction_solves_the_system(monkeypatch)
