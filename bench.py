@@ -228,25 +228,35 @@ def run_reference(args, cfg, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_path(fe, box, cfg, precision, solver, args, stream):
-    """Steps/s of one solver path on the same workload (untimed set-up excluded)."""
+def time_path(fe, box, cfg, precision, solver, args, stream, learned_every=0, weights=None):
+    """Steps/s of one solver path on the same workload (untimed set-up excluded).
+    Learned paths train the network on this run's own pressure pairs first
+    (or take `weights` from an earlier path); the trained weights are returned."""
     import torch
     from paper_1404_0959_gb300 import learned
     N = box["N"]
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
-                  p_maxit=1000, solver=solver, learned_every=0, stream=stream.cuda_stream)
+                  p_maxit=1000, solver=solver, learned_every=learned_every, stream=stream.cuda_stream)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
     out = {"precision": "fp64" if precision == fe.FE_FP64 else "mixed",
-           "solver": "jacobi-pcg" if solver == fe.FE_PCG_JACOBI else "fcg, learned first direction"}
+           "solver": "jacobi-pcg" if solver == fe.FE_PCG_JACOBI else
+           ("fcg, learned direction every iteration" if learned_every == 1 else
+            "fcg, learned first direction of each corrector")}
     if solver == fe.FE_FCG_LEARNED:
-        fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
-        bank = learned.PairBank(s, 12)
-        bank.harvest(s, args.learn_steps)
-        t0 = time.perf_counter()
-        hist = learned.train(s, bank, args.learn_iters, lr=1e-3)
-        torch.cuda.synchronize()
-        out.update(train_pairs=bank.n, train_iters=args.learn_iters, train_s=time.perf_counter() - t0,
-                   loss_first=hist[0], loss_last=hist[-1])
+        if weights is None:
+            fe.fe_load_preconditioner(s.ctx, learned.he_init(0))
+            bank = learned.PairBank(s, 6 * args.learn_steps)
+            bank.harvest(s, args.learn_steps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hist = learned.train(s, bank, args.learn_iters, lr=1e-3)
+            torch.cuda.synchronize()
+            out.update(train_pairs=bank.n, train_iters=args.learn_iters, train_s=time.perf_counter() - t0,
+                       loss_first=hist[0], loss_last=hist[-1])
+            weights = fe.fe_get_preconditioner(s.ctx)
+            s.init_state(0, fe.FE_INIT_SPECTRAL)
+        else:
+            fe.fe_load_preconditioner(s.ctx, weights)
         s.profile_start("unet")
         s.step(1)
         prof = s.profile_stop()
@@ -269,7 +279,7 @@ def time_path(fe, box, cfg, precision, solver, args, stream):
     out.update(steps=K, ms_per_step=1e3 * t / K, value=float(N) ** 3 * K / t, krylov_iters_last_step=info[0]["iters"],
                rel_res_last_step=info[0]["rel_res"])
     s.close()
-    return out
+    return out, weights
 
 
 # FLOPs of one network application at N^3 (2 x MACs; 27-tap convolutions over
@@ -377,8 +387,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="fixed tile depth (no autotuning)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and learned comparison paths")
     ap.add_argument("--no-graphs", action="store_true", help="host-driven steps in the headline region")
-    ap.add_argument("--learn-steps", type=int, default=2, help="steps harvested for training (learned path)")
-    ap.add_argument("--learn-iters", type=int, default=60, help="training iterations (learned path)")
+    ap.add_argument("--learn-steps", type=int, default=4, help="steps harvested for training (learned path)")
+    ap.add_argument("--learn-iters", type=int, default=120, help="training iterations (learned path)")
     ap.add_argument("--ensemble", action="store_true",
                     help="time the 64-box ensemble in one context against one context per box")
     ap.add_argument("--unet", action="store_true",
@@ -536,8 +546,18 @@ def main():
     # network's direction (trained first on this run's own pressure pairs)
     extra = {}
     if not args.no_compare:
-        extra["plain_fp64"] = time_path(fe, box, cfg, fe.FE_FP64, fe.FE_PCG_JACOBI, args, stream)
-        extra["learned_fp32"] = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args, stream)
+        extra["plain_fp64"], _ = time_path(fe, box, cfg, fe.FE_FP64, fe.FE_PCG_JACOBI, args, stream)
+        extra["learned_fp32"], wts = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args, stream, 0)
+        extra["learned_fp32_every_iteration"], _ = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args,
+                                                             stream, 1, wts)
+        # break-even: a network application against the CG iterations it would have to save
+        if share:
+            per = lambda k: share[k][0] / share[k][1] if share.get(k, (0, 0))[1] else 0.0
+            cg_ms = per("cg_dirmatvec") + per("cg_rupdate")
+            net_ms = extra["learned_fp32"].get("net_ms_per_apply")
+            extra["break_even"] = {"cg_iteration_ms": cg_ms, "net_ms_per_apply": net_ms,
+                                   "cg_iterations_one_application_must_save": (net_ms / cg_ms) if cg_ms and net_ms
+                                   else None}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
