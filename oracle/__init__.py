@@ -29,6 +29,7 @@ here is this project's reading of those passages.  Modules:
 ``krylov``  Jacobi-PCG, Jacobi-BiCGStab, flexible CG, flexible GMRES
 ``diag``    kinetic energy, enstrophy, Taylor microscale, spectrum, totals
 ``unet``    FP64 3D-conv U-Net forward/backward (learned preconditioner)
+``les``     top-hat filter, Favre sub-grid stress, Smagorinsky model, a-priori statistics
 
 Parity status of each function is stated in its module header.
 """

@@ -234,3 +234,46 @@ def test_precond_pins_catch_a_target_without_the_jacobi_part(monkeypatch):
     monkeypatch.setattr(unet, "training_target", bad_target)
     with pytest.raises(AssertionError):
         t_unet.test_target_direction_solves_the_system(monkeypatch)
+
+
+def test_les_pins_catch_uniform_filter_weights(monkeypatch):
+    from oracle import les
+
+    from . import test_oracle_les as t_les
+
+    def uniform(m):
+        return list(range(-m, m + 1)), np.full(2 * m + 1, 1.0 / (2 * m + 1))
+
+    monkeypatch.setattr(les, "filter_weights", uniform)
+    with pytest.raises(AssertionError):
+        t_les.test_filter_transfer_function_is_the_dirichlet_closed_form(1)
+
+
+def test_les_pins_catch_a_reynolds_filtered_stress(monkeypatch):
+    from oracle import les
+
+    from . import test_oracle_les as t_les
+
+    def reynolds(rho, u, m):
+        rb = les.box_filter(rho, m)
+        ub = [les.box_filter(u[i], m) for i in range(3)]
+        tau = [les.box_filter(rho * u[i] * u[j], m) - rb * ub[i] * ub[j] for i, j in les.PAIRS]
+        return rb, ub, tau
+
+    monkeypatch.setattr(les, "filtered_fields", reynolds)
+    with pytest.raises(AssertionError):
+        t_les.test_favre_stress_is_galilean_invariant()
+
+
+def test_les_pins_catch_a_strain_without_the_half(monkeypatch):
+    from oracle import les, ops
+
+    from . import test_oracle_les as t_les
+
+    def bad_strain(ut, h):
+        g = [[ops.Gc(ut[i], j, h) for j in range(3)] for i in range(3)]
+        return [g[i][j] + g[j][i] for i, j in les.PAIRS]
+
+    monkeypatch.setattr(les, "strain", bad_strain)
+    with pytest.raises(AssertionError):
+        t_les.test_smagorinsky_tensor_of_a_shear_mode()
