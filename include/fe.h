@@ -224,6 +224,34 @@ int fe_diagnostics(fe_ctx* ctx, int box, fe_diag* out, double* spectrum, int nbi
  * Q iso-surfaces). */
 int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
 
+/* A-priori analysis for large-eddy simulation (Sec. 1 names LES of the plume
+ * as the goal of the DNS; Sec. 2 the a-priori use of the DNS database; the
+ * paper names no filter or model).  From the current rho, u of a box:
+ * top-hat filter of width Delta = 2 m h per axis by the trapezoidal rule
+ * (end points at half weight), tensor product, 1 <= m <= FE_LES_MAX_M and
+ * 2 m + 1 <= N; Favre filtering rho_bar = bar(rho), u~ = bar(rho u) /
+ * rho_bar; sub-grid stress tau_ij = bar(rho u_i u_j) - bar(rho u_i)
+ * bar(rho u_j) / rho_bar; strain S_ij = (Gc_j u~_i + Gc_i u~_j) / 2 from the
+ * Gauss cell gradient, |S| = sqrt(2 S:S); Smagorinsky model slot tau^M =
+ * Cs^2 B with B_ij = -2 rho_bar Delta^2 |S| S^d_ij (d: deviatoric part).
+ * Means over the box: k_sgs = <tau_kk>/2, pi_sgs = -<tau^d:S>, cs2_opt =
+ * <tau^d:B>/<B:B> (least-squares Cs^2), corr = <tau^d:B>/sqrt(<tau^d:tau^d>
+ * <B:B>), pi_model = -cs^2 <B:S>.  fields: NULL or a device array of 10 N^3
+ * values of the context precision receiving rho_bar, u~_0..2 and tau in the
+ * order 00 01 02 11 12 22.  Work memory (23 N^3 values) is allocated on the
+ * first call and kept by the context (FE_ERR_OOM if it cannot be).  The model
+ * is evaluated a priori only; it does not enter fe_step. */
+#define FE_LES_MAX_M 8
+typedef struct {
+    double delta;       /* filter width 2 m h */
+    double k_sgs;       /* <tau_kk> / 2 */
+    double pi_sgs;      /* -<tau^d_ij S_ij> */
+    double cs2_opt;     /* <tau^d:B> / <B:B> */
+    double corr;        /* <tau^d:B> / sqrt(<tau^d:tau^d> <B:B>) */
+    double pi_model;    /* -cs^2 <B:S> */
+} fe_les_stats;
+int fe_les_apriori(fe_ctx* ctx, int box, int m, double cs, fe_les_stats* out, void* fields);
+
 /* Learned preconditioner (extension of the paper's pressure solve, Sec. 2
  * par. 1): a 3-level 3D-conv U-Net (16/32/64 channels, 3x3x3 kernels,
  * periodic padding, ReLU; BF16 weights and activations, FP32 accumulation on

@@ -24,6 +24,10 @@ template <typename T> int spectrum(const T*, const T*, const T*, int, double*, i
 template <typename T> int diag_sums(const Launch&, const BoxDev&, int, int, double*);
 template <typename T> void qcrit(const Launch&, int, int, T*);
 struct UNet;
+template <typename T>
+int les_apriori(const T* rho, const T* u0, const T* u1, const T* u2, int N, int m, double cs, T* work, double* part,
+                double* hpart, int nsm, T* out, double* stats, cudaStream_t st);
+int les_max_blocks(int nsm);
 UNet* unet_create(int N, bool training, int* rc);
 void unet_destroy(UNet* U);
 long unet_param_count();
@@ -122,6 +126,10 @@ struct fe_ctx {
   void* const* harvest_x = nullptr;
   int harvest_max = 0, harvest_n = 0;
   Prof prof;
+  void* les_work = nullptr;   // fe_les_apriori: 23 N^3 arrays of the largest box (allocated on first use)
+  size_t les_bytes = 0;
+  double* les_part = nullptr;  // its block partial sums (device) and their pinned host copy
+  double* les_hpart = nullptr;
   Launch L() {
     return Launch{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
                   prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
@@ -442,6 +450,9 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->douter);
   cudaFree(c->gm_basis);
   cudaFree(c->gm_part);
+  cudaFree(c->les_work);
+  cudaFree(c->les_part);
+  if (c->les_hpart) cudaFreeHost(c->les_hpart);
   if (c->gm_hpart) cudaFreeHost(c->gm_hpart);
   if (c->hactive) cudaFreeHost(c->hactive);
   if (c->hsc) cudaFreeHost(c->hsc);
@@ -1415,6 +1426,53 @@ extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   CK(cudaStreamSynchronize(c->st));
   if (best_tz) *best_tz = best;
   return rc != FE_OK ? rc : rc2;
+}
+
+// ---- a-priori LES analysis ----------------------------------------------------------------
+extern "C" int fe_les_apriori(fe_ctx* c, int box, int m, double cs, fe_les_stats* out, void* fields) {
+  if (!c || !out || box < 0 || box >= c->nb || m < 1 || m > FE_LES_MAX_M || !(cs >= 0.0)) return FE_ERR_INVALID_ARG;
+  const int N = c->N[box];
+  if (2 * m + 1 > N) return FE_ERR_INVALID_ARG;
+  const size_t w = c->fp64 ? 8 : 4;
+  const size_t need = (size_t)23 * N * N * N * w;
+  if (c->les_bytes < need) {
+    cudaFree(c->les_work);
+    c->les_work = nullptr;
+    c->les_bytes = 0;
+    if (cudaMalloc(&c->les_work, need) != cudaSuccess) {
+      cudaGetLastError();
+      return FE_ERR_OOM;
+    }
+    c->les_bytes = need;
+  }
+  const int nbl = les_max_blocks(c->nsm);
+  if (!c->les_part) {
+    if (cudaMalloc(&c->les_part, (size_t)nbl * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->les_hpart, (size_t)nbl * 8 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return FE_ERR_OOM;
+    }
+  }
+  const BoxDev& B = c->hbox[box];
+  const int s = c->cur;
+  double st[6];
+  int rc;
+  if (c->fp64)
+    rc = les_apriori<double>((const double*)B.f[S(s, F_RHO)], (const double*)B.f[S(s, F_U0)],
+                             (const double*)B.f[S(s, F_U1)], (const double*)B.f[S(s, F_U2)], N, m, cs,
+                             (double*)c->les_work, c->les_part, c->les_hpart, c->nsm, (double*)fields, st, c->st);
+  else
+    rc = les_apriori<float>((const float*)B.f[S(s, F_RHO)], (const float*)B.f[S(s, F_U0)],
+                            (const float*)B.f[S(s, F_U1)], (const float*)B.f[S(s, F_U2)], N, m, cs,
+                            (float*)c->les_work, c->les_part, c->les_hpart, c->nsm, (float*)fields, st, c->st);
+  if (rc != FE_OK) return rc;
+  out->delta = st[0];
+  out->k_sgs = st[1];
+  out->pi_sgs = st[2];
+  out->cs2_opt = st[3];
+  out->corr = st[4];
+  out->pi_model = st[5];
+  return FE_OK;
 }
 
 // ---- learned preconditioner --------------------------------------------------------------

@@ -24,6 +24,7 @@ FE_ERR_OOM = -5
 FE_ERR_UNSUPPORTED = -6
 FE_ERR_TOO_LARGE = -7
 FE_NOALLOC_MAX_N = 64
+FE_LES_MAX_M = 8
 FE_PROFILE_MAX_KERNELS = 64
 
 FE_FP64 = 0
@@ -64,6 +65,11 @@ class fe_diag(ctypes.Structure):
                 ("energy", c_double), ("t", c_double), ("dt_prev", c_double)]
 
 
+class fe_les_stats(ctypes.Structure):
+    _fields_ = [("delta", c_double), ("k_sgs", c_double), ("pi_sgs", c_double), ("cs2_opt", c_double),
+                ("corr", c_double), ("pi_model", c_double)]
+
+
 class fe_profile_info(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("target_launches", ctypes.c_int64), ("target_ms", c_double),
                 ("counts", ctypes.c_int64 * FE_PROFILE_MAX_KERNELS)]
@@ -75,8 +81,8 @@ EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
            "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
-           "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_destroy",
-           "fe_strerror"]
+           "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_les_apriori",
+           "fe_destroy", "fe_strerror"]
 
 
 def load_library(path=LIB_PATH):
@@ -114,6 +120,7 @@ def load_library(path=LIB_PATH):
     lib.fe_use_plane_streaming.argtypes = [c_void_p, c_int]
     lib.fe_plane_streaming_active.argtypes = [c_void_p]
     lib.fe_precond_kernels.argtypes = [c_void_p, c_int]
+    lib.fe_les_apriori.argtypes = [c_void_p, c_int, c_int, c_double, POINTER(fe_les_stats), c_void_p]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
@@ -263,6 +270,14 @@ def fe_get_preconditioner(ctx, gradients=False):
     w = np.empty(fe_preconditioner_size(), dtype=np.float32)
     _check(lib().fe_get_preconditioner(ctx, w.ctypes.data, w.size, int(gradients)), "fe_get_preconditioner")
     return w
+
+
+def fe_les_apriori(ctx, box, m, cs, fields_ptr=None):
+    """A-priori LES statistics of a box (dict); fields_ptr: optional device array of 10 N^3 values."""
+    out = fe_les_stats()
+    _check(lib().fe_les_apriori(ctx, box, m, cs, byref(out), c_void_p(fields_ptr) if fields_ptr else None),
+           "fe_les_apriori")
+    return {k: getattr(out, k) for k, _ in fe_les_stats._fields_}
 
 
 def fe_precond_apply(ctx, box, r_ptr, dt, z_ptr):

@@ -212,7 +212,11 @@ def test_gradients_match_oracle(fe):
     fe.fe_load_preconditioner(s.ctx, flat(P))
     rng = np.random.default_rng(9)
     r = smooth_field(N, 10, 1.0) + 0.1 * rng.standard_normal((N, N, N))
-    e = smooth_field(N, 11, 1.0)
+    # a correction e whose network target (e - r/d) / (rms(r) d0) is a unit-scale smooth field, the
+    # scale the residual form trains at
+    h = 2 * np.pi / N
+    rho_r, d0 = ounet.precond_scales(r, DT, h)
+    e = r / ounet.jacobi_diag(psi, DT, h) + rho_r * d0 * smooth_field(N, 11, 1.0)
     rt = torch.tensor(r, device="cuda")  # keep both tensors alive while the library reads them
     et = torch.tensor(e, device="cuda")
     loss = fe.fe_precond_train_step(s.ctx, 0, rt.data_ptr(), et.data_ptr(), DT, 0.0)
