@@ -282,6 +282,34 @@ def time_path(fe, box, cfg, precision, solver, args, stream, learned_every=0, we
     return out, weights
 
 
+def time_les(fe, box, cfg, args, stream, m=2):
+    """CUDA-event time of the a-priori LES analysis (fe_les_apriori) on the
+    workload's spectral state in FP32; roofline from its 74 algorithmic words
+    per cell (x pass 4 read + 10 written, y and z passes 10 + 10 each, Favre
+    velocity 4 + 3, statistics 13 read)."""
+    import torch
+    N = box["N"]
+    s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"],
+                  stream=stream.cuda_stream)
+    s.init_state(0, fe.FE_INIT_SPECTRAL)
+    for _ in range(max(args.warmup, 3)):
+        st = fe.fe_les_apriori(s.ctx, 0, m, 0.17)
+    K = max(3, args.steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(K):
+        st = fe.fe_les_apriori(s.ctx, 0, m, 0.17)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    ms = ev0.elapsed_time(ev1) / K
+    hbm, kind = peaks()
+    gbs = 74 * 4 * float(N) ** 3 / (ms / 1e3) / 1e9
+    return {"N": N, "m": m, "ms_per_call": ms, "alg_bytes": 74 * 4 * N ** 3, "achieved_gbs": gbs, "peak": hbm,
+            "frac": gbs / hbm, "note": "includes the host read of the block partial sums", "stats": st}
+
+
 # FLOPs of one network application at N^3 (2 x MACs; 27-tap convolutions over
 # the padded channel counts the kernels compute): e1a, e1b, out at N (16 -> 16),
 # d1 (N/2, 16 -> 32), e2 (N/2, 32 -> 32), d2 (N/4, 32 -> 64), e3 (N/4, 64 -> 64),
@@ -550,6 +578,7 @@ def main():
         extra["learned_fp32"], wts = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args, stream, 0)
         extra["learned_fp32_every_iteration"], _ = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args,
                                                              stream, 1, wts)
+        extra["les_apriori_fp32"] = time_les(fe, box, cfg, args, stream)
         # break-even: a network application against the CG iterations it would have to save
         if share:
             per = lambda k: share[k][0] / share[k][1] if share.get(k, (0, 0))[1] else 0.0

@@ -231,12 +231,8 @@ def test_gradients_match_oracle(fe):
     assert abs(loss - Lq) < 2e-3 * Lq
     errs = {n + k: rel(g[n + k], Gq[n + k]) for n in NAMES for k in (".W", ".b")}
     print("relative gradient errors vs the BF16-matched oracle:", {k: round(v, 4) for k, v in errs.items()})
-    # BF16 rounding of each layer's pre-activation gradient compounds toward the input layer.  The
-    # first layer's bias gradient and its weight gradient for the second input channel (the Laplacian
-    # share of the diagonal, nearly uniform) are sums of that gradient over every voxel with heavy
-    # cancellation, which scales the compounded rounding up: a wider bar there
-    bars = {k: (6e-2 if k.startswith("e1a.") else 3e-2) for k in errs}
-    assert all(errs[k] < bars[k] for k in errs), errs
+    # BF16 rounding of each layer's pre-activation gradient compounds toward the input layer
+    assert max(errs.values()) < 3e-2, errs
     s.close()
 
 
