@@ -30,6 +30,7 @@ here is this project's reading of those passages.  Modules:
 ``diag``    kinetic energy, enstrophy, Taylor microscale, spectrum, totals
 ``unet``    FP64 3D-conv U-Net forward/backward (learned preconditioner)
 ``les``     top-hat filter, Favre sub-grid stress, Smagorinsky model, a-priori statistics
+``twofluid`` Eulerian two-fluid dust phase (own momentum, Stokes drag), after the gas step
 
 Parity status of each function is stated in its module header.
 """

@@ -71,11 +71,13 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import ops
+from . import ops, twofluid
 from .krylov import bicgstab, fcg, fgmres, pcg
 
 BAROTROPIC = 0
 FOURIER = 1
+EQUILIBRIUM = 0  # dust model: particle velocity u - tau_p Du/Dt (Sec. 2 par. 2)
+TWO_FLUID = 1    # dust model: every class with its own momentum (oracle/twofluid.py)
 
 
 @dataclass
@@ -98,6 +100,7 @@ class Params:
     p_maxit: int = 500
     transonic: bool = False
     fgmres: bool = False  # flexible GMRES(20) for every solve (any operator)
+    dust_model: int = EQUILIBRIUM
 
     @property
     def h(self):
@@ -145,8 +148,9 @@ def face_flux(rho, u):
     return [ops.I4(rho, d) * ops.I4(u[d], d) for d in range(3)]
 
 
-def make_state(prm, rho, u, Y, T=None, phi=None):
-    """Assemble a state dict; p from the closure, phi = I4(rho) I4(u) unless given."""
+def make_state(prm, rho, u, Y, T=None, phi=None, V=None):
+    """Assemble a state dict; p from the closure, phi = I4(rho) I4(u) unless given.
+    Two-fluid dust: V[j] = the velocity of class j (the gas velocity unless given)."""
     rho = np.asarray(rho, dtype=np.float64)
     u = [np.asarray(c, dtype=np.float64) for c in u]
     Y = [np.asarray(y, dtype=np.float64) for y in Y]
@@ -155,8 +159,11 @@ def make_state(prm, rho, u, Y, T=None, phi=None):
     p = eos_pressure(prm, rho, T)
     if phi is None:
         phi = face_flux(rho, u)
-    return {"rho": rho, "u": u, "phi": phi, "p": p, "Y": Y, "T": T,
-            "t": 0.0, "dt_prev": math.inf}
+    st = {"rho": rho, "u": u, "phi": phi, "p": p, "Y": Y, "T": T,
+          "t": 0.0, "dt_prev": math.inf}
+    if prm.dust_model == TWO_FLUID:
+        st["V"] = [[np.array(c, dtype=np.float64) for c in (V[j] if V is not None else u)] for j in range(len(Y))]
+    return st
 
 
 def initial_state(prm):
@@ -255,7 +262,8 @@ def step(prm, state, precond=None, dt=None):
 
     a_n = accel(prm, rho_n, u_n, p_n)
     FY_n = []
-    for j in range(nd):
+    eq_dust = prm.dust_model == EQUILIBRIUM
+    for j in range(nd if eq_dust else 0):
         fp = particle_flux(prm, phi_n, rho_n, a_n, j)
         FY_n.append(ops.D([fp[d] * ops.I4(Y_n[j], d) for d in range(3)], h))
     if fourier:
@@ -296,8 +304,8 @@ def step(prm, state, precond=None, dt=None):
 
         # a7: particle velocity and dust transport
         a_k = accel(prm, rho_new, u_new, p_new)
-        Y_new = []
-        for j in range(nd):
+        Y_new = [] if eq_dust else list(Y_k)
+        for j in range(nd if eq_dust else 0):
             fp = particle_flux(prm, phi_new, rho_new, a_k, j)
             FY_k = ops.D([fp[d] * ops.I4(Y_k[j], d) for d in range(3)], h)
             rhoY = rho_n * Y_n[j] - 0.5 * dt * (FY_n[j] + FY_k)
@@ -322,6 +330,13 @@ def step(prm, state, precond=None, dt=None):
 
     new = {"rho": rho_k, "u": u_k, "phi": phi_k, "p": p_final, "Y": Y_k, "T": T_new,
            "t": state["t"] + dt, "dt_prev": dt}
+    if not eq_dust:  # two-fluid dust after the gas step (the gas does not depend on it)
+        new["Y"], new["V"] = [], []
+        for j in range(nd):
+            Yj, Vj = twofluid.step_class((rho_n, u_n, phi_n), (rho_k, u_k, phi_k), Y_n[j], state["V"][j],
+                                         prm.tau_p[j], dt, h)
+            new["Y"].append(Yj)
+            new["V"].append(Vj)
     info = {"dt": dt, "iters": iters, "rel_res": res, "psi": psi}
     return new, info
 
@@ -338,4 +353,7 @@ def totals(prm, state):
         out["energy"] = vol * float(np.sum(rho * prm.cv * state["T"] + ke))
     else:
         out["energy"] = vol * float(np.sum(ke))
+    if state.get("V") is not None:
+        out["dust_momentum"] = [[vol * float(np.sum(rho * y * v[m])) for m in range(3)]
+                                for y, v in zip(state["Y"], state["V"])]
     return out

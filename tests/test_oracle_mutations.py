@@ -277,3 +277,31 @@ def test_les_pins_catch_a_strain_without_the_half(monkeypatch):
     monkeypatch.setattr(les, "strain", bad_strain)
     with pytest.raises(AssertionError):
         t_les.test_smagorinsky_tensor_of_a_shear_mode()
+
+
+def test_two_fluid_pins_catch_a_trapezoidal_drag(monkeypatch):
+    from oracle import twofluid
+
+    from . import test_oracle_twofluid as t_tf
+
+    def cn_drag(sig, mom, u, dt, tau):
+        r = (1 - 0.5 * dt / tau) / (1 + 0.5 * dt / tau)
+        return [u[m] + (mom[m] / sig - u[m]) * r for m in range(3)]
+
+    monkeypatch.setattr(twofluid, "drag", cn_drag)
+    with pytest.raises(AssertionError):
+        t_tf.test_uniform_slip_relaxation_closed_form()
+
+
+def test_two_fluid_pins_catch_a_flux_without_slip(monkeypatch):
+    from oracle import ops, twofluid
+
+    from . import test_oracle_twofluid as t_tf
+
+    def no_slip(phi, rho, u, Y, V, h):
+        F = [phi[d] * ops.I4(Y, d) for d in range(3)]
+        return ops.D(F, h), [ops.D([F[d] * ops.I4(V[m], d) for d in range(3)], h) for m in range(3)]
+
+    monkeypatch.setattr(twofluid, "dust_fluxes", no_slip)
+    with pytest.raises(AssertionError):
+        t_tf.test_first_order_agreement_with_the_equilibrium_model()
