@@ -79,12 +79,17 @@ extern "C" {
 #define FE_PHIY  7
 #define FE_PHIZ  8
 #define FE_Y0    9   /* dust mass fraction of class j is FE_Y0 + j */
+#define FE_V0   17   /* two-fluid dust: velocity component m of class j is FE_V0 + 3 j + m */
 
 /* fe_init_state modes */
 #define FE_INIT_SPECTRAL 0  /* random solenoidal u from (seed, k0, mach_rms); rho = T = 1, Y = Y0 */
 #define FE_INIT_DERIVE   1  /* keep rho, u, Y (and T) already set; derive p (EOS) and phi = I4(rho) I4(u) */
 
 #define FE_MAX_DUST 8
+
+/* dust model (Sec. 2 par. 2) */
+#define FE_DUST_EQUILIBRIUM 0  /* Equilibrium-Eulerian: particle velocity u - tau_p Du/Dt    */
+#define FE_DUST_TWO_FLUID   1  /* Eulerian two-fluid: each class carries its own momentum */
 
 typedef struct fe_ctx fe_ctx;   /* opaque */
 
@@ -117,6 +122,7 @@ typedef struct {
                                  * direction of each corrector's solve only (mixed
                                  * precision: of its first refinement solve; such steps
                                  * are host-driven, not CUDA graphs) */
+    int32_t dust_model;         /* FE_DUST_EQUILIBRIUM | FE_DUST_TWO_FLUID (tau_p > 0 required) */
 } fe_params;
 
 typedef struct {
@@ -154,7 +160,9 @@ int fe_create(const fe_params* prm, void* cuda_stream, fe_ctx** out);
  * rho = 1, T = 1, Y_j = Y0_j, then as FE_INIT_DERIVE.  The random numbers
  * are SplitMix64 draws 2(3f+c), 2(3f+c)+1 for FFT mode f, component c,
  * through Box-Muller.  FE_INIT_DERIVE: p from the closure, phi = I4(rho)
- * I4(u_d), t = 0, no previous step (growth limit inactive). */
+ * I4(u_d), t = 0, no previous step (growth limit inactive).  Two-fluid dust:
+ * both modes also set every class's velocity V = u (set FE_V0 + 3 j + m
+ * afterwards for another start). */
 int fe_init_state(fe_ctx* ctx, int box, int mode);
 
 /* Copy one field of the current state in (set) or out (get).  src/dst hold
@@ -199,6 +207,15 @@ int fe_set_clock(fe_ctx* ctx, int box, double t, double dt_prev);
  *              - sum_m tau_dm I4(u_m) - kappa G4(T), kappa = mu c_p / Pr
  *   closure: barotropic p = rho^gamma/gamma; Fourier T = (E - |u|^2/2)/c_v,
  *   p = rho R T with R = 1/gamma, c_v = R/(gamma-1).
+ * Two-fluid dust (dust_model = FE_DUST_TWO_FLUID): the classes' Y are not
+ *   updated with u_p as above; after the gas step each class (bulk density
+ *   sigma = rho Y, velocity V; pressureless, one-way coupled) is advanced by
+ *   the dust face flux phi_v = phi + I4(rho) I4(V - u), mass flux F = phi_v I4(Y),
+ *   momentum flux G_m = F I4(V_m): predictor sigma* = sigma^n - dt D(F^n),
+ *   m* = sigma^n V^n - dt D(G^n); corrector from the gas at n+1 and the
+ *   predicted dust, sigma = sigma^n - dt/2 [D(F^n) + D(F*)], m likewise;
+ *   Stokes drag backward Euler after each stage,
+ *   V = u^{n+1} + (m/sigma - u^{n+1}) tau_p/(tau_p + dt); Y = sigma/rho^{n+1}.
  * info: NULL or [n_boxes] records of the last step.  On
  * FE_ERR_NOT_CONVERGED / FE_ERR_NONFINITE the failing step is not
  * committed (state stays at the previous step). */

@@ -77,7 +77,7 @@ static const char* kKernelNames[] = {
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
     "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec",
-    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "other"};
+    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "tf_pred", "tf_corr", "other"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
 static_assert(KID_COUNT <= FE_PROFILE_MAX_KERNELS, "profile counters");
 
@@ -155,11 +155,19 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   const size_t e = c->fp64 ? 8 : 4;
   const int nd = c->prm.n_dust;
   const bool fourier = c->prm.closure == FE_FOURIER;
+  const bool two_fluid = c->prm.dust_model == FE_DUST_TWO_FLUID;
   for (int set = 0; set < 2; ++set) {
     for (int f = F_RHO; f <= F_P; ++f) plan.push_back({S(set, f), e});
     if (fourier) plan.push_back({S(set, F_T), e});
     for (int j = 0; j < nd; ++j) plan.push_back({S(set, F_Y0 + j), e});
+    if (two_fluid)
+      for (int q = 0; q < 3 * nd; ++q) plan.push_back({S(set, F_V0 + q), e});
   }
+  if (two_fluid)
+    for (int q = 0; q < 4 * nd; ++q) {
+      plan.push_back({W_TFN0 + q, e});
+      plan.push_back({W_TFS0 + q, e});
+    }
   int w[] = {W_DIV, W_DIVPHI, W_RN0, W_RN1, W_RN2, W_AN0, W_AN1, W_AN2, W_PSI, W_DINV, W_HB0, W_HB1, W_HB2,
              W_PS0, W_PS1, W_PS2, W_PW0, W_PW1, K_B, K_X, K_R, K_PD, K_Q, K_AUX};
   for (int s : w) plan.push_back({s, e});
@@ -190,6 +198,10 @@ static int validate(const fe_params* p) {
   if (p->n_dust < 0 || p->n_dust > FE_MAX_DUST) return FE_ERR_INVALID_ARG;
   if (p->n_dust > 0 && (!p->tau_p || !p->Y0)) return FE_ERR_INVALID_ARG;
   if (p->n_corr < 1 || p->n_corr > 4) return FE_ERR_INVALID_ARG;
+  if (p->dust_model != FE_DUST_EQUILIBRIUM && p->dust_model != FE_DUST_TWO_FLUID) return FE_ERR_INVALID_ARG;
+  if (p->dust_model == FE_DUST_TWO_FLUID)
+    for (int q = 0; q < p->n_boxes * p->n_dust; ++q)
+      if (!(p->tau_p[q] > 0.0)) return FE_ERR_INVALID_ARG;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->p_tol > 0.0) || p->p_maxit < 1) return FE_ERR_INVALID_ARG;
   if (p->closure == FE_FOURIER && !(p->Pr > 0.0)) return FE_ERR_INVALID_ARG;
   if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED &&
@@ -480,6 +492,8 @@ static int field_slot(const fe_ctx* c, int field, int set) {
   if (field == FE_T) return c->prm.closure == FE_FOURIER ? S(set, F_T) : -1;
   if (field >= FE_PHIX && field <= FE_PHIZ) return S(set, F_PHI0 + (field - FE_PHIX));
   if (field >= FE_Y0 && field < FE_Y0 + c->prm.n_dust) return S(set, F_Y0 + (field - FE_Y0));
+  if (c->prm.dust_model == FE_DUST_TWO_FLUID && field >= FE_V0 && field < FE_V0 + 3 * c->prm.n_dust)
+    return S(set, F_V0 + (field - FE_V0));
   return -1;
 }
 
@@ -1036,6 +1050,9 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
     const int en = last ? -1 : W_EW0 + (kk & 1);
     launch_dust<T>(L, s, ks, pn, yp0, yn0, ep, en, last ? 1 : 0, kk == 0 ? 1 : 0);
   }
+  // two-fluid dust: its own transport and drag after the gas step (it overwrites the
+  // classes' Y of the new level and their totals)
+  if (c->prm.dust_model == FE_DUST_TWO_FLUID && c->prm.n_dust > 0) launch_two_fluid<T>(L, s, ks);
   CK(cudaGetLastError());
   return FE_OK;
 }
@@ -1206,6 +1223,7 @@ static int init_box(fe_ctx* c, int b, int mode) {
     for (int j = 0; j < B.nd; ++j) fill<T>((T*)B.f[S(s, F_Y0 + j)], n, c->Y0[(size_t)b * B.nd + j], c->st);
   }
   launch_derive_box<T>(c->L(), s, b);
+  if (c->prm.dust_model == FE_DUST_TWO_FLUID && B.nd > 0) launch_two_fluid_init<T>(c->L(), s, b);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   int rc = push_scalar(c, b, SC_TIME, 0.0);

@@ -28,7 +28,9 @@ constexpr int MAXP = 16;  // partial sums per block
 
 // ---- field slots -----------------------------------------------------------
 // state set s (0 or 1): base s * NSF
-enum StateField { F_RHO = 0, F_U0, F_U1, F_U2, F_PHI0, F_PHI1, F_PHI2, F_P, F_T, F_Y0, NSF = F_Y0 + MAXD };
+// F_V0 + 3 j + m: velocity component m of dust class j (two-fluid dust model only)
+enum StateField { F_RHO = 0, F_U0, F_U1, F_U2, F_PHI0, F_PHI1, F_PHI2, F_P, F_T, F_Y0, F_V0 = F_Y0 + MAXD,
+                  NSF = F_V0 + 3 * MAXD };
 __host__ __device__ constexpr int S(int set, int f) { return set * NSF + f; }
 enum WorkSlot {
   W_BASE = 2 * NSF,
@@ -46,8 +48,10 @@ enum WorkSlot {
   W_FYN0,                 // D(phi_p^n I4 Y^n), MAXD slots
   W_YW0 = W_FYN0 + MAXD,  // Y^k ping 0, MAXD slots
   W_YW1 = W_YW0 + MAXD,   // Y^k ping 1, MAXD slots
+  W_TFN0 = W_YW1 + MAXD,  // two-fluid dust: D(F^n), D(G^n_0..2) per class, 4 MAXD slots
+  W_TFS0 = W_TFN0 + 4 * MAXD,  // two-fluid dust: predicted Y*, V*_0..2 per class, 4 MAXD slots
   // Krylov vectors
-  K_B = W_YW1 + MAXD, K_X, K_R, K_PD, K_Q,
+  K_B = W_TFS0 + 4 * MAXD, K_X, K_R, K_PD, K_Q,
   K_RHAT, K_V, K_S, K_T,  // BiCGStab
   K_Z, K_PP, K_QP,        // flexible CG: preconditioned r, previous direction and its image
   K_X64,                  // double accumulator (mixed precision refinement)
@@ -562,7 +566,8 @@ enum KernelId {
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
   KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
-  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_OTHER, KID_COUNT
+  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_TF_PRED, KID_TF_CORR, KID_OTHER,
+  KID_COUNT
 };
 
 struct Prof;  // defined in fe_api.cu
@@ -596,6 +601,10 @@ struct Launch {
     call;                                \
     prof_end((L).prof, (kid), (L).st);   \
   } while (0)
+
+// Two-fluid dust phase after the gas step s -> ks (twofluid.cu); V = u in set s.
+template <typename T> void launch_two_fluid(const Launch& L, int s, int ks);
+template <typename T> void launch_two_fluid_init(const Launch& L, int s, int box);
 
 // Step kernels (step_kernels.cu); T = field type.
 template <typename T> void launch_dt(const Launch& L, int s, int first);

@@ -1,0 +1,183 @@
+// twofluid.cu -- Eulerian two-fluid dust phase (the paper's Sec. 2 par. 2
+// contrasts its Equilibrium-Eulerian model with the full Eulerian two-phase
+// model, where the particle phase carries its own momentum).  Reading: dilute,
+// pressureless, one-way coupled; per class j with bulk density sigma = rho Y
+// and velocity V:
+//     d sigma/dt + div(sigma V) = 0,  d(sigma V)/dt + div(sigma V V) = sigma (u - V)/tau_p.
+// After the gas step n -> n+1 (the gas does not depend on the dust):
+//   face flux of the carrier mass  phi_v,d = phi_d + I4_d(rho) I4_d(V_d - u_d),
+//   dust mass flux F_d = phi_v,d I4_d(Y), momentum flux G_dm = F_d I4_d(V_m);
+//   predictor sigma* = sigma^n - dt D(F^n), m* = sigma^n V^n - dt D(G^n);
+//   corrector from the gas at n+1 and the predicted dust (Heun):
+//   sigma = sigma^n - dt/2 [D(F^n) + D(F*)], m likewise;
+//   backward-Euler drag after each stage: V = u^{n+1} + (m/sigma - u^{n+1}) tau/(tau + dt),
+//   Y = sigma / rho^{n+1}.
+// One thread walks the z-planes of a column; neighbours through the read-only
+// cache with periodic wrap (the general stencil form of the step kernels).
+#include "fe_internal.cuh"
+
+namespace fe {
+
+__device__ __forceinline__ int tfx(int d) { return d == 0 ? -1 : 0; }
+__device__ __forceinline__ int tfy(int d) { return d == 1 ? -1 : 0; }
+__device__ __forceinline__ int tfz(int d) { return d == 2 ? -1 : 0; }
+
+template <typename T>
+__device__ __forceinline__ T* TF(const BoxDev& B, int slot) {
+  return reinterpret_cast<T*>(B.f[slot]);
+}
+
+// D(F) and D(G_m) of one class at one cell: gas (rho, u, phi), dust (Y, V)
+template <typename T>
+__device__ __forceinline__ void tf_div(const T* rho, const T* const (&u)[3], const T* const (&phi)[3], const T* Y,
+                                       const T* const (&V)[3], const Nbr& n, T ih, T& DF, T (&DG)[3]) {
+  DF = T(0);
+  DG[0] = DG[1] = DG[2] = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int ox = side ? tfx(d) : 0, oy = side ? tfy(d) : 0, oz = side ? tfz(d) : 0;
+      const T sgn = side ? T(-1) : T(1);
+      const T ph = __ldg(&phi[d][n(ox, oy, oz)]);
+      const T slip = I4f<T>(V[d], n, d, ox, oy, oz) - I4f<T>(u[d], n, d, ox, oy, oz);
+      const T F = (ph + I4f<T>(rho, n, d, ox, oy, oz) * slip) * I4f<T>(Y, n, d, ox, oy, oz);
+      DF += sgn * F;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) DG[m] += sgn * F * I4f<T>(V[m], n, d, ox, oy, oz);
+    }
+  }
+  DF *= ih;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) DG[m] *= ih;
+}
+
+// Predictor: n-level divergences into W_TFN (D(F), D(G_0..2)), predicted Y*, V* into W_TFS.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_tf_pred(const BoxDev* boxes, const int2* work, int s, int ks) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (!t.active) return;
+  const T* rho = TF<T>(B, S(s, F_RHO));
+  const T* u[3] = {TF<T>(B, S(s, F_U0)), TF<T>(B, S(s, F_U1)), TF<T>(B, S(s, F_U2))};
+  const T* phi[3] = {TF<T>(B, S(s, F_PHI0)), TF<T>(B, S(s, F_PHI1)), TF<T>(B, S(s, F_PHI2))};
+  const T* rho1 = TF<T>(B, S(ks, F_RHO));
+  const T* u1[3] = {TF<T>(B, S(ks, F_U0)), TF<T>(B, S(ks, F_U1)), TF<T>(B, S(ks, F_U2))};
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    const T rn = __ldg(&rho[c]), ir1 = T(1) / __ldg(&rho1[c]);
+    for (int j = 0; j < B.nd; ++j) {
+      const T* Y = TF<T>(B, S(s, F_Y0 + j));
+      const T* V[3] = {TF<T>(B, S(s, F_V0 + 3 * j)), TF<T>(B, S(s, F_V0 + 3 * j + 1)),
+                       TF<T>(B, S(s, F_V0 + 3 * j + 2))};
+      T DF, DG[3];
+      tf_div<T>(rho, u, phi, Y, V, n, ih, DF, DG);
+      const T sig_n = rn * __ldg(&Y[c]);
+      const T sig = sig_n - dt * DF;
+      const T isig = T(1) / sig;
+      const T tau = (T)B.tau_p[j];
+      const T r = tau / (tau + dt);
+      TF<T>(B, W_TFN0 + 4 * j)[c] = DF;
+      TF<T>(B, W_TFS0 + 4 * j)[c] = sig * ir1;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        TF<T>(B, W_TFN0 + 4 * j + 1 + m)[c] = DG[m];
+        const T mom = sig_n * __ldg(&V[m][c]) - dt * DG[m];
+        const T um = __ldg(&u1[m][c]);
+        TF<T>(B, W_TFS0 + 4 * j + 1 + m)[c] = um + (mom * isig - um) * r;
+      }
+    }
+  }
+}
+
+// Corrector: Y^{n+1}, V^{n+1} into state set ks; dust-mass totals and the
+// non-finite count (added to the gas step's) of the box.
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_tf_corr(const BoxDev* boxes, const int2* work, double* part, int s,
+                                                  int ks) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  const T* rhon = TF<T>(B, S(s, F_RHO));
+  const T* rho1 = TF<T>(B, S(ks, F_RHO));
+  const T* u1[3] = {TF<T>(B, S(ks, F_U0)), TF<T>(B, S(ks, F_U1)), TF<T>(B, S(ks, F_U2))};
+  const T* phi1[3] = {TF<T>(B, S(ks, F_PHI0)), TF<T>(B, S(ks, F_PHI1)), TF<T>(B, S(ks, F_PHI2))};
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], hdt = T(0.5) * dt;
+  DotAcc<T> ady[MAXD];
+  SumAcc<T> abad;
+  if (t.active) {
+    for (int k = t.k0; k < t.kend; ++k) {
+      Nbr n(t.i, t.j, k, B.N);
+      const int c = n(0, 0, 0);
+      const T rn = __ldg(&rhon[c]), r1 = __ldg(&rho1[c]);
+      for (int j = 0; j < B.nd; ++j) {
+        const T* Ys = TF<T>(B, W_TFS0 + 4 * j);
+        const T* Vs[3] = {TF<T>(B, W_TFS0 + 4 * j + 1), TF<T>(B, W_TFS0 + 4 * j + 2), TF<T>(B, W_TFS0 + 4 * j + 3)};
+        T DF, DG[3];
+        tf_div<T>(rho1, u1, phi1, Ys, Vs, n, ih, DF, DG);
+        const T sig_n = rn * __ldg(&TF<T>(B, S(s, F_Y0 + j))[c]);
+        const T sig = sig_n - hdt * (__ldg(&TF<T>(B, W_TFN0 + 4 * j)[c]) + DF);
+        const T isig = T(1) / sig;
+        const T tau = (T)B.tau_p[j];
+        const T r = tau / (tau + dt);
+        const T Yk = sig / r1;
+        TF<T>(B, S(ks, F_Y0 + j))[c] = Yk;
+        ady[j].add(r1, Yk);
+        bool bad = !isfinite(Yk);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const T mom = sig_n * __ldg(&TF<T>(B, S(s, F_V0 + 3 * j + m))[c]) -
+                        hdt * (__ldg(&TF<T>(B, W_TFN0 + 4 * j + 1 + m)[c]) + DG[m]);
+          const T um = __ldg(&u1[m][c]);
+          const T Vm = um + (mom * isig - um) * r;
+          TF<T>(B, S(ks, F_V0 + 3 * j + m))[c] = Vm;
+          bad = bad || !isfinite(Vm);
+        }
+        if (bad) abad.add(T(1));
+      }
+    }
+  }
+  Red<T> acc[1 + MAXD];
+  acc[0] = abad.red();
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) acc[1 + j] = ady[j].red();
+  __shared__ double res[1 + MAXD];
+  if (block_sum_last<1 + MAXD>(acc, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_BAD] += res[0];
+      for (int j = 0; j < B.nd; ++j) B.sc[SC_DUST0 + j] = res[1 + j];
+    }
+  }
+}
+
+// V = u (every class) in state set s: the dust starts with the gas velocity
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_tf_init(const BoxDev* boxes, const int2* work, int s, int only_box) {
+  Tile t = tile_of(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (!t.active || (only_box >= 0 && t.box != only_box)) return;
+  for (int k = t.k0; k < t.kend; ++k) {
+    const int c = t.i + B.N * (t.j + B.N * k);
+    for (int j = 0; j < B.nd; ++j)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) TF<T>(B, S(s, F_V0 + 3 * j + m))[c] = TF<T>(B, S(s, F_U0 + m))[c];
+  }
+}
+
+#define TF_GRID L.nblocks, dim3(TX, TY), 0, L.st
+template <typename T>
+void launch_two_fluid(const Launch& L, int s, int ks) {
+  FE_LAUNCH(L, KID_TF_PRED, (k_tf_pred<T><<<TF_GRID>>>(L.boxes, L.work, s, ks)));
+  FE_LAUNCH(L, KID_TF_CORR, (k_tf_corr<T><<<TF_GRID>>>(L.boxes, L.work, L.part, s, ks)));
+}
+template <typename T>
+void launch_two_fluid_init(const Launch& L, int s, int box) {
+  FE_LAUNCH(L, KID_OTHER, (k_tf_init<T><<<TF_GRID>>>(L.boxes, L.work, s, box)));
+}
+template void launch_two_fluid<double>(const Launch&, int, int);
+template void launch_two_fluid<float>(const Launch&, int, int);
+template void launch_two_fluid_init<double>(const Launch&, int, int);
+template void launch_two_fluid_init<float>(const Launch&, int, int);
+
+}  // namespace fe

@@ -37,9 +37,12 @@ FE_FCG_LEARNED = 2
 FE_FGMRES_LEARNED = 3
 
 FE_RHO, FE_UX, FE_UY, FE_UZ, FE_P, FE_T, FE_PHIX, FE_PHIY, FE_PHIZ, FE_Y0 = range(10)
+FE_V0 = 17  # two-fluid dust: velocity component m of class j is FE_V0 + 3 j + m
 FE_INIT_SPECTRAL = 0
 FE_INIT_DERIVE = 1
 FE_MAX_DUST = 8
+FE_DUST_EQUILIBRIUM = 0
+FE_DUST_TWO_FLUID = 1
 
 
 class fe_params(ctypes.Structure):
@@ -48,7 +51,8 @@ class fe_params(ctypes.Structure):
                 ("tau_p", POINTER(c_double)), ("Y0", POINTER(c_double)), ("mach_rms", POINTER(c_double)),
                 ("k0", POINTER(c_double)), ("seed", POINTER(c_uint64)), ("cfl", c_double),
                 ("dt_growth_max", c_double), ("dt_max", c_double), ("n_corr", c_int32), ("solver", c_int32),
-                ("p_tol", c_double), ("p_maxit", c_int32), ("transonic", c_int32), ("learned_every", c_int32)]
+                ("p_tol", c_double), ("p_maxit", c_int32), ("transonic", c_int32), ("learned_every", c_int32),
+                ("dust_model", c_int32)]
 
 
 class fe_step_info(ctypes.Structure):
@@ -355,7 +359,7 @@ class Solver:
 
     def __init__(self, boxes, precision=FE_FP64, closure=FE_BAROTROPIC, gamma=1.4, Pr=0.7, cfl=0.5,
                  dt_growth_max=1.2, dt_max=float("inf"), n_corr=2, solver=FE_PCG_JACOBI, p_tol=1e-10,
-                 p_maxit=500, transonic=False, learned_every=1, stream=None):
+                 p_maxit=500, transonic=False, learned_every=1, stream=None, dust_model=FE_DUST_EQUILIBRIUM):
         import torch
         self.torch = torch
         nb = len(boxes)
@@ -377,7 +381,8 @@ class Solver:
         self.params = fe_params(nb, self._N, precision, closure, gamma, Pr, self._nu, nd, self._tau, self._y0,
                                 self._mach, self._k0, self._seed, cfl, dt_growth_max,
                                 dt_max if np.isfinite(dt_max) else 0.0, n_corr, solver, p_tol, p_maxit,
-                                int(bool(transonic)), int(learned_every))
+                                int(bool(transonic)), int(learned_every), int(dust_model))
+        self.two_fluid = dust_model == FE_DUST_TWO_FLUID
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
@@ -421,7 +426,8 @@ class Solver:
         fe_get_field(self.ctx, box, field, out.ctypes.data, 0)
         return out
 
-    def set_state(self, box, rho, u, Y, T=None):
+    def set_state(self, box, rho, u, Y, T=None, V=None):
+        """rho, u, Y (and T), then p and phi derived; two-fluid dust velocities V[j][m] (u unless given)."""
         self.set_field(box, FE_RHO, rho)
         for d in range(3):
             self.set_field(box, FE_UX + d, u[d])
@@ -430,6 +436,10 @@ class Solver:
         if T is not None:
             self.set_field(box, FE_T, T)
         self.init_state(box, FE_INIT_DERIVE)
+        if V is not None:
+            for j, vj in enumerate(V):
+                for m in range(3):
+                    self.set_field(box, FE_V0 + 3 * j + m, vj[m])
 
     def load_state(self, box, st, t=0.0, dt_prev=0.0):
         """Set every state field (rho, u, phi, p, Y, T) as given, then the clock (checkpoint restore)."""
@@ -442,6 +452,10 @@ class Solver:
             self.set_field(box, FE_Y0 + j, y)
         if st.get("T") is not None:
             self.set_field(box, FE_T, st["T"])
+        if st.get("V") is not None:
+            for j, vj in enumerate(st["V"]):
+                for m in range(3):
+                    self.set_field(box, FE_V0 + 3 * j + m, vj[m])
         fe_set_clock(self.ctx, box, t, dt_prev)
 
     def get_state(self, box=0):
@@ -450,6 +464,8 @@ class Solver:
               "phi": [g(box, FE_PHIX + d) for d in range(3)], "p": g(box, FE_P),
               "Y": [g(box, FE_Y0 + j) for j in range(self.nd)]}
         st["T"] = g(box, FE_T) if self.params.closure == FE_FOURIER else None
+        if self.two_fluid:
+            st["V"] = [[g(box, FE_V0 + 3 * j + m) for m in range(3)] for j in range(self.nd)]
         return st
 
     def step(self, nsteps=1):
