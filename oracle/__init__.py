@@ -31,6 +31,7 @@ here is this project's reading of those passages.  Modules:
 ``unet``    FP64 3D-conv U-Net forward/backward (learned preconditioner)
 ``les``     top-hat filter, Favre sub-grid stress, Smagorinsky model, a-priori statistics
 ``twofluid`` Eulerian two-fluid dust phase (own momentum, Stokes drag), after the gas step
+``isosurface`` marching-tetrahedra iso-surface and orthographic z-buffer depth image
 
 Parity status of each function is stated in its module header.
 """

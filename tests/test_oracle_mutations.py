@@ -305,3 +305,27 @@ def test_two_fluid_pins_catch_a_flux_without_slip(monkeypatch):
     monkeypatch.setattr(twofluid, "dust_fluxes", no_slip)
     with pytest.raises(AssertionError):
         t_tf.test_first_order_agreement_with_the_equilibrium_model()
+
+
+def test_isosurface_pins_catch_a_non_tiling_split(monkeypatch):
+    from oracle import isosurface
+
+    from . import test_oracle_isosurface as t_iso
+    monkeypatch.setattr(isosurface, "TETS", [(0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7),
+                                             (0, 2, 6, 4)])
+    with pytest.raises(AssertionError):
+        t_iso.test_planes_count_and_area_exact()
+
+
+def test_isosurface_pins_catch_edge_points_from_either_end(monkeypatch):
+    from oracle import isosurface
+
+    from . import test_oracle_isosurface as t_iso
+
+    def either_end(pa, fa, pb, fb, iso, a, b):
+        t = (iso - fa) / (fb - fa)
+        return tuple(pa[q] + t * (pb[q] - pa[q]) for q in range(3))
+
+    monkeypatch.setattr(isosurface, "edge_point", either_end)
+    with pytest.raises(AssertionError):
+        t_iso.test_sphere_closed_and_second_order_area()
