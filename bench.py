@@ -363,6 +363,93 @@ def ensemble_only(args):
     print(json.dumps(line), flush=True)
 
 
+def part_only(args):
+    """--part les|twofluid|iso: one of the scope table's further rows alone at --N (FP32 fields,
+    the benchmark workload's physics), CUDA-event timed, one JSON line."""
+    import torch
+    from paper_1404_0959_gb300 import build, fe
+    from paper_1404_0959_gb300.inputs import WORKLOADS
+    build.build()
+    cfg = dict(WORKLOADS[WORKLOAD])
+    N = args.N
+    box = dict(N=N, nu=cfg["nu"], tau_p=cfg["tau_p"], Y0=cfg["Y0"], mach_rms=cfg["mach_rms"], k0=cfg["k0"], seed=0)
+    stream = torch.cuda.current_stream()
+    hbm, kind = peaks()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"part": args.part, "N": N, "dtype": "f32 fields", "data": "synthetic spectral HIT field", "peak": hbm,
+           "peak_kind": kind}
+    if args.part == "les":
+        out.update(time_les(fe, box, cfg, args, stream))
+    elif args.part == "twofluid":
+        res = {}
+        for model in (fe.FE_DUST_EQUILIBRIUM, fe.FE_DUST_TWO_FLUID):
+            s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"], p_maxit=1000,
+                          dust_model=model, stream=stream.cuda_stream)
+            s.init_state(0, fe.FE_INIT_SPECTRAL)
+            s.autotune(1)
+            s.use_graphs(True)
+            code, _ = s.step(args.warmup)
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            code, _ = s.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            name = "two_fluid" if model == fe.FE_DUST_TWO_FLUID else "equilibrium"
+            res[name] = {"ms_per_step": ev0.elapsed_time(ev1) / args.steps}
+            if model == fe.FE_DUST_TWO_FLUID:
+                s.use_graphs(False)
+                nd = len(cfg["tau_p"])
+                for k, words in (("tf_pred", 23 * nd), ("tf_corr", 24 * nd)):
+                    s.profile_start(k)
+                    s.step(args.steps)
+                    p = s.profile_stop()
+                    ms = p["target_ms"] / max(p["target_launches"], 1)
+                    gbs = words * 4 * float(N) ** 3 / (ms / 1e3) / 1e9
+                    res[k] = {"ms_per_launch": ms, "alg_words_per_cell": words, "achieved_gbs": gbs,
+                              "frac": gbs / hbm}
+            s.close()
+        out.update(res)
+    elif args.part == "iso":
+        s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"],
+                      stream=stream.cuda_stream)
+        s.init_state(0, fe.FE_INIT_SPECTRAL)
+        q = s.q_criterion(0)
+        iso = 0.5 * s.diagnostics(0)["enstrophy"]
+        n, area = fe.fe_isosurface(s.ctx, 0, q.data_ptr(), iso)
+        tri = torch.empty((n, 9), dtype=torch.float64, device="cuda")
+        W = args.width
+        depth = torch.empty((W, W), dtype=torch.float64, device="cuda")
+        h = 2 * math.pi / N
+        for _ in range(args.warmup):
+            fe.fe_isosurface(s.ctx, 0, q.data_ptr(), iso, tri.data_ptr(), n)
+            fe.fe_raster_depth(s.ctx, tri.data_ptr(), n, W, (N + 1) * h, depth.data_ptr())
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fe.fe_isosurface(s.ctx, 0, q.data_ptr(), iso, tri.data_ptr(), n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_ext = ev0.elapsed_time(ev1) / args.steps
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fe.fe_raster_depth(s.ctx, tri.data_ptr(), n, W, (N + 1) * h, depth.data_ptr())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_ras = ev0.elapsed_time(ev1) / args.steps
+        # extraction traffic: the field read by the count and the emit pass, the per-cube counts
+        # written and read, the triangles written (72 bytes each)
+        alg = 2 * 4 * N ** 3 + 2 * 4 * N ** 3 + 72 * n
+        gbs = alg / (ms_ext / 1e3) / 1e9
+        covered = int(torch.isfinite(depth).sum().item())
+        out.update(iso=iso, triangles=n, area=area, extract_ms=ms_ext, extract_alg_bytes=alg, extract_gbs=gbs,
+                   extract_frac=gbs / hbm, raster_width=W, raster_ms=ms_ras, covered_pixels=covered,
+                   note="extraction includes two host reads (block totals, block areas)")
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def unet_only(args):
     """--unet: CUDA-event time of fe_precond_apply on a random residual (He-initialised weights)."""
     import torch
@@ -421,10 +508,15 @@ def main():
                     help="time the 64-box ensemble in one context against one context per box")
     ap.add_argument("--unet", action="store_true",
                     help="time only the learned preconditioner's network pass (K applications at N^3)")
+    ap.add_argument("--part", default=None, choices=["les", "twofluid", "iso"],
+                    help="time one further row alone: a-priori LES, two-fluid dust step, Q iso-surface + raster")
+    ap.add_argument("--width", type=int, default=2048, help="depth image width for --part iso")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.unet:
         return unet_only(args)
+    if args.part:
+        return part_only(args)
     if args.ensemble:
         return ensemble_only(args)
 

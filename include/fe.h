@@ -241,6 +241,38 @@ int fe_diagnostics(fe_ctx* ctx, int box, fe_diag* out, double* spectrum, int nbi
  * Q iso-surfaces). */
 int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
 
+/* Iso-surface of a cell field (Fig. 3 of the paper shows iso-surfaces of Q;
+ * fe_q_criterion gives that field) by marching tetrahedra, without a
+ * graphics API.  field: device array of N^3 values of the context precision
+ * for box `box`.  The cube whose corners are cells (i + dx, j + dy, k + dz)
+ * (dx, dy, dz in {0, 1}, values with periodic wrap, corner b = dx + 2 dy +
+ * 4 dz at unwrapped position ((i + dx + 1/2) h, (j + dy + 1/2) h,
+ * (k + dz + 1/2) h)) is split into the six Freudenthal tetrahedra
+ * (0,1,3,7) (0,1,5,7) (0,2,3,7) (0,2,6,7) (0,4,5,7) (0,4,6,7); a corner is
+ * inside when f > iso; one corner apart a (inside or outside) gives the
+ * triangle (P(a,b), P(a,c), P(a,d)) with b, c, d the others in tetrahedron
+ * order, two inside (a, b) and two outside (c, d) give (P(a,c), P(a,d),
+ * P(b,d)) and (P(a,c), P(b,d), P(b,c)); P is the linear zero of f - iso on
+ * the edge, computed from its corner of smaller b as p_lo + t (p_hi - p_lo).
+ * Triangles are ordered by flat cube index i + N (j + N k), then tetrahedron.
+ * The surface is closed (the split is the same in every cube).  tri: NULL
+ * (max_tri = 0) or a device array of 9 * max_tri doubles (x, y, z of the three
+ * corners); the first min(total, max_tri) triangles are written.  *ntri
+ * receives the total count, *area the total area.  Work memory (N^3 ints) is
+ * allocated on the first call and kept by the context. */
+int fe_isosurface(fe_ctx* ctx, int box, const void* field, double iso, double* tri, long long max_tri,
+                  long long* ntri, double* area);
+/* Depth image of ntri triangles (device, 9 doubles each) viewed along +z
+ * (orthographic) on width x width pixels covering [0, extent)^2: pixel (px,
+ * py) has centre ((px + 1/2), (py + 1/2)) extent / width and is covered by a
+ * triangle when its three edge functions E_ab = (x_b - x_a)(y - y_a) -
+ * (y_b - y_a)(x - x_a) share a sign (a triangle with E_01(p2) = 0 covers
+ * nothing); depth (E_12 z_0 + E_20 z_1 + E_01 z_2) / (E_12 + E_20 + E_01),
+ * the smallest non-negative depth kept, +inf where nothing is covered.
+ * depth: device array of width^2 doubles, row py * width + px.  Each step is
+ * one correctly rounded double operation in this order. */
+int fe_raster_depth(fe_ctx* ctx, const double* tri, long long ntri, int width, double extent, double* depth);
+
 /* A-priori analysis for large-eddy simulation (Sec. 1 names LES of the plume
  * as the goal of the DNS; Sec. 2 the a-priori use of the DNS database; the
  * paper names no filter or model).  From the current rho, u of a box:

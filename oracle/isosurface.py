@@ -132,3 +132,15 @@ def raster_depth(T, width, extent):
                     if z < img[py, px]:
                         img[py, px] = z
     return img
+
+
+def cube_counts(f, iso):
+    """Triangles per cube (N^3 array [k, j, i]): per tetrahedron 1 for one corner
+    apart, 2 for two and two, summed over the six tetrahedra."""
+    ins = (f > iso).astype(np.int64)
+    corners = [np.roll(ins, (-((b >> 2) & 1), -((b >> 1) & 1), -(b & 1)), axis=(0, 1, 2)) for b in range(8)]
+    total = np.zeros_like(ins)
+    for tet in TETS:
+        n = corners[tet[0]] + corners[tet[1]] + corners[tet[2]] + corners[tet[3]]
+        total += np.where((n == 1) | (n == 3), 1, np.where(n == 2, 2, 0))
+    return total

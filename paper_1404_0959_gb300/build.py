@@ -9,7 +9,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfe.so")
 SOURCES = ["step_kernels.cu", "step_zkernels.cu", "step_rkernels.cu", "krylov_kernels.cu", "fgmres.cu", "fft_diag.cu", "fe_api.cu",
-           "noalloc.cu", "unet.cu", "unet_tc.cu", "les.cu", "twofluid.cu"]
+           "noalloc.cu", "unet.cu", "unet_tc.cu", "les.cu", "twofluid.cu", "isosurface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

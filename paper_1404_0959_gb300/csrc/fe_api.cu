@@ -28,6 +28,12 @@ template <typename T>
 int les_apriori(const T* rho, const T* u0, const T* u1, const T* u2, int N, int m, double cs, T* work, double* part,
                 double* hpart, int nsm, T* out, double* stats, cudaStream_t st);
 int les_max_blocks(int nsm);
+template <typename T>
+int isosurface(const T* f, int N, double iso, double* tri, long long max_tri, int* counts, long long* bsum,
+               long long* boff, double* apart, std::vector<double>& hscratch, int nsm, long long* ntri, double* area,
+               cudaStream_t st);
+long iso_blocks(long n);
+int raster_depth(const double* tri, long long ntri, int W, double extent, double* depth, int nsm, cudaStream_t st);
 UNet* unet_create(int N, bool training, int* rc);
 void unet_destroy(UNet* U);
 long unet_param_count();
@@ -130,6 +136,9 @@ struct fe_ctx {
   size_t les_bytes = 0;
   double* les_part = nullptr;  // its block partial sums (device) and their pinned host copy
   double* les_hpart = nullptr;
+  void* iso_work = nullptr;     // fe_isosurface: per-cube counts and block scan (allocated on first use)
+  size_t iso_bytes = 0;
+  std::vector<double> iso_host;
   Launch L() {
     return Launch{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
                   prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
@@ -463,6 +472,7 @@ extern "C" void fe_destroy(fe_ctx* c) {
   cudaFree(c->gm_basis);
   cudaFree(c->gm_part);
   cudaFree(c->les_work);
+  cudaFree(c->iso_work);
   cudaFree(c->les_part);
   if (c->les_hpart) cudaFreeHost(c->les_hpart);
   if (c->gm_hpart) cudaFreeHost(c->gm_hpart);
@@ -1455,6 +1465,7 @@ extern "C" int fe_les_apriori(fe_ctx* c, int box, int m, double cs, fe_les_stats
   const size_t need = (size_t)23 * N * N * N * w;
   if (c->les_bytes < need) {
     cudaFree(c->les_work);
+  cudaFree(c->iso_work);
     c->les_work = nullptr;
     c->les_bytes = 0;
     if (cudaMalloc(&c->les_work, need) != cudaSuccess) {
@@ -1490,6 +1501,47 @@ extern "C" int fe_les_apriori(fe_ctx* c, int box, int m, double cs, fe_les_stats
   out->cs2_opt = st[3];
   out->corr = st[4];
   out->pi_model = st[5];
+  return FE_OK;
+}
+
+// ---- iso-surfaces and their depth image -------------------------------------------------
+extern "C" int fe_isosurface(fe_ctx* c, int box, const void* field, double iso, double* tri, long long max_tri,
+                             long long* ntri, double* area) {
+  if (!c || !field || !ntri || !area || box < 0 || box >= c->nb || max_tri < 0 || (max_tri > 0 && !tri) ||
+      !std::isfinite(iso))
+    return FE_ERR_INVALID_ARG;
+  const int N = c->N[box];
+  const long n = (long)N * N * N, nb = iso_blocks(n);
+  const size_t need = (size_t)n * sizeof(int) + (size_t)nb * (2 * sizeof(long long) + sizeof(double)) + 256;
+  if (c->iso_bytes < need) {
+    cudaFree(c->iso_work);
+    c->iso_work = nullptr;
+    c->iso_bytes = 0;
+    if (cudaMalloc(&c->iso_work, need) != cudaSuccess) {
+      cudaGetLastError();
+      return FE_ERR_OOM;
+    }
+    c->iso_bytes = need;
+  }
+  char* w = (char*)c->iso_work;
+  long long* bsum = (long long*)w;
+  long long* boff = bsum + nb;
+  double* apart = (double*)(boff + nb);
+  int* counts = (int*)(apart + nb);
+  if (c->fp64)
+    return isosurface<double>((const double*)field, N, iso, tri, max_tri, counts, bsum, boff, apart, c->iso_host,
+                              c->nsm, ntri, area, c->st);
+  return isosurface<float>((const float*)field, N, iso, tri, max_tri, counts, bsum, boff, apart, c->iso_host, c->nsm,
+                           ntri, area, c->st);
+}
+
+extern "C" int fe_raster_depth(fe_ctx* c, const double* tri, long long ntri, int width, double extent,
+                               double* depth) {
+  if (!c || !depth || width < 1 || width > 65536 || ntri < 0 || (ntri > 0 && !tri) || !(extent > 0.0))
+    return FE_ERR_INVALID_ARG;
+  int rc = raster_depth(tri, ntri, width, extent, depth, c->nsm, c->st);
+  if (rc != FE_OK) return rc;
+  CK(cudaStreamSynchronize(c->st));
   return FE_OK;
 }
 

@@ -85,7 +85,7 @@ EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set
            "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
            "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
-           "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_les_apriori",
+           "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_les_apriori", "fe_isosurface", "fe_raster_depth",
            "fe_destroy", "fe_strerror"]
 
 
@@ -125,6 +125,9 @@ def load_library(path=LIB_PATH):
     lib.fe_plane_streaming_active.argtypes = [c_void_p]
     lib.fe_precond_kernels.argtypes = [c_void_p, c_int]
     lib.fe_les_apriori.argtypes = [c_void_p, c_int, c_int, c_double, POINTER(fe_les_stats), c_void_p]
+    lib.fe_isosurface.argtypes = [c_void_p, c_int, c_void_p, c_double, c_void_p, ctypes.c_longlong,
+                                  POINTER(ctypes.c_longlong), POINTER(c_double)]
+    lib.fe_raster_depth.argtypes = [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_double, c_void_p]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
@@ -282,6 +285,20 @@ def fe_les_apriori(ctx, box, m, cs, fields_ptr=None):
     _check(lib().fe_les_apriori(ctx, box, m, cs, byref(out), c_void_p(fields_ptr) if fields_ptr else None),
            "fe_les_apriori")
     return {k: getattr(out, k) for k, _ in fe_les_stats._fields_}
+
+
+def fe_isosurface(ctx, box, field_ptr, iso, tri_ptr=None, max_tri=0):
+    """(total triangle count, total area); the first max_tri triangles go to tri_ptr (9 doubles each)."""
+    n = ctypes.c_longlong(0)
+    a = c_double(0.0)
+    _check(lib().fe_isosurface(ctx, box, c_void_p(field_ptr), iso, c_void_p(tri_ptr) if tri_ptr else None, max_tri,
+                               byref(n), byref(a)), "fe_isosurface")
+    return n.value, a.value
+
+
+def fe_raster_depth(ctx, tri_ptr, ntri, width, extent, depth_ptr):
+    return _check(lib().fe_raster_depth(ctx, c_void_p(tri_ptr) if tri_ptr else None, ntri, width, extent,
+                                        c_void_p(depth_ptr)), "fe_raster_depth")
 
 
 def fe_precond_apply(ctx, box, r_ptr, dt, z_ptr):

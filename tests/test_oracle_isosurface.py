@@ -87,3 +87,18 @@ def test_depth_image_of_planes_and_sphere():
     exact = math.pi - np.sqrt(1.5 ** 2 - r2[core])
     assert np.max(np.abs(img[core] - exact)) < 0.05
     assert np.all(np.isinf(img[r2 > (1.5 + 2 * hs) ** 2]))
+
+
+def test_cube_counts_agree_with_the_extraction():
+    """The vectorised per-cube count equals the triangles cube_triangles emits."""
+    from paper_1404_0959_gb300.inputs import smooth_field
+    N = 10
+    h = 2 * math.pi / N
+    f = smooth_field(N, 4, 1.0)
+    counts = iso.cube_counts(f, 0.1)
+    T, _ = iso.extract(f, 0.1, h)
+    assert counts.sum() == len(T)
+    for flat in (0, 17, 345, 999):
+        k, rem = divmod(flat, N * N)
+        j, i = divmod(rem, N)
+        assert counts[k, j, i] == len(iso.cube_triangles(f, i, j, k, 0.1, h))
