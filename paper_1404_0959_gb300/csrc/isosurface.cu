@@ -28,10 +28,8 @@
 namespace fe {
 
 constexpr int ISO_THREADS = 256;
-constexpr int ISO_PER_THREAD = 16;
+constexpr int ISO_PER_THREAD = 1;
 constexpr int ISO_CH = ISO_THREADS * ISO_PER_THREAD;  // cubes per emit block
-
-__constant__ int kTet[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7}, {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
 
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -52,38 +50,101 @@ __device__ __forceinline__ void cube_values(const T* f, int N, long c, double (&
   }
 }
 
-__device__ __forceinline__ int tet_count(const double (&v)[8], int t, double iso) {
-  int n = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) n += v[kTet[t][q]] > iso ? 1 : 0;
+template <int A, int B, int C, int D>
+__device__ __forceinline__ int tet_count(const double (&v)[8], double iso) {
+  const int n = (v[A] > iso) + (v[B] > iso) + (v[C] > iso) + (v[D] > iso);
   return (n == 1 || n == 3) ? 1 : (n == 2 ? 2 : 0);
 }
 
-// edge point between corners a and b, from the lower one
-__device__ __forceinline__ void edge_pt(const double (&v)[8], int i, int j, int k, double h, double iso, int a,
-                                        int b, double* p) {
+__device__ __forceinline__ int cube_count(const double (&v)[8], double iso) {
+  return tet_count<0, 1, 3, 7>(v, iso) + tet_count<0, 1, 5, 7>(v, iso) + tet_count<0, 2, 3, 7>(v, iso) +
+         tet_count<0, 2, 6, 7>(v, iso) + tet_count<0, 4, 5, 7>(v, iso) + tet_count<0, 4, 6, 7>(v, iso);
+}
+
+// edge point between corners a and b (values fa, fb), from the lower one
+__device__ __forceinline__ void edge_pt(double fa, double fb, int i, int j, int k, double h, double iso, int a, int b,
+                                        double& px, double& py, double& pz) {
   if (b < a) {
     const int s = a;
     a = b;
     b = s;
+    const double t = fa;
+    fa = fb;
+    fb = t;
   }
-  const double t = (iso - v[a]) / sub(v[b], v[a]);
-  const int ia[3] = {i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1)};
-  const int ib[3] = {i + (b & 1), j + ((b >> 1) & 1), k + ((b >> 2) & 1)};
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const double pa = mul((double)ia[q] + 0.5, h), pb = mul((double)ib[q] + 0.5, h);
-    p[q] = add(pa, mul(t, sub(pb, pa)));
-  }
+  const double t = (iso - fa) / sub(fb, fa);
+  const double ax = mul((double)(i + (a & 1)) + 0.5, h), bx = mul((double)(i + (b & 1)) + 0.5, h);
+  const double ay = mul((double)(j + ((a >> 1) & 1)) + 0.5, h), by = mul((double)(j + ((b >> 1) & 1)) + 0.5, h);
+  const double az = mul((double)(k + ((a >> 2) & 1)) + 0.5, h), bz = mul((double)(k + ((b >> 2) & 1)) + 0.5, h);
+  px = add(ax, mul(t, sub(bx, ax)));
+  py = add(ay, mul(t, sub(by, ay)));
+  pz = add(az, mul(t, sub(bz, az)));
 }
 
-__device__ __forceinline__ double tri_area(const double* p) {
+__device__ __forceinline__ double tri_area(const double (&p)[9]) {
   const double e1[3] = {p[3] - p[0], p[4] - p[1], p[5] - p[2]};
   const double e2[3] = {p[6] - p[0], p[7] - p[1], p[8] - p[2]};
   const double c0 = e1[1] * e2[2] - e1[2] * e2[1];
   const double c1 = e1[2] * e2[0] - e1[0] * e2[2];
   const double c2 = e1[0] * e2[1] - e1[1] * e2[0];
   return 0.5 * sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+__device__ __forceinline__ void put_tri(const double (&p)[9], double* tri, long long& off, long long max_tri,
+                                        double& area) {
+  area += tri_area(p);
+  if (tri && off < max_tri) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) tri[off * 9 + q] = p[q];
+  }
+  ++off;
+}
+
+// value and corner bit of tetrahedron corner q (0..3), selected without indexing
+template <int A, int B, int C, int D>
+__device__ __forceinline__ double tv(const double (&v)[8], int q) {
+  return q == 0 ? v[A] : (q == 1 ? v[B] : (q == 2 ? v[C] : v[D]));
+}
+template <int A, int B, int C, int D>
+__device__ __forceinline__ int tb(int q) {
+  return q == 0 ? A : (q == 1 ? B : (q == 2 ? C : D));
+}
+
+// the triangles of one tetrahedron (corners A, B, C, D in order), as defined above
+template <int A, int B, int C, int D>
+__device__ __forceinline__ void tet_emit(const double (&v)[8], int i, int j, int k, double h, double iso,
+                                         double* tri, long long& off, long long max_tri, double& area) {
+  const int in0 = v[A] > iso, in1 = v[B] > iso, in2 = v[C] > iso, in3 = v[D] > iso;
+  const int n = in0 + in1 + in2 + in3;
+  if (n == 0 || n == 4) return;
+  const int ins = in0 | (in1 << 1) | (in2 << 2) | (in3 << 3);
+  double p[9];
+  auto P = [&](int qa, int qb, int slot) {
+    edge_pt(tv<A, B, C, D>(v, qa), tv<A, B, C, D>(v, qb), i, j, k, h, iso, tb<A, B, C, D>(qa), tb<A, B, C, D>(qb),
+            p[3 * slot], p[3 * slot + 1], p[3 * slot + 2]);
+  };
+  if (n == 1 || n == 3) {
+    const int lonemask = n == 1 ? ins : (~ins & 15);
+    const int lone = __ffs(lonemask) - 1;
+    // the other three corners in tetrahedron order
+    const int r0 = lone == 0 ? 1 : 0, r1 = lone <= 1 ? 2 : 1, r2 = lone <= 2 ? 3 : 2;
+    P(lone, r0, 0);
+    P(lone, r1, 1);
+    P(lone, r2, 2);
+    put_tri(p, tri, off, max_tri, area);
+  } else {
+    const int a = __ffs(ins) - 1, b = __ffs(ins & ~(1 << a)) - 1;
+    const int outm = ~ins & 15;
+    const int c = __ffs(outm) - 1, d = __ffs(outm & ~(1 << c)) - 1;
+    P(a, c, 0);
+    P(a, d, 1);
+    P(b, d, 2);
+    put_tri(p, tri, off, max_tri, area);
+    P(a, c, 0);
+    P(b, d, 1);
+    P(b, c, 2);
+    put_tri(p, tri, off, max_tri, area);
+  }
 }
 
 template <typename T>
@@ -94,10 +155,7 @@ __global__ void __launch_bounds__(ISO_THREADS) k_iso_count(const T* __restrict__
     double v[8];
     int i, j, k;
     cube_values<T>(f, N, c, v, i, j, k);
-    int s = 0;
-#pragma unroll
-    for (int t = 0; t < 6; ++t) s += tet_count(v, t, iso);
-    counts[c] = s;
+    counts[c] = cube_count(v, iso);
   }
 }
 
@@ -152,43 +210,12 @@ __global__ void __launch_bounds__(ISO_THREADS) k_iso_emit(const T* __restrict__ 
     double v[8];
     int i, j, k;
     cube_values<T>(f, N, c, v, i, j, k);
-    for (int t = 0; t < 6; ++t) {
-      int ins[4], outs[4], ni = 0, no = 0;
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const int b = kTet[t][qq];
-        if (v[b] > iso) ins[ni++] = b;
-        else outs[no++] = b;
-      }
-      double p[2][9];
-      int nt = 0;
-      if (ni == 1 || ni == 3) {
-        const int lone = ni == 1 ? ins[0] : outs[0];
-        int rest[3], nr = 0;
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-          if (kTet[t][qq] != lone) rest[nr++] = kTet[t][qq];
-        edge_pt(v, i, j, k, h, iso, lone, rest[0], p[0]);
-        edge_pt(v, i, j, k, h, iso, lone, rest[1], p[0] + 3);
-        edge_pt(v, i, j, k, h, iso, lone, rest[2], p[0] + 6);
-        nt = 1;
-      } else if (ni == 2) {
-        const int a = ins[0], b = ins[1], cc = outs[0], d = outs[1];
-        edge_pt(v, i, j, k, h, iso, a, cc, p[0]);
-        edge_pt(v, i, j, k, h, iso, a, d, p[0] + 3);
-        edge_pt(v, i, j, k, h, iso, b, d, p[0] + 6);
-        edge_pt(v, i, j, k, h, iso, a, cc, p[1]);
-        edge_pt(v, i, j, k, h, iso, b, d, p[1] + 3);
-        edge_pt(v, i, j, k, h, iso, b, cc, p[1] + 6);
-        nt = 2;
-      }
-      for (int e = 0; e < nt; ++e) {
-        area += tri_area(p[e]);
-        if (tri && off < max_tri)
-          for (int qq = 0; qq < 9; ++qq) tri[off * 9 + qq] = p[e][qq];
-        ++off;
-      }
-    }
+    tet_emit<0, 1, 3, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
+    tet_emit<0, 1, 5, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
+    tet_emit<0, 2, 3, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
+    tet_emit<0, 2, 6, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
+    tet_emit<0, 4, 5, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
+    tet_emit<0, 4, 6, 7>(v, i, j, k, h, iso, tri, off, max_tri, area);
   }
   red[threadIdx.x] = area;
   __syncthreads();
@@ -207,7 +234,24 @@ __global__ void k_fill_u64(unsigned long long* a, long n, unsigned long long v) 
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) a[q] = v;
 }
 
-// one thread per triangle; depth bits of z >= 0 are ordered like z
+// Edge function in FP32 from FP32 copies of the coordinates, with a bound on
+// its distance from the exact value of the FP64 inputs: each input is within
+// 2^-24 relative of its double, each difference, product and the final
+// subtraction add one rounding; 2^-20 (16 units) of the magnitude of the
+// two products covers them all.
+__device__ __forceinline__ float edge_fn32(float xa, float ya, float xb, float yb, float px, float py, float& bound) {
+  const float p1 = (xb - xa) * (py - ya), p2 = (yb - ya) * (px - xa);
+  bound = (fabsf(p1) + fabsf(p2)) * 9.5367431640625e-07f + 1e-37f;
+  return p1 - p2;
+}
+
+// sign of a filtered edge function: +1 / -1 when certain, 0 when the exact test decides
+__device__ __forceinline__ int certain_sign(float e, float bound) { return e > bound ? 1 : (e < -bound ? -1 : 0); }
+
+// one thread per triangle; depth bits of z >= 0 are ordered like z.  Every
+// coverage decision equals the exact-rounding FP64 test: FP32 decides only
+// when all three signs are certain (covered: one sign; not covered: two
+// opposite certain signs), otherwise the FP64 edge functions decide.
 __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict__ tri, long long ntri, int W,
                                                         double step, unsigned long long* __restrict__ depth) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ntri;
@@ -215,22 +259,44 @@ __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict
     const double* p = tri + q * 9;
     const double x0 = p[0], y0 = p[1], z0 = p[2], x1 = p[3], y1 = p[4], z1 = p[5], x2 = p[6], y2 = p[7], z2 = p[8];
     if (edge_fn(x0, y0, x1, y1, x2, y2) == 0.0) continue;
+    const float fx0 = (float)x0, fy0 = (float)y0, fx1 = (float)x1, fy1 = (float)y1, fx2 = (float)x2, fy2 = (float)y2;
+    // a lower bound of any depth the barycentric formula can give inside the triangle (a convex
+    // combination of the corners, a few roundings below its smallest corner at most)
+    const double zlow = fmin(z0, fmin(z1, z2)) - 1e-12 * fmax(z0, fmax(z1, z2));
     const int lo_x = max((int)floor(fmin(x0, fmin(x1, x2)) / step - 0.5) - 1, 0);
     const int hi_x = min((int)ceil(fmax(x0, fmax(x1, x2)) / step - 0.5) + 1, W - 1);
     const int lo_y = max((int)floor(fmin(y0, fmin(y1, y2)) / step - 0.5) - 1, 0);
     const int hi_y = min((int)ceil(fmax(y0, fmax(y1, y2)) / step - 0.5) + 1, W - 1);
     for (int py = lo_y; py <= hi_y; ++py) {
       const double cy = mul((double)py + 0.5, step);
+      const float fcy = (float)cy;
       for (int px = lo_x; px <= hi_x; ++px) {
         const double cx = mul((double)px + 0.5, step);
-        const double e12 = edge_fn(x1, y1, x2, y2, cx, cy);
-        const double e20 = edge_fn(x2, y2, x0, y0, cx, cy);
-        const double e01 = edge_fn(x0, y0, x1, y1, cx, cy);
-        if ((e12 >= 0.0 && e20 >= 0.0 && e01 >= 0.0) || (e12 <= 0.0 && e20 <= 0.0 && e01 <= 0.0)) {
-          const double num = add(add(mul(e12, z0), mul(e20, z1)), mul(e01, z2));
-          const double z = num / add(add(e12, e20), e01);
-          if (z >= 0.0) atomicMin(&depth[(long)py * W + px], (unsigned long long)__double_as_longlong(z));
+        const float fcx = (float)cx;
+        float b12, b20, b01;
+        const int s12 = certain_sign(edge_fn32(fx1, fy1, fx2, fy2, fcx, fcy, b12), b12);
+        const int s20 = certain_sign(edge_fn32(fx2, fy2, fx0, fy0, fcx, fcy, b20), b20);
+        const int s01 = certain_sign(edge_fn32(fx0, fy0, fx1, fy1, fcx, fcy, b01), b01);
+        const bool pos = s12 > 0 || s20 > 0 || s01 > 0, neg = s12 < 0 || s20 < 0 || s01 < 0;
+        if (pos && neg) continue;  // certainly outside
+        double e12 = 0.0, e20 = 0.0, e01 = 0.0;
+        if (s12 == 0 || s20 == 0 || s01 == 0) {  // a near-tie: the exact-rounding test decides
+          e12 = edge_fn(x1, y1, x2, y2, cx, cy);
+          e20 = edge_fn(x2, y2, x0, y0, cx, cy);
+          e01 = edge_fn(x0, y0, x1, y1, cx, cy);
+          if (!((e12 >= 0.0 && e20 >= 0.0 && e01 >= 0.0) || (e12 <= 0.0 && e20 <= 0.0 && e01 <= 0.0))) continue;
+        } else {
+          e12 = edge_fn(x1, y1, x2, y2, cx, cy);
+          e20 = edge_fn(x2, y2, x0, y0, cx, cy);
+          e01 = edge_fn(x0, y0, x1, y1, cx, cy);
         }
+        // a triangle whose nearest corner is behind the stored depth cannot lower it
+        unsigned long long* slot = &depth[(long)py * W + px];
+        const double cur = __longlong_as_double((long long)*((volatile unsigned long long*)slot));
+        if (zlow > cur) continue;
+        const double num = add(add(mul(e12, z0), mul(e20, z1)), mul(e01, z2));
+        const double z = num / add(add(e12, e20), e01);
+        if (z >= 0.0 && z < cur) atomicMin(slot, (unsigned long long)__double_as_longlong(z));
       }
     }
   }

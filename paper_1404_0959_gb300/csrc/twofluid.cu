@@ -27,7 +27,22 @@ __device__ __forceinline__ T* TF(const BoxDev& B, int slot) {
   return reinterpret_cast<T*>(B.f[slot]);
 }
 
-// D(F) and D(G_m) of one class at one cell: gas (rho, u, phi), dust (Y, V)
+// Five values of f along d around the cell (offsets -2..2)
+template <typename T>
+__device__ __forceinline__ void tf_win(const T* f, const Nbr& n, int d, T (&w)[5]) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) w[q] = __ldg(&f[n.at(d, 0, 0, 0, q - 2)]);
+}
+
+// fourth-order interpolation to the face between window entries a+1 and a+2 (a = 0: minus face,
+// a = 1: plus face), the same formula as I4f
+template <typename T>
+__device__ __forceinline__ T tf_i4(const T (&w)[5], int a) {
+  return (T(9) * (w[a + 1] + w[a + 2]) - (w[a] + w[a + 3])) * T(0.0625);
+}
+
+// D(F) and D(G_m) of one class at one cell: gas (rho, u, phi), dust (Y, V).  Per direction one
+// five-point window of each field gives both faces.
 template <typename T>
 __device__ __forceinline__ void tf_div(const T* rho, const T* const (&u)[3], const T* const (&phi)[3], const T* Y,
                                        const T* const (&V)[3], const Nbr& n, T ih, T& DF, T (&DG)[3]) {
@@ -35,16 +50,23 @@ __device__ __forceinline__ void tf_div(const T* rho, const T* const (&u)[3], con
   DG[0] = DG[1] = DG[2] = T(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
+    T wr[5], wu[5], wy[5], wv[3][5];
+    tf_win<T>(rho, n, d, wr);
+    tf_win<T>(u[d], n, d, wu);
+    tf_win<T>(Y, n, d, wy);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) tf_win<T>(V[m], n, d, wv[m]);
+    const T php = __ldg(&phi[d][n(0, 0, 0)]);
+    const T phm = __ldg(&phi[d][n(tfx(d), tfy(d), tfz(d))]);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-      const int ox = side ? tfx(d) : 0, oy = side ? tfy(d) : 0, oz = side ? tfz(d) : 0;
+      const int a = side ? 0 : 1;  // plus face: entries 1..4, minus face: 0..3
       const T sgn = side ? T(-1) : T(1);
-      const T ph = __ldg(&phi[d][n(ox, oy, oz)]);
-      const T slip = I4f<T>(V[d], n, d, ox, oy, oz) - I4f<T>(u[d], n, d, ox, oy, oz);
-      const T F = (ph + I4f<T>(rho, n, d, ox, oy, oz) * slip) * I4f<T>(Y, n, d, ox, oy, oz);
+      const T slip = tf_i4<T>(wv[d], a) - tf_i4<T>(wu, a);
+      const T F = ((side ? phm : php) + tf_i4<T>(wr, a) * slip) * tf_i4<T>(wy, a);
       DF += sgn * F;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) DG[m] += sgn * F * I4f<T>(V[m], n, d, ox, oy, oz);
+      for (int m = 0; m < 3; ++m) DG[m] += sgn * F * tf_i4<T>(wv[m], a);
     }
   }
   DF *= ih;
