@@ -234,19 +234,26 @@ __global__ void k_fill_u64(unsigned long long* a, long n, unsigned long long v) 
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) a[q] = v;
 }
 
-// Edge function in FP32 from FP32 copies of the coordinates, with a bound on
-// its distance from the exact value of the FP64 inputs: each input is within
-// 2^-24 relative of its double, each difference, product and the final
-// subtraction add one rounding; 2^-20 (16 units) of the magnitude of the
-// two products covers them all.
-__device__ __forceinline__ float edge_fn32(float xa, float ya, float xb, float yb, float px, float py, float& bound) {
-  const float p1 = (xb - xa) * (py - ya), p2 = (yb - ya) * (px - xa);
-  bound = (fabsf(p1) + fabsf(p2)) * 9.5367431640625e-07f + 1e-37f;
+// Edge function in FP32 from coordinates relative to the triangle's first
+// corner (shifted in FP64, then rounded to FP32, so every value has the size
+// of the triangle), with a bound on its distance from the exact edge function:
+// each shifted coordinate carries one FP32 rounding (relative 2^-24 of at most
+// S, the largest of them), each difference adds one, each product one and the
+// final subtraction one; 8 * 2^-24 (S (|d1| + |d2|) over both products + |p1|
+// + |p2|) covers them with room, and the FP64 shift adds far less.
+__device__ __forceinline__ float edge_fn32(float xa, float ya, float xb, float yb, float px, float py, float S,
+                                           float& bound) {
+  const float d1 = xb - xa, d2 = py - ya, d3 = yb - ya, d4 = px - xa;
+  const float p1 = d1 * d2, p2 = d3 * d4;
+  bound = 4.76837158203125e-07f * (S * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4)) + fabsf(p1) + fabsf(p2)) +
+          1e-30f;
   return p1 - p2;
 }
 
 // sign of a filtered edge function: +1 / -1 when certain, 0 when the exact test decides
-__device__ __forceinline__ int certain_sign(float e, float bound) { return e > bound ? 1 : (e < -bound ? -1 : 0); }
+__device__ __forceinline__ int certain_sign(float e, float bound) {
+  return e > 2.f * bound ? 1 : (e < -2.f * bound ? -1 : 0);
+}
 
 // one thread per triangle; depth bits of z >= 0 are ordered like z.  Every
 // coverage decision equals the exact-rounding FP64 test: FP32 decides only
@@ -259,7 +266,9 @@ __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict
     const double* p = tri + q * 9;
     const double x0 = p[0], y0 = p[1], z0 = p[2], x1 = p[3], y1 = p[4], z1 = p[5], x2 = p[6], y2 = p[7], z2 = p[8];
     if (edge_fn(x0, y0, x1, y1, x2, y2) == 0.0) continue;
-    const float fx0 = (float)x0, fy0 = (float)y0, fx1 = (float)x1, fy1 = (float)y1, fx2 = (float)x2, fy2 = (float)y2;
+    // FP32 copies relative to corner 0 (the shift itself in FP64)
+    const float fx0 = 0.f, fy0 = 0.f, fx1 = (float)(x1 - x0), fy1 = (float)(y1 - y0), fx2 = (float)(x2 - x0),
+                fy2 = (float)(y2 - y0);
     // a lower bound of any depth the barycentric formula can give inside the triangle (a convex
     // combination of the corners, a few roundings below its smallest corner at most)
     const double zlow = fmin(z0, fmin(z1, z2)) - 1e-12 * fmax(z0, fmax(z1, z2));
@@ -269,14 +278,16 @@ __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict
     const int hi_y = min((int)ceil(fmax(y0, fmax(y1, y2)) / step - 0.5) + 1, W - 1);
     for (int py = lo_y; py <= hi_y; ++py) {
       const double cy = mul((double)py + 0.5, step);
-      const float fcy = (float)cy;
+      const float fcy = (float)(cy - y0);
       for (int px = lo_x; px <= hi_x; ++px) {
         const double cx = mul((double)px + 0.5, step);
-        const float fcx = (float)cx;
+        const float fcx = (float)(cx - x0);
+        const float S = fmaxf(fmaxf(fmaxf(fabsf(fx1), fabsf(fy1)), fmaxf(fabsf(fx2), fabsf(fy2))),
+                              fmaxf(fabsf(fcx), fabsf(fcy)));
         float b12, b20, b01;
-        const int s12 = certain_sign(edge_fn32(fx1, fy1, fx2, fy2, fcx, fcy, b12), b12);
-        const int s20 = certain_sign(edge_fn32(fx2, fy2, fx0, fy0, fcx, fcy, b20), b20);
-        const int s01 = certain_sign(edge_fn32(fx0, fy0, fx1, fy1, fcx, fcy, b01), b01);
+        const int s12 = certain_sign(edge_fn32(fx1, fy1, fx2, fy2, fcx, fcy, S, b12), b12);
+        const int s20 = certain_sign(edge_fn32(fx2, fy2, fx0, fy0, fcx, fcy, S, b20), b20);
+        const int s01 = certain_sign(edge_fn32(fx0, fy0, fx1, fy1, fcx, fcy, S, b01), b01);
         const bool pos = s12 > 0 || s20 > 0 || s01 > 0, neg = s12 < 0 || s20 < 0 || s01 < 0;
         if (pos && neg) continue;  // certainly outside
         double e12 = 0.0, e20 = 0.0, e01 = 0.0;

@@ -13,8 +13,9 @@
 //
 // Passes over HBM (N^3 words each): x pass reads rho, u (4) and writes the ten
 // x-filtered quantities (rho, rho u_i, rho u_i u_j); y and z passes read ten
-// and write ten; the Favre velocity reads four and writes three; the
-// statistics pass reads thirteen.  74 words per cell in all.
+// and write ten (each thread eight consecutive outputs from a register window
+// when N is a multiple of eight and m <= 4); the Favre velocity reads four and
+// writes three; the statistics pass reads thirteen.  74 words per cell in all.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -91,6 +92,39 @@ __global__ void __launch_bounds__(LES_THREADS) k_les_line(LesPtrs<T> in, LesPtrs
     }
 #pragma unroll
     for (int q = 0; q < LES_NF; ++q) out.f[q][c] = acc[q];
+  }
+}
+
+// y (axis 1) or z (axis 2) pass with a register window: each thread makes LES_OUTS consecutive outputs
+// along the axis from LES_OUTS + 2M loads per field (N a multiple of LES_OUTS); the weighted sum of
+// each output runs over the offsets -M..M in order, as in k_les_line.
+constexpr int LES_OUTS = 8;
+template <typename T, int M>
+__global__ void __launch_bounds__(LES_THREADS) k_les_win(LesPtrs<T> in, LesPtrs<T> out, int N, int axis) {
+  const long nb = (long)N * N * (N / LES_OUTS);
+  const long stride = axis == 1 ? N : (long)N * N;
+  const T w = T(1) / T(2 * M), we = T(0.5) * w;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < nb; q += (long)gridDim.x * blockDim.x) {
+    // q = i + N (a + N b): axis 1: (i, jb = a, k = b); axis 2: (i, j = a, kb = b)
+    const long i = q % N, a = (q / N) % N, b = q / ((long)N * N);
+    const long blk = axis == 1 ? a : b;
+    const long base = axis == 1 ? i + (long)N * (long)N * b : i + (long)N * a;
+    const long p0 = blk * LES_OUTS;
+#pragma unroll
+    for (int f = 0; f < LES_NF; ++f) {  // unrolled: the field pointers stay in registers
+      const T* src = in.f[f];
+      T win[LES_OUTS + 2 * M];
+#pragma unroll
+      for (int t = 0; t < LES_OUTS + 2 * M; ++t) win[t] = src[base + les_wrap(p0 - M + t, N) * stride];
+      T* dst = out.f[f];
+#pragma unroll
+      for (int o = 0; o < LES_OUTS; ++o) {
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t <= 2 * M; ++t) acc += ((t == 0 || t == 2 * M) ? we : w) * win[o + t];
+        dst[base + (p0 + o) * stride] = acc;
+      }
+    }
   }
 }
 
@@ -227,8 +261,22 @@ int les_apriori(const T* rho, const T* u0, const T* u1, const T* u2, int N, int 
   T* ut = work + 2 * LES_NF * n;
   const int grid = les_grid(n, nsm);
   k_les_x<T><<<grid, LES_THREADS, 0, st>>>(rho, u0, u1, u2, N, m, A);
-  k_les_line<T><<<grid, LES_THREADS, 0, st>>>(A, Bp, N, m, 1);
-  k_les_line<T><<<grid, LES_THREADS, 0, st>>>(Bp, A, N, m, 2);
+  if (N % LES_OUTS == 0 && m <= 4) {
+    const int gw = les_grid(n / LES_OUTS, nsm);
+    for (int axis = 1; axis <= 2; ++axis) {
+      const LesPtrs<T>& src = axis == 1 ? A : Bp;
+      const LesPtrs<T>& dst = axis == 1 ? Bp : A;
+      switch (m) {
+        case 1: k_les_win<T, 1><<<gw, LES_THREADS, 0, st>>>(src, dst, N, axis); break;
+        case 2: k_les_win<T, 2><<<gw, LES_THREADS, 0, st>>>(src, dst, N, axis); break;
+        case 3: k_les_win<T, 3><<<gw, LES_THREADS, 0, st>>>(src, dst, N, axis); break;
+        default: k_les_win<T, 4><<<gw, LES_THREADS, 0, st>>>(src, dst, N, axis); break;
+      }
+    }
+  } else {
+    k_les_line<T><<<grid, LES_THREADS, 0, st>>>(A, Bp, N, m, 1);
+    k_les_line<T><<<grid, LES_THREADS, 0, st>>>(Bp, A, N, m, 2);
+  }
   k_les_favre<T><<<grid, LES_THREADS, 0, st>>>(A, ut, ut + n, ut + 2 * n, n);
   const double h = 2.0 * M_PI / N, delta = 2.0 * m * h;
   k_les_stats<T><<<grid, LES_THREADS, 0, st>>>(A, ut, ut + n, ut + 2 * n, N, 1.0 / h, delta, part, out);
