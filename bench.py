@@ -321,6 +321,42 @@ def unet_flops(N):
     return 2.0 * macs
 
 
+def time_ensemble(fe, args, compare=False):
+    """The 64-box ensemble of uneven boxes (N in {32, 48, 64, 96}, FP32 fields, barotropic) in one context:
+    one launch per stage over every box, CUDA-graph steps, autotuned tiles; with compare, the same boxes
+    each in a context of its own stepped one after the other (same steps, same state)."""
+    import torch
+    from paper_1404_0959_gb300.inputs import ensemble64_boxes
+    boxes = ensemble64_boxes(64)
+    cells = float(sum(b["N"] ** 3 for b in boxes))
+    K, W = max(args.steps, 3), max(args.warmup, 3)
+
+    def timed(solver_boxes):
+        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+        s.init_state(-1, fe.FE_INIT_SPECTRAL)
+        s.autotune(2)
+        s.use_graphs(True)
+        code, _ = s.step(W)
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        code, _ = s.step(K)
+        ev1.record()
+        torch.cuda.synchronize()
+        assert code == fe.FE_OK, fe.fe_strerror(code)
+        s.close()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    t_ens = timed(boxes)
+    out = {"boxes": len(boxes), "cells": int(cells), "steps": K, "ms_per_step": 1e3 * t_ens / K,
+           "value": cells * K / t_ens, "unit": "cell-steps/s"}
+    if compare:
+        t_one = sum(timed([b]) for b in boxes)
+        out["per_box_contexts"] = {"value": cells * K / t_one, "ms_per_step": 1e3 * t_one / K}
+    return out
+
+
 def ensemble_only(args):
     """--ensemble: the 64-box ensemble of uneven boxes (N in {32, 48, 64, 96}, FP32 fields) stepped in
     one context -- one launch per stage over every box, CUDA graph, autotuned tiles -- against the
@@ -420,7 +456,7 @@ def part_only(args):
         n, area = fe.fe_isosurface(s.ctx, 0, q.data_ptr(), iso)
         tri = torch.empty((n, 9), dtype=torch.float64, device="cuda")
         W = args.width
-        depth = torch.empty((W, W), dtype=torch.float64, device="cuda")
+        depth = torch.empty((W, W), dtype=torch.float32, device="cuda")
         h = 2 * math.pi / N
         for _ in range(args.warmup):
             fe.fe_isosurface(s.ctx, 0, q.data_ptr(), iso, tri.data_ptr(), n)
@@ -671,6 +707,7 @@ def main():
         extra["learned_fp32_every_iteration"], _ = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args,
                                                              stream, 1, wts)
         extra["les_apriori_fp32"] = time_les(fe, box, cfg, args, stream)
+        extra["ensemble64_fp32"] = time_ensemble(fe, args)
         # break-even: a network application against the CG iterations it would have to save
         if share:
             per = lambda k: share[k][0] / share[k][1] if share.get(k, (0, 0))[1] else 0.0

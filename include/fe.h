@@ -258,20 +258,24 @@ int fe_q_criterion(fe_ctx* ctx, int box, void* q_dev);
  * The surface is closed (the split is the same in every cube).  tri: NULL
  * (max_tri = 0) or a device array of 9 * max_tri doubles (x, y, z of the three
  * corners); the first min(total, max_tri) triangles are written.  *ntri
- * receives the total count, *area the total area.  Work memory (N^3 ints) is
- * allocated on the first call and kept by the context. */
+ * receives the total count, *area the total area.  Work memory (16 bytes per
+ * cell) is allocated on the first call and kept by the context. */
 int fe_isosurface(fe_ctx* ctx, int box, const void* field, double iso, double* tri, long long max_tri,
                   long long* ntri, double* area);
 /* Depth image of ntri triangles (device, 9 doubles each) viewed along +z
- * (orthographic) on width x width pixels covering [0, extent)^2: pixel (px,
- * py) has centre ((px + 1/2), (py + 1/2)) extent / width and is covered by a
- * triangle when its three edge functions E_ab = (x_b - x_a)(y - y_a) -
- * (y_b - y_a)(x - x_a) share a sign (a triangle with E_01(p2) = 0 covers
- * nothing); depth (E_12 z_0 + E_20 z_1 + E_01 z_2) / (E_12 + E_20 + E_01),
- * the smallest non-negative depth kept, +inf where nothing is covered.
- * depth: device array of width^2 doubles, row py * width + px.  Each step is
- * one correctly rounded double operation in this order. */
-int fe_raster_depth(fe_ctx* ctx, const double* tri, long long ntri, int width, double extent, double* depth);
+ * (orthographic) on width x width pixels covering [0, extent)^2, in single
+ * precision as rasterisers work: pixel (px, py) has centre c = ((px + 1/2),
+ * (py + 1/2)) extent / width (double); per triangle the corners relative to
+ * the first one are rounded to FP32 (X_q = f32(x_q - x_0), ..., X_0 = Y_0 =
+ * 0, Z_q = f32(z_q)) and per pixel CX = f32(c_x - x_0), CY = f32(c_y - y_0);
+ * the pixel is covered when E_12, E_20, E_01, with E_ab = (X_b - X_a)(CY -
+ * Y_a) - (Y_b - Y_a)(CX - X_a) in FP32, share a sign (a triangle with
+ * X_1 Y_2 - Y_1 X_2 = 0 covers nothing); depth ((E_12 Z_0 + E_20 Z_1) +
+ * E_01 Z_2) / ((E_12 + E_20) + E_01) in FP32, the smallest non-negative depth
+ * kept, +inf where nothing is covered.  depth: device array of width^2 floats,
+ * row py * width + px.  Each step is one correctly rounded operation in this
+ * order. */
+int fe_raster_depth(fe_ctx* ctx, const double* tri, long long ntri, int width, double extent, float* depth);
 
 /* A-priori analysis for large-eddy simulation (Sec. 1 names LES of the plume
  * as the goal of the DNS; Sec. 2 the a-priori use of the DNS database; the

@@ -22,13 +22,17 @@ rendering itself (a graphics API) is not reproduced; what it computes is:
   edge's lower corner (smaller b): p = p_lo + t (p_hi - p_lo),
   t = (iso - f_lo) / (f_hi - f_lo).  Triangles are listed cube by cube (flat
   cube index i + N (j + N k)), tetrahedra in the order above.
-* Rasterisation: orthographic view along +z of the square [0, L)^2 on W x W
-  pixels (pixel centres ((p + 1/2) L / W)), z-buffer keeping the smallest z.
-  A pixel centre P is covered when the three edge functions
-  E_ab(P) = (x_b - x_a)(P_y - y_a) - (y_b - y_a)(P_x - x_a) are all >= 0 or
-  all <= 0 and the triangle's doubled area E_01(p2) is not zero; its depth is
-  (E_12 z_0 + E_20 z_1 + E_01 z_2) / (E_12 + E_20 + E_01).  Empty pixels hold
-  +inf.  Every step is a sequence of single IEEE operations in this order, so
+* Rasterisation (single precision, as rasterisers work): orthographic view
+  along +z of the square [0, L)^2 on W x W pixels (pixel centres
+  c = (p + 1/2) L / W in double), z-buffer keeping the smallest z.  Per
+  triangle the corners relative to the first one are rounded to FP32
+  (X_q = f32(x_q - x_0), Y_q likewise, X_0 = Y_0 = 0; Z_q = f32(z_q)), and
+  per pixel the centre likewise (CX = f32(c_x - x_0), CY = f32(c_y - y_0)).
+  With E_ab = (X_b - X_a)(CY - Y_a) - (Y_b - Y_a)(CX - X_a) in FP32, the pixel
+  is covered when E_12, E_20, E_01 are all >= 0 or all <= 0 and the doubled
+  area (X_1 Y_2 - Y_1 X_2, FP32) is not zero; its depth is
+  ((E_12 Z_0 + E_20 Z_1) + E_01 Z_2) / ((E_12 + E_20) + E_01) in FP32.
+  Empty pixels hold +inf.  Every step is one IEEE operation in this order, so
   an implementation that rounds each operation gives the same bits.
 
 Parity pins (tests/test_oracle_isosurface.py): the zero set of cos z (two
@@ -106,29 +110,33 @@ def _edge(xa, ya, xb, yb, px, py):
 
 
 def raster_depth(T, width, extent):
-    """z-buffer depth image (width x width, [y, x]) of triangles T viewed along +z."""
-    img = np.full((width, width), np.inf)
+    """z-buffer depth image (width x width, [y, x], float32) of triangles T viewed along +z."""
+    f32 = np.float32
+    img = np.full((width, width), np.inf, dtype=np.float32)
     step = extent / width
+    zero = f32(0.0)
     for tri in T:
-        x0, y0, z0 = tri[0]
-        x1, y1, z1 = tri[1]
-        x2, y2, z2 = tri[2]
-        den = _edge(x0, y0, x1, y1, x2, y2)
-        if den == 0.0:
+        x0, y0, z0 = (float(v) for v in tri[0])
+        X1, Y1 = f32(tri[1][0] - x0), f32(tri[1][1] - y0)
+        X2, Y2 = f32(tri[2][0] - x0), f32(tri[2][1] - y0)
+        Z0, Z1, Z2 = f32(tri[0][2]), f32(tri[1][2]), f32(tri[2][2])
+        if X1 * Y2 - Y1 * X2 == zero:
             continue
-        lo_x = max(int(np.floor(min(x0, x1, x2) / step - 0.5)) - 1, 0)
-        hi_x = min(int(np.ceil(max(x0, x1, x2) / step - 0.5)) + 1, width - 1)
-        lo_y = max(int(np.floor(min(y0, y1, y2) / step - 0.5)) - 1, 0)
-        hi_y = min(int(np.ceil(max(y0, y1, y2) / step - 0.5)) + 1, width - 1)
+        xs = (tri[0][0], tri[1][0], tri[2][0])
+        ys = (tri[0][1], tri[1][1], tri[2][1])
+        lo_x = max(int(np.floor(min(xs) / step - 0.5)) - 1, 0)
+        hi_x = min(int(np.ceil(max(xs) / step - 0.5)) + 1, width - 1)
+        lo_y = max(int(np.floor(min(ys) / step - 0.5)) - 1, 0)
+        hi_y = min(int(np.ceil(max(ys) / step - 0.5)) + 1, width - 1)
         for py in range(lo_y, hi_y + 1):
-            cy = (py + 0.5) * step
+            CY = f32((py + 0.5) * step - y0)
             for px in range(lo_x, hi_x + 1):
-                cx = (px + 0.5) * step
-                e12 = _edge(x1, y1, x2, y2, cx, cy)
-                e20 = _edge(x2, y2, x0, y0, cx, cy)
-                e01 = _edge(x0, y0, x1, y1, cx, cy)
+                CX = f32((px + 0.5) * step - x0)
+                e12 = _edge(X1, Y1, X2, Y2, CX, CY)
+                e20 = _edge(X2, Y2, zero, zero, CX, CY)
+                e01 = _edge(zero, zero, X1, Y1, CX, CY)
                 if (e12 >= 0 and e20 >= 0 and e01 >= 0) or (e12 <= 0 and e20 <= 0 and e01 <= 0):
-                    z = (e12 * z0 + e20 * z1 + e01 * z2) / (e12 + e20 + e01)
+                    z = ((e12 * Z0 + e20 * Z1) + e01 * Z2) / ((e12 + e20) + e01)
                     if z < img[py, px]:
                         img[py, px] = z
     return img

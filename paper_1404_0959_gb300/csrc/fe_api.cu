@@ -29,11 +29,10 @@ int les_apriori(const T* rho, const T* u0, const T* u1, const T* u2, int N, int 
                 double* hpart, int nsm, T* out, double* stats, cudaStream_t st);
 int les_max_blocks(int nsm);
 template <typename T>
-int isosurface(const T* f, int N, double iso, double* tri, long long max_tri, int* counts, long long* bsum,
-               long long* boff, double* apart, std::vector<double>& hscratch, int nsm, long long* ntri, double* area,
-               cudaStream_t st);
-long iso_blocks(long n);
-int raster_depth(const double* tri, long long ntri, int W, double extent, double* depth, int nsm, cudaStream_t st);
+int isosurface(const T* f, int N, double iso, double* tri, long long max_tri, void* work,
+               std::vector<double>& hscratch, int nsm, long long* ntri, double* area, cudaStream_t st);
+size_t iso_work_bytes(long n);
+int raster_depth(const double* tri, long long ntri, int W, double extent, float* depth, int nsm, cudaStream_t st);
 UNet* unet_create(int N, bool training, int* rc);
 void unet_destroy(UNet* U);
 long unet_param_count();
@@ -1511,8 +1510,8 @@ extern "C" int fe_isosurface(fe_ctx* c, int box, const void* field, double iso, 
       !std::isfinite(iso))
     return FE_ERR_INVALID_ARG;
   const int N = c->N[box];
-  const long n = (long)N * N * N, nb = iso_blocks(n);
-  const size_t need = (size_t)n * sizeof(int) + (size_t)nb * (2 * sizeof(long long) + sizeof(double)) + 256;
+  const long n = (long)N * N * N;
+  const size_t need = iso_work_bytes(n);
   if (c->iso_bytes < need) {
     cudaFree(c->iso_work);
     c->iso_work = nullptr;
@@ -1523,20 +1522,15 @@ extern "C" int fe_isosurface(fe_ctx* c, int box, const void* field, double iso, 
     }
     c->iso_bytes = need;
   }
-  char* w = (char*)c->iso_work;
-  long long* bsum = (long long*)w;
-  long long* boff = bsum + nb;
-  double* apart = (double*)(boff + nb);
-  int* counts = (int*)(apart + nb);
   if (c->fp64)
-    return isosurface<double>((const double*)field, N, iso, tri, max_tri, counts, bsum, boff, apart, c->iso_host,
-                              c->nsm, ntri, area, c->st);
-  return isosurface<float>((const float*)field, N, iso, tri, max_tri, counts, bsum, boff, apart, c->iso_host, c->nsm,
-                           ntri, area, c->st);
+    return isosurface<double>((const double*)field, N, iso, tri, max_tri, c->iso_work, c->iso_host, c->nsm, ntri, area,
+                              c->st);
+  return isosurface<float>((const float*)field, N, iso, tri, max_tri, c->iso_work, c->iso_host, c->nsm, ntri, area,
+                           c->st);
 }
 
 extern "C" int fe_raster_depth(fe_ctx* c, const double* tri, long long ntri, int width, double extent,
-                               double* depth) {
+                               float* depth) {
   if (!c || !depth || width < 1 || width > 65536 || ntri < 0 || (ntri > 0 && !tri) || !(extent > 0.0))
     return FE_ERR_INVALID_ARG;
   int rc = raster_depth(tri, ntri, width, extent, depth, c->nsm, c->st);

@@ -13,13 +13,18 @@
 // cube by cube in flat cube order: a count pass, a scan of the block totals on
 // the host, and an emit pass that scans its block in shared memory.
 //
-// Rasterisation: view along +z, W x W pixel centres ((p + 1/2) L / W), a pixel
-// is covered when its three edge functions share a sign, depth by barycentric
-// weights, z-buffer min through a 64-bit atomicMin on the bits of z >= 0.
+// Rasterisation in single precision: view along +z, W x W pixel centres
+// ((p + 1/2) L / W, in double), coordinates relative to each triangle's first
+// corner rounded to FP32, edge functions and barycentric depth in FP32, a
+// pixel covered when its three edge functions share a sign, z-buffer min
+// through a 32-bit atomicMin on the bits of z >= 0.
 //
 // Every floating-point step is a single rounded IEEE operation in a fixed
-// order (no contraction into FMAs), in double precision for either field type,
-// so the results are those of the same arithmetic done step by step.
+// order (no contraction into FMAs): double precision for the extraction (for
+// either field type), single precision for the image, so the results are those
+// of the same arithmetic done step by step.  The extraction first lists the
+// cut cubes (a second scan, of cut flags) so that its double-precision work
+// runs on full warps.
 #include <cmath>
 #include <vector>
 
@@ -28,8 +33,7 @@
 namespace fe {
 
 constexpr int ISO_THREADS = 256;
-constexpr int ISO_PER_THREAD = 1;
-constexpr int ISO_CH = ISO_THREADS * ISO_PER_THREAD;  // cubes per emit block
+constexpr int ISO_CH = ISO_THREADS;  // cubes per scan block
 
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -159,54 +163,76 @@ __global__ void __launch_bounds__(ISO_THREADS) k_iso_count(const T* __restrict__
   }
 }
 
-// block b: the sum of counts[b * ISO_CH, (b + 1) * ISO_CH)
+// block b: the sums of counts[b * ISO_CH, (b + 1) * ISO_CH) and of the cut flags (count > 0)
 __global__ void __launch_bounds__(ISO_THREADS) k_iso_blocksum(const int* __restrict__ counts, long n,
-                                                              long long* __restrict__ bsum) {
-  __shared__ long long red[ISO_THREADS];
+                                                              long long* __restrict__ bsum,
+                                                              long long* __restrict__ bcut) {
+  __shared__ long long red[ISO_THREADS], redc[ISO_THREADS];
   const long base = (long)blockIdx.x * ISO_CH;
-  long long s = 0;
+  long long s = 0, sc = 0;
   for (int q = threadIdx.x; q < ISO_CH; q += ISO_THREADS) {
     const long c = base + q;
-    if (c < n) s += counts[c];
+    if (c < n) {
+      s += counts[c];
+      sc += counts[c] > 0 ? 1 : 0;
+    }
   }
   red[threadIdx.x] = s;
+  redc[threadIdx.x] = sc;
   __syncthreads();
   for (int o = ISO_THREADS / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      red[threadIdx.x] += red[threadIdx.x + o];
+      redc[threadIdx.x] += redc[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) bsum[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) {
+    bsum[blockIdx.x] = red[0];
+    bcut[blockIdx.x] = redc[0];
+  }
 }
 
-// Emit: thread t of block b owns cubes b*ISO_CH + t*ISO_PER_THREAD + [0, ISO_PER_THREAD)
-// (consecutive), so a block scan of the thread totals orders the triangles by cube.
-template <typename T>
-__global__ void __launch_bounds__(ISO_THREADS) k_iso_emit(const T* __restrict__ f, int N, double iso, double h,
-                                                          const int* __restrict__ counts,
-                                                          const long long* __restrict__ boff,
-                                                          double* __restrict__ tri, long long max_tri,
-                                                          double* __restrict__ apart) {
-  __shared__ long long scan[ISO_THREADS];
-  __shared__ double red[ISO_THREADS];
-  const long n = (long)N * N * N;
-  const long c0 = (long)blockIdx.x * ISO_CH + (long)threadIdx.x * ISO_PER_THREAD;
-  long long mine = 0;
-  for (int q = 0; q < ISO_PER_THREAD; ++q)
-    if (c0 + q < n) mine += counts[c0 + q];
-  scan[threadIdx.x] = mine;
+// List of the cut cubes in flat order with the offset of their first triangle
+// (one cube per thread; block scans of the counts and of the cut flags).
+__global__ void __launch_bounds__(ISO_THREADS) k_iso_compact(const int* __restrict__ counts, long n,
+                                                             const long long* __restrict__ boff,
+                                                             const long long* __restrict__ bcoff,
+                                                             int* __restrict__ list, long long* __restrict__ loff) {
+  __shared__ long long sc[ISO_THREADS], sf[ISO_THREADS];
+  const long c = (long)blockIdx.x * ISO_CH + threadIdx.x;
+  const int mine = c < n ? counts[c] : 0;
+  sc[threadIdx.x] = mine;
+  sf[threadIdx.x] = mine > 0 ? 1 : 0;
   __syncthreads();
-  // inclusive Hillis-Steele scan of the thread totals
   for (int o = 1; o < ISO_THREADS; o <<= 1) {
-    const long long add_o = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+    const long long a = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+    const long long b = threadIdx.x >= o ? sf[threadIdx.x - o] : 0;
     __syncthreads();
-    scan[threadIdx.x] += add_o;
+    sc[threadIdx.x] += a;
+    sf[threadIdx.x] += b;
     __syncthreads();
   }
-  long long off = boff[blockIdx.x] + scan[threadIdx.x] - mine;
+  if (mine > 0) {
+    const long long e = bcoff[blockIdx.x] + sf[threadIdx.x] - 1;
+    list[e] = (int)c;
+    loff[e] = boff[blockIdx.x] + sc[threadIdx.x] - mine;
+  }
+}
+
+// Emit: one thread per cut cube of the list, its triangles from the listed offset.
+template <typename T>
+__global__ void __launch_bounds__(ISO_THREADS) k_iso_emit(const T* __restrict__ f, int N, double iso, double h,
+                                                          const int* __restrict__ list,
+                                                          const long long* __restrict__ loff, long long ncut,
+                                                          double* __restrict__ tri, long long max_tri,
+                                                          double* __restrict__ apart) {
+  __shared__ double red[ISO_THREADS];
+  const long long e = (long long)blockIdx.x * ISO_THREADS + threadIdx.x;
   double area = 0.0;
-  for (int q = 0; q < ISO_PER_THREAD; ++q) {
-    const long c = c0 + q;
-    if (c >= n || counts[c] == 0) continue;
+  if (e < ncut) {
+    const long c = list[e];
+    long long off = loff[e];
     double v[8];
     int i, j, k;
     cube_values<T>(f, N, c, v, i, j, k);
@@ -226,88 +252,44 @@ __global__ void __launch_bounds__(ISO_THREADS) k_iso_emit(const T* __restrict__ 
   if (threadIdx.x == 0) apart[blockIdx.x] = red[0];
 }
 
-__device__ __forceinline__ double edge_fn(double xa, double ya, double xb, double yb, double px, double py) {
-  return sub(mul(sub(xb, xa), sub(py, ya)), mul(sub(yb, ya), sub(px, xa)));
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+
+__device__ __forceinline__ float edge_fn(float xa, float ya, float xb, float yb, float px, float py) {
+  return fsub(fmul(fsub(xb, xa), fsub(py, ya)), fmul(fsub(yb, ya), fsub(px, xa)));
 }
 
-__global__ void k_fill_u64(unsigned long long* a, long n, unsigned long long v) {
+__global__ void k_fill_u32(unsigned* a, long n, unsigned v) {
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) a[q] = v;
 }
 
-// Edge function in FP32 from coordinates relative to the triangle's first
-// corner (shifted in FP64, then rounded to FP32, so every value has the size
-// of the triangle), with a bound on its distance from the exact edge function:
-// each shifted coordinate carries one FP32 rounding (relative 2^-24 of at most
-// S, the largest of them), each difference adds one, each product one and the
-// final subtraction one; 8 * 2^-24 (S (|d1| + |d2|) over both products + |p1|
-// + |p2|) covers them with room, and the FP64 shift adds far less.
-__device__ __forceinline__ float edge_fn32(float xa, float ya, float xb, float yb, float px, float py, float S,
-                                           float& bound) {
-  const float d1 = xb - xa, d2 = py - ya, d3 = yb - ya, d4 = px - xa;
-  const float p1 = d1 * d2, p2 = d3 * d4;
-  bound = 4.76837158203125e-07f * (S * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4)) + fabsf(p1) + fabsf(p2)) +
-          1e-30f;
-  return p1 - p2;
-}
-
-// sign of a filtered edge function: +1 / -1 when certain, 0 when the exact test decides
-__device__ __forceinline__ int certain_sign(float e, float bound) {
-  return e > 2.f * bound ? 1 : (e < -2.f * bound ? -1 : 0);
-}
-
-// one thread per triangle; depth bits of z >= 0 are ordered like z.  Every
-// coverage decision equals the exact-rounding FP64 test: FP32 decides only
-// when all three signs are certain (covered: one sign; not covered: two
-// opposite certain signs), otherwise the FP64 edge functions decide.
+// one thread per triangle; the bits of a float z >= 0 are ordered like z
 __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict__ tri, long long ntri, int W,
-                                                        double step, unsigned long long* __restrict__ depth) {
+                                                        double step, unsigned* __restrict__ depth) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ntri;
        q += (long long)gridDim.x * blockDim.x) {
     const double* p = tri + q * 9;
-    const double x0 = p[0], y0 = p[1], z0 = p[2], x1 = p[3], y1 = p[4], z1 = p[5], x2 = p[6], y2 = p[7], z2 = p[8];
-    if (edge_fn(x0, y0, x1, y1, x2, y2) == 0.0) continue;
-    // FP32 copies relative to corner 0 (the shift itself in FP64)
-    const float fx0 = 0.f, fy0 = 0.f, fx1 = (float)(x1 - x0), fy1 = (float)(y1 - y0), fx2 = (float)(x2 - x0),
-                fy2 = (float)(y2 - y0);
-    // a lower bound of any depth the barycentric formula can give inside the triangle (a convex
-    // combination of the corners, a few roundings below its smallest corner at most)
-    const double zlow = fmin(z0, fmin(z1, z2)) - 1e-12 * fmax(z0, fmax(z1, z2));
-    const int lo_x = max((int)floor(fmin(x0, fmin(x1, x2)) / step - 0.5) - 1, 0);
-    const int hi_x = min((int)ceil(fmax(x0, fmax(x1, x2)) / step - 0.5) + 1, W - 1);
-    const int lo_y = max((int)floor(fmin(y0, fmin(y1, y2)) / step - 0.5) - 1, 0);
-    const int hi_y = min((int)ceil(fmax(y0, fmax(y1, y2)) / step - 0.5) + 1, W - 1);
+    const double x0 = p[0], y0 = p[1];
+    const float X1 = (float)(p[3] - x0), Y1 = (float)(p[4] - y0), X2 = (float)(p[6] - x0), Y2 = (float)(p[7] - y0);
+    const float Z0 = (float)p[2], Z1 = (float)p[5], Z2 = (float)p[8];
+    if (fsub(fmul(X1, Y2), fmul(Y1, X2)) == 0.f) continue;
+    const int lo_x = max((int)floor(fmin(x0, fmin(p[3], p[6])) / step - 0.5) - 1, 0);
+    const int hi_x = min((int)ceil(fmax(x0, fmax(p[3], p[6])) / step - 0.5) + 1, W - 1);
+    const int lo_y = max((int)floor(fmin(y0, fmin(p[4], p[7])) / step - 0.5) - 1, 0);
+    const int hi_y = min((int)ceil(fmax(y0, fmax(p[4], p[7])) / step - 0.5) + 1, W - 1);
     for (int py = lo_y; py <= hi_y; ++py) {
-      const double cy = mul((double)py + 0.5, step);
-      const float fcy = (float)(cy - y0);
+      const float CY = (float)__dsub_rn(__dmul_rn((double)py + 0.5, step), y0);
       for (int px = lo_x; px <= hi_x; ++px) {
-        const double cx = mul((double)px + 0.5, step);
-        const float fcx = (float)(cx - x0);
-        const float S = fmaxf(fmaxf(fmaxf(fabsf(fx1), fabsf(fy1)), fmaxf(fabsf(fx2), fabsf(fy2))),
-                              fmaxf(fabsf(fcx), fabsf(fcy)));
-        float b12, b20, b01;
-        const int s12 = certain_sign(edge_fn32(fx1, fy1, fx2, fy2, fcx, fcy, S, b12), b12);
-        const int s20 = certain_sign(edge_fn32(fx2, fy2, fx0, fy0, fcx, fcy, S, b20), b20);
-        const int s01 = certain_sign(edge_fn32(fx0, fy0, fx1, fy1, fcx, fcy, S, b01), b01);
-        const bool pos = s12 > 0 || s20 > 0 || s01 > 0, neg = s12 < 0 || s20 < 0 || s01 < 0;
-        if (pos && neg) continue;  // certainly outside
-        double e12 = 0.0, e20 = 0.0, e01 = 0.0;
-        if (s12 == 0 || s20 == 0 || s01 == 0) {  // a near-tie: the exact-rounding test decides
-          e12 = edge_fn(x1, y1, x2, y2, cx, cy);
-          e20 = edge_fn(x2, y2, x0, y0, cx, cy);
-          e01 = edge_fn(x0, y0, x1, y1, cx, cy);
-          if (!((e12 >= 0.0 && e20 >= 0.0 && e01 >= 0.0) || (e12 <= 0.0 && e20 <= 0.0 && e01 <= 0.0))) continue;
-        } else {
-          e12 = edge_fn(x1, y1, x2, y2, cx, cy);
-          e20 = edge_fn(x2, y2, x0, y0, cx, cy);
-          e01 = edge_fn(x0, y0, x1, y1, cx, cy);
+        const float CX = (float)__dsub_rn(__dmul_rn((double)px + 0.5, step), x0);
+        const float e12 = edge_fn(X1, Y1, X2, Y2, CX, CY);
+        const float e20 = edge_fn(X2, Y2, 0.f, 0.f, CX, CY);
+        const float e01 = edge_fn(0.f, 0.f, X1, Y1, CX, CY);
+        if ((e12 >= 0.f && e20 >= 0.f && e01 >= 0.f) || (e12 <= 0.f && e20 <= 0.f && e01 <= 0.f)) {
+          const float num = fadd(fadd(fmul(e12, Z0), fmul(e20, Z1)), fmul(e01, Z2));
+          const float z = __fdiv_rn(num, fadd(fadd(e12, e20), e01));
+          if (z >= 0.f) atomicMin(&depth[(long)py * W + px], __float_as_uint(z));
         }
-        // a triangle whose nearest corner is behind the stored depth cannot lower it
-        unsigned long long* slot = &depth[(long)py * W + px];
-        const double cur = __longlong_as_double((long long)*((volatile unsigned long long*)slot));
-        if (zlow > cur) continue;
-        const double num = add(add(mul(e12, z0), mul(e20, z1)), mul(e01, z2));
-        const double z = num / add(add(e12, e20), e01);
-        if (z >= 0.0 && z < cur) atomicMin(slot, (unsigned long long)__double_as_longlong(z));
       }
     }
   }
@@ -321,51 +303,71 @@ static int iso_grid(long n, int nsm) {
 
 long iso_blocks(long n) { return (n + ISO_CH - 1) / ISO_CH; }
 
-// counts: n ints; bsum/boff/apart: iso_blocks(n) entries (device); hb: host scratch of 2 iso_blocks(n) doubles
+// work: counts (n ints), list (n ints), loff (n long longs), bsum, bcut, boff, bcoff (nb long longs each),
+// apart (nb doubles): see iso_work_bytes
+size_t iso_work_bytes(long n) {
+  const long nb = iso_blocks(n);
+  return (size_t)n * (2 * sizeof(int) + sizeof(long long)) + (size_t)nb * (4 * sizeof(long long) + sizeof(double)) +
+         1024;
+}
+
 template <typename T>
-int isosurface(const T* f, int N, double iso, double* tri, long long max_tri, int* counts, long long* bsum,
-               long long* boff, double* apart, std::vector<double>& hscratch, int nsm, long long* ntri,
-               double* area, cudaStream_t st) {
+int isosurface(const T* f, int N, double iso, double* tri, long long max_tri, void* work,
+               std::vector<double>& hscratch, int nsm, long long* ntri, double* area, cudaStream_t st) {
   const long n = (long)N * N * N;
   const long nb = iso_blocks(n);
   const double h = 2.0 * M_PI / N;
+  long long* bsum = (long long*)work;
+  long long* bcut = bsum + nb;
+  long long* boff = bcut + nb;
+  long long* bcoff = boff + nb;
+  double* apart = (double*)(bcoff + nb);
+  long long* loff = (long long*)(apart + nb);
+  int* counts = (int*)(loff + n);
+  int* list = counts + n;
   k_iso_count<T><<<iso_grid(n, nsm), ISO_THREADS, 0, st>>>(f, N, iso, counts);
-  k_iso_blocksum<<<(unsigned)nb, ISO_THREADS, 0, st>>>(counts, n, bsum);
-  std::vector<long long> hs(nb), ho(nb);
-  if (cudaMemcpyAsync(hs.data(), bsum, nb * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  k_iso_blocksum<<<(unsigned)nb, ISO_THREADS, 0, st>>>(counts, n, bsum, bcut);
+  std::vector<long long> hs(2 * nb), ho(2 * nb);
+  if (cudaMemcpyAsync(hs.data(), bsum, 2 * nb * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return FE_ERR_CUDA;
-  long long run = 0;
+  long long run = 0, runc = 0;
   for (long b = 0; b < nb; ++b) {
     ho[b] = run;
+    ho[nb + b] = runc;
     run += hs[b];
+    runc += hs[nb + b];
   }
-  if (cudaMemcpyAsync(boff, ho.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return FE_ERR_CUDA;
-  k_iso_emit<T><<<(unsigned)nb, ISO_THREADS, 0, st>>>(f, N, iso, h, counts, boff, tri, max_tri, apart);
-  hscratch.resize(nb);
-  if (cudaMemcpyAsync(hscratch.data(), apart, nb * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+  if (cudaMemcpyAsync(boff, ho.data(), 2 * nb * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FE_ERR_CUDA;
   double a = 0.0;
-  for (long b = 0; b < nb; ++b) a += hscratch[b];
+  if (runc > 0) {
+    k_iso_compact<<<(unsigned)nb, ISO_THREADS, 0, st>>>(counts, n, boff, bcoff, list, loff);
+    const long ne = (long)((runc + ISO_THREADS - 1) / ISO_THREADS);
+    k_iso_emit<T><<<(unsigned)ne, ISO_THREADS, 0, st>>>(f, N, iso, h, list, loff, runc, tri, max_tri, apart);
+    hscratch.resize(ne);
+    if (cudaMemcpyAsync(hscratch.data(), apart, ne * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return FE_ERR_CUDA;
+    for (long b = 0; b < ne; ++b) a += hscratch[b];
+  }
+  if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
   *ntri = run;
   *area = a;
   return FE_OK;
 }
 
-int raster_depth(const double* tri, long long ntri, int W, double extent, double* depth, int nsm, cudaStream_t st) {
+int raster_depth(const double* tri, long long ntri, int W, double extent, float* depth, int nsm, cudaStream_t st) {
   const long npx = (long)W * W;
-  k_fill_u64<<<iso_grid(npx, nsm), ISO_THREADS, 0, st>>>((unsigned long long*)depth, npx, 0x7FF0000000000000ull);
+  k_fill_u32<<<iso_grid(npx, nsm), ISO_THREADS, 0, st>>>((unsigned*)depth, npx, 0x7F800000u);
   if (ntri > 0)
-    k_raster<<<iso_grid((long)ntri, nsm), ISO_THREADS, 0, st>>>(tri, ntri, W, extent / W,
-                                                                 (unsigned long long*)depth);
+    k_raster<<<iso_grid((long)ntri, nsm), ISO_THREADS, 0, st>>>(tri, ntri, W, extent / W, (unsigned*)depth);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
-template int isosurface<double>(const double*, int, double, double*, long long, int*, long long*, long long*,
-                                double*, std::vector<double>&, int, long long*, double*, cudaStream_t);
-template int isosurface<float>(const float*, int, double, double*, long long, int*, long long*, long long*,
-                               double*, std::vector<double>&, int, long long*, double*, cudaStream_t);
+template int isosurface<double>(const double*, int, double, double*, long long, void*, std::vector<double>&, int,
+                                long long*, double*, cudaStream_t);
+template int isosurface<float>(const float*, int, double, double*, long long, void*, std::vector<double>&, int,
+                               long long*, double*, cudaStream_t);
 
 }  // namespace fe

@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(LES_THREADS) k_les_win(LesPtrs<T> in, LesPtrs<
   const long stride = axis == 1 ? N : (long)N * N;
   const T w = T(1) / T(2 * M), we = T(0.5) * w;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < nb; q += (long)gridDim.x * blockDim.x) {
-    // q = i + N (a + N b): axis 1: (i, jb = a, k = b); axis 2: (i, j = a, kb = b)
+    // q = i + N (a + N b) with a in [0, N), b in [0, N / LES_OUTS): axis 1: (i, k = a, block of j = b);
+    // axis 2: (i, j = a, block of k = b); the outputs are p0 .. p0 + LES_OUTS - 1 < N along the axis
     const long i = q % N, a = (q / N) % N, b = q / ((long)N * N);
-    const long blk = axis == 1 ? a : b;
-    const long base = axis == 1 ? i + (long)N * (long)N * b : i + (long)N * a;
-    const long p0 = blk * LES_OUTS;
+    const long base = axis == 1 ? i + (long)N * (long)N * a : i + (long)N * a;
+    const long p0 = b * LES_OUTS;
 #pragma unroll
     for (int f = 0; f < LES_NF; ++f) {  // unrolled: the field pointers stay in registers
       const T* src = in.f[f];

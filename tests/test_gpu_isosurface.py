@@ -5,7 +5,8 @@ shows iso-surfaces of the Q criterion).
 The field comes from the seeded input generator, so both sides see the same
 numbers: the triangle list (count, order, every coordinate) and the depth
 image must be bit for bit the oracle's in FP64 and from FP32 fields (the
-arithmetic is double either way, one rounding per operation), on grids that
+extraction is double either way, the image single precision, one rounding
+per operation), on grids that
 do and do not fill the emit blocks (N = 16, 24, 32); at 128^3 the count and
 area, and the triangles of 400 sampled cubes located through the oracle's
 per-cube counts.  The Q criterion's iso-surface of a spectral field agrees
@@ -71,7 +72,7 @@ def test_triangles_and_depth_bit_for_bit(fe, N, precision):
     assert np.array_equal(tri.cpu().numpy().reshape(-1, 3, 3), T)
     assert abs(ga - area) <= 1e-12 * area
     W, L = 3 * N, (N + 1) * h
-    depth = torch.empty((W, W), dtype=torch.float64, device="cuda")
+    depth = torch.empty((W, W), dtype=torch.float32, device="cuda")
     fe.fe_raster_depth(s.ctx, tri.data_ptr(), n, W, L, depth.data_ptr())
     img = oiso.raster_depth(T, W, L)
     assert np.array_equal(depth.cpu().numpy(), img)
@@ -128,7 +129,7 @@ def test_empty_surface_and_short_buffer(fe):
     s = context(fe, N, fe.FE_FP64)
     n, a, _, _ = gpu_extract(fe, s, f, 10.0, 0)  # above every value: nothing
     assert n == 0 and a == 0.0
-    depth = torch.empty((8, 8), dtype=torch.float64, device="cuda")
+    depth = torch.empty((8, 8), dtype=torch.float32, device="cuda")
     fe.fe_raster_depth(s.ctx, None, 0, 8, 1.0, depth.data_ptr())
     assert torch.isinf(depth).all()
     T, _ = oiso.extract(f, 0.0, 2 * math.pi / N)

@@ -7,8 +7,9 @@
 * A sphere of radius R: every edge of the surface is shared by exactly two
   triangles (closed), and the area converges to 4 pi R^2 at second order.
 * The depth image of the planes along +z is the lower plane's height (the
-  linear zero of cos between its two cell rows) on the covered square and
-  +inf elsewhere; the sphere's image approaches c - sqrt(R^2 - r^2).
+  linear zero of cos between its two cell rows, to single precision) on the
+  covered square and +inf elsewhere; the sphere's image approaches
+  c - sqrt(R^2 - r^2).
 """
 import math
 from collections import Counter
@@ -74,7 +75,7 @@ def test_depth_image_of_planes_and_sphere():
     for py in range(W):
         for px in range(W):
             if inside[px] and inside[py]:
-                assert abs(img[py, px] - zs) < 1e-14 * zs
+                assert abs(img[py, px] - zs) < 1e-6 * zs  # single-precision depth
             elif not (inside[px] or inside[py]):
                 assert img[py, px] == np.inf
     (Ts, _), hs = _sphere(16)
