@@ -15,6 +15,12 @@ Paper passages it restates (arXiv:1404.0959):
   Stokes number with Stokes drag: u_p = u - tau_p Du/Dt ("kinematic
   quasi-equilibrium").
 * Sec. 2, par. 3 and footnote: tau_p = 0 is Marble's dusty gas (u_p = u).
+* Two-way coupling (the dusty-gas mixture of the Sec. 2 par. 3 footnote's
+  reference): the dust drag acts back on the gas.  With the first-order
+  particle velocity the drag per unit dust mass is the gas acceleration a, so
+  the gas momentum gains f = -rho Ysum a (Ysum = sum_j Y_j), and a itself
+  solves rho a = D tau - Gc p + f, i.e. a = (D tau - Gc p) / (rho (1 + Ysum)):
+  the mixture inertia of Marble's dusty gas.
 
 The paper gives no equations; the discrete algorithm below ("Algorithm O") is
 this project's reading, in the order it is computed.  Symbols: operators from
@@ -23,12 +29,13 @@ frozen at level n; mu = nu (reference density 1).
 
  a1  dt = min(CFL h / max_i sum_d |u_d|, growth * dt_prev, dt_max)
  a3  rho0 = rho^n - dt D(phi^n)
-     R^n  = L(u^n, phi^n)
+     R^n  = L(u^n, phi^n)                    [+ f^n = -(rho^n Ysum) a^n  two-way]
      u*   = (rho^n u^n + dt (R^n - Gc p^n)) / rho0
      n-level dust and energy flux divergences (a7, a8)
      iterates: (u, phi, p, rho, Y, E)^0 = (u*, phi^n, p^n, rho0, Y^n, E^n)
  for k = 1 .. n_corr:
- a4  R^k   = (R^n + L(u^{k-1}, phi^{k-1})) / 2
+ a4  R^k   = (R^n + L(u^{k-1}, phi^{k-1}) [- (rho^{k-1} Ysum) A]) / 2
+                (two-way: A = a^n in the first corrector, a^{k-1} after)
      HbyA  = (rho^n u^n + dt R^k) / rho^{k-1}
      phiH  = I4(rho^{k-1}) I4(HbyA)          (per face direction)
      phi*  = phiH - dt G2(p^{k-1})
@@ -42,6 +49,7 @@ frozen at level n; mu = nu (reference density 1).
      u^k   = HbyA - (dt / rho^{k-1}) Gc(p^k)
      rho^k = rho^n - (dt/2) [D(phi^n) + D(phi^k)]
  a7  a^k     = (-Gc p^k + D tau(u^k)) / rho^k                (Du/Dt)
+              [/ (rho^k (1 + Ysum)) two-way; Ysum = sum_j Y_j^n over the step]
      phi_p^k = phi^k - tau_p I4(rho^k) I4(a^k)             (per class)
      (rho Y)^k = rho^n Y^n - (dt/2) [D(phi_p^n I4(Y^n)) + D(phi_p^k I4(Y^{k-1}))]
  a8  Fourier: F_E = phi I4(E + p/rho) - sum_m tau_dm I4(u_m) - kappa G4(T)
@@ -65,6 +73,11 @@ advection at second order in time;
 acoustic wave speed c = 1; psi c^2 = 1 with c^2 the isentropic derivative of
 the closure's EOS; the adaptive step's Courant number, growth limit and cap;
 with one corrector, sum rho^0 u^{n+1} = sum rho^n u^n exactly.
+Two-way coupling (tests/test_oracle_twoway.py): Ysum = 0 gives the one-way
+step bit for bit; the momentum the gas gains in the last corrector equals
+dt/2 sum (f^n + f^{K-1}) exactly; the acoustic period grows by sqrt(1 + Y)
+and the shear-wave decay rate falls by 1 + Y (Marble's effective gas) as
+dt -> 0.
 """
 import math
 from dataclasses import dataclass, field
@@ -78,6 +91,8 @@ BAROTROPIC = 0
 FOURIER = 1
 EQUILIBRIUM = 0  # dust model: particle velocity u - tau_p Du/Dt (Sec. 2 par. 2)
 TWO_FLUID = 1    # dust model: every class with its own momentum (oracle/twofluid.py)
+ONE_WAY = 0      # coupling: the dust does not act on the gas
+TWO_WAY = 1      # coupling: the drag's reaction -rho Ysum a on the gas (equilibrium dust, barotropic)
 
 
 @dataclass
@@ -101,6 +116,7 @@ class Params:
     transonic: bool = False
     fgmres: bool = False  # flexible GMRES(20) for every solve (any operator)
     dust_model: int = EQUILIBRIUM
+    coupling: int = ONE_WAY
 
     @property
     def h(self):
@@ -184,11 +200,26 @@ def time_step(prm, u, dt_prev):
     return min(dt, prm.dt_growth_max * dt_prev, prm.dt_max)
 
 
-def accel(prm, rho, u, p):
-    """Du/Dt in dynamic form: (-Gc p + D tau(u)) / rho, three components."""
+def accel(prm, rho, u, p, Ysum=None):
+    """Du/Dt in dynamic form: (-Gc p + D tau(u)) / rho, three components;
+    with the dust's reaction (two-way coupling) the inertia is rho (1 + Ysum)."""
     h = prm.h
     visc = ops.div_stress(u, prm.mu, h)
-    return [(-ops.Gc(p, m, h) + visc[m]) / rho for m in range(3)]
+    inertia = rho if Ysum is None else rho * (1.0 + Ysum)
+    return [(-ops.Gc(p, m, h) + visc[m]) / inertia for m in range(3)]
+
+
+def reaction(rho, Ysum, a):
+    """Two-way coupling: the force of the dust drag on the gas, f = -(rho Ysum) a."""
+    return [-(rho * Ysum) * a[m] for m in range(3)]
+
+
+def dust_sum(Y):
+    """Ysum = sum_j Y_j, summed in class order."""
+    s = Y[0]
+    for j in range(1, len(Y)):
+        s = s + Y[j]
+    return s
 
 
 def particle_flux(prm, phi, rho, a, j):
@@ -253,16 +284,24 @@ def step(prm, state, precond=None, dt=None):
         dt = time_step(prm, u_n, state["dt_prev"])
     psi = compressibility(prm, rho_n, p_n)
 
+    eq_dust = prm.dust_model == EQUILIBRIUM
+    two_way = prm.coupling == TWO_WAY and nd > 0
+    if two_way and (fourier or not eq_dust):
+        raise ValueError("two-way coupling: barotropic closure and equilibrium dust only")
+    Ysum = dust_sum(Y_n) if two_way else None
+
     # a3: predictor
     divphi_n = ops.D(phi_n, h)
     rho0 = rho_n - dt * divphi_n
+    a_n = accel(prm, rho_n, u_n, p_n, Ysum)
     R_n = ops.L(u_n, phi_n, prm.mu, h)
+    if two_way:
+        f_n = reaction(rho_n, Ysum, a_n)
+        R_n = [R_n[m] + f_n[m] for m in range(3)]
     mom_n = [rho_n * u_n[m] for m in range(3)]
     u_star = [(mom_n[m] + dt * (R_n[m] - ops.Gc(p_n, m, h))) / rho0 for m in range(3)]
 
-    a_n = accel(prm, rho_n, u_n, p_n)
     FY_n = []
-    eq_dust = prm.dust_model == EQUILIBRIUM
     for j in range(nd if eq_dust else 0):
         fp = particle_flux(prm, phi_n, rho_n, a_n, j)
         FY_n.append(ops.D([fp[d] * ops.I4(Y_n[j], d) for d in range(3)], h))
@@ -273,12 +312,16 @@ def step(prm, state, precond=None, dt=None):
     rho_k, u_k, phi_k, p_k = rho0, u_star, phi_n, p_n
     Y_k = list(Y_n)
     E_k = E_n if fourier else None
+    A = a_n  # the latest Du/Dt (two-way: the reaction force of the next assembly)
     iters = []
     res = []
 
     for _k in range(prm.n_corr):
         # a4: corrector assembly
         Lk = ops.L(u_k, phi_k, prm.mu, h)
+        if two_way:
+            f_k = reaction(rho_k, Ysum, A)
+            Lk = [Lk[m] + f_k[m] for m in range(3)]
         R_k = [0.5 * (R_n[m] + Lk[m]) for m in range(3)]
         HbyA = [(mom_n[m] + dt * R_k[m]) / rho_k for m in range(3)]
         phiH = [ops.I4(rho_k, d) * ops.I4(HbyA[d], d) for d in range(3)]
@@ -303,7 +346,8 @@ def step(prm, state, precond=None, dt=None):
         rho_new = rho_n - 0.5 * dt * (divphi_n + ops.D(phi_new, h))
 
         # a7: particle velocity and dust transport
-        a_k = accel(prm, rho_new, u_new, p_new)
+        a_k = accel(prm, rho_new, u_new, p_new, Ysum)
+        A = a_k
         Y_new = [] if eq_dust else list(Y_k)
         for j in range(nd if eq_dust else 0):
             fp = particle_flux(prm, phi_new, rho_new, a_k, j)
@@ -337,7 +381,7 @@ def step(prm, state, precond=None, dt=None):
                                          prm.tau_p[j], dt, h)
             new["Y"].append(Yj)
             new["V"].append(Vj)
-    info = {"dt": dt, "iters": iters, "rel_res": res, "psi": psi}
+    info = {"dt": dt, "iters": iters, "rel_res": res, "psi": psi, "p_iter": p_k}
     return new, info
 
 

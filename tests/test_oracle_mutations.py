@@ -11,6 +11,7 @@ from oracle import krylov, ops, piso
 from . import test_oracle_ops as t_ops
 from . import test_oracle_piso as t_piso
 from . import test_oracle_solve as t_solve
+from . import test_oracle_twoway as t_tw
 
 
 def _bad_I4(f, d):
@@ -52,9 +53,19 @@ def _eos_no_gamma_division(prm, rho, T=None):
     return rho * prm.R * T
 
 
-def _accel_wrong_sign(prm, rho, u, p):
+def _accel_wrong_sign(prm, rho, u, p, Ysum=None):
     visc = ops.div_stress(u, prm.mu, prm.h)
-    return [(ops.Gc(p, m, prm.h) + visc[m]) / rho for m in range(3)]
+    inertia = rho if Ysum is None else rho * (1.0 + Ysum)
+    return [(ops.Gc(p, m, prm.h) + visc[m]) / inertia for m in range(3)]
+
+
+def _accel_one_way_inertia(prm, rho, u, p, Ysum=None):
+    visc = ops.div_stress(u, prm.mu, prm.h)
+    return [(-ops.Gc(p, m, prm.h) + visc[m]) / rho for m in range(3)]
+
+
+def _reaction_wrong_sign(rho, Ysum, a):
+    return [(rho * Ysum) * a[m] for m in range(3)]
 
 
 def _energy_no_pressure_work(prm, phi, u, rho, p, E, T):
@@ -121,6 +132,12 @@ CASES = [
      lambda: t_piso.test_viscous_heating_pattern()),
     ("enthalpy flux without p/rho", piso, "energy_flux", _energy_no_pressure_work,
      lambda: t_piso.test_isobaric_heat_conduction_rate()),
+    ("two-way Du/Dt with the gas inertia only", piso, "accel", _accel_one_way_inertia,
+     lambda: t_tw.test_mixture_viscosity()),
+    ("two-way reaction force with the wrong sign", piso, "reaction", _reaction_wrong_sign,
+     lambda: t_tw.test_effective_sound_speed()),
+    ("two-way reaction force with the wrong sign (momentum)", piso, "reaction", _reaction_wrong_sign,
+     lambda: t_tw.test_momentum_exchange_identity(1)),
 ]
 
 
