@@ -278,18 +278,10 @@ __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict
     const int hi_x = min((int)ceil(fmax(x0, fmax(p[3], p[6])) / step - 0.5) + 1, W - 1);
     const int lo_y = max((int)floor(fmin(y0, fmin(p[4], p[7])) / step - 0.5) - 1, 0);
     const int hi_y = min((int)ceil(fmax(y0, fmax(p[4], p[7])) / step - 0.5) + 1, W - 1);
-    // the column centres of the bounding box once per triangle (the same double-precision formula),
-    // then every row reuses them
-    constexpr int kCols = 24;
-    float cxs[kCols];
-    const int ncol = hi_x - lo_x + 1;
-    if (ncol <= kCols)
-      for (int q = 0; q < ncol; ++q) cxs[q] = (float)__dsub_rn(__dmul_rn((double)(lo_x + q) + 0.5, step), x0);
     for (int py = lo_y; py <= hi_y; ++py) {
       const float CY = (float)__dsub_rn(__dmul_rn((double)py + 0.5, step), y0);
       for (int px = lo_x; px <= hi_x; ++px) {
-        const float CX =
-            ncol <= kCols ? cxs[px - lo_x] : (float)__dsub_rn(__dmul_rn((double)px + 0.5, step), x0);
+        const float CX = (float)__dsub_rn(__dmul_rn((double)px + 0.5, step), x0);
         const float e12 = edge_fn(X1, Y1, X2, Y2, CX, CY);
         const float e20 = edge_fn(X2, Y2, 0.f, 0.f, CX, CY);
         const float e01 = edge_fn(0.f, 0.f, X1, Y1, CX, CY);
