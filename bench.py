@@ -400,7 +400,7 @@ def ensemble_only(args):
 
 
 def part_only(args):
-    """--part les|twofluid|iso: one of the scope table's further rows alone at --N (FP32 fields,
+    """--part les|twofluid|twoway|iso: one of the scope table's further rows alone at --N (FP32 fields,
     the benchmark workload's physics), CUDA-event timed, one JSON line."""
     import torch
     from paper_1404_0959_gb300 import build, fe
@@ -445,6 +445,39 @@ def part_only(args):
                     gbs = words * 4 * float(N) ** 3 / (ms / 1e3) / 1e9
                     res[k] = {"ms_per_launch": ms, "alg_words_per_cell": words, "achieved_gbs": gbs,
                               "frac": gbs / hbm}
+            s.close()
+        out.update(res)
+    elif args.part == "twoway":
+        # the benchmark workload's physics with the dust's reaction on the gas (one class, Y = 0.01)
+        res = {}
+        for coupling in (fe.FE_COUPLING_ONE_WAY, fe.FE_COUPLING_TWO_WAY):
+            s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"],
+                          p_maxit=1000, coupling=coupling, stream=stream.cuda_stream)
+            s.init_state(0, fe.FE_INIT_SPECTRAL)
+            s.autotune(1)
+            s.use_graphs(True)
+            code, _ = s.step(args.warmup)
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            code, info = s.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            two = coupling == fe.FE_COUPLING_TWO_WAY
+            r = {"ms_per_step": ev0.elapsed_time(ev1) / args.steps, "krylov_iters_last_step": info[0]["iters"]}
+            s.use_graphs(False)
+            nd = len(cfg["tau_p"])
+            # two-way adds Ysum to the predictor and Du/Dt, Ysum and Du/Dt to the assembly
+            for k, extra in (("pred", 1), ("asm", 4), ("accel", 1)):
+                words = alg_words(k, nd, True) + (extra if two else 0)
+                s.profile_start(k)
+                s.step(args.steps)
+                pr = s.profile_stop()
+                ms = pr["target_ms"] / max(pr["target_launches"], 1)
+                gbs = words * 4 * float(N) ** 3 / (ms / 1e3) / 1e9
+                r[k] = {"ms_per_launch": ms, "alg_words_per_cell": words, "achieved_gbs": gbs, "frac": gbs / hbm}
+            res["two_way" if two else "one_way"] = r
             s.close()
         out.update(res)
     elif args.part == "iso":
@@ -544,8 +577,9 @@ def main():
                     help="time the 64-box ensemble in one context against one context per box")
     ap.add_argument("--unet", action="store_true",
                     help="time only the learned preconditioner's network pass (K applications at N^3)")
-    ap.add_argument("--part", default=None, choices=["les", "twofluid", "iso"],
-                    help="time one further row alone: a-priori LES, two-fluid dust step, Q iso-surface + raster")
+    ap.add_argument("--part", default=None, choices=["les", "twofluid", "twoway", "iso"],
+                    help="time one further row alone: a-priori LES, two-fluid dust step, two-way coupled step, "
+                         "Q iso-surface + raster")
     ap.add_argument("--width", type=int, default=2048, help="depth image width for --part iso")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -91,6 +91,10 @@ extern "C" {
 #define FE_DUST_EQUILIBRIUM 0  /* Equilibrium-Eulerian: particle velocity u - tau_p Du/Dt    */
 #define FE_DUST_TWO_FLUID   1  /* Eulerian two-fluid: each class carries its own momentum */
 
+/* coupling of the dust to the gas (Marble's dusty-gas mixture, the Sec. 2 par. 3 footnote) */
+#define FE_COUPLING_ONE_WAY 0  /* the dust does not act on the gas                          */
+#define FE_COUPLING_TWO_WAY 1  /* the drag's reaction -rho Ysum Du/Dt loads the gas momentum */
+
 typedef struct fe_ctx fe_ctx;   /* opaque */
 
 typedef struct {
@@ -123,6 +127,8 @@ typedef struct {
                                  * precision: of its first refinement solve; such steps
                                  * are host-driven, not CUDA graphs) */
     int32_t dust_model;         /* FE_DUST_EQUILIBRIUM | FE_DUST_TWO_FLUID (tau_p > 0 required) */
+    int32_t coupling;           /* FE_COUPLING_ONE_WAY | FE_COUPLING_TWO_WAY (barotropic closure
+                                 * and equilibrium dust only, else FE_ERR_UNSUPPORTED) */
 } fe_params;
 
 typedef struct {
@@ -207,6 +213,16 @@ int fe_set_clock(fe_ctx* ctx, int box, double t, double dt_prev);
  *              - sum_m tau_dm I4(u_m) - kappa G4(T), kappa = mu c_p / Pr
  *   closure: barotropic p = rho^gamma/gamma; Fourier T = (E - |u|^2/2)/c_v,
  *   p = rho R T with R = 1/gamma, c_v = R/(gamma-1).
+ * Two-way coupling (coupling = FE_COUPLING_TWO_WAY): with u_p = u - tau_p a the
+ *   drag per unit dust mass is the gas acceleration a, so the gas momentum gains
+ *   f = -(rho Ysum) a, Ysum = sum_j Y_j^n (held over the step), and a is taken
+ *   with the mixture inertia: a = (D tau - Gc p) / (rho (1 + Ysum)).  R^n above
+ *   includes f^n = -(rho^n Ysum) a^n; corrector k adds -(rho^{k-1} Ysum) a to
+ *   L(u^{k-1}, phi^{k-1}) with a the latest Du/Dt (a^n in the first corrector,
+ *   a^{k-1} after); the pressure operator is unchanged.  For a uniform loading
+ *   Y this is Marble's dusty gas: sound speed c / sqrt(1 + Y), kinematic
+ *   viscosity nu / (1 + Y).  The reaction lags the implicit pressure by one
+ *   corrector, so the loading must stay below 1 (dilute suspensions).
  * Two-fluid dust (dust_model = FE_DUST_TWO_FLUID): the classes' Y are not
  *   updated with u_p as above; after the gas step each class (bulk density
  *   sigma = rho Y, velocity V; pressureless, one-way coupled) is advanced by

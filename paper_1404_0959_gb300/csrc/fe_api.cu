@@ -186,6 +186,7 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
     plan.push_back({W_YW0 + j, e});
     plan.push_back({W_YW1 + j, e});
   }
+  if (c->prm.coupling == FE_COUPLING_TWO_WAY && nd > 1) plan.push_back({W_YSUM, e});
   // BiCGStab vectors: its own solver, and the harvest of a transonic flexible-GMRES context (which
   // generates its training pairs with BiCGStab)
   if (c->prm.solver == FE_BICGSTAB_JACOBI || (c->prm.solver == FE_FGMRES_LEARNED && c->prm.transonic))
@@ -210,6 +211,9 @@ static int validate(const fe_params* p) {
   if (p->dust_model == FE_DUST_TWO_FLUID)
     for (int q = 0; q < p->n_boxes * p->n_dust; ++q)
       if (!(p->tau_p[q] > 0.0)) return FE_ERR_INVALID_ARG;
+  if (p->coupling != FE_COUPLING_ONE_WAY && p->coupling != FE_COUPLING_TWO_WAY) return FE_ERR_INVALID_ARG;
+  if (p->coupling == FE_COUPLING_TWO_WAY && (p->closure != FE_BAROTROPIC || p->dust_model != FE_DUST_EQUILIBRIUM))
+    return FE_ERR_UNSUPPORTED;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->p_tol > 0.0) || p->p_maxit < 1) return FE_ERR_INVALID_ARG;
   if (p->closure == FE_FOURIER && !(p->Pr > 0.0)) return FE_ERR_INVALID_ARG;
   if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED &&
@@ -1020,6 +1024,10 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
   Launch L = c->L();
   if (graph) L.st = c->cap[0];
   const int ks = 1 - s, nc = c->prm.n_corr;
+  if (c->prm.coupling == FE_COUPLING_TWO_WAY && c->prm.n_dust > 0) {  // the loading sum_j Y_j^n of the step
+    L.ysum = c->prm.n_dust == 1 ? S(s, F_Y0) : W_YSUM;
+    if (c->prm.n_dust > 1) launch_ysum<T>(L, s);
+  }
   launch_dt_div<T>(L, s);
   launch_pred<T>(L, s, ks);
   launch_fluxn<T>(L, s);

@@ -59,6 +59,7 @@ enum WorkSlot {
   K_XH,                   // fused refinement: high parts of the pairs = the FP32 solution the corrector reads
   K_B64,                  // double right-hand side (mixed precision refinement)
   K_AUX,                  // scratch (diagnostics, user solve)
+  W_YSUM,                 // two-way coupling with several classes: sum_j Y_j^n of the step
   NSLOT
 };
 
@@ -592,6 +593,7 @@ struct Launch {
   int nbblocks;
   int bsmem;          // dynamic shared memory of the streamed CG kernel
   int* rstart = nullptr;  // right-hand-side kernels: also start the refined solve (outer counter)
+  int ysum = -1;          // two-way coupling: slot of the dust loading sum_j Y_j^n (-1: one-way)
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -620,6 +622,7 @@ template <typename T> void launch_accel(const Launch& L, int kset, int pk);
 template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk, int yprev0, int ynew0, int eprev,
                                       int enew, int last, int first);
 template <typename T> void launch_derive_box(const Launch& L, int s, int box);
+template <typename T> void launch_ysum(const Launch& L, int s);  // W_YSUM = sum_j Y_j of set s
 // Krylov kernels (krylov_kernels.cu); V = vector type.
 template <typename V> void launch_cg_init(const Launch& L, double dt_override);
 template <typename V> void launch_cg_matvec(const Launch& L);

@@ -288,7 +288,11 @@ __global__ void __launch_bounds__(ISO_THREADS) k_raster(const double* __restrict
         if ((e12 >= 0.f && e20 >= 0.f && e01 >= 0.f) || (e12 <= 0.f && e20 <= 0.f && e01 <= 0.f)) {
           const float num = fadd(fadd(fmul(e12, Z0), fmul(e20, Z1)), fmul(e01, Z2));
           const float z = __fdiv_rn(num, fadd(fadd(e12, e20), e01));
-          if (z >= 0.f) atomicMin(&depth[(long)py * W + px], __float_as_uint(z));
+          // the depth only decreases, so a read that is already <= z (even an older value) means the
+          // atomic would change nothing: most covered pixels of a many-layered surface skip it
+          unsigned* d = &depth[(long)py * W + px];
+          const unsigned zb = __float_as_uint(z);
+          if (z >= 0.f && zb < *d) atomicMin(d, zb);
         }
       }
     }

@@ -122,6 +122,20 @@ __global__ void __launch_bounds__(NTHR) k_dt(const BoxDev* boxes, const int2* ew
   }
 }
 
+// two-way coupling with several dust classes: W_YSUM = sum_j Y_j of set s, in class order
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_ysum(const BoxDev* boxes, const int2* ework, int s) {
+  const Chunk ch = chunk_of(boxes, ework);
+  const BoxDev& B = boxes[ch.box];
+  T* __restrict__ out = F<T>(B, W_YSUM);
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  for (int c = ch.begin + tid; c < ch.end; c += NTHR) {
+    T v = F<T>(B, S(s, F_Y0))[c];
+    for (int j = 1; j < B.nd; ++j) v = v + F<T>(B, S(s, F_Y0 + j))[c];
+    out[c] = v;
+  }
+}
+
 // cell divergence of a velocity (three consecutive slots from u0) -> W_DIV
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_div(const BoxDev* boxes, const int2* work, int u0) {
@@ -599,6 +613,9 @@ template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk,
   else
     FE_LAUNCH(L, KID_DUST, (k_dust<T, false><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
 }
+template <typename T> void launch_ysum(const Launch& L, int s) {
+  FE_LAUNCH(L, KID_OTHER, (k_ysum<T><<<L.neblocks, dim3(TX, TY), 0, L.st>>>(L.boxes, L.ework, s)));
+}
 template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
   FE_LAUNCH(L, KID_DERIVE, (k_derive<T><<<GRID>>>(L.boxes, L.work, s, box)));
 }
@@ -614,7 +631,8 @@ template <typename T> void launch_derive_box(const Launch& L, int s, int box) {
   template void launch_corr<T>(const Launch&, int, int, int, int, int, int, int);            \
   template void launch_accel<T>(const Launch&, int, int);                                    \
   template void launch_dust<T>(const Launch&, int, int, int, int, int, int, int, int, int);  \
-  template void launch_derive_box<T>(const Launch&, int, int);
+  template void launch_derive_box<T>(const Launch&, int, int);                                \
+  template void launch_ysum<T>(const Launch&, int);
 INST(double)
 INST(float)
 

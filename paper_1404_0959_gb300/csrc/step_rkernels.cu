@@ -43,7 +43,7 @@ __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
 constexpr int kMaxDev = 64;
 // per device, one bit per ring kernel (set when its shared-memory limit was accepted)
 enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
-                  RK_DUST3, RK_DIV, RK_RHS };
+                  RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW };
 template <typename T>
 struct RingReady {
   static unsigned ok[kMaxDev];
@@ -172,11 +172,14 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_corr(const BoxDev* boxes
   }
 }
 
-template <typename T>
-using PredPlan = RingPlan<T, kA, 5, 3, 1>;  // u0..2, div, p | phi | rho
-template <typename T>
-__global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_RING_MINB) kr_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
-  RING_PROLOGUE(PredPlan<T>);
+// two-way: Ysum as a second centre field with one plane of lookahead, so that three blocks per
+// multiprocessor still fit in FP32
+template <typename T, bool TW = false>
+using PredPlan = RingPlan<T, TW ? kA1 : kA, 5, 3, TW ? 2 : 1>;  // u0..2, div, p | phi | rho [, Ysum]
+// TW: two-way coupling (a with the inertia rho (1 + Ysum), R^n with the reaction -(rho Ysum) a)
+template <typename T, bool TW>
+__global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_RING_MINB) kr_pred(const BoxDev* boxes, const int2* work, int s, int kset, int ysl) {
+  RING_PROLOGUE((PredPlan<T, TW>));
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(s, F_U0 + m));
   R.gs[3] = Fr<T>(B, W_DIV);
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
 #pragma unroll
   for (int d = 0; d < 3; ++d) R.gf[d] = Fr<T>(B, S(s, F_PHI0 + d));
   R.gc[0] = Fr<T>(B, S(s, F_RHO));
+  if (TW) R.gc[TW ? 1 : 0] = Fr<T>(B, ysl);
   T* __restrict__ divphi = Fr<T>(B, W_DIVPHI);
   T* __restrict__ Rn[3] = {Fr<T>(B, W_RN0), Fr<T>(B, W_RN1), Fr<T>(B, W_RN2)};
   T* __restrict__ An[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
@@ -200,6 +204,8 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     const P2<T> crho = R.cen(0, k, tid);
+    P2<T> ys2;
+    if (TW) ys2 = R.cen(TW ? 1 : 0, k, tid);
     T ous[3][2], oRn[3][2], oAn[3][2], ops[2], odi[2], odp[2], or0[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -213,12 +219,26 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
       const T ir0 = rcp_rn(r0), ir = rcp_rn(rc);
       T L[3], visc[3];
       zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+      if (TW) {
+        const T ys = pc<T>(ys2, r);
+        const T ia = rcp_rn(rc * (T(1) + ys)), w = rc * ys;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const T gp = zGc_h(p, G, m) * ih;
-        ous[m][r] = (rc * u[m].c() + dt * (L[m] - gp)) * ir0;
-        oRn[m][r] = L[m];
-        oAn[m][r] = (visc[m] - gp) * ir;
+        for (int m = 0; m < 3; ++m) {
+          const T gp = zGc_h(p, G, m) * ih;
+          const T a = (visc[m] - gp) * ia;
+          const T Rf = L[m] - w * a;
+          ous[m][r] = (rc * u[m].c() + dt * (Rf - gp)) * ir0;
+          oRn[m][r] = Rf;
+          oAn[m][r] = a;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const T gp = zGc_h(p, G, m) * ih;
+          ous[m][r] = (rc * u[m].c() + dt * (L[m] - gp)) * ir0;
+          oRn[m][r] = L[m];
+          oAn[m][r] = (visc[m] - gp) * ir;
+        }
       }
       const T ps = rc / (gam * p.c());
       ops[r] = ps;
@@ -241,12 +261,15 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
 }
 
 // ---- corrector assembly ------------------------------------------------------------------------------
-template <typename T>
-using AsmPlan = RingPlan<T, kA1, 4, 3, 8>;  // u0..2 (level k-1), div | phi | rho, un0..2, rho', Rn0..2
-template <typename T>
-__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
-                                               int rhop) {
-  RING_PROLOGUE(AsmPlan<T>);
+template <typename T, bool TW = false>
+using AsmPlan = RingPlan<T, kA1, 4, 3, TW ? 12 : 8>;  // u0..2 (level k-1), div | phi | rho, un0..2, rho', Rn0..2
+                                                       // [, Ysum, a0..2]
+// TW: two-way coupling, L^{k-1} - (rho^{k-1} Ysum) a with a the latest Du/Dt (read per cell pair)
+template <typename T, bool TW>
+__global__ void __launch_bounds__(RNT, sizeof(T) == 4 && TW ? 3 : FE_RING_MINB) kr_asm(const BoxDev* boxes, const int2* work,
+                                                                                   int s, int up0, int php0, int rhop,
+                                                                                   int ysl) {
+  RING_PROLOGUE((AsmPlan<T, TW>));
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, up0 + m);
   R.gs[3] = Fr<T>(B, W_DIV);
@@ -258,6 +281,11 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes,
   R.gc[4] = Fr<T>(B, rhop);
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gc[5 + m] = Fr<T>(B, W_RN0 + m);
+  if (TW) {
+    R.gc[TW ? 8 : 0] = Fr<T>(B, ysl);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) R.gc[TW ? 9 + m : 0] = Fr<T>(B, W_AN0 + m);
+  }
   T* __restrict__ hb[3] = {Fr<T>(B, W_HB0), Fr<T>(B, W_HB1), Fr<T>(B, W_HB2)};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
   R.prologue(G);
@@ -278,6 +306,11 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes,
       zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
       const T rc = pc<T>(crho, r);
       const T irp = rcp_rn(pc<T>(crp, r));
+      if (TW) {
+        const T w = pc<T>(crp, r) * pc<T>(R.cen(TW ? 8 : 0, k, tid), r);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) L[m] = L[m] - w * pc<T>(R.cen(TW ? 9 + m : 0, k, tid), r);
+      }
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const T Rm = T(0.5) * (pc<T>(R.cen(5 + m, k, tid), r) + L[m]);
@@ -291,16 +324,19 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_asm(const BoxDev* boxes,
 }
 
 // ---- Du/Dt at level k -----------------------------------------------------------------------------------
-template <typename T>
-using AccelPlan = RingPlan<T, kA, 5, 0, 1>;  // u0..2, div, p | | rho
-template <typename T>
-__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
-  RING_PROLOGUE(AccelPlan<T>);
+template <typename T, bool TW = false>
+using AccelPlan = RingPlan<T, kA, 5, 0, TW ? 2 : 1>;  // u0..2, div, p | | rho [, Ysum]
+// TW: two-way coupling, inertia rho (1 + Ysum) with Ysum from slot ysl (a centre field of the ring)
+template <typename T, bool TW>
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxes, const int2* work, int kset, int pk,
+                                                              int ysl) {
+  RING_PROLOGUE((AccelPlan<T, TW>));
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, S(kset, F_U0 + m));
   R.gs[3] = Fr<T>(B, W_DIV);
   R.gs[4] = Fr<T>(B, pk);
   R.gc[0] = Fr<T>(B, S(kset, F_RHO));
+  if (TW) R.gc[TW ? 1 : 0] = Fr<T>(B, ysl);
   T* __restrict__ a[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
   const T ih = (T)B.ih, mu = (T)B.mu;
   R.prologue(G);
@@ -310,12 +346,14 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxe
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     const P2<T> crho = R.cen(0, k, tid);
+    P2<T> ys2;
+    if (TW) ys2 = R.cen(TW ? 1 : 0, k, tid);
     T oa[3][2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
       const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
-      const T ir = rcp_rn(pc<T>(crho, r));
+      const T ir = TW ? rcp_rn(pc<T>(crho, r) * (T(1) + pc<T>(ys2, r))) : rcp_rn(pc<T>(crho, r));
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
@@ -618,20 +656,33 @@ int rlaunch_corr(const Launch& L, int s, int rhop, int pp, int pnew, int kset, i
 
 template <typename T>
 int rlaunch_pred(const Launch& L, int s, int kset) {
-  if (!L.ring_ok || !ring_ready<T>(RK_PRED)) return 0;
-  FE_LAUNCH(L, KID_PRED, (kr_pred<T><<<RGRID(PredPlan<T>::bytes)>>>(L.boxes, L.work, s, kset)));
+  const bool tw = L.ysum >= 0;
+  if (!L.ring_ok || !ring_ready<T>(tw ? RK_PRED_TW : RK_PRED)) return 0;
+  if (tw)
+    FE_LAUNCH(L, KID_PRED, (kr_pred<T, true><<<RGRID((PredPlan<T, true>::bytes))>>>(L.boxes, L.work, s, kset, L.ysum)));
+  else
+    FE_LAUNCH(L, KID_PRED, (kr_pred<T, false><<<RGRID(PredPlan<T>::bytes)>>>(L.boxes, L.work, s, kset, -1)));
   return 1;
 }
 template <typename T>
 int rlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
-  if (!L.ring_ok || !ring_ready<T>(RK_ASM)) return 0;
-  FE_LAUNCH(L, KID_ASM, (kr_asm<T><<<RGRID(AsmPlan<T>::bytes)>>>(L.boxes, L.work, s, up0, php0, rhop)));
+  const bool tw = L.ysum >= 0;
+  if (!L.ring_ok || !ring_ready<T>(tw ? RK_ASM_TW : RK_ASM)) return 0;
+  if (tw)
+    FE_LAUNCH(L, KID_ASM,
+              (kr_asm<T, true><<<RGRID((AsmPlan<T, true>::bytes))>>>(L.boxes, L.work, s, up0, php0, rhop, L.ysum)));
+  else
+    FE_LAUNCH(L, KID_ASM, (kr_asm<T, false><<<RGRID(AsmPlan<T>::bytes)>>>(L.boxes, L.work, s, up0, php0, rhop, -1)));
   return 1;
 }
 template <typename T>
 int rlaunch_accel(const Launch& L, int kset, int pk) {
-  if (!L.ring_ok || !ring_ready<T>(RK_ACCEL)) return 0;
-  FE_LAUNCH(L, KID_ACCEL, (kr_accel<T><<<RGRID(AccelPlan<T>::bytes)>>>(L.boxes, L.work, kset, pk)));
+  const bool tw = L.ysum >= 0;
+  if (!L.ring_ok || !ring_ready<T>(tw ? RK_ACCEL_TW : RK_ACCEL)) return 0;
+  if (tw)
+    FE_LAUNCH(L, KID_ACCEL, (kr_accel<T, true><<<RGRID((AccelPlan<T, true>::bytes))>>>(L.boxes, L.work, kset, pk, L.ysum)));
+  else
+    FE_LAUNCH(L, KID_ACCEL, (kr_accel<T, false><<<RGRID(AccelPlan<T>::bytes)>>>(L.boxes, L.work, kset, pk, -1)));
   return 1;
 }
 template <typename T>
@@ -688,9 +739,12 @@ int rprepare() {
   auto set = [&](int bit, bool accepted) { ok |= accepted ? 1u << bit : 0u; };
   set(RK_CORR_M, set_smem(kr_corr<T, true>, CorrPlan<T, true>::bytes));
   set(RK_CORR_F, set_smem(kr_corr<T, false>, CorrPlan<T, false>::bytes));
-  set(RK_PRED, set_smem(kr_pred<T>, PredPlan<T>::bytes));
-  set(RK_ASM, set_smem(kr_asm<T>, AsmPlan<T>::bytes));
-  set(RK_ACCEL, set_smem(kr_accel<T>, AccelPlan<T>::bytes));
+  set(RK_PRED, set_smem(kr_pred<T, false>, PredPlan<T>::bytes));
+  set(RK_ASM, set_smem(kr_asm<T, false>, AsmPlan<T>::bytes));
+  set(RK_ACCEL, set_smem(kr_accel<T, false>, AccelPlan<T>::bytes));
+  set(RK_PRED_TW, set_smem(kr_pred<T, true>, PredPlan<T, true>::bytes));
+  set(RK_ASM_TW, set_smem(kr_asm<T, true>, AsmPlan<T, true>::bytes));
+  set(RK_ACCEL_TW, set_smem(kr_accel<T, true>, AccelPlan<T, true>::bytes));
   set(RK_FLUX1, set_smem(kr_fluxn<T, 1>, FluxPlan<T, 1>::bytes));
   set(RK_FLUX2, set_smem(kr_fluxn<T, 2>, FluxPlan<T, 2>::bytes));
   set(RK_FLUX3, set_smem(kr_fluxn<T, 3>, FluxPlan<T, 3>::bytes));

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(NTHR) kz_div(const BoxDev* boxes, const int2* 
 
 // ---- predictor ------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
+__global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2* work, int s, int kset, int ysl) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   const ZGeom<2> G(t.x0, t.y0, B.N);
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
   T* __restrict__ dinv = Fz<T>(B, W_DINV);
   T* __restrict__ rho0 = Fz<T>(B, S(kset, F_RHO));
   T* __restrict__ us[3] = {Fz<T>(B, S(kset, F_U0)), Fz<T>(B, S(kset, F_U1)), Fz<T>(B, S(kset, F_U2))};
+  const T* __restrict__ ysum = ysl >= 0 ? Fz<T>(B, ysl) : nullptr;
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
   const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
   for (int k = t.k0; k < t.kend; ++k) {
@@ -110,12 +111,26 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
     const T ir0 = rcp_rn(r0), ir = rcp_rn(r);
     T L[3], visc[3];
     zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
+    if (ysum) {  // two-way: a = (D tau - Gc p) / (rho (1 + Ysum)), R^n = L - (rho Ysum) a
+      const T ys = __ldg(&ysum[c]);
+      const T ia = rcp_rn(r * (T(1) + ys)), w = r * ys;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const T gp = zGc_h(p, G, m) * ih;
-      us[m][c] = (r * u[m].c() + dt * (L[m] - gp)) * ir0;
-      Rn[m][c] = L[m];
-      An[m][c] = (visc[m] - gp) * ir;
+      for (int m = 0; m < 3; ++m) {
+        const T gp = zGc_h(p, G, m) * ih;
+        const T a = (visc[m] - gp) * ia;
+        const T Rf = L[m] - w * a;
+        us[m][c] = (r * u[m].c() + dt * (Rf - gp)) * ir0;
+        Rn[m][c] = Rf;
+        An[m][c] = a;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T gp = zGc_h(p, G, m) * ih;
+        us[m][c] = (r * u[m].c() + dt * (L[m] - gp)) * ir0;
+        Rn[m][c] = L[m];
+        An[m][c] = (visc[m] - gp) * ir;
+      }
     }
     const T ps = r / (gam * p.c());
     psi[c] = ps;
@@ -128,7 +143,7 @@ __global__ void __launch_bounds__(NTHR) kz_pred(const BoxDev* boxes, const int2*
 // ---- corrector assembly ------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(NTHR) kz_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
-                                                int rhop) {
+                                                int rhop, int ysl) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   const ZGeom<2> G(t.x0, t.y0, B.N);
@@ -144,6 +159,8 @@ __global__ void __launch_bounds__(NTHR) kz_asm(const BoxDev* boxes, const int2* 
   const T* __restrict__ rp = Fz<T>(B, rhop);
   const T* __restrict__ Rn[3] = {Fz<T>(B, W_RN0), Fz<T>(B, W_RN1), Fz<T>(B, W_RN2)};
   T* __restrict__ hb[3] = {Fz<T>(B, W_HB0), Fz<T>(B, W_HB1), Fz<T>(B, W_HB2)};
+  const T* __restrict__ ysum = ysl >= 0 ? Fz<T>(B, ysl) : nullptr;
+  const T* __restrict__ An[3] = {Fz<T>(B, W_AN0), Fz<T>(B, W_AN1), Fz<T>(B, W_AN2)};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
   for (int k = t.k0; k < t.kend; ++k) {
 #pragma unroll
@@ -161,7 +178,13 @@ __global__ void __launch_bounds__(NTHR) kz_asm(const BoxDev* boxes, const int2* 
     T L[3], visc[3];
     zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
     const T r = __ldg(&rho[c]);
-    const T irp = rcp_rn(__ldg(&rp[c]));
+    const T rpv = __ldg(&rp[c]);
+    const T irp = rcp_rn(rpv);
+    if (ysum) {  // two-way: L^{k-1} - (rho^{k-1} Ysum) a, a the latest Du/Dt
+      const T w = rpv * __ldg(&ysum[c]);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) L[m] = L[m] - w * __ldg(&An[m][c]);
+    }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T R = T(0.5) * (__ldg(&Rn[m][c]) + L[m]);
@@ -341,7 +364,7 @@ __global__ void __launch_bounds__(NTHR, 2) kz_corr(const BoxDev* boxes, const in
 
 // ---- Du/Dt at level k ------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTHR) kz_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
+__global__ void __launch_bounds__(NTHR) kz_accel(const BoxDev* boxes, const int2* work, int kset, int pk, int ysl) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   const ZGeom<2> G(t.x0, t.y0, B.N);
@@ -353,6 +376,7 @@ __global__ void __launch_bounds__(NTHR) kz_accel(const BoxDev* boxes, const int2
   p.init(Fz<T>(B, pk), sm[4], G, t.k0);
   const T* __restrict__ rho = Fz<T>(B, S(kset, F_RHO));
   T* __restrict__ a[3] = {Fz<T>(B, W_AN0), Fz<T>(B, W_AN1), Fz<T>(B, W_AN2)};
+  const T* __restrict__ ysum = ysl >= 0 ? Fz<T>(B, ysl) : nullptr;
   const T ih = (T)B.ih, mu = (T)B.mu;
   for (int k = t.k0; k < t.kend; ++k) {
 #pragma unroll
@@ -367,7 +391,8 @@ __global__ void __launch_bounds__(NTHR) kz_accel(const BoxDev* boxes, const int2
     __syncthreads();
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
-    const T ir = rcp_rn(__ldg(&rho[c]));
+    // inertia rho, or rho (1 + Ysum) with the dust's reaction (two-way)
+    const T ir = ysum ? rcp_rn(__ldg(&rho[c]) * (T(1) + __ldg(&ysum[c]))) : rcp_rn(__ldg(&rho[c]));
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
@@ -549,11 +574,11 @@ template <typename T> void zlaunch_div(const Launch& L, int u0) {
 }
 template <typename T> void zlaunch_pred(const Launch& L, int s, int k) {
   if (rlaunch_pred<T>(L, s, k)) return;
-  FE_LAUNCH(L, KID_PRED, (kz_pred<T><<<ZGRID>>>(L.boxes, L.work, s, k)));
+  FE_LAUNCH(L, KID_PRED, (kz_pred<T><<<ZGRID>>>(L.boxes, L.work, s, k, L.ysum)));
 }
 template <typename T> void zlaunch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
   if (rlaunch_asm<T>(L, s, up0, php0, rhop)) return;
-  FE_LAUNCH(L, KID_ASM, (kz_asm<T><<<ZGRID>>>(L.boxes, L.work, s, up0, php0, rhop)));
+  FE_LAUNCH(L, KID_ASM, (kz_asm<T><<<ZGRID>>>(L.boxes, L.work, s, up0, php0, rhop, L.ysum)));
 }
 template <typename T> void zlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (rlaunch_rhs<T>(L, s, rhop, pp)) return;
@@ -566,7 +591,7 @@ template <typename T> void zlaunch_corr(const Launch& L, int s, int rhop, int pp
 }
 template <typename T> void zlaunch_accel(const Launch& L, int kset, int pk) {
   if (rlaunch_accel<T>(L, kset, pk)) return;
-  FE_LAUNCH(L, KID_ACCEL, (kz_accel<T><<<ZGRID>>>(L.boxes, L.work, kset, pk)));
+  FE_LAUNCH(L, KID_ACCEL, (kz_accel<T><<<ZGRID>>>(L.boxes, L.work, kset, pk, L.ysum)));
 }
 template <typename T> void zlaunch_fluxn(const Launch& L, int s, int nd) {
   if (rlaunch_fluxn<T>(L, s, nd)) return;

@@ -43,6 +43,8 @@ FE_INIT_DERIVE = 1
 FE_MAX_DUST = 8
 FE_DUST_EQUILIBRIUM = 0
 FE_DUST_TWO_FLUID = 1
+FE_COUPLING_ONE_WAY = 0
+FE_COUPLING_TWO_WAY = 1
 
 
 class fe_params(ctypes.Structure):
@@ -52,7 +54,7 @@ class fe_params(ctypes.Structure):
                 ("k0", POINTER(c_double)), ("seed", POINTER(c_uint64)), ("cfl", c_double),
                 ("dt_growth_max", c_double), ("dt_max", c_double), ("n_corr", c_int32), ("solver", c_int32),
                 ("p_tol", c_double), ("p_maxit", c_int32), ("transonic", c_int32), ("learned_every", c_int32),
-                ("dust_model", c_int32)]
+                ("dust_model", c_int32), ("coupling", c_int32)]
 
 
 class fe_step_info(ctypes.Structure):
@@ -376,7 +378,8 @@ class Solver:
 
     def __init__(self, boxes, precision=FE_FP64, closure=FE_BAROTROPIC, gamma=1.4, Pr=0.7, cfl=0.5,
                  dt_growth_max=1.2, dt_max=float("inf"), n_corr=2, solver=FE_PCG_JACOBI, p_tol=1e-10,
-                 p_maxit=500, transonic=False, learned_every=1, stream=None, dust_model=FE_DUST_EQUILIBRIUM):
+                 p_maxit=500, transonic=False, learned_every=1, stream=None, dust_model=FE_DUST_EQUILIBRIUM,
+                 coupling=FE_COUPLING_ONE_WAY):
         import torch
         self.torch = torch
         nb = len(boxes)
@@ -398,7 +401,7 @@ class Solver:
         self.params = fe_params(nb, self._N, precision, closure, gamma, Pr, self._nu, nd, self._tau, self._y0,
                                 self._mach, self._k0, self._seed, cfl, dt_growth_max,
                                 dt_max if np.isfinite(dt_max) else 0.0, n_corr, solver, p_tol, p_maxit,
-                                int(bool(transonic)), int(learned_every), int(dust_model))
+                                int(bool(transonic)), int(learned_every), int(dust_model), int(coupling))
         self.two_fluid = dust_model == FE_DUST_TWO_FLUID
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
