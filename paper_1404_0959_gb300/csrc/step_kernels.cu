@@ -2,8 +2,13 @@
 // PISO, fourth-order central interpolation, adaptive dt; Sec. 2 par. 2:
 // Equilibrium-Eulerian dust, Fourier / barotropic closure).
 //
-// One thread owns one (i, j) column of a tile and walks its z-planes; every
-// neighbour value is read through the read-only cache with periodic wrap.
+// The general kernels: the time-step maximum, the dust-loading sum, the
+// Fourier closure's flux divergences and dust/energy update (and any number of
+// dust classes), the transonic corrector and the derived initial fields; the
+// other stages run the ring and z-marching kernels (step_rkernels.cu,
+// step_zkernels.cu).  One thread owns one (i, j) column of a tile and walks its
+// z-planes; every neighbour value is read through the read-only cache with
+// periodic wrap.
 // The viscous term uses the identity D tau(u)_m = mu (sum_d D G4_d u_m +
 // Gc_m(div u)/3), which holds exactly for the stencils here because the Gauss
 // gradients along different axes commute on the periodic grid; the face
@@ -32,27 +37,6 @@ __device__ __forceinline__ T* F(const BoxDev& B, int slot) {
 __device__ __forceinline__ int bx(int d) { return d == 0 ? -1 : 0; }
 __device__ __forceinline__ int by(int d) { return d == 1 ? -1 : 0; }
 __device__ __forceinline__ int bz(int d) { return d == 2 ? -1 : 0; }
-
-// L_m(u, phi) = -D(phi_d I4_d u_m) + D tau_m and the viscous part D tau_m.
-template <typename T>
-__device__ __forceinline__ void eval_L(const T* const (&u)[3], const T* const (&phi)[3], const T* div,
-                                       const Nbr& n, T ih, T mu, T (&L)[3], T (&visc)[3]) {
-  const int c = n(0, 0, 0);
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    T conv = T(0), lap = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T fp = __ldg(&phi[d][c]) * I4f<T>(u[m], n, d, 0, 0, 0);
-      T fm = __ldg(&phi[d][n(bx(d), by(d), bz(d))]) * I4f<T>(u[m], n, d, bx(d), by(d), bz(d));
-      conv += fp - fm;
-      lap += DG4_h2<T>(u[m], n, d, 0, 0, 0);
-    }
-    T gdiv = Gc_h<T>(div, n, m, 0, 0, 0);
-    visc[m] = mu * (lap * ih * ih + gdiv * ih * T(1.0 / 3.0));
-    L[m] = visc[m] - conv * ih;
-  }
-}
 
 // Viscous face stress tau_dm on the d-face of cell offset o:
 // mu (G4_d u_m + I4_d Gc_m u_d - 2/3 delta_dm I4_d div).
@@ -136,70 +120,6 @@ __global__ void __launch_bounds__(NTHR) k_ysum(const BoxDev* boxes, const int2* 
   }
 }
 
-// cell divergence of a velocity (three consecutive slots from u0) -> W_DIV
-template <typename T>
-__global__ void __launch_bounds__(NTHR) k_div(const BoxDev* boxes, const int2* work, int u0) {
-  Tile t = tile_of(boxes, work);
-  if (!t.active) return;
-  const BoxDev& B = boxes[t.box];
-  const T* u[3] = {F<T>(B, u0), F<T>(B, u0 + 1), F<T>(B, u0 + 2)};
-  T* div = F<T>(B, W_DIV);
-  const T ih = (T)B.ih;
-  for (int k = t.k0; k < t.kend; ++k) {
-    Nbr n(t.i, t.j, k, B.N);
-    T s = Gc_h<T>(u[0], n, 0, 0, 0, 0) + Gc_h<T>(u[1], n, 1, 0, 0, 0) + Gc_h<T>(u[2], n, 2, 0, 0, 0);
-    div[n(0, 0, 0)] = s * ih;
-  }
-}
-
-// a3: predictor.  Writes D(phi^n), R^n, Du/Dt at level n, psi, rho0 and u*
-// (rho0 and u* into state set kset).
-template <typename T>
-__global__ void __launch_bounds__(NTHR, 3) k_pred(const BoxDev* boxes, const int2* work, int s, int kset) {
-  Tile t = tile_of(boxes, work);
-  if (!t.active) return;
-  const BoxDev& B = boxes[t.box];
-  const T* rho = F<T>(B, S(s, F_RHO));
-  const T* u[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
-  const T* phi[3] = {F<T>(B, S(s, F_PHI0)), F<T>(B, S(s, F_PHI1)), F<T>(B, S(s, F_PHI2))};
-  const T* p = F<T>(B, S(s, F_P));
-  const T* div = F<T>(B, W_DIV);
-  T* divphi = F<T>(B, W_DIVPHI);
-  T* Rn[3] = {F<T>(B, W_RN0), F<T>(B, W_RN1), F<T>(B, W_RN2)};
-  T* An[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
-  T* psi = F<T>(B, W_PSI);
-  T* dinv = F<T>(B, W_DINV);
-  T* rho0 = F<T>(B, S(kset, F_RHO));
-  T* us[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
-  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
-  const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
-  for (int k = t.k0; k < t.kend; ++k) {
-    Nbr n(t.i, t.j, k, B.N);
-    const int c = n(0, 0, 0);
-    T dph = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) dph += __ldg(&phi[d][c]) - __ldg(&phi[d][n(bx(d), by(d), bz(d))]);
-    dph *= ih;
-    const T r = __ldg(&rho[c]);
-    const T r0 = r - dt * dph;
-    const T ir0 = T(1) / r0, ir = T(1) / r;
-    T L[3], visc[3];
-    eval_L<T>(u, phi, div, n, ih, mu, L, visc);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
-      us[m][c] = (r * __ldg(&u[m][c]) + dt * (L[m] - gp)) * ir0;
-      Rn[m][c] = L[m];
-      An[m][c] = (visc[m] - gp) * ir;
-    }
-    const T ps = r / (gam * __ldg(&p[c]));
-    psi[c] = ps;
-    dinv[c] = jd.inv(ps);
-    divphi[c] = dph;
-    rho0[c] = r0;
-  }
-}
-
 // n-level dust flux divergences D(phi_p^n I4 Y^n) and, Fourier, D(F_E^n).
 template <typename T, bool FOURIER>
 __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_fluxn(const BoxDev* boxes, const int2* work, int s) {
@@ -253,68 +173,6 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_fluxn(const BoxDev* b
       }
       F<T>(B, W_FEN)[c] = acc * ih;
     }
-  }
-}
-
-// a4: HbyA = (rho^n u^n + dt (R^n + L(u^{k-1}, phi^{k-1}))/2) / rho^{k-1}
-template <typename T>
-__global__ void __launch_bounds__(NTHR, 3) k_asm(const BoxDev* boxes, const int2* work, int s, int up0, int php0,
-                                               int rhop) {
-  Tile t = tile_of(boxes, work);
-  if (!t.active) return;
-  const BoxDev& B = boxes[t.box];
-  const T* rho = F<T>(B, S(s, F_RHO));
-  const T* un[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
-  const T* u[3] = {F<T>(B, up0), F<T>(B, up0 + 1), F<T>(B, up0 + 2)};
-  const T* phi[3] = {F<T>(B, php0), F<T>(B, php0 + 1), F<T>(B, php0 + 2)};
-  const T* rp = F<T>(B, rhop);
-  const T* div = F<T>(B, W_DIV);
-  const T* Rn[3] = {F<T>(B, W_RN0), F<T>(B, W_RN1), F<T>(B, W_RN2)};
-  T* hb[3] = {F<T>(B, W_HB0), F<T>(B, W_HB1), F<T>(B, W_HB2)};
-  const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
-  for (int k = t.k0; k < t.kend; ++k) {
-    Nbr n(t.i, t.j, k, B.N);
-    const int c = n(0, 0, 0);
-    T L[3], visc[3];
-    eval_L<T>(u, phi, div, n, ih, mu, L, visc);
-    const T r = __ldg(&rho[c]);
-    const T irp = T(1) / __ldg(&rp[c]);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      T R = T(0.5) * (__ldg(&Rn[m][c]) + L[m]);
-      hb[m][c] = (r * __ldg(&un[m][c]) + dt * R) * irp;
-    }
-  }
-}
-
-// a4: phi* = I4(rho^{k-1}) I4(HbyA) - dt G2(p^{k-1}); right-hand side b.
-template <typename T>
-__global__ void __launch_bounds__(NTHR) k_rhs(const BoxDev* boxes, const int2* work, int s, int rhop, int pp) {
-  Tile t = tile_of(boxes, work);
-  if (!t.active) return;
-  const BoxDev& B = boxes[t.box];
-  const T* rho = F<T>(B, S(s, F_RHO));
-  const T* rp = F<T>(B, rhop);
-  const T* p = F<T>(B, pp);
-  const T* hb[3] = {F<T>(B, W_HB0), F<T>(B, W_HB1), F<T>(B, W_HB2)};
-  const T* divphi = F<T>(B, W_DIVPHI);
-  T* ps[3] = {F<T>(B, W_PS0), F<T>(B, W_PS1), F<T>(B, W_PS2)};
-  T* b = F<T>(B, K_B);
-  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
-  for (int k = t.k0; k < t.kend; ++k) {
-    Nbr n(t.i, t.j, k, B.N);
-    const int c = n(0, 0, 0);
-    T dsum = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T fp = I4f<T>(rp, n, d, 0, 0, 0) * I4f<T>(hb[d], n, d, 0, 0, 0) -
-             dt * (__ldg(&p[n.at(d, 0, 0, 0, 1)]) - __ldg(&p[c])) * ih;
-      T fm = I4f<T>(rp, n, d, bx(d), by(d), bz(d)) * I4f<T>(hb[d], n, d, bx(d), by(d), bz(d)) -
-             dt * (__ldg(&p[c]) - __ldg(&p[n.at(d, 0, 0, 0, -1)])) * ih;
-      ps[d][c] = fp;
-      dsum += fp - fm;
-    }
-    b[c] = -((__ldg(&rp[c]) - __ldg(&rho[c])) * idt + T(0.5) * __ldg(&divphi[c]) + T(0.5) * dsum * ih);
   }
 }
 
@@ -406,32 +264,6 @@ __global__ void __launch_bounds__(NTHR, 2) k_corr(const BoxDev* boxes, const int
         B.sc[SC_RES0 + kidx] = bb > 0.0 ? sqrt(res[0] / bb) : 0.0;
         B.sc[SC_IT0 + kidx] = B.sc[SC_ITERS];
       }
-    }
-  }
-}
-
-// a7: Du/Dt at level k = (-Gc p^k + D tau(u^k)) / rho^k  (W_DIV holds div u^k)
-template <typename T>
-__global__ void __launch_bounds__(NTHR) k_accel(const BoxDev* boxes, const int2* work, int kset, int pk) {
-  Tile t = tile_of(boxes, work);
-  if (!t.active) return;
-  const BoxDev& B = boxes[t.box];
-  const T* rho = F<T>(B, S(kset, F_RHO));
-  const T* u[3] = {F<T>(B, S(kset, F_U0)), F<T>(B, S(kset, F_U1)), F<T>(B, S(kset, F_U2))};
-  const T* p = F<T>(B, pk);
-  const T* div = F<T>(B, W_DIV);
-  T* a[3] = {F<T>(B, W_AN0), F<T>(B, W_AN1), F<T>(B, W_AN2)};
-  const T ih = (T)B.ih, mu = (T)B.mu;
-  for (int k = t.k0; k < t.kend; ++k) {
-    Nbr n(t.i, t.j, k, B.N);
-    const int c = n(0, 0, 0);
-    const T ir = T(1) / __ldg(&rho[c]);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      T lap = DG4_h2<T>(u[m], n, 0, 0, 0, 0) + DG4_h2<T>(u[m], n, 1, 0, 0, 0) + DG4_h2<T>(u[m], n, 2, 0, 0, 0);
-      T visc = mu * (lap * ih * ih + Gc_h<T>(div, n, m, 0, 0, 0) * ih * T(1.0 / 3.0));
-      T gp = Gc_h<T>(p, n, m, 0, 0, 0) * ih;
-      a[m][c] = (visc - gp) * ir;
     }
   }
 }
