@@ -413,11 +413,17 @@ int fe_plane_streaming_active(const fe_ctx* ctx);
 
 /* Tile depth of the stencil kernels: every kernel launch covers all boxes
  * with 32 x 8-cell column tiles that walk tz z-planes.  fe_set_tiling sets tz
- * (0 = built-in default: 8 for N >= 128, else 4).  fe_autotune times `trials`
- * trial steps (computed from the current state and discarded: the state and
- * clock are unchanged) for tz in {4, 8, 16, 32}, keeps the fastest and
- * returns it in *best_tz.  Not part of the method. */
+ * for every box, fe_set_box_tiling for one (0 = built-in default: 8 for
+ * N >= 128, else 4).  fe_autotune times `trials` trial steps (computed from
+ * the current state and discarded: the state and clock are unchanged) for
+ * tz in {4, 8, 16, 32} for all boxes, then, when the boxes have several
+ * sizes, for each size in turn (largest first) with the other boxes fixed;
+ * it keeps the fastest tiling and returns the depth of the largest box in
+ * *best_tz (NULL allowed).  The x/y tile (32 x 8) and the copy lookahead of
+ * the stencil kernels are compile-time constants, measured at 256^3.  Not
+ * part of the method. */
 int fe_set_tiling(fe_ctx* ctx, int tz);
+int fe_set_box_tiling(fe_ctx* ctx, int box, int tz);
 int fe_autotune(fe_ctx* ctx, int trials, int* best_tz);
 
 /* Instrumentation (not part of the method).  fe_profile_start resets the

@@ -106,7 +106,7 @@ struct fe_ctx {
   bool use_bulk = true;     // streamed CG kernel where the boxes allow it
   int unet_tc = 1;          // U-Net stride-1 layers on tcgen05 (1) or warp-level MMA (0)
   int neblocks = 0;
-  int tz_override = 0;     // 0: default tile depth per N
+  std::vector<int> tzb;    // tile depth per box (0: default for its N)
   int nsm = 152;           // multiprocessors of the device
   double* dpart = nullptr;
   double* dsc = nullptr;
@@ -237,7 +237,8 @@ static int tz_for(int N) { return N >= 128 ? 8 : 4; }
 
 // (Re)build both work lists for tile depth tz (0: default per N) and upload the
 // descriptors.  Grows the partial-sum buffer when needed.
-static int set_tiling(fe_ctx* c, int tz) {
+// tzb[b]: tile depth of box b (0: the default for its N)
+static int set_tiling(fe_ctx* c, const std::vector<int>& tzb) {
   std::vector<int2> work, ework;
   // element-wise chunk: about two waves of 8 blocks per SM over all boxes, so
   // the per-block reduction tail (fence + counter) is paid rarely
@@ -249,6 +250,7 @@ static int set_tiling(fe_ctx* c, int tz) {
   for (int b = 0; b < c->nb; ++b) {
     BoxDev& B = c->hbox[b];
     const int N = B.N;
+    const int tz = tzb[b];
     B.tz = tz > 0 ? (tz < N ? tz : N) : tz_for(N);
     B.tnx = (N + TX - 1) / TX;
     B.tny = (N + TY - 1) / TY;
@@ -323,7 +325,7 @@ static int set_tiling(fe_ctx* c, int tz) {
   }
   c->nblocks = (int)work.size();
   c->neblocks = (int)ework.size();
-  c->tz_override = tz;
+  c->tzb = tzb;
   drop_graphs(c);
   CK(cudaMemcpyAsync(c->dwork, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->dework, ework.data(), ework.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
@@ -331,6 +333,8 @@ static int set_tiling(fe_ctx* c, int tz) {
   CK(cudaStreamSynchronize(c->st));
   return FE_OK;
 }
+
+static int set_tiling(fe_ctx* c, int tz) { return set_tiling(c, std::vector<int>(c->nb, tz)); }
 
 extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
   if (!out) return FE_ERR_INVALID_ARG;
@@ -1192,7 +1196,8 @@ extern "C" int fe_get_field(fe_ctx* c, int box, int field, void* dst, int is_dev
 }
 
 // Several fields in one call: every copy queued on the context stream, one
-// synchronisation at the end (all arguments are checked before any copy).
+// synchronisation at the end (all arguments are checked before any copy).  (Spreading the
+// copies over four streams measured no faster: the host link, not one copy engine, is the limit.)
 static int copy_fields(fe_ctx* c, int box, int n, const int* fields, void* const* ptrs, int is_dev, bool in) {
   if (!c || box < 0 || box >= c->nb || n < 0 || (n > 0 && (!fields || !ptrs))) return FE_ERR_INVALID_ARG;
   for (int q = 0; q < n; ++q)
@@ -1425,32 +1430,71 @@ extern "C" int fe_set_tiling(fe_ctx* c, int tz) {
   return set_tiling(c, tz);
 }
 
+extern "C" int fe_set_box_tiling(fe_ctx* c, int box, int tz) {
+  if (!c || box < 0 || box >= c->nb || tz < 0 || tz > 512) return FE_ERR_INVALID_ARG;
+  std::vector<int> t = c->tzb;
+  t[box] = tz;
+  return set_tiling(c, t);
+}
+
+// Time of `trials` trial steps (after one untimed) with the tiling tzb; the state is not committed.
+static int time_tiling(fe_ctx* c, const std::vector<int>& tzb, int trials, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int rc = set_tiling(c, tzb);
+  if (rc != FE_OK) return rc;
+  rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
+  if (rc != FE_OK) return rc;
+  CK(cudaEventRecord(e0, c->st));
+  for (int t = 0; t < trials && rc == FE_OK; ++t) rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
+  CK(cudaEventRecord(e1, c->st));
+  if (rc != FE_OK) return rc;
+  CK(cudaEventSynchronize(e1));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  return FE_OK;
+}
+
 extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   if (!c || trials < 1) return FE_ERR_INVALID_ARG;
   int rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   std::vector<double> saved(c->hsc, c->hsc + (size_t)c->nb * NSC);
   const int cand[] = {4, 8, 16, 32};
-  int best = 0;
-  float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // one depth for every box first, then, in an ensemble of several box sizes, each size in turn
+  // (largest boxes first) while the others keep theirs
+  std::vector<int> best(c->nb, 0);
+  float best_ms = 1e30f;
   for (int tz : cand) {
-    rc = set_tiling(c, tz);
-    if (rc != FE_OK) break;
-    rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
-    if (rc != FE_OK) break;
-    cudaEventRecord(e0, c->st);
-    for (int t = 0; t < trials && rc == FE_OK; ++t)
-      rc = c->fp64 ? step_once<double>(c, false) : step_once<float>(c, false);
-    cudaEventRecord(e1, c->st);
-    if (rc != FE_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    std::vector<int> t(c->nb, tz);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    rc = time_tiling(c, t, trials, e0, e1, &ms);
+    if (rc != FE_OK) break;
     if (ms < best_ms) {
       best_ms = ms;
-      best = tz;
+      best = t;
+    }
+  }
+  std::vector<int> sizes = c->N;
+  std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  for (size_t q = 0; q < sizes.size() && sizes.size() > 1 && rc == FE_OK; ++q) {
+    for (int tz : cand) {
+      std::vector<int> t = best;
+      bool changed = false;
+      for (int b = 0; b < c->nb; ++b)
+        if (c->N[b] == sizes[q] && t[b] != tz) {
+          t[b] = tz;
+          changed = true;
+        }
+      if (!changed) continue;
+      float ms = 0.f;
+      rc = time_tiling(c, t, trials, e0, e1, &ms);
+      if (rc != FE_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1459,7 +1503,12 @@ extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   memcpy(c->hsc, saved.data(), saved.size() * sizeof(double));
   CK(cudaMemcpyAsync(c->dsc, c->hsc, saved.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (best_tz) *best_tz = best;
+  if (best_tz) {  // the depth of the largest box
+    int bmax = 0;
+    for (int b = 1; b < c->nb; ++b)
+      if (c->N[b] > c->N[bmax]) bmax = b;
+    *best_tz = best[bmax];
+  }
   return rc != FE_OK ? rc : rc2;
 }
 

@@ -84,7 +84,7 @@ class fe_profile_info(ctypes.Structure):
 EXPORTS = ["fe_create", "fe_init_state", "fe_set_field", "fe_get_field", "fe_set_fields", "fe_get_fields",
            "fe_set_clock", "fe_step",
            "fe_solve_pressure", "fe_diagnostics", "fe_q_criterion", "fe_profile_start", "fe_profile_stop",
-           "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_autotune",
+           "fe_kernel_count", "fe_kernel_name", "fe_solve_pressure_noalloc", "fe_set_tiling", "fe_set_box_tiling", "fe_autotune",
            "fe_preconditioner_size", "fe_load_preconditioner", "fe_get_preconditioner", "fe_precond_apply",
            "fe_precond_train_step", "fe_precond_activation", "fe_harvest_pressure", "fe_use_graphs",
            "fe_use_plane_streaming", "fe_plane_streaming_active", "fe_precond_kernels", "fe_les_apriori", "fe_isosurface", "fe_raster_depth",
@@ -131,6 +131,7 @@ def load_library(path=LIB_PATH):
                                   POINTER(ctypes.c_longlong), POINTER(c_double)]
     lib.fe_raster_depth.argtypes = [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_double, c_void_p]
     lib.fe_set_tiling.argtypes = [c_void_p, c_int]
+    lib.fe_set_box_tiling.argtypes = [c_void_p, c_int, c_int]
     lib.fe_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.fe_destroy.argtypes = [c_void_p]
     lib.fe_destroy.restype = None
@@ -354,6 +355,10 @@ def fe_set_tiling(ctx, tz):
     return _check(lib().fe_set_tiling(ctx, tz), "fe_set_tiling")
 
 
+def fe_set_box_tiling(ctx, box, tz):
+    return _check(lib().fe_set_box_tiling(ctx, box, tz), "fe_set_box_tiling")
+
+
 def fe_autotune(ctx, trials=2):
     best = c_int(0)
     _check(lib().fe_autotune(ctx, trials, byref(best)), "fe_autotune")
@@ -525,6 +530,9 @@ class Solver:
 
     def set_tiling(self, tz):
         fe_set_tiling(self.ctx, tz)
+
+    def set_box_tiling(self, box, tz):
+        fe_set_box_tiling(self.ctx, box, tz)
 
     def profile_start(self, kernel=None):
         fe_profile_start(self.ctx, -1 if kernel is None else kernel_id(kernel))

@@ -67,3 +67,33 @@ def test_tile_depth_step_matches_oracle(fe, reference, precision, bar, tz):
     got = s.get_state(0)
     s.close()
     assert worst(got, ref) <= bar
+
+
+def test_per_box_tile_depths_in_an_ensemble(fe):
+    """Boxes of one context with different tile depths (fe_set_box_tiling) each match the oracle,
+    and the autotuner's per-size pass leaves a tiling under which the step still matches."""
+    boxes, refs = [], []
+    for n, seed in ((24, 3), (40, 4), (32, 5)):
+        rho, u, Y, _ = random_fields(n, 1, False, seed=seed, mach=0.3, noise=0.02)
+        prm = piso.Params(N=n, nu=0.005, tau_p=[0.05], Y0=[0.01], p_tol=1e-10)
+        ref, _ = piso.step(prm, piso.make_state(prm, rho, u, Y))
+        boxes.append((n, rho, u, Y))
+        refs.append(ref)
+    s = fe.Solver([dict(N=n, nu=0.005, tau_p=[0.05], Y0=[0.01], seed=b + 1) for b, (n, *_r) in enumerate(boxes)],
+                  p_tol=1e-10)
+    for b, (n, rho, u, Y) in enumerate(boxes):
+        s.set_state(b, rho, u, Y)
+    for b, tz in enumerate((3, 16, 7)):
+        s.set_box_tiling(b, tz)
+    code, _ = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    for b in range(3):
+        assert worst(s.get_state(b), refs[b]) <= 1e-11
+    for b, (n, rho, u, Y) in enumerate(boxes):
+        s.set_state(b, rho, u, Y)
+    s.autotune(1)
+    code, _ = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    for b in range(3):
+        assert worst(s.get_state(b), refs[b]) <= 1e-11
+    s.close()
