@@ -355,6 +355,10 @@ extern "C" int fe_create(const fe_params* prm, void* stream, fe_ctx** out) {
     // ring kernels need their shared-memory limits set before any capture (else z-marching kernels run)
     if (c->fp64) rprepare<double>();
     else rprepare<float>();
+    if (prm->dust_model == FE_DUST_TWO_FLUID) {
+      if (c->fp64) tfprepare<double>();
+      else tfprepare<float>();
+    }
   }
   const int nb = c->nb, nd = prm->n_dust;
   c->N.assign(prm->N, prm->N + nb);

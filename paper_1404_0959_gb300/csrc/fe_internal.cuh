@@ -607,6 +607,7 @@ struct Launch {
 // Two-fluid dust phase after the gas step s -> ks (twofluid.cu); V = u in set s.
 template <typename T> void launch_two_fluid(const Launch& L, int s, int ks);
 template <typename T> void launch_two_fluid_init(const Launch& L, int s, int box);
+template <typename T> int tfprepare();  // shared-memory limits of the two-fluid ring kernels (before any capture)
 
 // Step kernels (step_kernels.cu); T = field type.
 template <typename T> void launch_dt(const Launch& L, int s, int first);

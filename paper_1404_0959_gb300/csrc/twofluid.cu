@@ -12,9 +12,12 @@
 //   sigma = sigma^n - dt/2 [D(F^n) + D(F*)], m likewise;
 //   backward-Euler drag after each stage: V = u^{n+1} + (m/sigma - u^{n+1}) tau/(tau + dt),
 //   Y = sigma / rho^{n+1}.
-// One thread walks the z-planes of a column; neighbours through the read-only
-// cache with periodic wrap (the general stencil form of the step kernels).
-#include "fe_internal.cuh"
+// Two forms: the ring kernels (every box's N a multiple of the 16-byte chunk;
+// one class per launch, its planes and the gas planes arriving in shared-memory
+// rings by asynchronous copies, zring.cuh) and the general kernels (one thread
+// walks the z-planes of a column; neighbours through the read-only cache with
+// periodic wrap).  Both evaluate the same expressions in the same order.
+#include "zring.cuh"
 
 namespace fe {
 
@@ -173,6 +176,209 @@ __global__ void __launch_bounds__(NTHR) k_tf_corr(const BoxDev* boxes, const int
   }
 }
 
+// ---- ring forms (one class j per launch) --------------------------------------------------------
+// D(F) and D(G_m) from ring views of the carrier density, the carrier velocity, the class's Y and V,
+// and the carrier face fluxes (the same expressions as tf_div: I4 to the +1/2 face from offsets
+// -1..2, to the -1/2 face from -2..1).
+template <typename T, typename RP, typename GT>
+__device__ __forceinline__ void tfr_div(const RP& R, const GT& G, int k, int r, T ih, T& DF, T (&DG)[3]) {
+  const ZView<T> rho = R.view(0, k, G, r), Y = R.view(4, k, G, r);
+  const ZView<T> u[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
+  const ZView<T> V[3] = {R.view(5, k, G, r), R.view(6, k, G, r), R.view(7, k, G, r)};
+  T php[3], phm[3];
+  R.faces(0, k, G, r, php, phm);
+  DF = T(0);
+  DG[0] = DG[1] = DG[2] = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int o = side ? -1 : 0;  // plus face first, as in tf_div
+      const T sgn = side ? T(-1) : T(1);
+      const T slip = zI4(V[d], G, d, o) - zI4(u[d], G, d, o);
+      const T F = ((side ? phm[d] : php[d]) + zI4(rho, G, d, o) * slip) * zI4(Y, G, d, o);
+      DF += sgn * F;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) DG[m] += sgn * F * zI4(V[m], G, d, o);
+    }
+  }
+  DF *= ih;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) DG[m] *= ih;
+}
+
+#define TF_RING_PROLOGUE(P)                              \
+  const TileXYZ t = tile_xyz(boxes, work);               \
+  const BoxDev& B = boxes[t.box];                        \
+  const RGeom<T> G(t.x0, t.y0, B.N);                     \
+  const int tid = threadIdx.x + RTX * threadIdx.y;       \
+  extern __shared__ __align__(16) unsigned char rsm[];   \
+  P R;                                                   \
+  R.init(rsm, t.k0, t.kend)
+
+// predictor: rho^n, u^n (3), Y^n_j, V^n_j (3) | phi^n | rho^{n+1}, u^{n+1} (3)
+template <typename T>
+using TfPredPlan = RingPlan<T, 1, 8, 3, 4>;
+template <typename T>
+__global__ void __launch_bounds__(RNT) kr_tf_pred(const BoxDev* boxes, const int2* work, int s, int ks, int j) {
+  TF_RING_PROLOGUE(TfPredPlan<T>);
+  R.gs[0] = TF<T>(B, S(s, F_RHO));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[1 + m] = TF<T>(B, S(s, F_U0 + m));
+  R.gs[4] = TF<T>(B, S(s, F_Y0 + j));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[5 + m] = TF<T>(B, S(s, F_V0 + 3 * j + m));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = TF<T>(B, S(s, F_PHI0 + d));
+  R.gc[0] = TF<T>(B, S(ks, F_RHO));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[1 + m] = TF<T>(B, S(ks, F_U0 + m));
+  T* __restrict__ tfn = TF<T>(B, W_TFN0 + 4 * j);
+  T* __restrict__ tfs = TF<T>(B, W_TFS0 + 4 * j);
+  T* __restrict__ tfn_m[3] = {TF<T>(B, W_TFN0 + 4 * j + 1), TF<T>(B, W_TFN0 + 4 * j + 2), TF<T>(B, W_TFN0 + 4 * j + 3)};
+  T* __restrict__ tfs_m[3] = {TF<T>(B, W_TFS0 + 4 * j + 1), TF<T>(B, W_TFS0 + 4 * j + 2), TF<T>(B, W_TFS0 + 4 * j + 3)};
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT];
+  const T tau = (T)B.tau_p[j];
+  const T rr = tau / (tau + dt);
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+    const P2<T> cr1 = R.cen(0, k, tid);
+    const P2<T> cu1[3] = {R.cen(1, k, tid), R.cen(2, k, tid), R.cen(3, k, tid)};
+    T oDF[2], oDG[3][2], oY[2], oV[3][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      T DF, DG[3];
+      tfr_div<T>(R, G, k, r, ih, DF, DG);
+      const T rn = R.view(0, k, G, r).c(), ir1 = T(1) / pc<T>(cr1, r);
+      const T sig_n = rn * R.view(4, k, G, r).c();
+      const T sig = sig_n - dt * DF;
+      const T isig = T(1) / sig;
+      oDF[r] = DF;
+      oY[r] = sig * ir1;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        oDG[m][r] = DG[m];
+        const T mom = sig_n * R.view(5 + m, k, G, r).c() - dt * DG[m];
+        const T um = pc<T>(cu1[m], r);
+        oV[m][r] = um + (mom * isig - um) * rr;
+      }
+    }
+    stp(tfn + c, oDF[0], oDF[1]);
+    stp(tfs + c, oY[0], oY[1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      stp(tfn_m[m] + c, oDG[m][0], oDG[m][1]);
+      stp(tfs_m[m] + c, oV[m][0], oV[m][1]);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// corrector: rho^{n+1}, u^{n+1} (3), Y*_j, V*_j (3) | phi^{n+1} | rho^n, Y^n_j, D(F^n), D(G^n) (3), V^n_j (3)
+template <typename T>
+using TfCorrPlan = RingPlan<T, 1, 8, 3, 9>;
+template <typename T>
+__global__ void __launch_bounds__(RNT) kr_tf_corr(const BoxDev* boxes, const int2* work, double* part, int s, int ks,
+                                                  int j) {
+  TF_RING_PROLOGUE(TfCorrPlan<T>);
+  R.gs[0] = TF<T>(B, S(ks, F_RHO));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[1 + m] = TF<T>(B, S(ks, F_U0 + m));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) R.gs[4 + q] = TF<T>(B, W_TFS0 + 4 * j + q);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gf[d] = TF<T>(B, S(ks, F_PHI0 + d));
+  R.gc[0] = TF<T>(B, S(s, F_RHO));
+  R.gc[1] = TF<T>(B, S(s, F_Y0 + j));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) R.gc[2 + q] = TF<T>(B, W_TFN0 + 4 * j + q);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[6 + m] = TF<T>(B, S(s, F_V0 + 3 * j + m));
+  T* __restrict__ yo = TF<T>(B, S(ks, F_Y0 + j));
+  T* __restrict__ vo[3] = {TF<T>(B, S(ks, F_V0 + 3 * j)), TF<T>(B, S(ks, F_V0 + 3 * j + 1)),
+                           TF<T>(B, S(ks, F_V0 + 3 * j + 2))};
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], hdt = T(0.5) * dt;
+  const T tau = (T)B.tau_p[j];
+  const T rr = tau / (tau + dt);
+  DotAcc<T> ady;
+  SumAcc<T> abad;
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+    const P2<T> crn = R.cen(0, k, tid), cyn = R.cen(1, k, tid), cfn = R.cen(2, k, tid);
+    const P2<T> cgn[3] = {R.cen(3, k, tid), R.cen(4, k, tid), R.cen(5, k, tid)};
+    const P2<T> cvn[3] = {R.cen(6, k, tid), R.cen(7, k, tid), R.cen(8, k, tid)};
+    T oY[2], oV[3][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      T DF, DG[3];
+      tfr_div<T>(R, G, k, r, ih, DF, DG);
+      const T rn = pc<T>(crn, r), r1 = R.view(0, k, G, r).c();
+      const T sig_n = rn * pc<T>(cyn, r);
+      const T sig = sig_n - hdt * (pc<T>(cfn, r) + DF);
+      const T isig = T(1) / sig;
+      const T Yk = sig / r1;
+      oY[r] = Yk;
+      ady.add(r1, Yk);
+      bool bad = !isfinite(Yk);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T mom = sig_n * pc<T>(cvn[m], r) - hdt * (pc<T>(cgn[m], r) + DG[m]);
+        const T um = R.view(1 + m, k, G, r).c();
+        const T Vm = um + (mom * isig - um) * rr;
+        oV[m][r] = Vm;
+        bad = bad || !isfinite(Vm);
+      }
+      if (bad) abad.add(T(1));
+    }
+    stp(yo + c, oY[0], oY[1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) stp(vo[m] + c, oV[m][0], oV[m][1]);
+  }
+  cp_async_wait<0>();
+  Red<T> acc[2] = {abad.red(), ady.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(acc, B, part, res, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.sc[SC_BAD] += res[0];
+      B.sc[SC_DUST0 + j] = res[1];
+    }
+  }
+}
+
+// Dynamic shared-memory limits of the ring forms, set once per device outside any capture.
+constexpr int kTfMaxDev = 64;
+template <typename T>
+struct TfReady {
+  static int ok[kTfMaxDev];
+};
+template <typename T>
+int TfReady<T>::ok[kTfMaxDev] = {};
+template <typename T>
+int tfprepare() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTfMaxDev) return 0;
+  const bool a = cudaFuncSetAttribute(kr_tf_pred<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TfPredPlan<T>::bytes) == cudaSuccess;
+  const bool b = cudaFuncSetAttribute(kr_tf_corr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TfCorrPlan<T>::bytes) == cudaSuccess;
+  cudaGetLastError();  // a refused limit is not an error of the context
+  TfReady<T>::ok[dev] = a && b ? 1 : -1;
+  return a && b;
+}
+template <typename T>
+static bool tf_ring_ready() {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kTfMaxDev && TfReady<T>::ok[dev] == 1;
+}
+
 // V = u (every class) in state set s: the dust starts with the gas velocity
 template <typename T>
 __global__ void __launch_bounds__(NTHR) k_tf_init(const BoxDev* boxes, const int2* work, int s, int only_box) {
@@ -190,6 +396,15 @@ __global__ void __launch_bounds__(NTHR) k_tf_init(const BoxDev* boxes, const int
 #define TF_GRID L.nblocks, dim3(TX, TY), 0, L.st
 template <typename T>
 void launch_two_fluid(const Launch& L, int s, int ks) {
+  if (L.ring_ok && tf_ring_ready<T>()) {  // one class per launch; predictor of every class first
+    for (int j = 0; j < L.nd; ++j)
+      FE_LAUNCH(L, KID_TF_PRED,
+                (kr_tf_pred<T><<<L.nblocks, dim3(RTX, TY), TfPredPlan<T>::bytes, L.st>>>(L.boxes, L.work, s, ks, j)));
+    for (int j = 0; j < L.nd; ++j)
+      FE_LAUNCH(L, KID_TF_CORR, (kr_tf_corr<T><<<L.nblocks, dim3(RTX, TY), TfCorrPlan<T>::bytes, L.st>>>(
+                                    L.boxes, L.work, L.part, s, ks, j)));
+    return;
+  }
   FE_LAUNCH(L, KID_TF_PRED, (k_tf_pred<T><<<TF_GRID>>>(L.boxes, L.work, s, ks)));
   FE_LAUNCH(L, KID_TF_CORR, (k_tf_corr<T><<<TF_GRID>>>(L.boxes, L.work, L.part, s, ks)));
 }
@@ -201,5 +416,7 @@ template void launch_two_fluid<double>(const Launch&, int, int);
 template void launch_two_fluid<float>(const Launch&, int, int);
 template void launch_two_fluid_init<double>(const Launch&, int, int);
 template void launch_two_fluid_init<float>(const Launch&, int, int);
+template int tfprepare<double>();
+template int tfprepare<float>();
 
 }  // namespace fe

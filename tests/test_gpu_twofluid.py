@@ -79,8 +79,10 @@ def solver(fe, prm, precision, **kw):
 @pytest.mark.parametrize("N,tau,closure,slip", [(16, (0.05,), piso.BAROTROPIC, True),
                                                 (24, (0.02, 0.1, 0.3), piso.BAROTROPIC, True),
                                                 (16, (0.02, 0.1, 0.3), piso.FOURIER, True),
-                                                (20, (0.1,), piso.BAROTROPIC, False)])
+                                                (20, (0.1,), piso.BAROTROPIC, False),
+                                                (21, (0.05, 0.2), piso.BAROTROPIC, True)])
 def test_fp64_two_fluid_step_matches_oracle(fe, N, tau, closure, slip):
+    """Even N runs the ring kernels (one class per launch), N = 21 the general column kernels."""
     prm, st = case(N, tau, closure, slip=slip)
     ref, rinfo = piso.step(prm, st)
     s = solver(fe, prm, fe.FE_FP64)
@@ -110,8 +112,10 @@ def test_fp64_two_fluid_three_steps_and_conservation(fe):
         assert abs(b - a) <= 1e-13 * a
 
 
-def test_mixed_two_fluid_step_matches_oracle(fe):
-    prm, st = case(24, (0.02, 0.1, 0.3), seed=5, rounded=True)
+@pytest.mark.parametrize("N", [24, 30])
+def test_mixed_two_fluid_step_matches_oracle(fe, N):
+    """N = 24 runs the ring kernels, N = 30 (not a multiple of four cells) the general ones."""
+    prm, st = case(N, (0.02, 0.1, 0.3), seed=5, rounded=True)
     ref, _ = piso.step(prm, st)
     s = solver(fe, prm, fe.FE_FP32_MIXED)
     s.load_state(0, st)
