@@ -161,3 +161,25 @@ def test_batched_field_copies(fe):
         fe.fe_set_fields(s.ctx, 0, [fe.FE_RHO, 999], [dev[0].data_ptr(), dev[1].data_ptr()], 1)
     assert np.array_equal(s.get_field(0, fe.FE_RHO), before)
     s.close()
+
+
+@pytest.mark.parametrize("N,prec", [(24, 0), (32, 1), (21, 1)])
+def test_batched_copies_through_page_locked_host_memory(fe, N, prec):
+    # page-locked host buffers (the end-to-end benchmark's path), both precisions, an odd size
+    import torch
+    rho, u, Y, _ = random_fields(N, 1, False, seed=22, noise=0.02)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])], precision=prec)
+    s.set_state(0, rho, u, Y)
+    ids = [fe.FE_RHO, fe.FE_UX, fe.FE_UY, fe.FE_UZ, fe.FE_P, fe.FE_PHIX, fe.FE_PHIY, fe.FE_PHIZ, fe.FE_Y0]
+    single = {f: s.get_field(0, f) for f in ids}
+    dt = torch.float64 if prec == 0 else torch.float32
+    pinned = [torch.empty((N, N, N), dtype=dt, pin_memory=True) for _ in ids]
+    fe.fe_get_fields(s.ctx, 0, ids, [h.data_ptr() for h in pinned], 0)
+    for f, h in zip(ids, pinned):
+        assert np.array_equal(h.numpy(), single[f])
+    for h in pinned:
+        h.mul_(3.0)
+    fe.fe_set_fields(s.ctx, 0, ids, [h.data_ptr() for h in pinned], 0)
+    for f, h in zip(ids, pinned):
+        assert np.array_equal(s.get_field(0, f), h.numpy())
+    s.close()
