@@ -400,7 +400,7 @@ def ensemble_only(args):
 
 
 def part_only(args):
-    """--part les|twofluid|twoway|iso: one of the scope table's further rows alone at --N (FP32 fields,
+    """--part les|twofluid|twoway|fourier|iso: one of the scope table's further rows alone at --N (FP32 fields,
     the benchmark workload's physics), CUDA-event timed, one JSON line."""
     import torch
     from paper_1404_0959_gb300 import build, fe
@@ -478,6 +478,37 @@ def part_only(args):
                 gbs = words * 4 * float(N) ** 3 / (ms / 1e3) / 1e9
                 r[k] = {"ms_per_launch": ms, "alg_words_per_cell": words, "achieved_gbs": gbs, "frac": gbs / hbm}
             res["two_way" if two else "one_way"] = r
+            s.close()
+        out.update(res)
+    elif args.part == "fourier":
+        # the Fourier-closure workloads: 128^3 (one class) and 512^3 (three classes), FP32 fields
+        res = {}
+        for name, n_ in (("hit128f", 128), ("hit512f", 512)):
+            w = WORKLOADS[name]
+            bx_ = dict(N=n_, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], mach_rms=w["mach_rms"], k0=w["k0"], seed=0)
+            s = fe.Solver([bx_], precision=fe.FE_FP32_MIXED, closure=w["closure"], p_tol=w["p_tol"], p_maxit=1000,
+                          stream=stream.cuda_stream)
+            s.init_state(0, fe.FE_INIT_SPECTRAL)
+            s.autotune(1)
+            s.use_graphs(True)
+            code, _ = s.step(args.warmup)
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            code, info = s.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            assert code == fe.FE_OK, fe.fe_strerror(code)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            r = {"N": n_, "classes": len(w["tau_p"]), "ms_per_step": ms, "value": float(n_) ** 3 / (ms / 1e3),
+                 "unit": "cell-steps/s", "krylov_iters_last_step": info[0]["iters"]}
+            s.use_graphs(False)
+            for k in ("fe_cell", "fe_face", "fluxn", "dust"):
+                s.profile_start(k)
+                s.step(2)
+                pr = s.profile_stop()
+                r[k + "_ms_per_step"] = pr["target_ms"] / 2
+            res[name] = r
             s.close()
         out.update(res)
     elif args.part == "iso":
@@ -577,9 +608,9 @@ def main():
                     help="time the 64-box ensemble in one context against one context per box")
     ap.add_argument("--unet", action="store_true",
                     help="time only the learned preconditioner's network pass (K applications at N^3)")
-    ap.add_argument("--part", default=None, choices=["les", "twofluid", "twoway", "iso"],
+    ap.add_argument("--part", default=None, choices=["les", "twofluid", "twoway", "fourier", "iso"],
                     help="time one further row alone: a-priori LES, two-fluid dust step, two-way coupled step, "
-                         "Q iso-surface + raster")
+                         "Fourier-closure workloads, Q iso-surface + raster")
     ap.add_argument("--width", type=int, default=2048, help="depth image width for --part iso")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -82,7 +82,8 @@ static const char* kKernelNames[] = {
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
     "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec",
-    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "tf_pred", "tf_corr", "other"};
+    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "tf_pred", "tf_corr", "fe_cell", "fe_face",
+    "other"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
 static_assert(KID_COUNT <= FE_PROFILE_MAX_KERNELS, "profile counters");
 
@@ -179,8 +180,11 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
   int w[] = {W_DIV, W_DIVPHI, W_RN0, W_RN1, W_RN2, W_AN0, W_AN1, W_AN2, W_PSI, W_DINV, W_HB0, W_HB1, W_HB2,
              W_PS0, W_PS1, W_PS2, W_PW0, W_PW1, K_B, K_X, K_R, K_PD, K_Q, K_AUX};
   for (int s : w) plan.push_back({s, e});
-  if (fourier)
-    for (int s : {W_EW0, W_EW1, W_FEN}) plan.push_back({s, e});
+  if (fourier) {
+    for (int s : {(int)W_EW0, (int)W_EW1, (int)W_FEN, (int)W_FEH, (int)W_FET}) plan.push_back({s, e});
+    for (int q = 0; q < 9; ++q) plan.push_back({W_FEG0 + q, e});
+    for (int q = 0; q < 3; ++q) plan.push_back({W_FEF0 + q, e});
+  }
   for (int j = 0; j < nd; ++j) {
     plan.push_back({W_FYN0 + j, e});
     plan.push_back({W_YW0 + j, e});

@@ -60,7 +60,10 @@ enum WorkSlot {
   K_B64,                  // double right-hand side (mixed precision refinement)
   K_AUX,                  // scratch (diagnostics, user solve)
   W_YSUM,                 // two-way coupling with several classes: sum_j Y_j^n of the step
-  NSLOT
+  // Fourier closure, total-energy flux: per cell H = E + p/rho, T and the Gauss gradients h Gc_m u_l
+  // (m, l = 0..2: slot W_FEG0 + 3 m + l); the +1/2 face fluxes F_E along x, y, z
+  W_FEH, W_FET, W_FEG0, W_FEF0 = W_FEG0 + 9,
+  NSLOT = W_FEF0 + 3
 };
 
 // ---- per-box scalars (double) ---------------------------------------------
@@ -567,7 +570,8 @@ enum KernelId {
   KID_CG_INIT, KID_CG_MATVEC, KID_CG_UPDATE, KID_CG_DIR, KID_TRUE_RES,
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
   KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
-  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_TF_PRED, KID_TF_CORR, KID_OTHER,
+  KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_TF_PRED, KID_TF_CORR, KID_FE_CELL,
+  KID_FE_FACE, KID_OTHER,
   KID_COUNT
 };
 

@@ -38,46 +38,94 @@ __device__ __forceinline__ int bx(int d) { return d == 0 ? -1 : 0; }
 __device__ __forceinline__ int by(int d) { return d == 1 ? -1 : 0; }
 __device__ __forceinline__ int bz(int d) { return d == 2 ? -1 : 0; }
 
-// Viscous face stress tau_dm on the d-face of cell offset o:
-// mu (G4_d u_m + I4_d Gc_m u_d - 2/3 delta_dm I4_d div).
+// ---- Fourier closure: the total-energy face flux in two passes -------------------------------
+// F_E = phi I4(H) - sum_m tau_dm I4(u_m) - kappa G4(T) on a d-face reads H and T at four cells
+// along d and the Gauss gradients h Gc_m u_d at four cells along d for every face; evaluated inside
+// the dust kernels it cost each face twice (from both of its cells) and hundreds of neighbour loads
+// per cell.  Here (1) every cell's H = E + p/rho, T and h Gc_m u_l (nine) are formed once, (2) every
+// cell's three +1/2 face fluxes once from star stencils of those, and the dust kernels difference
+// the face arrays.  face stress tau_dm = mu (G4_d u_m + I4_d(Gc_m u_d) - 2/3 delta_dm I4_d(div u)).
+//
+// k_fe_cell: velocity slots u0..u0+2, density and pressure slots; E from slot es, or (es < 0) the
+// level-n energy c_v T^n + |u^n|^2/2 of set s; T = T^n of set s (tmode 0) or p/(rho R) (tmode 1).
 template <typename T>
-__device__ __forceinline__ T face_stress(const T* const (&u)[3], const T* div, const Nbr& n, int d, int m,
-                                         int ox, int oy, int oz, T ih, T mu) {
-  T g[4];
+__global__ void __launch_bounds__(NTHR) k_fe_cell(const BoxDev* boxes, const int2* work, int s, int u0, int rhos,
+                                                  int ps, int es, int tmode) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* u[3] = {F<T>(B, u0), F<T>(B, u0 + 1), F<T>(B, u0 + 2)};
+  const T* un[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
+  const T* Tn = F<T>(B, S(s, F_T));
+  const T* rho = F<T>(B, rhos);
+  const T* p = F<T>(B, ps);
+  const T* E = es >= 0 ? F<T>(B, es) : nullptr;
+  T* __restrict__ Hc = F<T>(B, W_FEH);
+  T* __restrict__ Tc = F<T>(B, W_FET);
+  const T cv = (T)B.cv, Rg = (T)B.R;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    T e;
+    if (E) {
+      e = __ldg(&E[c]);
+    } else {
+      const T uu = __ldg(&un[0][c]) * __ldg(&un[0][c]) + __ldg(&un[1][c]) * __ldg(&un[1][c]) +
+                   __ldg(&un[2][c]) * __ldg(&un[2][c]);
+      e = cv * __ldg(&Tn[c]) + T(0.5) * uu;
+    }
+    const T pc = __ldg(&p[c]), rc = __ldg(&rho[c]);
+    Hc[c] = e + pc / rc;
+    Tc[c] = tmode ? pc / (rc * Rg) : __ldg(&Tn[c]);
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    int s = t - 1;
-    g[t] = Gc_h<T>(u[d], n, m, ox + (d == 0 ? s : 0), oy + (d == 1 ? s : 0), oz + (d == 2 ? s : 0));
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) F<T>(B, W_FEG0 + 3 * m + l)[c] = Gc_h<T>(u[l], n, m, 0, 0, 0);
   }
-  T ig = (T(9) * (g[1] + g[2]) - (g[0] + g[3])) * T(0.0625);  // I4_d of h*Gc_m u_d
-  T tau = (G4f_h<T>(u[m], n, d, ox, oy, oz) + ig) * ih;
-  if (d == m) tau -= T(2.0 / 3.0) * I4f<T>(div, n, d, ox, oy, oz);  // W_DIV holds div u itself
-  return mu * tau;
 }
 
-// Total-energy face flux on the d-face of cell offset o:
-// phi I4(H) - sum_m tau_dm I4(u_m) - kappa G4(T), with H and T given per cell
-// by the functors.
-template <typename T, typename HF, typename TF>
-__device__ __forceinline__ T energy_face(const T* const (&u)[3], const T* const (&phi)[3], const T* div,
-                                         const Nbr& n, int d, int ox, int oy, int oz, T ih, T mu, T kappa,
-                                         HF Hat, TF Tat) {
-  T hq[4], tq[4];
+// k_fe_face: the three +1/2 face fluxes of every cell (face d of cell c between c and c + e_d) from
+// k_fe_cell's fields, the velocity u0..u0+2, the face mass fluxes phi0..phi0+2 and W_DIV (div u).
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fe_face(const BoxDev* boxes, const int2* work, int u0, int phi0) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T* u[3] = {F<T>(B, u0), F<T>(B, u0 + 1), F<T>(B, u0 + 2)};
+  const T* Hc = F<T>(B, W_FEH);
+  const T* Tc = F<T>(B, W_FET);
+  const T* div = F<T>(B, W_DIV);
+  const T ih = (T)B.ih, mu = (T)B.mu, kappa = (T)B.kappa;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    int s = t - 1;
-    int q = n.at(d, ox, oy, oz, s);
-    hq[t] = Hat(q);
-    tq[t] = Tat(q);
+    for (int d = 0; d < 3; ++d) {
+      T hq[4], tq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = n.at(d, 0, 0, 0, q - 1);
+        hq[q] = __ldg(&Hc[a]);
+        tq[q] = __ldg(&Tc[a]);
+      }
+      const T IH = (T(9) * (hq[1] + hq[2]) - (hq[0] + hq[3])) * T(0.0625);
+      const T G4T = (T(27) * (tq[2] - tq[1]) - (tq[3] - tq[0])) * T(1.0 / 24.0) * ih;
+      T work = T(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T* gmd = F<T>(B, W_FEG0 + 3 * m + d);  // h Gc_m u_d
+        T g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] = __ldg(&gmd[n.at(d, 0, 0, 0, q - 1)]);
+        const T ig = (T(9) * (g[1] + g[2]) - (g[0] + g[3])) * T(0.0625);
+        T tau = (G4f_h<T>(u[m], n, d, 0, 0, 0) + ig) * ih;
+        if (d == m) tau -= T(2.0 / 3.0) * I4f<T>(div, n, d, 0, 0, 0);
+        work += (mu * tau) * I4f<T>(u[m], n, d, 0, 0, 0);
+      }
+      const T ph = __ldg(&F<T>(B, phi0 + d)[c]);
+      F<T>(B, W_FEF0 + d)[c] = ph * IH - work - kappa * G4T;
+    }
   }
-  T IH = (T(9) * (hq[1] + hq[2]) - (hq[0] + hq[3])) * T(0.0625);
-  T G4T = (T(27) * (tq[2] - tq[1]) - (tq[3] - tq[0])) * T(1.0 / 24.0) * ih;
-  T work = T(0);
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-    work += face_stress<T>(u, div, n, d, m, ox, oy, oz, ih, mu) * I4f<T>(u[m], n, d, ox, oy, oz);
-  T ph = __ldg(&phi[d][n(ox, oy, oz)]);
-  return ph * IH - work - kappa * G4T;
 }
 
 // ---------------------------------------------------------------------------------
@@ -155,21 +203,12 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_fluxn(const BoxDev* b
       }
       F<T>(B, W_FYN0 + j)[c] = acc * ih;
     }
-    if (FOURIER) {
-      const T* Tf = F<T>(B, S(s, F_T));
-      const T* p = F<T>(B, S(s, F_P));
-      const T* div = F<T>(B, W_DIV);
-      const T cv = (T)B.cv;
-      auto Hat = [&](int q) {
-        T uu = __ldg(&u[0][q]) * __ldg(&u[0][q]) + __ldg(&u[1][q]) * __ldg(&u[1][q]) + __ldg(&u[2][q]) * __ldg(&u[2][q]);
-        return cv * __ldg(&Tf[q]) + T(0.5) * uu + __ldg(&p[q]) / __ldg(&rho[q]);
-      };
-      auto Tat = [&](int q) { return __ldg(&Tf[q]); };
+    if (FOURIER) {  // D(F_E^n) from the face fluxes of k_fe_face
       T acc = T(0);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        acc += energy_face<T>(u, phi, div, n, d, 0, 0, 0, ih, (T)B.mu, (T)B.kappa, Hat, Tat) -
-               energy_face<T>(u, phi, div, n, d, bx(d), by(d), bz(d), ih, (T)B.mu, (T)B.kappa, Hat, Tat);
+        const T* fe = F<T>(B, W_FEF0 + d);
+        acc += __ldg(&fe[c]) - __ldg(&fe[n(bx(d), by(d), bz(d))]);
       }
       F<T>(B, W_FEN)[c] = acc * ih;
     }
@@ -324,8 +363,7 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* bo
       }
       T Ek = T(0);
       if (fourier) {
-        const T* div = F<T>(B, W_DIV);
-        const T cv = (T)B.cv, Rg = (T)B.R;
+        const T cv = (T)B.cv;
         const T* un[3] = {F<T>(B, S(s, F_U0)), F<T>(B, S(s, F_U1)), F<T>(B, S(s, F_U2))};
         const T* Tn = F<T>(B, S(s, F_T));
         auto En_at = [&](int q) {
@@ -333,17 +371,11 @@ __global__ void __launch_bounds__(NTHR, FOURIER ? 1 : 2) k_dust(const BoxDev* bo
                  __ldg(&un[2][q]) * __ldg(&un[2][q]);
           return cv * __ldg(&Tn[q]) + T(0.5) * uu;
         };
-        const T* Ep = eprev >= 0 ? F<T>(B, eprev) : nullptr;
-        auto Hat = [&](int q) {
-          T e = Ep ? __ldg(&Ep[q]) : En_at(q);
-          return e + __ldg(&p[q]) / __ldg(&rho[q]);
-        };
-        auto Tat = [&](int q) { return __ldg(&p[q]) / (__ldg(&rho[q]) * Rg); };
-        T fl = T(0);
+        T fl = T(0);  // D(F_E^k) from the face fluxes of k_fe_face
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          fl += energy_face<T>(u, phi, div, n, d, 0, 0, 0, ih, (T)B.mu, (T)B.kappa, Hat, Tat) -
-                energy_face<T>(u, phi, div, n, d, bx(d), by(d), bz(d), ih, (T)B.mu, (T)B.kappa, Hat, Tat);
+          const T* fe = F<T>(B, W_FEF0 + d);
+          fl += __ldg(&fe[c]) - __ldg(&fe[n(bx(d), by(d), bz(d))]);
         }
         T rE = rn * En_at(c) - T(0.5) * dt * (__ldg(&F<T>(B, W_FEN)[c]) + fl * ih);
         Ek = rE * irk;
@@ -421,10 +453,21 @@ template <typename T> void launch_dt_div(const Launch& L, int s) {
   launch_div<T>(L, S(s, F_U0));
 }
 template <typename T> void launch_pred(const Launch& L, int s, int k) { zlaunch_pred<T>(L, s, k); }
+// Fourier closure: the energy face fluxes of a level (k_fe_cell, then k_fe_face)
+template <typename T> static void launch_fe_faces(const Launch& L, int s, int u0, int rhos, int ps, int es, int tmode,
+                                                  int phi0) {
+  FE_LAUNCH(L, KID_FE_CELL, (k_fe_cell<T><<<GRID>>>(L.boxes, L.work, s, u0, rhos, ps, es, tmode)));
+  FE_LAUNCH(L, KID_FE_FACE, (k_fe_face<T><<<GRID>>>(L.boxes, L.work, u0, phi0)));
+}
 template <typename T> void launch_fluxn(const Launch& L, int s) {
-  if (!L.fourier && L.nd >= 1 && L.nd <= 3) zlaunch_fluxn<T>(L, s, L.nd);
-  else if (L.fourier) FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
-  else FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, false><<<GRID>>>(L.boxes, L.work, s)));
+  if (!L.fourier && L.nd >= 1 && L.nd <= 3) {
+    zlaunch_fluxn<T>(L, s, L.nd);
+  } else if (L.fourier) {  // level n: E^n = c_v T^n + |u^n|^2/2, T^n stored
+    launch_fe_faces<T>(L, s, S(s, F_U0), S(s, F_RHO), S(s, F_P), -1, 0, S(s, F_PHI0));
+    FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
+  } else {
+    FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, false><<<GRID>>>(L.boxes, L.work, s)));
+  }
 }
 template <typename T> void launch_asm(const Launch& L, int s, int up0, int php0, int rhop) {
   zlaunch_asm<T>(L, s, up0, php0, rhop);
@@ -440,8 +483,10 @@ template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk,
                                        int last, int) {
   if (!L.fourier && L.nd >= 1 && L.nd <= 3)
     zlaunch_dust<T>(L, s, kset, yp0, yn0, last, L.nd);
-  else if (L.fourier)
+  else if (L.fourier) {  // level k: E^{k-1} (E^n in the first corrector), T = p^k / (rho^k R)
+    launch_fe_faces<T>(L, s, S(kset, F_U0), S(kset, F_RHO), pk, eprev, 1, S(kset, F_PHI0));
     FE_LAUNCH(L, KID_DUST, (k_dust<T, true><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
+  }
   else
     FE_LAUNCH(L, KID_DUST, (k_dust<T, false><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
 }
