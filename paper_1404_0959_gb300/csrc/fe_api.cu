@@ -184,6 +184,8 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
     for (int s : {(int)W_EW0, (int)W_EW1, (int)W_FEN, (int)W_FEH, (int)W_FET}) plan.push_back({s, e});
     for (int q = 0; q < 9; ++q) plan.push_back({W_FEG0 + q, e});
     for (int q = 0; q < 3; ++q) plan.push_back({W_FEF0 + q, e});
+    plan.push_back({W_EN, e});
+    plan.push_back({W_FED, e});
   }
   for (int j = 0; j < nd; ++j) {
     plan.push_back({W_FYN0 + j, e});

@@ -63,7 +63,9 @@ enum WorkSlot {
   // Fourier closure, total-energy flux: per cell H = E + p/rho, T and the Gauss gradients h Gc_m u_l
   // (m, l = 0..2: slot W_FEG0 + 3 m + l); the +1/2 face fluxes F_E along x, y, z
   W_FEH, W_FET, W_FEG0, W_FEF0 = W_FEG0 + 9,
-  NSLOT = W_FEF0 + 3
+  W_EN = W_FEF0 + 3,  // Fourier: E^n = c_v T^n + |u^n|^2 / 2 of the step (ring dust kernel)
+  W_FED,              // Fourier: D(F_E^k) of the current corrector (ring dust kernel)
+  NSLOT
 };
 
 // ---- per-box scalars (double) ---------------------------------------------
@@ -645,6 +647,9 @@ template <typename V> int rlaunch_asm(const Launch& L, int s, int up0, int php0,
 template <typename V> int rlaunch_accel(const Launch& L, int kset, int pk);
 template <typename V> int rlaunch_fluxn(const Launch& L, int s, int nd);
 template <typename V> int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd);
+// Fourier closure: dust, energy E^k (to slot enew unless negative) and, last, T, p and totals
+template <typename V> int rlaunch_dust_fourier(const Launch& L, int s, int kset, int yp0, int yn0, int enew, int last,
+                                               int nd);
 template <typename V> int rlaunch_div(const Launch& L, int u0, int with_dt = 0);
 template <typename V> int rlaunch_rhs(const Launch& L, int s, int rhop, int pp);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)

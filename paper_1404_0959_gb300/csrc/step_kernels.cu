@@ -69,10 +69,11 @@ __global__ void __launch_bounds__(NTHR) k_fe_cell(const BoxDev* boxes, const int
     T e;
     if (E) {
       e = __ldg(&E[c]);
-    } else {
+    } else {  // the level-n energy, kept for the dust kernels (W_EN)
       const T uu = __ldg(&un[0][c]) * __ldg(&un[0][c]) + __ldg(&un[1][c]) * __ldg(&un[1][c]) +
                    __ldg(&un[2][c]) * __ldg(&un[2][c]);
       e = cv * __ldg(&Tn[c]) + T(0.5) * uu;
+      F<T>(B, W_EN)[c] = e;
     }
     const T pc = __ldg(&p[c]), rc = __ldg(&rho[c]);
     Hc[c] = e + pc / rc;
@@ -81,6 +82,26 @@ __global__ void __launch_bounds__(NTHR) k_fe_cell(const BoxDev* boxes, const int
     for (int m = 0; m < 3; ++m)
 #pragma unroll
       for (int l = 0; l < 3; ++l) F<T>(B, W_FEG0 + 3 * m + l)[c] = Gc_h<T>(u[l], n, m, 0, 0, 0);
+  }
+}
+
+// D(F_E) * (1/h) from the face arrays into slot out (the same sum as the dust kernels form)
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_fe_div(const BoxDev* boxes, const int2* work, int out) {
+  Tile t = tile_of(boxes, work);
+  if (!t.active) return;
+  const BoxDev& B = boxes[t.box];
+  const T ih = (T)B.ih;
+  for (int k = t.k0; k < t.kend; ++k) {
+    Nbr n(t.i, t.j, k, B.N);
+    const int c = n(0, 0, 0);
+    T acc = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* fe = F<T>(B, W_FEF0 + d);
+      acc += __ldg(&fe[c]) - __ldg(&fe[n(bx(d), by(d), bz(d))]);
+    }
+    F<T>(B, out)[c] = acc * ih;
   }
 }
 
@@ -464,7 +485,12 @@ template <typename T> void launch_fluxn(const Launch& L, int s) {
     zlaunch_fluxn<T>(L, s, L.nd);
   } else if (L.fourier) {  // level n: E^n = c_v T^n + |u^n|^2/2, T^n stored
     launch_fe_faces<T>(L, s, S(s, F_U0), S(s, F_RHO), S(s, F_P), -1, 0, S(s, F_PHI0));
-    FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
+    if (L.nd >= 1 && L.nd <= 3) {  // D(F_E^n), then the dust flux divergences as in the barotropic step
+      FE_LAUNCH(L, KID_FE_FACE, (k_fe_div<T><<<GRID>>>(L.boxes, L.work, W_FEN)));
+      zlaunch_fluxn<T>(L, s, L.nd);
+    } else {
+      FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, true><<<GRID>>>(L.boxes, L.work, s)));
+    }
   } else {
     FE_LAUNCH(L, KID_FLUXN, (k_fluxn<T, false><<<GRID>>>(L.boxes, L.work, s)));
   }
@@ -485,6 +511,10 @@ template <typename T> void launch_dust(const Launch& L, int s, int kset, int pk,
     zlaunch_dust<T>(L, s, kset, yp0, yn0, last, L.nd);
   else if (L.fourier) {  // level k: E^{k-1} (E^n in the first corrector), T = p^k / (rho^k R)
     launch_fe_faces<T>(L, s, S(kset, F_U0), S(kset, F_RHO), pk, eprev, 1, S(kset, F_PHI0));
+    if (L.nd >= 1 && L.nd <= 3 && L.ring_ok) {  // D(F_E^k), then the ring kernel (when it can run)
+      FE_LAUNCH(L, KID_FE_FACE, (k_fe_div<T><<<GRID>>>(L.boxes, L.work, W_FED)));
+      if (rlaunch_dust_fourier<T>(L, s, kset, yp0, yn0, enew, last, L.nd)) return;
+    }
     FE_LAUNCH(L, KID_DUST, (k_dust<T, true><<<GRID>>>(L.boxes, L.work, L.part, s, kset, pk, yp0, yn0, eprev, enew, last)));
   }
   else

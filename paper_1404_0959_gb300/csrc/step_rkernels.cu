@@ -43,7 +43,7 @@ __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
 constexpr int kMaxDev = 64;
 // per device, one bit per ring kernel (set when its shared-memory limit was accepted)
 enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
-                  RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW };
+                  RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW, RK_DUST1F, RK_DUST2F, RK_DUST3F };
 template <typename T>
 struct RingReady {
   static unsigned ok[kMaxDev];
@@ -425,12 +425,17 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fluxn(const BoxDev* boxe
 }
 
 // ---- dust: level k, (rho Y)^k and Y^k; on the last corrector the barotropic closure and totals -----------------
-template <typename T, int ND>
-using DustPlan = RingPlan<T, kA1, 4 + ND, 3, 4 + 2 * ND>;  // rho^k, a0..2, Y_j^{k-1} | phi^k | rho^n, Y^n, FYN, u0..2
-template <typename T, int ND>
+// FR: Fourier closure -- also E^k = (rho^n E^n - dt/2 (D F_E^n + D F_E^k)) / rho^k (E^n, D F_E^n and
+// D F_E^k as centre fields, k_fe_cell / k_fe_div), and on the last corrector T = (E - |u|^2/2) / c_v,
+// p = rho R T and the total energy sum rho E (the general k_dust<T, true>'s expressions)
+template <typename T, int ND, bool FR = false>
+using DustPlan = RingPlan<T, kA1, 4 + ND, 3, 4 + 2 * ND + (FR ? 3 : 0)>;  // rho^k, a0..2, Y_j^{k-1} | phi^k |
+                                                                         // rho^n, Y^n, FYN, [E^n, DFE^n, DFE^k,] u0..2
+template <typename T, int ND, bool FR>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes, const int2* work, double* part, int s, int kset,
-                                                int yp0, int yn0, int last) {
-  RING_PROLOGUE((DustPlan<T, ND>));
+                                                int yp0, int yn0, int last, int enew) {
+  RING_PROLOGUE((DustPlan<T, ND, FR>));
+  constexpr int EB = 1 + 2 * ND, UB = EB + (FR ? 3 : 0);  // centre indices of E^n (FR) and of u^k
   R.gs[0] = Fr<T>(B, S(kset, F_RHO));
 #pragma unroll
   for (int d = 0; d < 3; ++d) R.gs[1 + d] = Fr<T>(B, W_AN0 + d);
@@ -444,9 +449,16 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
     R.gc[1 + j] = Fr<T>(B, S(s, F_Y0 + j));
     R.gc[1 + ND + j] = Fr<T>(B, W_FYN0 + j);
   }
+  if (FR) {
+    R.gc[FR ? EB : 0] = Fr<T>(B, W_EN);
+    R.gc[FR ? EB + 1 : 0] = Fr<T>(B, W_FEN);
+    R.gc[FR ? EB + 2 : 0] = Fr<T>(B, W_FED);
+  }
 #pragma unroll
-  for (int m = 0; m < 3; ++m) R.gc[1 + 2 * ND + m] = Fr<T>(B, S(kset, F_U0 + m));
-  if (!last) R.ncf = 1 + 2 * ND;  // u^k is read on the last corrector only
+  for (int m = 0; m < 3; ++m) R.gc[UB + m] = Fr<T>(B, S(kset, F_U0 + m));
+  if (!last) R.ncf = UB;  // u^k is read on the last corrector only
+  T* __restrict__ eout = FR && enew >= 0 ? Fr<T>(B, enew) : nullptr;
+  T* __restrict__ tout = FR ? Fr<T>(B, S(kset, F_T)) : nullptr;
   const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
   T taup[ND];
   T* ynew[ND];
@@ -465,7 +477,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     const P2<T> crn = R.cen(0, k, tid);
-    T oy[ND][2], op[2];
+    T oy[ND][2], op[2], oe[2], ot[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const ZView<T> rho = R.view(0, k, G, r);
@@ -497,21 +509,41 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
           if (!isfinite(Yk)) abad.add(T(1));
         }
       }
+      T Ek = T(0);
+      if (FR) {
+        const T rE = rn * pc<T>(R.cen(FR ? EB : 0, k, tid), r) -
+                     T(0.5) * dt * (pc<T>(R.cen(FR ? EB + 1 : 0, k, tid), r) + pc<T>(R.cen(FR ? EB + 2 : 0, k, tid), r));
+        Ek = rE * irk;
+        oe[r] = Ek;
+      }
       op[r] = T(0);
+      ot[r] = T(0);
       if (last) {
-        const T u0 = pc<T>(R.cen(1 + 2 * ND, k, tid), r), u1 = pc<T>(R.cen(2 + 2 * ND, k, tid), r),
-                u2 = pc<T>(R.cen(3 + 2 * ND, k, tid), r);
+        const T u0 = pc<T>(R.cen(UB, k, tid), r), u1 = pc<T>(R.cen(UB + 1, k, tid), r),
+                u2 = pc<T>(R.cen(UB + 2, k, tid), r);
         const T uu = u0 * u0 + u1 * u1 + u2 * u2;
-        const T pf = pow(rk, gam) / gam;
+        T pf;
+        if (FR) {
+          const T Tk = (Ek - T(0.5) * uu) / (T)B.cv;
+          ot[r] = Tk;
+          pf = rk * (T)B.R * Tk;
+          aen.add(rk, Ek);
+        } else {
+          pf = pow(rk, gam) / gam;
+          aen.add(rk, uu);
+        }
         op[r] = pf;
         amass.add(rk);
-        aen.add(rk, uu);
         if (!(isfinite(rk) && isfinite(uu) && isfinite(pf))) abad.add(T(1));
       }
     }
 #pragma unroll
     for (int j = 0; j < ND; ++j) stp(ynew[j] + c, oy[j][0], oy[j][1]);
-    if (last) stp(pout + c, op[0], op[1]);
+    if (eout) stp(eout + c, oe[0], oe[1]);
+    if (last) {
+      stp(pout + c, op[0], op[1]);
+      if (FR) stp(tout + c, ot[0], ot[1]);
+    }
   }
   cp_async_wait<0>();
   if (!last) return;
@@ -525,7 +557,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
   if (block_sum_last<3 + ND>(acc, B, part, res, B.tile0, B.ntiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       B.sc[SC_MASS] = res[0];
-      B.sc[SC_ENERGY] = 0.5 * res[1];
+      B.sc[SC_ENERGY] = FR ? res[1] : 0.5 * res[1];
       B.sc[SC_BAD] = res[2];
       for (int j = 0; j < MAXD; ++j) B.sc[SC_DUST0 + j] = j < ND ? res[3 + j] : 0.0;
     }
@@ -696,25 +728,33 @@ int rlaunch_fluxn(const Launch& L, int s, int nd) {
   }
   return 1;
 }
-template <typename T>
-int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd) {
-  if (nd < 1 || nd > 3 || !L.ring_ok || !ring_ready<T>(RK_DUST1 + nd - 1)) return 0;
+template <typename T, bool FR>
+static int rlaunch_dust_any(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd, int enew) {
+  if (nd < 1 || nd > 3 || !L.ring_ok || !ring_ready<T>((FR ? RK_DUST1F : RK_DUST1) + nd - 1)) return 0;
   switch (nd) {
     case 1:
-      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 1><<<RGRID((DustPlan<T, 1>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
-                                                                                 yn0, last)));
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 1, FR><<<RGRID((DustPlan<T, 1, FR>::bytes))>>>(L.boxes, L.work, L.part, s, kset,
+                                                                                         yp0, yn0, last, enew)));
       break;
     case 2:
-      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 2><<<RGRID((DustPlan<T, 2>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
-                                                                                 yn0, last)));
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 2, FR><<<RGRID((DustPlan<T, 2, FR>::bytes))>>>(L.boxes, L.work, L.part, s, kset,
+                                                                                         yp0, yn0, last, enew)));
       break;
     case 3:
-      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 3><<<RGRID((DustPlan<T, 3>::bytes))>>>(L.boxes, L.work, L.part, s, kset, yp0,
-                                                                                 yn0, last)));
+      FE_LAUNCH(L, KID_DUST, (kr_dust<T, 3, FR><<<RGRID((DustPlan<T, 3, FR>::bytes))>>>(L.boxes, L.work, L.part, s, kset,
+                                                                                         yp0, yn0, last, enew)));
       break;
     default: return 0;
   }
   return 1;
+}
+template <typename T>
+int rlaunch_dust(const Launch& L, int s, int kset, int yp0, int yn0, int last, int nd) {
+  return rlaunch_dust_any<T, false>(L, s, kset, yp0, yn0, last, nd, -1);
+}
+template <typename T>
+int rlaunch_dust_fourier(const Launch& L, int s, int kset, int yp0, int yn0, int enew, int last, int nd) {
+  return rlaunch_dust_any<T, true>(L, s, kset, yp0, yn0, last, nd, enew);
 }
 
 template <typename T>
@@ -748,9 +788,12 @@ int rprepare() {
   set(RK_FLUX1, set_smem(kr_fluxn<T, 1>, FluxPlan<T, 1>::bytes));
   set(RK_FLUX2, set_smem(kr_fluxn<T, 2>, FluxPlan<T, 2>::bytes));
   set(RK_FLUX3, set_smem(kr_fluxn<T, 3>, FluxPlan<T, 3>::bytes));
-  set(RK_DUST1, set_smem(kr_dust<T, 1>, DustPlan<T, 1>::bytes));
-  set(RK_DUST2, set_smem(kr_dust<T, 2>, DustPlan<T, 2>::bytes));
-  set(RK_DUST3, set_smem(kr_dust<T, 3>, DustPlan<T, 3>::bytes));
+  set(RK_DUST1, set_smem(kr_dust<T, 1, false>, DustPlan<T, 1>::bytes));
+  set(RK_DUST2, set_smem(kr_dust<T, 2, false>, DustPlan<T, 2>::bytes));
+  set(RK_DUST3, set_smem(kr_dust<T, 3, false>, DustPlan<T, 3>::bytes));
+  set(RK_DUST1F, set_smem(kr_dust<T, 1, true>, DustPlan<T, 1, true>::bytes));
+  set(RK_DUST2F, set_smem(kr_dust<T, 2, true>, DustPlan<T, 2, true>::bytes));
+  set(RK_DUST3F, set_smem(kr_dust<T, 3, true>, DustPlan<T, 3, true>::bytes));
   set(RK_DIV, set_smem(kr_div<T>, DivPlan<T>::bytes));
   set(RK_RHS, set_smem(kr_rhs<T>, RhsPlan<T>::bytes));
   cudaGetLastError();  // a refused limit is not an error of the context
@@ -766,6 +809,7 @@ int rprepare() {
   template int rlaunch_accel<T>(const Launch&, int, int);                         \
   template int rlaunch_fluxn<T>(const Launch&, int, int);                         \
   template int rlaunch_dust<T>(const Launch&, int, int, int, int, int, int);      \
+  template int rlaunch_dust_fourier<T>(const Launch&, int, int, int, int, int, int, int); \
   template int rlaunch_div<T>(const Launch&, int, int);                           \
   template int rlaunch_rhs<T>(const Launch&, int, int, int);                      \
   template int rprepare<T>();
