@@ -35,7 +35,11 @@ UNIT = "cell-steps/s"
 # launch of each kernel, barotropic closure, nd dust classes.  Mixed precision:
 # the right-hand side also writes the first inner right-hand side and reads
 # D^{-1} (it starts the refined solve); the corrector reads neither psi nor b.
-def alg_words(kernel, nd, mixed=False):
+def alg_words(kernel, nd, mixed=False, poly=False):
+    if poly and kernel in ("cg_dirmatvec", "cg_rupdate", "cg_start"):
+        # Neumann-polynomial CG: z, pd_old, psi, x read, q, pd_new, x written | r, q, D^-1, psi read, z and r
+        # written | r, D^-1, psi read, z written
+        return {"cg_dirmatvec": 7, "cg_rupdate": 6, "cg_start": 4}[kernel]
     table = {
         "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 13 if mixed else 11,
         "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4,
@@ -45,7 +49,7 @@ def alg_words(kernel, nd, mixed=False):
         # refinement (field word = 4 bytes; x64 counts as two words)
         "mix_residual": 6, "mix_accum": 5, "mix_finish": 3, "commit": 0,
         # fused refinement: pairs read and written, x, pd, b, psi, dinv read, r and the FP32 solution written
-        "refine": 11,
+        "refine": 11, "cg_start": 4,
     }
     return table[kernel]
 
@@ -590,6 +594,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--solver", default="jacobi", choices=["jacobi", "poly"],
+                    help="pressure CG preconditioner: Jacobi, or the first-order Neumann polynomial")
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--cpu-n", type=int, default=128)
@@ -653,8 +659,10 @@ def main():
     nd = len(cfg["tau_p"])
     box = rank_box(cfg, rank)
     stream = torch.cuda.current_stream()
+    solver = fe.FE_PCG_POLY if args.solver == "poly" else fe.FE_PCG_JACOBI
+    poly = solver == fe.FE_PCG_POLY and precision == fe.FE_FP32_MIXED
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
-                  p_maxit=1000, stream=stream.cuda_stream)
+                  p_maxit=1000, solver=solver, stream=stream.cuda_stream)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
     if args.tile > 0:
         s.set_tiling(args.tile)
@@ -681,8 +689,8 @@ def main():
 
     # untimed pass: per-kernel device time over one step, one kernel id at a time
     names = ["dt", "div", "pred", "fluxn", "asm", "rhs", "cg_init", "cg_matvec", "cg_update", "cg_dir",
-             "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "corr", "accel", "dust", "mix_residual", "mix_accum",
-             "refine", "mix_finish", "commit"]
+             "cg_dirmatvec", "cg_rupdate", "cg_start", "cg_xfinal", "corr", "accel", "dust", "mix_residual",
+             "mix_accum", "refine", "mix_finish", "commit"]
     share = {}
     for k in ([] if args.no_breakdown else names):
         restore()
@@ -730,9 +738,9 @@ def main():
     hbm, peak_kind = peaks()
     per_launch_ms = prof["target_ms"] / max(prof["target_launches"], 1)
     mixed = precision == fe.FE_FP32_MIXED
-    alg_bytes = alg_words(kernel, nd, mixed) * w * cells
+    alg_bytes = alg_words(kernel, nd, mixed, poly) * w * cells
     # whole step: algorithmic bytes of every launch of the breakdown step over the headline step time
-    step_bytes = sum(n * alg_words(k, nd, mixed) * w * cells for k, (_, n) in share.items()) if share else None
+    step_bytes = sum(n * alg_words(k, nd, mixed, poly) * w * cells for k, (_, n) in share.items()) if share else None
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     iters = info[0]["iters"]
 
@@ -804,7 +812,8 @@ def main():
                 "data": "synthetic spectral HIT field (seed per rank), no dataset",
                 "config": {"workload": WORKLOAD, "N": N, "closure": "barotropic", "mach_rms": cfg["mach_rms"],
                            "k0": cfg["k0"], "nu": cfg["nu"], "tau_p": cfg["tau_p"], "Y0": cfg["Y0"],
-                           "p_tol": cfg["p_tol"], "solver": "jacobi-pcg", "precision": args.precision,
+                           "p_tol": cfg["p_tol"], "precision": args.precision,
+                           "solver": "neumann1-pcg" if poly else "jacobi-pcg",
                            "n_corr": 2, "krylov_iters_last_step": iters, "tile": "32x8x%d" % tz if tz else "default",
                            "cuda_graphs": not args.no_graphs,
                            "timed_from": "state after the warm-up steps, restored before every measured pass",

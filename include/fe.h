@@ -67,6 +67,13 @@ extern "C" {
                                  * (transonic included): learned directions when *
                                  * a network is loaded, Jacobi otherwise; one box, *
                                  * N divisible by 4; host-driven (no CUDA graph)  */
+#define FE_PCG_POLY         4   /* SPD operator (transonic = 0): CG with the      *
+                                 * first-order Neumann polynomial preconditioner *
+                                 * P = D^-1 (2 I - M D^-1) (Dubois, Greenbaum and *
+                                 * Rodrigue 1979) on the plane-streamed FP32      *
+                                 * iteration (mixed precision, every box's N a    *
+                                 * power of two in 64..512); FE_PCG_JACOBI        *
+                                 * wherever that iteration does not run          */
 
 /* field ids for fe_set_field / fe_get_field */
 #define FE_RHO   0
@@ -116,7 +123,7 @@ typedef struct {
     double dt_max;              /* upper bound on dt (use HUGE_VAL for none)     */
     int32_t n_corr;             /* PISO correctors, >= 1 (2 recommended)         */
     int32_t solver;             /* FE_PCG_JACOBI | FE_BICGSTAB_JACOBI | FE_FCG_LEARNED |
-                                 * FE_FGMRES_LEARNED */
+                                 * FE_FGMRES_LEARNED | FE_PCG_POLY */
     double p_tol;               /* ||b - M x||_2 <= p_tol ||b||_2                */
     int32_t p_maxit;            /* Krylov iteration cap per solve                */
     int32_t transonic;          /* 1: add the psi-convection term (non-symmetric) */

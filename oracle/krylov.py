@@ -7,7 +7,17 @@ solved each corrector; the paper does not name the linear solver.  Readings
 adopted (standard algorithms, written from their textbook definitions):
 
 * ``pcg``       Jacobi-preconditioned conjugate gradient (Hestenes-Stiefel),
-                for the symmetric positive definite default operator.
+                for the symmetric positive definite default operator; with
+                ``precond`` any fixed symmetric positive definite
+                preconditioner, e.g. ``neumann1``.
+* ``neumann1``  first-order Neumann polynomial preconditioner
+                P = D^-1 (2 I - M D^-1) (Dubois, Greenbaum and Rodrigue 1979,
+                SIAM J. Numer. Anal. 16): the Neumann series of
+                M^-1 = (I - (I - D^-1 M))^-1 D^-1 cut after its linear term,
+                equivalently two Jacobi sweeps from zero.  Not the paper's
+                (it names no preconditioner); symmetric positive definite
+                because the eigenvalues of D^-1 M lie in (0, 2) for this
+                strictly diagonally dominant operator.
 * ``bicgstab``  Jacobi-preconditioned BiCGStab (van der Vorst 1992) for the
                 non-symmetric "transonic" operator.
 * ``fcg``       flexible CG (Notay 2000, truncation m_max = 1) for a
@@ -29,7 +39,10 @@ recomputed from x.  ||b|| == 0 returns x = 0 after zero iterations.
 Parity pins (tests/test_oracle_solve.py): uniform psi against the exact
 Fourier solution; variable psi on 8^3 against a dense LU solve of the matrix
 assembled from the stencil coefficients; BiCGStab on the transonic operator
-against its Fourier closed form; flexible GMRES against the same closed form,
+against its Fourier closed form; ``neumann1`` against two Jacobi sweeps, its
+symmetry and the spectrum 1 - (1 - mu)^2 of P M for the eigenvalues mu of
+D^-1 M (dense 6^3), PCG with it against the dense LU solve; flexible GMRES
+against the same closed form,
 and its defining property -- after k directions, x minimises ||b - M x|| over
 the span of the k preconditioned directions -- against a least-squares solve
 over an explicitly built basis.
@@ -41,14 +54,24 @@ def _norm(v):
     return float(np.sqrt(np.sum(v * v)))
 
 
-def pcg(matvec, b, diag, tol, maxit):
-    """Jacobi-PCG.  Returns (x, iterations, rel_res_recurrence, rel_res_true)."""
+def neumann1(matvec, diag):
+    """The map v -> D^-1 (2 v - M (D^-1 v)) (first-order Neumann polynomial in D^-1 M)."""
+    def apply(v):
+        w = v / diag
+        return (2.0 * v - matvec(w)) / diag
+    return apply
+
+
+def pcg(matvec, b, diag, tol, maxit, precond=None):
+    """PCG with z = precond(r) (default Jacobi: z = r / diag).  Returns
+    (x, iterations, rel_res_recurrence, rel_res_true)."""
+    pre = precond if precond is not None else (lambda v: v / diag)
     x = np.zeros_like(b)
     bnorm = _norm(b)
     if bnorm == 0.0:
         return x, 0, 0.0, 0.0
     r = b.copy()
-    z = r / diag
+    z = pre(r)
     p = z.copy()
     rz = float(np.sum(r * z))
     it = 0
@@ -62,7 +85,7 @@ def pcg(matvec, b, diag, tol, maxit):
         rnorm = _norm(r)
         if rnorm <= tol * bnorm:
             break
-        z = r / diag
+        z = pre(r)
         rz_new = float(np.sum(r * z))
         beta = rz_new / rz
         p = z + beta * p

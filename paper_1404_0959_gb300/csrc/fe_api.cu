@@ -82,7 +82,7 @@ static const char* kKernelNames[] = {
     "dust",    "derive",    "cg_init",   "cg_matvec", "cg_update", "cg_dir", "true_res", "bicg_init",
     "bicg_p",  "bicg_v",    "bicg_s",    "bicg_t", "bicg_x",   "commit",    "dinv",
     "mix_residual", "mix_accum", "mix_finish", "fcg_dots", "fcg_dir", "fcg_matvec",
-    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "tf_pred", "tf_corr", "fe_cell", "fe_face",
+    "cg_dirmatvec", "cg_rupdate", "cg_xfinal", "refine", "unet", "tf_pred", "tf_corr", "fe_cell", "fe_face", "cg_start",
     "other"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT, "kernel name table");
 static_assert(KID_COUNT <= FE_PROFILE_MAX_KERNELS, "profile counters");
@@ -140,9 +140,11 @@ struct fe_ctx {
   size_t iso_bytes = 0;
   std::vector<double> iso_host;
   Launch L() {
-    return Launch{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
-                  prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
-                  nbblocks, bsmem};
+    Launch l{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
+             prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
+             nbblocks, bsmem};
+    l.poly = prm.solver == FE_PCG_POLY && l.bwork != nullptr;  // Jacobi where the planes are not streamed
+    return l;
   }
 };
 
@@ -199,6 +201,10 @@ static void slot_plan(const fe_ctx* c, std::vector<std::pair<int, size_t>>& plan
     for (int s : {K_RHAT, K_V, K_S, K_T}) plan.push_back({s, e});
   // second CG direction buffer (the learned solver's harvest runs plain CG)
   if (c->prm.solver != FE_BICGSTAB_JACOBI) plan.push_back({K_PP, e});
+  if (c->prm.solver == FE_PCG_POLY && !c->fp64) {  // z = P r and the residual ping-pong of the streamed CG
+    plan.push_back({K_Z, e});
+    plan.push_back({K_RB, e});
+  }
   if (!c->fp64) plan.push_back({K_X64, 8});
   if (!c->fp64 && c->prm.solver != FE_BICGSTAB_JACOBI) {
     plan.push_back({K_X64B, 8});
@@ -223,9 +229,9 @@ static int validate(const fe_params* p) {
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->p_tol > 0.0) || p->p_maxit < 1) return FE_ERR_INVALID_ARG;
   if (p->closure == FE_FOURIER && !(p->Pr > 0.0)) return FE_ERR_INVALID_ARG;
   if (p->solver != FE_PCG_JACOBI && p->solver != FE_BICGSTAB_JACOBI && p->solver != FE_FCG_LEARNED &&
-      p->solver != FE_FGMRES_LEARNED)
+      p->solver != FE_FGMRES_LEARNED && p->solver != FE_PCG_POLY)
     return FE_ERR_INVALID_ARG;
-  if (p->transonic && p->solver == FE_PCG_JACOBI) return FE_ERR_INVALID_ARG;
+  if (p->transonic && (p->solver == FE_PCG_JACOBI || p->solver == FE_PCG_POLY)) return FE_ERR_INVALID_ARG;
   if (p->solver == FE_FCG_LEARNED && (p->n_boxes != 1 || p->N[0] % 4 != 0 || p->transonic))
     return FE_ERR_UNSUPPORTED;
   if (p->solver == FE_FGMRES_LEARNED && (p->n_boxes != 1 || p->N[0] % 4 != 0)) return FE_ERR_UNSUPPORTED;
@@ -818,7 +824,8 @@ static int inner_solve(fe_ctx* c, int maxit, int key, int outer = 0) {
 // (last direction, pair accumulation, double-float residual, next start) is
 // one kernel.
 static bool fused_refine(const fe_ctx* c) {
-  return !c->fp64 && c->prm.solver == FE_PCG_JACOBI && !c->prm.transonic && !c->harvest_b &&
+  return !c->fp64 && (c->prm.solver == FE_PCG_JACOBI || c->prm.solver == FE_PCG_POLY) && !c->prm.transonic &&
+         !c->harvest_b &&
          c->hbox[0].f[K_PP] != nullptr && c->hbox[0].f[K_X64B] != nullptr;
 }
 
@@ -1059,6 +1066,7 @@ static int issue_step(fe_ctx* c, int s, bool graph) {
       Launch Lr = L;
       Lr.rstart = c->douter;
       launch_rhs<T>(Lr, s, rhop, pp);
+      launch_cg_start<T>(L);
     } else {
       launch_rhs<T>(L, s, rhop, pp);
     }

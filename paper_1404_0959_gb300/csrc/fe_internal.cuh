@@ -54,6 +54,7 @@ enum WorkSlot {
   K_B = W_TFS0 + 4 * MAXD, K_X, K_R, K_PD, K_Q,
   K_RHAT, K_V, K_S, K_T,  // BiCGStab
   K_Z, K_PP, K_QP,        // flexible CG: preconditioned r, previous direction and its image
+  K_RB,                   // polynomial-preconditioned CG: residual ping-pong partner of K_R
   K_X64,                  // double accumulator (mixed precision refinement)
   K_X64B,                 // its ping-pong partner (fused refinement of plain CG)
   K_XH,                   // fused refinement: high parts of the pairs = the FP32 solution the corrector reads
@@ -573,7 +574,7 @@ enum KernelId {
   KID_BICG_INIT, KID_BICG_P, KID_BICG_V, KID_BICG_S, KID_BICG_T, KID_BICG_X,
   KID_COMMIT, KID_DINV, KID_MIX_RES, KID_MIX_ACC, KID_MIX_FIN, KID_FCG_DOTS, KID_FCG_DIR, KID_FCG_MATVEC,
   KID_CG_DIRMATVEC, KID_CG_RUPDATE, KID_CG_XFINAL, KID_REFINE, KID_UNET, KID_TF_PRED, KID_TF_CORR, KID_FE_CELL,
-  KID_FE_FACE, KID_OTHER,
+  KID_FE_FACE, KID_CG_START, KID_OTHER,
   KID_COUNT
 };
 
@@ -600,6 +601,7 @@ struct Launch {
   int bsmem;          // dynamic shared memory of the streamed CG kernel
   int* rstart = nullptr;  // right-hand-side kernels: also start the refined solve (outer counter)
   int ysum = -1;          // two-way coupling: slot of the dust loading sum_j Y_j^n (-1: one-way)
+  int poly = 0;           // streamed CG with the Neumann polynomial preconditioner (needs bwork)
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -638,6 +640,7 @@ template <typename V> void launch_cg_fused(const Launch& L);   // symmetric oper
 template <typename V> void launch_cg_xfinal(const Launch& L);  // after launch_cg_fused iterations
 template <typename V> void launch_refine_start(const Launch& L, int* outer_active);  // fused refinement: start from K_B
 template <typename V> void launch_refine(const Launch& L, int* outer_active);          // fused refinement: boundary
+template <typename V> void launch_cg_start(const Launch& L);  // polynomial-preconditioned CG: first z = P r
 template <typename V> void launch_mix_finish_pp(const Launch& L);  // final x from the ping-ponged pairs
 // PISO kernels on asynchronous-copy rings (return 0: not launched, use the z-marching kernel)
 template <typename V> int rprepare();  // shared-memory limits of the ring kernels on the current device

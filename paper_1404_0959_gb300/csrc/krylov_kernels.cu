@@ -417,7 +417,9 @@ int bulk_smem_bytes(int N) {
   return 128 + (kBulkStages * bulk_stage_elems<T>(N) + bulk_ring_elems<T>(N)) * (int)sizeof(T);
 }
 
-template <typename T>
+// POLY: the direction is pd_new = z + beta pd_old with z = P r from kb_cg_rpoly (first-order Neumann
+// polynomial preconditioner), streamed with y-halo rows in place of r and D^{-1}.
+template <typename T, bool POLY>
 __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, const int2* bwork, double* part) {
   const int2 w = bwork[blockIdx.x];
   const BoxDev& B = boxes[w.x];
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
   const int odd = ((int)B.sc[SC_ITERS]) & 1;
   const T* __restrict__ po = F<T>(B, odd ? K_PP : K_PD);
   T* __restrict__ pn = F<T>(B, odd ? K_PD : K_PP);
-  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ r = F<T>(B, POLY ? K_Z : K_R);  // POLY: z
   const T* __restrict__ dinv = F<T>(B, W_DINV);
   const T* __restrict__ psi = F<T>(B, W_PSI);
   T* __restrict__ x = F<T>(B, K_X);
@@ -442,11 +444,12 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
   const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
   const T lapc = T(0.5) * dt * ih * ih;
-  const bool first = B.sc[SC_ITERS] == 0.0;  // pd_new = D^{-1} r, x = 0 whatever pd_old and x hold
+  const bool first = B.sc[SC_ITERS] == 0.0;  // pd_new = D^{-1} r (POLY: z), x = 0 whatever pd_old and x hold
   const int nseq = Gm.count();
   const size_t NN = (size_t)N * N;
+  constexpr int NHS = POLY ? 2 : 3;  // streams with y-halo rows
 
-  // stage layout: r | dinv | pd_old (R + 2 rows each, halo rows first and last) | psi | x (R rows)
+  // stage layout: r | dinv | pd_old (POLY: z | pd_old) (R + 2 rows each, halo rows first and last) | psi | x (R rows)
   auto issue = [&](int j) {
     const BulkPos P = bulk_pos(Gm, j);
     T* st = stage0 + (j % kBulkStages) * SE;
@@ -456,19 +459,19 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
     const size_t pl = (size_t)P.m * NN;
     const bool comp = P.pos >= 1 && P.pos <= P.len;
     const unsigned row = (unsigned)(N * sizeof(T)), rows = (unsigned)(RN * sizeof(T));
-    mbar_expect_tx(bj, 3 * (rows + 2 * row) + (comp ? 2 * rows : 0));
-    const T* src[3] = {r, dinv, po};
+    mbar_expect_tx(bj, NHS * (rows + 2 * row) + (comp ? 2 * rows : 0));
+    const T* src[3] = {r, POLY ? po : dinv, po};
     // rows ym .. ym + R + 1 of each stream: one copy, two where they wrap in y
     const int n0 = min(R + 2, N - ym);
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
+    for (int f = 0; f < NHS; ++f) {
       T* d = st + f * HN;
       bulk_g2s(d, src[f] + pl + (size_t)ym * N, (unsigned)n0 * row, bj);
       if (n0 < R + 2) bulk_g2s(d + n0 * N, src[f] + pl, (unsigned)(R + 2 - n0) * row, bj);
     }
     if (comp) {
-      bulk_g2s(st + 3 * HN, psi + pl + (size_t)y0 * N, rows, bj);
-      bulk_g2s(st + 3 * HN + RN, x + pl + (size_t)y0 * N, rows, bj);
+      bulk_g2s(st + NHS * HN, psi + pl + (size_t)y0 * N, rows, bj);
+      bulk_g2s(st + NHS * HN + RN, x + pl + (size_t)y0 * N, rows, bj);
     }
   };
 
@@ -499,23 +502,37 @@ __global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, con
       for (int u = 0; u < kBulkRows; ++u) {  // own rows: pd_new, and the centre values needed one plane later
         const int jr = tid / Q + RS * u;
         const int o = (jr + 1) * N + x4;
-        const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
-        V4<T> nv;
+        V4<T> nv, pv;
+        if (POLY) {
+          const V4<T> zv = ld4(st + o);
+          pv = ld4(st + HN + o);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
+          for (int e = 0; e < 4; ++e) nv.v[e] = first ? zv.v[e] : zv.v[e] + beta * pv.v[e];
+        } else {
+          const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o);
+          pv = ld4(st + 2 * HN + o);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
+        }
         st4(slot + o, nv);
         cu_po[u] = pv;
         if (P.pos >= 1 && P.pos <= P.len) {
-          cu_psi[u] = ld4(st + 3 * HN + jr * N + x4);
-          cu_x[u] = ld4(st + 3 * HN + RN + jr * N + x4);
+          cu_psi[u] = ld4(st + NHS * HN + jr * N + x4);
+          cu_x[u] = ld4(st + NHS * HN + RN + jr * N + x4);
         }
       }
       if (halo) {
         const int o = hr * N + x4;
-        const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
         V4<T> nv;
+        if (POLY) {
+          const V4<T> zv = ld4(st + o), pv = ld4(st + HN + o);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
+          for (int e = 0; e < 4; ++e) nv.v[e] = first ? zv.v[e] : zv.v[e] + beta * pv.v[e];
+        } else {
+          const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
+        }
         st4(slot + o, nv);
       }
     }
@@ -656,6 +673,182 @@ __global__ void __launch_bounds__(NTHR) k_cg_rupdate(const BoxDev* boxes, const 
   __shared__ double res[2];
   if (block_sum_last<2>(v, B, part, res, B.etile0, B.entiles)) {
     if (threadIdx.x == 0 && threadIdx.y == 0) cg_update_scalars(B, res[0], res[1], active);
+  }
+}
+
+// Residual update with the polynomial-preconditioned residual, on streamed planes (the step after
+// kb_cg_dirmatvec<T, true>): r_new = r - alpha q and w = D^{-1} r_new on the own and y-halo rows, then,
+// one plane behind, z = D^{-1} (2 r_new - M w), i.e. z = P r_new with the first-order Neumann polynomial
+// P = D^{-1} (2 I - M D^{-1}) (Dubois, Greenbaum and Rodrigue 1979; symmetric, and positive definite
+// because the eigenvalues of D^{-1} M lie in (0, 2) for this diagonally dominant operator), <r_new, z>,
+// ||r_new||^2 and the CG bookkeeping.  r alternates between K_R and K_RB by the parity of the iteration
+// count (neighbouring blocks read the old residual as halo).  START: the first residual of an inner
+// solve (alpha = 0, r stays in K_R): z and <r, z> only, no iteration counted.
+template <typename T, bool START>
+__global__ void __launch_bounds__(NTHR) kb_cg_rpoly(const BoxDev* boxes, const int2* bwork, double* part, int* active) {
+  const int2 w = bwork[blockIdx.x];
+  const BoxDev& B = boxes[w.x];
+  if (box_done(B)) return;
+  extern __shared__ __align__(128) unsigned char zsm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(zsm);
+  const int N = B.N;
+  const BulkGeom Gm(N, w.y, B.bntiles);
+  const int R = Gm.R, HN = (R + 2) * N, RN = R * N;
+  T* stage0 = reinterpret_cast<T*>(zsm + 128);
+  const int SE = bulk_stage_elems<T>(N);
+  T* ring = stage0 + kBulkStages * SE;
+  const int tid = threadIdx.x;
+  const int odd = START ? 0 : ((int)B.sc[SC_ITERS]) & 1;  // iterations before this one
+  const T* __restrict__ ro = F<T>(B, odd ? K_RB : K_R);
+  T* __restrict__ rn = F<T>(B, odd ? K_R : K_RB);
+  const T* __restrict__ qv = F<T>(B, K_Q);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  const T* __restrict__ psi = F<T>(B, W_PSI);
+  T* __restrict__ z = F<T>(B, K_Z);
+  const T alpha = START ? T(0) : (T)B.sc[SC_ALPHA];
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  const int nseq = Gm.count();
+  const size_t NN = (size_t)N * N;
+  constexpr int NHS = START ? 2 : 3;  // streams with y-halo rows: r, D^{-1} (and q)
+  constexpr int FD = NHS - 1;         // stage index of D^{-1}
+
+  // stage layout: r | q | D^{-1} (START: r | D^{-1}) (R + 2 rows each) | psi (R rows)
+  auto issue = [&](int j) {
+    const BulkPos P = bulk_pos(Gm, j);
+    T* st = stage0 + (j % kBulkStages) * SE;
+    uint64_t* bj = bar + (j % kBulkStages);
+    const int y0 = P.g * R;
+    const int ym = y0 == 0 ? N - 1 : y0 - 1;
+    const size_t pl = (size_t)P.m * NN;
+    const bool comp = P.pos >= 1 && P.pos <= P.len;
+    const unsigned row = (unsigned)(N * sizeof(T)), rows = (unsigned)(RN * sizeof(T));
+    mbar_expect_tx(bj, NHS * (rows + 2 * row) + (comp ? rows : 0));
+    const T* src[3] = {ro, START ? dinv : qv, dinv};
+    const int n0 = min(R + 2, N - ym);
+#pragma unroll
+    for (int f = 0; f < NHS; ++f) {
+      T* d = st + f * HN;
+      bulk_g2s(d, src[f] + pl + (size_t)ym * N, (unsigned)n0 * row, bj);
+      if (n0 < R + 2) bulk_g2s(d + n0 * N, src[f] + pl, (unsigned)(R + 2 - n0) * row, bj);
+    }
+    if (comp) bulk_g2s(st + NHS * HN, psi + pl + (size_t)y0 * N, rows, bj);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < kBulkStages; ++s) mbar_init(bar + s, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < kBulkStages && j < nseq; ++j) issue(j);
+
+  const int Q = Gm.Q;
+  const int x4 = (tid % Q) * 4;
+  const int RS = R / kBulkRows;
+  const int hr = tid < Q ? 0 : R + 1;
+  const bool halo = tid < 2 * Q;
+  const int xm1 = x4 == 0 ? N - 1 : x4 - 1, xp4 = x4 + 4 == N ? 0 : x4 + 4;
+  V4<T> sv_psi[kBulkRows], sv_r[kBulkRows], sv_d[kBulkRows], cu_psi[kBulkRows], cu_r[kBulkRows], cu_d[kBulkRows];
+  DotAcc<T> a0, a1;
+  bool failed = false;
+  for (int i = 0; i < nseq; ++i) {
+    const BulkPos P = bulk_pos(Gm, i);
+    const bool ok = mbar_wait(bar + (i % kBulkStages), (unsigned)((i / kBulkStages) & 1));
+    const T* st = stage0 + (i % kBulkStages) * SE;
+    T* slot = ring + (i & 3) * HN;
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < kBulkRows; ++u) {  // own rows: w = D^{-1} r_new, and r_new, D^{-1}, psi kept for the operator
+        const int jr = tid / Q + RS * u;
+        const int o = (jr + 1) * N + x4;
+        const V4<T> rv = ld4(st + o), dv = ld4(st + FD * HN + o);
+        V4<T> nr, wv;
+        if (START) {
+          nr = rv;
+        } else {
+          const V4<T> qq = ld4(st + HN + o);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) nr.v[e] = rv.v[e] - alpha * qq.v[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) wv.v[e] = nr.v[e] * dv.v[e];
+        st4(slot + o, wv);
+        cu_r[u] = nr;
+        cu_d[u] = dv;
+        if (P.pos >= 1 && P.pos <= P.len) cu_psi[u] = ld4(st + NHS * HN + jr * N + x4);
+      }
+      if (halo) {
+        const int o = hr * N + x4;
+        const V4<T> rv = ld4(st + o), dv = ld4(st + FD * HN + o);
+        V4<T> wv;
+        if (START) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) wv.v[e] = rv.v[e] * dv.v[e];
+        } else {
+          const V4<T> qq = ld4(st + HN + o);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) wv.v[e] = (rv.v[e] - alpha * qq.v[e]) * dv.v[e];
+        }
+        st4(slot + o, wv);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && i + kBulkStages < nseq) issue(i + kBulkStages);
+    if (P.pos >= 2) {  // the plane below (pos - 1 in 1..len): z = D^{-1} (2 r_new - M w)
+      const int mo = P.m == 0 ? N - 1 : P.m - 1;
+      const T* c = ring + ((i - 1) & 3) * HN;
+      const T* zm = ring + ((i - 2) & 3) * HN;
+      const T* zp = slot;
+#pragma unroll
+      for (int u = 0; u < kBulkRows; ++u) {
+        const int jr = tid / Q + RS * u;
+        const int o = (jr + 1) * N;
+        const size_t gbase = (size_t)mo * NN + (size_t)(P.g * R + jr) * N + x4;
+        const V4<T> cc = ld4(c + o + x4), cs = ld4(c + o - N + x4), cn = ld4(c + o + N + x4);
+        const V4<T> cb = ld4(zm + o + x4), ca = ld4(zp + o + x4);
+        const T left = c[o + xm1], right = c[o + xp4];
+        V4<T> zv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T vc = cc.v[e];
+          const T vxm = e == 0 ? left : cc.v[e == 0 ? 0 : e - 1];
+          const T vxp = e == 3 ? right : cc.v[e == 3 ? 3 : e + 1];
+          const T nb = (vxm + vxp) + (cs.v[e] + cn.v[e]) + (cb.v[e] + ca.v[e]);
+          const T mw = sv_psi[u].v[e] * vc * idt - lapc * (nb - T(6) * vc);
+          const T ze = sv_d[u].v[e] * (T(2) * sv_r[u].v[e] - mw);
+          zv.v[e] = ze;
+          a0.add(sv_r[u].v[e], ze);
+          a1.add(sv_r[u].v[e], sv_r[u].v[e]);
+        }
+        st4(z + gbase, zv);
+        if (!START) st4(rn + gbase, sv_r[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBulkRows; ++u) {
+      sv_psi[u] = cu_psi[u];
+      sv_r[u] = cu_r[u];
+      sv_d[u] = cu_d[u];
+    }
+  }
+  if (failed) {
+    if (tid == 0) {
+      for (int s = 0; s < kBulkStages; ++s) mbar_wait(bar + s, 0u, 1 << 16), mbar_wait(bar + s, 1u, 1 << 16);
+      B.sc[SC_KERR] = 1.0;
+    }
+    return;
+  }
+  Red<T> v[2] = {a0.red(), a1.red()};
+  __shared__ double res[2];
+  if (block_sum_last<2>(v, B, part, res, B.btile0, B.bntiles)) {
+    if (tid == 0) {
+      if (START) B.sc[SC_RZ] = res[0];
+      else cg_update_scalars(B, res[0], res[1], active);
+    }
   }
 }
 
@@ -1557,12 +1750,25 @@ template <typename T> void launch_cg_update(const Launch& L) {
   FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_fused(const Launch& L) {
+  if (L.bwork && L.poly) {  // polynomial preconditioner: direction from z, residual update forms the next z
+    FE_LAUNCH(L, KID_CG_DIRMATVEC,
+              (kb_cg_dirmatvec<T, true><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+    FE_LAUNCH(L, KID_CG_RUPDATE,
+              (kb_cg_rpoly<T, false><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+    return;
+  }
   if (L.bwork)
     FE_LAUNCH(L, KID_CG_DIRMATVEC,
-              (kb_cg_dirmatvec<T><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+              (kb_cg_dirmatvec<T, false><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
   else
     FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
   FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
+}
+// First polynomial-preconditioned residual z = P r of an inner solve and <r, z> (nothing without it)
+template <typename T> void launch_cg_start(const Launch& L) {
+  if (L.bwork && L.poly)
+    FE_LAUNCH(L, KID_CG_START,
+              (kb_cg_rpoly<T, true><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
 }
 template <typename T> void launch_cg_xfinal(const Launch& L) {
   FE_LAUNCH(L, KID_CG_XFINAL, (k_cg_xfinal<T><<<EGRID>>>(L.boxes, L.ework)));
@@ -1605,6 +1811,7 @@ template <typename T> void launch_mix_residual(const Launch& L, int first, int* 
 }
 template <typename T> void launch_refine_start(const Launch& L, int* outer_active) {
   FE_LAUNCH(L, KID_MIX_RES, (k_refine_start<T><<<EGRID>>>(L.boxes, L.ework, L.part, outer_active, L.active)));
+  launch_cg_start<T>(L);
 }
 template <typename T> void launch_refine(const Launch& L, int* outer_active) {
   if (L.ring_ok)  // every box's N a multiple of the 16-byte chunk, so even: column pairs
@@ -1612,6 +1819,7 @@ template <typename T> void launch_refine(const Launch& L, int* outer_active) {
               (kp_refine<T><<<L.nblocks, dim3(RTX, TY), 0, L.st>>>(L.boxes, L.work, L.part, outer_active, L.active)));
   else
     FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+  launch_cg_start<T>(L);
 }
 template <typename T> void launch_mix_finish_pp(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework, 1)));
@@ -1629,7 +1837,12 @@ template <typename T>
 int bulk_cg_prepare(int N) {
   const int bytes = bulk_smem_bytes<T>(N);
   if (bytes > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(kb_cg_dirmatvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+  if (cudaFuncSetAttribute(kb_cg_dirmatvec<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kb_cg_dirmatvec<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kb_cg_rpoly<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+      cudaFuncSetAttribute(kb_cg_rpoly<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
     return 0;
   return bytes;
 }
@@ -1638,7 +1851,7 @@ int bulk_cg_pairs(int N) { return N * (N / (kBulkCells / N)); }
 template <typename T>
 int bulk_cg_blocks_per_sm(int bytes) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T>, NTHR, bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T, false>, NTHR, bytes) != cudaSuccess) return 0;
   return nb;
 }
 
@@ -1661,6 +1874,7 @@ int bulk_cg_blocks_per_sm(int bytes) {
   template void launch_mix_accum<T>(const Launch&);              \
   template void launch_refine<T>(const Launch&, int*);           \
   template void launch_refine_start<T>(const Launch&, int*);     \
+  template void launch_cg_start<T>(const Launch&);               \
   template void launch_mix_finish_pp<T>(const Launch&);          \
   template void launch_mix_finish<T>(const Launch&);              \
   template void launch_fcg<T>(const Launch&, const float*);

@@ -35,6 +35,7 @@ FE_PCG_JACOBI = 0
 FE_BICGSTAB_JACOBI = 1
 FE_FCG_LEARNED = 2
 FE_FGMRES_LEARNED = 3
+FE_PCG_POLY = 4
 
 FE_RHO, FE_UX, FE_UY, FE_UZ, FE_P, FE_T, FE_PHIX, FE_PHIY, FE_PHIZ, FE_Y0 = range(10)
 FE_V0 = 17  # two-fluid dust: velocity component m of class j is FE_V0 + 3 j + m

@@ -108,6 +108,14 @@ def _psi_isothermal(prm, rho, p):
     return rho / p
 
 
+def _neumann1_without_the_two(matvec, diag):
+    return lambda v: (v - matvec(v / diag)) / diag
+
+
+def _neumann1_left_right_swapped(matvec, diag):
+    return lambda v: 2.0 * v / diag - matvec(v) / diag ** 2
+
+
 CASES = [
     ("I4 normalisation", ops, "I4", _bad_I4, lambda: t_ops.test_symbols(16, 1, 0)),
     ("G4 normalisation", ops, "G4", _bad_G4, lambda: t_ops.test_order_G4()),
@@ -124,6 +132,10 @@ CASES = [
      lambda: t_piso.test_adaptive_time_step_courant_number_and_growth()),
     ("Givens rotation with swapped entries", krylov, "_givens", _givens_transposed,
      lambda: t_solve.test_fgmres_minimises_residual_over_its_directions(3)),
+    ("Neumann polynomial without the factor 2", krylov, "neumann1", _neumann1_without_the_two,
+     lambda: t_solve.test_neumann1_is_two_jacobi_sweeps()),
+    ("Neumann polynomial with M D^-1 D^-1 order", krylov, "neumann1", _neumann1_left_right_swapped,
+     lambda: t_solve.test_neumann1_symmetric_positive_with_squared_jacobi_spectrum(0.4)),
     ("isothermal compressibility", piso, "compressibility", _psi_isothermal,
      lambda: t_piso.test_psi_is_inverse_isentropic_sound_speed_squared(piso.FOURIER)),
     ("Du/Dt pressure sign", piso, "accel", _accel_wrong_sign,

@@ -241,3 +241,64 @@ def test_fgmres_replaces_directions_that_make_no_progress():
     _, it_s, rec_s, _ = krylov.fgmres(matvec, b, lambda v, k: rnd.standard_normal(v.shape), diag, 1e-12, 60,
                                       m=20, keep=1.0)
     assert it_s == 60 and rec_s > 1e-6
+
+
+def _variable_system(N, dt, seed):
+    prm = piso.Params(N=N)
+    rng = np.random.default_rng(seed)
+    psi = 0.6 + 0.6 * rng.random((N, N, N))
+    matvec, diag = piso.helmholtz(prm, psi, dt)
+    return matvec, diag, rng
+
+
+def test_neumann1_is_two_jacobi_sweeps():
+    # the first-order Neumann polynomial applied to b is the second Jacobi iterate for M x = b from x = 0
+    matvec, diag, rng = _variable_system(10, 0.3, 21)
+    b = rng.standard_normal((10, 10, 10))
+    x = np.zeros_like(b)
+    for _ in range(2):
+        x = x + (b - matvec(x)) / diag
+    y = krylov.neumann1(matvec, diag)(b)
+    assert np.max(np.abs(y - x)) <= 1e-14 * np.max(np.abs(x))
+
+
+def _dense(apply, N):
+    n = N ** 3
+    A = np.zeros((n, n))
+    e = np.zeros(n)
+    for j in range(n):
+        e[j] = 1.0
+        A[:, j] = apply(e.reshape(N, N, N)).reshape(-1)
+        e[j] = 0.0
+    return A
+
+
+@pytest.mark.parametrize("dt", [0.05, 0.4])
+def test_neumann1_symmetric_positive_with_squared_jacobi_spectrum(dt):
+    N = 6
+    matvec, diag, _ = _variable_system(N, dt, 22)
+    M = _dense(matvec, N)
+    P = _dense(krylov.neumann1(matvec, diag), N)
+    assert np.max(np.abs(P - P.T)) <= 1e-13 * np.max(np.abs(P))
+    assert np.linalg.eigvalsh(0.5 * (P + P.T)).min() > 0.0
+    # D^-1 M is similar to the symmetric D^-1/2 M D^-1/2: eigenvalues mu in (0, 2)
+    d = diag.reshape(-1)
+    mu = np.sort(np.linalg.eigvalsh(M / np.sqrt(np.outer(d, d))))
+    assert mu.min() > 0.0 and mu.max() < 2.0
+    # I - P M = (I - D^-1 M)^2, so P M has the eigenvalues 1 - (1 - mu)^2, all in (0, 1]
+    lam = np.sort(np.real(np.linalg.eigvals(P @ M)))
+    np.testing.assert_allclose(lam, np.sort(1.0 - (1.0 - mu) ** 2), atol=1e-12)
+    # the preconditioned condition number is below the Jacobi one
+    assert lam.max() / lam.min() < mu.max() / mu.min()
+
+
+def test_pcg_neumann1_matches_dense_lu_in_fewer_iterations():
+    N, dt = 8, 0.4
+    matvec, diag, rng = _variable_system(N, dt, 23)
+    b = rng.standard_normal((N, N, N))
+    xe = scipy.linalg.solve(_dense(matvec, N), b.reshape(-1)).reshape(N, N, N)
+    xj, itj, _, tj = krylov.pcg(matvec, b, diag, 1e-13, 600)
+    xp, itp, _, tp = krylov.pcg(matvec, b, diag, 1e-13, 600, precond=krylov.neumann1(matvec, diag))
+    assert tp < 1e-13 and tj < 1e-13
+    assert np.max(np.abs(xp - xe)) < 1e-12 * np.max(np.abs(xe))
+    assert itp < itj
