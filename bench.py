@@ -243,7 +243,7 @@ def time_path(fe, box, cfg, precision, solver, args, stream, learned_every=0, we
                   p_maxit=1000, solver=solver, learned_every=learned_every, stream=stream.cuda_stream)
     s.init_state(0, fe.FE_INIT_SPECTRAL)
     out = {"precision": "fp64" if precision == fe.FE_FP64 else "mixed",
-           "solver": "jacobi-pcg" if solver == fe.FE_PCG_JACOBI else
+           "solver": "jacobi-pcg" if solver == fe.FE_PCG_JACOBI else "neumann1-pcg" if solver == fe.FE_PCG_POLY else
            ("fcg, learned direction every iteration" if learned_every == 1 else
             "fcg, learned first direction of each corrector")}
     if solver == fe.FE_FCG_LEARNED:
@@ -325,6 +325,12 @@ def unet_flops(N):
     return 2.0 * macs
 
 
+def solver_id(fe, args):
+    """The pressure solver of the FP32 paths: CG with the first-order Neumann polynomial preconditioner
+    (Jacobi-PCG where the planes are not streamed), or Jacobi-PCG."""
+    return fe.FE_PCG_POLY if args.solver == "poly" else fe.FE_PCG_JACOBI
+
+
 def time_ensemble(fe, args, compare=False):
     """The 64-box ensemble of uneven boxes (N in {32, 48, 64, 96}, FP32 fields, barotropic) in one context:
     one launch per stage over every box, CUDA-graph steps, autotuned tiles; with compare, the same boxes
@@ -336,7 +342,7 @@ def time_ensemble(fe, args, compare=False):
     K, W = max(args.steps, 3), max(args.warmup, 3)
 
     def timed(solver_boxes):
-        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8, solver=solver_id(fe, args))
         s.init_state(-1, fe.FE_INIT_SPECTRAL)
         s.autotune(2)
         s.use_graphs(True)
@@ -374,7 +380,7 @@ def ensemble_only(args):
     K, W = args.steps, args.warmup
 
     def timed(solver_boxes):
-        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+        s = fe.Solver(solver_boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8, solver=solver_id(fe, args))
         s.init_state(-1, fe.FE_INIT_SPECTRAL)
         s.autotune(2)
         s.use_graphs(True)
@@ -417,6 +423,7 @@ def part_only(args):
     hbm, kind = peaks()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"part": args.part, "N": N, "dtype": "f32 fields", "data": "synthetic spectral HIT field", "peak": hbm,
+           "solver": "neumann1-pcg" if args.solver == "poly" else "jacobi-pcg",
            "peak_kind": kind}
     if args.part == "les":
         out.update(time_les(fe, box, cfg, args, stream))
@@ -424,7 +431,7 @@ def part_only(args):
         res = {}
         for model in (fe.FE_DUST_EQUILIBRIUM, fe.FE_DUST_TWO_FLUID):
             s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"], p_maxit=1000,
-                          dust_model=model, stream=stream.cuda_stream)
+                          dust_model=model, solver=solver_id(fe, args), stream=stream.cuda_stream)
             s.init_state(0, fe.FE_INIT_SPECTRAL)
             s.autotune(1)
             s.use_graphs(True)
@@ -456,7 +463,7 @@ def part_only(args):
         res = {}
         for coupling in (fe.FE_COUPLING_ONE_WAY, fe.FE_COUPLING_TWO_WAY):
             s = fe.Solver([box], precision=fe.FE_FP32_MIXED, closure=cfg["closure"], p_tol=cfg["p_tol"],
-                          p_maxit=1000, coupling=coupling, stream=stream.cuda_stream)
+                          p_maxit=1000, coupling=coupling, solver=solver_id(fe, args), stream=stream.cuda_stream)
             s.init_state(0, fe.FE_INIT_SPECTRAL)
             s.autotune(1)
             s.use_graphs(True)
@@ -491,7 +498,7 @@ def part_only(args):
             w = WORKLOADS[name]
             bx_ = dict(N=n_, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], mach_rms=w["mach_rms"], k0=w["k0"], seed=0)
             s = fe.Solver([bx_], precision=fe.FE_FP32_MIXED, closure=w["closure"], p_tol=w["p_tol"], p_maxit=1000,
-                          stream=stream.cuda_stream)
+                          solver=solver_id(fe, args), stream=stream.cuda_stream)
             s.init_state(0, fe.FE_INIT_SPECTRAL)
             s.autotune(1)
             s.use_graphs(True)
@@ -594,7 +601,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--solver", default="jacobi", choices=["jacobi", "poly"],
+    ap.add_argument("--solver", default="poly", choices=["jacobi", "poly"],
                     help="pressure CG preconditioner: Jacobi, or the first-order Neumann polynomial")
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--ref-n", type=int, default=64)
@@ -659,7 +666,7 @@ def main():
     nd = len(cfg["tau_p"])
     box = rank_box(cfg, rank)
     stream = torch.cuda.current_stream()
-    solver = fe.FE_PCG_POLY if args.solver == "poly" else fe.FE_PCG_JACOBI
+    solver = solver_id(fe, args)
     poly = solver == fe.FE_PCG_POLY and precision == fe.FE_FP32_MIXED
     s = fe.Solver([box], precision=precision, closure=cfg["closure"], cfl=cfg["cfl"], p_tol=cfg["p_tol"],
                   p_maxit=1000, solver=solver, stream=stream.cuda_stream)
@@ -776,6 +783,9 @@ def main():
     extra = {}
     if not args.no_compare:
         extra["plain_fp64"], _ = time_path(fe, box, cfg, fe.FE_FP64, fe.FE_PCG_JACOBI, args, stream)
+        other = fe.FE_PCG_JACOBI if solver == fe.FE_PCG_POLY else fe.FE_PCG_POLY
+        extra["jacobi_fp32" if other == fe.FE_PCG_JACOBI else "neumann1_fp32"], _ = time_path(
+            fe, box, cfg, fe.FE_FP32_MIXED, other, args, stream)
         extra["learned_fp32"], wts = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args, stream, 0)
         extra["learned_fp32_every_iteration"], _ = time_path(fe, box, cfg, fe.FE_FP32_MIXED, fe.FE_FCG_LEARNED, args,
                                                              stream, 1, wts)
@@ -825,10 +835,12 @@ def main():
                     "unit": "GB/s", "frac": step_bytes / t * args.steps / 1e9 / hbm},
                 "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "peak_kind": peak_kind,
-                             "traffic": recorded_traffic(kernel, WORKLOAD) if N == 256 else None,
+                             "traffic": recorded_traffic(kernel + ("@neumann1" if poly and kernel in (
+                                 "cg_dirmatvec", "cg_rupdate", "cg_start") else ""), WORKLOAD) if N == 256 else None,
                              "alg_bytes_per_launch": alg_bytes, "launches": prof["target_launches"],
                              "ms_per_launch": per_launch_ms},
                 "kernel_ms_per_step": {k: round(v[0], 4) for k, v in share.items() if v[1] > 0},
+                "kernel_launches_per_step": {k: v[1] for k, v in share.items() if v[1] > 0},
                 "paths": extra,
                 "gpu_launches": prof["launches"],
                 "gpu_launches_note": "kernel launches of %d host-driven steps (the graph steps run the same kernels "

@@ -420,7 +420,7 @@ int bulk_smem_bytes(int N) {
 // POLY: the direction is pd_new = z + beta pd_old with z = P r from kb_cg_rpoly (first-order Neumann
 // polynomial preconditioner), streamed with y-halo rows in place of r and D^{-1}.
 template <typename T, bool POLY>
-__global__ void __launch_bounds__(NTHR) kb_cg_dirmatvec(const BoxDev* boxes, const int2* bwork, double* part) {
+__global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* boxes, const int2* bwork, double* part) {
   const int2 w = bwork[blockIdx.x];
   const BoxDev& B = boxes[w.x];
   if (box_done(B)) return;
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(NTHR) k_cg_rupdate(const BoxDev* boxes, const 
 // count (neighbouring blocks read the old residual as halo).  START: the first residual of an inner
 // solve (alpha = 0, r stays in K_R): z and <r, z> only, no iteration counted.
 template <typename T, bool START>
-__global__ void __launch_bounds__(NTHR) kb_cg_rpoly(const BoxDev* boxes, const int2* bwork, double* part, int* active) {
+__global__ void __launch_bounds__(kBulkThreads) kb_cg_rpoly(const BoxDev* boxes, const int2* bwork, double* part, int* active) {
   const int2 w = bwork[blockIdx.x];
   const BoxDev& B = boxes[w.x];
   if (box_done(B)) return;
@@ -1752,14 +1752,14 @@ template <typename T> void launch_cg_update(const Launch& L) {
 template <typename T> void launch_cg_fused(const Launch& L) {
   if (L.bwork && L.poly) {  // polynomial preconditioner: direction from z, residual update forms the next z
     FE_LAUNCH(L, KID_CG_DIRMATVEC,
-              (kb_cg_dirmatvec<T, true><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+              (kb_cg_dirmatvec<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
     FE_LAUNCH(L, KID_CG_RUPDATE,
-              (kb_cg_rpoly<T, false><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+              (kb_cg_rpoly<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
     return;
   }
   if (L.bwork)
     FE_LAUNCH(L, KID_CG_DIRMATVEC,
-              (kb_cg_dirmatvec<T, false><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+              (kb_cg_dirmatvec<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
   else
     FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
   FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
@@ -1768,7 +1768,7 @@ template <typename T> void launch_cg_fused(const Launch& L) {
 template <typename T> void launch_cg_start(const Launch& L) {
   if (L.bwork && L.poly)
     FE_LAUNCH(L, KID_CG_START,
-              (kb_cg_rpoly<T, true><<<L.nbblocks, NTHR, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+              (kb_cg_rpoly<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
 }
 template <typename T> void launch_cg_xfinal(const Launch& L) {
   FE_LAUNCH(L, KID_CG_XFINAL, (k_cg_xfinal<T><<<EGRID>>>(L.boxes, L.ework)));
@@ -1851,7 +1851,7 @@ int bulk_cg_pairs(int N) { return N * (N / (kBulkCells / N)); }
 template <typename T>
 int bulk_cg_blocks_per_sm(int bytes) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T, false>, NTHR, bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T, false>, kBulkThreads, bytes) != cudaSuccess) return 0;
   return nb;
 }
 

@@ -58,13 +58,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int ca
 }
 
 // ---- geometry and plane sequence ------------------------------------------------
-// Rows of four-cell groups per thread: a block covers kBulkCells cells of
-// each plane (4 x kBulkRows per thread).
-#ifndef FE_BULK_ROWS
-#define FE_BULK_ROWS 2
+// A block of kBulkThreads threads covers kBulkCells cells of each plane:
+// kBulkRows rows of four x-consecutive cells per thread.
+#ifndef FE_BULK_THREADS
+#define FE_BULK_THREADS 256
 #endif
-constexpr int kBulkRows = FE_BULK_ROWS;
-constexpr int kBulkCells = 1024 * kBulkRows;
+constexpr int kBulkThreads = FE_BULK_THREADS;
+#ifndef FE_BULK_CELLS
+#define FE_BULK_CELLS 2048
+#endif
+constexpr int kBulkCells = FE_BULK_CELLS;
+constexpr int kBulkRows = kBulkCells / (4 * kBulkThreads);
+static_assert(kBulkRows >= 1 && 4 * kBulkThreads * kBulkRows == kBulkCells, "bulk block shape");
 
 struct BulkGeom {
   int N, R, G, Q;  // box edge, rows per group, row groups, threads per row (N / 4)
