@@ -423,7 +423,7 @@ int fe_plane_streaming_active(const fe_ctx* ctx);
  * for every box, fe_set_box_tiling for one (0 = built-in default: 8 for
  * N >= 128, else 4).  fe_autotune times `trials` trial steps (computed from
  * the current state and discarded: the state and clock are unchanged) for
- * tz in {4, 8, 16, 32} for all boxes, then, when the boxes have several
+ * tz in {4, 8, 16, 24, 32, 48, 64} for all boxes, then, when the boxes have several
  * sizes, for each size in turn (largest first) with the other boxes fixed;
  * it keeps the fastest tiling and returns the depth of the largest box in
  * *best_tz (NULL allowed).  The x/y tile (32 x 8) and the copy lookahead of

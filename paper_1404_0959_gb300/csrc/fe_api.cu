@@ -1476,7 +1476,7 @@ extern "C" int fe_autotune(fe_ctx* c, int trials, int* best_tz) {
   int rc = pull_scalars(c);
   if (rc != FE_OK) return rc;
   std::vector<double> saved(c->hsc, c->hsc + (size_t)c->nb * NSC);
-  const int cand[] = {4, 8, 16, 32};
+  const int cand[] = {4, 8, 16, 24, 32, 48, 64};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
