@@ -176,3 +176,73 @@ def test_poly_with_transonic_operator_is_refused(fe):
     with pytest.raises(fe.FeError):
         fe.Solver([dict(N=64, nu=0.005, tau_p=[0.05], Y0=[0.01])], precision=fe.FE_FP32_MIXED,
                   solver=fe.FE_PCG_POLY, transonic=1)
+
+
+def rounded_state(prm, rho, u, Y, T=None):
+    st = piso.make_state(prm, f32(rho), [f32(c) for c in u], [f32(y) for y in Y], None if T is None else f32(T))
+    out = dict(st)
+    for k in ("rho", "p", "T"):
+        if st.get(k) is not None:
+            out[k] = f32(st[k])
+    for k in ("u", "phi", "Y"):
+        out[k] = [f32(c) for c in st[k]]
+    if st.get("V") is not None:
+        out["V"] = [[f32(c) for c in vj] for vj in st["V"]]
+    return out
+
+
+def test_poly_fourier_three_classes_matches_oracle(fe):
+    N, tau = 64, (0.02, 0.1, 0.3)
+    rho, u, Y, T = random_fields(N, 3, True, seed=11, mach=0.5, noise=0.02)
+    prm = piso.Params(N=N, closure=piso.FOURIER, nu=0.002, tau_p=list(tau), Y0=[0.02] * 3, p_tol=1e-8)
+    st = rounded_state(prm, rho, u, Y, T)
+    ref, _ = piso.step(prm, st)
+    s = fe.Solver([dict(N=N, nu=0.002, tau_p=list(tau), Y0=[0.02] * 3)], precision=fe.FE_FP32_MIXED,
+                  closure=fe.FE_FOURIER, p_tol=1e-8, solver=fe.FE_PCG_POLY)
+    s.load_state(0, st)
+    assert s.plane_streaming_active()
+    code, ginf = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    got = s.get_state(0)
+    s.close()
+    assert max(ginf[0]["rel_res"]) <= 1e-8 * (1 + 1e-3)
+    assert worst(got, ref) <= 1e-5
+    assert rel(got["T"], ref["T"]) <= 1e-5
+
+
+def test_poly_two_fluid_matches_oracle(fe):
+    N, tau = 64, (0.05, 0.2)
+    rho, u, Y, _ = random_fields(N, 2, False, seed=12, mach=0.3, noise=0.01)
+    prm = piso.Params(N=N, nu=0.005, tau_p=list(tau), Y0=[0.01] * 2, dust_model=piso.TWO_FLUID, p_tol=1e-8)
+    st = rounded_state(prm, rho, u, Y)
+    ref, _ = piso.step(prm, st)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=list(tau), Y0=[0.01] * 2)], precision=fe.FE_FP32_MIXED, p_tol=1e-8,
+                  dust_model=fe.FE_DUST_TWO_FLUID, solver=fe.FE_PCG_POLY)
+    s.load_state(0, st)
+    assert s.plane_streaming_active()
+    code, _ = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    got = s.get_state(0)
+    s.close()
+    assert worst(got, ref) <= 1e-5
+    for j in range(2):
+        for m in range(3):
+            assert rel(got["V"][j][m], ref["V"][j][m]) <= 1e-5, (j, m)
+
+
+def test_poly_two_way_matches_oracle(fe):
+    N, tau = 64, (0.05,)
+    rho, u, Y, _ = random_fields(N, 1, False, seed=13, mach=0.3, noise=0.02)
+    Y = [20.0 * y for y in Y]  # loading 0.2
+    prm = piso.Params(N=N, nu=0.005, tau_p=list(tau), Y0=[0.2], p_tol=1e-8, coupling=piso.TWO_WAY)
+    st = rounded_state(prm, rho, u, Y)
+    ref, _ = piso.step(prm, st)
+    s = fe.Solver([dict(N=N, nu=0.005, tau_p=list(tau), Y0=[0.2])], precision=fe.FE_FP32_MIXED, p_tol=1e-8,
+                  coupling=fe.FE_COUPLING_TWO_WAY, solver=fe.FE_PCG_POLY)
+    s.load_state(0, st)
+    assert s.plane_streaming_active()
+    code, _ = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    got = s.get_state(0)
+    s.close()
+    assert worst(got, ref) <= 1e-5
