@@ -339,6 +339,10 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxe
   if (TW) R.gc[TW ? 1 : 0] = Fr<T>(B, ysl);
   T* __restrict__ a[3] = {Fr<T>(B, W_AN0), Fr<T>(B, W_AN1), Fr<T>(B, W_AN2)};
   const T ih = (T)B.ih, mu = (T)B.mu;
+  // a_m = (mu (lap u_m + Gc_m(div) / 3) - Gc_m p) / rho with the compact fourth-order Laplacian
+  // sum_d D G4_d = (28 S1 - 162 u - S2) / (24 h^2) (S1, S2: sums of the six neighbours at distance 1
+  // and 2) and Gc_m = (10 (f_+1 - f_-1) - (f_+2 - f_-2)) / (16 h); the constant factors are folded
+  const T cl = mu * ih * ih * T(1.0 / 24.0), cd = mu * ih * T(1.0 / 48.0), cg = ih * T(0.0625);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
@@ -348,21 +352,33 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxe
     const P2<T> crho = R.cen(0, k, tid);
     P2<T> ys2;
     if (TW) ys2 = R.cen(TW ? 1 : 0, k, tid);
-    T oa[3][2];
+    T ir[2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
-      const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
-      const T ir = TW ? rcp_rn(pc<T>(crho, r) * (T(1) + pc<T>(ys2, r))) : rcp_rn(pc<T>(crho, r));
+    for (int r = 0; r < 2; ++r)
+      ir[r] = TW ? rcp_rn(pc<T>(crho, r) * (T(1) + pc<T>(ys2, r))) : rcp_rn(pc<T>(crho, r));
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const T lap = zDG4_h2(u[m], G, 0) + zDG4_h2(u[m], G, 1) + zDG4_h2(u[m], G, 2);
-        const T visc = mu * (lap * ih * ih + zGc_h(div, G, m) * ih * T(1.0 / 3.0));
-        oa[m][r] = (visc - zGc_h(p, G, m) * ih) * ir;
+    for (int m = 0; m < 3; ++m) {
+      T lap[2];
+      {
+        const Line2<T> lx = ring_line(R, m, k, G, 0), ly = ring_line(R, m, k, G, 1), lz = ring_line(R, m, k, G, 2);
+        const P2<T> uc = R.zq[m][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const T s1 = (lx.m1[r] + lx.p1[r]) + (ly.m1[r] + ly.p1[r]) + (lz.m1[r] + lz.p1[r]);
+          const T s2 = (lx.m2[r] + lx.p2[r]) + (ly.m2[r] + ly.p2[r]) + (lz.m2[r] + lz.p2[r]);
+          lap[r] = fma(T(28), s1, -fma(T(162), pc<T>(uc, r), s2));
+        }
       }
-    }
+      const Line2<T> ld = ring_line(R, 3, k, G, m), lp = ring_line(R, 4, k, G, m);
+      T oa[2];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) stp(a[m] + c, oa[m][0], oa[m][1]);
+      for (int r = 0; r < 2; ++r) {
+        const T gd = fma(T(10), ld.p1[r] - ld.m1[r], -(ld.p2[r] - ld.m2[r]));
+        const T gp = fma(T(10), lp.p1[r] - lp.m1[r], -(lp.p2[r] - lp.m2[r]));
+        oa[r] = (fma(cl, lap[r], cd * gd) - cg * gp) * ir[r];
+      }
+      stp(a[m] + c, oa[0], oa[1]);
+    }
   }
   cp_async_wait<0>();
 }

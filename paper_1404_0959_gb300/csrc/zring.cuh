@@ -306,4 +306,36 @@ struct RingPlan {
   }
 };
 
+// The neighbours at distance 1 and 2 along axis d of both cells (index r) of the thread's pair, for
+// stencil field f of a ring plan at plane k: two pair reads along x (the pairs left and right of the
+// own one, which is the queue's centre), four along y, none along z (the queue).  Loading a line once
+// and evaluating both cells from registers replaces the per-cell, per-stencil reads of ZView.
+template <typename T>
+struct Line2 {
+  T m2[2], m1[2], p1[2], p2[2];
+};
+template <typename T, typename Plan>
+__device__ __forceinline__ Line2<T> ring_line(const Plan& R, int f, int k, const RGeom<T>& G, int d) {
+  Line2<T> L;
+  const P2<T> c = R.zq[f][2];
+  if (d == 2) {
+    const P2<T> a = R.zq[f][0], b = R.zq[f][1], e = R.zq[f][3], g = R.zq[f][4];
+    L.m2[0] = a.x, L.m2[1] = a.y, L.m1[0] = b.x, L.m1[1] = b.y;
+    L.p1[0] = e.x, L.p1[1] = e.y, L.p2[0] = g.x, L.p2[1] = g.y;
+    return L;
+  }
+  const T* p = R.sslot(f, k) + G.csm;
+  if (d == 1) {
+    constexpr int W = RGeom<T>::W;
+    const P2<T> a = ldp(p - 2 * W), b = ldp(p - W), e = ldp(p + W), g = ldp(p + 2 * W);
+    L.m2[0] = a.x, L.m2[1] = a.y, L.m1[0] = b.x, L.m1[1] = b.y;
+    L.p1[0] = e.x, L.p1[1] = e.y, L.p2[0] = g.x, L.p2[1] = g.y;
+    return L;
+  }
+  const P2<T> l = ldp(p - 2), r = ldp(p + 2);  // cells x-2, x-1 and x+2, x+3
+  L.m2[0] = l.x, L.m1[0] = l.y, L.p1[0] = c.y, L.p2[0] = r.x;
+  L.m2[1] = l.y, L.m1[1] = c.x, L.p1[1] = r.x, L.p2[1] = r.y;
+  return L;
+}
+
 }  // namespace fe
