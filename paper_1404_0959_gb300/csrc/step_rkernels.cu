@@ -384,11 +384,50 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_accel(const BoxDev* boxe
 }
 
 // ---- dust: n-level flux divergences FYN_j = D(phi_p^n I4 Y_j^n) --------------------------------------------
+// h D(phi_p I4 Y_j) for both cells of the pair and every class: phi_p = phi - tau_j I4(rho) I4(a_d) at each
+// face (rho, a0..2, Y_j: stencil fields 0, 1..3, 4 + j of the plan; phi: face arrays 0..2).  Lines of rho
+// and a_d along d, and of Y_j along d, each read once; 16 I4 evaluated unscaled, the factors folded.
+template <typename T, int ND, typename Plan>
+__device__ __forceinline__ void ring_particle_flux(const Plan& R, int k, const RGeom<T>& G, const T (&taup)[ND],
+                                                   T (&fl)[ND][2]) {
+  T php[3][2], phm[3][2];
+  R.faces2(0, k, G, php, phm);
+  const P2<T> rc = R.zq[0][2];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) fl[j][0] = fl[j][1] = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T rap[2], ram[2];
+    {
+      const Line2<T> lr = ring_line(R, 0, k, G, d), la = ring_line(R, 1 + d, k, G, d);
+      const P2<T> ac = R.zq[1 + d][2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        rap[r] = i4p16(lr, pc<T>(rc, r), r) * i4p16(la, pc<T>(ac, r), r);
+        ram[r] = i4m16(lr, pc<T>(rc, r), r) * i4m16(la, pc<T>(ac, r), r);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const T tq = taup[j] * T(1.0 / 256.0);
+      const Line2<T> ly = ring_line(R, 4 + j, k, G, d);
+      const P2<T> yc = R.zq[4 + j][2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        fl[j][r] += fma(-tq, rap[r], php[d][r]) * i4p16(ly, pc<T>(yc, r), r) -
+                    fma(-tq, ram[r], phm[d][r]) * i4m16(ly, pc<T>(yc, r), r);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < ND; ++j) fl[j][0] *= T(0.0625), fl[j][1] *= T(0.0625);
+}
+
 template <typename T, int ND>
-using FluxPlan = RingPlan<T, kA1, 4 + ND, 3, 0>;  // rho, a0..2, Y_j | phi
+using FluxPlan = RingPlan<T, kA, 4 + ND, 3, 0>;  // rho, a0..2, Y_j | phi (two planes ahead: measured)
 template <typename T, int ND>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fluxn(const BoxDev* boxes, const int2* work, int s) {
   RING_PROLOGUE((FluxPlan<T, ND>));
+  (void)tid;  // no centre fields
   R.gs[0] = Fr<T>(B, S(s, F_RHO));
 #pragma unroll
   for (int d = 0; d < 3; ++d) R.gs[1 + d] = Fr<T>(B, W_AN0 + d);
@@ -410,32 +449,10 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fluxn(const BoxDev* boxe
     R.next(G, i);
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
-    T of[ND][2];
+    T fl[ND][2];
+    ring_particle_flux<T, ND>(R, k, G, taup, fl);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const ZView<T> rho = R.view(0, k, G, r);
-      const ZView<T> a[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
-      T php[3], phm[3];
-      R.faces(0, k, G, r, php, phm);
-      T ra_p[3], ra_m[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
-        ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
-      }
-#pragma unroll
-      for (int j = 0; j < ND; ++j) {
-        const ZView<T> Y = R.view(4 + j, k, G, r);
-        const T tp = taup[j];
-        T acc = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-          acc += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
-        of[j][r] = acc * ih;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < ND; ++j) stp(fyn[j] + c, of[j][0], of[j][1]);
+    for (int j = 0; j < ND; ++j) stp(fyn[j] + c, fl[j][0] * ih, fl[j][1] * ih);
   }
   cp_async_wait<0>();
 }
@@ -494,29 +511,16 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
     const int c = G.col + G.plane(k);
     const P2<T> crn = R.cen(0, k, tid);
     T oy[ND][2], op[2], oe[2], ot[2];
+    T flx[ND][2];
+    ring_particle_flux<T, ND>(R, k, G, taup, flx);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const ZView<T> rho = R.view(0, k, G, r);
-      const ZView<T> a[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
-      T php[3], phm[3];
-      R.faces(0, k, G, r, php, phm);
-      const T rk = rho.c();
+      const T rk = pc<T>(R.zq[0][2], r);
       const T irk = rcp_rn(rk);
       const T rn = pc<T>(crn, r);
-      T ra_p[3], ra_m[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        ra_p[d] = zI4(rho, G, d, 0) * zI4(a[d], G, d, 0);
-        ra_m[d] = zI4(rho, G, d, -1) * zI4(a[d], G, d, -1);
-      }
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
-        const ZView<T> Y = R.view(4 + j, k, G, r);
-        const T tp = taup[j];
-        T fl = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-          fl += (php[d] - tp * ra_p[d]) * zI4(Y, G, d, 0) - (phm[d] - tp * ra_m[d]) * zI4(Y, G, d, -1);
+        const T fl = flx[j][r];
         const T rY = rn * pc<T>(R.cen(1 + j, k, tid), r) - T(0.5) * dt * (pc<T>(R.cen(1 + ND + j, k, tid), r) + fl * ih);
         const T Yk = rY * irk;
         oy[j][r] = Yk;
@@ -589,10 +593,11 @@ template <typename T>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes, const int2* work, int u0,
                                                             double* part, int with_dt) {
   RING_PROLOGUE(DivPlan<T>);
+  (void)tid;  // no centre fields
 #pragma unroll
   for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, u0 + m);
   T* __restrict__ div = Fr<T>(B, W_DIV);
-  const T ih = (T)B.ih;
+  const T ih16 = (T)B.ih * T(0.0625);
   T umax = T(0);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
@@ -600,11 +605,12 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes,
     R.next(G, i);
     if (!G.active) continue;
     T od[2];
+    const Line2<T> l0 = ring_line(R, 0, k, G, 0), l1 = ring_line(R, 1, k, G, 1), l2 = ring_line(R, 2, k, G, 2);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
-      od[r] = (zGc_h(u[0], G, 0) + zGc_h(u[1], G, 1) + zGc_h(u[2], G, 2)) * ih;
-      if (with_dt) umax = fmax(umax, fabs(u[0].c()) + fabs(u[1].c()) + fabs(u[2].c()));
+      od[r] = ((gc16(l0, r) + gc16(l1, r)) + gc16(l2, r)) * ih16;
+      if (with_dt)
+        umax = fmax(umax, fabs(pc<T>(R.zq[0][2], r)) + fabs(pc<T>(R.zq[1][2], r)) + fabs(pc<T>(R.zq[2][2], r)));
     }
     stp(div + G.col + G.plane(k), od[0], od[1]);
   }

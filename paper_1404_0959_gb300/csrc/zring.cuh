@@ -300,6 +300,19 @@ struct RingPlan {
     plus[2] = pc<T>(ldp(fz + G.csm), r);
     minus[2] = pc<T>(ldp(fzm + G.csm), r);
   }
+  // the same for both cells at once: plus[d][r], minus[d][r]
+  __device__ __forceinline__ void faces2(int f0, int k, const G_& G, T (&plus)[3][2], T (&minus)[3][2]) const {
+    const T* fx = rf + (f0 * SL::NF + sl.f(k)) * HW;
+    const T* fy = rf + ((f0 + 1) * SL::NF + sl.f(k)) * HW;
+    const T* fz = rf + ((f0 + 2) * SL::NF + sl.f(k)) * HW;
+    const T* fzm = rf + ((f0 + 2) * SL::NF + sl.f(k - 1)) * HW;
+    const P2<T> xc = ldp(fx + G.csm), xl = ldp(fx + G.csm - 2);
+    const P2<T> yc = ldp(fy + G.csm), yl = ldp(fy + G.csm - G_::W);
+    const P2<T> zc = ldp(fz + G.csm), zl = ldp(fzm + G.csm);
+    plus[0][0] = xc.x, plus[0][1] = xc.y, minus[0][0] = xl.y, minus[0][1] = xc.x;
+    plus[1][0] = yc.x, plus[1][1] = yc.y, minus[1][0] = yl.x, minus[1][1] = yl.y;
+    plus[2][0] = zc.x, plus[2][1] = zc.y, minus[2][0] = zl.x, minus[2][1] = zl.y;
+  }
   // centre field f at plane k, both cells of the pair
   __device__ __forceinline__ P2<T> cen(int f, int k, int tid) const {
     return ldp(rc + (f * SL::NC + sl.c(k)) * NTHR + 2 * tid);
@@ -336,6 +349,20 @@ __device__ __forceinline__ Line2<T> ring_line(const Plan& R, int f, int k, const
   L.m2[0] = l.x, L.m1[0] = l.y, L.p1[0] = c.y, L.p2[0] = r.x;
   L.m2[1] = l.y, L.m1[1] = c.x, L.p1[1] = r.x, L.p2[1] = r.y;
   return L;
+}
+// 16 x the fourth-order face values I4 at the +1/2 and -1/2 faces of cell r along a line (centre value c)
+template <typename T>
+__device__ __forceinline__ T i4p16(const Line2<T>& L, T c, int r) {
+  return fma(T(9), c + L.p1[r], -(L.m1[r] + L.p2[r]));
+}
+template <typename T>
+__device__ __forceinline__ T i4m16(const Line2<T>& L, T c, int r) {
+  return fma(T(9), L.m1[r] + c, -(L.m2[r] + L.p1[r]));
+}
+// 16 h x the centred fourth-order derivative Gc of cell r along a line
+template <typename T>
+__device__ __forceinline__ T gc16(const Line2<T>& L, int r) {
+  return fma(T(10), L.p1[r] - L.m1[r], -(L.p2[r] - L.m2[r]));
 }
 
 }  // namespace fe
