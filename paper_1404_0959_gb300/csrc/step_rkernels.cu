@@ -11,8 +11,9 @@ namespace fe {
 
 // Lookahead planes of each ring kernel (shared memory per block grows with
 // it; measured at 256^3 FP32 with column-pair threads: the corrector, the
-// predictor, Du/Dt, the divergence and the right-hand side run best with two
-// planes, the assembly and the dust kernels with one), and the predictor's
+// predictor, Du/Dt, the divergence, the right-hand side and the n-level flux
+// divergences run best with two planes, the assembly and the dust kernels with
+// one), and the predictor's
 // register cap (three resident blocks per SM in FP32: its 174-register build
 // left it at two and ran 25 % slower).
 #ifndef FE_RING_A
@@ -172,6 +173,41 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_corr(const BoxDev* boxes
   }
 }
 
+// L_m = -D(phi I4 u_m) + mu (lap u_m + Gc_m(div) / 3) and its viscous part for both cells of the pair
+// (u0..2, div: stencil fields 0..3 of the plan; face fluxes phm / php of both cells), from one line of
+// u_m per axis and one of div along m: the convection from the unscaled 16 I4 at both faces, the compact
+// Laplacian as (28 S1 - 162 u - S2) / 24 (S1, S2: the six neighbours at distance 1 and 2), Gc unscaled;
+// cl = mu / (24 h^2), cd = mu / (48 h), cc = 1 / (16 h).
+template <typename T, typename Plan>
+__device__ __forceinline__ void ring_L(const Plan& R, int k, const RGeom<T>& G, const T (&php)[3][2],
+                                       const T (&phm)[3][2], T cl, T cd, T cc, T (&L)[3][2], T (&visc)[3][2]) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T conv[2], lap[2];
+    {
+      const Line2<T> l[3] = {ring_line(R, m, k, G, 0), ring_line(R, m, k, G, 1), ring_line(R, m, k, G, 2)};
+      const P2<T> uc = R.zq[m][2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T u = pc<T>(uc, r);
+        T cv = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cv += php[d][r] * i4p16(l[d], u, r) - phm[d][r] * i4m16(l[d], u, r);
+        conv[r] = cv;
+        const T s1 = (l[0].m1[r] + l[0].p1[r]) + (l[1].m1[r] + l[1].p1[r]) + (l[2].m1[r] + l[2].p1[r]);
+        const T s2 = (l[0].m2[r] + l[0].p2[r]) + (l[1].m2[r] + l[1].p2[r]) + (l[2].m2[r] + l[2].p2[r]);
+        lap[r] = fma(T(28), s1, -fma(T(162), u, s2));
+      }
+    }
+    const Line2<T> ld = ring_line(R, 3, k, G, m);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      visc[m][r] = fma(cl, lap[r], cd * gc16(ld, r));
+      L[m][r] = visc[m][r] - cc * conv[r];
+    }
+  }
+}
+
 // two-way: Ysum as a second centre field with one plane of lookahead, so that three blocks per
 // multiprocessor still fit in FP32
 template <typename T, bool TW = false>
@@ -196,6 +232,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
   T* __restrict__ rho0 = Fr<T>(B, S(kset, F_RHO));
   T* __restrict__ us[3] = {Fr<T>(B, S(kset, F_U0)), Fr<T>(B, S(kset, F_U1)), Fr<T>(B, S(kset, F_U2))};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT], gam = (T)B.gamma;
+  const T cl = mu * ih * ih * T(1.0 / 24.0), cd = mu * ih * T(1.0 / 48.0), cc = ih * T(0.0625);
   const JacobiDiag<T> jd(B.sc[SC_DT], B.ih);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
@@ -207,40 +244,43 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 ? FE_RING_MINB_PRED : FE_R
     P2<T> ys2;
     if (TW) ys2 = R.cen(TW ? 1 : 0, k, tid);
     T ous[3][2], oRn[3][2], oAn[3][2], ops[2], odi[2], odp[2], or0[2];
+    T php[3][2], phm[3][2];
+    R.faces2(0, k, G, php, phm);
+    T L[3][2], visc[3][2];
+    ring_L(R, k, G, php, phm, cl, cd, cc, L, visc);
+    T gp[3][2];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const Line2<T> lp = ring_line(R, 4, k, G, m);
+      gp[m][0] = cc * gc16(lp, 0);
+      gp[m][1] = cc * gc16(lp, 1);
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
-      const ZView<T> div = R.view(3, k, G, r), p = R.view(4, k, G, r);
-      T php[3], phm[3];
-      R.faces(0, k, G, r, php, phm);
-      const T dph = ((php[0] - phm[0]) + (php[1] - phm[1]) + (php[2] - phm[2])) * ih;
+      const T dph = ((php[0][r] - phm[0][r]) + (php[1][r] - phm[1][r]) + (php[2][r] - phm[2][r])) * ih;
       const T rc = pc<T>(crho, r);
       const T r0 = rc - dt * dph;
       const T ir0 = rcp_rn(r0), ir = rcp_rn(rc);
-      T L[3], visc[3];
-      zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
       if (TW) {
         const T ys = pc<T>(ys2, r);
         const T ia = rcp_rn(rc * (T(1) + ys)), w = rc * ys;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const T gp = zGc_h(p, G, m) * ih;
-          const T a = (visc[m] - gp) * ia;
-          const T Rf = L[m] - w * a;
-          ous[m][r] = (rc * u[m].c() + dt * (Rf - gp)) * ir0;
+          const T a = (visc[m][r] - gp[m][r]) * ia;
+          const T Rf = L[m][r] - w * a;
+          ous[m][r] = (rc * pc<T>(R.zq[m][2], r) + dt * (Rf - gp[m][r])) * ir0;
           oRn[m][r] = Rf;
           oAn[m][r] = a;
         }
       } else {
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const T gp = zGc_h(p, G, m) * ih;
-          ous[m][r] = (rc * u[m].c() + dt * (L[m] - gp)) * ir0;
-          oRn[m][r] = L[m];
-          oAn[m][r] = (visc[m] - gp) * ir;
+          ous[m][r] = (rc * pc<T>(R.zq[m][2], r) + dt * (L[m][r] - gp[m][r])) * ir0;
+          oRn[m][r] = L[m][r];
+          oAn[m][r] = (visc[m][r] - gp[m][r]) * ir;
         }
       }
-      const T ps = rc / (gam * p.c());
+      const T ps = rc / (gam * pc<T>(R.zq[4][2], r));
       ops[r] = ps;
       odi[r] = jd.inv(ps);
       odp[r] = dph;
@@ -288,6 +328,7 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 && TW ? 3 : FE_RING_MINB) 
   }
   T* __restrict__ hb[3] = {Fr<T>(B, W_HB0), Fr<T>(B, W_HB1), Fr<T>(B, W_HB2)};
   const T ih = (T)B.ih, mu = (T)B.mu, dt = (T)B.sc[SC_DT];
+  const T cl = mu * ih * ih * T(1.0 / 24.0), cd = mu * ih * T(1.0 / 48.0), cc = ih * T(0.0625);
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
     const int k = t.k0 + i;
@@ -296,24 +337,22 @@ __global__ void __launch_bounds__(RNT, sizeof(T) == 4 && TW ? 3 : FE_RING_MINB) 
     const int c = G.col + G.plane(k);
     const P2<T> crho = R.cen(0, k, tid), crp = R.cen(4, k, tid);
     T ohb[3][2];
+    T php[3][2], phm[3][2];
+    R.faces2(0, k, G, php, phm);
+    T L[3][2], visc[3][2];
+    ring_L(R, k, G, php, phm, cl, cd, cc, L, visc);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const ZView<T> u[3] = {R.view(0, k, G, r), R.view(1, k, G, r), R.view(2, k, G, r)};
-      const ZView<T> div = R.view(3, k, G, r);
-      T php[3], phm[3];
-      R.faces(0, k, G, r, php, phm);
-      T L[3], visc[3];
-      zeval_L<T>(u, div, php, phm, G, ih, mu, L, visc);
       const T rc = pc<T>(crho, r);
       const T irp = rcp_rn(pc<T>(crp, r));
       if (TW) {
         const T w = pc<T>(crp, r) * pc<T>(R.cen(TW ? 8 : 0, k, tid), r);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) L[m] = L[m] - w * pc<T>(R.cen(TW ? 9 + m : 0, k, tid), r);
+        for (int m = 0; m < 3; ++m) L[m][r] = L[m][r] - w * pc<T>(R.cen(TW ? 9 + m : 0, k, tid), r);
       }
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const T Rm = T(0.5) * (pc<T>(R.cen(5 + m, k, tid), r) + L[m]);
+        const T Rm = T(0.5) * (pc<T>(R.cen(5 + m, k, tid), r) + L[m][r]);
         ohb[m][r] = (rc * pc<T>(R.cen(1 + m, k, tid), r) + dt * Rm) * irp;
       }
     }
