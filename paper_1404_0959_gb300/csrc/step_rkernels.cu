@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
   T* __restrict__ ps[3] = {Fr<T>(B, W_PS0), Fr<T>(B, W_PS1), Fr<T>(B, W_PS2)};
   T* __restrict__ b = Fr<T>(B, start ? K_AUX : K_B);
   T* __restrict__ r0 = Fr<T>(B, K_R);
-  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt;
+  const T ih = (T)B.ih, dt = (T)B.sc[SC_DT], idt = T(1) / dt, dih = dt * ih;
   DotAcc<T> abb, abz;
   R.prologue(G);
   for (int i = 0; i < t.kend - t.k0; ++i) {
@@ -692,21 +692,26 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
     if (!G.active) continue;
     const int c = G.col + G.plane(k);
     const P2<T> crho = R.cen(0, k, tid), cdp = R.cen(1, k, tid);
-    T ops[3][2], ob[2];
+    // phi* at the +1/2 faces and D phi* from lines of rho', HbyA_d and p along d (16 I4 unscaled)
+    T ops[3][2], ob[2], dsum[2] = {T(0), T(0)};
+    const P2<T> rpc = R.zq[0][2], pcc = R.zq[4][2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const ZView<T> rp = R.view(0, k, G, r), p = R.view(4, k, G, r);
-      const ZView<T> hb[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
-      T dsum = T(0);
+    for (int d = 0; d < 3; ++d) {
+      const Line2<T> lr = ring_line(R, 0, k, G, d), lh = ring_line(R, 1 + d, k, G, d);
+      const Line2<T> lp = ring_line1(R, 4, k, G, d);
+      const P2<T> hc = R.zq[1 + d][2];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const T fp = zI4(rp, G, d, 0) * zI4(hb[d], G, d, 0) - dt * (p.at(G, d, 1) - p.c()) * ih;
-        const T fm = zI4(rp, G, d, -1) * zI4(hb[d], G, d, -1) - dt * (p.c() - p.at(G, d, -1)) * ih;
+      for (int r = 0; r < 2; ++r) {
+        const T rc = pc<T>(rpc, r), h = pc<T>(hc, r), p = pc<T>(pcc, r);
+        const T fp = i4p16(lr, rc, r) * i4p16(lh, h, r) * T(1.0 / 256.0) - dih * (lp.p1[r] - p);
+        const T fm = i4m16(lr, rc, r) * i4m16(lh, h, r) * T(1.0 / 256.0) - dih * (p - lp.m1[r]);
         ops[d][r] = fp;
-        dsum += fp - fm;
+        dsum[r] += fp - fm;
       }
-      ob[r] = -((rp.c() - pc<T>(crho, r)) * idt + T(0.5) * pc<T>(cdp, r) + T(0.5) * dsum * ih);
     }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      ob[r] = -((pc<T>(rpc, r) - pc<T>(crho, r)) * idt + T(0.5) * pc<T>(cdp, r) + T(0.5) * dsum[r] * ih);
 #pragma unroll
     for (int d = 0; d < 3; ++d) stp(ps[d] + c, ops[d][0], ops[d][1]);
     stp(b + c, ob[0], ob[1]);

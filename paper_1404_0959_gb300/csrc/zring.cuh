@@ -350,6 +350,27 @@ __device__ __forceinline__ Line2<T> ring_line(const Plan& R, int f, int k, const
   L.m2[1] = l.y, L.m1[1] = c.x, L.p1[1] = r.x, L.p2[1] = r.y;
   return L;
 }
+// Only the neighbours at distance 1 (m1, p1; m2, p2 left unset): two reads along x, two along y.
+template <typename T, typename Plan>
+__device__ __forceinline__ Line2<T> ring_line1(const Plan& R, int f, int k, const RGeom<T>& G, int d) {
+  Line2<T> L;
+  const P2<T> c = R.zq[f][2];
+  if (d == 2) {
+    const P2<T> b = R.zq[f][1], e = R.zq[f][3];
+    L.m1[0] = b.x, L.m1[1] = b.y, L.p1[0] = e.x, L.p1[1] = e.y;
+    return L;
+  }
+  const T* p = R.sslot(f, k) + G.csm;
+  if (d == 1) {
+    constexpr int W = RGeom<T>::W;
+    const P2<T> b = ldp(p - W), e = ldp(p + W);
+    L.m1[0] = b.x, L.m1[1] = b.y, L.p1[0] = e.x, L.p1[1] = e.y;
+    return L;
+  }
+  const P2<T> l = ldp(p - 2), r = ldp(p + 2);
+  L.m1[0] = l.y, L.p1[0] = c.y, L.m1[1] = c.x, L.p1[1] = r.x;
+  return L;
+}
 // 16 x the fourth-order face values I4 at the +1/2 and -1/2 faces of cell r along a line (centre value c)
 template <typename T>
 __device__ __forceinline__ T i4p16(const Line2<T>& L, T c, int r) {
