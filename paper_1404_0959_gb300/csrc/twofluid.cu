@@ -177,34 +177,39 @@ __global__ void __launch_bounds__(NTHR) k_tf_corr(const BoxDev* boxes, const int
 }
 
 // ---- ring forms (one class j per launch) --------------------------------------------------------
-// D(F) and D(G_m) from ring views of the carrier density, the carrier velocity, the class's Y and V,
-// and the carrier face fluxes (the same expressions as tf_div: I4 to the +1/2 face from offsets
-// -1..2, to the -1/2 face from -2..1).
+// D(F) and D(G_m) of both cells of the pair from the carrier density, the carrier velocity, the class's
+// Y and V (stencil fields 0, 1..3, 4, 5..7) and the carrier face fluxes: the expressions of tf_div
+// (I4 to the +1/2 face from offsets -1..2, to the -1/2 face from -2..1), with the lines of the six
+// fields along each axis read once and 16 I4 evaluated unscaled, the factors folded.
 template <typename T, typename RP, typename GT>
-__device__ __forceinline__ void tfr_div(const RP& R, const GT& G, int k, int r, T ih, T& DF, T (&DG)[3]) {
-  const ZView<T> rho = R.view(0, k, G, r), Y = R.view(4, k, G, r);
-  const ZView<T> u[3] = {R.view(1, k, G, r), R.view(2, k, G, r), R.view(3, k, G, r)};
-  const ZView<T> V[3] = {R.view(5, k, G, r), R.view(6, k, G, r), R.view(7, k, G, r)};
-  T php[3], phm[3];
-  R.faces(0, k, G, r, php, phm);
-  DF = T(0);
-  DG[0] = DG[1] = DG[2] = T(0);
+__device__ __forceinline__ void tfr_div(const RP& R, const GT& G, int k, T ih, T (&DF)[2], T (&DG)[3][2]) {
+  T php[3][2], phm[3][2];
+  R.faces2(0, k, G, php, phm);
+  T dg[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}}, df[2] = {T(0), T(0)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
+    const Line2<T> lr = ring_line(R, 0, k, G, d), ly = ring_line(R, 4, k, G, d), lu = ring_line(R, 1 + d, k, G, d);
+    const Line2<T> lv[3] = {ring_line(R, 5, k, G, d), ring_line(R, 6, k, G, d), ring_line(R, 7, k, G, d)};
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int o = side ? -1 : 0;  // plus face first, as in tf_div
-      const T sgn = side ? T(-1) : T(1);
-      const T slip = zI4(V[d], G, d, o) - zI4(u[d], G, d, o);
-      const T F = ((side ? phm[d] : php[d]) + zI4(rho, G, d, o) * slip) * zI4(Y, G, d, o);
-      DF += sgn * F;
+    for (int r = 0; r < 2; ++r) {
+      const T rc = pc<T>(R.zq[0][2], r), yc = pc<T>(R.zq[4][2], r), uc = pc<T>(R.zq[1 + d][2], r);
+      T vc[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) DG[m] += sgn * F * zI4(V[m], G, d, o);
+      for (int m = 0; m < 3; ++m) vc[m] = pc<T>(R.zq[5 + m][2], r);
+      const T sp = i4p16(lv[d], vc[d], r) - i4p16(lu, uc, r), sm = i4m16(lv[d], vc[d], r) - i4m16(lu, uc, r);
+      const T Fp = fma(i4p16(lr, rc, r) * T(1.0 / 256.0), sp, php[d][r]) * i4p16(ly, yc, r);
+      const T Fm = fma(i4m16(lr, rc, r) * T(1.0 / 256.0), sm, phm[d][r]) * i4m16(ly, yc, r);
+      df[r] += Fp - Fm;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) dg[m][r] += Fp * i4p16(lv[m], vc[m], r) - Fm * i4m16(lv[m], vc[m], r);
     }
   }
-  DF *= ih;
 #pragma unroll
-  for (int m = 0; m < 3; ++m) DG[m] *= ih;
+  for (int r = 0; r < 2; ++r) {
+    DF[r] = df[r] * (ih * T(0.0625));
+#pragma unroll
+    for (int m = 0; m < 3; ++m) DG[m][r] = dg[m][r] * (ih * T(1.0 / 256.0));
+  }
 }
 
 #define TF_RING_PROLOGUE(P)                              \
@@ -249,20 +254,20 @@ __global__ void __launch_bounds__(RNT) kr_tf_pred(const BoxDev* boxes, const int
     const P2<T> cr1 = R.cen(0, k, tid);
     const P2<T> cu1[3] = {R.cen(1, k, tid), R.cen(2, k, tid), R.cen(3, k, tid)};
     T oDF[2], oDG[3][2], oY[2], oV[3][2];
+    T DF[2], DG[3][2];
+    tfr_div<T>(R, G, k, ih, DF, DG);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      T DF, DG[3];
-      tfr_div<T>(R, G, k, r, ih, DF, DG);
-      const T rn = R.view(0, k, G, r).c(), ir1 = T(1) / pc<T>(cr1, r);
-      const T sig_n = rn * R.view(4, k, G, r).c();
-      const T sig = sig_n - dt * DF;
+      const T rn = pc<T>(R.zq[0][2], r), ir1 = T(1) / pc<T>(cr1, r);
+      const T sig_n = rn * pc<T>(R.zq[4][2], r);
+      const T sig = sig_n - dt * DF[r];
       const T isig = T(1) / sig;
-      oDF[r] = DF;
+      oDF[r] = DF[r];
       oY[r] = sig * ir1;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        oDG[m][r] = DG[m];
-        const T mom = sig_n * R.view(5 + m, k, G, r).c() - dt * DG[m];
+        oDG[m][r] = DG[m][r];
+        const T mom = sig_n * pc<T>(R.zq[5 + m][2], r) - dt * DG[m][r];
         const T um = pc<T>(cu1[m], r);
         oV[m][r] = um + (mom * isig - um) * rr;
       }
@@ -316,13 +321,13 @@ __global__ void __launch_bounds__(RNT) kr_tf_corr(const BoxDev* boxes, const int
     const P2<T> cgn[3] = {R.cen(3, k, tid), R.cen(4, k, tid), R.cen(5, k, tid)};
     const P2<T> cvn[3] = {R.cen(6, k, tid), R.cen(7, k, tid), R.cen(8, k, tid)};
     T oY[2], oV[3][2];
+    T DF[2], DG[3][2];
+    tfr_div<T>(R, G, k, ih, DF, DG);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      T DF, DG[3];
-      tfr_div<T>(R, G, k, r, ih, DF, DG);
-      const T rn = pc<T>(crn, r), r1 = R.view(0, k, G, r).c();
+      const T rn = pc<T>(crn, r), r1 = pc<T>(R.zq[0][2], r);
       const T sig_n = rn * pc<T>(cyn, r);
-      const T sig = sig_n - hdt * (pc<T>(cfn, r) + DF);
+      const T sig = sig_n - hdt * (pc<T>(cfn, r) + DF[r]);
       const T isig = T(1) / sig;
       const T Yk = sig / r1;
       oY[r] = Yk;
@@ -330,8 +335,8 @@ __global__ void __launch_bounds__(RNT) kr_tf_corr(const BoxDev* boxes, const int
       bool bad = !isfinite(Yk);
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const T mom = sig_n * pc<T>(cvn[m], r) - hdt * (pc<T>(cgn[m], r) + DG[m]);
-        const T um = R.view(1 + m, k, G, r).c();
+        const T mom = sig_n * pc<T>(cvn[m], r) - hdt * (pc<T>(cgn[m], r) + DG[m][r]);
+        const T um = pc<T>(R.zq[1 + m][2], r);
         const T Vm = um + (mom * isig - um) * rr;
         oV[m][r] = Vm;
         bad = bad || !isfinite(Vm);
