@@ -10,7 +10,8 @@ oracle, loaded into FP64 and mixed-precision contexts in the benchmark's
 launch configuration (autotuned tiles, CUDA-graph step), and one step of each
 is compared: FP64 within 1e-11 (relative L2 over the sampled cells and in
 every full-field norm) with the oracle's Krylov iteration counts; mixed
-precision within 1e-5.
+precision within 1e-5, with Jacobi-PCG and with the Neumann-polynomial CG
+(the benchmark's solver).
 """
 import json
 import os
@@ -45,13 +46,14 @@ def case():
     return g, st, want
 
 
-def _gpu_step(fe, g, st, precision):
+def _gpu_step(fe, g, st, precision, solver=None):
     P = g.PARAMS
     s = fe.Solver([dict(N=P["N"], nu=P["nu"], tau_p=P["tau_p"], Y0=P["Y0"], mach_rms=P["mach_rms"],
                         k0=P["k0"], seed=P["seed"])], precision=precision, p_tol=P["p_tol"],
-                  p_maxit=P["p_maxit"])
+                  p_maxit=P["p_maxit"], solver=fe.FE_PCG_JACOBI if solver is None else solver)
     s.autotune(2)
     s.load_state(0, st)
+    s.use_graphs(True)
     code, info = s.step(1)
     assert code == fe.FE_OK, fe.fe_strerror(code)
     out = s.get_state(0)
@@ -85,9 +87,11 @@ def test_fp64_full_size_matches_oracle(fe, case):
         assert abs(d[k] / want["diag"][k] - 1) < 1e-10, k
 
 
-def test_mixed_full_size_matches_oracle(fe, case):
+@pytest.mark.parametrize("solver", ["jacobi", "poly"])
+def test_mixed_full_size_matches_oracle(fe, case, solver):
     g, st, want = case
-    out, info, d = _gpu_step(fe, g, st, fe.FE_FP32_MIXED)
+    out, info, d = _gpu_step(fe, g, st, fe.FE_FP32_MIXED,
+                             fe.FE_PCG_POLY if solver == "poly" else fe.FE_PCG_JACOBI)
     assert max(info["rel_res"]) <= 1e-8 * (1 + 1e-3)
     assert abs(info["dt"] / want["dt"] - 1) < 1e-6
     _compare(g, out, want, 1e-5)
