@@ -70,10 +70,8 @@ extern "C" {
 #define FE_PCG_POLY         4   /* SPD operator (transonic = 0): CG with the      *
                                  * first-order Neumann polynomial preconditioner *
                                  * P = D^-1 (2 I - M D^-1) (Dubois, Greenbaum and *
-                                 * Rodrigue 1979) on the plane-streamed FP32      *
-                                 * iteration (mixed precision, every box's N a    *
-                                 * power of two in 64..512); FE_PCG_JACOBI        *
-                                 * wherever that iteration does not run          */
+                                 * Rodrigue 1979) in FP32 (mixed-precision)       *
+                                 * contexts; FP64 contexts run FE_PCG_JACOBI     */
 
 /* field ids for fe_set_field / fe_get_field */
 #define FE_RHO   0

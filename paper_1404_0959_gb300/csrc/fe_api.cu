@@ -143,7 +143,7 @@ struct fe_ctx {
     Launch l{dbox,           dwork,         nblocks,       dework, neblocks, dpart, dactive, st, &prof,
              prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
              nbblocks, bsmem};
-    l.poly = prm.solver == FE_PCG_POLY && l.bwork != nullptr;  // Jacobi where the planes are not streamed
+    l.poly = prm.solver == FE_PCG_POLY && !fp64;  // FP64 contexts run Jacobi-PCG
     return l;
   }
 };

@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(NTHR) kz_cg_matvec(const BoxDev* boxes, const 
 // pd_old and pd_new alternate between slots K_PD and K_PP with the parity of
 // the iteration counter (neighbouring tiles still read pd_old as halo).  At
 // iteration 0 alpha = beta = 0 (set by k_cg_init) and pd_new = D^{-1} b.
-template <typename T>
+// POLY: pd_new = z + beta pd_old with z = P r from kz_cg_rpoly (the first-order Neumann
+// polynomial preconditioner), z read in place of r and D^{-1}.
+template <typename T, bool POLY>
 __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_dirmatvec(const BoxDev* boxes, const int2* work, double* part) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
@@ -303,17 +305,22 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
   const int odd = ((int)B.sc[SC_ITERS]) & 1;
   const T* __restrict__ po = F<T>(B, odd ? K_PP : K_PD);
   T* __restrict__ pn = F<T>(B, odd ? K_PD : K_PP);
-  const T* __restrict__ r = F<T>(B, K_R);
+  const T* __restrict__ r = F<T>(B, POLY ? K_Z : K_R);  // POLY: z
   const T* __restrict__ dinv = F<T>(B, W_DINV);
   T* __restrict__ x = F<T>(B, K_X);
   T* __restrict__ q = F<T>(B, K_Q);
   const T alpha = (T)B.sc[SC_ALPHA], beta = (T)B.sc[SC_BETA];
   const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
   const T lapc = T(0.5) * dt * ih * ih;
-  // first iteration of a solve: pd_new = D^{-1} r and x = 0 whatever pd_old and x hold
+  // first iteration of a solve: pd_new = D^{-1} r (POLY: z) and x = 0 whatever pd_old and x hold
   const bool first = B.sc[SC_ITERS] == 0.0;
-  auto dir = [&](T rv, T dv, T pv) { return first ? rv * dv : rv * dv + beta * pv; };
+  auto dir = [&](T rv, T dv, T pv) {
+    if (POLY) return first ? rv : rv + beta * pv;
+    return first ? rv * dv : rv * dv + beta * pv;
+  };
   auto ld = [&](const T* f, int col, int k) { return __ldg(&f[col + G.plane(G.wrapz(k))]); };
+  // D^{-1} is not read in the polynomial form
+  auto ldd = [&](int col, int k) { return POLY ? T(1) : ld(dinv, col, k); };
   // centre column: r, dinv, pd_old for planes k + 1 .. k + KPF in flight
   T cr[KPF], cd[KPF], cp[KPF];
   // halo cell: r, dinv, pd_old for planes k .. k + KPF - 1
@@ -324,18 +331,18 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
 #pragma unroll
   for (int j = 0; j < KPF; ++j) {
     cr[j] = ld(r, G.col, t.k0 + 1 + j);
-    cd[j] = ld(dinv, G.col, t.k0 + 1 + j);
+    cd[j] = ldd(G.col, t.k0 + 1 + j);
     cp[j] = ld(po, G.col, t.k0 + 1 + j);
     if (G.hcol >= 0) {
       hr[j] = ld(r, G.hcol, t.k0 + j);
-      hd[j] = ld(dinv, G.hcol, t.k0 + j);
+      hd[j] = ldd(G.hcol, t.k0 + j);
       hp[j] = ld(po, G.hcol, t.k0 + j);
     }
   }
   // z-queue of pd_new at k - 1, k; pd_old at k (for the x update)
-  T zm = dir(ld(r, G.col, t.k0 - 1), ld(dinv, G.col, t.k0 - 1), ld(po, G.col, t.k0 - 1));
+  T zm = dir(ld(r, G.col, t.k0 - 1), ldd(G.col, t.k0 - 1), ld(po, G.col, t.k0 - 1));
   T oc = ld(po, G.col, t.k0);
-  T zc = dir(ld(r, G.col, t.k0), ld(dinv, G.col, t.k0), oc);
+  T zc = dir(ld(r, G.col, t.k0), ldd(G.col, t.k0), oc);
   DotAcc<T> a0;
   for (int k = t.k0; k < t.kend; ++k) {
     const T op = cp[0];
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
       cp[j] = cp[j + 1];
     }
     cr[KPF - 1] = ld(r, G.col, k + 1 + KPF);
-    cd[KPF - 1] = ld(dinv, G.col, k + 1 + KPF);
+    cd[KPF - 1] = ldd(G.col, k + 1 + KPF);
     cp[KPF - 1] = ld(po, G.col, k + 1 + KPF);
     const T ps = psi.next(G, k);
     const T xv = xs.next(G, k);
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
         hp[j] = hp[j + 1];
       }
       hr[KPF - 1] = ld(r, G.hcol, k + KPF);
-      hd[KPF - 1] = ld(dinv, G.hcol, k + KPF);
+      hd[KPF - 1] = ldd(G.hcol, k + KPF);
       hp[KPF - 1] = ld(po, G.hcol, k + KPF);
     }
     __syncthreads();
@@ -848,6 +855,106 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_rpoly(const BoxDev* boxes,
     if (tid == 0) {
       if (START) B.sc[SC_RZ] = res[0];
       else cg_update_scalars(B, res[0], res[1], active);
+    }
+  }
+}
+
+// kb_cg_rpoly in z-marching form (boxes whose planes are not streamed): r_new = r - alpha q and
+// w = D^{-1} r_new at the tile's cells and their one-cell x/y halo (staged per plane in shared memory,
+// z-neighbours of w in registers), z = D^{-1} (2 r_new - M w) at the own cells, <r_new, z>, ||r_new||^2
+// and the CG bookkeeping; r alternates between K_R and K_RB by the parity of the iteration count.
+// START: the first z of an inner solve (alpha = 0, r in K_R).
+template <typename T, bool START>
+__global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_rpoly(const BoxDev* boxes, const int2* work,
+                                                                                     double* part, int* active) {
+  const TileXYZ t = tile_xyz(boxes, work);
+  const BoxDev& B = boxes[t.box];
+  if (box_done(B)) return;
+  const ZGeom<1> G(t.x0, t.y0, B.N);
+  __shared__ T smb[kDmBuf][ZGeom<1>::H * ZGeom<1>::W];
+  const int odd = START ? 0 : ((int)B.sc[SC_ITERS]) & 1;
+  const T* __restrict__ ro = F<T>(B, odd ? K_RB : K_R);
+  T* __restrict__ rn = F<T>(B, odd ? K_R : K_RB);
+  const T* __restrict__ qv = F<T>(B, K_Q);
+  const T* __restrict__ dinv = F<T>(B, W_DINV);
+  T* __restrict__ z = F<T>(B, K_Z);
+  const T alpha = START ? T(0) : (T)B.sc[SC_ALPHA];
+  const T dt = (T)B.sc[SC_KDT], ih = (T)B.ih, idt = T(1) / dt;
+  const T lapc = T(0.5) * dt * ih * ih;
+  auto ld = [&](const T* f, int col, int k) { return __ldg(&f[col + G.plane(G.wrapz(k))]); };
+  auto ldq = [&](int col, int k) { return START ? T(0) : ld(qv, col, k); };
+  auto res = [&](T rv, T qq) { return START ? rv : rv - alpha * qq; };
+  // centre column: r, q, D^{-1} for planes k + 1 .. k + KPF in flight; halo cell: planes k .. k + KPF - 1
+  T cr[KPF], cq[KPF], cd[KPF], hr[KPF], hq[KPF], hd[KPF];
+  ZStream<T, KPF> psi;
+  psi.init(F<T>(B, W_PSI), G, t.k0);
+#pragma unroll
+  for (int j = 0; j < KPF; ++j) {
+    cr[j] = ld(ro, G.col, t.k0 + 1 + j);
+    cq[j] = ldq(G.col, t.k0 + 1 + j);
+    cd[j] = ld(dinv, G.col, t.k0 + 1 + j);
+    if (G.hcol >= 0) {
+      hr[j] = ld(ro, G.hcol, t.k0 + j);
+      hq[j] = ldq(G.hcol, t.k0 + j);
+      hd[j] = ld(dinv, G.hcol, t.k0 + j);
+    }
+  }
+  // z-queue of w at k - 1, k; r_new and D^{-1} at k
+  T wm = res(ld(ro, G.col, t.k0 - 1), ldq(G.col, t.k0 - 1)) * ld(dinv, G.col, t.k0 - 1);
+  T rc = res(ld(ro, G.col, t.k0), ldq(G.col, t.k0)), dc = ld(dinv, G.col, t.k0);
+  T wc = rc * dc;
+  DotAcc<T> a0, a1;
+  for (int k = t.k0; k < t.kend; ++k) {
+    const T r1 = res(cr[0], cq[0]), d1 = cd[0];
+    const T wp = r1 * d1;
+#pragma unroll
+    for (int j = 0; j + 1 < KPF; ++j) {
+      cr[j] = cr[j + 1];
+      cq[j] = cq[j + 1];
+      cd[j] = cd[j + 1];
+    }
+    cr[KPF - 1] = ld(ro, G.col, k + 1 + KPF);
+    cq[KPF - 1] = ldq(G.col, k + 1 + KPF);
+    cd[KPF - 1] = ld(dinv, G.col, k + 1 + KPF);
+    const T ps = psi.next(G, k);
+    T* sm = smb[kDmBuf == 2 ? (k & 1) : 0];
+    if (kDmBuf == 1) __syncthreads();
+    sm[G.csm] = wc;
+    if (G.hcol >= 0) {
+      sm[G.hsm] = res(hr[0], hq[0]) * hd[0];
+#pragma unroll
+      for (int j = 0; j + 1 < KPF; ++j) {
+        hr[j] = hr[j + 1];
+        hq[j] = hq[j + 1];
+        hd[j] = hd[j + 1];
+      }
+      hr[KPF - 1] = ld(ro, G.hcol, k + KPF);
+      hq[KPF - 1] = ldq(G.hcol, k + KPF);
+      hd[KPF - 1] = ld(dinv, G.hcol, k + KPF);
+    }
+    __syncthreads();
+    if (G.active) {
+      const int c = G.col + G.plane(k);
+      const T* s = sm + G.csm;
+      const T nb = (s[-1] + s[1]) + (s[-ZGeom<1>::W] + s[ZGeom<1>::W]) + (wm + wp);
+      const T mw = ps * wc * idt - lapc * (nb - T(6) * wc);
+      const T zv = dc * (T(2) * rc - mw);
+      z[c] = zv;
+      if (!START) rn[c] = rc;
+      a0.add(rc, zv);
+      a1.add(rc, rc);
+    }
+    wm = wc;
+    wc = wp;
+    rc = r1;
+    dc = d1;
+  }
+  Red<T> v[2] = {a0.red(), a1.red()};
+  __shared__ double sres[2];
+  if (block_sum_last<2>(v, B, part, sres, B.tile0, B.ntiles)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      if (START) B.sc[SC_RZ] = sres[0];
+      else cg_update_scalars(B, sres[0], sres[1], active);
     }
   }
 }
@@ -1750,25 +1857,33 @@ template <typename T> void launch_cg_update(const Launch& L) {
   FE_LAUNCH(L, KID_CG_UPDATE, (k_cg_update<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 template <typename T> void launch_cg_fused(const Launch& L) {
-  if (L.bwork && L.poly) {  // polynomial preconditioner: direction from z, residual update forms the next z
-    FE_LAUNCH(L, KID_CG_DIRMATVEC,
-              (kb_cg_dirmatvec<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
-    FE_LAUNCH(L, KID_CG_RUPDATE,
-              (kb_cg_rpoly<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+  if (L.poly) {  // polynomial preconditioner: direction from z, residual update forms the next z
+    if (L.bwork) {
+      FE_LAUNCH(L, KID_CG_DIRMATVEC,
+                (kb_cg_dirmatvec<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+      FE_LAUNCH(L, KID_CG_RUPDATE, (kb_cg_rpoly<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                       L.boxes, L.bwork, L.part, L.active)));
+    } else {
+      FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T, true><<<GRID>>>(L.boxes, L.work, L.part)));
+      FE_LAUNCH(L, KID_CG_RUPDATE, (kz_cg_rpoly<T, false><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
+    }
     return;
   }
   if (L.bwork)
     FE_LAUNCH(L, KID_CG_DIRMATVEC,
               (kb_cg_dirmatvec<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
   else
-    FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T><<<GRID>>>(L.boxes, L.work, L.part)));
+    FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T, false><<<GRID>>>(L.boxes, L.work, L.part)));
   FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
 }
 // First polynomial-preconditioned residual z = P r of an inner solve and <r, z> (nothing without it)
 template <typename T> void launch_cg_start(const Launch& L) {
-  if (L.bwork && L.poly)
+  if (!L.poly) return;
+  if (L.bwork)
     FE_LAUNCH(L, KID_CG_START,
               (kb_cg_rpoly<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+  else
+    FE_LAUNCH(L, KID_CG_START, (kz_cg_rpoly<T, true><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
 }
 template <typename T> void launch_cg_xfinal(const Launch& L) {
   FE_LAUNCH(L, KID_CG_XFINAL, (k_cg_xfinal<T><<<EGRID>>>(L.boxes, L.ework)));

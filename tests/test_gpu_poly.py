@@ -1,13 +1,14 @@
 """CG with the first-order Neumann polynomial preconditioner (solver
-FE_PCG_POLY) on the plane-streamed FP32 iteration, against the FP64 oracle
-(oracle/krylov.py: pcg with neumann1) and against the Jacobi solver.
+FE_PCG_POLY) in FP32 contexts, on the plane-streamed iteration (every N a
+power of two in 64..512) and on the z-marching one (any other N), against the
+FP64 oracle (oracle/krylov.py: pcg with neumann1) and against the Jacobi
+solver.
 
 The preconditioner changes the Krylov space, not the system: mixed-precision
 steps meet the reduced-precision bar (1e-5 relative L2 per field) against
 the oracle step, a standalone solve reaches the requested FP64-class
-residual, and the inner solves take fewer iterations than Jacobi's.  Where
-the planes are not streamed (N not a power of two in 64..512, FP64) the
-solver is plain Jacobi-PCG, bit for bit.
+residual, and the inner solves take fewer iterations than Jacobi's.  FP64
+contexts run plain Jacobi-PCG, bit for bit.
 """
 import numpy as np
 import pytest
@@ -124,13 +125,10 @@ def test_poly_graph_steps_equal_host_steps(fe):
         assert np.array_equal(v, fields(b)[k]), k
 
 
-@pytest.mark.parametrize("N,precision", [(48, "mixed"), (64, "fp64")])
-def test_poly_is_jacobi_where_planes_are_not_streamed(fe, N, precision):
-    prec = fe.FE_FP64 if precision == "fp64" else fe.FE_FP32_MIXED
+def test_poly_fp64_is_jacobi(fe):
     out = []
     for sid in (fe.FE_PCG_POLY, fe.FE_PCG_JACOBI):
-        s, _ = solver(fe, N, sid, precision=prec, seed=6)
-        assert not s.plane_streaming_active()
+        s, _ = solver(fe, 64, sid, precision=fe.FE_FP64, seed=6)
         code, info = s.step(2)
         assert code == fe.FE_OK, fe.fe_strerror(code)
         out.append((s.get_state(0), info[0]["iters"]))
@@ -141,17 +139,57 @@ def test_poly_is_jacobi_where_planes_are_not_streamed(fe, N, precision):
         assert np.array_equal(v, fields(b)[k]), k
 
 
-def test_poly_streaming_off_is_jacobi(fe):
+# N = 48: rings, z-marching CG; N = 30: not a multiple of four cells, z-marching kernels everywhere
+@pytest.mark.parametrize("N", [48, 30])
+def test_poly_zmarched_matches_oracle_in_fewer_iterations(fe, N):
+    s, (rho, u, Y) = solver(fe, N, fe.FE_PCG_POLY, seed=6)
+    assert not s.plane_streaming_active()
+    code, ginf = s.step(1)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    got = s.get_state(0)
+    s.close()
+    prm = piso.Params(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01], p_tol=1e-10)
+    ref, _ = piso.step(prm, piso.make_state(prm, rho, u, Y))
+    assert worst(got, ref) <= 1e-5
+    assert max(ginf[0]["rel_res"]) <= 1e-8 * (1 + 1e-3)
+    j, _ = solver(fe, N, fe.FE_PCG_JACOBI, seed=6)
+    code, jinf = j.step(1)
+    assert code == fe.FE_OK
+    j.close()
+    assert sum(ginf[0]["iters"]) < sum(jinf[0]["iters"]), (ginf[0]["iters"], jinf[0]["iters"])
+
+
+def test_poly_streamed_matches_zmarched(fe):
     out = []
-    for sid in (fe.FE_PCG_POLY, fe.FE_PCG_JACOBI):
-        s, _ = solver(fe, 64, sid, seed=7)
-        s.use_plane_streaming(False)
-        code, info = s.step(1)
-        assert code == fe.FE_OK
+    for streaming in (True, False):
+        s, _ = solver(fe, 64, fe.FE_PCG_POLY, seed=7)
+        s.use_plane_streaming(streaming)
+        assert s.plane_streaming_active() == streaming
+        code, info = s.step(2)
+        assert code == fe.FE_OK, fe.fe_strerror(code)
         out.append((s.get_state(0), info[0]["iters"]))
         s.close()
-    assert out[0][1] == out[1][1]
-    assert np.array_equal(out[0][0]["p"], out[1][0]["p"])
+    (a, ia), (b, ib) = out
+    assert worst(a, b) <= 1e-5
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib)), (ia, ib)
+
+
+def test_poly_uneven_ensemble_matches_single_boxes(fe):
+    boxes = [dict(N=32, nu=0.005, tau_p=[0.05], Y0=[0.01], seed=3),
+             dict(N=48, nu=0.004, tau_p=[0.2], Y0=[0.01], seed=4, mach_rms=0.5)]
+    ens = fe.Solver(boxes, precision=fe.FE_FP32_MIXED, p_tol=1e-8, solver=fe.FE_PCG_POLY)
+    ens.init_state(-1, fe.FE_INIT_SPECTRAL)
+    ens.use_graphs(True)
+    code, _ = ens.step(2)
+    assert code == fe.FE_OK, fe.fe_strerror(code)
+    for b, box in enumerate(boxes):
+        one = fe.Solver([box], precision=fe.FE_FP32_MIXED, p_tol=1e-8, solver=fe.FE_PCG_POLY)
+        one.init_state(0, fe.FE_INIT_SPECTRAL)
+        code, _ = one.step(2)
+        assert code == fe.FE_OK
+        assert worst(ens.get_state(b), one.get_state(0)) <= 1e-5
+        one.close()
+    ens.close()
 
 
 def test_poly_ensemble_matches_single_boxes(fe):
