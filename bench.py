@@ -36,10 +36,11 @@ UNIT = "cell-steps/s"
 # the right-hand side also writes the first inner right-hand side and reads
 # D^{-1} (it starts the refined solve); the corrector reads neither psi nor b.
 def alg_words(kernel, nd, mixed=False, poly=False):
-    if poly and kernel in ("cg_dirmatvec", "cg_rupdate", "cg_start"):
+    if poly and kernel in ("cg_dirmatvec", "cg_rupdate", "cg_start", "rhs", "refine"):
         # Neumann-polynomial CG: z, pd_old, psi, x read, q, pd_new, x written | r, q, D^-1, psi read, z and r
-        # written | r, D^-1, psi read, z written
-        return {"cg_dirmatvec": 7, "cg_rupdate": 6, "cg_start": 4}[kernel]
+        # written | r, D^-1, psi read, z written; the right-hand side and the refinement boundary do not
+        # read D^-1 (the solve's first z has its own pass)
+        return {"cg_dirmatvec": 7, "cg_rupdate": 6, "cg_start": 4, "rhs": 12, "refine": 10}[kernel]
     table = {
         "dt": 3, "div": 4, "pred": 21, "fluxn": 7 + 2 * nd, "asm": 18, "rhs": 13 if mixed else 11,
         "cg_init": 5, "cg_matvec": 3, "cg_update": 7, "cg_dir": 4,

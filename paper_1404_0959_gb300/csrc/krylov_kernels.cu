@@ -1538,10 +1538,12 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
 // kz_refine on column pairs: 16 x 8 threads per 32 x 8 tile, each thread the
 // cells (x, x+1) of its column pair (N even), pair loads and stores; the
 // inner x-neighbours come from registers, the outer ones and the y-neighbours
-// from the staged plane of updated pairs.
+// from the staged plane of updated pairs.  poly: the next inner solve starts
+// with the polynomial preconditioner's own pass (kb/kz_cg_rpoly<T, true>), so
+// D^{-1} is not read and <r, D^{-1} r> not formed.
 template <typename T>
 __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2* work, double* part,
-                                                 int* outer_active, int* active) {
+                                                 int* outer_active, int* active, int poly) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   if (B.sc[SC_ODONE] != 0.0) return;
@@ -1617,7 +1619,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
     const int q = col + plane(t.k0 + j);
     nb_[j] = ldp(borig + q);
     np_[j] = ldp(psi + q);
-    nd_[j] = ldp(dinv + q);
+    if (!poly) nd_[j] = ldp(dinv + q);
   }
   DotAcc<float> arr, arz;
   for (int k = t.k0; k < t.kend; ++k) {
@@ -1640,7 +1642,7 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
       const int q = col + plane(k + KPF);
       nb_[KPF - 1] = ldp(borig + q);
       np_[KPF - 1] = ldp(psi + q);
-      nd_[KPF - 1] = ldp(dinv + q);
+      if (!poly) nd_[KPF - 1] = ldp(dinv + q);
     }
     __syncthreads();
     sm[csm] = zc[0];
@@ -1663,8 +1665,10 @@ __global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2
     stp(r + c, (T)r0, (T)r1);
     arr.add(r0, r0);
     arr.add(r1, r1);
-    arz.add(r0, (float)((T)r0 * dc.x));
-    arz.add(r1, (float)((T)r1 * dc.y));
+    if (!poly) {
+      arz.add(r0, (float)((T)r0 * dc.x));
+      arz.add(r1, (float)((T)r1 * dc.y));
+    }
   }
   DF v[2] = {arr.red(), arz.red()};
   __shared__ double res[2];
@@ -1931,7 +1935,8 @@ template <typename T> void launch_refine_start(const Launch& L, int* outer_activ
 template <typename T> void launch_refine(const Launch& L, int* outer_active) {
   if (L.ring_ok)  // every box's N a multiple of the 16-byte chunk, so even: column pairs
     FE_LAUNCH(L, KID_REFINE,
-              (kp_refine<T><<<L.nblocks, dim3(RTX, TY), 0, L.st>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+              (kp_refine<T><<<L.nblocks, dim3(RTX, TY), 0, L.st>>>(L.boxes, L.work, L.part, outer_active, L.active,
+                                                                     L.poly)));
   else
     FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
   launch_cg_start<T>(L);

@@ -669,7 +669,7 @@ template <typename T>
 using RhsPlan = RingPlan<T, kA, 5, 0, 3>;  // rho', HbyA0..2, p | | rho^n, D phi^n [, D^{-1}]
 template <typename T>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
-                                                            int pp, double* part, int* rstart, int* active) {
+                                                            int pp, double* part, int* rstart, int* active, int poly) {
   RING_PROLOGUE(RhsPlan<T>);
   R.gs[0] = Fr<T>(B, rhop);
 #pragma unroll
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
   R.gc[1] = Fr<T>(B, W_DIVPHI);
   R.gc[2] = Fr<T>(B, W_DINV);
   const bool start = rstart != nullptr;
-  if (!start) R.ncf = 2;
+  if (!start || poly) R.ncf = 2;  // D^{-1} only for <b, D^{-1} b> of a Jacobi start
   T* __restrict__ ps[3] = {Fr<T>(B, W_PS0), Fr<T>(B, W_PS1), Fr<T>(B, W_PS2)};
   T* __restrict__ b = Fr<T>(B, start ? K_AUX : K_B);
   T* __restrict__ r0 = Fr<T>(B, K_R);
@@ -716,12 +716,12 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes,
     for (int d = 0; d < 3; ++d) stp(ps[d] + c, ops[d][0], ops[d][1]);
     stp(b + c, ob[0], ob[1]);
     if (start) {
-      const P2<T> cd = R.cen(2, k, tid);
+      const P2<T> cd = poly ? P2<T>{} : R.cen(2, k, tid);
       stp(r0 + c, ob[0], ob[1]);
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         abb.add(ob[r], ob[r]);
-        abz.add(ob[r], ob[r] * pc<T>(cd, r));
+        if (!poly) abz.add(ob[r], ob[r] * pc<T>(cd, r));
       }
     }
   }
@@ -833,7 +833,8 @@ template <typename T>
 int rlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (!L.ring_ok || !ring_ready<T>(RK_RHS)) return 0;
   FE_LAUNCH(L, KID_RHS,
-            (kr_rhs<T><<<RGRID(RhsPlan<T>::bytes)>>>(L.boxes, L.work, s, rhop, pp, L.part, L.rstart, L.active)));
+            (kr_rhs<T><<<RGRID(RhsPlan<T>::bytes)>>>(L.boxes, L.work, s, rhop, pp, L.part, L.rstart, L.active,
+                                                     L.poly)));
   return 1;
 }
 
