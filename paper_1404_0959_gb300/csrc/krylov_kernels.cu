@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_rpoly(const BoxDev* boxes,
           const T ze = sv_d[u].v[e] * (T(2) * sv_r[u].v[e] - mw);
           zv.v[e] = ze;
           a0.add(sv_r[u].v[e], ze);
-          a1.add(sv_r[u].v[e], sv_r[u].v[e]);
+          if (!START) a1.add(sv_r[u].v[e], sv_r[u].v[e]);  // START: the boundary measured ||r||
         }
         st4(z + gbase, zv);
         if (!START) st4(rn + gbase, sv_r[u]);
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_r
       z[c] = zv;
       if (!START) rn[c] = rc;
       a0.add(rc, zv);
-      a1.add(rc, rc);
+      if (!START) a1.add(rc, rc);  // START: the boundary measured ||r||
     }
     wm = wc;
     wc = wp;
