@@ -1463,7 +1463,7 @@ __device__ __forceinline__ float refine_residual(float2 zc, float2 n0, float2 n1
 
 template <typename T>
 __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int2* work, double* part,
-                                                  int* outer_active, int* active) {
+                                                  int* outer_active, int* active, int poly) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
   if (B.sc[SC_ODONE] != 0.0) return;
@@ -1523,7 +1523,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
                                      idt, kl);
     r[c] = (T)rv;
     arr.add(rv, rv);
-    arz.add(rv, (float)((T)rv * dc));
+    if (!poly) arz.add(rv, (float)((T)rv * dc));  // poly: the next solve's start pass forms <r, z>
   }
   DF v[2] = {arr.red(), arz.red()};
   __shared__ double res[2];
@@ -1938,7 +1938,7 @@ template <typename T> void launch_refine(const Launch& L, int* outer_active) {
               (kp_refine<T><<<L.nblocks, dim3(RTX, TY), 0, L.st>>>(L.boxes, L.work, L.part, outer_active, L.active,
                                                                      L.poly)));
   else
-    FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active)));
+    FE_LAUNCH(L, KID_REFINE, (kz_refine<T><<<GRID>>>(L.boxes, L.work, L.part, outer_active, L.active, L.poly)));
   launch_cg_start<T>(L);
 }
 template <typename T> void launch_mix_finish_pp(const Launch& L) {
