@@ -495,7 +495,8 @@ def part_only(args):
     elif args.part == "fourier":
         # the Fourier-closure workloads: 128^3 (one class) and 512^3 (three classes), FP32 fields
         res = {}
-        for name, n_ in (("hit128f", 128), ("hit512f", 512)):
+        for name, n_ in [(w_, n_) for w_, n_ in (("hit128f", 128), ("hit512f", 512))
+                         if str(n_) in args.fourier_sizes.split(",")]:
             w = WORKLOADS[name]
             bx_ = dict(N=n_, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], mach_rms=w["mach_rms"], k0=w["k0"], seed=0)
             s = fe.Solver([bx_], precision=fe.FE_FP32_MIXED, closure=w["closure"], p_tol=w["p_tol"], p_maxit=1000,
@@ -626,6 +627,7 @@ def main():
                     help="time one further row alone: a-priori LES, two-fluid dust step, two-way coupled step, "
                          "Fourier-closure workloads, Q iso-surface + raster")
     ap.add_argument("--width", type=int, default=2048, help="depth image width for --part iso")
+    ap.add_argument("--fourier-sizes", default="128,512", help="box sizes of --part fourier (128, 512)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.unet:
