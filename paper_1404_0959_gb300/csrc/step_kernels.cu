@@ -477,7 +477,8 @@ template <typename T> void launch_pred(const Launch& L, int s, int k) { zlaunch_
 // Fourier closure: the energy face fluxes of a level (k_fe_cell, then k_fe_face)
 template <typename T> static void launch_fe_faces(const Launch& L, int s, int u0, int rhos, int ps, int es, int tmode,
                                                   int phi0) {
-  FE_LAUNCH(L, KID_FE_CELL, (k_fe_cell<T><<<GRID>>>(L.boxes, L.work, s, u0, rhos, ps, es, tmode)));
+  if (!rlaunch_fe_cell<T>(L, s, u0, rhos, ps, es, tmode))
+    FE_LAUNCH(L, KID_FE_CELL, (k_fe_cell<T><<<GRID>>>(L.boxes, L.work, s, u0, rhos, ps, es, tmode)));
   FE_LAUNCH(L, KID_FE_FACE, (k_fe_face<T><<<GRID>>>(L.boxes, L.work, u0, phi0)));
 }
 template <typename T> void launch_fluxn(const Launch& L, int s) {

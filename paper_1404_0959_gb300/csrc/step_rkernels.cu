@@ -44,7 +44,8 @@ __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
 constexpr int kMaxDev = 64;
 // per device, one bit per ring kernel (set when its shared-memory limit was accepted)
 enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
-                  RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW, RK_DUST1F, RK_DUST2F, RK_DUST3F };
+                  RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW, RK_DUST1F, RK_DUST2F, RK_DUST3F,
+                  RK_FECELL };
 template <typename T>
 struct RingReady {
   static unsigned ok[kMaxDev];
@@ -623,6 +624,63 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_dust(const BoxDev* boxes
   }
 }
 
+// ---- Fourier closure: per cell H = E + p/rho, T and the nine Gauss gradients h Gc_m u_l ------------------
+// (the fields the energy face fluxes k_fe_face read; k_fe_cell's expressions).  es >= 0: E from slot es
+// (tmode 1); es < 0: the level-n energy E^n = c_v T^n + |u^n|^2 / 2 from T^n and u^n, also stored in W_EN.
+// tmode 0: T = T^n, 1: T = p / (rho R).  The gradients from line loads of u_l along m, both cells.
+template <typename T>
+using FeCellPlan = RingPlan<T, kA, 3, 0, 6>;  // u0..2 | | rho, p, E or T^n, u^n_0..2
+template <typename T>
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fe_cell(const BoxDev* boxes, const int2* work, int s, int u0,
+                                                                int rhos, int ps, int es, int tmode) {
+  RING_PROLOGUE(FeCellPlan<T>);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[m] = Fr<T>(B, u0 + m);
+  R.gc[0] = Fr<T>(B, rhos);
+  R.gc[1] = Fr<T>(B, ps);
+  R.gc[2] = Fr<T>(B, es >= 0 ? es : S(s, F_T));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gc[3 + m] = Fr<T>(B, S(s, F_U0 + m));
+  R.ncf = es >= 0 ? 3 : 6;  // u^n only for E^n
+  T* __restrict__ Hc = Fr<T>(B, W_FEH);
+  T* __restrict__ Tc = Fr<T>(B, W_FET);
+  T* __restrict__ En = Fr<T>(B, W_EN);
+  const T cv = (T)B.cv, Rg = (T)B.R;
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+    const P2<T> crho = R.cen(0, k, tid), cp = R.cen(1, k, tid), cx = R.cen(2, k, tid);
+    T oh[2], ot[2], oe[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const T rc = pc<T>(crho, r), p = pc<T>(cp, r), x = pc<T>(cx, r);
+      T e = x;
+      if (es < 0) {
+        const T a = pc<T>(R.cen(3, k, tid), r), b = pc<T>(R.cen(4, k, tid), r), d = pc<T>(R.cen(5, k, tid), r);
+        e = cv * x + T(0.5) * (a * a + b * b + d * d);
+        oe[r] = e;
+      }
+      oh[r] = e + p / rc;
+      ot[r] = tmode ? p / (rc * Rg) : x;
+    }
+    stp(Hc + c, oh[0], oh[1]);
+    stp(Tc + c, ot[0], ot[1]);
+    if (es < 0) stp(En + c, oe[0], oe[1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const Line2<T> ln = ring_line(R, l, k, G, m);
+        stp(Fr<T>(B, W_FEG0 + 3 * m + l) + c, gc16(ln, 0) * T(0.0625), gc16(ln, 1) * T(0.0625));
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // ---- velocity divergence div = sum_m Gc_m(u_m) --------------------------------------------------------
 template <typename T>
 using DivPlan = RingPlan<T, kA, 3, 0, 0>;  // u0..2
@@ -830,6 +888,13 @@ int rlaunch_div(const Launch& L, int u0, int with_dt) {
   return 1;
 }
 template <typename T>
+int rlaunch_fe_cell(const Launch& L, int s, int u0, int rhos, int ps, int es, int tmode) {
+  if (!L.ring_ok || !ring_ready<T>(RK_FECELL)) return 0;
+  FE_LAUNCH(L, KID_FE_CELL, (kr_fe_cell<T><<<RGRID(FeCellPlan<T>::bytes)>>>(L.boxes, L.work, s, u0, rhos, ps, es,
+                                                                             tmode)));
+  return 1;
+}
+template <typename T>
 int rlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (!L.ring_ok || !ring_ready<T>(RK_RHS)) return 0;
   FE_LAUNCH(L, KID_RHS,
@@ -863,6 +928,7 @@ int rprepare() {
   set(RK_DUST3F, set_smem(kr_dust<T, 3, true>, DustPlan<T, 3, true>::bytes));
   set(RK_DIV, set_smem(kr_div<T>, DivPlan<T>::bytes));
   set(RK_RHS, set_smem(kr_rhs<T>, RhsPlan<T>::bytes));
+  set(RK_FECELL, set_smem(kr_fe_cell<T>, FeCellPlan<T>::bytes));
   cudaGetLastError();  // a refused limit is not an error of the context
   ok &= ~(unsigned)(FE_RING_OFF);
   RingReady<T>::ok[dev] = ok;
@@ -879,6 +945,7 @@ int rprepare() {
   template int rlaunch_dust_fourier<T>(const Launch&, int, int, int, int, int, int, int); \
   template int rlaunch_div<T>(const Launch&, int, int);                           \
   template int rlaunch_rhs<T>(const Launch&, int, int, int);                      \
+  template int rlaunch_fe_cell<T>(const Launch&, int, int, int, int, int, int);   \
   template int rprepare<T>();
 RINST(double)
 RINST(float)
