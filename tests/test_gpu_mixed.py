@@ -103,15 +103,17 @@ def test_mixed_fourier_three_classes(fe):
     s.close()
 
 
-def test_mixed_histories_20_steps(fe):
-    """KE and enstrophy histories of the hit32 physics within 1e-3 over 20 steps."""
+@pytest.mark.parametrize("N,solver", [(32, "jacobi"), (32, "poly"), (64, "poly")])
+def test_mixed_histories_20_steps(fe, N, solver):
+    """KE and enstrophy histories of the hit32 physics within 1e-3 over 20 steps, with Jacobi-PCG and
+    with the Neumann-polynomial CG (z-marched at 32^3, plane-streamed at 64^3)."""
     w = WORKLOADS["hit32"]
-    N = w["N"]
     from oracle import ic as oic
     u0 = [f32(c) for c in oic.spectral_velocity(N, w["k0"], w["mach_rms"], 0)]
     ones = np.ones((N, N, N))
     prm = piso.Params(N=N, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"], p_tol=1e-8)
-    s = fe.Solver([dict(N=N, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"])], precision=fe.FE_FP32_MIXED, p_tol=1e-8)
+    s = fe.Solver([dict(N=N, nu=w["nu"], tau_p=w["tau_p"], Y0=w["Y0"])], precision=fe.FE_FP32_MIXED, p_tol=1e-8,
+                  solver=fe.FE_PCG_POLY if solver == "poly" else fe.FE_PCG_JACOBI)
     st = f32_state(piso.make_state(prm, ones, u0, [f32(0.01 * ones)]))
     s.load_state(0, st)
     h = 2 * math.pi / N
