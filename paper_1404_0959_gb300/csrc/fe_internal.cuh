@@ -655,6 +655,7 @@ template <typename V> int rlaunch_dust_fourier(const Launch& L, int s, int kset,
                                                int nd);
 template <typename V> int rlaunch_div(const Launch& L, int u0, int with_dt = 0);
 template <typename V> int rlaunch_fe_cell(const Launch& L, int s, int u0, int rhos, int ps, int es, int tmode);
+template <typename V> int rlaunch_fe_face(const Launch& L, int u0, int phi0);
 template <typename V> int rlaunch_rhs(const Launch& L, int s, int rhop, int pp);
 template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
 template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);

@@ -479,7 +479,7 @@ template <typename T> static void launch_fe_faces(const Launch& L, int s, int u0
                                                   int phi0) {
   if (!rlaunch_fe_cell<T>(L, s, u0, rhos, ps, es, tmode))
     FE_LAUNCH(L, KID_FE_CELL, (k_fe_cell<T><<<GRID>>>(L.boxes, L.work, s, u0, rhos, ps, es, tmode)));
-  FE_LAUNCH(L, KID_FE_FACE, (k_fe_face<T><<<GRID>>>(L.boxes, L.work, u0, phi0)));
+  if (!rlaunch_fe_face<T>(L, u0, phi0)) FE_LAUNCH(L, KID_FE_FACE, (k_fe_face<T><<<GRID>>>(L.boxes, L.work, u0, phi0)));
 }
 template <typename T> void launch_fluxn(const Launch& L, int s) {
   if (!L.fourier && L.nd >= 1 && L.nd <= 3) {

@@ -45,7 +45,7 @@ constexpr int kMaxDev = 64;
 // per device, one bit per ring kernel (set when its shared-memory limit was accepted)
 enum RingKernel { RK_CORR_M, RK_CORR_F, RK_PRED, RK_ASM, RK_ACCEL, RK_FLUX1, RK_FLUX2, RK_FLUX3, RK_DUST1, RK_DUST2,
                   RK_DUST3, RK_DIV, RK_RHS, RK_PRED_TW, RK_ASM_TW, RK_ACCEL_TW, RK_DUST1F, RK_DUST2F, RK_DUST3F,
-                  RK_FECELL };
+                  RK_FECELL, RK_FEFACE };
 template <typename T>
 struct RingReady {
   static unsigned ok[kMaxDev];
@@ -681,6 +681,86 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fe_cell(const BoxDev* bo
   cp_async_wait<0>();
 }
 
+// The three +1/2 face fluxes F_E = phi I4(H) - sum_m tau_dm I4(u_m) - kappa G4(T) of every cell
+// (k_fe_face's expressions): lines of H, T, u0..2 and div along each axis from the ring, the gradient
+// fields h Gc_m u_d (needed only along d, at offsets -1..2) by pair loads through the read-only path.
+template <typename T>
+using FeFacePlan = RingPlan<T, kA1, 6, 0, 3>;  // H, T, u0..2, div | | phi0..2
+template <typename T>
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fe_face(const BoxDev* boxes, const int2* work, int u0, int phi0) {
+  RING_PROLOGUE(FeFacePlan<T>);
+  R.gs[0] = Fr<T>(B, W_FEH);
+  R.gs[1] = Fr<T>(B, W_FET);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R.gs[2 + m] = Fr<T>(B, u0 + m);
+  R.gs[5] = Fr<T>(B, W_DIV);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.gc[d] = Fr<T>(B, phi0 + d);
+  const T ih = (T)B.ih, mu = (T)B.mu, kappa = (T)B.kappa;
+  const int N = B.N, NN = N * N;
+  // own pair (x, x+1) and its neighbours for the gradient loads (N even: pairs never straddle the seam)
+  const int xg = RGeom<T>::wrap(t.x0 + 2 * threadIdx.x, N), yg = RGeom<T>::wrap(t.y0 + threadIdx.y, N);
+  const int xl = xg == 0 ? N - 2 : xg - 2, xr = xg + 2 == N ? 0 : xg + 2;
+  int yrow[4];  // rows y-1 .. y+2
+#pragma unroll
+  for (int q = 0; q < 4; ++q) yrow[q] = RGeom<T>::wrap(yg + q - 1, N) * N;
+  R.prologue(G);
+  for (int i = 0; i < t.kend - t.k0; ++i) {
+    const int k = t.k0 + i;
+    R.next(G, i);
+    if (!G.active) continue;
+    const int c = G.col + G.plane(k);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {  // unrolled: the axis selects the line loads at compile time
+      const Line2<T> lh = ring_line(R, 0, k, G, d), lt = ring_line(R, 1, k, G, d);
+      const P2<T> hc = R.zq[0][2], tc = R.zq[1][2];
+      const P2<T> ph = R.cen(d, k, tid);
+      T work[2] = {T(0), T(0)}, of[2];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const Line2<T> lu = ring_line(R, 2 + m, k, G, d);
+        const P2<T> uc = R.zq[2 + m][2];
+        // g = h Gc_m u_d at offsets -1..2 along d of both cells
+        const T* g = Fr<T>(B, W_FEG0 + 3 * m + d);
+        T gv[2][4];
+        if (d == 0) {
+          const int row = yrow[1] + k * NN;
+          const P2<T> a = ldg2(g + row + xl), b = ldg2(g + row + xg), e = ldg2(g + row + xr);
+          gv[0][0] = a.y, gv[0][1] = b.x, gv[0][2] = b.y, gv[0][3] = e.x;
+          gv[1][0] = b.x, gv[1][1] = b.y, gv[1][2] = e.x, gv[1][3] = e.y;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int o = d == 1 ? yrow[q] + k * NN : yrow[1] + G.wrapz(k + q - 1) * NN;
+            const P2<T> v = ldg2(g + o + xg);
+            gv[0][q] = v.x, gv[1][q] = v.y;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const T u = pc<T>(uc, r);
+          const T ig = (T(9) * (gv[r][1] + gv[r][2]) - (gv[r][0] + gv[r][3])) * T(0.0625);
+          const T g4u = (T(27) * (lu.p1[r] - u) - (lu.p2[r] - lu.m1[r])) * T(1.0 / 24.0);
+          T tau = (g4u + ig) * ih;
+          if (d == m) {
+            const Line2<T> ld = ring_line(R, 5, k, G, d);
+            tau -= T(2.0 / 3.0) * (i4p16(ld, pc<T>(R.zq[5][2], r), r) * T(0.0625));
+          }
+          work[r] += (mu * tau) * (i4p16(lu, u, r) * T(0.0625));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T IH = i4p16(lh, pc<T>(hc, r), r) * T(0.0625);
+        const T G4T = (T(27) * (lt.p1[r] - pc<T>(tc, r)) - (lt.p2[r] - lt.m1[r])) * T(1.0 / 24.0) * ih;
+        of[r] = pc<T>(ph, r) * IH - work[r] - kappa * G4T;
+      }
+      stp(Fr<T>(B, W_FEF0 + d) + c, of[0], of[1]);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // ---- velocity divergence div = sum_m Gc_m(u_m) --------------------------------------------------------
 template <typename T>
 using DivPlan = RingPlan<T, kA, 3, 0, 0>;  // u0..2
@@ -895,6 +975,12 @@ int rlaunch_fe_cell(const Launch& L, int s, int u0, int rhos, int ps, int es, in
   return 1;
 }
 template <typename T>
+int rlaunch_fe_face(const Launch& L, int u0, int phi0) {
+  if (!L.ring_ok || !ring_ready<T>(RK_FEFACE)) return 0;
+  FE_LAUNCH(L, KID_FE_FACE, (kr_fe_face<T><<<RGRID(FeFacePlan<T>::bytes)>>>(L.boxes, L.work, u0, phi0)));
+  return 1;
+}
+template <typename T>
 int rlaunch_rhs(const Launch& L, int s, int rhop, int pp) {
   if (!L.ring_ok || !ring_ready<T>(RK_RHS)) return 0;
   FE_LAUNCH(L, KID_RHS,
@@ -929,6 +1015,7 @@ int rprepare() {
   set(RK_DIV, set_smem(kr_div<T>, DivPlan<T>::bytes));
   set(RK_RHS, set_smem(kr_rhs<T>, RhsPlan<T>::bytes));
   set(RK_FECELL, set_smem(kr_fe_cell<T>, FeCellPlan<T>::bytes));
+  set(RK_FEFACE, set_smem(kr_fe_face<T>, FeFacePlan<T>::bytes));
   cudaGetLastError();  // a refused limit is not an error of the context
   ok &= ~(unsigned)(FE_RING_OFF);
   RingReady<T>::ok[dev] = ok;
@@ -946,6 +1033,7 @@ int rprepare() {
   template int rlaunch_div<T>(const Launch&, int, int);                           \
   template int rlaunch_rhs<T>(const Launch&, int, int, int);                      \
   template int rlaunch_fe_cell<T>(const Launch&, int, int, int, int, int, int);   \
+  template int rlaunch_fe_face<T>(const Launch&, int, int);                       \
   template int rprepare<T>();
 RINST(double)
 RINST(float)

@@ -65,6 +65,11 @@ template <typename T>
 __device__ __forceinline__ P2<T> ldp(const T* p) {
   return *reinterpret_cast<const P2<T>*>(p);
 }
+// the same from global memory through the read-only path
+template <typename T>
+__device__ __forceinline__ P2<T> ldg2(const T* p) {
+  return __ldg(reinterpret_cast<const P2<T>*>(p));
+}
 template <typename T>
 __device__ __forceinline__ void stp(T* p, T a, T b) {
   P2<T> v;
