@@ -111,30 +111,61 @@ def job_rate(cells_per_rank, steps, world, t):
 
 
 class Clocks:
-    """nvidia-smi sampler (200 ms) running during the timed region."""
+    """nvidia-smi sampler (every 25 ms) running across the timed region.
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Each sample carries nvidia-smi's own timestamp; ``begin()`` and ``end()``
+    mark the timed region on the same wall clock, and only the samples taken
+    between the two marks are summarised (the sampler is already producing
+    samples when ``start()`` returns, so a short region still gets some)."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 25
 
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 5.0  # until the first samples are on disk
+        while time.time() < deadline and self.proc.poll() is None:
+            with open(self.path) as f:
+                if sum(1 for _ in f) >= 2:
+                    break
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        from datetime import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(2.0 * self.PERIOD_MS / 1e3)  # the sample that closes the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -143,17 +174,23 @@ class Clocks:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            stamped = [(self._stamp(r[0]), r) for r in rows]
+            inside = [r for ts, r in stamped if ts is not None and self.t0 <= ts <= self.t1]
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = [float(r[2]) for r in inside if num(r[2])]
+        mx = [float(r[3]) for r in rows if num(r[3])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "period_ms": self.PERIOD_MS,
+                "region_s": (self.t1 - self.t0) if self.t0 is not None and self.t1 is not None else None}
 
 
 def oracle_sample(N, steps, cfg):
@@ -734,10 +771,12 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
+    clocks.begin()
     ev0.record(stream)
     code, info = s.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier()
     ck = clocks.stop()
     assert code == fe.FE_OK, fe.fe_strerror(code)

@@ -466,19 +466,22 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* bo
     const size_t pl = (size_t)P.m * NN;
     const bool comp = P.pos >= 1 && P.pos <= P.len;
     const unsigned row = (unsigned)(N * sizeof(T)), rows = (unsigned)(RN * sizeof(T));
-    mbar_expect_tx(bj, NHS * (rows + 2 * row) + (comp ? 2 * rows : 0));
+    // the first iteration of a solve reads neither pd_old (the last halo stream) nor x
+    const int nh = first ? NHS - 1 : NHS;
+    mbar_expect_tx(bj, nh * (rows + 2 * row) + (comp ? (first ? 1 : 2) * rows : 0));
     const T* src[3] = {r, POLY ? po : dinv, po};
     // rows ym .. ym + R + 1 of each stream: one copy, two where they wrap in y
     const int n0 = min(R + 2, N - ym);
 #pragma unroll
     for (int f = 0; f < NHS; ++f) {
+      if (f >= nh) break;
       T* d = st + f * HN;
       bulk_g2s(d, src[f] + pl + (size_t)ym * N, (unsigned)n0 * row, bj);
       if (n0 < R + 2) bulk_g2s(d + n0 * N, src[f] + pl, (unsigned)(R + 2 - n0) * row, bj);
     }
     if (comp) {
       bulk_g2s(st + NHS * HN, psi + pl + (size_t)y0 * N, rows, bj);
-      bulk_g2s(st + NHS * HN + RN, x + pl + (size_t)y0 * N, rows, bj);
+      if (!first) bulk_g2s(st + NHS * HN + RN, x + pl + (size_t)y0 * N, rows, bj);
     }
   };
 
@@ -509,15 +512,15 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* bo
       for (int u = 0; u < kBulkRows; ++u) {  // own rows: pd_new, and the centre values needed one plane later
         const int jr = tid / Q + RS * u;
         const int o = (jr + 1) * N + x4;
-        V4<T> nv, pv;
+        V4<T> nv, pv = {};
         if (POLY) {
           const V4<T> zv = ld4(st + o);
-          pv = ld4(st + HN + o);
+          if (!first) pv = ld4(st + HN + o);
 #pragma unroll
           for (int e = 0; e < 4; ++e) nv.v[e] = first ? zv.v[e] : zv.v[e] + beta * pv.v[e];
         } else {
           const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o);
-          pv = ld4(st + 2 * HN + o);
+          if (!first) pv = ld4(st + 2 * HN + o);
 #pragma unroll
           for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
         }
@@ -525,18 +528,18 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* bo
         cu_po[u] = pv;
         if (P.pos >= 1 && P.pos <= P.len) {
           cu_psi[u] = ld4(st + NHS * HN + jr * N + x4);
-          cu_x[u] = ld4(st + NHS * HN + RN + jr * N + x4);
+          cu_x[u] = first ? V4<T>{} : ld4(st + NHS * HN + RN + jr * N + x4);
         }
       }
       if (halo) {
         const int o = hr * N + x4;
         V4<T> nv;
         if (POLY) {
-          const V4<T> zv = ld4(st + o), pv = ld4(st + HN + o);
+          const V4<T> zv = ld4(st + o), pv = first ? V4<T>{} : ld4(st + HN + o);
 #pragma unroll
           for (int e = 0; e < 4; ++e) nv.v[e] = first ? zv.v[e] : zv.v[e] + beta * pv.v[e];
         } else {
-          const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = ld4(st + 2 * HN + o);
+          const V4<T> rv = ld4(st + o), dv = ld4(st + HN + o), pv = first ? V4<T>{} : ld4(st + 2 * HN + o);
 #pragma unroll
           for (int e = 0; e < 4; ++e) nv.v[e] = first ? rv.v[e] * dv.v[e] : rv.v[e] * dv.v[e] + beta * pv.v[e];
         }
