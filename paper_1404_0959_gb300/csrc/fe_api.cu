@@ -102,7 +102,7 @@ struct fe_ctx {
   int nblocks = 0;
   int2* dework = nullptr;
   int2* dbwork = nullptr;   // plane-streaming blocks (box, block of box)
-  int nbblocks = 0, bsmem = 0, npart = 0;
+  int nbblocks = 0, bsmem = 0, bcells = 0, npart = 0;
   int ring_ok = 0;          // all N multiples of the 16-byte chunk of the ring kernels
   bool use_bulk = true;     // streamed CG kernel where the boxes allow it
   int unet_tc = 1;          // U-Net stride-1 layers on tcgen05 (1) or warp-level MMA (0)
@@ -144,6 +144,7 @@ struct fe_ctx {
              prm.closure == FE_FOURIER, prm.transonic, prm.n_dust, ring_ok, use_bulk && nbblocks > 0 ? dbwork : nullptr,
              nbblocks, bsmem};
     l.poly = prm.solver == FE_PCG_POLY && !fp64;  // FP64 contexts run Jacobi-PCG
+    l.bcells = bcells;
     return l;
   }
 };
@@ -291,16 +292,21 @@ static int set_tiling(fe_ctx* c, const std::vector<int>& tzb) {
     stream = N >= 64 && N <= 512 && (N & (N - 1)) == 0;
     scells += (long)N * N * N;
   }
+  int bcells = 0;
   if (stream) {
-    int maxN = 0;
-    for (int b = 0; b < c->nb; ++b) maxN = std::max(maxN, c->hbox[b].N);
-    bsmem = c->fp64 ? bulk_cg_prepare<double>(maxN) : bulk_cg_prepare<float>(maxN);
-    const int per_sm = bsmem <= 0 ? 0 : c->fp64 ? bulk_cg_blocks_per_sm<double>(bsmem) : bulk_cg_blocks_per_sm<float>(bsmem);
+    int maxN = 0, minN = 1 << 30;
+    for (int b = 0; b < c->nb; ++b) maxN = std::max(maxN, c->hbox[b].N), minN = std::min(minN, c->hbox[b].N);
+    const bool poly = c->prm.solver == FE_PCG_POLY;
+    bcells = c->fp64 ? bulk_cg_cells<double>(minN, maxN, poly) : bulk_cg_cells<float>(minN, maxN, poly);
+    bsmem = c->fp64 ? bulk_cg_prepare<double>(maxN, bcells, poly) : bulk_cg_prepare<float>(maxN, bcells, poly);
+    const int per_sm = bsmem <= 0 ? 0
+                       : c->fp64 ? bulk_cg_blocks_per_sm<double>(bsmem, bcells)
+                                 : bulk_cg_blocks_per_sm<float>(bsmem, bcells);
     stream = per_sm > 0;
     const long grid = (long)per_sm * c->nsm;
     for (int b = 0; b < c->nb && stream; ++b) {
       BoxDev& B = c->hbox[b];
-      const long N = B.N, planes = bulk_cg_pairs(B.N);
+      const long N = B.N, planes = bulk_cg_pairs(B.N, bcells);
       long nb = (grid * N * N * N + scells - 1) / scells;
       nb = std::max(1L, std::min(nb, planes / 4));
       B.btile0 = (int)bwork.size();
@@ -311,6 +317,7 @@ static int set_tiling(fe_ctx* c, const std::vector<int>& tzb) {
   if (!stream) {
     bwork.clear();
     bsmem = 0;
+    bcells = 0;
     for (int b = 0; b < c->nb; ++b) c->hbox[b].btile0 = c->hbox[b].bntiles = 0;
   }
   CK(cudaStreamSynchronize(c->st));
@@ -322,6 +329,7 @@ static int set_tiling(fe_ctx* c, const std::vector<int>& tzb) {
     CK(cudaMemcpyAsync(c->dbwork, bwork.data(), bwork.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   c->nbblocks = (int)bwork.size();
   c->bsmem = bsmem;
+  c->bcells = bcells;
   if ((int)work.size() != c->nblocks || (int)ework.size() != c->neblocks || !c->dpart || need > c->npart) {
     cudaFree(c->dwork);
     cudaFree(c->dework);

@@ -602,6 +602,7 @@ struct Launch {
   int* rstart = nullptr;  // right-hand-side kernels: also start the refined solve (outer counter)
   int ysum = -1;          // two-way coupling: slot of the dust loading sum_j Y_j^n (-1: one-way)
   int poly = 0;           // streamed CG with the Neumann polynomial preconditioner (needs bwork)
+  int bcells = 0;         // cells per block of the streamed CG kernels (kBulkCells or kBulkCellsPoly)
 };
 
 // Launch `call` (a kernel launch statement) under instrumentation id kid.
@@ -657,9 +658,10 @@ template <typename V> int rlaunch_div(const Launch& L, int u0, int with_dt = 0);
 template <typename V> int rlaunch_fe_cell(const Launch& L, int s, int u0, int rhos, int ps, int es, int tmode);
 template <typename V> int rlaunch_fe_face(const Launch& L, int u0, int phi0);
 template <typename V> int rlaunch_rhs(const Launch& L, int s, int rhop, int pp);
-template <typename V> int bulk_cg_prepare(int N);               // dynamic smem of the streamed CG kernel (0: unusable)
-template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes);
-int bulk_cg_pairs(int N);  // (row group, plane) pairs of the streamed CG kernel for an N^3 box
+template <typename V> int bulk_cg_cells(int minN, int maxN, bool poly);  // cells per block of the streamed CG kernels
+template <typename V> int bulk_cg_prepare(int N, int cells, bool poly);  // their dynamic smem (0: unusable)
+template <typename V> int bulk_cg_blocks_per_sm(int smem_bytes, int cells);
+int bulk_cg_pairs(int N, int cells);  // (row group, plane) pairs of the streamed CG kernels for an N^3 box
 template <typename V> void launch_cg_dir(const Launch& L);
 template <typename V> void launch_true_res(const Launch& L, int xslot);
 template <typename V> void launch_bicg_init(const Launch& L);

@@ -410,34 +410,39 @@ __global__ void __launch_bounds__(NTHR, sizeof(T) == 4 ? FE_DM_MINB : 2) kz_cg_d
 #endif
 constexpr int kBulkStages = FE_BULK_STAGES;
 
-template <typename T>
-__host__ __device__ constexpr int bulk_stage_elems(int N) {
-  return 3 * (kBulkCells + 2 * N) + 2 * kBulkCells;
+// One ring stage of a kernel: nh streams with their two y-halo rows and no
+// own-row-only streams, for blocks of `cells` cells per plane of edge N.
+__host__ __device__ constexpr int bulk_stage_elems(int N, int cells, int nh, int no) {
+  return nh * (cells + 2 * N) + no * cells;
 }
-template <typename T>
-__host__ __device__ constexpr int bulk_ring_elems(int N) {
-  return 4 * (kBulkCells + 2 * N);
+__host__ __device__ constexpr int bulk_ring_elems(int N, int cells) {
+  return 4 * (cells + 2 * N);
 }
-// dynamic shared memory of kb_cg_dirmatvec for edge N
+// Dynamic shared memory of the streamed CG kernels of one solver for edge N:
+// the largest stage among them (Jacobi: kb_cg_dirmatvec<T, false>, three halo
+// streams and two own; polynomial: kb_cg_rpoly<T, false>, three and one).
 template <typename T>
-int bulk_smem_bytes(int N) {
-  return 128 + (kBulkStages * bulk_stage_elems<T>(N) + bulk_ring_elems<T>(N)) * (int)sizeof(T);
+int bulk_smem_bytes(int N, int cells, bool poly) {
+  const int se = poly ? bulk_stage_elems(N, cells, 3, 1) : bulk_stage_elems(N, cells, 3, 2);
+  return 128 + (kBulkStages * se + bulk_ring_elems(N, cells)) * (int)sizeof(T);
 }
 
 // POLY: the direction is pd_new = z + beta pd_old with z = P r from kb_cg_rpoly (first-order Neumann
 // polynomial preconditioner), streamed with y-halo rows in place of r and D^{-1}.
-template <typename T, bool POLY>
+template <typename T, bool POLY, int CELLS>
 __global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* boxes, const int2* bwork, double* part) {
+  constexpr int kBulkRows = bulk_rows<CELLS>();
   const int2 w = bwork[blockIdx.x];
   const BoxDev& B = boxes[w.x];
   if (box_done(B)) return;
   extern __shared__ __align__(128) unsigned char zsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(zsm);
   const int N = B.N;
-  const BulkGeom Gm(N, w.y, B.bntiles);
+  const BulkGeom Gm(N, w.y, B.bntiles, CELLS);
   const int R = Gm.R, RN = R * N, HN = (R + 2) * N;
   T* stage0 = reinterpret_cast<T*>(zsm + 128);
-  const int SE = bulk_stage_elems<T>(N);
+  constexpr int NHS = POLY ? 2 : 3;  // streams with y-halo rows
+  const int SE = bulk_stage_elems(N, CELLS, NHS, 2);
   T* ring = stage0 + kBulkStages * SE;
   const int tid = threadIdx.x;
   const int odd = ((int)B.sc[SC_ITERS]) & 1;
@@ -454,7 +459,6 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_dirmatvec(const BoxDev* bo
   const bool first = B.sc[SC_ITERS] == 0.0;  // pd_new = D^{-1} r (POLY: z), x = 0 whatever pd_old and x hold
   const int nseq = Gm.count();
   const size_t NN = (size_t)N * N;
-  constexpr int NHS = POLY ? 2 : 3;  // streams with y-halo rows
 
   // stage layout: r | dinv | pd_old (POLY: z | pd_old) (R + 2 rows each, halo rows first and last) | psi | x (R rows)
   auto issue = [&](int j) {
@@ -694,18 +698,20 @@ __global__ void __launch_bounds__(NTHR) k_cg_rupdate(const BoxDev* boxes, const 
 // ||r_new||^2 and the CG bookkeeping.  r alternates between K_R and K_RB by the parity of the iteration
 // count (neighbouring blocks read the old residual as halo).  START: the first residual of an inner
 // solve (alpha = 0, r stays in K_R): z and <r, z> only, no iteration counted.
-template <typename T, bool START>
+template <typename T, bool START, int CELLS>
 __global__ void __launch_bounds__(kBulkThreads) kb_cg_rpoly(const BoxDev* boxes, const int2* bwork, double* part, int* active) {
+  constexpr int kBulkRows = bulk_rows<CELLS>();
   const int2 w = bwork[blockIdx.x];
   const BoxDev& B = boxes[w.x];
   if (box_done(B)) return;
   extern __shared__ __align__(128) unsigned char zsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(zsm);
   const int N = B.N;
-  const BulkGeom Gm(N, w.y, B.bntiles);
+  const BulkGeom Gm(N, w.y, B.bntiles, CELLS);
   const int R = Gm.R, HN = (R + 2) * N, RN = R * N;
   T* stage0 = reinterpret_cast<T*>(zsm + 128);
-  const int SE = bulk_stage_elems<T>(N);
+  constexpr int NHS = START ? 2 : 3;  // streams with y-halo rows: r, D^{-1} (and q)
+  const int SE = bulk_stage_elems(N, CELLS, NHS, 1);
   T* ring = stage0 + kBulkStages * SE;
   const int tid = threadIdx.x;
   const int odd = START ? 0 : ((int)B.sc[SC_ITERS]) & 1;  // iterations before this one
@@ -720,7 +726,6 @@ __global__ void __launch_bounds__(kBulkThreads) kb_cg_rpoly(const BoxDev* boxes,
   const T lapc = T(0.5) * dt * ih * ih;
   const int nseq = Gm.count();
   const size_t NN = (size_t)N * N;
-  constexpr int NHS = START ? 2 : 3;  // streams with y-halo rows: r, D^{-1} (and q)
   constexpr int FD = NHS - 1;         // stage index of D^{-1}
 
   // stage layout: r | q | D^{-1} (START: r | D^{-1}) (R + 2 rows each) | psi (R rows)
@@ -1865,10 +1870,15 @@ template <typename T> void launch_cg_update(const Launch& L) {
 }
 template <typename T> void launch_cg_fused(const Launch& L) {
   if (L.poly) {  // polynomial preconditioner: direction from z, residual update forms the next z
-    if (L.bwork) {
-      FE_LAUNCH(L, KID_CG_DIRMATVEC,
-                (kb_cg_dirmatvec<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
-      FE_LAUNCH(L, KID_CG_RUPDATE, (kb_cg_rpoly<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+    if (L.bwork && L.bcells == kBulkCellsPoly) {
+      FE_LAUNCH(L, KID_CG_DIRMATVEC, (kb_cg_dirmatvec<T, true, kBulkCellsPoly><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                         L.boxes, L.bwork, L.part)));
+      FE_LAUNCH(L, KID_CG_RUPDATE, (kb_cg_rpoly<T, false, kBulkCellsPoly><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                       L.boxes, L.bwork, L.part, L.active)));
+    } else if (L.bwork) {
+      FE_LAUNCH(L, KID_CG_DIRMATVEC, (kb_cg_dirmatvec<T, true, kBulkCells><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                         L.boxes, L.bwork, L.part)));
+      FE_LAUNCH(L, KID_CG_RUPDATE, (kb_cg_rpoly<T, false, kBulkCells><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
                                        L.boxes, L.bwork, L.part, L.active)));
     } else {
       FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T, true><<<GRID>>>(L.boxes, L.work, L.part)));
@@ -1877,8 +1887,8 @@ template <typename T> void launch_cg_fused(const Launch& L) {
     return;
   }
   if (L.bwork)
-    FE_LAUNCH(L, KID_CG_DIRMATVEC,
-              (kb_cg_dirmatvec<T, false><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part)));
+    FE_LAUNCH(L, KID_CG_DIRMATVEC, (kb_cg_dirmatvec<T, false, kBulkCells><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                       L.boxes, L.bwork, L.part)));
   else
     FE_LAUNCH(L, KID_CG_DIRMATVEC, (kz_cg_dirmatvec<T, false><<<GRID>>>(L.boxes, L.work, L.part)));
   FE_LAUNCH(L, KID_CG_RUPDATE, (k_cg_rupdate<T><<<EGRID>>>(L.boxes, L.ework, L.part, L.active)));
@@ -1886,9 +1896,12 @@ template <typename T> void launch_cg_fused(const Launch& L) {
 // First polynomial-preconditioned residual z = P r of an inner solve and <r, z> (nothing without it)
 template <typename T> void launch_cg_start(const Launch& L) {
   if (!L.poly) return;
-  if (L.bwork)
-    FE_LAUNCH(L, KID_CG_START,
-              (kb_cg_rpoly<T, true><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(L.boxes, L.bwork, L.part, L.active)));
+  if (L.bwork && L.bcells == kBulkCellsPoly)
+    FE_LAUNCH(L, KID_CG_START, (kb_cg_rpoly<T, true, kBulkCellsPoly><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                   L.boxes, L.bwork, L.part, L.active)));
+  else if (L.bwork)
+    FE_LAUNCH(L, KID_CG_START, (kb_cg_rpoly<T, true, kBulkCells><<<L.nbblocks, kBulkThreads, L.bsmem, L.st>>>(
+                                   L.boxes, L.bwork, L.part, L.active)));
   else
     FE_LAUNCH(L, KID_CG_START, (kz_cg_rpoly<T, true><<<GRID>>>(L.boxes, L.work, L.part, L.active)));
 }
@@ -1954,28 +1967,48 @@ template <typename T> void launch_mix_finish(const Launch& L) {
   FE_LAUNCH(L, KID_MIX_FIN, (k_mix_finish<T><<<EGRID>>>(L.boxes, L.ework, 0)));
 }
 
-// Dynamic shared memory of the streamed CG kernel for edge N (sets the
-// kernel's opt-in limit); 0 if it does not fit.
+// Cells per block of the streamed CG kernels of one solver for the box edges
+// minN..maxN: the larger polynomial block where every box has at least
+// sixteen row groups (enough (group, plane) pairs per block that the two
+// z-halo planes of each segment stay a small share) and its shared memory
+// fits, else kBulkCells.
 template <typename T>
-int bulk_cg_prepare(int N) {
-  const int bytes = bulk_smem_bytes<T>(N);
+int bulk_cg_cells(int minN, int maxN, bool poly) {
+  if (poly && kBulkCellsPoly != kBulkCells && minN * minN >= 16 * kBulkCellsPoly &&
+      bulk_smem_bytes<T>(maxN, kBulkCellsPoly, true) <= 227 * 1024)
+    return kBulkCellsPoly;
+  return kBulkCells;
+}
+template <typename T, int CELLS>
+static bool bulk_set_smem(int bytes) {
+  return cudaFuncSetAttribute(kb_cg_dirmatvec<T, false, CELLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(kb_cg_dirmatvec<T, true, CELLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(kb_cg_rpoly<T, false, CELLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(kb_cg_rpoly<T, true, CELLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess;
+}
+// Dynamic shared memory of the streamed CG kernels of one solver for edge N
+// and `cells` per block (sets the kernels' opt-in limit); 0 if it does not fit.
+template <typename T>
+int bulk_cg_prepare(int N, int cells, bool poly) {
+  const int bytes = bulk_smem_bytes<T>(N, cells, poly);
   if (bytes > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(kb_cg_dirmatvec<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(kb_cg_dirmatvec<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(kb_cg_rpoly<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-      cudaFuncSetAttribute(kb_cg_rpoly<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
-    return 0;
-  return bytes;
+  const bool ok = cells == kBulkCellsPoly ? bulk_set_smem<T, kBulkCellsPoly>(bytes) : bulk_set_smem<T, kBulkCells>(bytes);
+  return ok ? bytes : 0;
 }
 // (row group, plane) pairs of an N^3 box
-int bulk_cg_pairs(int N) { return N * (N / (kBulkCells / N)); }
+int bulk_cg_pairs(int N, int cells) { return N * (N / (cells / N)); }
 template <typename T>
-int bulk_cg_blocks_per_sm(int bytes) {
+int bulk_cg_blocks_per_sm(int bytes, int cells) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T, false>, kBulkThreads, bytes) != cudaSuccess) return 0;
-  return nb;
+  const cudaError_t e =
+      cells == kBulkCellsPoly
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_rpoly<T, false, kBulkCellsPoly>, kBulkThreads, bytes)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cg_dirmatvec<T, false, kBulkCells>, kBulkThreads, bytes);
+  return e == cudaSuccess ? nb : 0;
 }
 
 #define INST(T)                                                  \
@@ -1984,8 +2017,9 @@ int bulk_cg_blocks_per_sm(int bytes) {
   template void launch_cg_update<T>(const Launch&);              \
   template void launch_cg_fused<T>(const Launch&);               \
   template void launch_cg_xfinal<T>(const Launch&);              \
-  template int bulk_cg_prepare<T>(int);                          \
-  template int bulk_cg_blocks_per_sm<T>(int);                    \
+  template int bulk_cg_prepare<T>(int, int, bool);              \
+  template int bulk_cg_cells<T>(int, int, bool);                 \
+  template int bulk_cg_blocks_per_sm<T>(int, int);               \
   template void launch_cg_dir<T>(const Launch&);                 \
   template void launch_true_res<T>(const Launch&, int);          \
   template void launch_bicg_init<T>(const Launch&);              \

@@ -64,19 +64,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int ca
 #define FE_BULK_THREADS 256
 #endif
 constexpr int kBulkThreads = FE_BULK_THREADS;
+// Two block sizes: kBulkCells for the Jacobi iteration (its stage of five
+// streams), kBulkCellsPoly for the polynomial iteration where the box edge
+// lets a group of that many cells fit (fewer, larger plane steps).
 #ifndef FE_BULK_CELLS
 #define FE_BULK_CELLS 2048
 #endif
+#ifndef FE_BULK_CELLS_POLY
+#define FE_BULK_CELLS_POLY 4096
+#endif
 constexpr int kBulkCells = FE_BULK_CELLS;
-constexpr int kBulkRows = kBulkCells / (4 * kBulkThreads);
-static_assert(kBulkRows >= 1 && 4 * kBulkThreads * kBulkRows == kBulkCells, "bulk block shape");
+constexpr int kBulkCellsPoly = FE_BULK_CELLS_POLY;
+// rows of four cells per thread for a block of `cells` cells per plane
+template <int CELLS>
+__host__ __device__ constexpr int bulk_rows() {
+  return CELLS / (4 * kBulkThreads);
+}
+static_assert(bulk_rows<kBulkCells>() >= 1 && 4 * kBulkThreads * bulk_rows<kBulkCells>() == kBulkCells,
+              "bulk block shape");
+static_assert(bulk_rows<kBulkCellsPoly>() >= 1 && 4 * kBulkThreads * bulk_rows<kBulkCellsPoly>() == kBulkCellsPoly,
+              "bulk block shape (polynomial iteration)");
 
 struct BulkGeom {
   int N, R, G, Q;  // box edge, rows per group, row groups, threads per row (N / 4)
   int a, b;        // this block's range of (group, plane) pairs, group-major
-  __device__ __forceinline__ BulkGeom(int N_, int blk, int nblk) {
+  __device__ __forceinline__ BulkGeom(int N_, int blk, int nblk, int cells) {
     N = N_;
-    R = kBulkCells / N;
+    R = cells / N;
     G = N / R;
     Q = N / 4;
     const long tot = (long)G * N;
