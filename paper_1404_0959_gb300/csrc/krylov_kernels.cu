@@ -230,9 +230,11 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
 }
 
 // Planes requested ahead by the z-marching Krylov kernels, minimum resident
-// blocks per SM of the fused CG kernel (FP32), and shared-memory plane
-// buffers (2: the next plane is staged while the current one is read, one
-// barrier per plane).
+// blocks per SM of the fused CG kernel (FP32), shared-memory plane buffers
+// (2: the next plane is staged while the current one is read, one barrier per
+// plane), and minimum resident blocks per SM of the column-pair refinement
+// boundary (5: 96 registers instead of 122, one more block of four warps per
+// SM to cover its global-load latency).
 #ifndef FE_KPF
 #define FE_KPF 2
 #endif
@@ -241,6 +243,9 @@ __global__ void __launch_bounds__(NTHR) k_cg_matvec(const BoxDev* boxes, const i
 #endif
 #ifndef FE_DM_NBUF
 #define FE_DM_NBUF 2
+#endif
+#ifndef FE_REFINE_MINB
+#define FE_REFINE_MINB 5
 #endif
 constexpr int KPF = FE_KPF;
 constexpr int kDmBuf = FE_DM_NBUF;
@@ -1550,7 +1555,7 @@ __global__ void __launch_bounds__(NTHR) kz_refine(const BoxDev* boxes, const int
 // with the polynomial preconditioner's own pass (kb/kz_cg_rpoly<T, true>), so
 // D^{-1} is not read and <r, D^{-1} r> not formed.
 template <typename T>
-__global__ void __launch_bounds__(RNT) kp_refine(const BoxDev* boxes, const int2* work, double* part,
+__global__ void __launch_bounds__(RNT, FE_REFINE_MINB) kp_refine(const BoxDev* boxes, const int2* work, double* part,
                                                  int* outer_active, int* active, int poly) {
   const TileXYZ t = tile_xyz(boxes, work);
   const BoxDev& B = boxes[t.box];
@@ -1972,9 +1977,12 @@ template <typename T> void launch_mix_finish(const Launch& L) {
 // sixteen row groups (enough (group, plane) pairs per block that the two
 // z-halo planes of each segment stay a small share) and its shared memory
 // fits, else kBulkCells.
+#ifndef FE_BULK_POLY_MIN_GROUPS
+#define FE_BULK_POLY_MIN_GROUPS 16
+#endif
 template <typename T>
 int bulk_cg_cells(int minN, int maxN, bool poly) {
-  if (poly && kBulkCellsPoly != kBulkCells && minN * minN >= 16 * kBulkCellsPoly &&
+  if (poly && kBulkCellsPoly != kBulkCells && minN * minN >= FE_BULK_POLY_MIN_GROUPS * kBulkCellsPoly &&
       bulk_smem_bytes<T>(maxN, kBulkCellsPoly, true) <= 227 * 1024)
     return kBulkCellsPoly;
   return kBulkCells;
