@@ -28,9 +28,6 @@ namespace fe {
 #ifndef FE_RING_MINB_PRED
 #define FE_RING_MINB_PRED 3
 #endif
-#ifndef FE_RING_MINB_RHS
-#define FE_RING_MINB_RHS 1
-#endif
 #ifndef FE_RING_OFF
 #define FE_RING_OFF 0u  // ring kernels left out (bits of RingKernel): their z-marching versions run
 #endif
@@ -809,7 +806,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes,
 template <typename T>
 using RhsPlan = RingPlan<T, kA, 5, 0, 3>;  // rho', HbyA0..2, p | | rho^n, D phi^n [, D^{-1}]
 template <typename T>
-__global__ void __launch_bounds__(RNT, FE_RING_MINB_RHS) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
+__global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
                                                             int pp, double* part, int* rstart, int* active, int poly) {
   RING_PROLOGUE(RhsPlan<T>);
   R.gs[0] = Fr<T>(B, rhop);
