@@ -87,9 +87,11 @@ static_assert(bulk_rows<kBulkCellsPoly>() >= 1 && 4 * kBulkThreads * bulk_rows<k
 
 struct BulkGeom {
   int N, R, G, Q;  // box edge, rows per group, row groups, threads per row (N / 4)
+  int lgN;         // log2 N (streamed boxes have power-of-two edges)
   int a, b;        // this block's range of (group, plane) pairs, group-major
   __device__ __forceinline__ BulkGeom(int N_, int blk, int nblk, int cells) {
     N = N_;
+    lgN = __ffs(N) - 1;
     R = cells / N;
     G = N / R;
     Q = N / 4;
@@ -114,7 +116,7 @@ struct BulkPos {
 __device__ __forceinline__ BulkPos bulk_pos(const BulkGeom& Gm, int i) {
   int s = Gm.a;
   while (true) {
-    const int g = s / Gm.N, k0 = s - g * Gm.N;
+    const int g = s >> Gm.lgN, k0 = s & (Gm.N - 1);
     const int e = min(Gm.b, (g + 1) * Gm.N);
     const int len = e - s;
     if (i < len + 2) {

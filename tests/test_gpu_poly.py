@@ -109,6 +109,39 @@ def test_poly_solve_reaches_fp64_residual_and_oracle_solution(fe, N):
     s.close()
 
 
+def test_poly_solve_256_streamed_blocks_match_oracle(fe):
+    """N = 256: the streamed polynomial iteration in its 4096-cell blocks (16 rows of a plane per
+    block, four rows of four cells per thread), standalone, against the oracle's Neumann-preconditioned
+    PCG solution; then the same solve on the z-marching iteration."""
+    import torch
+    N = 256
+    rho = f32(1.0 + 0.02 * random_vector(N, 11))
+    prm0 = piso.Params(N=N)
+    st = piso.make_state(prm0, rho, [np.zeros((N, N, N))] * 3, [np.full((N, N, N), 0.01)])
+    st = {k: ([f32(c) for c in v] if isinstance(v, list) else (f32(v) if isinstance(v, np.ndarray) else v))
+          for k, v in st.items()}
+    psi = f32(np.float32(st["rho"]) / (np.float32(1.4) * np.float32(st["p"])))
+    dt = 0.02
+    b = f32(random_vector(N, 5))
+    matvec, dg = piso.helmholtz(prm0, psi, dt)
+    xr, _, _, _ = krylov.pcg(matvec, b, dg, 1e-13, 500, precond=krylov.neumann1(matvec, dg))
+    bt = torch.tensor(b, dtype=torch.float32, device="cuda")
+    iters = []
+    for streaming in (True, False):
+        s = fe.Solver([dict(N=N, nu=0.005, tau_p=[0.05], Y0=[0.01])], precision=fe.FE_FP32_MIXED,
+                      solver=fe.FE_PCG_POLY)
+        s.load_state(0, st)
+        s.use_plane_streaming(streaming)
+        assert s.plane_streaming_active() == streaming
+        code, x, info = s.solve_pressure(0, bt, dt, 1e-10, 500)
+        assert code == fe.FE_OK
+        assert info.rel_res_true <= 1e-10
+        assert rel(x.cpu().numpy(), xr) < 1e-6
+        iters.append(info.iters)
+        s.close()
+    assert abs(iters[0] - iters[1]) <= 1, iters
+
+
 def test_poly_graph_steps_equal_host_steps(fe):
     out = []
     for graphs in (False, True):
