@@ -31,7 +31,19 @@ namespace fe {
 #ifndef FE_RING_OFF
 #define FE_RING_OFF 0u  // ring kernels left out (bits of RingKernel): their z-marching versions run
 #endif
+#ifndef FE_RING_A_RHS
+#define FE_RING_A_RHS 3
+#endif
+#ifndef FE_RING_A_DIV
+#define FE_RING_A_DIV 3
+#endif
 constexpr int kA = FE_RING_A, kA1 = FE_RING_A_LIGHT;
+// Lookahead of the right-hand side and the divergence: three planes in flight.  The right-hand side is
+// held to three resident blocks by its registers whatever its rings take, and the divergence keeps six
+// blocks of its small rings (seven with two planes), so both gain bytes in flight per SM (measured at
+// 256^3: divergence 0.277 -> 0.248 ms, right-hand side 0.360 -> 0.346 ms per step; four planes for the
+// divergence 0.255).
+constexpr int kArhs = FE_RING_A_RHS, kAdiv = FE_RING_A_DIV;
 
 template <typename T>
 __device__ __forceinline__ T* Fr(const BoxDev& B, int slot) {
@@ -763,7 +775,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_fe_face(const BoxDev* bo
 
 // ---- velocity divergence div = sum_m Gc_m(u_m) --------------------------------------------------------
 template <typename T>
-using DivPlan = RingPlan<T, kA, 3, 0, 0>;  // u0..2
+using DivPlan = RingPlan<T, kAdiv, 3, 0, 0>;  // u0..2
 // with_dt: also max_i sum_d |u_d| over the box and the adaptive time step
 // from it (the first divergence of a step reads u^n, the field k_dt reads).
 template <typename T>
@@ -804,7 +816,7 @@ __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_div(const BoxDev* boxes,
 // starts the refined solve: ||b||^2 and <b, D^{-1} b> into the refinement and
 // CG scalars (the solution pairs start as zero by the outer-step count).
 template <typename T>
-using RhsPlan = RingPlan<T, kA, 5, 0, 3>;  // rho', HbyA0..2, p | | rho^n, D phi^n [, D^{-1}]
+using RhsPlan = RingPlan<T, kArhs, 5, 0, 3>;  // rho', HbyA0..2, p | | rho^n, D phi^n [, D^{-1}]
 template <typename T>
 __global__ void __launch_bounds__(RNT, FE_RING_MINB) kr_rhs(const BoxDev* boxes, const int2* work, int s, int rhop,
                                                             int pp, double* part, int* rstart, int* active, int poly) {
